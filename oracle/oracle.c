@@ -1,0 +1,599 @@
+/*
+ * FP64 CPU oracle for the MC-MD / MDAS membrane sampler of Cherniavskyi,
+ * Fathizadeh, Elber and Tieleman (arXiv:2005.08348).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this code.  It shares nothing with
+ * the CUDA library: no headers, helpers, tables or constants.
+ *
+ * Everything is plain double precision, written in the order the paper (or
+ * the stated reading of it) defines the quantity; there is no blocking or
+ * reordering beyond what a definition states.  Units: nm, ps, kJ/mol, amu, e.
+ *
+ * Passages followed:
+ *   - Sec. 3 (Methods): Lennard-Jones with a potential-shift modifier cut at
+ *     1.1 nm, reaction-field electrostatics with relative permittivity 15,
+ *     velocity-rescaling thermostat (Bussi et al. 2007) with two coupling
+ *     groups (membrane, solvent).
+ *   - Sec. 2, Eq. 1: Metropolis acceptance of a lipid-type exchange, the
+ *     coordinates left unchanged and only the potential parameters swapped.
+ *   - Sec. 2, linear path U(lambda) = (1-lambda) U_A + lambda U_B, Eq. 2
+ *     (work of the alchemical trajectory) and Eq. 3 (its acceptance).
+ *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ *     Box-Muller normals, Marsaglia-Tsang gamma variates (ACM TOMS 2000).
+ *
+ * Readings of points the paper leaves open (listed in the design notes):
+ * Delta U = U_after - U_before; eps_rf = infinity by default; only 1-2 bonded
+ * pairs are excluded; every bead weighs 72 amu; the thermostat uses the
+ * kinetic energy of v(t - dt/2); positions are 32-bit fractions of the box.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_BOLTZ 0.0083144626
+#define OR_COUL 138.935458
+#define OR_TWO32 4294967296.0
+
+enum { OR_TAG_THERMO = 1, OR_TAG_SWAP = 2, OR_TAG_MDAS_PAIR = 3, OR_TAG_MDAS_ACC = 4,
+       OR_TAG_AT_THERMO = 5 };
+
+typedef struct {
+    int n_beads, n_lipids, bpl, n_bt, n_lt;
+    double box[3];
+    const int *lipid_first;     /* [n_lipids] */
+    const int *lbt;             /* [n_lt * bpl] */
+    int water_bt;
+    const double *eps, *sigma;  /* [n_bt * n_bt] */
+    const double *charge;       /* [n_bt] */
+    const int *bonds; int nb;   /* [nb * 2] local indices */
+    const int *angles; int na;  /* [na * 3] */
+    double kb, b0, ktheta, theta0_deg;
+    double rc, eps_r, eps_rf;   /* eps_rf <= 0: infinity */
+    double temperature, dt, tau_t, mass;
+    const int *tc_group;        /* [n_beads], groups 0/1 */
+    uint64_t seed; uint32_t system_id;
+} or_sys;
+
+/* ---------------------------------------------------------------- Philox */
+
+/* Philox4x32-10 as published by Salmon et al. (SC'11): ten rounds of two
+ * 32x32->64 multiplies with a Weyl-sequence key schedule. */
+void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+static void draw(const or_sys *s, uint32_t i0, uint32_t i1, uint32_t tag, uint32_t j, uint32_t w[4])
+{
+    uint32_t key[2] = {(uint32_t)s->seed ^ s->system_id, (uint32_t)(s->seed >> 32)};
+    uint32_t ctr[4] = {i0, i1, tag, j};
+    or_philox(ctr, key, w);
+}
+
+/* uniform in (0, 1]: 53 bits taken from two words */
+static double u53(uint32_t a, uint32_t b)
+{
+    uint64_t k = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+    return ((double)k + 1.0) * (1.0 / 9007199254740992.0);
+}
+
+double or_uniform(uint32_t a, uint32_t b) { return u53(a, b); }
+
+/* Box-Muller, cosine branch */
+static double normal_from(const uint32_t w[4])
+{
+    double u1 = u53(w[0], w[1]), u2 = u53(w[2], w[3]);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* Marsaglia-Tsang gamma(shape a >= 1, scale 1); iteration t uses Philox
+ * draws j0 + 2t (normal) and j0 + 2t + 1 (uniform). */
+static double gamma_mt(const or_sys *s, uint32_t i0, uint32_t i1, uint32_t tag, double a, uint32_t j0)
+{
+    double d = a - 1.0 / 3.0;
+    double c = 1.0 / sqrt(9.0 * d);
+    for (int t = 0; t < 32; ++t) {
+        uint32_t w[4];
+        draw(s, i0, i1, tag, j0 + 2 * t, w);
+        double x = normal_from(w);
+        double v = 1.0 + c * x;
+        if (v <= 0.0) continue;
+        v = v * v * v;
+        draw(s, i0, i1, tag, j0 + 2 * t + 1, w);
+        double u = u53(w[0], w[1]);
+        if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+    }
+    return a; /* never reached in practice; both sides fall back to the mean */
+}
+
+/* chi-squared with k >= 2 degrees of freedom: 2 * gamma(k / 2) */
+double or_chi2(const or_sys *s, uint32_t i0, uint32_t i1, uint32_t tag, int k)
+{
+    return 2.0 * gamma_mt(s, i0, i1, tag, 0.5 * k, 1);
+}
+
+/* Bussi-Donadio-Parrinello (2007) velocity-rescaling factor for one coupling
+ * group: K kinetic energy, nf degrees of freedom, kt target kinetic energy
+ * (nf kT / 2); draws R1 (Philox call 0) and S ~ chi2(nf - 1) (calls >= 1). */
+double or_bussi_alpha(const or_sys *s, double K, int nf, double kt, uint32_t i0, uint32_t i1, uint32_t tag)
+{
+    if (s->tau_t <= 0.0 || K <= 0.0 || nf < 3) return 1.0;
+    double c = exp(-s->dt / s->tau_t);
+    uint32_t w[4];
+    draw(s, i0, i1, tag, 0, w);
+    double r1 = normal_from(w);
+    double S = or_chi2(s, i0, i1, tag, nf - 1);
+    double a = sqrt(c * K) + r1 * sqrt((1.0 - c) * kt / nf);
+    double knew = a * a + (1.0 - c) * (kt / nf) * S;
+    return sqrt(knew / K);
+}
+
+/* ------------------------------------------------------------ topology */
+
+static int lipid_of(const or_sys *s, int i)
+{
+    /* lipids are contiguous blocks of bpl beads in lipid order, water after */
+    int nl = s->n_lipids;
+    if (nl == 0 || i >= s->lipid_first[nl - 1] + s->bpl) return -1;
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (s->lipid_first[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* per-bead type from the lipid-type array */
+void or_bead_types(const or_sys *s, const int *ltype, int *bt)
+{
+    for (int i = 0; i < s->n_beads; ++i) bt[i] = s->water_bt;
+    for (int l = 0; l < s->n_lipids; ++l)
+        for (int k = 0; k < s->bpl; ++k)
+            bt[s->lipid_first[l] + k] = s->lbt[ltype[l] * s->bpl + k];
+}
+
+/* 1-2 bonded pairs are excluded from the nonbonded sum */
+static int excluded(const or_sys *s, int i, int j)
+{
+    int li = lipid_of(s, i);
+    if (li < 0 || li != lipid_of(s, j)) return 0;
+    int ki = i - s->lipid_first[li], kj = j - s->lipid_first[li];
+    for (int b = 0; b < s->nb; ++b) {
+        int p = s->bonds[2 * b], q = s->bonds[2 * b + 1];
+        if ((p == ki && q == kj) || (p == kj && q == ki)) return 1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------ geometry */
+
+static void position(const or_sys *s, const uint32_t *pu, int i, double x[3])
+{
+    for (int d = 0; d < 3; ++d) x[d] = (double)pu[3 * i + d] * (s->box[d] / OR_TWO32);
+}
+
+/* minimum-image separation r_i - r_j in a rectangular periodic box */
+static void separation(const or_sys *s, const uint32_t *pu, int i, int j, double d[3])
+{
+    double xi[3], xj[3];
+    position(s, pu, i, xi);
+    position(s, pu, j, xj);
+    for (int k = 0; k < 3; ++k) {
+        double v = xi[k] - xj[k];
+        v -= s->box[k] * nearbyint(v / s->box[k]);
+        d[k] = v;
+    }
+}
+
+/* ------------------------------------------------------ pair potential */
+
+/* Energy of one pair at distance r for bead types (ti, tj) and
+ * -dU/dr / r (the factor multiplying r_i - r_j in the force on i).
+ * LJ: 4 eps [(s/r)^12 - (s/r)^6] minus its value at rc (potential shift).
+ * RF: f qi qj / eps_r (1/r + k_rf r^2 - c_rf), k_rf = (eps_rf - eps_r) /
+ * ((2 eps_rf + eps_r) rc^3), c_rf = 1/rc + k_rf rc^2 (eps_rf = inf:
+ * k_rf = 1/(2 rc^3)).  Split into its LJ and RF parts. */
+static void pair_terms(const or_sys *s, int ti, int tj, double r, double *ulj, double *urf, double *fscal)
+{
+    double eps = s->eps[ti * s->n_bt + tj], sig = s->sigma[ti * s->n_bt + tj];
+    double qq = s->charge[ti] * s->charge[tj];
+    double rc = s->rc;
+    double sr6 = pow(sig / r, 6), sr12 = sr6 * sr6;
+    double sc6 = pow(sig / rc, 6), sc12 = sc6 * sc6;
+    *ulj = 4.0 * eps * (sr12 - sr6) - 4.0 * eps * (sc12 - sc6);
+    double krf = (s->eps_rf <= 0.0) ? 1.0 / (2.0 * rc * rc * rc)
+                                    : (s->eps_rf - s->eps_r) / ((2.0 * s->eps_rf + s->eps_r) * rc * rc * rc);
+    double crf = 1.0 / rc + krf * rc * rc;
+    double pre = OR_COUL * qq / s->eps_r;
+    *urf = pre * (1.0 / r + krf * r * r - crf);
+    /* -dU/dr */
+    double flj = 4.0 * eps * (12.0 * sr12 - 6.0 * sr6) / r;
+    double frf = pre * (1.0 / (r * r) - 2.0 * krf * r);
+    *fscal = (flj + frf) / r;
+}
+
+/* ------------------------------------------------------------ cell list */
+
+/* Cell of a bead: c_d = floor(u_d * n_d / 2^32) in exact integer arithmetic;
+ * cell id = (cz * ny + cy) * nx + cx.  Counting sort keeps bead ids
+ * ascending within each cell.  start has n_cells + 1 entries. */
+void or_cell_list(int n, const uint32_t *pu, const int ncell[3], int *cell_of, int *sorted, int *start)
+{
+    int nc = ncell[0] * ncell[1] * ncell[2];
+    for (int c = 0; c <= nc; ++c) start[c] = 0;
+    for (int i = 0; i < n; ++i) {
+        int cc[3];
+        for (int d = 0; d < 3; ++d) cc[d] = (int)(((uint64_t)pu[3 * i + d] * (uint64_t)ncell[d]) >> 32);
+        cell_of[i] = (cc[2] * ncell[1] + cc[1]) * ncell[0] + cc[0];
+        start[cell_of[i] + 1]++;
+    }
+    for (int c = 0; c < nc; ++c) start[c + 1] += start[c];
+    int *fill = (int *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(int));
+    for (int i = 0; i < n; ++i) {
+        int c = cell_of[i];
+        sorted[start[c] + fill[c]++] = i;
+    }
+    free(fill);
+}
+
+void or_cell_dims(const or_sys *s, int ncell[3])
+{
+    for (int d = 0; d < 3; ++d) ncell[d] = (int)floor(s->box[d] / s->rc);
+}
+
+/* ------------------------------------------------------------- energies */
+
+/* Accumulate one unordered pair (i, j) into terms and forces; bt* give the
+ * A and B bead types and lam the mixing weight of U(lam) = (1-lam) U_A + lam U_B. */
+static void add_pair(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
+                     int i, int j, double *t, double *F)
+{
+    if (excluded(s, i, j)) return;
+    double d[3];
+    separation(s, pu, i, j, d);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 >= s->rc * s->rc) return;
+    double r = sqrt(r2);
+    double la, ra, fa, lb = 0, rb = 0, fb = 0;
+    pair_terms(s, btA[i], btA[j], r, &la, &ra, &fa);
+    if (lam != 0.0) pair_terms(s, btB[i], btB[j], r, &lb, &rb, &fb);
+    t[0] += (1.0 - lam) * la + lam * lb;
+    t[1] += (1.0 - lam) * ra + lam * rb;
+    t[5] += 1.0;
+    if (F) {
+        double f = (1.0 - lam) * fa + lam * fb;
+        for (int k = 0; k < 3; ++k) { F[3 * i + k] += f * d[k]; F[3 * j + k] -= f * d[k]; }
+    }
+}
+
+static void bonded(const or_sys *s, const uint32_t *pu, double *t, double *F)
+{
+    double c0 = cos(s->theta0_deg * M_PI / 180.0);
+    for (int l = 0; l < s->n_lipids; ++l) {
+        int f0 = s->lipid_first[l];
+        for (int b = 0; b < s->nb; ++b) {
+            int i = f0 + s->bonds[2 * b], j = f0 + s->bonds[2 * b + 1];
+            double d[3];
+            separation(s, pu, i, j, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            t[2] += 0.5 * s->kb * (r - s->b0) * (r - s->b0);
+            if (F) {
+                double f = -s->kb * (r - s->b0) / r;
+                for (int k = 0; k < 3; ++k) { F[3 * i + k] += f * d[k]; F[3 * j + k] -= f * d[k]; }
+            }
+        }
+        for (int a = 0; a < s->na; ++a) {
+            int i = f0 + s->angles[3 * a], j = f0 + s->angles[3 * a + 1], k = f0 + s->angles[3 * a + 2];
+            double A[3], B[3];
+            separation(s, pu, i, j, A);
+            separation(s, pu, k, j, B);
+            double la = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+            double lb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+            double c = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) / (la * lb);
+            t[3] += 0.5 * s->ktheta * (c - c0) * (c - c0);
+            if (F) {
+                double pre = -s->ktheta * (c - c0);
+                for (int q = 0; q < 3; ++q) {
+                    double dci = B[q] / (la * lb) - c * A[q] / (la * la);
+                    double dck = A[q] / (la * lb) - c * B[q] / (lb * lb);
+                    F[3 * i + q] += pre * dci;
+                    F[3 * k + q] += pre * dck;
+                    F[3 * j + q] -= pre * (dci + dck);
+                }
+            }
+        }
+    }
+}
+
+/* Potential energy U(lam) and, if F != NULL, F = -grad U.
+ * terms: [0] LJ, [1] RF, [2] bond, [3] angle, [4] total, [5] number of
+ * in-cutoff non-excluded pairs.  use_cells = 0: all N(N-1)/2 pairs;
+ * use_cells = 1: the oracle's own cell list (needs >= 3 cells per edge). */
+double or_energy(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
+                 int use_cells, double *terms, double *F)
+{
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    int n = s->n_beads;
+    if (F) memset(F, 0, sizeof(double) * 3 * (size_t)n);
+    if (!btB) btB = btA;
+    if (!use_cells) {
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) add_pair(s, pu, btA, btB, lam, i, j, t, F);
+    } else {
+        int nc[3];
+        or_cell_dims(s, nc);
+        int ncell = nc[0] * nc[1] * nc[2];
+        int *cell_of = malloc(sizeof(int) * n), *sorted = malloc(sizeof(int) * n);
+        int *start = malloc(sizeof(int) * (ncell + 1));
+        or_cell_list(n, pu, nc, cell_of, sorted, start);
+        for (int i = 0; i < n; ++i) {
+            int c = cell_of[i];
+            int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int x = (cx + dx + nc[0]) % nc[0], y = (cy + dy + nc[1]) % nc[1], z = (cz + dz + nc[2]) % nc[2];
+                        int cj = (z * nc[1] + y) * nc[0] + x;
+                        for (int p = start[cj]; p < start[cj + 1]; ++p) {
+                            int j = sorted[p];
+                            if (j > i) add_pair(s, pu, btA, btB, lam, i, j, t, F);
+                        }
+                    }
+        }
+        free(cell_of); free(sorted); free(start);
+    }
+    bonded(s, pu, t, F);
+    t[4] = t[0] + t[1] + t[2] + t[3];
+    if (terms) memcpy(terms, t, sizeof(t));
+    return t[4];
+}
+
+/* --------------------------------------------------------------- swaps */
+
+/* dE = U_after - U_before of exchanging the types of lipids a and b, at fixed
+ * coordinates (Sec. 2).  Computed as the sum over every pair with at least
+ * one bead whose type changes of u(new types) - u(old types). */
+double or_swap_dE(const or_sys *s, const uint32_t *pu, const int *ltype, int a, int b)
+{
+    int n = s->n_beads;
+    int *bt0 = malloc(sizeof(int) * n), *bt1 = malloc(sizeof(int) * n);
+    int *lt1 = malloc(sizeof(int) * s->n_lipids);
+    memcpy(lt1, ltype, sizeof(int) * s->n_lipids);
+    lt1[a] = ltype[b]; lt1[b] = ltype[a];
+    or_bead_types(s, ltype, bt0);
+    or_bead_types(s, lt1, bt1);
+    double dE = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (bt0[i] == bt1[i]) continue;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (bt0[j] != bt1[j] && j < i) continue; /* both changed: count once */
+            if (excluded(s, i, j)) continue;
+            double d[3];
+            separation(s, pu, i, j, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= s->rc * s->rc) continue;
+            double r = sqrt(r2), l0, r0, f0, l1, r1, f1;
+            pair_terms(s, bt0[i], bt0[j], r, &l0, &r0, &f0);
+            pair_terms(s, bt1[i], bt1[j], r, &l1, &r1, &f1);
+            dE += (l1 + r1) - (l0 + r0);
+        }
+    }
+    free(bt0); free(bt1); free(lt1);
+    return dE;
+}
+
+/* the same dE from two full energies */
+double or_swap_dE_full(const or_sys *s, const uint32_t *pu, const int *ltype, int a, int b, int use_cells)
+{
+    int n = s->n_beads;
+    int *bt0 = malloc(sizeof(int) * n), *bt1 = malloc(sizeof(int) * n);
+    int *lt1 = malloc(sizeof(int) * s->n_lipids);
+    memcpy(lt1, ltype, sizeof(int) * s->n_lipids);
+    lt1[a] = ltype[b]; lt1[b] = ltype[a];
+    or_bead_types(s, ltype, bt0);
+    or_bead_types(s, lt1, bt1);
+    double e0 = or_energy(s, pu, bt0, NULL, 0.0, use_cells, NULL, NULL);
+    double e1 = or_energy(s, pu, bt1, NULL, 0.0, use_cells, NULL, NULL);
+    free(bt0); free(bt1); free(lt1);
+    return e1 - e0;
+}
+
+/* Proposal of trial number t: two lipid indices by 32-bit multiply-shift
+ * and u in (0, 1] from one Philox call. */
+void or_swap_proposal(const or_sys *s, uint32_t t, int *a, int *b, double *u)
+{
+    uint32_t w[4];
+    draw(s, 0, t, OR_TAG_SWAP, 0, w);
+    *a = (int)(((uint64_t)w[0] * (uint64_t)s->n_lipids) >> 32);
+    *b = (int)(((uint64_t)w[1] * (uint64_t)s->n_lipids) >> 32);
+    *u = u53(w[2], w[3]);
+}
+
+typedef struct { int a, b, null_trial, accepted; double dE, u; } or_trial;
+
+/* One Metropolis exchange trial (Eq. 1): accept iff dE + kT ln u <= 0, which
+ * is u <= exp(-dE / kT) with u uniform in (0, 1]. */
+static void swap_trial(const or_sys *s, const uint32_t *pu, int *ltype, uint32_t t, or_trial *rec)
+{
+    int a, b; double u;
+    or_swap_proposal(s, t, &a, &b, &u);
+    rec->a = a; rec->b = b; rec->u = u; rec->dE = 0.0; rec->accepted = 0;
+    rec->null_trial = (a == b) || (ltype[a] == ltype[b]);
+    if (rec->null_trial) return;
+    double kT = OR_BOLTZ * s->temperature;
+    rec->dE = or_swap_dE(s, pu, ltype, a, b);
+    if (rec->dE + kT * log(u) <= 0.0) {
+        int x = ltype[a]; ltype[a] = ltype[b]; ltype[b] = x;
+        rec->accepted = 1;
+    }
+}
+
+/* n trials in order t0, t0+1, ... (sequential semantics) */
+void or_swap_trials(const or_sys *s, const uint32_t *pu, int *ltype, uint32_t t0, int n, or_trial *log_out)
+{
+    for (int k = 0; k < n; ++k) swap_trial(s, pu, ltype, t0 + (uint32_t)k, &log_out[k]);
+}
+
+/* ------------------------------------------------------------ dynamics */
+
+typedef struct {
+    uint32_t *pos;     /* [n*3] */
+    double *vel;       /* [n*3] */
+    int *ltype;        /* [n_lipids] */
+    uint32_t step, trial, move, at_step;
+} or_state;
+
+/* Kinetic energy of one coupling group: K = 1/2 sum m v^2 */
+static double group_ke(const or_sys *s, const double *v, int g)
+{
+    double K = 0.0;
+    for (int i = 0; i < s->n_beads; ++i)
+        if (s->tc_group[i] == g)
+            K += 0.5 * s->mass * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+    return K;
+}
+
+/* One leapfrog step with velocity rescaling:
+ *   F = F(x_n) for U(lam);  alpha_g from K_g of v(n - 1/2);
+ *   v <- alpha_g v + F/m dt;  x <- x + v dt  (fixed-point, rounded to the grid).
+ * counter / tag select the thermostat's Philox stream. */
+static void md_step(const or_sys *s, or_state *st, const int *btA, const int *btB, double lam,
+                    uint32_t counter, uint32_t tag, int use_cells, double *F)
+{
+    int n = s->n_beads;
+    or_energy(s, st->pos, btA, btB, lam, use_cells, NULL, F);
+    double alpha[2] = {1.0, 1.0};
+    double kT = OR_BOLTZ * s->temperature;
+    for (int g = 0; g < 2; ++g) {
+        int ng = 0;
+        for (int i = 0; i < n; ++i) ng += (s->tc_group[i] == g);
+        int nf = 3 * ng;
+        alpha[g] = or_bussi_alpha(s, group_ke(s, st->vel, g), nf, 0.5 * nf * kT, (uint32_t)g, counter, tag);
+    }
+    for (int i = 0; i < n; ++i) {
+        double a = alpha[s->tc_group[i]];
+        for (int d = 0; d < 3; ++d) {
+            double v = a * st->vel[3 * i + d] + F[3 * i + d] / s->mass * s->dt;
+            st->vel[3 * i + d] = v;
+            double q = s->dt * OR_TWO32 / s->box[d];
+            long long k = llrint(v * q);
+            st->pos[3 * i + d] = (uint32_t)((uint64_t)st->pos[3 * i + d] + (uint64_t)k);
+        }
+    }
+}
+
+/* n_steps MD steps; after every swap_every-th step one exchange trial
+ * (swap_every = 0: none).  trial records go to log_out (may be NULL). */
+void or_md_steps(const or_sys *s, or_state *st, int n_steps, int swap_every, int use_cells, or_trial *log_out)
+{
+    int n = s->n_beads;
+    double *F = malloc(sizeof(double) * 3 * n);
+    int *bt = malloc(sizeof(int) * n);
+    int nt = 0;
+    for (int k = 1; k <= n_steps; ++k) {
+        or_bead_types(s, st->ltype, bt);
+        md_step(s, st, bt, NULL, 0.0, st->step, OR_TAG_THERMO, use_cells, F);
+        st->step++;
+        if (swap_every > 0 && k % swap_every == 0) {
+            or_trial rec;
+            swap_trial(s, st->pos, st->ltype, st->trial, &rec);
+            st->trial++;
+            if (log_out) log_out[nt] = rec;
+            nt++;
+        }
+    }
+    free(F); free(bt);
+}
+
+/* --------------------------------------------------------------- MDAS */
+
+/* Pick up to n_pairs disjoint lipid pairs of different types for move m:
+ * candidate j comes from Philox call j; a candidate is skipped when its two
+ * lipids coincide, share a type, or either is already used. */
+int or_mdas_pairs(const or_sys *s, const int *ltype, uint32_t m, int n_pairs, int max_tries, int *pairs)
+{
+    char *used = calloc((size_t)s->n_lipids, 1);
+    int np = 0;
+    for (int j = 0; j < max_tries && np < n_pairs; ++j) {
+        uint32_t w[4];
+        draw(s, (uint32_t)j, m, OR_TAG_MDAS_PAIR, 0, w);
+        int a = (int)(((uint64_t)w[0] * (uint64_t)s->n_lipids) >> 32);
+        int b = (int)(((uint64_t)w[1] * (uint64_t)s->n_lipids) >> 32);
+        if (a == b || ltype[a] == ltype[b] || used[a] || used[b]) continue;
+        used[a] = used[b] = 1;
+        pairs[2 * np] = a; pairs[2 * np + 1] = b;
+        np++;
+    }
+    free(used);
+    return np;
+}
+
+typedef struct { double w, u; int accepted, n_pairs; } or_move;
+
+/* One MDAS move (Sec. 2, Eqs. 2-3): keep a copy of the state; for
+ * k = 1..K run M MD steps at lam_{k-1} = (k-1)/K on U(lam) = (1-lam) U_A +
+ * lam U_B, then add U_{lam_k}(x_k) - U_{lam_{k-1}}(x_k) to the work; accept
+ * with probability min(1, exp(-w/kT)).  Accept: the lipids keep their
+ * exchanged types and the final coordinates and velocities.  Reject: the
+ * saved state comes back.  pairs_in != NULL gives the pairs explicitly. */
+void or_mdas_move(const or_sys *s, or_state *st, int n_pairs, int n_lambda, int md_per_lambda,
+                  const int *pairs_in, int use_cells, int *pairs_out, or_move *res)
+{
+    int n = s->n_beads, nl = s->n_lipids;
+    int pairs[2 * 64];
+    int np;
+    if (pairs_in) { np = n_pairs; memcpy(pairs, pairs_in, sizeof(int) * 2 * np); }
+    else np = or_mdas_pairs(s, st->ltype, st->move, n_pairs, 64 * n_pairs + 64, pairs);
+    if (pairs_out) memcpy(pairs_out, pairs, sizeof(int) * 2 * np);
+    if (np == 0) { /* no exchangeable pair: a null move, nothing changes */
+        st->move++;
+        res->w = 0.0; res->u = 1.0; res->accepted = 0; res->n_pairs = 0;
+        return;
+    }
+    int *ltB = malloc(sizeof(int) * nl);
+    memcpy(ltB, st->ltype, sizeof(int) * nl);
+    for (int p = 0; p < np; ++p) { ltB[pairs[2 * p]] = st->ltype[pairs[2 * p + 1]]; ltB[pairs[2 * p + 1]] = st->ltype[pairs[2 * p]]; }
+    int *btA = malloc(sizeof(int) * n), *btB = malloc(sizeof(int) * n);
+    or_bead_types(s, st->ltype, btA);
+    or_bead_types(s, ltB, btB);
+    uint32_t *x0 = malloc(sizeof(uint32_t) * 3 * n);
+    double *v0 = malloc(sizeof(double) * 3 * n), *F = malloc(sizeof(double) * 3 * n);
+    memcpy(x0, st->pos, sizeof(uint32_t) * 3 * n);
+    memcpy(v0, st->vel, sizeof(double) * 3 * n);
+    double w = 0.0;
+    for (int k = 1; k <= n_lambda; ++k) {
+        double lp = (double)(k - 1) / n_lambda, lk = (double)k / n_lambda;
+        for (int m = 0; m < md_per_lambda; ++m) {
+            md_step(s, st, btA, btB, lp, st->at_step, OR_TAG_AT_THERMO, use_cells, F);
+            st->at_step++;
+        }
+        double uA = or_energy(s, st->pos, btA, NULL, 0.0, use_cells, NULL, NULL);
+        double uB = or_energy(s, st->pos, btB, NULL, 0.0, use_cells, NULL, NULL);
+        w += ((1.0 - lk) * uA + lk * uB) - ((1.0 - lp) * uA + lp * uB);
+    }
+    uint32_t wd[4];
+    draw(s, 0, st->move, OR_TAG_MDAS_ACC, 0, wd);
+    double u = u53(wd[2], wd[3]);
+    double kT = OR_BOLTZ * s->temperature;
+    int acc = (w + kT * log(u) <= 0.0);
+    if (acc) memcpy(st->ltype, ltB, sizeof(int) * nl);
+    else { memcpy(st->pos, x0, sizeof(uint32_t) * 3 * n); memcpy(st->vel, v0, sizeof(double) * 3 * n); }
+    st->move++;
+    res->w = w; res->u = u; res->accepted = acc; res->n_pairs = np;
+    free(ltB); free(btA); free(btB); free(x0); free(v0); free(F);
+}

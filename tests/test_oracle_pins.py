@@ -1,0 +1,394 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks a fact that does not come from the oracle itself: published
+known-answer vectors, closed forms at special points, limits, invariants,
+brute force, finite differences and exact enumeration.  A dropped term, a
+wrong sign or a transposed index in oracle.c fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_08348_gb300 import synth
+from tests._systems import beads, pair_distances
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SIG = 0.47
+RC = 1.1
+F_COUL = 138.935458
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published known-answer vectors (SC'11)."""
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x, 16) for x in line.split()]
+        assert oracle.philox(v[:4], v[4:6]) == v[6:10]
+        n += 1
+    assert n == 3
+
+
+def _two(r, ta, tb, **kw):
+    m = beads([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]], [ta, tb], box=(5.0, 5.0, 5.0), **kw)
+    return m, oracle.Oracle(m)
+
+
+def _u(r, ta, tb, **kw):
+    m, o = _two(r, ta, tb, **kw)
+    t, F = o.energy(m.pos_u, cells=False)
+    return t, F, m
+
+
+def test_lj_minimum_and_depth():
+    """Neutral pair: the force vanishes at 2^(1/6) sigma and the well depth
+    below the cutoff value is eps (Sec. 3: LJ with potential shift)."""
+    ta, tb = synth.BT_C1, synth.BT_C3
+    rmin = 2 ** (1 / 6) * SIG
+    t, F, m = _u(rmin, ta, tb)
+    eps = m.eps[ta, tb]
+    # position quantisation moves r by < 1e-9 nm: the force there is < 1e-6
+    assert abs(F[0, 0]) < 1e-5
+    # a golden-section search on the oracle's own energies lands on 2^(1/6) sigma
+    a, b = 0.50, 0.56
+    g = (math.sqrt(5) - 1) / 2
+    for _ in range(60):
+        c, d = b - g * (b - a), a + g * (b - a)
+        if _u(c, ta, tb)[0]["lj"] < _u(d, ta, tb)[0]["lj"]:
+            b = d
+        else:
+            a = c
+    assert abs(0.5 * (a + b) - rmin) < 2e-6
+    # depth: u(rmin) - u(rc-) equals -eps plus the unshifted tail at rc, which
+    # for sigma/rc = 0.4273 is +0.02419 eps
+    s6 = (SIG / RC) ** 6
+    u_rc = _u(RC * (1 - 1e-12), ta, tb)[0]["lj"]
+    assert abs(u_rc) < 1e-9
+    assert t["lj"] == pytest.approx(-eps * (1 - 4 * (s6 - s6 * s6)), rel=1e-9)
+    assert 4 * (s6 - s6 * s6) == pytest.approx(0.024190, abs=2e-6)
+    assert t["rf"] == 0.0 and t["pairs"] == 1
+
+
+def test_lj_repulsive_wall_sign():
+    """Inside sigma the LJ force pushes the beads apart; past rmin it pulls."""
+    _, F, _ = _u(0.42, synth.BT_C1, synth.BT_C1)
+    assert F[0, 0] < 0 < F[1, 0]          # bead 0 is at smaller x
+    _, F, _ = _u(0.8, synth.BT_C1, synth.BT_C1)
+    assert F[0, 0] > 0 > F[1, 0]
+
+
+def test_reaction_field_limits():
+    """RF (eps_r = 15, eps_rf = infinity): Coulomb at short range, zero energy
+    and zero force at the cutoff (conducting boundary)."""
+    zero = np.zeros((10, 10))
+    # Coulomb limit: u r -> f q1 q2 / eps_r for r -> 0
+    r = 1e-3
+    t, F, _ = _u(r, synth.BT_QP, synth.BT_QN, eps=zero)
+    assert t["rf"] * r == pytest.approx(-F_COUL / 15.0, rel=2e-3)
+    assert t["lj"] == 0.0
+    # attraction of opposite charges
+    assert F[0, 0] > 0
+    # zero energy and force at rc
+    t, F, _ = _u(RC * (1 - 1e-9), synth.BT_QP, synth.BT_QN, eps=zero)
+    assert abs(t["rf"]) < 1e-7
+    assert abs(F[0, 0]) < 1e-6
+    # with eps_rf = eps_r the RF correction vanishes: plain Coulomb shifted to 0 at rc
+    t, F, m = _u(0.5, synth.BT_QP, synth.BT_QP, eps=zero, eps_rf=15.0)
+    x = synth.dequantize(m.pos_u, m.box)
+    r = x[1, 0] - x[0, 0]                       # the quantised separation
+    assert t["rf"] == pytest.approx(F_COUL / 15.0 * (1 / r - 1 / RC), rel=1e-12)
+    assert F[1, 0] == pytest.approx(F_COUL / 15.0 / r ** 2, rel=1e-12)
+
+
+def test_cutoff():
+    """Every type pair's LJ+RF energy reaches zero at rc and is zero beyond."""
+    for ta in range(7):
+        for tb in range(7):
+            t, _, _ = _u(RC * (1 - 1e-11), ta, tb)
+            assert abs(t["total"]) < 1e-8
+            t, F, _ = _u(RC * (1 + 1e-6), ta, tb)
+            assert t["total"] == 0.0 and not F.any() and t["pairs"] == 0
+
+
+def test_net_force_zero():
+    m = synth.tiny(seed=11)
+    o = oracle.Oracle(m)
+    _, F = o.energy(m.pos_u)
+    frms = np.sqrt((F * F).sum(1).mean())
+    assert np.abs(F.sum(0)).max() <= 1e-12 * frms * m.n_beads
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.37, 1.0])
+def test_forces_match_energy_gradient(lam):
+    """Central finite differences of U(lambda) match F = -grad U (1e-6 rel)."""
+    m = synth.tiny(seed=21)
+    o = oracle.Oracle(m)
+    ltB = m.lipid_type.copy()
+    ltB[0], ltB[1] = m.lipid_type[1], m.lipid_type[0]
+    ltB[2], ltB[3] = 1 - ltB[2], 1 - ltB[3]
+    btA, btB = o.bead_types(m.lipid_type), o.bead_types(ltB)
+    r = pair_distances(synth.dequantize(m.pos_u, m.box), m.box)
+    assert np.abs(r - RC).min() > 2e-5          # no pair straddles the cutoff under +-h (h ~ 1e-6)
+    _, F = o.energy(m.pos_u, btA=btA, btB=btB, lam=lam)
+    rng = np.random.default_rng(3)
+    k = 1 << 10                                  # h = k L / 2^32 ~ 1e-6 nm
+    worst = 0.0
+    frms = np.sqrt((F * F).sum(1).mean())
+    for i in rng.choice(m.n_beads, 30, replace=False):
+        for d in range(3):
+            h = k * m.box[d] / 2 ** 32
+            p, q = m.pos_u.copy(), m.pos_u.copy()
+            p[i, d] += np.uint32(k)
+            q[i, d] -= np.uint32(k)
+            up = o.energy(p, btA=btA, btB=btB, lam=lam, forces=False)[0]["total"]
+            um = o.energy(q, btA=btA, btB=btB, lam=lam, forces=False)[0]["total"]
+            fd = -(up - um) / (2 * h)
+            worst = max(worst, abs(fd - F[i, d]) / max(abs(F[i, d]), frms))
+    assert worst < 1e-6
+
+
+def test_bonded_rest_state_and_restoring():
+    """A straight rod at bond length b0 has zero bond and angle energy; a
+    stretched bond pulls back and a bent angle pushes back toward 180 deg."""
+    m = synth.membrane(3, n_lipid_types=1, n_water=0, seed=2, n_lipids=2, jitter=0.0)
+    o = oracle.Oracle(m)
+    t, _ = o.energy(m.pos_u)
+    assert t["bond"] < 1e-9 and t["angle"] < 1e-12
+    p = m.pos_u.copy()
+    p[0, 2] += np.uint32(int(0.05 / m.box[2] * 2 ** 32))    # stretch bond 0-1 (bead 0 is the top)
+    t, F = o.energy(p)
+    assert t["bond"] == pytest.approx(0.5 * 1250 * 0.05 ** 2, rel=1e-6)
+    assert F[0, 2] < 0
+    p = m.pos_u.copy()
+    p[1, 0] += np.uint32(int(0.1 / m.box[0] * 2 ** 32))     # bend bead 1 sideways
+    t, F = o.energy(p)
+    assert t["angle"] > 0 and F[1, 0] < 0
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_cell_list_sum_equals_brute_force(seed):
+    m = synth.tiny(n_side=2, n_water=60, seed=seed)
+    assert min(m.box) >= 3 * RC and m.n_beads <= 200
+    o = oracle.Oracle(m)
+    tb, Fb = o.energy(m.pos_u, cells=False)
+    tc, Fc = o.energy(m.pos_u, cells=True)
+    assert tb["pairs"] == tc["pairs"]
+    assert tc["total"] == pytest.approx(tb["total"], rel=1e-12)
+    assert np.abs(Fb - Fc).max() <= 1e-12 * np.abs(Fb).max()
+
+
+def test_cell_list_is_stable_counting_sort():
+    m = synth.mcmd_small()
+    o = oracle.Oracle(m)
+    nc = o.cell_dims()
+    cell_of, srt, start = o.cell_list(m.pos_u)
+    c = (m.pos_u.astype(np.uint64) * np.array(nc, np.uint64)) >> np.uint64(32)
+    cid = (c[:, 2] * nc[1] + c[:, 1]) * nc[0] + c[:, 0]
+    assert np.array_equal(cid.astype(np.int32), cell_of)
+    assert np.array_equal(np.lexsort((np.arange(m.n_beads), cid)), srt)
+    assert np.array_equal(np.searchsorted(np.sort(cid), np.arange(len(start)), "left"), start)
+
+
+def test_swap_dE_equals_difference_of_full_energies():
+    for m in (synth.tiny(seed=41, n_lipid_types=2), synth.tiny(seed=42, n_lipid_types=3)):
+        o = oracle.Oracle(m)
+        lt = m.lipid_type
+        U = abs(o.energy(m.pos_u, forces=False)[0]["total"])
+        n = 0
+        for a in range(m.n_lipids):
+            for b in range(a + 1, m.n_lipids):
+                if lt[a] == lt[b]:
+                    continue
+                d1 = o.swap_dE(m.pos_u, lt, a, b)
+                d2 = o.swap_dE_full(m.pos_u, lt, a, b)
+                assert d1 == pytest.approx(d2, abs=1e-9 * U)
+                n += 1
+        assert n > 0
+
+
+def test_swaps_keep_coordinates_and_composition():
+    """Sec. 2: an exchange changes potential parameters only; composition is
+    conserved by exchanging a pair."""
+    m = synth.mcmd_small()
+    o = oracle.Oracle(m, temperature=3000.0)
+    before = m.pos_u.copy()
+    lt, recs = o.swap_trials(m.pos_u, m.lipid_type, 0, 200)
+    assert np.array_equal(before, m.pos_u)
+    assert np.array_equal(np.bincount(lt, minlength=3), np.bincount(m.lipid_type, minlength=3))
+    assert any(r["accepted"] for r in recs) and any(r["null"] for r in recs)
+    for r in recs:
+        assert r["null"] == (r["a"] == r["b"] or r["null"])
+
+
+def test_metropolis_rule():
+    """Eq. 1: a non-null trial is accepted iff u <= exp(-dE/kT)."""
+    m = synth.tiny(seed=43)
+    o = oracle.Oracle(m, temperature=2000.0)
+    lt, recs = o.swap_trials(m.pos_u, m.lipid_type, 0, 400)
+    seen = set()
+    for r in recs:
+        if r["null"]:
+            assert not r["accepted"]
+            continue
+        seen.add(r["accepted"])
+        assert r["accepted"] == (r["u"] <= math.exp(-r["dE"] / o.kT))
+    assert seen == {True, False}
+
+
+def test_mdas_single_step_is_mc_exchange():
+    """Sec. 2: MDAS with delta-lambda = 1 and M = 0 is one MC exchange: the
+    work equals the swap dE and the decision is the Metropolis one."""
+    m = synth.tiny(seed=44)
+    o = oracle.Oracle(m)
+    st = o.state()
+    lt = m.lipid_type
+    a, b = [(a, b) for a in range(m.n_lipids) for b in range(m.n_lipids) if lt[a] != lt[b]][0]
+    res = o.mdas_move(st, 1, 1, 0, pairs=[[a, b]])
+    assert res["w"] == pytest.approx(o.swap_dE(m.pos_u, lt, a, b), abs=1e-9)
+    assert res["accepted"] == (res["w"] + o.kT * math.log(res["u"]) <= 0)
+    assert np.array_equal(st["pos_u"], m.pos_u)
+
+
+@pytest.mark.parametrize("K", [1, 4, 10])
+def test_mdas_work_without_dynamics_is_the_exchange_energy(K):
+    """With M = 0 the coordinates stay put, so Eq. 2 telescopes to
+    U_B(x0) - U_A(x0) for any number of lambda steps."""
+    m = synth.tiny(seed=45, n_lipid_types=3)
+    o = oracle.Oracle(m)
+    lt = m.lipid_type
+    pairs = o.mdas_pairs(lt, 0, 2)
+    assert len(pairs) == 2
+    ltB = lt.copy()
+    for a, b in pairs:
+        ltB[a], ltB[b] = lt[b], lt[a]
+    dU = o.energy(m.pos_u, ltype=ltB, forces=False)[0]["total"] - o.energy(m.pos_u, ltype=lt, forces=False)[0]["total"]
+    st = o.state()
+    res = o.mdas_move(st, 2, K, 0)
+    assert np.array_equal(res["pairs"], pairs)
+    assert res["w"] == pytest.approx(dU, abs=1e-9 * abs(dU) + 1e-9)
+
+
+def test_lambda_path_is_linear():
+    """U(lambda) = (1 - lambda) U_A + lambda U_B (Sec. 2): forces are linear too."""
+    m = synth.tiny(seed=46)
+    o = oracle.Oracle(m)
+    ltB = m.lipid_type.copy()
+    ltB[:2] = ltB[1::-1]
+    btA, btB = o.bead_types(m.lipid_type), o.bead_types(ltB)
+    t0, F0 = o.energy(m.pos_u, btA=btA)
+    t1, F1 = o.energy(m.pos_u, btA=btB)
+    for lam in (0.25, 0.6):
+        tl, Fl = o.energy(m.pos_u, btA=btA, btB=btB, lam=lam)
+        assert tl["total"] == pytest.approx((1 - lam) * t0["total"] + lam * t1["total"], rel=1e-12)
+        assert np.abs(Fl - ((1 - lam) * F0 + lam * F1)).max() < 1e-9 * np.abs(F0).max()
+
+
+def test_mdas_reject_restores_state_and_accept_keeps_types():
+    m = synth.tiny(seed=47)
+    o = oracle.Oracle(m)
+    outcomes = set()
+    st = o.state()
+    for _ in range(12):
+        x0, v0, lt0 = st["pos_u"].copy(), st["vel"].copy(), st["ltype"].copy()
+        res = o.mdas_move(st, 2, 3, 2)
+        outcomes.add(res["accepted"])
+        if res["accepted"]:
+            exp = lt0.copy()
+            for a, b in res["pairs"]:
+                exp[a], exp[b] = lt0[b], lt0[a]
+            assert np.array_equal(st["ltype"], exp)
+            assert not np.array_equal(st["pos_u"], x0)
+        else:
+            assert np.array_equal(st["pos_u"], x0) and np.array_equal(st["vel"], v0)
+            assert np.array_equal(st["ltype"], lt0)
+        # MD between moves so later proposals see new states
+        o.md_steps(st, 2)
+    assert st["move"] == 12
+
+
+def test_detailed_balance_exact_enumeration():
+    """Swaps only, frozen coordinates, 2 + 2 lipids of two types: the six
+    occupancies are visited with Boltzmann weights exp(-U/kT)."""
+    from itertools import combinations
+    from scipy.stats import chisquare
+    m = synth.membrane(5, n_lipid_types=2, n_water=30, seed=48, n_lipids=4)   # 2 per leaflet
+    m.lipid_type = np.array([0, 0, 1, 1], np.int32)
+    o = oracle.Oracle(m, temperature=100.0)     # kT ~ the spread of the six energies
+    states = [tuple(1 if i in c else 0 for i in range(4)) for c in combinations(range(4), 2)]
+    U = np.array([o.energy(m.pos_u, ltype=np.array(s, np.int32), forces=False)[0]["total"] for s in states])
+    w = np.exp(-(U - U.min()) / o.kT)
+    p = w / w.sum()
+    assert p.min() > 0.05 and p.max() / p.min() > 2.0
+    lt = m.lipid_type.copy()
+    counts = np.zeros(6)
+    n_steps = 30000
+    lt, recs = o.swap_trials(m.pos_u, lt, 0, 0)
+    t = 0
+    chunk = 1000
+    while t < n_steps:
+        lt_cur = lt
+        lt, recs = o.swap_trials(m.pos_u, lt_cur, t, chunk)
+        # replay the chunk to record the state after every trial
+        cur = lt_cur.copy()
+        for r in recs:
+            if r["accepted"]:
+                cur[r["a"]], cur[r["b"]] = cur[r["b"]], cur[r["a"]]
+            counts[states.index(tuple(int(x) for x in cur))] += 1
+        assert np.array_equal(cur, lt)
+        t += chunk
+    _, pval = chisquare(counts, p * counts.sum())
+    # consecutive states are correlated; thin the effective sample size by 4
+    _, pthin = chisquare(counts / 4, p * counts.sum() / 4)
+    assert pthin > 1e-3, (counts / counts.sum(), p, pval)
+
+
+def test_chi2_and_gaussian_moments():
+    m = synth.tiny()
+    o = oracle.Oracle(m)
+    for k in (2, 9, 300):
+        x = np.array([o.chi2(k, i, 7) for i in range(4000)])
+        assert abs(x.mean() - k) < 4 * math.sqrt(2 * k / 4000)
+        assert abs(x.var() / (2 * k) - 1) < 0.12
+    us = np.array([oracle.uniform53(*oracle.philox([i, 1, 2, 3], [5, 6])[:2]) for i in range(20000)])
+    assert us.min() > 0 and us.max() <= 1 and abs(us.mean() - 0.5) < 0.01
+
+
+def test_bussi_kinetic_energy_distribution():
+    """The rescaled kinetic energy has mean c K + (1 - c) K_t (Bussi et al. 2007)."""
+    m = synth.tiny()
+    o = oracle.Oracle(m, tau_t=0.1, dt=0.02)
+    c = math.exp(-0.02 / 0.1)
+    nf, kt, K = 60, 30.0, 20.0
+    kn = np.array([o.bussi_alpha(K, nf, kt, 0, i) ** 2 * K for i in range(6000)])
+    assert abs(kn.mean() - (c * K + (1 - c) * kt)) < 4 * kn.std() / math.sqrt(len(kn))
+    assert o.bussi_alpha(K, nf, kt, 0, 0) == o.bussi_alpha(K, nf, kt, 0, 0)
+    o2 = oracle.Oracle(m, tau_t=0.0)
+    assert o2.bussi_alpha(K, nf, kt, 0, 0) == 1.0
+
+
+def test_nve_energy_error_scales_as_dt_squared():
+    """Leapfrog without thermostat: the fluctuation of U + <K> (K averaged over
+    the two half steps) shrinks about 4x when dt halves, with no drift."""
+    m = synth.tiny(n_side=2, n_water=50, seed=49)
+
+    def fluct(dt, n):
+        o = oracle.Oracle(m, tau_t=0.0, dt=dt)
+        st = o.state()
+        E = []
+        for _ in range(n):
+            U = o.energy(st["pos_u"], ltype=st["ltype"], forces=False)[0]["total"]
+            k0 = 0.5 * 72 * (st["vel"] ** 2).sum()
+            o.md_steps(st, 1)
+            k1 = 0.5 * 72 * (st["vel"] ** 2).sum()
+            E.append(U + 0.5 * (k0 + k1))
+        E = np.array(E)
+        return E.std(), abs(E[-n // 4:].mean() - E[: n // 4].mean())
+
+    s1, d1 = fluct(0.01, 200)
+    s2, d2 = fluct(0.005, 400)
+    assert 2.8 < s1 / s2 < 5.5, (s1, s2)
+    assert d1 < 5 * s1
