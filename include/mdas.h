@@ -1,0 +1,214 @@
+/*
+ * mdas.h — C ABI of the GB300 (sm_103a) library for the data-parallel hot path
+ * of MC-MD / MDAS sampling of a coarse-grained lipid membrane, after
+ * Cherniavskyi, Fathizadeh, Elber, Tieleman, arXiv:2005.08348.
+ *
+ * Conventions for every call:
+ *   - Units: nm, ps, kJ/mol, amu, elementary charge.
+ *   - Host pointers are borrowed for the duration of the call only; the
+ *     library owns all device memory of a system (allocated at creation
+ *     through dev_alloc when given, else cudaMalloc).
+ *   - Work is ordered on the system's CUDA stream (desc.cuda_stream) and every
+ *     call returns only after its results are on the host (synchronous).
+ *   - Every call returns an mdas_status; on failure mdas_last_error() holds a
+ *     one-line message.  A system that reported MDAS_ERR_UNSTABLE (a
+ *     non-finite velocity, a cell or neighbourhood overflow) refuses further
+ *     dynamics until mdas_set_state() installs a new state.
+ *   - Device-side waits are bounded; no call traps or hangs the GPU.
+ *
+ * Positions are stored as unsigned 32-bit fractions of the box edge,
+ * x = u * L / 2^32, so the minimum image is an exact wrap-around integer
+ * difference and the cell of a bead, floor(u * n / 2^32), is exact.
+ */
+#ifndef MDAS_H
+#define MDAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdas_system mdas_system;
+
+typedef enum {
+    MDAS_OK = 0,
+    MDAS_ERR_INVALID_ARG = 1, /* a size, pointer or parameter out of range */
+    MDAS_ERR_OOM = 2,         /* device allocation failed */
+    MDAS_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    MDAS_ERR_UNSTABLE = 4,    /* non-finite velocity or a capacity overflow on the device */
+    MDAS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    MDAS_ERR_BUSY = 6         /* the system is in use by another call */
+} mdas_status;
+
+typedef enum { MDAS_FP32 = 0, MDAS_FP64 = 1 } mdas_precision;
+
+/* System description (Sec. 3, Methods: Martini-type force field with
+ * Lennard-Jones cut at rc with a potential shift, reaction-field
+ * electrostatics, velocity-rescaling thermostat).  All pointers are HOST
+ * memory, read during mdas_create_system only.
+ *
+ * Layout rules: lipid l owns beads [l * beads_per_lipid, (l+1) * beads_per_lipid),
+ * water beads follow all lipid beads.  lipid_first_bead must match that
+ * layout (it is checked).  Limits: beads_per_lipid <= 16, n_bead_types <= 16,
+ * n_lipid_types <= 16, n_lipids < 2^20, every box edge >= 3 rc.
+ * Thermostat coupling groups: lipid beads (group 0) and water beads (group 1). */
+typedef struct {
+    int32_t n_beads, n_lipids, beads_per_lipid, n_bead_types, n_lipid_types;
+    double box[3];                     /* rectangular periodic box, fixed (NVT) */
+    const double *pos;                 /* [n_beads*3], wrapped into the box on entry */
+    const double *vel;                 /* [n_beads*3] or NULL (all zero) */
+    const int32_t *lipid_first_bead;   /* [n_lipids] */
+    const int32_t *lipid_type;         /* [n_lipids], each < n_lipid_types */
+    const int32_t *lipid_bead_type;    /* [n_lipid_types * beads_per_lipid] */
+    int32_t water_bead_type;
+    const double *eps, *sigma;         /* [n_bead_types^2], symmetric LJ pair table */
+    const double *charge;              /* [n_bead_types] */
+    const int32_t *bonds;              /* [n_bonds*2] local bead indices within a lipid */
+    int32_t n_bonds;
+    const int32_t *angles;             /* [n_angles*3] local indices, vertex in the middle */
+    int32_t n_angles;
+    double kb, b0;                     /* harmonic bond 1/2 kb (b - b0)^2 */
+    double ktheta, theta0_deg;         /* cosine angle 1/2 ktheta (cos t - cos t0)^2 */
+    double rc, eps_r, eps_rf;          /* cutoff, relative permittivity, RF dielectric (<= 0: infinity) */
+    double temperature, dt, tau_t;     /* K, ps, ps (tau_t <= 0: no thermostat, NVE) */
+    double mass;                       /* every bead, amu */
+    uint64_t seed;                     /* Philox key = (seed_lo ^ system_id, seed_hi) */
+    uint32_t system_id;
+    int32_t precision;                 /* mdas_precision: pair arithmetic and velocities */
+    void *cuda_stream;                 /* cudaStream_t to order work on; NULL = legacy default stream */
+    void *(*dev_alloc)(size_t bytes, void *stream, void *ctx);   /* optional device allocator */
+    void (*dev_free)(void *ptr, void *stream, void *ctx);
+    void *alloc_ctx;
+} mdas_system_desc;
+
+typedef struct {
+    double lj, rf, bond, angle, kinetic, potential, total;
+    int64_t pairs;                     /* in-cutoff, non-excluded unordered pairs */
+} mdas_energy_terms;
+
+typedef struct {
+    int32_t a, b;                      /* proposed lipids */
+    int32_t null_trial;                /* a == b or same lipid type: rejected without energy */
+    int32_t accepted;
+    double dE;                         /* U_after - U_before, FP64 (0 for a null trial) */
+    double u;                          /* uniform in (0, 1]; accepted iff dE + kT ln u <= 0 */
+    uint64_t index;                    /* global trial number of this system */
+} mdas_trial_record;
+
+typedef struct {
+    int64_t trials, null_trials, accepted;
+    int32_t rounds;                    /* speculation rounds used by the batched evaluation */
+} mdas_swap_stats;
+
+#define MDAS_MAX_PAIRS 64
+typedef struct {
+    double w;                          /* alchemical work, Eq. 2, FP64 */
+    double u;
+    int32_t accepted, n_pairs;
+    int32_t pairs[2 * MDAS_MAX_PAIRS];
+} mdas_move_result;
+
+typedef struct {
+    uint32_t *pos_fixed;               /* [n*3] fixed-point positions, or NULL */
+    double *pos;                       /* [n*3] nm, or NULL (set_state: used when pos_fixed is NULL) */
+    double *vel;                       /* [n*3] nm/ps, or NULL */
+    int32_t *lipid_type;               /* [n_lipids], or NULL */
+    uint64_t step, trial, move, at_step;   /* Philox counters of MD steps, trials, moves, AT steps */
+} mdas_state_view;
+
+/* Create a device-resident system from a description (Sec. 3 force field,
+ * the readings above).  On success *out owns all device memory.
+ * Errors: MDAS_ERR_INVALID_ARG for a size, layout or limit violation,
+ * MDAS_ERR_OOM, MDAS_ERR_CUDA. */
+mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out);
+
+/* Free a system and its device memory (NULL is ignored). */
+void mdas_destroy_system(mdas_system *s);
+
+/* One force evaluation at the current state (Sec. 3: LJ with potential shift
+ * plus reaction field inside rc, harmonic bonds and cosine angles):
+ * f_out [n*3] host, FP32 or FP64 pair arithmetic per the system's precision,
+ * accumulated in 64-bit fixed point; u_out, if not NULL, receives the FP64
+ * potential energy.  Either pointer may be NULL. */
+mdas_status mdas_forces(mdas_system *s, double *f_out, double *u_out);
+
+/* FP64 energy terms at the current state with a fixed-order reduction
+ * (the U of Eq. 1). */
+mdas_status mdas_energy(mdas_system *s, mdas_energy_terms *out);
+
+/* n_steps leapfrog steps with velocity rescaling (Sec. 3); after every
+ * swap_every-th step one Metropolis exchange trial (Sec. 2, Eq. 1), swap_every
+ * = 0 for none.  Trial records go to the system's trial log. */
+mdas_status mdas_md_steps(mdas_system *s, int64_t n_steps, int32_t swap_every);
+
+/* n_trials exchange trials at the current coordinates (Sec. 2: a random pair
+ * of lipids of different types exchange types, coordinates unchanged,
+ * accepted with min(1, exp(-dE/kT)), Eq. 1), evaluated in batched rounds whose
+ * result equals processing the trials one after another.  st and log
+ * ([n_trials]) may be NULL. */
+mdas_status mdas_swap_trials(mdas_system *s, int32_t n_trials, mdas_swap_stats *st, mdas_trial_record *log);
+
+/* Copy trial records first .. first+n-1 of the system's trial log (kept for
+ * the last 65536 trials) to rec [n].  Errors: MDAS_ERR_INVALID_ARG when a
+ * record is no longer (or not yet) in the log. */
+mdas_status mdas_trial_log(mdas_system *s, uint64_t first, int32_t n, mdas_trial_record *rec);
+
+/* One MDAS move (Sec. 2, Eqs. 2-3): n_pairs disjoint pairs of lipids of
+ * different types (pairs [n_pairs*2] host, or NULL to draw them) change into
+ * each other over n_lambda steps of lambda on U(l) = (1-l) U_A + l U_B, with
+ * md_per_lambda MD steps at each lambda; the FP64 work w decides acceptance by
+ * min(1, exp(-w/kT)); on rejection the pre-move coordinates, velocities and
+ * types come back.  n_pairs <= MDAS_MAX_PAIRS. */
+mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                                 const int32_t *pairs, mdas_move_result *r);
+
+/* FP64 energy change U(after) - U(before) of setting lipids[k] to type
+ * new_types[k] (k < n, distinct lipids) at the current coordinates, without
+ * applying it (the Delta U of Eq. 1 for any collective type change). */
+mdas_status mdas_delta_energy(mdas_system *s, const int32_t *lipids, const int32_t *new_types, int32_t n,
+                              double *dE);
+
+/* Copy the state to host arrays (any pointer may be NULL). */
+mdas_status mdas_get_state(const mdas_system *s, mdas_state_view *out);
+
+/* Install a state from host arrays; clears MDAS_ERR_UNSTABLE. */
+mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in);
+
+/* The cell list of the current positions: sorted_ids [n_beads] (bead ids by
+ * cell, ascending id within a cell), cell_start [n_cells+1]; cell dims in
+ * ncell[3] (floor(L/rc) per edge).  Any pointer may be NULL. */
+mdas_status mdas_cell_list(mdas_system *s, int32_t *sorted_ids, int32_t *cell_start, int32_t *ncell);
+
+/* Advance several systems together, each kernel launch covering all of them:
+ * md_steps MD steps, then swap_trials exchange trials per system.  All systems
+ * must share one precision and one CUDA stream. */
+mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32_t md_steps, int32_t swap_trials);
+
+/* Philox4x32-10 evaluated on the GPU for counters (i, c1, c2, c3), i =
+ * 0..n-1, key (k0, k1): out [n*4] host. */
+mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out);
+
+/* Kernel timing: when enabled, every pair-kernel launch of mdas_md_steps and
+ * mdas_batch_run is bracketed by CUDA events on the launching stream;
+ * mdas_pair_kernel_time returns the sum of their durations (ms) and the launch
+ * count since the last reset (reset = 1 clears after reading). */
+mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable);
+mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *launches, int32_t reset);
+
+/* Per-system counters: MD steps, force evaluations (one per MD step and one
+ * per exchange trial, as counted in Sec. 3), trials, accepted trials, in-cutoff
+ * pairs of the last force evaluation. */
+typedef struct {
+    int64_t md_steps, force_evals, trials, null_trials, accepted, moves, moves_accepted;
+} mdas_counters;
+mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
+
+const char *mdas_last_error(const mdas_system *s);
+const char *mdas_status_string(mdas_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDAS_H */

@@ -1,0 +1,908 @@
+// C ABI of the library (include/mdas.h): system lifetime, device memory,
+// CUDA-graph replay of MD segments, batched exchange trials, MDAS moves and
+// multi-system batches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mdas.h"
+#include "mdas_dev.cuh"
+
+using namespace mdas;
+
+namespace {
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pair_events;
+};
+
+struct Batch {
+    std::vector<mdas_system *> sys;
+    SysDev *dsys = nullptr;
+    BlockMap beads, cells, sortcells, syss;
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    int max_bead_blocks = 1;
+    int *dscratch = nullptr;      // [2]: pending sum, error or
+    std::map<std::string, GraphEntry> graphs;
+    LaunchCtx ctx() const {
+        LaunchCtx L;
+        L.sys = dsys; L.n_sys = (int)sys.size();
+        L.beads = &beads; L.cells = &cells; L.sortcells = &sortcells; L.syss = &syss;
+        L.precision = precision; L.stream = stream; L.max_bead_blocks = max_bead_blocks;
+        return L;
+    }
+};
+
+std::string g_last_error;
+
+}  // namespace
+
+struct mdas_system {
+    Params hp;
+    SysDev hs;
+    int n = 0, n_lip = 0, bpl = 0, precision = 0;
+    cudaStream_t stream = nullptr;
+    void *(*dev_alloc)(size_t, void *, void *) = nullptr;
+    void (*dev_free)(void *, void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    double *fout = nullptr;
+    std::unique_ptr<Batch> solo;
+    std::string err;
+    bool unstable = false;
+    bool timing = false;
+    double pair_ms = 0.0;
+    long long pair_launches = 0;
+};
+
+namespace {
+
+std::map<std::vector<mdas_system *>, std::unique_ptr<Batch>> g_batches;
+
+mdas_status fail(mdas_system *s, mdas_status st, const std::string &msg) {
+    if (s) s->err = msg;
+    g_last_error = msg;
+    return st;
+}
+
+mdas_status cuda_fail(mdas_system *s, cudaError_t e, const char *where) {
+    return fail(s, MDAS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, #call);    \
+    } while (0)
+
+void *dalloc(mdas_system *s, size_t bytes) {
+    void *p = nullptr;
+    if (s->dev_alloc) p = s->dev_alloc(bytes, (void *)s->stream, s->alloc_ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    return p;
+}
+
+void dfree(mdas_system *s, void *p) {
+    if (!p) return;
+    if (s->dev_free) s->dev_free(p, (void *)s->stream, s->alloc_ctx);
+    else cudaFree(p);
+}
+
+void free_map(BlockMap &m) {
+    if (m.d) cudaFree(m.d);
+    m.d = nullptr;
+    m.n = 0;
+}
+
+cudaError_t upload_map(BlockMap &m, const std::vector<int2> &v) {
+    m.n = (int)v.size();
+    cudaError_t e = cudaMalloc(&m.d, sizeof(int2) * std::max<size_t>(1, v.size()));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(m.d, v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice);
+}
+
+void destroy_batch(Batch *b) {
+    for (auto &kv : b->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto &ev : kv.second.pair_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    }
+    free_map(b->beads); free_map(b->cells); free_map(b->sortcells); free_map(b->syss);
+    if (b->dsys) cudaFree(b->dsys);
+    if (b->dscratch) cudaFree(b->dscratch);
+}
+
+mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batch> &out) {
+    mdas_system *s = v[0];
+    auto b = std::make_unique<Batch>();
+    b->sys = v;
+    b->precision = v[0]->precision;
+    b->stream = v[0]->stream;
+    std::vector<SysDev> hs;
+    std::vector<int2> beads, cells, sortcells, syss;
+    for (int k = 0; k < (int)v.size(); ++k) {
+        const mdas_system *x = v[k];
+        if (x->precision != b->precision) return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision");
+        if (x->stream != b->stream) return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in CUDA stream");
+        hs.push_back(x->hs);
+        for (int i = 0; i < x->n; i += BEAD_BLOCK) beads.push_back(make_int2(k, i));
+        for (int c = 0; c < x->hp.n_cells; ++c) cells.push_back(make_int2(k, c));
+        for (int c = 0; c < x->hp.n_cells; c += CELLS_PER_SORT_BLOCK) sortcells.push_back(make_int2(k, c));
+        syss.push_back(make_int2(k, 0));
+        b->max_bead_blocks = std::max(b->max_bead_blocks, (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK);
+    }
+    CK(cudaMalloc(&b->dsys, sizeof(SysDev) * hs.size()));
+    CK(cudaMemcpy(b->dsys, hs.data(), sizeof(SysDev) * hs.size(), cudaMemcpyHostToDevice));
+    CK(upload_map(b->beads, beads));
+    CK(upload_map(b->cells, cells));
+    CK(upload_map(b->sortcells, sortcells));
+    CK(upload_map(b->syss, syss));
+    CK(cudaMalloc(&b->dscratch, sizeof(int) * 4));
+    out = std::move(b);
+    return MDAS_OK;
+}
+
+// ------------------------------------------------------------ step bodies
+void md_step_launches(const Batch &b, bool lambda) {
+    LaunchCtx L = b.ctx();
+    launch_thermostat(L);
+    launch_cells(L);
+    launch_pair(L, lambda, false, b.precision == 1);
+    launch_integrate(L);
+}
+
+void trial_launches(const Batch &b) {
+    LaunchCtx L = b.ctx();
+    launch_cells(L);
+    launch_swap_propose(L, 1);
+    launch_swap_dE(L, 1);
+    launch_swap_resolve(L, 1);
+}
+
+__global__ void k_batch_status(const SysDev *__restrict__ sys, int n, int *out) {
+    int pend = 0, err = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) { pend += sys[k].c->pending; err |= sys[k].c->err; }
+    for (int o = 16; o > 0; o >>= 1) {
+        pend += __shfl_xor_sync(0xffffffffu, pend, o);
+        err |= __shfl_xor_sync(0xffffffffu, err, o);
+    }
+    if (threadIdx.x == 0) { out[0] = pend; out[1] = err; }
+}
+
+mdas_status batch_status(mdas_system *s, Batch &b, int *pending, int *err) {
+    k_batch_status<<<1, 32, 0, b.stream>>>(b.dsys, (int)b.sys.size(), b.dscratch);
+    int h[2];
+    CK(cudaMemcpyAsync(h, b.dscratch, sizeof(h), cudaMemcpyDeviceToHost, b.stream));
+    CK(cudaStreamSynchronize(b.stream));
+    *pending = h[0];
+    *err = h[1];
+    return MDAS_OK;
+}
+
+mdas_status check_err(mdas_system *s, Batch &b) {
+    int pend, err;
+    mdas_status st = batch_status(s, b, &pend, &err);
+    if (st != MDAS_OK) return st;
+    if (err) {
+        for (auto *x : b.sys) x->unstable = true;
+        std::string why;
+        if (err & ERR_NONFINITE) why += " non-finite velocity;";
+        if (err & ERR_STAGE_OVERFLOW) why += " more than 1024 beads in a 27-cell neighbourhood;";
+        if (err & ERR_TIMEOUT) why += " bounded wait expired;";
+        if (err & ERR_ROUNDS) why += " exchange rounds exhausted;";
+        return fail(s, MDAS_ERR_UNSTABLE, "unstable:" + why);
+    }
+    return MDAS_OK;
+}
+
+// Capture (or reuse) a graph of `units` repetitions of [steps_per_unit MD
+// steps + optional exchange trial]; timing adds event pairs around every
+// pair-kernel launch.
+mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, bool trial, bool lambda, bool timing,
+                      GraphEntry **out) {
+    char key[96];
+    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d", units, steps_per_unit, (int)trial, (int)lambda, (int)timing);
+    auto it = b.graphs.find(key);
+    if (it != b.graphs.end()) { *out = &it->second; return MDAS_OK; }
+    GraphEntry ge;
+    cudaGraph_t g;
+    if (timing) {
+        for (int k = 0; k < units * steps_per_unit; ++k) {
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            ge.pair_events.push_back({e0, e1});
+        }
+    }
+    CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+    LaunchCtx L = b.ctx();
+    int ev = 0;
+    for (int u = 0; u < units; ++u) {
+        for (int k = 0; k < steps_per_unit; ++k) {
+            launch_thermostat(L);
+            launch_cells(L);
+            if (timing) {
+                cudaEventRecord(ge.pair_events[ev].first, b.stream);
+                launch_pair(L, lambda, false, b.precision == 1);
+                cudaEventRecord(ge.pair_events[ev].second, b.stream);
+                ++ev;
+            } else {
+                launch_pair(L, lambda, false, b.precision == 1);
+            }
+            launch_integrate(L);
+        }
+        if (trial) trial_launches(b);
+    }
+    cudaError_t e = cudaStreamEndCapture(b.stream, &g);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+    auto r = b.graphs.emplace(key, std::move(ge));
+    *out = &r.first->second;
+    return MDAS_OK;
+}
+
+mdas_status replay(mdas_system *s, Batch &b, GraphEntry *ge) {
+    CK(cudaGraphLaunch(ge->exec, b.stream));
+    if (!ge->pair_events.empty()) {
+        CK(cudaStreamSynchronize(b.stream));
+        for (auto &ev : ge->pair_events) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev.first, ev.second));
+            for (auto *x : b.sys) { x->pair_ms += ms; x->pair_launches += 1; }
+        }
+    }
+    return MDAS_OK;
+}
+
+// n_steps MD steps on a batch; after every swap_every-th step one trial.
+mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every) {
+    if (n_steps <= 0) return MDAS_OK;
+    const bool trial = swap_every > 0;
+    const long long unit = trial ? swap_every : 1;
+    const long long n_units = n_steps / unit;
+    const long long rem = n_steps % unit;
+    bool timing = false;
+    for (auto *x : b.sys) timing = timing || x->timing;
+    const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
+    if (n_units > 0) {
+        GraphEntry *ge;
+        mdas_status st = get_graph(s, b, (int)E, (int)unit, trial, false, timing, &ge);
+        if (st != MDAS_OK) return st;
+        for (long long r = 0; r < n_units / E; ++r) {
+            st = replay(s, b, ge);
+            if (st != MDAS_OK) return st;
+        }
+        const long long left = n_units % E;
+        if (left > 0) {
+            st = get_graph(s, b, (int)left, (int)unit, trial, false, timing, &ge);
+            if (st != MDAS_OK) return st;
+            st = replay(s, b, ge);
+            if (st != MDAS_OK) return st;
+        }
+    }
+    for (long long k = 0; k < rem; ++k) md_step_launches(b, false);
+    CK(cudaGetLastError());
+    return check_err(s, b);
+}
+
+// n exchange trials per system of a batch with sequential semantics.
+mdas_status run_trials(mdas_system *s, Batch &b, int n, int *rounds_out) {
+    LaunchCtx L = b.ctx();
+    launch_cells(L);
+    int rounds = 0;
+    for (int done = 0; done < n;) {
+        const int m = std::min(n - done, MAX_ROUND_TRIALS);
+        launch_swap_propose(L, m);
+        for (int r = 0;; ++r) {
+            if (r > m + 1) return fail(s, MDAS_ERR_TIMEOUT, "exchange trials: round limit reached");
+            launch_swap_dE(L, m);
+            launch_swap_resolve(L, m);
+            ++rounds;
+            int pend, err;
+            mdas_status st = batch_status(s, b, &pend, &err);
+            if (st != MDAS_OK) return st;
+            if (pend == 0) break;
+        }
+        done += m;
+    }
+    CK(cudaGetLastError());
+    if (rounds_out) *rounds_out = rounds;
+    return check_err(s, b);
+}
+
+}  // namespace
+
+// =================================================================== ABI
+
+extern "C" {
+
+const char *mdas_status_string(mdas_status st) {
+    switch (st) {
+        case MDAS_OK: return "ok";
+        case MDAS_ERR_INVALID_ARG: return "invalid argument";
+        case MDAS_ERR_OOM: return "out of device memory";
+        case MDAS_ERR_CUDA: return "CUDA error";
+        case MDAS_ERR_UNSTABLE: return "unstable state";
+        case MDAS_ERR_TIMEOUT: return "timeout";
+        case MDAS_ERR_BUSY: return "busy";
+    }
+    return "unknown";
+}
+
+const char *mdas_last_error(const mdas_system *s) { return s ? s->err.c_str() : g_last_error.c_str(); }
+
+mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
+    mdas_system *s = nullptr;
+    if (!d || !out) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: NULL argument");
+    *out = nullptr;
+    const int n = d->n_beads, nl = d->n_lipids, bpl = d->beads_per_lipid, nbt = d->n_bead_types, nlt = d->n_lipid_types;
+    if (n <= 0 || nl < 0 || bpl <= 0 || bpl > MAXT || nbt <= 0 || nbt > MAXT || nlt <= 0 || nlt > MAXT ||
+        nl * bpl > n || nl >= (1 << 20) || n > (1 << 28))
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: sizes out of range");
+    if (!d->pos || !d->lipid_type || !d->lipid_bead_type || !d->eps || !d->sigma || !d->charge)
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: missing array");
+    if (d->water_bead_type < 0 || d->water_bead_type >= nbt) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: water type");
+    if (!(d->rc > 0) || !(d->eps_r > 0) || !(d->mass > 0) || !(d->dt > 0) || !(d->temperature >= 0))
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: rc, eps_r, mass, dt, temperature");
+    if (d->n_bonds < 0 || d->n_angles < 0 || (d->n_bonds && !d->bonds) || (d->n_angles && !d->angles))
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: topology");
+    if (d->precision != MDAS_FP32 && d->precision != MDAS_FP64) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: precision");
+    int nc[3];
+    for (int k = 0; k < 3; ++k) {
+        if (!(d->box[k] > 0)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: box");
+        nc[k] = (int)std::floor(d->box[k] / d->rc);
+        if (nc[k] < 3) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: every box edge must be >= 3 rc");
+    }
+    if ((long long)nc[0] * nc[1] * nc[2] > (1 << 26)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: too many cells");
+    for (int l = 0; l < nl; ++l) {
+        if (d->lipid_first_bead && d->lipid_first_bead[l] != l * bpl)
+            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: lipid l must own beads [l*bpl, (l+1)*bpl)");
+        if (d->lipid_type[l] < 0 || d->lipid_type[l] >= nlt) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: lipid type");
+    }
+    for (int k = 0; k < nlt * bpl; ++k)
+        if (d->lipid_bead_type[k] < 0 || d->lipid_bead_type[k] >= nbt) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: lipid bead type");
+
+    {
+        cudaError_t e = setup_kernels();
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "create: kernel setup");
+    }
+    s = new mdas_system();
+    s->n = n; s->n_lip = nl; s->bpl = bpl; s->precision = d->precision;
+    s->stream = (cudaStream_t)d->cuda_stream;
+    s->dev_alloc = d->dev_alloc; s->dev_free = d->dev_free; s->alloc_ctx = d->alloc_ctx;
+    if ((s->dev_alloc == nullptr) != (s->dev_free == nullptr)) {
+        delete s;
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: dev_alloc and dev_free go together");
+    }
+
+    // ---- parameters
+    Params &P = s->hp;
+    memset(&P, 0, sizeof(P));
+    P.n = n; P.n_lip = nl; P.bpl = bpl; P.n_bt = nbt; P.n_lt = nlt; P.n_lipid_beads = nl * bpl;
+    P.n_cells = nc[0] * nc[1] * nc[2];
+    for (int k = 0; k < 3; ++k) {
+        P.nc[k] = nc[k];
+        P.box[k] = d->box[k];
+        P.qs[k] = d->box[k] / TWO32;
+        P.qsf[k] = (float)P.qs[k];
+        P.qdt[k] = d->dt * TWO32 / d->box[k];
+        P.rcu[k] = (uint32_t)std::ceil(d->rc / P.qs[k]) + 2;
+    }
+    P.rc = d->rc; P.rc2 = d->rc * d->rc;
+    P.krf = d->eps_rf <= 0 ? 1.0 / (2.0 * d->rc * d->rc * d->rc)
+                           : (d->eps_rf - d->eps_r) / ((2.0 * d->eps_rf + d->eps_r) * d->rc * d->rc * d->rc);
+    P.crf = 1.0 / d->rc + P.krf * d->rc * d->rc;
+    P.rc2f = (float)P.rc2;
+    P.krf2f = (float)(2.0 * P.krf);
+    P.dt = d->dt; P.tau_t = d->tau_t; P.mass = d->mass; P.kT = BOLTZ * d->temperature;
+    P.dt_over_m = d->dt / d->mass;
+    P.nf[0] = 3 * nl * bpl; P.nf[1] = 3 * (n - nl * bpl);
+    for (int g = 0; g < 2; ++g) P.ktarget[g] = 0.5 * P.nf[g] * P.kT;
+    P.kb = d->kb; P.b0 = d->b0; P.kth = d->ktheta; P.cos0 = std::cos(d->theta0_deg * M_PI / 180.0);
+    P.key0 = (uint32_t)d->seed ^ d->system_id;
+    P.key1 = (uint32_t)(d->seed >> 32);
+    P.precision = d->precision;
+    const double rc6 = std::pow(d->rc, 6);
+    for (int a = 0; a < nbt; ++a)
+        for (int b = 0; b < nbt; ++b) {
+            const double e = d->eps[a * nbt + b], sg = d->sigma[a * nbt + b];
+            const double s6 = std::pow(sg, 6);
+            const int x = a * 16 + b;
+            P.c12[x] = 4.0 * e * s6 * s6;
+            P.c6[x] = 4.0 * e * s6;
+            P.ush[x] = P.c12[x] / (rc6 * rc6) - P.c6[x] / rc6;
+            P.qq[x] = COUL * d->charge[a] * d->charge[b] / d->eps_r;
+            P.f12f[x] = (float)(12.0 * P.c12[x]);
+            P.f6f[x] = (float)(6.0 * P.c6[x]);
+            P.qqf[x] = (float)P.qq[x];
+        }
+    for (int lt = 0; lt < nlt; ++lt)
+        for (int k = 0; k < bpl; ++k) P.lbt[lt * 16 + k] = (uint8_t)d->lipid_bead_type[lt * bpl + k];
+    for (int b = 0; b < d->n_bonds; ++b) {
+        const int p = d->bonds[2 * b], q = d->bonds[2 * b + 1];
+        if (p < 0 || q < 0 || p >= bpl || q >= bpl || p == q || P.nbond[p] >= 4 || P.nbond[q] >= 4) {
+            delete s;
+            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: bond (at most 4 per bead)");
+        }
+        P.excl[p] |= (uint16_t)(1u << q);
+        P.excl[q] |= (uint16_t)(1u << p);
+        P.bpart[p][P.nbond[p]++] = (int8_t)q;
+        P.bpart[q][P.nbond[q]++] = (int8_t)p;
+    }
+    for (int a = 0; a < d->n_angles; ++a) {
+        const int t3[3] = {d->angles[3 * a], d->angles[3 * a + 1], d->angles[3 * a + 2]};
+        for (int r = 0; r < 3; ++r) {
+            const int k = t3[r];
+            if (k < 0 || k >= bpl || P.nang[k] >= 8) {
+                delete s;
+                return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: angle (at most 8 per bead)");
+            }
+            for (int c = 0; c < 3; ++c) P.ang[k][P.nang[k]][c] = (int8_t)t3[c];
+            P.nang[k]++;
+        }
+    }
+
+    // ---- device memory: one arena
+    const int nbb = (n + BEAD_BLOCK - 1) / BEAD_BLOCK;
+    const size_t vsz = d->precision == MDAS_FP64 ? 32 : 16;
+    struct Item { void **ptr; size_t bytes; };
+    SysDev &H = s->hs;
+    memset(&H, 0, sizeof(H));
+    Params *dp = nullptr; Counters *dc = nullptr;
+    std::vector<Item> items = {
+        {(void **)&dp, sizeof(Params)}, {(void **)&dc, sizeof(Counters)},
+        {(void **)&H.pos, 16ull * n}, {(void **)&H.vel, vsz * n},
+        {(void **)&H.fx, 8ull * n}, {(void **)&H.fy, 8ull * n}, {(void **)&H.fz, 8ull * n},
+        {(void **)&H.ltype, 4ull * std::max(nl, 1)},
+        {(void **)&H.cell_of, 4ull * n}, {(void **)&H.cell_slot, 4ull * n},
+        {(void **)&H.cell_count, 4ull * P.n_cells}, {(void **)&H.cell_start, 4ull * (P.n_cells + 1)},
+        {(void **)&H.tmp_ids, 4ull * n}, {(void **)&H.sorted_id, 4ull * n}, {(void **)&H.sidx, 4ull * n},
+        {(void **)&H.spos, 16ull * n},
+        {(void **)&H.ke_part, 16ull * nbb}, {(void **)&H.bpart, 16ull * nbb}, {(void **)&H.epart, 32ull * P.n_cells},
+        {(void **)&H.pos_snap, 16ull * n}, {(void **)&H.vel_snap, vsz * n},
+        {(void **)&H.ltype_snap, 4ull * std::max(nl, 1)},
+        {(void **)&H.tprop, 16ull * MAX_ROUND_TRIALS}, {(void **)&H.tu, 8ull * MAX_ROUND_TRIALS},
+        {(void **)&H.tdE, 8ull * MAX_ROUND_TRIALS}, {(void **)&H.tstate, 4ull * MAX_ROUND_TRIALS},
+        {(void **)&H.conflict, 4ull * MAX_ROUND_TRIALS * (MAX_ROUND_TRIALS / 32)},
+        {(void **)&H.lbox, 32ull * MAX_ROUND_TRIALS}, {(void **)&H.lhalf, 32ull * MAX_ROUND_TRIALS},
+        {(void **)&H.log, sizeof(TrialRec) * (size_t)LOG_CAP}, {(void **)&H.result, 8ull * 64},
+        {(void **)&s->fout, 24ull * n},
+    };
+    size_t total = 0;
+    for (auto &it : items) total += (it.bytes + 255) / 256 * 256;
+    s->arena = dalloc(s, total);
+    if (!s->arena) {
+        delete s;
+        return fail(nullptr, MDAS_ERR_OOM, "create: device allocation of " + std::to_string(total) + " bytes failed");
+    }
+    s->arena_bytes = total;
+    size_t off = 0;
+    for (auto &it : items) {
+        *it.ptr = (char *)s->arena + off;
+        off += (it.bytes + 255) / 256 * 256;
+    }
+    H.p = dp; H.c = dc; H.n_bead_blocks = nbb;
+
+    mdas_status st = MDAS_OK;
+    {
+        cudaError_t e = cudaMemsetAsync(s->arena, 0, total, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dp, &P, sizeof(Params), cudaMemcpyHostToDevice, s->stream);
+        // positions: floor(x / L * 2^32) mod 2^32, with the bead's meta word
+        std::vector<uint4> pos(n);
+        for (int i = 0; i < n; ++i) {
+            uint32_t u[3];
+            for (int k = 0; k < 3; ++k) {
+                const double f = std::floor(d->pos[3 * i + k] / d->box[k] * 4294967296.0);
+                u[k] = (uint32_t)(uint64_t)(long long)f;
+            }
+            const int bt = i < nl * bpl ? d->lipid_bead_type[d->lipid_type[i / bpl] * bpl + i % bpl] : d->water_bead_type;
+            const uint32_t m = i < nl * bpl ? meta_make(bt, bt, i % bpl, i / bpl + 1) : meta_make(bt, bt, 15, 0);
+            pos[i] = make_uint4(u[0], u[1], u[2], m);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(H.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream);
+        if (d->precision == MDAS_FP64) {
+            std::vector<Dbl4> v(n);
+            for (int i = 0; i < n; ++i)
+                v[i] = d->vel ? Dbl4{d->vel[3 * i], d->vel[3 * i + 1], d->vel[3 * i + 2], 0.0} : Dbl4{0.0, 0.0, 0.0, 0.0};
+            if (e == cudaSuccess) e = cudaMemcpyAsync(H.vel, v.data(), 32ull * n, cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        } else {
+            std::vector<float4> v(n);
+            for (int i = 0; i < n; ++i)
+                v[i] = d->vel ? make_float4((float)d->vel[3 * i], (float)d->vel[3 * i + 1], (float)d->vel[3 * i + 2], 0.f)
+                              : make_float4(0, 0, 0, 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(H.vel, v.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        }
+        if (e == cudaSuccess && nl > 0) e = cudaMemcpy(H.ltype, d->lipid_type, 4ull * nl, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(s, e, "create: upload");
+    }
+    if (st == MDAS_OK) st = make_batch({s}, s->solo);
+    if (st == MDAS_OK) {
+        launch_kinetic(s->solo->ctx());
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(s, e, "create: kinetic energy");
+    }
+    if (st != MDAS_OK) {
+        g_last_error = s->err;
+        mdas_destroy_system(s);
+        return st;
+    }
+    *out = s;
+    return MDAS_OK;
+}
+
+void mdas_destroy_system(mdas_system *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        if (std::find(it->first.begin(), it->first.end(), s) != it->first.end()) {
+            destroy_batch(it->second.get());
+            it = g_batches.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (s->solo) destroy_batch(s->solo.get());
+    dfree(s, s->arena);
+    delete s;
+}
+
+mdas_status mdas_forces(mdas_system *s, double *f_out, double *u_out) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "forces: NULL system");
+    Batch &b = *s->solo;
+    LaunchCtx L = b.ctx();
+    if (f_out) {
+        launch_cells(L);
+        launch_pair(L, false, false, s->precision == 1);
+        launch_total_force(L, s->fout, 0);
+        CK(cudaMemcpyAsync(f_out, s->fout, 24ull * s->n, cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (u_out) {
+        mdas_energy_terms t;
+        mdas_status st = mdas_energy(s, &t);
+        if (st != MDAS_OK) return st;
+        *u_out = t.potential;
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return check_err(s, b);
+}
+
+mdas_status mdas_energy(mdas_system *s, mdas_energy_terms *out) {
+    if (!s || !out) return fail(s, MDAS_ERR_INVALID_ARG, "energy: NULL argument");
+    Batch &b = *s->solo;
+    LaunchCtx L = b.ctx();
+    launch_cells(L);
+    launch_pair(L, false, true, true);
+    launch_energy_reduce(L);
+    double r[8];
+    CK(cudaMemcpyAsync(r, s->hs.result, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    out->lj = r[0]; out->rf = r[1]; out->bond = r[2]; out->angle = r[3]; out->kinetic = r[4];
+    out->pairs = (int64_t)llround(r[5]);
+    out->potential = r[0] + r[1] + r[2] + r[3];
+    out->total = out->potential + out->kinetic;
+    return check_err(s, b);
+}
+
+mdas_status mdas_md_steps(mdas_system *s, int64_t n_steps, int32_t swap_every) {
+    if (!s || n_steps < 0 || swap_every < 0) return fail(s, MDAS_ERR_INVALID_ARG, "md_steps: bad argument");
+    if (s->unstable) return fail(s, MDAS_ERR_UNSTABLE, "md_steps: system is unstable; install a state first");
+    return run_md(s, *s->solo, n_steps, swap_every);
+}
+
+mdas_status mdas_swap_trials(mdas_system *s, int32_t n_trials, mdas_swap_stats *stats, mdas_trial_record *log) {
+    if (!s || n_trials < 0) return fail(s, MDAS_ERR_INVALID_ARG, "swap_trials: bad argument");
+    if (s->unstable) return fail(s, MDAS_ERR_UNSTABLE, "swap_trials: system is unstable");
+    if (n_trials == 0 || s->n_lip == 0) return MDAS_OK;
+    Counters c0;
+    CK(cudaMemcpyAsync(&c0, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    int rounds = 0;
+    mdas_status st = run_trials(s, *s->solo, n_trials, &rounds);
+    if (st != MDAS_OK) return st;
+    Counters c1;
+    CK(cudaMemcpyAsync(&c1, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (stats) {
+        stats->trials = (int64_t)(c1.trials - c0.trials);
+        stats->null_trials = (int64_t)(c1.null_trials - c0.null_trials);
+        stats->accepted = (int64_t)(c1.accepted - c0.accepted);
+        stats->rounds = rounds;
+    }
+    if (log) return mdas_trial_log(s, c0.trial, n_trials, log);
+    return MDAS_OK;
+}
+
+mdas_status mdas_trial_log(mdas_system *s, uint64_t first, int32_t n, mdas_trial_record *rec) {
+    if (!s || n < 0 || (n > 0 && !rec)) return fail(s, MDAS_ERR_INVALID_ARG, "trial_log: bad argument");
+    Counters c;
+    CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (first + (uint64_t)n > c.trial || c.trial - first > (uint64_t)LOG_CAP)
+        return fail(s, MDAS_ERR_INVALID_ARG, "trial_log: records not in the log");
+    static_assert(sizeof(TrialRec) == sizeof(mdas_trial_record), "trial record layout");
+    for (int k = 0; k < n;) {
+        const uint64_t idx = (first + k) % LOG_CAP;
+        const int m = (int)std::min<uint64_t>((uint64_t)(n - k), LOG_CAP - idx);
+        CK(cudaMemcpyAsync(rec + k, s->hs.log + idx, sizeof(TrialRec) * m, cudaMemcpyDeviceToHost, s->stream));
+        k += m;
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return MDAS_OK;
+}
+
+mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                                 const int32_t *pairs, mdas_move_result *res) {
+    if (!s || n_pairs < 0 || n_pairs > MAX_PAIRS || n_lambda < 1 || md_per_lambda < 0)
+        return fail(s, MDAS_ERR_INVALID_ARG, "alchemical_move: bad argument");
+    if (s->unstable) return fail(s, MDAS_ERR_UNSTABLE, "alchemical_move: system is unstable");
+    Batch &b = *s->solo;
+    LaunchCtx L = b.ctx();
+    if (pairs) {
+        std::vector<int> lt(std::max(s->n_lip, 1));
+        CK(cudaMemcpy(lt.data(), s->hs.ltype, 4ull * s->n_lip, cudaMemcpyDeviceToHost));
+        std::vector<char> used(s->n_lip, 0);
+        for (int p = 0; p < 2 * n_pairs; ++p) {
+            const int l = pairs[p];
+            if (l < 0 || l >= s->n_lip || used[l]) return fail(s, MDAS_ERR_INVALID_ARG, "alchemical_move: pairs must be distinct lipids");
+            used[l] = 1;
+        }
+        for (int p = 0; p < n_pairs; ++p)
+            if (lt[pairs[2 * p]] == lt[pairs[2 * p + 1]]) return fail(s, MDAS_ERR_INVALID_ARG, "alchemical_move: a pair shares its type");
+        Counters *dc = s->hs.c;
+        CK(cudaMemcpyAsync(&dc->pairs, pairs, 8ull * n_pairs, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync(&dc->n_pairs, &n_pairs, 4, cudaMemcpyHostToDevice, s->stream));
+    }
+    launch_snapshot(L);
+    launch_mdas_select(L, n_pairs, 64 * n_pairs + 64, pairs != nullptr);
+    int np = 0;
+    CK(cudaMemcpyAsync(&np, &s->hs.c->n_pairs, 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (np > 0) {
+        const double dl = 1.0 / n_lambda;
+        for (int k = 1; k <= n_lambda; ++k) {
+            launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
+            if (md_per_lambda > 0) {
+                GraphEntry *ge;
+                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, &ge);
+                if (st != MDAS_OK) return st;
+                st = replay(s, b, ge);
+                if (st != MDAS_OK) return st;
+            }
+            launch_cells(L);
+            launch_mdas_dE(L, dl);
+        }
+    }
+    launch_mdas_accept(L);
+    launch_mdas_restore(L);
+    launch_kinetic(L);
+    Counters c;
+    double r[10];
+    CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(r, s->hs.result, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    if (res) {
+        res->w = c.w;
+        res->u = r[9];
+        res->accepted = c.mdas_accept;
+        res->n_pairs = c.n_pairs;
+        for (int k = 0; k < 2 * c.n_pairs; ++k) res->pairs[k] = c.pairs[k];
+    }
+    return check_err(s, b);
+}
+
+mdas_status mdas_delta_energy(mdas_system *s, const int32_t *lipids, const int32_t *new_types, int32_t n, double *dE) {
+    if (!s || !dE || n < 0 || n > MAX_PAIRS || (n > 0 && (!lipids || !new_types)))
+        return fail(s, MDAS_ERR_INVALID_ARG, "delta_energy: bad argument (at most 64 lipids)");
+    for (int k = 0; k < n; ++k) {
+        if (lipids[k] < 0 || lipids[k] >= s->n_lip || new_types[k] < 0 || new_types[k] >= s->hp.n_lt)
+            return fail(s, MDAS_ERR_INVALID_ARG, "delta_energy: lipid or type out of range");
+        for (int j = 0; j < k; ++j)
+            if (lipids[j] == lipids[k]) return fail(s, MDAS_ERR_INVALID_ARG, "delta_energy: lipids must be distinct");
+    }
+    if (n == 0) { *dE = 0.0; return MDAS_OK; }
+    Batch &b = *s->solo;
+    LaunchCtx L = b.ctx();
+    Counters *dc = s->hs.c;
+    int np_save = 0;
+    CK(cudaMemcpyAsync(&np_save, &dc->n_pairs, 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&dc->pairs[0], lipids, 4ull * n, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&dc->pairs[MAX_PAIRS], new_types, 4ull * n, cudaMemcpyHostToDevice, s->stream));
+    launch_cells(L);
+    launch_delta_energy(L, n);
+    CK(cudaMemcpyAsync(dE, s->hs.result + 8, 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpyAsync(&dc->n_pairs, &np_save, 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return MDAS_OK;
+}
+
+mdas_status mdas_get_state(const mdas_system *cs, mdas_state_view *out) {
+    mdas_system *s = const_cast<mdas_system *>(cs);
+    if (!s || !out) return fail(s, MDAS_ERR_INVALID_ARG, "get_state: NULL argument");
+    const int n = s->n;
+    std::vector<uint4> pos(n);
+    CK(cudaMemcpyAsync(pos.data(), s->hs.pos, 16ull * n, cudaMemcpyDeviceToHost, s->stream));
+    Counters c;
+    CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<double> v(3ull * n);
+    if (out->vel) {
+        if (s->precision == MDAS_FP64) {
+            std::vector<Dbl4> dv(n);
+            CK(cudaMemcpyAsync(dv.data(), s->hs.vel, 32ull * n, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            for (int i = 0; i < n; ++i) { out->vel[3 * i] = dv[i].x; out->vel[3 * i + 1] = dv[i].y; out->vel[3 * i + 2] = dv[i].z; }
+        } else {
+            std::vector<float4> fv(n);
+            CK(cudaMemcpyAsync(fv.data(), s->hs.vel, 16ull * n, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            for (int i = 0; i < n; ++i) { out->vel[3 * i] = fv[i].x; out->vel[3 * i + 1] = fv[i].y; out->vel[3 * i + 2] = fv[i].z; }
+        }
+    }
+    if (out->lipid_type && s->n_lip > 0)
+        CK(cudaMemcpyAsync(out->lipid_type, s->hs.ltype, 4ull * s->n_lip, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < n; ++i) {
+        const uint32_t u[3] = {pos[i].x, pos[i].y, pos[i].z};
+        for (int k = 0; k < 3; ++k) {
+            if (out->pos_fixed) out->pos_fixed[3 * i + k] = u[k];
+            if (out->pos) out->pos[3 * i + k] = (double)u[k] * s->hp.qs[k];
+        }
+    }
+    out->step = c.step; out->trial = c.trial; out->move = c.move; out->at_step = c.at_step;
+    return MDAS_OK;
+}
+
+mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
+    if (!s || !in) return fail(s, MDAS_ERR_INVALID_ARG, "set_state: NULL argument");
+    const int n = s->n, nl = s->n_lip, bpl = s->bpl;
+    std::vector<int> lt(std::max(nl, 1));
+    if (in->lipid_type) {
+        for (int l = 0; l < nl; ++l)
+            if (in->lipid_type[l] < 0 || in->lipid_type[l] >= s->hp.n_lt) return fail(s, MDAS_ERR_INVALID_ARG, "set_state: lipid type");
+        std::copy(in->lipid_type, in->lipid_type + nl, lt.begin());
+    } else if (nl > 0) {
+        CK(cudaMemcpy(lt.data(), s->hs.ltype, 4ull * nl, cudaMemcpyDeviceToHost));
+    }
+    std::vector<uint4> pos(n);
+    CK(cudaMemcpyAsync(pos.data(), s->hs.pos, 16ull * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < n; ++i) {
+        if (in->pos_fixed) {
+            pos[i].x = in->pos_fixed[3 * i]; pos[i].y = in->pos_fixed[3 * i + 1]; pos[i].z = in->pos_fixed[3 * i + 2];
+        } else if (in->pos) {
+            uint32_t u[3];
+            for (int k = 0; k < 3; ++k)
+                u[k] = (uint32_t)(uint64_t)(long long)std::floor(in->pos[3 * i + k] / s->hp.box[k] * 4294967296.0);
+            pos[i].x = u[0]; pos[i].y = u[1]; pos[i].z = u[2];
+        }
+        if (i < nl * bpl) {
+            const int bt = s->hp.lbt[lt[i / bpl] * 16 + i % bpl];
+            pos[i].w = meta_make(bt, bt, i % bpl, i / bpl + 1);
+        }
+    }
+    CK(cudaMemcpyAsync(s->hs.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
+    if (nl > 0) CK(cudaMemcpyAsync(s->hs.ltype, lt.data(), 4ull * nl, cudaMemcpyHostToDevice, s->stream));
+    if (in->vel) {
+        if (s->precision == MDAS_FP64) {
+            std::vector<Dbl4> v(n);
+            for (int i = 0; i < n; ++i) v[i] = Dbl4{in->vel[3 * i], in->vel[3 * i + 1], in->vel[3 * i + 2], 0.0};
+            CK(cudaMemcpyAsync(s->hs.vel, v.data(), 32ull * n, cudaMemcpyHostToDevice, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        } else {
+            std::vector<float4> v(n);
+            for (int i = 0; i < n; ++i) v[i] = make_float4((float)in->vel[3 * i], (float)in->vel[3 * i + 1], (float)in->vel[3 * i + 2], 0.f);
+            CK(cudaMemcpyAsync(s->hs.vel, v.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        }
+    }
+    Counters c;
+    CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    c.step = in->step; c.trial = in->trial; c.move = in->move; c.at_step = in->at_step;
+    c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0;
+    CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
+    launch_kinetic(s->solo->ctx());
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    s->unstable = false;
+    return MDAS_OK;
+}
+
+mdas_status mdas_cell_list(mdas_system *s, int32_t *sorted_ids, int32_t *cell_start, int32_t *ncell) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "cell_list: NULL system");
+    launch_cells(s->solo->ctx());
+    if (sorted_ids) CK(cudaMemcpyAsync(sorted_ids, s->hs.sorted_id, 4ull * s->n, cudaMemcpyDeviceToHost, s->stream));
+    if (cell_start) CK(cudaMemcpyAsync(cell_start, s->hs.cell_start, 4ull * (s->hp.n_cells + 1), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    if (ncell) for (int k = 0; k < 3; ++k) ncell[k] = s->hp.nc[k];
+    return MDAS_OK;
+}
+
+mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32_t md_steps, int32_t swap_trials) {
+    if (!systems || n_systems <= 0 || md_steps < 0 || swap_trials < 0)
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "batch_run: bad argument");
+    std::vector<mdas_system *> v(systems, systems + n_systems);
+    for (auto *x : v) {
+        if (!x) return fail(nullptr, MDAS_ERR_INVALID_ARG, "batch_run: NULL system");
+        if (x->unstable) return fail(x, MDAS_ERR_UNSTABLE, "batch_run: a system is unstable");
+    }
+    mdas_system *s = v[0];
+    auto it = g_batches.find(v);
+    if (it == g_batches.end()) {
+        std::unique_ptr<Batch> b;
+        mdas_status st = make_batch(v, b);
+        if (st != MDAS_OK) return st;
+        it = g_batches.emplace(v, std::move(b)).first;
+    }
+    Batch &b = *it->second;
+    mdas_status st = run_md(s, b, md_steps, 0);
+    if (st != MDAS_OK) return st;
+    if (swap_trials > 0) {
+        for (auto *x : v)
+            if (x->n_lip == 0) return fail(x, MDAS_ERR_INVALID_ARG, "batch_run: a system has no lipids");
+        st = run_trials(s, b, swap_trials, nullptr);
+    }
+    return st;
+}
+
+mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out) {
+    mdas_system *s = nullptr;
+    if (n < 0 || (n > 0 && !out)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "philox: bad argument");
+    if (n == 0) return MDAS_OK;
+    uint4 *d = nullptr;
+    CK(cudaMalloc(&d, 16ull * n));
+    launch_philox(k0, k1, c1, c2, c3, n, d, 0);
+    cudaError_t e = cudaMemcpy(out, d, 16ull * n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox");
+    return MDAS_OK;
+}
+
+mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_kernel_timing: NULL system");
+    s->timing = enable != 0;
+    return MDAS_OK;
+}
+
+mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *launches, int32_t reset) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "pair_kernel_time: NULL system");
+    if (total_ms) *total_ms = s->pair_ms;
+    if (launches) *launches = s->pair_launches;
+    if (reset) { s->pair_ms = 0.0; s->pair_launches = 0; }
+    return MDAS_OK;
+}
+
+mdas_status mdas_get_counters(const mdas_system *cs, mdas_counters *out) {
+    mdas_system *s = const_cast<mdas_system *>(cs);
+    if (!s || !out) return fail(s, MDAS_ERR_INVALID_ARG, "get_counters: NULL argument");
+    Counters c;
+    CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    out->md_steps = (int64_t)c.md_steps;
+    out->force_evals = (int64_t)c.force_evals;
+    out->trials = (int64_t)c.trials;
+    out->null_trials = (int64_t)c.null_trials;
+    out->accepted = (int64_t)c.accepted;
+    out->moves = (int64_t)c.moves;
+    out->moves_accepted = (int64_t)c.moves_accepted;
+    return MDAS_OK;
+}
+
+}  // extern "C"

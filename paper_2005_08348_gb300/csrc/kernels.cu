@@ -1,0 +1,660 @@
+// Force, energy, cell-list and integrator kernels for sm_103a.
+//
+// Physics (arXiv:2005.08348, Sec. 3 Methods): Lennard-Jones with a
+// potential-shift modifier cut at rc = 1.1 nm, reaction-field electrostatics
+// (eps_r = 15), harmonic bonds and cosine-harmonic angles inside each lipid,
+// leapfrog integration with the velocity-rescaling thermostat of Bussi,
+// Donadio and Parrinello (2007) on two coupling groups (membrane, solvent).
+//
+// Every kernel takes an array of systems plus a block map, so one launch can
+// advance one system or a whole batch of them.
+#include <cmath>
+#include <cstdio>
+
+#include "mdas_dev.cuh"
+
+namespace mdas {
+
+template <typename Real>
+struct Vec4 {};
+template <>
+struct Vec4<float> { using T = float4; };
+template <>
+struct Vec4<double> { using T = Dbl4; };
+
+// ------------------------------------------------------------------ cells
+// Cell of a bead: c_d = floor(u_d * n_d / 2^32) (exact integer arithmetic),
+// cell id = (cz * ny + cy) * nx + cx.
+
+__global__ void k_cell_count(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const Params &P = *S.p;
+    const int i = bm.y + threadIdx.x;
+    if (i >= P.n) return;
+    const uint4 q = S.pos[i];
+    const int cx = (int)(((unsigned long long)q.x * (unsigned)P.nc[0]) >> 32);
+    const int cy = (int)(((unsigned long long)q.y * (unsigned)P.nc[1]) >> 32);
+    const int cz = (int)(((unsigned long long)q.z * (unsigned)P.nc[2]) >> 32);
+    const int c = (cz * P.nc[1] + cy) * P.nc[0] + cx;
+    S.cell_of[i] = c;
+    S.cell_slot[i] = atomicAdd(&S.cell_count[c], 1);
+}
+
+// exclusive scan of the cell counts (one block per system); zeroes the
+// counts for the next build and records the largest cell
+__global__ void __launch_bounds__(1024) k_cell_scan(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const SysDev &S = sys[bmap[blockIdx.x].x];
+    const Params &P = *S.p;
+    const int nc = P.n_cells;
+    const int T = blockDim.x;
+    const int per = (nc + T - 1) / T;
+    const int lo = min(nc, threadIdx.x * per), hi = min(nc, lo + per);
+    int sum = 0, mx = 0;
+    for (int c = lo; c < hi; ++c) { int v = S.cell_count[c]; sum += v; mx = max(mx, v); }
+    __shared__ int warp_sum[32], warp_max[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int wm = mx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    if (lane == 31) warp_sum[wid] = incl;
+    if (lane == 0) warp_max[wid] = wm;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = T >> 5;
+        int v = lane < nw ? warp_sum[lane] : 0;
+        int m = lane < nw ? warp_max[lane] : 0;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane < nw) warp_sum[lane] = inc - v;   // exclusive warp offsets
+        if (lane == 0) S.c->max_cell = m;
+    }
+    __syncthreads();
+    int run = warp_sum[wid] + incl - sum;
+    for (int c = lo; c < hi; ++c) {
+        S.cell_start[c] = run;
+        run += S.cell_count[c];
+        S.cell_count[c] = 0;
+    }
+    if (threadIdx.x == T - 1) S.cell_start[nc] = run;
+}
+
+__global__ void k_cell_scatter(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const int i = bm.y + threadIdx.x;
+    if (i >= S.p->n) return;
+    S.tmp_ids[S.cell_start[S.cell_of[i]] + S.cell_slot[i]] = i;
+}
+
+// One warp per cell: order the cell's beads by id (rank = number of smaller
+// ids in the cell) and gather their positions into cell order.
+__global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const int c = bm.y + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= S.p->n_cells) return;
+    const int s = S.cell_start[c], e = S.cell_start[c + 1];
+    for (int a = s + lane; a < e; a += 32) {
+        const int id = S.tmp_ids[a];
+        int rank = 0;
+        for (int b = s; b < e; ++b) rank += (S.tmp_ids[b] < id);
+        const int p = s + rank;
+        S.sorted_id[p] = id;
+        S.sidx[id] = p;
+        S.spos[p] = S.pos[id];
+    }
+}
+
+void launch_cells(const LaunchCtx &L) {
+    k_cell_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+    k_cell_scan<<<L.syss->n, 1024, 0, L.stream>>>(L.sys, L.syss->d);
+    k_cell_scatter<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+    k_cell_finish<<<L.sortcells->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.sortcells->d);
+}
+
+// ------------------------------------------------------------ thermostat
+// Box-Muller normal (cosine branch) from one Philox output.
+__device__ double normal_of(uint4 w) {
+    const double u1 = unit53(w.x, w.y), u2 = unit53(w.z, w.w);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2);
+}
+
+// Marsaglia-Tsang (2000) gamma variate of shape a >= 1; attempt t draws the
+// normal from Philox call j0 + 2t and the uniform from call j0 + 2t + 1.
+__device__ double gamma_variate(const Params &P, uint32_t i0, uint32_t i1, uint32_t tag, double a, uint32_t j0) {
+    const double d = a - 1.0 / 3.0;
+    const double cc = 1.0 / sqrt(9.0 * d);
+    for (int t = 0; t < 32; ++t) {
+        const double x = normal_of(draw4(P, i0, i1, tag, j0 + 2 * t));
+        double v = 1.0 + cc * x;
+        if (v <= 0.0) continue;
+        v = v * v * v;
+        const uint4 w = draw4(P, i0, i1, tag, j0 + 2 * t + 1);
+        const double u = unit53(w.x, w.y);
+        if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+    }
+    return a;
+}
+
+// Bussi et al. (2007) rescaling factor: new kinetic energy
+// (sqrt(c K) + R1 sqrt((1-c) Kt/Nf))^2 + (1-c) (Kt/Nf) S with S ~ chi2(Nf-1).
+__device__ double bussi_alpha(const Params &P, double K, int nf, double kt, uint32_t g, uint32_t ctr, uint32_t tag) {
+    if (P.tau_t <= 0.0 || K <= 0.0 || nf < 3) return 1.0;
+    const double c = exp(-P.dt / P.tau_t);
+    const double r1 = normal_of(draw4(P, g, ctr, tag, 0));
+    const double S = 2.0 * gamma_variate(P, g, ctr, tag, 0.5 * (nf - 1), 1);
+    const double a = sqrt(c * K) + r1 * sqrt((1.0 - c) * kt / nf);
+    const double knew = a * a + (1.0 - c) * (kt / nf) * S;
+    return sqrt(knew / K);
+}
+
+__global__ void k_thermostat(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const SysDev &S = sys[bmap[blockIdx.x].x];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    const int g = threadIdx.x;
+    const int in_at = C.in_at;
+    const unsigned long long ctr = in_at ? C.at_step : C.step;
+    if (g < 2) {
+        double K = 0.0;
+        for (int b = 0; b < S.n_bead_blocks; ++b) K += S.ke_part[2 * b + g];
+        C.alpha[g] = bussi_alpha(P, K, P.nf[g], P.ktarget[g], (uint32_t)g, (uint32_t)ctr,
+                                 in_at ? TAG_AT_THERMO : TAG_THERMO);
+    }
+    __syncthreads();
+    if (g == 0) {
+        if (in_at) C.at_step = ctr + 1; else C.step = ctr + 1;
+        C.md_steps++;
+        C.force_evals++;
+    }
+}
+
+void launch_thermostat(const LaunchCtx &L) {
+    k_thermostat<<<L.syss->n, 32, 0, L.stream>>>(L.sys, L.syss->d);
+}
+
+// ------------------------------------------------------------ pair forces
+// One CTA per cell.  The 27 neighbour cells are staged in shared memory in a
+// frame centred on the cell (exact integer wrap-around differences, so the
+// staged copy of every bead is its periodic image nearest the cell).  Threads
+// are (i-bead, j-stream) pairs; each thread first culls its candidates into a
+// private queue of in-cutoff, non-excluded partners, then evaluates the queue
+// with all lanes busy.  Partial forces are summed over the streams in a fixed
+// order and stored once per bead, so results do not depend on scheduling.
+// Every pair is evaluated from both sides (no atomics on the j bead).
+
+template <typename Real, bool LAM, bool ENERGY>
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const Params &P = *S.p;
+    const int c = bm.y;
+    const int t = threadIdx.x;
+
+    Real *tf12 = reinterpret_cast<Real *>(smem);
+    Real *tf6 = tf12 + 256;
+    Real *tqq = tf6 + 256;
+    Real *sx = tqq + 256;
+    Real *sy = sx + STAGE_CAP;
+    Real *sz = sy + STAGE_CAP;
+    uint32_t *sm = reinterpret_cast<uint32_t *>(sz + STAGE_CAP);
+    uint16_t *q = reinterpret_cast<uint16_t *>(sm + STAGE_CAP);          // [QCAP][PAIR_THREADS]
+    Real *red = reinterpret_cast<Real *>(q + QCAP * PAIR_THREADS);       // [3][PAIR_THREADS]
+
+    __shared__ int cst[27], ccnt[27], coff[28];
+    __shared__ double ered[3][PAIR_THREADS];
+
+    for (int k = t; k < 256; k += PAIR_THREADS) {
+        if (sizeof(Real) == 4) {
+            tf12[k] = (Real)P.f12f[k]; tf6[k] = (Real)P.f6f[k]; tqq[k] = (Real)P.qqf[k];
+        } else {
+            tf12[k] = (Real)(12.0 * P.c12[k]); tf6[k] = (Real)(6.0 * P.c6[k]); tqq[k] = (Real)P.qq[k];
+        }
+    }
+    const int nx = P.nc[0], ny = P.nc[1], nz = P.nc[2];
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    if (t < 27) {
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        const int x = (cx + dx + nx) % nx, y = (cy + dy + ny) % ny, z = (cz + dz + nz) % nz;
+        const int cj = (z * ny + y) * nx + x;
+        const int s0 = S.cell_start[cj];
+        cst[t] = s0;
+        ccnt[t] = S.cell_start[cj + 1] - s0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int o = 0;
+        for (int k = 0; k < 27; ++k) { coff[k] = o; o += ccnt[k]; }
+        coff[27] = o;
+    }
+    __syncthreads();
+    const int M = coff[27];
+    if (M > STAGE_CAP) {
+        if (t == 0) atomicOr(&S.c->err, ERR_STAGE_OVERFLOW);
+        return;
+    }
+    // frame origin: the cell centre in fixed-point units
+    const uint32_t rx = (uint32_t)((((unsigned long long)(2 * cx + 1)) << 32) / (2ull * nx));
+    const uint32_t ry = (uint32_t)((((unsigned long long)(2 * cy + 1)) << 32) / (2ull * ny));
+    const uint32_t rz = (uint32_t)((((unsigned long long)(2 * cz + 1)) << 32) / (2ull * nz));
+    for (int k = t; k < M; k += PAIR_THREADS) {
+        int s = 0;
+        while (k >= coff[s + 1]) ++s;
+        const uint4 v = S.spos[cst[s] + (k - coff[s])];
+        if (sizeof(Real) == 4) {
+            sx[k] = (Real)((float)(int)(v.x - rx) * P.qsf[0]);
+            sy[k] = (Real)((float)(int)(v.y - ry) * P.qsf[1]);
+            sz[k] = (Real)((float)(int)(v.z - rz) * P.qsf[2]);
+        } else {
+            sx[k] = (Real)((double)(int)(v.x - rx) * P.qs[0]);
+            sy[k] = (Real)((double)(int)(v.y - ry) * P.qs[1]);
+            sz[k] = (Real)((double)(int)(v.z - rz) * P.qs[2]);
+        }
+        sm[k] = v.w;
+    }
+    __syncthreads();
+
+    const int ni = ccnt[13], self0 = coff[13], ifirst = cst[13];
+    const int IW = ni <= 16 ? 16 : 32;
+    const int NS = PAIR_THREADS / IW;
+    const int il = t % IW, js = t / IW;
+    const Real rc2 = (Real)(sizeof(Real) == 4 ? (double)P.rc2f : P.rc2);
+    const Real krf2 = (Real)(sizeof(Real) == 4 ? (double)P.krf2f : 2.0 * P.krf);
+    const Real lam = LAM ? (Real)S.c->lambda : (Real)0;
+    double elj = 0.0, erf = 0.0, epairs = 0.0;
+
+    for (int ib = 0; ib < ni; ib += IW) {
+        const int i = ib + il;
+        const bool valid = i < ni;
+        const int si = self0 + (valid ? i : 0);
+        const Real xi = sx[si], yi = sy[si], zi = sz[si];
+        const uint32_t mi = sm[si];
+        const int tai = meta_ta(mi), tbi = meta_tb(mi), ki = meta_k(mi);
+        const uint32_t lipi = mi >> 12;
+        const uint32_t emask = P.excl[ki];
+        Real ax = 0, ay = 0, az = 0;
+        int nq = 0;
+
+        auto flush = [&](int count) {
+            for (int e = 0; e < count; ++e) {
+                const int j = q[e * PAIR_THREADS + t];
+                const Real dx = xi - sx[j], dy = yi - sy[j], dz = zi - sz[j];
+                const Real r2 = dx * dx + dy * dy + dz * dz;
+                const uint32_t mj = sm[j];
+                const int ta = tai * 16 + meta_ta(mj);
+                Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
+                if (LAM) {
+                    const int tb = tbi * 16 + meta_tb(mj);
+                    f12 = ((Real)1 - lam) * f12 + lam * tf12[tb];
+                    f6 = ((Real)1 - lam) * f6 + lam * tf6[tb];
+                    qq = ((Real)1 - lam) * qq + lam * tqq[tb];
+                }
+                Real rinv;
+                if (sizeof(Real) == 4) rinv = (Real)rsqrtf((float)r2);
+                else rinv = (Real)(1.0 / sqrt((double)r2));
+                const Real r2inv = rinv * rinv;
+                const Real r6inv = r2inv * r2inv * r2inv;
+                const Real fs = (f12 * r6inv - f6) * r6inv * r2inv + qq * (rinv * r2inv - krf2);
+                ax += fs * dx; ay += fs * dy; az += fs * dz;
+                if (ENERGY) {
+                    const int ia = tai * 16 + meta_ta(mj);
+                    double c12 = P.c12[ia], c6 = P.c6[ia], qd = P.qq[ia], sh = P.ush[ia];
+                    if (LAM) {
+                        const int ibb = tbi * 16 + meta_tb(mj);
+                        const double l = (double)lam;
+                        c12 = (1 - l) * c12 + l * P.c12[ibb];
+                        c6 = (1 - l) * c6 + l * P.c6[ibb];
+                        qd = (1 - l) * qd + l * P.qq[ibb];
+                        sh = (1 - l) * sh + l * P.ush[ibb];
+                    }
+                    const double ri = (double)rinv, r2d = (double)r2;
+                    const double r6 = ri * ri * ri * ri * ri * ri;
+                    elj += 0.5 * (c12 * r6 * r6 - c6 * r6 - sh);
+                    erf += 0.5 * qd * (ri + P.krf * r2d - P.crf);
+                    epairs += 0.5;
+                }
+            }
+        };
+
+        for (int j = js; j < M; j += NS) {
+            const Real dx = xi - sx[j], dy = yi - sy[j], dz = zi - sz[j];
+            const Real r2 = dx * dx + dy * dy + dz * dz;
+            bool hit = valid && (r2 < rc2) && (j != si);
+            if (hit) {
+                const uint32_t mj = sm[j];
+                if (lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u)) hit = false;
+            }
+            if (hit) {
+                q[nq * PAIR_THREADS + t] = (uint16_t)j;
+                if (++nq == QCAP) { flush(nq); nq = 0; }
+            }
+        }
+        flush(nq);
+
+        red[0 * PAIR_THREADS + t] = ax;
+        red[1 * PAIR_THREADS + t] = ay;
+        red[2 * PAIR_THREADS + t] = az;
+        __syncthreads();
+        if (t < IW && ib + t < ni) {
+            Real fx = 0, fy = 0, fz = 0;
+            for (int s = 0; s < NS; ++s) {
+                fx += red[0 * PAIR_THREADS + s * IW + t];
+                fy += red[1 * PAIR_THREADS + s * IW + t];
+                fz += red[2 * PAIR_THREADS + s * IW + t];
+            }
+            const int id = S.sorted_id[ifirst + ib + t];
+            if (sizeof(Real) == 4) {
+                S.fx[id] = __float2ll_rn((float)fx * 4294967296.0f);
+                S.fy[id] = __float2ll_rn((float)fy * 4294967296.0f);
+                S.fz[id] = __float2ll_rn((float)fz * 4294967296.0f);
+            } else {
+                S.fx[id] = __double2ll_rn((double)fx * FIX);
+                S.fy[id] = __double2ll_rn((double)fy * FIX);
+                S.fz[id] = __double2ll_rn((double)fz * FIX);
+            }
+        }
+        __syncthreads();
+    }
+    if (ENERGY) {
+        ered[0][t] = elj; ered[1][t] = erf; ered[2][t] = epairs;
+        __syncthreads();
+        if (t == 0) {
+            double a = 0, b = 0, p = 0;
+            for (int k = 0; k < PAIR_THREADS; ++k) { a += ered[0][k]; b += ered[1][k]; p += ered[2][k]; }
+            S.epart[4 * c + 0] = a;
+            S.epart[4 * c + 1] = b;
+            S.epart[4 * c + 2] = p;
+        }
+    }
+}
+
+template <typename Real>
+static size_t pair_smem() {
+    return sizeof(Real) * (3 * 256 + 3 * STAGE_CAP) + sizeof(uint32_t) * STAGE_CAP +
+           sizeof(uint16_t) * QCAP * PAIR_THREADS + sizeof(Real) * 3 * PAIR_THREADS;
+}
+
+template <typename Real, bool LAM, bool ENERGY>
+static void pair_launch(const LaunchCtx &L) {
+    k_pair<Real, LAM, ENERGY><<<L.cells->n, PAIR_THREADS, pair_smem<Real>(), L.stream>>>(L.sys, L.cells->d);
+}
+
+template <typename Real, bool LAM, bool ENERGY>
+static cudaError_t pair_attr() {
+    return cudaFuncSetAttribute(k_pair<Real, LAM, ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pair_smem<Real>());
+}
+
+// once per process, before any capture: shared-memory limits of the pair kernels
+cudaError_t setup_kernels() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done != cudaErrorNotReady) return done;
+    cudaError_t e = pair_attr<float, false, false>();
+    if (e == cudaSuccess) e = pair_attr<float, true, false>();
+    if (e == cudaSuccess) e = pair_attr<double, false, false>();
+    if (e == cudaSuccess) e = pair_attr<double, true, false>();
+    if (e == cudaSuccess) e = pair_attr<double, false, true>();
+    if (e == cudaSuccess) e = pair_attr<double, true, true>();
+    done = e;
+    return e;
+}
+
+void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64) {
+    if (energy) {
+        if (lambda) pair_launch<double, true, true>(L); else pair_launch<double, false, true>(L);
+    } else if (fp64) {
+        if (lambda) pair_launch<double, true, false>(L); else pair_launch<double, false, false>(L);
+    } else {
+        if (lambda) pair_launch<float, true, false>(L); else pair_launch<float, false, false>(L);
+    }
+}
+
+// ---------------------------------------------------------- bonded terms
+// Separation r_a - r_b of two beads (exact integer minimum image).
+template <typename Real>
+__device__ __forceinline__ void sep(const Params &P, uint4 a, uint4 b, Real d[3]) {
+    if (sizeof(Real) == 4) {
+        d[0] = (Real)((float)(int)(a.x - b.x) * P.qsf[0]);
+        d[1] = (Real)((float)(int)(a.y - b.y) * P.qsf[1]);
+        d[2] = (Real)((float)(int)(a.z - b.z) * P.qsf[2]);
+    } else {
+        d[0] = (Real)((double)(int)(a.x - b.x) * P.qs[0]);
+        d[1] = (Real)((double)(int)(a.y - b.y) * P.qs[1]);
+        d[2] = (Real)((double)(int)(a.z - b.z) * P.qs[2]);
+    }
+}
+
+// Bonded force on bead i (local index k of lipid l): harmonic bonds to its
+// partners and the cosine-angle terms of every angle containing it.
+template <typename Real>
+__device__ void bonded_force(const Params &P, const uint4 *__restrict__ pos, int i, int l, int k, uint4 pi, Real f[3]) {
+    const int base = l * P.bpl;
+    for (int b = 0; b < P.nbond[k]; ++b) {
+        const int j = base + P.bpart[k][b];
+        Real d[3];
+        sep<Real>(P, pi, pos[j], d);
+        const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
+        f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
+    }
+    for (int a = 0; a < P.nang[k]; ++a) {
+        const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
+        const uint4 qi = pos[base + li], qj = pos[base + lj], qk = pos[base + lk];
+        Real A[3], B[3];
+        sep<Real>(P, qi, qj, A);
+        sep<Real>(P, qk, qj, B);
+        const Real la2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+        const Real lb2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const Real iab = (Real)1 / sqrt(la2 * lb2);
+        const Real cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * iab;
+        const Real pre = -(Real)P.kth * (cs - (Real)P.cos0);
+        for (int d = 0; d < 3; ++d) {
+            const Real dci = B[d] * iab - cs * A[d] / la2;
+            const Real dck = A[d] * iab - cs * B[d] / lb2;
+            Real g;
+            if (k == li) g = dci;
+            else if (k == lk) g = dck;
+            else g = -(dci + dck);
+            f[d] += pre * g;
+        }
+    }
+}
+
+// ------------------------------------------------------------- integrator
+// v <- alpha_g v + F/m dt ; x <- x + v dt rounded to the fixed-point grid;
+// then the per-block kinetic energy of each group for the next thermostat.
+template <typename Real>
+__global__ void __launch_bounds__(BEAD_BLOCK) k_integrate(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    using V4 = typename Vec4<Real>::T;
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const Params &P = *S.p;
+    const int i = bm.y + threadIdx.x;
+    double ke[2] = {0.0, 0.0};
+    if (i < P.n) {
+        uint4 pi = S.pos[i];
+        const uint32_t m = pi.w;
+        const int l = meta_lip(m), k = meta_k(m);
+        const Real sc = (Real)(1.0 / FIX);
+        Real f[3] = {(Real)S.fx[i] * sc, (Real)S.fy[i] * sc, (Real)S.fz[i] * sc};
+        if (l >= 0) bonded_force<Real>(P, S.pos, i, l, k, pi, f);
+        const int g = i < P.n_lipid_beads ? 0 : 1;
+        const Real a = (Real)S.c->alpha[g];
+        const Real dtm = (Real)P.dt_over_m;
+        V4 *vel = reinterpret_cast<V4 *>(S.vel);
+        V4 v = vel[i];
+        v.x = a * v.x + f[0] * dtm;
+        v.y = a * v.y + f[1] * dtm;
+        v.z = a * v.z + f[2] * dtm;
+        vel[i] = v;
+        if (!(isfinite((double)v.x) && isfinite((double)v.y) && isfinite((double)v.z))) atomicOr(&S.c->err, ERR_NONFINITE);
+        pi.x += (uint32_t)(long long)rint((double)v.x * P.qdt[0]);
+        pi.y += (uint32_t)(long long)rint((double)v.y * P.qdt[1]);
+        pi.z += (uint32_t)(long long)rint((double)v.z * P.qdt[2]);
+        S.pos[i] = pi;
+        const double vx = (double)v.x, vy = (double)v.y, vz = (double)v.z;
+        ke[g] = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz);
+    }
+    // fixed-order block reduction of the two group sums
+    __shared__ double part[2][BEAD_BLOCK / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        double v = ke[g];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) part[g][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int w = 0; w < BEAD_BLOCK / 32; ++w) s += part[threadIdx.x][w];
+        S.ke_part[2 * (bm.y / BEAD_BLOCK) + threadIdx.x] = s;
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(BEAD_BLOCK) k_kinetic(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    using V4 = typename Vec4<Real>::T;
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const Params &P = *S.p;
+    const int i = bm.y + threadIdx.x;
+    double ke[2] = {0.0, 0.0};
+    if (i < P.n) {
+        const V4 v = reinterpret_cast<const V4 *>(S.vel)[i];
+        const double vx = (double)v.x, vy = (double)v.y, vz = (double)v.z;
+        ke[i < P.n_lipid_beads ? 0 : 1] = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz);
+    }
+    __shared__ double part[2][BEAD_BLOCK / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        double v = ke[g];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) part[g][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int w = 0; w < BEAD_BLOCK / 32; ++w) s += part[threadIdx.x][w];
+        S.ke_part[2 * (bm.y / BEAD_BLOCK) + threadIdx.x] = s;
+    }
+}
+
+void launch_integrate(const LaunchCtx &L) {
+    if (L.precision == 1) k_integrate<double><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+    else k_integrate<float><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+}
+
+void launch_kinetic(const LaunchCtx &L) {
+    if (L.precision == 1) k_kinetic<double><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+    else k_kinetic<float><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+}
+
+// total force of one system (pair + bonded), as double, for the host
+template <typename Real>
+__global__ void k_total_force(const SysDev *__restrict__ sys, int si, double *__restrict__ out) {
+    const SysDev &S = sys[si];
+    const Params &P = *S.p;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const uint4 pi = S.pos[i];
+    const Real sc = (Real)(1.0 / FIX);
+    Real f[3] = {(Real)S.fx[i] * sc, (Real)S.fy[i] * sc, (Real)S.fz[i] * sc};
+    const int l = meta_lip(pi.w);
+    if (l >= 0) bonded_force<Real>(P, S.pos, i, l, meta_k(pi.w), pi, f);
+    out[3 * i] = (double)f[0];
+    out[3 * i + 1] = (double)f[1];
+    out[3 * i + 2] = (double)f[2];
+}
+
+void launch_total_force(const LaunchCtx &L, double *out, int si) {
+    // n of the system is read on the device; the grid covers the largest system
+    const int blocks = L.max_bead_blocks;
+    if (L.precision == 1) k_total_force<double><<<blocks, BEAD_BLOCK, 0, L.stream>>>(L.sys, si, out);
+    else k_total_force<float><<<blocks, BEAD_BLOCK, 0, L.stream>>>(L.sys, si, out);
+}
+
+// ------------------------------------------------------- FP64 energies
+// Bond energy counted once by the lower-index bead, angle energy by the vertex.
+__global__ void __launch_bounds__(BEAD_BLOCK) k_bonded_energy(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const Params &P = *S.p;
+    const int i = bm.y + threadIdx.x;
+    double eb = 0.0, ea = 0.0;
+    if (i < P.n) {
+        const uint4 pi = S.pos[i];
+        const int l = meta_lip(pi.w), k = meta_k(pi.w);
+        if (l >= 0) {
+            const int base = l * P.bpl;
+            for (int b = 0; b < P.nbond[k]; ++b) {
+                if (P.bpart[k][b] < k) continue;
+                double d[3];
+                sep<double>(P, pi, S.pos[base + P.bpart[k][b]], d);
+                const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                eb += 0.5 * P.kb * (r - P.b0) * (r - P.b0);
+            }
+            for (int a = 0; a < P.nang[k]; ++a) {
+                if (P.ang[k][a][1] != k) continue;
+                double A[3], B[3];
+                sep<double>(P, S.pos[base + P.ang[k][a][0]], pi, A);
+                sep<double>(P, S.pos[base + P.ang[k][a][2]], pi, B);
+                const double cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) /
+                                  sqrt((A[0] * A[0] + A[1] * A[1] + A[2] * A[2]) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+                ea += 0.5 * P.kth * (cs - P.cos0) * (cs - P.cos0);
+            }
+        }
+    }
+    __shared__ double part[2][BEAD_BLOCK];
+    part[0][threadIdx.x] = eb;
+    part[1][threadIdx.x] = ea;
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int w = 0; w < BEAD_BLOCK; ++w) s += part[threadIdx.x][w];
+        S.bpart[2 * (bm.y / BEAD_BLOCK) + threadIdx.x] = s;
+    }
+}
+
+// fixed-order sums: result[0..5] = lj, rf, bond, angle, kinetic, pairs
+__global__ void k_energy_reduce(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const SysDev &S = sys[bmap[blockIdx.x].x];
+    const Params &P = *S.p;
+    const int t = threadIdx.x;
+    double v = 0.0;
+    if (t < 3) {
+        for (int c = 0; c < P.n_cells; ++c) v += S.epart[4 * c + t];
+        S.result[t == 2 ? 5 : t] = v;
+    } else if (t < 5) {
+        for (int b = 0; b < S.n_bead_blocks; ++b) v += S.bpart[2 * b + (t - 3)];
+        S.result[t - 1] = v;
+    } else if (t == 5) {
+        for (int b = 0; b < S.n_bead_blocks; ++b) v += S.ke_part[2 * b] + S.ke_part[2 * b + 1];
+        S.result[4] = v;
+    }
+}
+
+void launch_energy_reduce(const LaunchCtx &L) {
+    k_bonded_energy<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+    k_energy_reduce<<<L.syss->n, 32, 0, L.stream>>>(L.sys, L.syss->d);
+}
+
+}  // namespace mdas

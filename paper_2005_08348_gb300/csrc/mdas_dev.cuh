@@ -1,0 +1,183 @@
+// Device-side data layout, counter-based RNG and launch plumbing shared by the
+// translation units of the GB300 library.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mdas {
+
+// 32-byte aligned four-double vector (velocity of one bead in FP64 mode)
+struct __align__(32) Dbl4 {
+    double x, y, z, w;
+};
+
+constexpr int MAXT = 16;               // bead types, lipid types, beads per lipid
+constexpr int PAIR_THREADS = 128;      // threads per cell in the pair kernel
+constexpr int STAGE_CAP = 1024;        // neighbour beads staged per cell (27 cells)
+constexpr int QCAP = 48;               // per-thread hit queue of the pair kernel
+constexpr int BEAD_BLOCK = 256;        // beads per block of per-bead kernels
+constexpr int CELLS_PER_SORT_BLOCK = 4;
+constexpr int LOG_CAP = 65536;         // trial records kept per system
+constexpr int MAX_ROUND_TRIALS = 1024; // trials per batched swap evaluation
+constexpr int MAX_PAIRS = 64;
+constexpr int MAX_CHANGED = 2 * MAXT * MAX_PAIRS;
+constexpr double FIX = 4294967296.0;   // force fixed point: 2^32 units per kJ/mol/nm
+constexpr double TWO32 = 4294967296.0;
+constexpr double BOLTZ = 0.0083144626;
+constexpr double COUL = 138.935458;
+
+enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5 };
+enum : int { ERR_NONFINITE = 1, ERR_STAGE_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8 };
+
+// Per-bead meta word carried in the 4th lane of every position:
+// bits 0-3 current bead type (A), 4-7 alchemical target type (B),
+// 8-11 index within the lipid, 12-31 lipid index + 1 (0 for water).
+__host__ __device__ inline uint32_t meta_make(int ta, int tb, int k, int lip1) {
+    return (uint32_t)ta | ((uint32_t)tb << 4) | ((uint32_t)k << 8) | ((uint32_t)lip1 << 12);
+}
+__host__ __device__ inline int meta_ta(uint32_t m) { return (int)(m & 15u); }
+__host__ __device__ inline int meta_tb(uint32_t m) { return (int)((m >> 4) & 15u); }
+__host__ __device__ inline int meta_k(uint32_t m) { return (int)((m >> 8) & 15u); }
+__host__ __device__ inline int meta_lip(uint32_t m) { return (int)(m >> 12) - 1; }
+
+// Constant parameters of one system (device memory, read-only in kernels).
+struct Params {
+    int n, n_lip, bpl, n_bt, n_lt, n_lipid_beads;
+    int nc[3], n_cells;
+    double box[3], qs[3], qdt[3];      // qs = L/2^32; qdt = dt 2^32 / L
+    float qsf[3];
+    double rc, rc2, krf, crf;
+    float rc2f, krf2f;                 // rc^2, 2 k_rf
+    double dt, tau_t, mass, kT, dt_over_m;
+    int nf[2];
+    double ktarget[2];
+    double kb, b0, kth, cos0;
+    uint32_t key0, key1;
+    int precision;
+    uint32_t rcu[3];                   // rc in fixed-point units per axis (rounded up)
+    // pair tables [ti*16 + tj]; qq includes f / eps_r
+    double c12[256], c6[256], qq[256], ush[256];
+    float f12f[256], f6f[256], qqf[256];   // 12 C12, 6 C6, f qi qj / eps_r
+    uint8_t lbt[256];                  // [lipid type * 16 + k] -> bead type
+    uint16_t excl[16];                 // excluded partners of local index k (1-2 bonds)
+    int8_t nbond[16], bpart[16][4];
+    int8_t nang[16], ang[16][8][3];    // angles containing local index k
+};
+
+struct TrialRec {                      // mirrors mdas_trial_record
+    int a, b, null_trial, accepted;
+    double dE, u;
+    unsigned long long index;
+};
+
+// Mutable per-system scalars (device memory).
+struct Counters {
+    unsigned long long step, trial, move, at_step;
+    unsigned long long md_steps, force_evals, trials, null_trials, accepted, moves, moves_accepted;
+    double lambda, w, alpha[2];
+    int err, in_at, mdas_accept, n_pairs;
+    int pairs[2 * MAX_PAIRS];
+    int max_cell, pending;
+    int n_trials_round, rounds;
+    double w_part[2 * MAX_PAIRS];
+};
+
+// Everything a kernel needs to reach one system.
+struct SysDev {
+    const Params *p;
+    Counters *c;
+    uint4 *pos;                        // id order: x, y, z fixed point, w = meta
+    void *vel;                         // float4 or double4 per bead
+    long long *fx, *fy, *fz;           // pair forces, fixed point
+    int *ltype;                        // [n_lip]
+    int *cell_of, *cell_slot, *cell_count, *cell_start, *tmp_ids, *sorted_id, *sidx;
+    uint4 *spos;                       // positions in cell order
+    double *ke_part;                   // [n_bead_blocks * 2]
+    double *epart;                     // [n_cells * 4] lj, rf, pairs, (unused)
+    double *bpart;                     // [n_bead_blocks * 2] bond, angle energies
+    uint4 *pos_snap;
+    void *vel_snap;
+    int *ltype_snap;
+    // batched exchange trials
+    int4 *tprop;                       // a, b, type a, type b
+    double *tu, *tdE;
+    int *tstate;                       // 0 pending, 1 resolved
+    uint32_t *conflict;                // [MAX_ROUND_TRIALS * MAX_ROUND_TRIALS / 32]
+    int4 *lbox;                        // per-lipid box: centre (x,y,z), unused
+    int4 *lhalf;                       // per-lipid half widths
+    TrialRec *log;                     // [LOG_CAP]
+    double *result;                    // scratch for reductions to the host [64]
+    int n_bead_blocks;
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, two 32x32->64
+// multiplications per round, key advanced by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+        uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw4(const Params &P, uint32_t i0, uint32_t i1, uint32_t tag, uint32_t j) {
+    return philox4x32_10(make_uint4(i0, i1, tag, j), P.key0, P.key1);
+}
+
+// uniform in (0, 1] from 53 bits of two words
+__device__ __forceinline__ double unit53(uint32_t a, uint32_t b) {
+    unsigned long long k = ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+    return ((double)k + 1.0) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ int pick(uint32_t w, int n) {   // multiply-shift into [0, n)
+    return (int)(((unsigned long long)w * (unsigned long long)n) >> 32);
+}
+
+// ------------------------------------------------------------ launches
+// A block map entry names the system and the first item a block works on.
+struct BlockMap {
+    int2 *d = nullptr;
+    int n = 0;
+};
+
+// kernels.cu launchers (all take the batch's device arrays)
+struct LaunchCtx {
+    const SysDev *sys;        // device array
+    int n_sys;
+    const BlockMap *beads, *cells, *sortcells, *syss;
+    int precision;
+    cudaStream_t stream;
+    int max_bead_blocks;
+};
+
+cudaError_t setup_kernels();
+void launch_cells(const LaunchCtx &L);
+void launch_thermostat(const LaunchCtx &L);
+void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64);
+void launch_integrate(const LaunchCtx &L);
+void launch_kinetic(const LaunchCtx &L);
+void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
+void launch_energy_reduce(const LaunchCtx &L);
+
+// swap.cu launchers
+void launch_swap_propose(const LaunchCtx &L, int n_trials);
+void launch_swap_dE(const LaunchCtx &L, int n_trials);
+void launch_swap_resolve(const LaunchCtx &L, int n_trials);
+void launch_mdas_select(const LaunchCtx &L, int n_pairs, int max_tries, int explicit_pairs);
+void launch_mdas_set_lambda(const LaunchCtx &L, double lambda, int in_at);
+void launch_mdas_dE(const LaunchCtx &L, double dlambda);
+void launch_mdas_accept(const LaunchCtx &L);
+void launch_mdas_restore(const LaunchCtx &L);
+void launch_snapshot(const LaunchCtx &L);
+void launch_delta_energy(const LaunchCtx &L, int n_changed_lipids);
+void launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int n, uint4 *out,
+                   cudaStream_t st);
+
+}  // namespace mdas

@@ -1,0 +1,467 @@
+// Lipid-exchange trials (arXiv:2005.08348 Sec. 2, Eq. 1) and MDAS
+// alchemical moves (Sec. 2, Eqs. 2-3) for sm_103a.
+//
+// An exchange swaps the lipid types of two lipids at fixed coordinates; its
+// energy change is a sum over pairs with at least one bead whose type
+// changes, of u(new types) - u(old types), evaluated in FP64 from exact
+// integer separations.  Bonded terms do not depend on type and drop out.
+//
+// Batched trials keep sequential semantics: all pending trials are evaluated
+// speculatively against the current types; a single thread then walks them in
+// order and resolves every trial that no earlier accepted or still pending
+// trial can influence (no shared lipid and no bead of one within reach of the
+// other); the rest are re-evaluated in the next round.
+#include <cmath>
+
+#include "mdas_dev.cuh"
+
+namespace mdas {
+
+// pair energy (LJ with potential shift + reaction field), FP64
+__device__ __forceinline__ double pair_u(const Params &P, int ti, int tj, double r2) {
+    const int x = ti * 16 + tj;
+    const double ri = 1.0 / sqrt(r2);
+    const double r6 = ri * ri * ri * ri * ri * ri;
+    return P.c12[x] * r6 * r6 - P.c6[x] * r6 - P.ush[x] + P.qq[x] * (ri + P.krf * r2 - P.crf);
+}
+
+__device__ __forceinline__ double r2_of(const Params &P, uint4 a, uint4 b) {
+    const double dx = (double)(int)(a.x - b.x) * P.qs[0];
+    const double dy = (double)(int)(a.y - b.y) * P.qs[1];
+    const double dz = (double)(int)(a.z - b.z) * P.qs[2];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Sum over the neighbours j (27 cells) of changed bead i of
+// u(new_i, new_j) - u(old_i, old_j); pairs of two changed beads are counted
+// by the lower id only.  Types come from a functor of (meta, id) and a
+// predicate telling whether a neighbour is changed.
+template <class NewT, class Changed>
+__device__ double bead_delta(const SysDev &S, const Params &P, int i, uint4 pi, int old_i, int new_i, int slot,
+                             NewT newt, Changed changed) {
+    const int nx = P.nc[0], ny = P.nc[1], nz = P.nc[2];
+    const int cx = (int)(((unsigned long long)pi.x * (unsigned)nx) >> 32);
+    const int cy = (int)(((unsigned long long)pi.y * (unsigned)ny) >> 32);
+    const int cz = (int)(((unsigned long long)pi.z * (unsigned)nz) >> 32);
+    const int dz = slot / 9 - 1, dy = (slot / 3) % 3 - 1, dx = slot % 3 - 1;
+    const int x = (cx + dx + nx) % nx, y = (cy + dy + ny) % ny, z = (cz + dz + nz) % nz;
+    const int cj = (z * ny + y) * nx + x;
+    const int li = meta_lip(pi.w), ki = meta_k(pi.w);
+    const uint32_t em = P.excl[ki];
+    double acc = 0.0;
+    for (int p = S.cell_start[cj]; p < S.cell_start[cj + 1]; ++p) {
+        const int j = S.sorted_id[p];
+        if (j == i) continue;
+        const uint4 pj = S.spos[p];
+        const bool cj_ = changed(pj.w, j);
+        if (cj_ && j < i) continue;
+        if (li >= 0 && meta_lip(pj.w) == li && ((em >> meta_k(pj.w)) & 1u)) continue;
+        const double r2 = r2_of(P, pi, pj);
+        if (r2 >= P.rc2) continue;
+        const int old_j = meta_ta(pj.w);
+        const int new_j = cj_ ? newt(pj.w, j) : old_j;
+        acc += pair_u(P, new_i, new_j, r2) - pair_u(P, old_i, old_j, r2);
+    }
+    return acc;
+}
+
+__device__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < blockDim.x; ++k) s += sh[k];
+    __syncthreads();
+    return s;
+}
+
+// -------------------------------------------------------------- proposals
+// grid (ceil(n/128), n_sys): trial t of system y draws (a, b, u) from
+// Philox counter (0, trial + t, TAG_SWAP, 0); a, b by multiply-shift.
+__global__ void k_swap_propose(const SysDev *__restrict__ sys, int n) {
+    const SysDev &S = sys[blockIdx.y];
+    const Params &P = *S.p;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const unsigned long long T = S.c->trial + (unsigned long long)t;
+    const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
+    const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
+    S.tprop[t] = make_int4(a, b, -1, -1);
+    S.tu[t] = unit53(w.z, w.w);
+    S.tstate[t] = 0;
+    // bounding boxes of the two lipids for the conflict test
+    for (int side = 0; side < 2; ++side) {
+        const int l = side ? b : a;
+        const uint4 p0 = S.pos[l * P.bpl];
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int k = 1; k < P.bpl; ++k) {
+            const uint4 pk = S.pos[l * P.bpl + k];
+            const int d[3] = {(int)(pk.x - p0.x), (int)(pk.y - p0.y), (int)(pk.z - p0.z)};
+            for (int e = 0; e < 3; ++e) { lo[e] = min(lo[e], d[e]); hi[e] = max(hi[e], d[e]); }
+        }
+        const uint32_t cen[3] = {p0.x + (uint32_t)(int)(((long long)lo[0] + hi[0]) / 2),
+                                 p0.y + (uint32_t)(int)(((long long)lo[1] + hi[1]) / 2),
+                                 p0.z + (uint32_t)(int)(((long long)lo[2] + hi[2]) / 2)};
+        S.lbox[2 * t + side] = make_int4((int)cen[0], (int)cen[1], (int)cen[2], 0);
+        S.lhalf[2 * t + side] = make_int4((hi[0] - lo[0]) / 2 + 1, (hi[1] - lo[1]) / 2 + 1, (hi[2] - lo[2]) / 2 + 1, 0);
+    }
+}
+
+__device__ __forceinline__ bool boxes_near(const Params &P, int4 ca, int4 ha, int4 cb, int4 hb) {
+    const long long gx = llabs((long long)(int)((uint32_t)ca.x - (uint32_t)cb.x)) - ha.x - hb.x;
+    const long long gy = llabs((long long)(int)((uint32_t)ca.y - (uint32_t)cb.y)) - ha.y - hb.y;
+    const long long gz = llabs((long long)(int)((uint32_t)ca.z - (uint32_t)cb.z)) - ha.z - hb.z;
+    return gx < (long long)P.rcu[0] && gy < (long long)P.rcu[1] && gz < (long long)P.rcu[2];
+}
+
+// conflict bit (t, t') for t' < t: a shared lipid, or a lipid of one within
+// reach of a lipid of the other.  grid (ceil(n*W/128), n_sys), W = words per row.
+__global__ void k_swap_conflicts(const SysDev *__restrict__ sys, int n) {
+    const SysDev &S = sys[blockIdx.y];
+    const Params &P = *S.p;
+    const int W = (n + 31) / 32;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n * W) return;
+    const int t = g / W, wd = g % W;
+    const int4 pt = S.tprop[t];
+    uint32_t bits = 0;
+    for (int k = 0; k < 32; ++k) {
+        const int u = wd * 32 + k;
+        if (u >= t) break;
+        const int4 pu = S.tprop[u];
+        bool c = pt.x == pu.x || pt.x == pu.y || pt.y == pu.x || pt.y == pu.y;
+        for (int s = 0; s < 2 && !c; ++s)
+            for (int r = 0; r < 2 && !c; ++r)
+                c = boxes_near(P, S.lbox[2 * t + s], S.lhalf[2 * t + s], S.lbox[2 * u + r], S.lhalf[2 * u + r]);
+        if (c) bits |= 1u << k;
+    }
+    S.conflict[t * W + wd] = bits;
+}
+
+void launch_swap_propose(const LaunchCtx &L, int n) {
+    dim3 g1((n + 127) / 128, L.n_sys);
+    k_swap_propose<<<g1, 128, 0, L.stream>>>(L.sys, n);
+    const int W = (n + 31) / 32;
+    dim3 g2((n * W + 127) / 128, L.n_sys);
+    k_swap_conflicts<<<g2, 128, 0, L.stream>>>(L.sys, n);
+}
+
+// ------------------------------------------------------------ speculation
+// grid (n, n_sys), one CTA per trial: dE of exchanging the current types of
+// lipids a and b (FP64, fixed-order reduction).
+__global__ void __launch_bounds__(128) k_swap_dE(const SysDev *__restrict__ sys, int n) {
+    const SysDev &S = sys[blockIdx.y];
+    const Params &P = *S.p;
+    const int t = blockIdx.x;
+    __shared__ double sh[128];
+    __shared__ int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT];
+    __shared__ int nchg, kmask;
+    if (S.tstate[t] != 0) return;
+    int4 pr = S.tprop[t];
+    const int a = pr.x, b = pr.y;
+    const int ta = S.ltype[a], tb = S.ltype[b];
+    if (threadIdx.x == 0) {
+        S.tprop[t] = make_int4(a, b, ta, tb);
+        int m = 0, nc = 0;
+        if (a != b && ta != tb) {
+            for (int k = 0; k < P.bpl; ++k)
+                if (P.lbt[ta * 16 + k] != P.lbt[tb * 16 + k]) m |= 1 << k;
+            for (int side = 0; side < 2; ++side)
+                for (int k = 0; k < P.bpl; ++k)
+                    if ((m >> k) & 1) {
+                        chg_id[nc] = (side ? b : a) * P.bpl + k;
+                        chg_old[nc] = P.lbt[(side ? tb : ta) * 16 + k];
+                        chg_new[nc] = P.lbt[(side ? ta : tb) * 16 + k];
+                        ++nc;
+                    }
+        }
+        nchg = nc;
+        kmask = m;
+    }
+    __syncthreads();
+    const int nc = nchg, m = kmask;
+    auto changed = [&](uint32_t mj, int) {
+        const int l = meta_lip(mj);
+        return (l == a || l == b) && ((m >> meta_k(mj)) & 1);
+    };
+    auto newt = [&](uint32_t mj, int) {
+        const int l = meta_lip(mj);
+        return (int)P.lbt[(l == a ? tb : ta) * 16 + meta_k(mj)];
+    };
+    double acc = 0.0;
+    for (int it = threadIdx.x; it < nc * 27; it += blockDim.x) {
+        const int ci = it / 27, slot = it % 27;
+        const int i = chg_id[ci];
+        acc += bead_delta(S, P, i, S.pos[i], chg_old[ci], chg_new[ci], slot, newt, changed);
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) S.tdE[t] = s;
+}
+
+void launch_swap_dE(const LaunchCtx &L, int n) {
+    dim3 g(n, L.n_sys);
+    k_swap_dE<<<g, 128, 0, L.stream>>>(L.sys, n);
+}
+
+// Rewrite the A type of every bead of lipid l for lipid type lt (position
+// array and its cell-ordered copy).
+__device__ void set_lipid_type(const SysDev &S, const Params &P, int l, int lt) {
+    S.ltype[l] = lt;
+    for (int k = 0; k < P.bpl; ++k) {
+        const int id = l * P.bpl + k;
+        const int bt = P.lbt[lt * 16 + k];
+        const uint32_t m = meta_make(bt, bt, k, l + 1);
+        S.pos[id].w = m;
+        S.spos[S.sidx[id]].w = m;
+    }
+}
+
+// one block per system, one thread walks the trials in order
+__global__ void k_swap_resolve(const SysDev *__restrict__ sys, int n) {
+    const SysDev &S = sys[blockIdx.x];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    if (threadIdx.x != 0) return;
+    const int W = (n + 31) / 32;
+    uint32_t blocked[MAX_ROUND_TRIALS / 32];
+    for (int w = 0; w < W; ++w) blocked[w] = 0;
+    int pending = 0;
+    for (int t = 0; t < n; ++t) {
+        if (S.tstate[t] != 0) continue;
+        bool blk = false;
+        for (int w = 0; w <= t / 32 && !blk; ++w) blk = (S.conflict[t * W + w] & blocked[w]) != 0;
+        if (blk) { blocked[t / 32] |= 1u << (t % 32); ++pending; continue; }
+        const int4 pr = S.tprop[t];
+        const int a = pr.x, b = pr.y;
+        const double u = S.tu[t];
+        TrialRec r;
+        r.a = a; r.b = b; r.u = u; r.dE = 0.0; r.accepted = 0;
+        r.index = C.trial + (unsigned long long)t;
+        r.null_trial = (a == b) || (S.ltype[a] == S.ltype[b]);
+        if (!r.null_trial) {
+            r.dE = S.tdE[t];
+            if (r.dE + P.kT * log(u) <= 0.0) {
+                const int ta = S.ltype[a], tb = S.ltype[b];
+                set_lipid_type(S, P, a, tb);
+                set_lipid_type(S, P, b, ta);
+                r.accepted = 1;
+                blocked[t / 32] |= 1u << (t % 32);
+            }
+        }
+        S.log[r.index % LOG_CAP] = r;
+        C.trials++;
+        C.force_evals++;
+        C.null_trials += r.null_trial;
+        C.accepted += r.accepted;
+        S.tstate[t] = 1;
+    }
+    C.pending = pending;
+    C.rounds++;
+    if (pending == 0) C.trial += (unsigned long long)n;
+}
+
+void launch_swap_resolve(const LaunchCtx &L, int n) {
+    k_swap_resolve<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n);
+}
+
+// ------------------------------------------------------------------ MDAS
+// Pick up to n_pairs disjoint lipid pairs of different types: candidate j
+// from Philox call (j, move, TAG_MDAS_PAIR, 0), skipped when the lipids
+// coincide, share a type, or one is already used.  Then mark the B types.
+__global__ void k_mdas_select(const SysDev *__restrict__ sys, int n_pairs, int max_tries, int explicit_pairs) {
+    const SysDev &S = sys[blockIdx.x];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    if (threadIdx.x != 0) return;
+    int np = 0;
+    if (explicit_pairs) {
+        np = C.n_pairs;
+    } else {
+        for (int j = 0; j < max_tries && np < n_pairs; ++j) {
+            const uint4 w = draw4(P, (uint32_t)j, (uint32_t)C.move, TAG_MDAS_PAIR, 0u);
+            const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
+            if (a == b || S.ltype[a] == S.ltype[b]) continue;
+            bool used = false;
+            for (int k = 0; k < 2 * np && !used; ++k) used = C.pairs[k] == a || C.pairs[k] == b;
+            if (used) continue;
+            C.pairs[2 * np] = a;
+            C.pairs[2 * np + 1] = b;
+            ++np;
+        }
+        C.n_pairs = np;
+    }
+    for (int p = 0; p < np; ++p)
+        for (int side = 0; side < 2; ++side) {
+            const int l = C.pairs[2 * p + side], o = C.pairs[2 * p + 1 - side];
+            const int tnew = S.ltype[o];
+            for (int k = 0; k < P.bpl; ++k) {
+                const int id = l * P.bpl + k;
+                const uint32_t m = S.pos[id].w;
+                S.pos[id].w = meta_make(meta_ta(m), P.lbt[tnew * 16 + k], k, l + 1);
+            }
+        }
+    C.w = 0.0;
+}
+
+void launch_mdas_select(const LaunchCtx &L, int n_pairs, int max_tries, int explicit_pairs) {
+    k_mdas_select<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n_pairs, max_tries, explicit_pairs);
+}
+
+__global__ void k_mdas_set_lambda(const SysDev *__restrict__ sys, double lambda, int in_at) {
+    const SysDev &S = sys[blockIdx.x];
+    if (threadIdx.x == 0) { S.c->lambda = lambda; S.c->in_at = in_at; }
+}
+
+void launch_mdas_set_lambda(const LaunchCtx &L, double lambda, int in_at) {
+    k_mdas_set_lambda<<<L.n_sys, 32, 0, L.stream>>>(L.sys, lambda, in_at);
+}
+
+// grid (2 * MAX_PAIRS, n_sys): CTA x handles lipid x of the pair list; the
+// changed beads are those whose A and B types differ (U_B - U_A at the
+// current coordinates, pairs of two changed beads counted once).
+__global__ void __launch_bounds__(128) k_mdas_dE(const SysDev *__restrict__ sys, int n_lip) {
+    const SysDev &S = sys[blockIdx.y];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    __shared__ double sh[128];
+    const int x = blockIdx.x;
+    if (x >= (n_lip >= 0 ? n_lip : 2 * C.n_pairs)) return;
+    const int l = C.pairs[x];
+    auto changed = [&](uint32_t mj, int) { return meta_ta(mj) != meta_tb(mj); };
+    auto newt = [&](uint32_t mj, int) { return meta_tb(mj); };
+    double acc = 0.0;
+    for (int it = threadIdx.x; it < P.bpl * 27; it += blockDim.x) {
+        const int k = it / 27, slot = it % 27;
+        const int i = l * P.bpl + k;
+        const uint4 pi = S.pos[i];
+        if (meta_ta(pi.w) == meta_tb(pi.w)) continue;
+        acc += bead_delta(S, P, i, pi, meta_ta(pi.w), meta_tb(pi.w), slot, newt, changed);
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) C.w_part[x] = s;
+}
+
+__global__ void k_mdas_accumulate(const SysDev *__restrict__ sys, double dlambda, int n_lip) {
+    const SysDev &S = sys[blockIdx.x];
+    Counters &C = *S.c;
+    if (threadIdx.x != 0) return;
+    const int to_result = n_lip >= 0;
+    const int nl = to_result ? n_lip : 2 * C.n_pairs;
+    double s = 0.0;
+    for (int x = 0; x < nl; ++x) s += C.w_part[x];
+    if (to_result) S.result[8] = s;
+    else C.w += dlambda * s;
+}
+
+void launch_mdas_dE(const LaunchCtx &L, double dlambda) {
+    dim3 g(2 * MAX_PAIRS, L.n_sys);
+    k_mdas_dE<<<g, 128, 0, L.stream>>>(L.sys, -1);
+    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, dlambda, -1);
+}
+
+// Eq. 3: accept with min(1, exp(-w/kT)), i.e. w + kT ln u <= 0, u from
+// Philox (0, move, TAG_MDAS_ACC, 0) words 2-3.
+__global__ void k_mdas_accept(const SysDev *__restrict__ sys) {
+    const SysDev &S = sys[blockIdx.x];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    if (threadIdx.x != 0) return;
+    const uint4 w = draw4(P, 0u, (uint32_t)C.move, TAG_MDAS_ACC, 0u);
+    const double u = unit53(w.z, w.w);
+    const int acc = (C.n_pairs > 0) && (C.w + P.kT * log(u) <= 0.0);
+    S.result[9] = u;
+    C.mdas_accept = acc;
+    if (acc) {
+        int newt[2 * MAX_PAIRS];
+        for (int p = 0; p < C.n_pairs; ++p) {
+            newt[2 * p] = S.ltype[C.pairs[2 * p + 1]];
+            newt[2 * p + 1] = S.ltype[C.pairs[2 * p]];
+        }
+        for (int x = 0; x < 2 * C.n_pairs; ++x) {
+            const int l = C.pairs[x];
+            S.ltype[l] = newt[x];
+            for (int k = 0; k < P.bpl; ++k) {
+                const int bt = P.lbt[newt[x] * 16 + k];
+                S.pos[l * P.bpl + k].w = meta_make(bt, bt, k, l + 1);
+            }
+        }
+    }
+    C.move++;
+    C.moves++;
+    C.moves_accepted += acc;
+    C.in_at = 0;
+    C.lambda = 0.0;
+}
+
+void launch_mdas_accept(const LaunchCtx &L) { k_mdas_accept<<<L.n_sys, 32, 0, L.stream>>>(L.sys); }
+
+template <typename V4>
+__global__ void k_restore(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const int i = bm.y + threadIdx.x;
+    if (i >= S.p->n || S.c->mdas_accept) return;
+    S.pos[i] = S.pos_snap[i];
+    reinterpret_cast<V4 *>(S.vel)[i] = reinterpret_cast<const V4 *>(S.vel_snap)[i];
+}
+
+template <typename V4>
+__global__ void k_snapshot(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const int i = bm.y + threadIdx.x;
+    if (i >= S.p->n) return;
+    S.pos_snap[i] = S.pos[i];
+    reinterpret_cast<V4 *>(S.vel_snap)[i] = reinterpret_cast<const V4 *>(S.vel)[i];
+}
+
+void launch_mdas_restore(const LaunchCtx &L) {
+    if (L.precision == 1) k_restore<Dbl4><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+    else k_restore<float4><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+}
+
+void launch_snapshot(const LaunchCtx &L) {
+    if (L.precision == 1) k_snapshot<Dbl4><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+    else k_snapshot<float4><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+}
+
+// Hypothetical collective type change: lipids C.pairs[0..n) get the types in
+// C.pairs[MAX_PAIRS..MAX_PAIRS+n) as B types; dE = U_B - U_A into result[8];
+// the B marks are removed again afterwards.
+__global__ void k_mark_b(const SysDev *__restrict__ sys, int n, int clear) {
+    const SysDev &S = sys[blockIdx.x];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    if (threadIdx.x != 0) return;
+    for (int x = 0; x < n; ++x) {
+        const int l = C.pairs[x];
+        for (int k = 0; k < P.bpl; ++k) {
+            const int id = l * P.bpl + k;
+            const uint32_t m = S.pos[id].w;
+            const int tb = clear ? meta_ta(m) : (int)P.lbt[C.pairs[MAX_PAIRS + x] * 16 + k];
+            const uint32_t nm = meta_make(meta_ta(m), tb, k, l + 1);
+            S.pos[id].w = nm;
+            S.spos[S.sidx[id]].w = nm;
+        }
+    }
+}
+
+void launch_delta_energy(const LaunchCtx &L, int n) {
+    k_mark_b<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n, 0);
+    dim3 g(2 * MAX_PAIRS, L.n_sys);
+    k_mdas_dE<<<g, 128, 0, L.stream>>>(L.sys, n);
+    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, 0.0, n);
+    k_mark_b<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n, 1);
+}
+
+// ----------------------------------------------------------------- Philox
+__global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int n, uint4 *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(make_uint4((uint32_t)i, c1, c2, c3), k0, k1);
+}
+
+void launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int n, uint4 *out, cudaStream_t st) {
+    k_philox<<<(n + 255) / 256, 256, 0, st>>>(k0, k1, c1, c2, c3, n, out);
+}
+
+}  // namespace mdas

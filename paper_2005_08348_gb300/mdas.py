@@ -1,0 +1,302 @@
+"""Python binding of the C ABI in include/mdas.h (argument marshalling only).
+
+Every computation runs in the CUDA library libmdas.so; this module only
+converts numpy arrays to pointers and back.  PyTorch supplies the CUDA stream
+and, by default, device memory through its caching allocator.  Importing this
+module fails loudly if the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_keep_callbacks = []
+
+MDAS_FP32, MDAS_FP64 = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+          4: "unstable state", 5: "timeout", 6: "busy"}
+MAX_PAIRS = 64
+
+
+class MdasError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("n_beads", C.c_int32), ("n_lipids", C.c_int32), ("beads_per_lipid", C.c_int32),
+        ("n_bead_types", C.c_int32), ("n_lipid_types", C.c_int32),
+        ("box", C.c_double * 3),
+        ("pos", C.c_void_p), ("vel", C.c_void_p),
+        ("lipid_first_bead", C.c_void_p), ("lipid_type", C.c_void_p), ("lipid_bead_type", C.c_void_p),
+        ("water_bead_type", C.c_int32),
+        ("eps", C.c_void_p), ("sigma", C.c_void_p), ("charge", C.c_void_p),
+        ("bonds", C.c_void_p), ("n_bonds", C.c_int32),
+        ("angles", C.c_void_p), ("n_angles", C.c_int32),
+        ("kb", C.c_double), ("b0", C.c_double), ("ktheta", C.c_double), ("theta0_deg", C.c_double),
+        ("rc", C.c_double), ("eps_r", C.c_double), ("eps_rf", C.c_double),
+        ("temperature", C.c_double), ("dt", C.c_double), ("tau_t", C.c_double), ("mass", C.c_double),
+        ("seed", C.c_uint64), ("system_id", C.c_uint32), ("precision", C.c_int32),
+        ("cuda_stream", C.c_void_p), ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_ctx", C.c_void_p),
+    ]
+
+
+class EnergyTerms(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("lj", "rf", "bond", "angle", "kinetic", "potential", "total")] + \
+               [("pairs", C.c_int64)]
+
+
+class SwapStats(C.Structure):
+    _fields_ = [("trials", C.c_int64), ("null_trials", C.c_int64), ("accepted", C.c_int64), ("rounds", C.c_int32)]
+
+
+class MoveResult(C.Structure):
+    _fields_ = [("w", C.c_double), ("u", C.c_double), ("accepted", C.c_int32), ("n_pairs", C.c_int32),
+                ("pairs", C.c_int32 * (2 * MAX_PAIRS))]
+
+
+class StateView(C.Structure):
+    _fields_ = [("pos_fixed", C.c_void_p), ("pos", C.c_void_p), ("vel", C.c_void_p), ("lipid_type", C.c_void_p),
+                ("step", C.c_uint64), ("trial", C.c_uint64), ("move", C.c_uint64), ("at_step", C.c_uint64)]
+
+
+class Counters(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("md_steps", "force_evals", "trials", "null_trials", "accepted",
+                                         "moves", "moves_accepted")]
+
+
+TRIAL_DTYPE = np.dtype([("a", np.int32), ("b", np.int32), ("null", np.int32), ("accepted", np.int32),
+                        ("dE", np.float64), ("u", np.float64), ("index", np.uint64)])
+
+EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_energy", "mdas_md_steps",
+           "mdas_swap_trials", "mdas_trial_log", "mdas_alchemical_move", "mdas_delta_energy", "mdas_get_state",
+           "mdas_set_state", "mdas_cell_list", "mdas_batch_run", "mdas_philox", "mdas_set_kernel_timing",
+           "mdas_pair_kernel_time", "mdas_get_counters", "mdas_last_error", "mdas_status_string"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libmdas.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libmdas.so not found at {path}")
+        L = C.CDLL(path)
+        L.mdas_last_error.restype = C.c_char_p
+        L.mdas_status_string.restype = C.c_char_p
+        L.mdas_destroy_system.restype = None
+        for name in EXPORTS:
+            getattr(L, name)
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(st, sysptr=None):
+    if st != 0:
+        msg = lib().mdas_last_error(sysptr).decode()
+        raise MdasError(st, msg)
+
+
+def _torch_allocator():
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC(alloc), _FREE(free)
+    _keep_callbacks.append((a, f))
+    return a, f
+
+
+def _current_stream():
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class System:
+    """One device-resident membrane system built from a `synth.Membrane`."""
+
+    def __init__(self, m, precision="fp32", stream=None, torch_allocator=True, tau_t=None, dt=None,
+                 temperature=None, seed=None, system_id=None, eps_rf=None):
+        L = lib()
+        self.m = m
+        self.n = m.n_beads
+        self.n_lipids = m.n_lipids
+        self.precision = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
+        k = dict(pos=np.ascontiguousarray(m.pos, np.float64), vel=np.ascontiguousarray(m.vel, np.float64),
+                 first=np.ascontiguousarray(m.lipid_first_bead, np.int32),
+                 lt=np.ascontiguousarray(m.lipid_type, np.int32),
+                 lbt=np.ascontiguousarray(m.lipid_bead_type, np.int32),
+                 eps=np.ascontiguousarray(m.eps, np.float64), sig=np.ascontiguousarray(m.sigma, np.float64),
+                 q=np.ascontiguousarray(m.charge, np.float64), bonds=np.ascontiguousarray(m.bonds, np.int32),
+                 angles=np.ascontiguousarray(m.angles, np.int32))
+        d = Desc()
+        d.n_beads, d.n_lipids = self.n, self.n_lipids
+        d.beads_per_lipid = m.lipid_bead_type.shape[1]
+        d.n_bead_types, d.n_lipid_types = m.eps.shape[0], m.lipid_bead_type.shape[0]
+        d.box = (C.c_double * 3)(*[float(x) for x in m.box])
+        d.pos, d.vel = _p(k["pos"]), _p(k["vel"])
+        d.lipid_first_bead, d.lipid_type, d.lipid_bead_type = _p(k["first"]), _p(k["lt"]), _p(k["lbt"])
+        d.water_bead_type = int(m.water_bead_type)
+        d.eps, d.sigma, d.charge = _p(k["eps"]), _p(k["sig"]), _p(k["q"])
+        d.bonds, d.n_bonds = _p(k["bonds"]), int(m.bonds.shape[0])
+        d.angles, d.n_angles = _p(k["angles"]), int(m.angles.shape[0])
+        d.kb, d.b0, d.ktheta, d.theta0_deg = m.kb, m.b0, m.ktheta, m.theta0_deg
+        d.rc, d.eps_r = m.rc, m.eps_r
+        d.eps_rf = m.eps_rf if eps_rf is None else eps_rf
+        d.temperature = m.temperature if temperature is None else temperature
+        d.dt = m.dt if dt is None else dt
+        d.tau_t = m.tau_t if tau_t is None else tau_t
+        d.mass = m.mass
+        d.seed = int(m.seed if seed is None else seed)
+        d.system_id = int(m.system_id if system_id is None else system_id)
+        d.precision = self.precision
+        self.stream = _current_stream() if stream is None else int(stream)
+        d.cuda_stream = self.stream
+        if torch_allocator:
+            d.dev_alloc, d.dev_free = _torch_allocator()
+        self._ptr = C.c_void_p()
+        _check(L.mdas_create_system(C.byref(d), C.byref(self._ptr)))
+        self.kT = 0.0083144626 * d.temperature
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ptr", None):
+            lib().mdas_destroy_system(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        _check(st, self._ptr)
+
+    # -- evaluation -------------------------------------------------------------
+    def forces(self):
+        F = np.empty((self.n, 3), np.float64)
+        self._ck(lib().mdas_forces(self._ptr, _p(F), None))
+        return F
+
+    def potential(self):
+        u = C.c_double()
+        self._ck(lib().mdas_forces(self._ptr, None, C.byref(u)))
+        return u.value
+
+    def energy(self):
+        t = EnergyTerms()
+        self._ck(lib().mdas_energy(self._ptr, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in EnergyTerms._fields_}
+
+    def delta_energy(self, lipids, new_types):
+        li = np.ascontiguousarray(lipids, np.int32)
+        nt = np.ascontiguousarray(new_types, np.int32)
+        dE = C.c_double()
+        self._ck(lib().mdas_delta_energy(self._ptr, _p(li), _p(nt), int(li.size), C.byref(dE)))
+        return dE.value
+
+    # -- sampling -----------------------------------------------------------------
+    def md_steps(self, n_steps, swap_every=0):
+        self._ck(lib().mdas_md_steps(self._ptr, C.c_int64(n_steps), C.c_int32(swap_every)))
+
+    def swap_trials(self, n, log=True):
+        st = SwapStats()
+        rec = np.zeros(n, TRIAL_DTYPE) if log else None
+        self._ck(lib().mdas_swap_trials(self._ptr, int(n), C.byref(st), _p(rec)))
+        return dict(trials=st.trials, null=st.null_trials, accepted=st.accepted, rounds=st.rounds), rec
+
+    def trial_log(self, first, n):
+        rec = np.zeros(n, TRIAL_DTYPE)
+        self._ck(lib().mdas_trial_log(self._ptr, C.c_uint64(first), int(n), _p(rec)))
+        return rec
+
+    def alchemical_move(self, n_pairs, n_lambda, md_per_lambda, pairs=None):
+        r = MoveResult()
+        pin = None
+        if pairs is not None:
+            pin = np.ascontiguousarray(np.asarray(pairs).reshape(-1), np.int32)
+            n_pairs = pin.size // 2
+        self._ck(lib().mdas_alchemical_move(self._ptr, int(n_pairs), int(n_lambda), int(md_per_lambda), _p(pin),
+                                            C.byref(r)))
+        pr = np.array(r.pairs[: 2 * r.n_pairs], np.int32).reshape(-1, 2)
+        return dict(w=r.w, u=r.u, accepted=bool(r.accepted), n_pairs=r.n_pairs, pairs=pr)
+
+    # -- state ------------------------------------------------------------------
+    def get_state(self):
+        pu = np.empty((self.n, 3), np.uint32)
+        pos = np.empty((self.n, 3), np.float64)
+        vel = np.empty((self.n, 3), np.float64)
+        lt = np.empty(max(self.n_lipids, 1), np.int32)
+        v = StateView(_p(pu), _p(pos), _p(vel), _p(lt), 0, 0, 0, 0)
+        self._ck(lib().mdas_get_state(self._ptr, C.byref(v)))
+        return dict(pos_u=pu, pos=pos, vel=vel, ltype=lt[: self.n_lipids].copy(), step=v.step, trial=v.trial,
+                    move=v.move, at_step=v.at_step)
+
+    def set_state(self, pos_u=None, pos=None, vel=None, ltype=None, step=0, trial=0, move=0, at_step=0):
+        a = None if pos_u is None else np.ascontiguousarray(pos_u, np.uint32)
+        b = None if pos is None else np.ascontiguousarray(pos, np.float64)
+        c = None if vel is None else np.ascontiguousarray(vel, np.float64)
+        d = None if ltype is None else np.ascontiguousarray(ltype, np.int32)
+        v = StateView(_p(a), _p(b), _p(c), _p(d), step, trial, move, at_step)
+        self._ck(lib().mdas_set_state(self._ptr, C.byref(v)))
+
+    def cell_list(self):
+        ids = np.empty(self.n, np.int32)
+        nc = (C.c_int32 * 3)()
+        self._ck(lib().mdas_cell_list(self._ptr, _p(ids), None, nc))
+        ncell = tuple(nc)
+        start = np.empty(ncell[0] * ncell[1] * ncell[2] + 1, np.int32)
+        self._ck(lib().mdas_cell_list(self._ptr, None, _p(start), None))
+        return ids, start, ncell
+
+    def counters(self):
+        c = Counters()
+        self._ck(lib().mdas_get_counters(self._ptr, C.byref(c)))
+        return {k: getattr(c, k) for k, _ in Counters._fields_}
+
+    def set_kernel_timing(self, on=True):
+        self._ck(lib().mdas_set_kernel_timing(self._ptr, int(bool(on))))
+
+    def pair_kernel_time(self, reset=False):
+        ms, n = C.c_double(), C.c_int64()
+        self._ck(lib().mdas_pair_kernel_time(self._ptr, C.byref(ms), C.byref(n), int(bool(reset))))
+        return ms.value, n.value
+
+
+def batch_run(systems, md_steps, swap_trials):
+    arr = (C.c_void_p * len(systems))(*[s._ptr.value for s in systems])
+    _check(lib().mdas_batch_run(arr, len(systems), int(md_steps), int(swap_trials)), systems[0]._ptr)
+
+
+def philox(k0, k1, c1, c2, c3, n):
+    out = np.empty((n, 4), np.uint32)
+    _check(lib().mdas_philox(C.c_uint32(k0), C.c_uint32(k1), C.c_uint32(c1), C.c_uint32(c2), C.c_uint32(c3),
+                             int(n), _p(out)))
+    return out
