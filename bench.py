@@ -1,0 +1,309 @@
+"""Benchmark of the MC-MD hot path on one GB300 (or N replicas on N GPUs).
+
+Workload: the 1152-lipid bilayer (24x24 per leaflet, 3 lipid types 40/40/20,
+~20k water beads, 33.6k beads), FP32 pair arithmetic with 64-bit fixed-point
+force accumulation.  One step = one MC-MD round: 100 MD steps at dt = 20 fs
+with one lipid-exchange trial after every MD step (the run of 10k steps with
+one trial per step is 100 such steps).  Headline: pair interactions per second
+(in-cutoff unordered pairs x MD steps / time); swap trials per second beside.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (the
+reference arm: a deliberately plain program, not a target).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MD_PER_STEP = 100
+PAIR_FLOPS = 30          # algorithmic FP32 flops of one pair interaction (FMA = 2)
+LAUNCHES_PER_MD = 7      # thermostat, 4 cell-list kernels, pair, integrate
+LAUNCHES_PER_TRIAL = 8   # 4 cell-list kernels, proposal, conflicts, dE, resolve
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload():
+    from paper_2005_08348_gb300 import synth
+    return synth.mcmd_large()
+
+
+def config(m, extra=None):
+    c = {"workload": "mcmd-bilayer-1152-lipids-3-types", "lipids": int(m.n_lipids), "beads": int(m.n_beads),
+         "box_nm": [round(float(x), 3) for x in m.box], "md_steps_per_step": MD_PER_STEP,
+         "swap_trials_per_step": MD_PER_STEP, "dt_ps": 0.02, "temperature_K": 310.0,
+         "l2": "flushed between steps (256 MB write, untimed)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_rate(m, budget_s=12.0, min_evals=2):
+    """FP64 oracle: force evaluations + exchange trials on the same system,
+    one host thread, until the time budget is spent."""
+    import oracle
+    o = oracle.Oracle(m)
+    st = o.state()
+    t0 = time.perf_counter()
+    pairs = 0
+    evals = 0
+    trials = 0
+    while evals < min_evals or time.perf_counter() - t0 < budget_s:
+        terms, _ = o.energy(st["pos_u"], ltype=st["ltype"])
+        pairs += terms["pairs"]
+        evals += 1
+        o.md_steps(st, 1, swap_every=1)
+        evals += 1
+        pairs += terms["pairs"]
+        trials += 1
+    dt = time.perf_counter() - t0
+    return dict(pairs_per_s=pairs / dt, trials_per_s=trials / dt, evals=evals, seconds=dt)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    m = workload()
+    import oracle
+    o = oracle.Oracle(m)
+    st = o.state()
+    pairs = o.energy(st["pos_u"], forces=False)[0]["pairs"]
+    for _ in range(args.warmup):
+        o.md_steps(st, 1, swap_every=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.md_steps(st, 1, swap_every=1)
+    dt = time.perf_counter() - t0
+    value = pairs * args.steps / dt
+    sample = f"{args.steps} oracle MD steps with one exchange trial each on the 1152-lipid system"
+    print(json.dumps({
+        "impl": "reference", "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config(m, {"reference_step": "1 MD step + 1 exchange trial (bounded sample)"}),
+        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "swap_trials_per_s": args.steps / dt,
+    }))
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, path, index):
+        self.path, self.index, self.p = path, index, None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p))
+    return {}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2005_08348_gb300 import mdas
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    m = workload()
+    m.system_id = rank
+    sysm = mdas.System(m, precision="fp32", stream=stream.cuda_stream)
+    n_pairs0 = sysm.energy()["pairs"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        sysm.md_steps(MD_PER_STEP, swap_every=1)
+    sysm.set_kernel_timing(True)
+    sysm.pair_kernel_time(reset=True)
+    c0 = sysm.counters()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f"bench_clocks_r{rank}.csv"), local)
+    if not args.no_clocks:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sysm.md_steps(MD_PER_STEP, swap_every=1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = None if args.no_clocks else clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    pair_ms, pair_launches = sysm.pair_kernel_time(reset=True)
+    sysm.set_kernel_timing(False)
+    c1 = sysm.counters()
+    n_pairs1 = sysm.energy()["pairs"]
+    pairs_per_eval = 0.5 * (n_pairs0 + n_pairs1)
+    md = c1["md_steps"] - c0["md_steps"]
+    trials = c1["trials"] - c0["trials"]
+    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item()) / 1e3
+    value = pairs_per_eval * md * ws / tmax
+    trials_per_s = trials * ws / tmax
+
+    # end to end through the C ABI with host buffers: upload the state, run a
+    # round, read the state back, every step
+    st = sysm.get_state()
+    host = {k: st[k] for k in ("pos_u", "vel", "ltype")}
+    for _ in range(2):
+        sysm.set_state(pos_u=host["pos_u"], vel=host["vel"], ltype=host["ltype"], step=st["step"], trial=st["trial"])
+        sysm.md_steps(MD_PER_STEP, swap_every=1)
+        st = sysm.get_state()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sysm.set_state(pos_u=host["pos_u"], vel=host["vel"], ltype=host["ltype"], step=st["step"], trial=st["trial"])
+        sysm.md_steps(MD_PER_STEP, swap_every=1)
+        st = sysm.get_state()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    n = m.n_beads
+    h2d = 16 * n + 16 * n + 4 * m.n_lipids          # fixed-point positions + meta, float4 velocities, types
+    d2h = 16 * n + 16 * n + 4 * m.n_lipids
+    e2e_value = pairs_per_eval * MD_PER_STEP * ws / e2e_s
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
+    pair_avg_s = pair_ms / max(1, pair_launches) / 1e3
+    achieved = pairs_per_eval * PAIR_FLOPS / pair_avg_s / 1e12 if pair_launches else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+    if os.path.exists(tfile):
+        tj = json.load(open(tfile))
+        if tj.get("beads") == n:
+            traffic = tj.get("bytes_per_launch")
+    out = {
+        "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded bilayer, no trained parameters)",
+        "config": config(m, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                             "pairs_per_force_eval": pairs_per_eval}),
+        "swap_trials_per_s": trials_per_s, "md_steps_per_s": md * ws / tmax,
+        "gpu_launches": int(md * LAUNCHES_PER_MD + trials * LAUNCHES_PER_TRIAL),
+        "e2e": {"value": e2e_value, "unit": "pair-interactions/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "roofline": {"kernel": "k_pair<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
+                     "traffic": traffic, "avg_launch_us": pair_avg_s * 1e6, "launches": pair_launches,
+                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                     "flops_per_pair": PAIR_FLOPS},
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if not args.no_cpu_baseline:
+        ob = oracle_rate(m)
+        out["cpu_baseline"] = {"value": ob["pairs_per_s"], "unit": "pair-interactions/s", "cores": 1,
+                               "kind": "oracle", "sample": f"{ob['evals']} FP64 force evaluations "
+                               f"(half of them inside oracle MD steps with one exchange trial) on the same "
+                               f"1152-lipid system, {ob['seconds']:.1f} s, one host thread",
+                               "swap_trials_per_s": ob["trials_per_s"]}
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

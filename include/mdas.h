@@ -77,7 +77,8 @@ typedef struct {
     uint64_t seed;                     /* Philox key = (seed_lo ^ system_id, seed_hi) */
     uint32_t system_id;
     int32_t precision;                 /* mdas_precision: pair arithmetic and velocities */
-    void *cuda_stream;                 /* cudaStream_t to order work on; NULL = legacy default stream */
+    void *cuda_stream;                 /* cudaStream_t to order work on (not the legacy default stream);
+                                          NULL = one non-blocking stream the library shares among such systems */
     void *(*dev_alloc)(size_t bytes, void *stream, void *ctx);   /* optional device allocator */
     void (*dev_free)(void *ptr, void *stream, void *ctx);
     void *alloc_ctx;

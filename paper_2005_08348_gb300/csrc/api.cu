@@ -47,7 +47,7 @@ std::string g_last_error;
 struct mdas_system {
     Params hp;
     SysDev hs;
-    int n = 0, n_lip = 0, bpl = 0, precision = 0;
+    int n = 0, n_lip = 0, bpl = 0, precision = 0, water_bt = 0;
     cudaStream_t stream = nullptr;
     void *(*dev_alloc)(size_t, void *, void *) = nullptr;
     void (*dev_free)(void *, void *, void *) = nullptr;
@@ -66,6 +66,16 @@ struct mdas_system {
 namespace {
 
 std::map<std::vector<mdas_system *>, std::unique_ptr<Batch>> g_batches;
+
+// The stream of systems created with cuda_stream == NULL: one non-blocking
+// stream per process (graph capture is not possible on the legacy stream).
+cudaError_t shared_stream(cudaStream_t *out) {
+    static cudaStream_t st = nullptr;
+    static cudaError_t err = cudaErrorNotReady;
+    if (err == cudaErrorNotReady) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    *out = st;
+    return err;
+}
 
 mdas_status fail(mdas_system *s, mdas_status st, const std::string &msg) {
     if (s) s->err = msg;
@@ -194,7 +204,7 @@ mdas_status check_err(mdas_system *s, Batch &b) {
         for (auto *x : b.sys) x->unstable = true;
         std::string why;
         if (err & ERR_NONFINITE) why += " non-finite velocity;";
-        if (err & ERR_STAGE_OVERFLOW) why += " more than 1024 beads in a 27-cell neighbourhood;";
+        if (err & ERR_STAGE_OVERFLOW) why += " more than 768 beads in a 27-cell neighbourhood;";
         if (err & ERR_TIMEOUT) why += " bounded wait expired;";
         if (err & ERR_ROUNDS) why += " exchange rounds exhausted;";
         return fail(s, MDAS_ERR_UNSTABLE, "unstable:" + why);
@@ -375,9 +385,14 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         cudaError_t e = setup_kernels();
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "create: kernel setup");
     }
+    cudaStream_t stream = (cudaStream_t)d->cuda_stream;
+    if (!stream) {
+        cudaError_t e = shared_stream(&stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "create: stream");
+    }
     s = new mdas_system();
-    s->n = n; s->n_lip = nl; s->bpl = bpl; s->precision = d->precision;
-    s->stream = (cudaStream_t)d->cuda_stream;
+    s->n = n; s->n_lip = nl; s->bpl = bpl; s->precision = d->precision; s->water_bt = d->water_bead_type;
+    s->stream = stream;
     s->dev_alloc = d->dev_alloc; s->dev_free = d->dev_free; s->alloc_ctx = d->alloc_ctx;
     if ((s->dev_alloc == nullptr) != (s->dev_free == nullptr)) {
         delete s;
@@ -394,6 +409,8 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         P.box[k] = d->box[k];
         P.qs[k] = d->box[k] / TWO32;
         P.qsf[k] = (float)P.qs[k];
+        P.qsh[k] = (float)P.qs[k];
+        P.qsl[k] = (float)(P.qs[k] - (double)P.qsh[k]);
         P.qdt[k] = d->dt * TWO32 / d->box[k];
         P.rcu[k] = (uint32_t)std::ceil(d->rc / P.qs[k]) + 2;
     }
@@ -401,7 +418,10 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     P.krf = d->eps_rf <= 0 ? 1.0 / (2.0 * d->rc * d->rc * d->rc)
                            : (d->eps_rf - d->eps_r) / ((2.0 * d->eps_rf + d->eps_r) * d->rc * d->rc * d->rc);
     P.crf = 1.0 / d->rc + P.krf * d->rc * d->rc;
-    P.rc2f = (float)P.rc2;
+    // float cull bounds: every pair with r^2 < rc^2 passes rc2f; pairs in
+    // [rc2f_lo, rc2f) are re-decided exactly from integer offsets
+    P.rc2f = std::nextafter((float)(P.rc2 * (1.0 + 1e-5)), 1e30f);
+    P.rc2f_lo = (float)(P.rc2 * (1.0 - 1e-5));
     P.krf2f = (float)(2.0 * P.krf);
     P.dt = d->dt; P.tau_t = d->tau_t; P.mass = d->mass; P.kT = BOLTZ * d->temperature;
     P.dt_over_m = d->dt / d->mass;
@@ -780,8 +800,10 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
         CK(cudaMemcpy(lt.data(), s->hs.ltype, 4ull * nl, cudaMemcpyDeviceToHost));
     }
     std::vector<uint4> pos(n);
-    CK(cudaMemcpyAsync(pos.data(), s->hs.pos, 16ull * n, cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
+    if (!in->pos_fixed && !in->pos) {   // keep the current coordinates
+        CK(cudaMemcpyAsync(pos.data(), s->hs.pos, 16ull * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
     for (int i = 0; i < n; ++i) {
         if (in->pos_fixed) {
             pos[i].x = in->pos_fixed[3 * i]; pos[i].y = in->pos_fixed[3 * i + 1]; pos[i].z = in->pos_fixed[3 * i + 2];
@@ -794,6 +816,8 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
         if (i < nl * bpl) {
             const int bt = s->hp.lbt[lt[i / bpl] * 16 + i % bpl];
             pos[i].w = meta_make(bt, bt, i % bpl, i / bpl + 1);
+        } else {
+            pos[i].w = meta_make(s->water_bt, s->water_bt, 15, 0);
         }
     }
     CK(cudaMemcpyAsync(s->hs.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));

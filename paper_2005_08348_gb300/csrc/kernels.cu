@@ -189,13 +189,27 @@ void launch_thermostat(const LaunchCtx &L) {
 
 // ------------------------------------------------------------ pair forces
 // One CTA per cell.  The 27 neighbour cells are staged in shared memory in a
-// frame centred on the cell (exact integer wrap-around differences, so the
-// staged copy of every bead is its periodic image nearest the cell).  Threads
-// are (i-bead, j-stream) pairs; each thread first culls its candidates into a
-// private queue of in-cutoff, non-excluded partners, then evaluates the queue
-// with all lanes busy.  Partial forces are summed over the streams in a fixed
-// order and stored once per bead, so results do not depend on scheduling.
-// Every pair is evaluated from both sides (no atomics on the j bead).
+// frame centred on the cell: each bead's exact integer offset from the centre
+// (wrap-around difference, so every staged copy is the periodic image nearest
+// the cell) and its coordinates in nm.  Threads are (i-bead, j-stream) pairs;
+// each thread first culls its candidates into a private queue of in-cutoff,
+// non-excluded partners (candidates within float rounding of rc are decided
+// exactly from the integer offsets), then evaluates the queue with all lanes
+// busy.  In FP32 the separation of a queued pair comes from the exact integer
+// difference; r^-2 is a correctly rounded reciprocal and r^-6 its error-free
+// cube, so a pair force carries only a few roundings.  Partial forces are
+// summed over the streams in a fixed order and stored once per bead; every
+// pair is evaluated from both sides (no atomics on the j bead).
+
+// a - b of two frame offsets, wrapped to 32 bits (the minimum image)
+__device__ __forceinline__ int wrap_diff(int a, int b) { return (int)((uint32_t)a - (uint32_t)b); }
+
+template <typename Real>
+struct StagedPos;
+template <>
+struct __align__(16) StagedPos<float> { float x, y, z; uint32_t m; };
+template <>
+struct __align__(16) StagedPos<double> { double x, y, z; uint32_t m, pad; };
 
 template <typename Real, bool LAM, bool ENERGY>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
@@ -205,22 +219,21 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     const Params &P = *S.p;
     const int c = bm.y;
     const int t = threadIdx.x;
+    constexpr bool F32 = sizeof(Real) == 4;
 
-    Real *tf12 = reinterpret_cast<Real *>(smem);
+    StagedPos<Real> *sp = reinterpret_cast<StagedPos<Real> *>(smem);         // [STAGE_CAP]
+    int4 *si = reinterpret_cast<int4 *>(sp + STAGE_CAP);                      // [STAGE_CAP]
+    Real *tf12 = reinterpret_cast<Real *>(si + STAGE_CAP);
     Real *tf6 = tf12 + 256;
     Real *tqq = tf6 + 256;
-    Real *sx = tqq + 256;
-    Real *sy = sx + STAGE_CAP;
-    Real *sz = sy + STAGE_CAP;
-    uint32_t *sm = reinterpret_cast<uint32_t *>(sz + STAGE_CAP);
-    uint16_t *q = reinterpret_cast<uint16_t *>(sm + STAGE_CAP);          // [QCAP][PAIR_THREADS]
-    Real *red = reinterpret_cast<Real *>(q + QCAP * PAIR_THREADS);       // [3][PAIR_THREADS]
+    Real *red = tqq + 256;                                                    // [3][PAIR_THREADS]
+    uint16_t *q = reinterpret_cast<uint16_t *>(red + 3 * PAIR_THREADS);       // [QCAP][PAIR_THREADS]
 
     __shared__ int cst[27], ccnt[27], coff[28];
     __shared__ double ered[3][PAIR_THREADS];
 
     for (int k = t; k < 256; k += PAIR_THREADS) {
-        if (sizeof(Real) == 4) {
+        if (F32) {
             tf12[k] = (Real)P.f12f[k]; tf6[k] = (Real)P.f6f[k]; tqq[k] = (Real)P.qqf[k];
         } else {
             tf12[k] = (Real)(12.0 * P.c12[k]); tf6[k] = (Real)(6.0 * P.c6[k]); tqq[k] = (Real)P.qq[k];
@@ -256,16 +269,21 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         int s = 0;
         while (k >= coff[s + 1]) ++s;
         const uint4 v = S.spos[cst[s] + (k - coff[s])];
-        if (sizeof(Real) == 4) {
-            sx[k] = (Real)((float)(int)(v.x - rx) * P.qsf[0]);
-            sy[k] = (Real)((float)(int)(v.y - ry) * P.qsf[1]);
-            sz[k] = (Real)((float)(int)(v.z - rz) * P.qsf[2]);
+        const int ox = (int)(v.x - rx), oy = (int)(v.y - ry), oz = (int)(v.z - rz);
+        StagedPos<Real> e;
+        if (F32) {
+            const float fx = (float)ox, fy = (float)oy, fz = (float)oz;
+            e.x = (Real)fmaf(fx, P.qsh[0], fx * P.qsl[0]);
+            e.y = (Real)fmaf(fy, P.qsh[1], fy * P.qsl[1]);
+            e.z = (Real)fmaf(fz, P.qsh[2], fz * P.qsl[2]);
         } else {
-            sx[k] = (Real)((double)(int)(v.x - rx) * P.qs[0]);
-            sy[k] = (Real)((double)(int)(v.y - ry) * P.qs[1]);
-            sz[k] = (Real)((double)(int)(v.z - rz) * P.qs[2]);
+            e.x = (Real)((double)ox * P.qs[0]);
+            e.y = (Real)((double)oy * P.qs[1]);
+            e.z = (Real)((double)oz * P.qs[2]);
         }
-        sm[k] = v.w;
+        e.m = v.w;
+        sp[k] = e;
+        si[k] = make_int4(ox, oy, oz, 0);
     }
     __syncthreads();
 
@@ -273,17 +291,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     const int IW = ni <= 16 ? 16 : 32;
     const int NS = PAIR_THREADS / IW;
     const int il = t % IW, js = t / IW;
-    const Real rc2 = (Real)(sizeof(Real) == 4 ? (double)P.rc2f : P.rc2);
-    const Real krf2 = (Real)(sizeof(Real) == 4 ? (double)P.krf2f : 2.0 * P.krf);
+    const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
+    const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
+    const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
     const Real lam = LAM ? (Real)S.c->lambda : (Real)0;
     double elj = 0.0, erf = 0.0, epairs = 0.0;
 
     for (int ib = 0; ib < ni; ib += IW) {
         const int i = ib + il;
         const bool valid = i < ni;
-        const int si = self0 + (valid ? i : 0);
-        const Real xi = sx[si], yi = sy[si], zi = sz[si];
-        const uint32_t mi = sm[si];
+        const int sidx = self0 + (valid ? i : 0);
+        const StagedPos<Real> pi = sp[sidx];
+        const int4 ii = si[sidx];
+        const uint32_t mi = pi.m;
         const int tai = meta_ta(mi), tbi = meta_tb(mi), ki = meta_k(mi);
         const uint32_t lipi = mi >> 12;
         const uint32_t emask = P.excl[ki];
@@ -293,9 +313,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         auto flush = [&](int count) {
             for (int e = 0; e < count; ++e) {
                 const int j = q[e * PAIR_THREADS + t];
-                const Real dx = xi - sx[j], dy = yi - sy[j], dz = zi - sz[j];
+                const StagedPos<Real> pj = sp[j];
+                Real dx, dy, dz;
+                if (F32) {
+                    const int4 ij = si[j];
+                    const float fx = (float)wrap_diff(ii.x, ij.x), fy = (float)wrap_diff(ii.y, ij.y), fz = (float)wrap_diff(ii.z, ij.z);
+                    dx = (Real)fmaf(fx, P.qsh[0], fx * P.qsl[0]);
+                    dy = (Real)fmaf(fy, P.qsh[1], fy * P.qsl[1]);
+                    dz = (Real)fmaf(fz, P.qsh[2], fz * P.qsl[2]);
+                } else {
+                    dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
+                }
                 const Real r2 = dx * dx + dy * dy + dz * dz;
-                const uint32_t mj = sm[j];
+                const uint32_t mj = pj.m;
                 const int ta = tai * 16 + meta_ta(mj);
                 Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
                 if (LAM) {
@@ -304,11 +334,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
                     f6 = ((Real)1 - lam) * f6 + lam * tf6[tb];
                     qq = ((Real)1 - lam) * qq + lam * tqq[tb];
                 }
-                Real rinv;
-                if (sizeof(Real) == 4) rinv = (Real)rsqrtf((float)r2);
-                else rinv = (Real)(1.0 / sqrt((double)r2));
-                const Real r2inv = rinv * rinv;
-                const Real r6inv = r2inv * r2inv * r2inv;
+                Real rinv, r2inv, r6inv;
+                if (F32) {
+                    const float r2i = __frcp_rn((float)r2);
+                    const float p = r2i * r2i;
+                    const float pe = fmaf(r2i, r2i, -p);                 // exact error of the square
+                    r6inv = (Real)fmaf(p, r2i, pe * r2i);               // r2i^3 rounded once
+                    r2inv = (Real)r2i;
+                    rinv = (Real)rsqrtf((float)r2);
+                } else {
+                    rinv = (Real)(1.0 / sqrt((double)r2));
+                    r2inv = rinv * rinv;
+                    r6inv = r2inv * r2inv * r2inv;
+                }
                 const Real fs = (f12 * r6inv - f6) * r6inv * r2inv + qq * (rinv * r2inv - krf2);
                 ax += fs * dx; ay += fs * dy; az += fs * dz;
                 if (ENERGY) {
@@ -332,12 +370,21 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         };
 
         for (int j = js; j < M; j += NS) {
-            const Real dx = xi - sx[j], dy = yi - sy[j], dz = zi - sz[j];
+            const StagedPos<Real> pj = sp[j];
+            const Real dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const Real r2 = dx * dx + dy * dy + dz * dz;
-            bool hit = valid && (r2 < rc2) && (j != si);
+            bool hit = valid && (r2 < rc2) && (j != sidx);
             if (hit) {
-                const uint32_t mj = sm[j];
+                const uint32_t mj = pj.m;
                 if (lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u)) hit = false;
+                if (F32 && hit && r2 >= rc2lo) {
+                    // within float rounding of the cutoff: decide from the exact offsets
+                    const int4 ij = si[j];
+                    const double ex = (double)wrap_diff(ii.x, ij.x) * P.qs[0];
+                    const double ey = (double)wrap_diff(ii.y, ij.y) * P.qs[1];
+                    const double ez = (double)wrap_diff(ii.z, ij.z) * P.qs[2];
+                    hit = ex * ex + ey * ey + ez * ez < P.rc2;
+                }
             }
             if (hit) {
                 q[nq * PAIR_THREADS + t] = (uint16_t)j;
@@ -358,7 +405,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
                 fz += red[2 * PAIR_THREADS + s * IW + t];
             }
             const int id = S.sorted_id[ifirst + ib + t];
-            if (sizeof(Real) == 4) {
+            if (F32) {
                 S.fx[id] = __float2ll_rn((float)fx * 4294967296.0f);
                 S.fy[id] = __float2ll_rn((float)fy * 4294967296.0f);
                 S.fz[id] = __float2ll_rn((float)fz * 4294967296.0f);
@@ -385,8 +432,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
 
 template <typename Real>
 static size_t pair_smem() {
-    return sizeof(Real) * (3 * 256 + 3 * STAGE_CAP) + sizeof(uint32_t) * STAGE_CAP +
-           sizeof(uint16_t) * QCAP * PAIR_THREADS + sizeof(Real) * 3 * PAIR_THREADS;
+    return sizeof(StagedPos<Real>) * STAGE_CAP + sizeof(int4) * STAGE_CAP + sizeof(Real) * (3 * 256 + 3 * PAIR_THREADS) +
+           sizeof(uint16_t) * QCAP * PAIR_THREADS;
 }
 
 template <typename Real, bool LAM, bool ENERGY>

@@ -13,8 +13,8 @@ struct __align__(32) Dbl4 {
 
 constexpr int MAXT = 16;               // bead types, lipid types, beads per lipid
 constexpr int PAIR_THREADS = 128;      // threads per cell in the pair kernel
-constexpr int STAGE_CAP = 1024;        // neighbour beads staged per cell (27 cells)
-constexpr int QCAP = 48;               // per-thread hit queue of the pair kernel
+constexpr int STAGE_CAP = 768;         // neighbour beads staged per cell (27 cells)
+constexpr int QCAP = 40;               // per-thread hit queue of the pair kernel
 constexpr int BEAD_BLOCK = 256;        // beads per block of per-bead kernels
 constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
@@ -45,9 +45,9 @@ struct Params {
     int n, n_lip, bpl, n_bt, n_lt, n_lipid_beads;
     int nc[3], n_cells;
     double box[3], qs[3], qdt[3];      // qs = L/2^32; qdt = dt 2^32 / L
-    float qsf[3];
+    float qsf[3], qsh[3], qsl[3];      // L/2^32 as float, and as a float pair hi + lo
     double rc, rc2, krf, crf;
-    float rc2f, krf2f;                 // rc^2, 2 k_rf
+    float rc2f, rc2f_lo, krf2f;        // rc^2 rounded up, rc^2 (1 - 1e-5), 2 k_rf
     double dt, tau_t, mass, kT, dt_over_m;
     int nf[2];
     double ktarget[2];

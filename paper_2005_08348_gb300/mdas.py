@@ -134,6 +134,8 @@ def _torch_allocator():
 
 
 def _current_stream():
+    # torch's default stream is the legacy stream (handle 0), on which CUDA
+    # graphs cannot be captured; 0 lets the library use its shared stream
     import torch
     return int(torch.cuda.current_stream().cuda_stream)
 
@@ -177,7 +179,7 @@ class System:
         d.system_id = int(m.system_id if system_id is None else system_id)
         d.precision = self.precision
         self.stream = _current_stream() if stream is None else int(stream)
-        d.cuda_stream = self.stream
+        d.cuda_stream = self.stream or None
         if torch_allocator:
             d.dev_alloc, d.dev_free = _torch_allocator()
         self._ptr = C.c_void_p()
