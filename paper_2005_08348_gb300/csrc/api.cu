@@ -58,6 +58,7 @@ struct mdas_system {
     std::unique_ptr<Batch> solo;
     std::string err;
     bool unstable = false;
+    bool cells_valid = false;   // the cell list matches the current positions and types
     bool timing = false;
     double pair_ms = 0.0;
     long long pair_launches = 0;
@@ -215,10 +216,14 @@ mdas_status check_err(mdas_system *s, Batch &b) {
 // Capture (or reuse) a graph of `units` repetitions of [steps_per_unit MD
 // steps + optional exchange trial]; timing adds event pairs around every
 // pair-kernel launch.
+// With trials, the cell list a trial builds serves the next MD step as well
+// (positions do not change in between); reuse_first also skips the first
+// step's build when the list is already valid when the graph starts.
 mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, bool trial, bool lambda, bool timing,
-                      GraphEntry **out) {
+                      bool reuse_first, GraphEntry **out) {
     char key[96];
-    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d", units, steps_per_unit, (int)trial, (int)lambda, (int)timing);
+    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d_r%d", units, steps_per_unit, (int)trial, (int)lambda, (int)timing,
+             (int)reuse_first);
     auto it = b.graphs.find(key);
     if (it != b.graphs.end()) { *out = &it->second; return MDAS_OK; }
     GraphEntry ge;
@@ -237,11 +242,13 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
     for (int u = 0; u < units; ++u) {
         for (int k = 0; k < steps_per_unit; ++k) {
             launch_thermostat(L);
-            launch_cells(L);
+            const bool have_cells = trial && k == 0 && (u > 0 || reuse_first);
+            if (!have_cells) launch_cells(L);
             if (timing) {
-                cudaEventRecord(ge.pair_events[ev].first, b.stream);
+                // external event nodes: recorded (and timed) at every replay
+                cudaEventRecordWithFlags(ge.pair_events[ev].first, b.stream, cudaEventRecordExternal);
                 launch_pair(L, lambda, false, b.precision == 1);
-                cudaEventRecord(ge.pair_events[ev].second, b.stream);
+                cudaEventRecordWithFlags(ge.pair_events[ev].second, b.stream, cudaEventRecordExternal);
                 ++ev;
             } else {
                 launch_pair(L, lambda, false, b.precision == 1);
@@ -284,8 +291,13 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every) 
     for (auto *x : b.sys) timing = timing || x->timing;
     const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
     if (n_units > 0) {
+        if (trial) {
+            bool valid = true;
+            for (auto *x : b.sys) valid = valid && x->cells_valid;
+            if (!valid) launch_cells(b.ctx());
+        }
         GraphEntry *ge;
-        mdas_status st = get_graph(s, b, (int)E, (int)unit, trial, false, timing, &ge);
+        mdas_status st = get_graph(s, b, (int)E, (int)unit, trial, false, timing, trial, &ge);
         if (st != MDAS_OK) return st;
         for (long long r = 0; r < n_units / E; ++r) {
             st = replay(s, b, ge);
@@ -293,13 +305,15 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every) 
         }
         const long long left = n_units % E;
         if (left > 0) {
-            st = get_graph(s, b, (int)left, (int)unit, trial, false, timing, &ge);
+            st = get_graph(s, b, (int)left, (int)unit, trial, false, timing, trial, &ge);
             if (st != MDAS_OK) return st;
             st = replay(s, b, ge);
             if (st != MDAS_OK) return st;
         }
     }
     for (long long k = 0; k < rem; ++k) md_step_launches(b, false);
+    const bool valid_after = trial && rem == 0 && n_units > 0;
+    for (auto *x : b.sys) x->cells_valid = valid_after;
     CK(cudaGetLastError());
     return check_err(s, b);
 }
@@ -324,6 +338,7 @@ mdas_status run_trials(mdas_system *s, Batch &b, int n, int *rounds_out) {
         }
         done += m;
     }
+    for (auto *x : b.sys) x->cells_valid = true;
     CK(cudaGetLastError());
     if (rounds_out) *rounds_out = rounds;
     return check_err(s, b);
@@ -491,7 +506,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.pos_snap, 16ull * n}, {(void **)&H.vel_snap, vsz * n},
         {(void **)&H.ltype_snap, 4ull * std::max(nl, 1)},
         {(void **)&H.tprop, 16ull * MAX_ROUND_TRIALS}, {(void **)&H.tu, 8ull * MAX_ROUND_TRIALS},
-        {(void **)&H.tdE, 8ull * MAX_ROUND_TRIALS}, {(void **)&H.tstate, 4ull * MAX_ROUND_TRIALS},
+        {(void **)&H.tdE, 8ull * 9 * MAX_ROUND_TRIALS}, {(void **)&H.tstate, 4ull * MAX_ROUND_TRIALS},
         {(void **)&H.conflict, 4ull * MAX_ROUND_TRIALS * (MAX_ROUND_TRIALS / 32)},
         {(void **)&H.lbox, 32ull * MAX_ROUND_TRIALS}, {(void **)&H.lhalf, 32ull * MAX_ROUND_TRIALS},
         {(void **)&H.log, sizeof(TrialRec) * (size_t)LOG_CAP}, {(void **)&H.result, 8ull * 64},
@@ -584,6 +599,7 @@ mdas_status mdas_forces(mdas_system *s, double *f_out, double *u_out) {
     LaunchCtx L = b.ctx();
     if (f_out) {
         launch_cells(L);
+        s->cells_valid = true;
         launch_pair(L, false, false, s->precision == 1);
         launch_total_force(L, s->fout, 0);
         CK(cudaMemcpyAsync(f_out, s->fout, 24ull * s->n, cudaMemcpyDeviceToHost, s->stream));
@@ -604,6 +620,7 @@ mdas_status mdas_energy(mdas_system *s, mdas_energy_terms *out) {
     Batch &b = *s->solo;
     LaunchCtx L = b.ctx();
     launch_cells(L);
+    s->cells_valid = true;
     launch_pair(L, false, true, true);
     launch_energy_reduce(L);
     double r[8];
@@ -697,7 +714,7 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
             launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
             if (md_per_lambda > 0) {
                 GraphEntry *ge;
-                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, &ge);
+                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, &ge);
                 if (st != MDAS_OK) return st;
                 st = replay(s, b, ge);
                 if (st != MDAS_OK) return st;
@@ -709,6 +726,7 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
     launch_mdas_accept(L);
     launch_mdas_restore(L);
     launch_kinetic(L);
+    s->cells_valid = false;
     Counters c;
     double r[10];
     CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
@@ -743,6 +761,7 @@ mdas_status mdas_delta_energy(mdas_system *s, const int32_t *lipids, const int32
     CK(cudaMemcpyAsync(&dc->pairs[0], lipids, 4ull * n, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(&dc->pairs[MAX_PAIRS], new_types, 4ull * n, cudaMemcpyHostToDevice, s->stream));
     launch_cells(L);
+    s->cells_valid = true;
     launch_delta_energy(L, n);
     CK(cudaMemcpyAsync(dE, s->hs.result + 8, 8, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -845,6 +864,7 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
     s->unstable = false;
+    s->cells_valid = false;
     return MDAS_OK;
 }
 

@@ -162,21 +162,31 @@ __device__ double bussi_alpha(const Params &P, double K, int nf, double kt, uint
     return sqrt(knew / K);
 }
 
-__global__ void k_thermostat(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+__global__ void __launch_bounds__(256) k_thermostat(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     const SysDev &S = sys[bmap[blockIdx.x].x];
     const Params &P = *S.p;
     Counters &C = *S.c;
-    const int g = threadIdx.x;
+    const int t = threadIdx.x;
+    // group kinetic energies: strided partial sums, then a fixed-order tree
+    __shared__ double ks[2][256];
+    double k0 = 0.0, k1 = 0.0;
+    for (int b = t; b < S.n_bead_blocks; b += 256) { k0 += S.ke_part[2 * b]; k1 += S.ke_part[2 * b + 1]; }
+    ks[0][t] = k0;
+    ks[1][t] = k1;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) { ks[0][t] += ks[0][t + w]; ks[1][t] += ks[1][t + w]; }
+        __syncthreads();
+    }
     const int in_at = C.in_at;
     const unsigned long long ctr = in_at ? C.at_step : C.step;
-    if (g < 2) {
-        double K = 0.0;
-        for (int b = 0; b < S.n_bead_blocks; ++b) K += S.ke_part[2 * b + g];
-        C.alpha[g] = bussi_alpha(P, K, P.nf[g], P.ktarget[g], (uint32_t)g, (uint32_t)ctr,
+    if ((t & 31) == 0 && t < 64) {          // one warp per coupling group
+        const int g = t >> 5;
+        C.alpha[g] = bussi_alpha(P, ks[g][0], P.nf[g], P.ktarget[g], (uint32_t)g, (uint32_t)ctr,
                                  in_at ? TAG_AT_THERMO : TAG_THERMO);
     }
     __syncthreads();
-    if (g == 0) {
+    if (t == 0) {
         if (in_at) C.at_step = ctr + 1; else C.step = ctr + 1;
         C.md_steps++;
         C.force_evals++;
@@ -184,22 +194,22 @@ __global__ void k_thermostat(const SysDev *__restrict__ sys, const int2 *__restr
 }
 
 void launch_thermostat(const LaunchCtx &L) {
-    k_thermostat<<<L.syss->n, 32, 0, L.stream>>>(L.sys, L.syss->d);
+    k_thermostat<<<L.syss->n, 256, 0, L.stream>>>(L.sys, L.syss->d);
 }
 
 // ------------------------------------------------------------ pair forces
-// One CTA per cell.  The 27 neighbour cells are staged in shared memory in a
-// frame centred on the cell: each bead's exact integer offset from the centre
-// (wrap-around difference, so every staged copy is the periodic image nearest
-// the cell) and its coordinates in nm.  Threads are (i-bead, j-stream) pairs;
-// each thread first culls its candidates into a private queue of in-cutoff,
-// non-excluded partners (candidates within float rounding of rc are decided
-// exactly from the integer offsets), then evaluates the queue with all lanes
-// busy.  In FP32 the separation of a queued pair comes from the exact integer
-// difference; r^-2 is a correctly rounded reciprocal and r^-6 its error-free
-// cube, so a pair force carries only a few roundings.  Partial forces are
-// summed over the streams in a fixed order and stored once per bead; every
-// pair is evaluated from both sides (no atomics on the j bead).
+// One CTA per cell.  The 27 neighbour cells are staged in shared memory (in
+// chunks of STAGE_CAP beads) in a frame centred on the cell: each bead's exact
+// integer offset from the centre (wrap-around difference, so every staged copy
+// is the periodic image nearest the cell) and its coordinates in nm.  Threads
+// are (i-bead, j-stream) pairs; each thread first culls its candidates into a
+// private queue of in-cutoff, non-excluded partners (candidates within float
+// rounding of rc are decided exactly from the integer offsets), then evaluates
+// the queue with all lanes busy.  In FP32 the separation of a queued pair comes
+// from the exact integer difference; r^-2 is a correctly rounded reciprocal and
+// r^-6 its error-free cube, so a pair force carries only a few roundings.
+// Partial forces are summed over the streams in a fixed order and stored once
+// per bead; every pair is evaluated from both sides (no atomics on the j bead).
 
 // a - b of two frame offsets, wrapped to 32 bits (the minimum image)
 __device__ __forceinline__ int wrap_diff(int a, int b) { return (int)((uint32_t)a - (uint32_t)b); }
@@ -207,9 +217,26 @@ __device__ __forceinline__ int wrap_diff(int a, int b) { return (int)((uint32_t)
 template <typename Real>
 struct StagedPos;
 template <>
-struct __align__(16) StagedPos<float> { float x, y, z; uint32_t m; };
+struct __align__(16) StagedPos<float> { float x, y, z, pad; };
 template <>
-struct __align__(16) StagedPos<double> { double x, y, z; uint32_t m, pad; };
+struct __align__(16) StagedPos<double> { double x, y, z, pad; };
+
+template <typename Real>
+__device__ __forceinline__ StagedPos<Real> frame_coords(const Params &P, int ox, int oy, int oz) {
+    StagedPos<Real> e;
+    if (sizeof(Real) == 4) {
+        const float fx = (float)ox, fy = (float)oy, fz = (float)oz;
+        e.x = (Real)fmaf(fx, P.qsh[0], fx * P.qsl[0]);
+        e.y = (Real)fmaf(fy, P.qsh[1], fy * P.qsl[1]);
+        e.z = (Real)fmaf(fz, P.qsh[2], fz * P.qsl[2]);
+    } else {
+        e.x = (Real)((double)ox * P.qs[0]);
+        e.y = (Real)((double)oy * P.qs[1]);
+        e.z = (Real)((double)oz * P.qs[2]);
+    }
+    e.pad = 0;
+    return e;
+}
 
 template <typename Real, bool LAM, bool ENERGY>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
@@ -218,16 +245,17 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     const SysDev &S = sys[bm.x];
     const Params &P = *S.p;
     const int c = bm.y;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr bool F32 = sizeof(Real) == 4;
+    constexpr int UNROLL = 4;
 
-    StagedPos<Real> *sp = reinterpret_cast<StagedPos<Real> *>(smem);         // [STAGE_CAP]
-    int4 *si = reinterpret_cast<int4 *>(sp + STAGE_CAP);                      // [STAGE_CAP]
+    StagedPos<Real> *sf = reinterpret_cast<StagedPos<Real> *>(smem);          // [STAGE_CAP]
+    int4 *si = reinterpret_cast<int4 *>(sf + STAGE_CAP);                       // [STAGE_CAP] offsets + meta
     Real *tf12 = reinterpret_cast<Real *>(si + STAGE_CAP);
     Real *tf6 = tf12 + 256;
     Real *tqq = tf6 + 256;
-    Real *red = tqq + 256;                                                    // [3][PAIR_THREADS]
-    uint16_t *q = reinterpret_cast<uint16_t *>(red + 3 * PAIR_THREADS);       // [QCAP][PAIR_THREADS]
+    uint16_t *q = reinterpret_cast<uint16_t *>(tqq + 256);                     // [QCAP][PAIR_THREADS]
+    Real *red = reinterpret_cast<Real *>(q);                                   // aliases q after the queues drain
 
     __shared__ int cst[27], ccnt[27], coff[28];
     __shared__ double ered[3][PAIR_THREADS];
@@ -257,38 +285,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     }
     __syncthreads();
     const int M = coff[27];
-    if (M > STAGE_CAP) {
-        if (t == 0) atomicOr(&S.c->err, ERR_STAGE_OVERFLOW);
-        return;
-    }
+    const int ni = ccnt[13], ifirst = cst[13];
     // frame origin: the cell centre in fixed-point units
     const uint32_t rx = (uint32_t)((((unsigned long long)(2 * cx + 1)) << 32) / (2ull * nx));
     const uint32_t ry = (uint32_t)((((unsigned long long)(2 * cy + 1)) << 32) / (2ull * ny));
     const uint32_t rz = (uint32_t)((((unsigned long long)(2 * cz + 1)) << 32) / (2ull * nz));
-    for (int k = t; k < M; k += PAIR_THREADS) {
-        int s = 0;
-        while (k >= coff[s + 1]) ++s;
-        const uint4 v = S.spos[cst[s] + (k - coff[s])];
-        const int ox = (int)(v.x - rx), oy = (int)(v.y - ry), oz = (int)(v.z - rz);
-        StagedPos<Real> e;
-        if (F32) {
-            const float fx = (float)ox, fy = (float)oy, fz = (float)oz;
-            e.x = (Real)fmaf(fx, P.qsh[0], fx * P.qsl[0]);
-            e.y = (Real)fmaf(fy, P.qsh[1], fy * P.qsl[1]);
-            e.z = (Real)fmaf(fz, P.qsh[2], fz * P.qsl[2]);
-        } else {
-            e.x = (Real)((double)ox * P.qs[0]);
-            e.y = (Real)((double)oy * P.qs[1]);
-            e.z = (Real)((double)oz * P.qs[2]);
-        }
-        e.m = v.w;
-        sp[k] = e;
-        si[k] = make_int4(ox, oy, oz, 0);
-    }
-    __syncthreads();
 
-    const int ni = ccnt[13], self0 = coff[13], ifirst = cst[13];
-    const int IW = ni <= 16 ? 16 : 32;
+    const int IW = ni <= 8 ? 8 : (ni <= 16 ? 16 : 32);
     const int NS = PAIR_THREADS / IW;
     const int il = t % IW, js = t / IW;
     const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
@@ -300,32 +303,33 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     for (int ib = 0; ib < ni; ib += IW) {
         const int i = ib + il;
         const bool valid = i < ni;
-        const int sidx = self0 + (valid ? i : 0);
-        const StagedPos<Real> pi = sp[sidx];
-        const int4 ii = si[sidx];
-        const uint32_t mi = pi.m;
+        const uint4 vi = S.spos[ifirst + (valid ? i : 0)];
+        const int oix = (int)(vi.x - rx), oiy = (int)(vi.y - ry), oiz = (int)(vi.z - rz);
+        StagedPos<Real> pi = frame_coords<Real>(P, oix, oiy, oiz);
+        if (!valid) pi.x = (Real)1e30;            // an idle lane never finds a partner
+        const uint32_t mi = vi.w;
         const int tai = meta_ta(mi), tbi = meta_tb(mi), ki = meta_k(mi);
         const uint32_t lipi = mi >> 12;
         const uint32_t emask = P.excl[ki];
         Real ax = 0, ay = 0, az = 0;
-        int nq = 0;
 
         auto flush = [&](int count) {
             for (int e = 0; e < count; ++e) {
                 const int j = q[e * PAIR_THREADS + t];
-                const StagedPos<Real> pj = sp[j];
+                const int4 ij = si[j];
                 Real dx, dy, dz;
                 if (F32) {
-                    const int4 ij = si[j];
-                    const float fx = (float)wrap_diff(ii.x, ij.x), fy = (float)wrap_diff(ii.y, ij.y), fz = (float)wrap_diff(ii.z, ij.z);
+                    const float fx = (float)wrap_diff(oix, ij.x), fy = (float)wrap_diff(oiy, ij.y),
+                                fz = (float)wrap_diff(oiz, ij.z);
                     dx = (Real)fmaf(fx, P.qsh[0], fx * P.qsl[0]);
                     dy = (Real)fmaf(fy, P.qsh[1], fy * P.qsl[1]);
                     dz = (Real)fmaf(fz, P.qsh[2], fz * P.qsl[2]);
                 } else {
+                    const StagedPos<Real> pj = sf[j];
                     dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
                 }
                 const Real r2 = dx * dx + dy * dy + dz * dz;
-                const uint32_t mj = pj.m;
+                const uint32_t mj = (uint32_t)ij.w;
                 const int ta = tai * 16 + meta_ta(mj);
                 Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
                 if (LAM) {
@@ -369,30 +373,65 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
             }
         };
 
-        for (int j = js; j < M; j += NS) {
-            const StagedPos<Real> pj = sp[j];
-            const Real dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const Real r2 = dx * dx + dy * dy + dz * dz;
-            bool hit = valid && (r2 < rc2) && (j != sidx);
-            if (hit) {
-                const uint32_t mj = pj.m;
-                if (lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u)) hit = false;
-                if (F32 && hit && r2 >= rc2lo) {
-                    // within float rounding of the cutoff: decide from the exact offsets
-                    const int4 ij = si[j];
-                    const double ex = (double)wrap_diff(ii.x, ij.x) * P.qs[0];
-                    const double ey = (double)wrap_diff(ii.y, ij.y) * P.qs[1];
-                    const double ez = (double)wrap_diff(ii.z, ij.z) * P.qs[2];
-                    hit = ex * ex + ey * ey + ez * ez < P.rc2;
+        for (int base = 0; base < M; base += STAGE_CAP) {
+            const int mc = min(STAGE_CAP, M - base);
+            __syncthreads();                      // the previous chunk (or the reduction) is done
+            // stage slots warp by warp, one bead per lane
+            for (int s = warp; s < 27; s += PAIR_THREADS / 32) {
+                const int lo = max(coff[s], base), hi = min(coff[s + 1], base + mc);
+                for (int k = lo + lane; k < hi; k += 32) {
+                    const uint4 v = S.spos[cst[s] + (k - coff[s])];
+                    const int ox = (int)(v.x - rx), oy = (int)(v.y - ry), oz = (int)(v.z - rz);
+                    sf[k - base] = frame_coords<Real>(P, ox, oy, oz);
+                    si[k - base] = make_int4(ox, oy, oz, (int)v.w);
                 }
             }
-            if (hit) {
-                q[nq * PAIR_THREADS + t] = (uint16_t)j;
-                if (++nq == QCAP) { flush(nq); nq = 0; }
+            __syncthreads();
+            int nq = 0;
+            auto consider = [&](int j, Real r2) {
+                const int4 ij = si[j];
+                const uint32_t mj = (uint32_t)ij.w;
+                bool hit = !(lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u));
+                if (F32 && hit && r2 >= rc2lo) {
+                    // within float rounding of the cutoff: decide from the exact offsets
+                    const double ex = (double)wrap_diff(oix, ij.x) * P.qs[0];
+                    const double ey = (double)wrap_diff(oiy, ij.y) * P.qs[1];
+                    const double ez = (double)wrap_diff(oiz, ij.z) * P.qs[2];
+                    hit = ex * ex + ey * ey + ez * ez < P.rc2;
+                }
+                if (hit) {
+                    q[nq * PAIR_THREADS + t] = (uint16_t)j;
+                    if (++nq == QCAP) { flush(nq); nq = 0; }
+                }
+            };
+            int j = js;
+            for (; j + (UNROLL - 1) * NS < mc; j += UNROLL * NS) {
+                Real r2u[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const StagedPos<Real> pj = sf[j + u * NS];
+                    const Real dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                    r2u[u] = dx * dx + dy * dy + dz * dz;
+                }
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) any |= (r2u[u] < rc2) & (r2u[u] > (Real)0);
+                if (any) {
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u)
+                        if ((r2u[u] < rc2) & (r2u[u] > (Real)0)) consider(j + u * NS, r2u[u]);
+                }
             }
+            for (; j < mc; j += NS) {
+                const StagedPos<Real> pj = sf[j];
+                const Real dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                const Real r2 = dx * dx + dy * dy + dz * dz;
+                if ((r2 < rc2) & (r2 > (Real)0)) consider(j, r2);
+            }
+            flush(nq);
         }
-        flush(nq);
 
+        __syncthreads();                          // every queue has drained: red may alias q
         red[0 * PAIR_THREADS + t] = ax;
         red[1 * PAIR_THREADS + t] = ay;
         red[2 * PAIR_THREADS + t] = az;
@@ -415,7 +454,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
                 S.fz[id] = __double2ll_rn((double)fz * FIX);
             }
         }
-        __syncthreads();
     }
     if (ENERGY) {
         ered[0][t] = elj; ered[1][t] = erf; ered[2][t] = epairs;
@@ -432,7 +470,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
 
 template <typename Real>
 static size_t pair_smem() {
-    return sizeof(StagedPos<Real>) * STAGE_CAP + sizeof(int4) * STAGE_CAP + sizeof(Real) * (3 * 256 + 3 * PAIR_THREADS) +
+    static_assert(3 * PAIR_THREADS * sizeof(double) <= sizeof(uint16_t) * QCAP * PAIR_THREADS, "red fits in q");
+    return sizeof(StagedPos<Real>) * STAGE_CAP + sizeof(int4) * STAGE_CAP + sizeof(Real) * 3 * 256 +
            sizeof(uint16_t) * QCAP * PAIR_THREADS;
 }
 

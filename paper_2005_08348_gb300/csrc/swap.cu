@@ -17,25 +17,26 @@
 
 namespace mdas {
 
-// pair energy (LJ with potential shift + reaction field), FP64
-__device__ __forceinline__ double pair_u(const Params &P, int ti, int tj, double r2) {
-    const int x = ti * 16 + tj;
-    const double ri = 1.0 / sqrt(r2);
-    const double r6 = ri * ri * ri * ri * ri * ri;
-    return P.c12[x] * r6 * r6 - P.c6[x] * r6 - P.ush[x] + P.qq[x] * (ri + P.krf * r2 - P.crf);
+// FP64 change of one pair's energy (LJ with potential shift + reaction field)
+// when its type pair goes from (oi, oj) to (ni, nj), at squared distance r2;
+// 1/r from a float seed refined by two Newton steps (no FP64 divide or sqrt).
+__device__ __forceinline__ double pair_du(const Params &P, int oi, int oj, int ni, int nj, double r2) {
+    const int xo = oi * 16 + oj, xn = ni * 16 + nj;
+    double ri = (double)rsqrtf((float)r2);
+    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+    const double r2i = ri * ri;
+    const double r6 = r2i * r2i * r2i;
+    return (P.c12[xn] - P.c12[xo]) * r6 * r6 - (P.c6[xn] - P.c6[xo]) * r6 - (P.ush[xn] - P.ush[xo]) +
+           (P.qq[xn] - P.qq[xo]) * (ri + P.krf * r2 - P.crf);
 }
 
-__device__ __forceinline__ double r2_of(const Params &P, uint4 a, uint4 b) {
-    const double dx = (double)(int)(a.x - b.x) * P.qs[0];
-    const double dy = (double)(int)(a.y - b.y) * P.qs[1];
-    const double dz = (double)(int)(a.z - b.z) * P.qs[2];
-    return dx * dx + dy * dy + dz * dz;
-}
-
-// Sum over the neighbours j (27 cells) of changed bead i of
+// Sum over the neighbours j in one of the 27 cells around changed bead i of
 // u(new_i, new_j) - u(old_i, old_j); pairs of two changed beads are counted
-// by the lower id only.  Types come from a functor of (meta, id) and a
-// predicate telling whether a neighbour is changed.
+// by the lower id only.  Candidates are culled in FP32 from exact integer
+// separations (those within float rounding of rc are decided in FP64); the
+// energies are FP64.  Types come from a functor of (meta, id) and a predicate
+// telling whether a neighbour is changed.
 template <class NewT, class Changed>
 __device__ double bead_delta(const SysDev &S, const Params &P, int i, uint4 pi, int old_i, int new_i, int slot,
                              NewT newt, Changed changed) {
@@ -49,18 +50,24 @@ __device__ double bead_delta(const SysDev &S, const Params &P, int i, uint4 pi, 
     const int li = meta_lip(pi.w), ki = meta_k(pi.w);
     const uint32_t em = P.excl[ki];
     double acc = 0.0;
-    for (int p = S.cell_start[cj]; p < S.cell_start[cj + 1]; ++p) {
+    const int e = S.cell_start[cj + 1];
+    for (int p = S.cell_start[cj]; p < e; ++p) {
+        const uint4 pj = S.spos[p];
+        const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
+        const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
+        const float r2f = fx * fx + fy * fy + fz * fz;
+        if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
         const int j = S.sorted_id[p];
         if (j == i) continue;
-        const uint4 pj = S.spos[p];
-        const bool cj_ = changed(pj.w, j);
-        if (cj_ && j < i) continue;
+        const bool chj = changed(pj.w, j);
+        if (chj && j < i) continue;
         if (li >= 0 && meta_lip(pj.w) == li && ((em >> meta_k(pj.w)) & 1u)) continue;
-        const double r2 = r2_of(P, pi, pj);
+        const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
+        const double r2 = ex * ex + ey * ey + ez * ez;
         if (r2 >= P.rc2) continue;
         const int old_j = meta_ta(pj.w);
-        const int new_j = cj_ ? newt(pj.w, j) : old_j;
-        acc += pair_u(P, new_i, new_j, r2) - pair_u(P, old_i, old_j, r2);
+        const int new_j = chj ? newt(pj.w, j) : old_j;
+        acc += pair_du(P, old_i, old_j, new_i, new_j, r2);
     }
     return acc;
 }
@@ -141,27 +148,32 @@ __global__ void k_swap_conflicts(const SysDev *__restrict__ sys, int n) {
 void launch_swap_propose(const LaunchCtx &L, int n) {
     dim3 g1((n + 127) / 128, L.n_sys);
     k_swap_propose<<<g1, 128, 0, L.stream>>>(L.sys, n);
-    const int W = (n + 31) / 32;
-    dim3 g2((n * W + 127) / 128, L.n_sys);
-    k_swap_conflicts<<<g2, 128, 0, L.stream>>>(L.sys, n);
+    if (n > 1) {   // a single trial has no earlier trial to conflict with
+        const int W = (n + 31) / 32;
+        dim3 g2((n * W + 127) / 128, L.n_sys);
+        k_swap_conflicts<<<g2, 128, 0, L.stream>>>(L.sys, n);
+    }
 }
 
 // ------------------------------------------------------------ speculation
-// grid (n, n_sys), one CTA per trial: dE of exchanging the current types of
-// lipids a and b (FP64, fixed-order reduction).
+// grid (n * 9, n_sys): CTA (t, g) sums the dE of trial t over the 3
+// neighbour cells (dz, dy) = g of every changed bead (FP64, fixed-order
+// reduction); the 9 partial sums are added in order by the resolve kernel.
+constexpr int DE_GROUPS = 9;
+
 __global__ void __launch_bounds__(128) k_swap_dE(const SysDev *__restrict__ sys, int n) {
     const SysDev &S = sys[blockIdx.y];
     const Params &P = *S.p;
-    const int t = blockIdx.x;
+    const int t = blockIdx.x / DE_GROUPS, grp = blockIdx.x % DE_GROUPS;
     __shared__ double sh[128];
     __shared__ int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT];
     __shared__ int nchg, kmask;
     if (S.tstate[t] != 0) return;
-    int4 pr = S.tprop[t];
+    const int4 pr = S.tprop[t];
     const int a = pr.x, b = pr.y;
     const int ta = S.ltype[a], tb = S.ltype[b];
     if (threadIdx.x == 0) {
-        S.tprop[t] = make_int4(a, b, ta, tb);
+        if (grp == 0) S.tprop[t] = make_int4(a, b, ta, tb);
         int m = 0, nc = 0;
         if (a != b && ta != tb) {
             for (int k = 0; k < P.bpl; ++k)
@@ -189,17 +201,17 @@ __global__ void __launch_bounds__(128) k_swap_dE(const SysDev *__restrict__ sys,
         return (int)P.lbt[(l == a ? tb : ta) * 16 + meta_k(mj)];
     };
     double acc = 0.0;
-    for (int it = threadIdx.x; it < nc * 27; it += blockDim.x) {
-        const int ci = it / 27, slot = it % 27;
+    for (int it = threadIdx.x; it < nc * 3; it += blockDim.x) {
+        const int ci = it / 3, slot = grp * 3 + it % 3;
         const int i = chg_id[ci];
         acc += bead_delta(S, P, i, S.pos[i], chg_old[ci], chg_new[ci], slot, newt, changed);
     }
     const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) S.tdE[t] = s;
+    if (threadIdx.x == 0) S.tdE[t * DE_GROUPS + grp] = s;
 }
 
 void launch_swap_dE(const LaunchCtx &L, int n) {
-    dim3 g(n, L.n_sys);
+    dim3 g(n * DE_GROUPS, L.n_sys);
     k_swap_dE<<<g, 128, 0, L.stream>>>(L.sys, n);
 }
 
@@ -229,7 +241,11 @@ __global__ void k_swap_resolve(const SysDev *__restrict__ sys, int n) {
     for (int t = 0; t < n; ++t) {
         if (S.tstate[t] != 0) continue;
         bool blk = false;
-        for (int w = 0; w <= t / 32 && !blk; ++w) blk = (S.conflict[t * W + w] & blocked[w]) != 0;
+        for (int w = 0; w <= t / 32 && !blk; ++w) {
+            uint32_t bits = S.conflict[t * W + w];
+            if (w == t / 32) bits &= (1u << (t % 32)) - 1u;      // only earlier trials
+            blk = (bits & blocked[w]) != 0;
+        }
         if (blk) { blocked[t / 32] |= 1u << (t % 32); ++pending; continue; }
         const int4 pr = S.tprop[t];
         const int a = pr.x, b = pr.y;
@@ -239,7 +255,9 @@ __global__ void k_swap_resolve(const SysDev *__restrict__ sys, int n) {
         r.index = C.trial + (unsigned long long)t;
         r.null_trial = (a == b) || (S.ltype[a] == S.ltype[b]);
         if (!r.null_trial) {
-            r.dE = S.tdE[t];
+            double dE = 0.0;
+            for (int g = 0; g < DE_GROUPS; ++g) dE += S.tdE[t * DE_GROUPS + g];
+            r.dE = dE;
             if (r.dE + P.kT * log(u) <= 0.0) {
                 const int ta = S.ltype[a], tb = S.ltype[b];
                 set_lipid_type(S, P, a, tb);
