@@ -59,6 +59,7 @@ struct mdas_system {
     std::string err;
     bool unstable = false;
     bool cells_valid = false;   // the cell list matches the current positions and types
+    bool counted = false;       // cell_count holds the integrator's counts of the current positions
     bool timing = false;
     double pair_ms = 0.0;
     long long pair_launches = 0;
@@ -161,20 +162,43 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
 }
 
 // ------------------------------------------------------------ step bodies
-void md_step_launches(const Batch &b, bool lambda) {
-    LaunchCtx L = b.ctx();
-    launch_thermostat(L);
-    launch_cells(L);
-    launch_pair(L, lambda, false, b.precision == 1);
-    launch_integrate(L);
+// Cell counts: the integrator counts every bead into its new cell, so a build
+// right after it skips the counting pass.  All systems of a batch must agree.
+mdas_status sync_counted(mdas_system *s, Batch &b, bool *counted) {
+    bool all = true, any = false;
+    for (auto *x : b.sys) { all = all && x->counted; any = any || x->counted; }
+    if (any && !all) {
+        for (auto *x : b.sys)
+            if (x->counted) {
+                CK(cudaMemsetAsync(x->hs.cell_count, 0, 4ull * x->hp.n_cells, b.stream));
+                x->counted = false;
+            }
+        all = false;
+    }
+    *counted = all;
+    return MDAS_OK;
 }
 
-void trial_launches(const Batch &b) {
+void set_counted(Batch &b, bool v) {
+    for (auto *x : b.sys) x->counted = v;
+}
+
+mdas_status build_cells(mdas_system *s, Batch &b) {
+    bool counted;
+    mdas_status st = sync_counted(s, b, &counted);
+    if (st != MDAS_OK) return st;
+    launch_cells(b.ctx(), counted);
+    set_counted(b, false);
+    for (auto *x : b.sys) x->cells_valid = true;
+    return MDAS_OK;
+}
+
+void md_step_launches(const Batch &b, bool lambda, bool counted) {
     LaunchCtx L = b.ctx();
-    launch_cells(L);
-    launch_swap_propose(L, 1);
-    launch_swap_dE(L, 1);
-    launch_swap_resolve(L, 1);
+    launch_thermostat(L);
+    launch_cells(L, counted);
+    launch_pair(L, lambda, false, b.precision == 1);
+    launch_integrate(L);
 }
 
 __global__ void k_batch_status(const SysDev *__restrict__ sys, int n, int *out) {
@@ -216,14 +240,19 @@ mdas_status check_err(mdas_system *s, Batch &b) {
 // Capture (or reuse) a graph of `units` repetitions of [steps_per_unit MD
 // steps + optional exchange trial]; timing adds event pairs around every
 // pair-kernel launch.
-// With trials, the cell list a trial builds serves the next MD step as well
-// (positions do not change in between); reuse_first also skips the first
-// step's build when the list is already valid when the graph starts.
+// Capture (or reuse) a graph of `units` repetitions of [steps_per_unit MD
+// steps + optional exchange trial]; its first node draws the thermostat
+// variates of all its steps.  With trials, the cell list a trial builds serves
+// the next MD step as well (positions do not change in between);
+// reuse_first also skips the first step's build because the list is valid
+// when the graph starts; counted_first tells whether the integrator's cell
+// counts are pending at the start.  timing adds event pairs around every
+// pair-kernel launch.
 mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, bool trial, bool lambda, bool timing,
-                      bool reuse_first, GraphEntry **out) {
-    char key[96];
-    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d_r%d", units, steps_per_unit, (int)trial, (int)lambda, (int)timing,
-             (int)reuse_first);
+                      bool reuse_first, bool counted_first, GraphEntry **out) {
+    char key[128];
+    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d_r%d_c%d", units, steps_per_unit, (int)trial, (int)lambda,
+             (int)timing, (int)reuse_first, (int)counted_first);
     auto it = b.graphs.find(key);
     if (it != b.graphs.end()) { *out = &it->second; return MDAS_OK; }
     GraphEntry ge;
@@ -238,12 +267,14 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
     }
     CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
     LaunchCtx L = b.ctx();
+    launch_thermo_draws(L, units * steps_per_unit);
     int ev = 0;
     for (int u = 0; u < units; ++u) {
         for (int k = 0; k < steps_per_unit; ++k) {
             launch_thermostat(L);
+            const bool first = u == 0 && k == 0;
             const bool have_cells = trial && k == 0 && (u > 0 || reuse_first);
-            if (!have_cells) launch_cells(L);
+            if (!have_cells) launch_cells(L, first ? counted_first : true);
             if (timing) {
                 // external event nodes: recorded (and timed) at every replay
                 cudaEventRecordWithFlags(ge.pair_events[ev].first, b.stream, cudaEventRecordExternal);
@@ -255,7 +286,10 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
             }
             launch_integrate(L);
         }
-        if (trial) trial_launches(b);
+        if (trial) {
+            launch_cells(L, true);
+            launch_trial_one(L);
+        }
     }
     cudaError_t e = cudaStreamEndCapture(b.stream, &g);
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
@@ -281,7 +315,7 @@ mdas_status replay(mdas_system *s, Batch &b, GraphEntry *ge) {
 }
 
 // n_steps MD steps on a batch; after every swap_every-th step one trial.
-mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every) {
+mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, bool lambda = false) {
     if (n_steps <= 0) return MDAS_OK;
     const bool trial = swap_every > 0;
     const long long unit = trial ? swap_every : 1;
@@ -290,28 +324,44 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every) 
     bool timing = false;
     for (auto *x : b.sys) timing = timing || x->timing;
     const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
+    bool counted;
+    mdas_status st = sync_counted(s, b, &counted);
+    if (st != MDAS_OK) return st;
     if (n_units > 0) {
+        bool reuse = false;
         if (trial) {
             bool valid = true;
             for (auto *x : b.sys) valid = valid && x->cells_valid;
-            if (!valid) launch_cells(b.ctx());
+            if (!valid) {
+                launch_cells(b.ctx(), counted);
+            } else if (counted) {
+                for (auto *x : b.sys) CK(cudaMemsetAsync(x->hs.cell_count, 0, 4ull * x->hp.n_cells, b.stream));
+            }
+            reuse = true;
+            counted = false;
         }
         GraphEntry *ge;
-        mdas_status st = get_graph(s, b, (int)E, (int)unit, trial, false, timing, trial, &ge);
-        if (st != MDAS_OK) return st;
         for (long long r = 0; r < n_units / E; ++r) {
+            st = get_graph(s, b, (int)E, (int)unit, trial, lambda, timing, reuse, counted, &ge);
+            if (st != MDAS_OK) return st;
             st = replay(s, b, ge);
             if (st != MDAS_OK) return st;
+            counted = !trial;
         }
         const long long left = n_units % E;
         if (left > 0) {
-            st = get_graph(s, b, (int)left, (int)unit, trial, false, timing, trial, &ge);
+            st = get_graph(s, b, (int)left, (int)unit, trial, lambda, timing, reuse, counted, &ge);
             if (st != MDAS_OK) return st;
             st = replay(s, b, ge);
             if (st != MDAS_OK) return st;
+            counted = !trial;
         }
     }
-    for (long long k = 0; k < rem; ++k) md_step_launches(b, false);
+    for (long long k = 0; k < rem; ++k) {
+        md_step_launches(b, lambda, counted);
+        counted = true;
+    }
+    set_counted(b, counted);
     const bool valid_after = trial && rem == 0 && n_units > 0;
     for (auto *x : b.sys) x->cells_valid = valid_after;
     CK(cudaGetLastError());
@@ -321,7 +371,8 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every) 
 // n exchange trials per system of a batch with sequential semantics.
 mdas_status run_trials(mdas_system *s, Batch &b, int n, int *rounds_out) {
     LaunchCtx L = b.ctx();
-    launch_cells(L);
+    mdas_status st0 = build_cells(s, b);
+    if (st0 != MDAS_OK) return st0;
     int rounds = 0;
     for (int done = 0; done < n;) {
         const int m = std::min(n - done, MAX_ROUND_TRIALS);
@@ -435,6 +486,11 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     P.crf = 1.0 / d->rc + P.krf * d->rc * d->rc;
     // float cull bounds: every pair with r^2 < rc^2 passes rc2f; pairs in
     // [rc2f_lo, rc2f) are re-decided exactly from integer offsets
+    for (int k = 0; k < 3; ++k) {
+        P.cwu[k] = (unsigned long long)(4294967296.0 / nc[k]);
+        P.qdtf[k] = (float)P.qdt[k];
+    }
+    P.therm_c = d->tau_t > 0 ? std::exp(-d->dt / d->tau_t) : 1.0;
     P.rc2f = std::nextafter((float)(P.rc2 * (1.0 + 1e-5)), 1e30f);
     P.rc2f_lo = (float)(P.rc2 * (1.0 - 1e-5));
     P.krf2f = (float)(2.0 * P.krf);
@@ -502,7 +558,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.cell_count, 4ull * P.n_cells}, {(void **)&H.cell_start, 4ull * (P.n_cells + 1)},
         {(void **)&H.tmp_ids, 4ull * n}, {(void **)&H.sorted_id, 4ull * n}, {(void **)&H.sidx, 4ull * n},
         {(void **)&H.spos, 16ull * n},
-        {(void **)&H.ke_part, 16ull * nbb}, {(void **)&H.bpart, 16ull * nbb}, {(void **)&H.epart, 32ull * P.n_cells},
+        {(void **)&H.ke_part, 16ull * nbb}, {(void **)&H.bpart, 24ull * nbb}, {(void **)&H.epart, 32ull * P.n_cells},
         {(void **)&H.pos_snap, 16ull * n}, {(void **)&H.vel_snap, vsz * n},
         {(void **)&H.ltype_snap, 4ull * std::max(nl, 1)},
         {(void **)&H.tprop, 16ull * MAX_ROUND_TRIALS}, {(void **)&H.tu, 8ull * MAX_ROUND_TRIALS},
@@ -510,6 +566,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.conflict, 4ull * MAX_ROUND_TRIALS * (MAX_ROUND_TRIALS / 32)},
         {(void **)&H.lbox, 32ull * MAX_ROUND_TRIALS}, {(void **)&H.lhalf, 32ull * MAX_ROUND_TRIALS},
         {(void **)&H.log, sizeof(TrialRec) * (size_t)LOG_CAP}, {(void **)&H.result, 8ull * 64},
+        {(void **)&H.tdraw, sizeof(double2) * 2ull * MAX_DRAW_STEPS},
         {(void **)&s->fout, 24ull * n},
     };
     size_t total = 0;
@@ -598,8 +655,8 @@ mdas_status mdas_forces(mdas_system *s, double *f_out, double *u_out) {
     Batch &b = *s->solo;
     LaunchCtx L = b.ctx();
     if (f_out) {
-        launch_cells(L);
-        s->cells_valid = true;
+        mdas_status st = build_cells(s, b);
+        if (st != MDAS_OK) return st;
         launch_pair(L, false, false, s->precision == 1);
         launch_total_force(L, s->fout, 0);
         CK(cudaMemcpyAsync(f_out, s->fout, 24ull * s->n, cudaMemcpyDeviceToHost, s->stream));
@@ -619,8 +676,8 @@ mdas_status mdas_energy(mdas_system *s, mdas_energy_terms *out) {
     if (!s || !out) return fail(s, MDAS_ERR_INVALID_ARG, "energy: NULL argument");
     Batch &b = *s->solo;
     LaunchCtx L = b.ctx();
-    launch_cells(L);
-    s->cells_valid = true;
+    mdas_status st0 = build_cells(s, b);
+    if (st0 != MDAS_OK) return st0;
     launch_pair(L, false, true, true);
     launch_energy_reduce(L);
     double r[8];
@@ -714,12 +771,14 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
             launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
             if (md_per_lambda > 0) {
                 GraphEntry *ge;
-                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, &ge);
+                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, s->counted, &ge);
                 if (st != MDAS_OK) return st;
                 st = replay(s, b, ge);
                 if (st != MDAS_OK) return st;
+                s->counted = true;
             }
-            launch_cells(L);
+            mdas_status st = build_cells(s, b);
+            if (st != MDAS_OK) return st;
             launch_mdas_dE(L, dl);
         }
     }
@@ -760,8 +819,8 @@ mdas_status mdas_delta_energy(mdas_system *s, const int32_t *lipids, const int32
     CK(cudaMemcpyAsync(&np_save, &dc->n_pairs, 4, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(&dc->pairs[0], lipids, 4ull * n, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(&dc->pairs[MAX_PAIRS], new_types, 4ull * n, cudaMemcpyHostToDevice, s->stream));
-    launch_cells(L);
-    s->cells_valid = true;
+    mdas_status st0 = build_cells(s, b);
+    if (st0 != MDAS_OK) return st0;
     launch_delta_energy(L, n);
     CK(cudaMemcpyAsync(dE, s->hs.result + 8, 8, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -860,6 +919,8 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     c.step = in->step; c.trial = in->trial; c.move = in->move; c.at_step = in->at_step;
     c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0;
     CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
+    if (s->counted) CK(cudaMemsetAsync(s->hs.cell_count, 0, 4ull * s->hp.n_cells, s->stream));
+    s->counted = false;
     launch_kinetic(s->solo->ctx());
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
@@ -870,7 +931,8 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
 
 mdas_status mdas_cell_list(mdas_system *s, int32_t *sorted_ids, int32_t *cell_start, int32_t *ncell) {
     if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "cell_list: NULL system");
-    launch_cells(s->solo->ctx());
+    mdas_status st0 = build_cells(s, *s->solo);
+    if (st0 != MDAS_OK) return st0;
     if (sorted_ids) CK(cudaMemcpyAsync(sorted_ids, s->hs.sorted_id, 4ull * s->n, cudaMemcpyDeviceToHost, s->stream));
     if (cell_start) CK(cudaMemcpyAsync(cell_start, s->hs.cell_start, 4ull * (s->hp.n_cells + 1), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));

@@ -119,8 +119,9 @@ __global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__rest
     }
 }
 
-void launch_cells(const LaunchCtx &L) {
-    k_cell_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+// counted: the integrator has already counted the current positions into cells
+void launch_cells(const LaunchCtx &L, bool counted) {
+    if (!counted) k_cell_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
     k_cell_scan<<<L.syss->n, 1024, 0, L.stream>>>(L.sys, L.syss->d);
     k_cell_scatter<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
     k_cell_finish<<<L.sortcells->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.sortcells->d);
@@ -150,16 +151,47 @@ __device__ double gamma_variate(const Params &P, uint32_t i0, uint32_t i1, uint3
     return a;
 }
 
-// Bussi et al. (2007) rescaling factor: new kinetic energy
-// (sqrt(c K) + R1 sqrt((1-c) Kt/Nf))^2 + (1-c) (Kt/Nf) S with S ~ chi2(Nf-1).
-__device__ double bussi_alpha(const Params &P, double K, int nf, double kt, uint32_t g, uint32_t ctr, uint32_t tag) {
-    if (P.tau_t <= 0.0 || K <= 0.0 || nf < 3) return 1.0;
-    const double c = exp(-P.dt / P.tau_t);
+// The two random variates of one Bussi et al. (2007) rescaling: R1 ~ N(0, 1)
+// from Philox call 0 and S ~ chi2(nf - 1) from calls >= 1 of counter
+// (g, ctr, tag).  They depend on the counters only, so a whole segment's
+// worth is drawn in parallel ahead of the steps.
+__device__ double2 bussi_draws(const Params &P, int nf, uint32_t g, uint32_t ctr, uint32_t tag) {
     const double r1 = normal_of(draw4(P, g, ctr, tag, 0));
-    const double S = 2.0 * gamma_variate(P, g, ctr, tag, 0.5 * (nf - 1), 1);
-    const double a = sqrt(c * K) + r1 * sqrt((1.0 - c) * kt / nf);
-    const double knew = a * a + (1.0 - c) * (kt / nf) * S;
+    const double S = nf >= 3 ? 2.0 * gamma_variate(P, g, ctr, tag, 0.5 * (nf - 1), 1) : 0.0;
+    return make_double2(r1, S);
+}
+
+// Rescaling factor: new kinetic energy (sqrt(c K) + R1 sqrt((1-c) Kt/Nf))^2 +
+// (1-c) (Kt/Nf) S, c = exp(-dt/tau), alpha = sqrt(K_new / K).
+__device__ double bussi_alpha(const Params &P, double K, int nf, double kt, double2 d) {
+    if (P.tau_t <= 0.0 || K <= 0.0 || nf < 3) return 1.0;
+    const double c = P.therm_c;
+    const double a = sqrt(c * K) + d.x * sqrt((1.0 - c) * kt / nf);
+    const double knew = a * a + (1.0 - c) * (kt / nf) * d.y;
     return sqrt(knew / K);
+}
+
+// grid (ceil(2 n / 64), n_sys): variates for the next n MD steps of the
+// current counter domain (plain MD or alchemical trajectory)
+__global__ void k_thermo_draws(const SysDev *__restrict__ sys, int n) {
+    const SysDev &S = sys[blockIdx.y];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    const int in_at = C.in_at;
+    const unsigned long long base = in_at ? C.at_step : C.step;
+    const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < 2 * n && P.tau_t > 0.0) {
+        const int g = k & 1;
+        S.tdraw[k] = bussi_draws(P, P.nf[g], (uint32_t)g, (uint32_t)(base + (k >> 1)), tag);
+    }
+    if (k == 0) { C.draw_base = base; C.draw_n = P.tau_t > 0.0 ? n : 0; C.draw_tag = (int)tag; }
+}
+
+void launch_thermo_draws(const LaunchCtx &L, int n) {
+    n = n < MAX_DRAW_STEPS ? n : MAX_DRAW_STEPS;
+    dim3 g((2 * n + 63) / 64, L.n_sys);
+    k_thermo_draws<<<g, 64, 0, L.stream>>>(L.sys, n);
 }
 
 __global__ void __launch_bounds__(256) k_thermostat(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
@@ -180,10 +212,17 @@ __global__ void __launch_bounds__(256) k_thermostat(const SysDev *__restrict__ s
     }
     const int in_at = C.in_at;
     const unsigned long long ctr = in_at ? C.at_step : C.step;
+    const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
     if ((t & 31) == 0 && t < 64) {          // one warp per coupling group
         const int g = t >> 5;
-        C.alpha[g] = bussi_alpha(P, ks[g][0], P.nf[g], P.ktarget[g], (uint32_t)g, (uint32_t)ctr,
-                                 in_at ? TAG_AT_THERMO : TAG_THERMO);
+        double2 d = make_double2(0.0, 0.0);
+        if (P.tau_t <= 0.0)
+            ;   // no thermostat: alpha = 1
+        else if ((int)tag == C.draw_tag && ctr >= C.draw_base && ctr < C.draw_base + (unsigned long long)C.draw_n)
+            d = S.tdraw[2 * (ctr - C.draw_base) + g];
+        else
+            d = bussi_draws(P, P.nf[g], (uint32_t)g, (uint32_t)ctr, tag);
+        C.alpha[g] = bussi_alpha(P, ks[g][0], P.nf[g], P.ktarget[g], d);
     }
     __syncthreads();
     if (t == 0) {
@@ -286,14 +325,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     __syncthreads();
     const int M = coff[27];
     const int ni = ccnt[13], ifirst = cst[13];
-    // frame origin: the cell centre in fixed-point units
-    const uint32_t rx = (uint32_t)((((unsigned long long)(2 * cx + 1)) << 32) / (2ull * nx));
-    const uint32_t ry = (uint32_t)((((unsigned long long)(2 * cy + 1)) << 32) / (2ull * ny));
-    const uint32_t rz = (uint32_t)((((unsigned long long)(2 * cz + 1)) << 32) / (2ull * nz));
+    // frame origin: the cell centre in fixed-point units (to within n units)
+    const uint32_t rx = (uint32_t)(((unsigned long long)(2 * cx + 1) * P.cwu[0]) >> 1);
+    const uint32_t ry = (uint32_t)(((unsigned long long)(2 * cy + 1) * P.cwu[1]) >> 1);
+    const uint32_t rz = (uint32_t)(((unsigned long long)(2 * cz + 1) * P.cwu[2]) >> 1);
 
-    const int IW = ni <= 8 ? 8 : (ni <= 16 ? 16 : 32);
+    // threads = IW i-beads x NS j-streams (IW = ni up to the block size)
+    const int IW = ni < PAIR_THREADS ? (ni > 0 ? ni : 1) : PAIR_THREADS;
     const int NS = PAIR_THREADS / IW;
-    const int il = t % IW, js = t / IW;
+    const int il = t % IW, js = t / IW;          // js == NS: idle thread
     const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
     const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
     const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
@@ -302,7 +342,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
 
     for (int ib = 0; ib < ni; ib += IW) {
         const int i = ib + il;
-        const bool valid = i < ni;
+        const bool valid = i < ni && js < NS;
         const uint4 vi = S.spos[ifirst + (valid ? i : 0)];
         const int oix = (int)(vi.x - rx), oiy = (int)(vi.y - ry), oiz = (int)(vi.z - rz);
         StagedPos<Real> pi = frame_coords<Real>(P, oix, oiy, oiz);
@@ -330,6 +370,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
                 }
                 const Real r2 = dx * dx + dy * dy + dz * dz;
                 const uint32_t mj = (uint32_t)ij.w;
+                bool keep = !(lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u));
+                if (F32 && r2 >= rc2lo) {
+                    // within float rounding of the cutoff: decide from the exact offsets
+                    const double ex = (double)wrap_diff(oix, ij.x) * P.qs[0];
+                    const double ey = (double)wrap_diff(oiy, ij.y) * P.qs[1];
+                    const double ez = (double)wrap_diff(oiz, ij.z) * P.qs[2];
+                    keep = keep && (ex * ex + ey * ey + ez * ez < P.rc2);
+                }
+                if (!keep) continue;
                 const int ta = tai * 16 + meta_ta(mj);
                 Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
                 if (LAM) {
@@ -388,45 +437,25 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
             }
             __syncthreads();
             int nq = 0;
-            auto consider = [&](int j, Real r2) {
-                const int4 ij = si[j];
-                const uint32_t mj = (uint32_t)ij.w;
-                bool hit = !(lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u));
-                if (F32 && hit && r2 >= rc2lo) {
-                    // within float rounding of the cutoff: decide from the exact offsets
-                    const double ex = (double)wrap_diff(oix, ij.x) * P.qs[0];
-                    const double ey = (double)wrap_diff(oiy, ij.y) * P.qs[1];
-                    const double ez = (double)wrap_diff(oiz, ij.z) * P.qs[2];
-                    hit = ex * ex + ey * ey + ez * ez < P.rc2;
-                }
-                if (hit) {
-                    q[nq * PAIR_THREADS + t] = (uint16_t)j;
-                    if (++nq == QCAP) { flush(nq); nq = 0; }
-                }
-            };
             int j = js;
             for (; j + (UNROLL - 1) * NS < mc; j += UNROLL * NS) {
-                Real r2u[UNROLL];
+                if (nq > QCAP - UNROLL) { flush(nq); nq = 0; }
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
                     const StagedPos<Real> pj = sf[j + u * NS];
                     const Real dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                    r2u[u] = dx * dx + dy * dy + dz * dz;
-                }
-                bool any = false;
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) any |= (r2u[u] < rc2) & (r2u[u] > (Real)0);
-                if (any) {
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u)
-                        if ((r2u[u] < rc2) & (r2u[u] > (Real)0)) consider(j + u * NS, r2u[u]);
+                    const Real r2 = dx * dx + dy * dy + dz * dz;
+                    q[nq * PAIR_THREADS + t] = (uint16_t)(j + u * NS);
+                    nq += (int)((r2 < rc2) & (r2 > (Real)0));
                 }
             }
             for (; j < mc; j += NS) {
+                if (nq == QCAP) { flush(nq); nq = 0; }
                 const StagedPos<Real> pj = sf[j];
                 const Real dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
                 const Real r2 = dx * dx + dy * dy + dz * dz;
-                if ((r2 < rc2) & (r2 > (Real)0)) consider(j, r2);
+                q[nq * PAIR_THREADS + t] = (uint16_t)j;
+                nq += (int)((r2 < rc2) & (r2 > (Real)0));
             }
             flush(nq);
         }
@@ -438,7 +467,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         __syncthreads();
         if (t < IW && ib + t < ni) {
             Real fx = 0, fy = 0, fz = 0;
-            for (int s = 0; s < NS; ++s) {
+            for (int s = 0; s < NS; ++s) {   // fixed order over the streams
                 fx += red[0 * PAIR_THREADS + s * IW + t];
                 fy += red[1 * PAIR_THREADS + s * IW + t];
                 fz += red[2 * PAIR_THREADS + s * IW + t];
@@ -562,8 +591,10 @@ __device__ void bonded_force(const Params &P, const uint4 *__restrict__ pos, int
 }
 
 // ------------------------------------------------------------- integrator
-// v <- alpha_g v + F/m dt ; x <- x + v dt rounded to the fixed-point grid;
-// then the per-block kinetic energy of each group for the next thermostat.
+// v <- alpha_g v + F/m dt ; x <- x + v dt rounded to the fixed-point grid
+// (in the velocity's precision); then the bead is counted into its new cell
+// for the next cell-list build, and the per-block kinetic energy of each
+// group is stored for the next thermostat.
 template <typename Real>
 __global__ void __launch_bounds__(BEAD_BLOCK) k_integrate(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     using V4 = typename Vec4<Real>::T;
@@ -571,7 +602,7 @@ __global__ void __launch_bounds__(BEAD_BLOCK) k_integrate(const SysDev *__restri
     const SysDev &S = sys[bm.x];
     const Params &P = *S.p;
     const int i = bm.y + threadIdx.x;
-    double ke[2] = {0.0, 0.0};
+    Real ke[2] = {(Real)0, (Real)0};
     if (i < P.n) {
         uint4 pi = S.pos[i];
         const uint32_t m = pi.w;
@@ -588,23 +619,34 @@ __global__ void __launch_bounds__(BEAD_BLOCK) k_integrate(const SysDev *__restri
         v.y = a * v.y + f[1] * dtm;
         v.z = a * v.z + f[2] * dtm;
         vel[i] = v;
-        if (!(isfinite((double)v.x) && isfinite((double)v.y) && isfinite((double)v.z))) atomicOr(&S.c->err, ERR_NONFINITE);
-        pi.x += (uint32_t)(long long)rint((double)v.x * P.qdt[0]);
-        pi.y += (uint32_t)(long long)rint((double)v.y * P.qdt[1]);
-        pi.z += (uint32_t)(long long)rint((double)v.z * P.qdt[2]);
+        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&S.c->err, ERR_NONFINITE);
+        if (sizeof(Real) == 4) {
+            pi.x += (uint32_t)__float2int_rn((float)v.x * P.qdtf[0]);
+            pi.y += (uint32_t)__float2int_rn((float)v.y * P.qdtf[1]);
+            pi.z += (uint32_t)__float2int_rn((float)v.z * P.qdtf[2]);
+        } else {
+            pi.x += (uint32_t)(long long)rint((double)v.x * P.qdt[0]);
+            pi.y += (uint32_t)(long long)rint((double)v.y * P.qdt[1]);
+            pi.z += (uint32_t)(long long)rint((double)v.z * P.qdt[2]);
+        }
         S.pos[i] = pi;
-        const double vx = (double)v.x, vy = (double)v.y, vz = (double)v.z;
-        ke[g] = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz);
+        const int cx = (int)(((unsigned long long)pi.x * (unsigned)P.nc[0]) >> 32);
+        const int cy = (int)(((unsigned long long)pi.y * (unsigned)P.nc[1]) >> 32);
+        const int cz = (int)(((unsigned long long)pi.z * (unsigned)P.nc[2]) >> 32);
+        const int c = (cz * P.nc[1] + cy) * P.nc[0] + cx;
+        S.cell_of[i] = c;
+        S.cell_slot[i] = atomicAdd(&S.cell_count[c], 1);
+        ke[g] = (Real)0.5 * (Real)P.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
     }
-    // fixed-order block reduction of the two group sums
+    // fixed-order reduction: warp trees in the velocity's precision, warps in FP64
     __shared__ double part[2][BEAD_BLOCK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
-        double v = ke[g];
+        Real v = ke[g];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[g][wid] = v;
+        if (lane == 0) part[g][wid] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < 2) {
@@ -614,6 +656,8 @@ __global__ void __launch_bounds__(BEAD_BLOCK) k_integrate(const SysDev *__restri
     }
 }
 
+// Kinetic energy partials for the thermostat from the current velocities,
+// reduced exactly as the integrator reduces them.
 template <typename Real>
 __global__ void __launch_bounds__(BEAD_BLOCK) k_kinetic(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     using V4 = typename Vec4<Real>::T;
@@ -621,20 +665,19 @@ __global__ void __launch_bounds__(BEAD_BLOCK) k_kinetic(const SysDev *__restrict
     const SysDev &S = sys[bm.x];
     const Params &P = *S.p;
     const int i = bm.y + threadIdx.x;
-    double ke[2] = {0.0, 0.0};
+    Real ke[2] = {(Real)0, (Real)0};
     if (i < P.n) {
         const V4 v = reinterpret_cast<const V4 *>(S.vel)[i];
-        const double vx = (double)v.x, vy = (double)v.y, vz = (double)v.z;
-        ke[i < P.n_lipid_beads ? 0 : 1] = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz);
+        ke[i < P.n_lipid_beads ? 0 : 1] = (Real)0.5 * (Real)P.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
     }
     __shared__ double part[2][BEAD_BLOCK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
-        double v = ke[g];
+        Real v = ke[g];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[g][wid] = v;
+        if (lane == 0) part[g][wid] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < 2) {
@@ -685,8 +728,17 @@ __global__ void __launch_bounds__(BEAD_BLOCK) k_bonded_energy(const SysDev *__re
     const SysDev &S = sys[bm.x];
     const Params &P = *S.p;
     const int i = bm.y + threadIdx.x;
-    double eb = 0.0, ea = 0.0;
+    double eb = 0.0, ea = 0.0, ek = 0.0;
     if (i < P.n) {
+        double vx, vy, vz;
+        if (P.precision == 1) {
+            const Dbl4 v = reinterpret_cast<const Dbl4 *>(S.vel)[i];
+            vx = v.x; vy = v.y; vz = v.z;
+        } else {
+            const float4 v = reinterpret_cast<const float4 *>(S.vel)[i];
+            vx = v.x; vy = v.y; vz = v.z;
+        }
+        ek = 0.5 * P.mass * (vx * vx + vy * vy + vz * vz);
         const uint4 pi = S.pos[i];
         const int l = meta_lip(pi.w), k = meta_k(pi.w);
         if (l >= 0) {
@@ -709,38 +761,43 @@ __global__ void __launch_bounds__(BEAD_BLOCK) k_bonded_energy(const SysDev *__re
             }
         }
     }
-    __shared__ double part[2][BEAD_BLOCK];
+    __shared__ double part[3][BEAD_BLOCK];
     part[0][threadIdx.x] = eb;
     part[1][threadIdx.x] = ea;
+    part[2][threadIdx.x] = ek;
     __syncthreads();
-    if (threadIdx.x < 2) {
-        double s = 0.0;
-        for (int w = 0; w < BEAD_BLOCK; ++w) s += part[threadIdx.x][w];
-        S.bpart[2 * (bm.y / BEAD_BLOCK) + threadIdx.x] = s;
+    for (int w = BEAD_BLOCK / 2; w > 0; w >>= 1) {   // fixed-order tree
+        if (threadIdx.x < w)
+            for (int q = 0; q < 3; ++q) part[q][threadIdx.x] += part[q][threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x < 3) S.bpart[3 * (bm.y / BEAD_BLOCK) + threadIdx.x] = part[threadIdx.x][0];
 }
 
-// fixed-order sums: result[0..5] = lj, rf, bond, angle, kinetic, pairs
-__global__ void k_energy_reduce(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+// fixed-order tree sums: result[0..5] = lj, rf, bond, angle, kinetic, pairs
+__global__ void __launch_bounds__(256) k_energy_reduce(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     const SysDev &S = sys[bmap[blockIdx.x].x];
     const Params &P = *S.p;
     const int t = threadIdx.x;
-    double v = 0.0;
-    if (t < 3) {
-        for (int c = 0; c < P.n_cells; ++c) v += S.epart[4 * c + t];
-        S.result[t == 2 ? 5 : t] = v;
-    } else if (t < 5) {
-        for (int b = 0; b < S.n_bead_blocks; ++b) v += S.bpart[2 * b + (t - 3)];
-        S.result[t - 1] = v;
-    } else if (t == 5) {
-        for (int b = 0; b < S.n_bead_blocks; ++b) v += S.ke_part[2 * b] + S.ke_part[2 * b + 1];
-        S.result[4] = v;
+    __shared__ double sh[6][256];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = t; c < P.n_cells; c += 256) { v[0] += S.epart[4 * c]; v[1] += S.epart[4 * c + 1]; v[5] += S.epart[4 * c + 2]; }
+    for (int b = t; b < S.n_bead_blocks; b += 256) {
+        v[2] += S.bpart[3 * b]; v[3] += S.bpart[3 * b + 1]; v[4] += S.bpart[3 * b + 2];
     }
+    for (int q = 0; q < 6; ++q) sh[q][t] = v[q];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w)
+            for (int q = 0; q < 6; ++q) sh[q][t] += sh[q][t + w];
+        __syncthreads();
+    }
+    if (t < 6) S.result[t] = sh[t][0];
 }
 
 void launch_energy_reduce(const LaunchCtx &L) {
     k_bonded_energy<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-    k_energy_reduce<<<L.syss->n, 32, 0, L.stream>>>(L.sys, L.syss->d);
+    k_energy_reduce<<<L.syss->n, 256, 0, L.stream>>>(L.sys, L.syss->d);
 }
 
 }  // namespace mdas

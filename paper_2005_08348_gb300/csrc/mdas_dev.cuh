@@ -15,7 +15,7 @@ constexpr int MAXT = 16;               // bead types, lipid types, beads per lip
 constexpr int PAIR_THREADS = 128;      // threads per cell in the pair kernel
 constexpr int STAGE_CAP = 384;         // neighbour beads staged per chunk (27 cells)
 constexpr int QCAP = 32;               // per-thread hit queue of the pair kernel
-constexpr int BEAD_BLOCK = 256;        // beads per block of per-bead kernels
+constexpr int BEAD_BLOCK = 128;        // beads per block of per-bead kernels
 constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
 constexpr int MAX_ROUND_TRIALS = 1024; // trials per batched swap evaluation
@@ -48,6 +48,9 @@ struct Params {
     float qsf[3], qsh[3], qsl[3];      // L/2^32 as float, and as a float pair hi + lo
     double rc, rc2, krf, crf;
     float rc2f, rc2f_lo, krf2f;        // rc^2 rounded up, rc^2 (1 - 1e-5), 2 k_rf
+    unsigned long long cwu[3];         // floor(2^32 / n_d): cell width in fixed-point units
+    float qdtf[3];                     // dt 2^32 / L as float (FP32 position update)
+    double therm_c;                    // exp(-dt / tau_t)
     double dt, tau_t, mass, kT, dt_over_m;
     int nf[2];
     double ktarget[2];
@@ -80,7 +83,12 @@ struct Counters {
     int max_cell, pending;
     int n_trials_round, rounds;
     double w_part[2 * MAX_PAIRS];
+    unsigned long long draw_base;      // thermostat variates precomputed for counters
+    int draw_n, draw_tag;              // [draw_base, draw_base + draw_n) of stream draw_tag
+    unsigned int ticket;               // last-block ticket of the fused single trial
 };
+
+constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
 
 // Everything a kernel needs to reach one system.
 struct SysDev {
@@ -94,7 +102,7 @@ struct SysDev {
     uint4 *spos;                       // positions in cell order
     double *ke_part;                   // [n_bead_blocks * 2]
     double *epart;                     // [n_cells * 4] lj, rf, pairs, (unused)
-    double *bpart;                     // [n_bead_blocks * 2] bond, angle energies
+    double *bpart;                     // [n_bead_blocks * 3] bond, angle, kinetic energies (FP64)
     uint4 *pos_snap;
     void *vel_snap;
     int *ltype_snap;
@@ -107,6 +115,7 @@ struct SysDev {
     int4 *lhalf;                       // per-lipid half widths
     TrialRec *log;                     // [LOG_CAP]
     double *result;                    // scratch for reductions to the host [64]
+    double2 *tdraw;                    // [MAX_DRAW_STEPS * 2] (R1, S) per step and group
     int n_bead_blocks;
 };
 
@@ -158,8 +167,10 @@ struct LaunchCtx {
 };
 
 cudaError_t setup_kernels();
-void launch_cells(const LaunchCtx &L);
+void launch_cells(const LaunchCtx &L, bool counted = false);
 void launch_thermostat(const LaunchCtx &L);
+void launch_thermo_draws(const LaunchCtx &L, int n_steps);
+void launch_trial_one(const LaunchCtx &L);
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64);
 void launch_integrate(const LaunchCtx &L);
 void launch_kinetic(const LaunchCtx &L);

@@ -72,12 +72,15 @@ __device__ double bead_delta(const SysDev &S, const Params &P, int i, uint4 pi, 
     return acc;
 }
 
+// fixed-order tree sum over the block (blockDim.x a power of two <= 128)
 __device__ double block_sum(double v, double *sh) {
     sh[threadIdx.x] = v;
     __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < blockDim.x; ++k) s += sh[k];
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double s = sh[0];
     __syncthreads();
     return s;
 }
@@ -96,22 +99,30 @@ __global__ void k_swap_propose(const SysDev *__restrict__ sys, int n) {
     S.tprop[t] = make_int4(a, b, -1, -1);
     S.tu[t] = unit53(w.z, w.w);
     S.tstate[t] = 0;
-    // bounding boxes of the two lipids for the conflict test
-    for (int side = 0; side < 2; ++side) {
-        const int l = side ? b : a;
-        const uint4 p0 = S.pos[l * P.bpl];
-        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-        for (int k = 1; k < P.bpl; ++k) {
-            const uint4 pk = S.pos[l * P.bpl + k];
-            const int d[3] = {(int)(pk.x - p0.x), (int)(pk.y - p0.y), (int)(pk.z - p0.z)};
-            for (int e = 0; e < 3; ++e) { lo[e] = min(lo[e], d[e]); hi[e] = max(hi[e], d[e]); }
-        }
-        const uint32_t cen[3] = {p0.x + (uint32_t)(int)(((long long)lo[0] + hi[0]) / 2),
-                                 p0.y + (uint32_t)(int)(((long long)lo[1] + hi[1]) / 2),
-                                 p0.z + (uint32_t)(int)(((long long)lo[2] + hi[2]) / 2)};
-        S.lbox[2 * t + side] = make_int4((int)cen[0], (int)cen[1], (int)cen[2], 0);
-        S.lhalf[2 * t + side] = make_int4((hi[0] - lo[0]) / 2 + 1, (hi[1] - lo[1]) / 2 + 1, (hi[2] - lo[2]) / 2 + 1, 0);
+}
+
+// bounding box of lipid l in fixed-point units: centre and half widths
+__device__ void lipid_box(const SysDev &S, const Params &P, int l, int4 *cen, int4 *half) {
+    const uint4 p0 = S.pos[l * P.bpl];
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 1; k < P.bpl; ++k) {
+        const uint4 pk = S.pos[l * P.bpl + k];
+        const int d[3] = {(int)(pk.x - p0.x), (int)(pk.y - p0.y), (int)(pk.z - p0.z)};
+        for (int e = 0; e < 3; ++e) { lo[e] = min(lo[e], d[e]); hi[e] = max(hi[e], d[e]); }
     }
+    *cen = make_int4((int)(p0.x + (uint32_t)(int)(((long long)lo[0] + hi[0]) / 2)),
+                     (int)(p0.y + (uint32_t)(int)(((long long)lo[1] + hi[1]) / 2)),
+                     (int)(p0.z + (uint32_t)(int)(((long long)lo[2] + hi[2]) / 2)), 0);
+    *half = make_int4((hi[0] - lo[0]) / 2 + 1, (hi[1] - lo[1]) / 2 + 1, (hi[2] - lo[2]) / 2 + 1, 0);
+}
+
+// grid (ceil(2n/128), n_sys): the boxes of both lipids of every trial
+__global__ void k_swap_boxes(const SysDev *__restrict__ sys, int n) {
+    const SysDev &S = sys[blockIdx.y];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * n) return;
+    const int4 pr = S.tprop[k >> 1];
+    lipid_box(S, *S.p, (k & 1) ? pr.y : pr.x, &S.lbox[k], &S.lhalf[k]);
 }
 
 __device__ __forceinline__ bool boxes_near(const Params &P, int4 ca, int4 ha, int4 cb, int4 hb) {
@@ -149,6 +160,8 @@ void launch_swap_propose(const LaunchCtx &L, int n) {
     dim3 g1((n + 127) / 128, L.n_sys);
     k_swap_propose<<<g1, 128, 0, L.stream>>>(L.sys, n);
     if (n > 1) {   // a single trial has no earlier trial to conflict with
+        dim3 g0((2 * n + 127) / 128, L.n_sys);
+        k_swap_boxes<<<g0, 128, 0, L.stream>>>(L.sys, n);
         const int W = (n + 31) / 32;
         dim3 g2((n * W + 127) / 128, L.n_sys);
         k_swap_conflicts<<<g2, 128, 0, L.stream>>>(L.sys, n);
@@ -227,6 +240,95 @@ __device__ void set_lipid_type(const SysDev &S, const Params &P, int l, int lt) 
         S.spos[S.sidx[id]].w = m;
     }
 }
+
+// One exchange trial per system, whole: grid (9, n_sys).  Every CTA draws the
+// proposal of trial C.trial, sums the dE over its 3 neighbour cells, and the
+// last CTA to finish (a ticket, no waiting) adds the 9 partial sums in order,
+// takes the Metropolis decision and applies it.  Equal to one sequential
+// trial; used when trials come one at a time (one after every MD step).
+__global__ void __launch_bounds__(128) k_trial_one(const SysDev *__restrict__ sys) {
+    const SysDev &S = sys[blockIdx.y];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    const int grp = blockIdx.x;
+    __shared__ double sh[128];
+    __shared__ int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT];
+    __shared__ int nchg, kmask, last;
+    const unsigned long long T = C.trial;
+    const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
+    const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
+    const int ta = S.ltype[a], tb = S.ltype[b];
+    const bool null_trial = (a == b) || (ta == tb);
+    if (threadIdx.x == 0) {
+        int m = 0, nc = 0;
+        if (!null_trial) {
+            for (int k = 0; k < P.bpl; ++k)
+                if (P.lbt[ta * 16 + k] != P.lbt[tb * 16 + k]) m |= 1 << k;
+            for (int side = 0; side < 2; ++side)
+                for (int k = 0; k < P.bpl; ++k)
+                    if ((m >> k) & 1) {
+                        chg_id[nc] = (side ? b : a) * P.bpl + k;
+                        chg_old[nc] = P.lbt[(side ? tb : ta) * 16 + k];
+                        chg_new[nc] = P.lbt[(side ? ta : tb) * 16 + k];
+                        ++nc;
+                    }
+        }
+        nchg = nc;
+        kmask = m;
+    }
+    __syncthreads();
+    const int nc = nchg, m = kmask;
+    auto changed = [&](uint32_t mj, int) {
+        const int l = meta_lip(mj);
+        return (l == a || l == b) && ((m >> meta_k(mj)) & 1);
+    };
+    auto newt = [&](uint32_t mj, int) {
+        const int l = meta_lip(mj);
+        return (int)P.lbt[(l == a ? tb : ta) * 16 + meta_k(mj)];
+    };
+    double acc = 0.0;
+    for (int it = threadIdx.x; it < nc * 3; it += blockDim.x) {
+        const int ci = it / 3, slot = grp * 3 + it % 3;
+        const int i = chg_id[ci];
+        acc += bead_delta(S, P, i, S.pos[i], chg_old[ci], chg_new[ci], slot, newt, changed);
+    }
+    const double part = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        S.tdE[grp] = part;
+        __threadfence();
+        last = atomicAdd(&C.ticket, 1u) == DE_GROUPS - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double dE = 0.0;
+    for (int g = 0; g < DE_GROUPS; ++g) dE += __ldcg(&S.tdE[g]);
+    TrialRec r;
+    r.a = a; r.b = b; r.u = unit53(w.z, w.w); r.dE = 0.0; r.accepted = 0; r.index = T;
+    r.null_trial = null_trial;
+    if (!null_trial) {
+        r.dE = dE;
+        if (dE + P.kT * log(r.u) <= 0.0) {
+            set_lipid_type(S, P, a, tb);
+            set_lipid_type(S, P, b, ta);
+            r.accepted = 1;
+        }
+    }
+    S.log[T % LOG_CAP] = r;
+    C.trials++;
+    C.force_evals++;
+    C.null_trials += r.null_trial;
+    C.accepted += r.accepted;
+    C.trial = T + 1;
+    C.pending = 0;
+    C.ticket = 0;
+}
+
+void launch_trial_one(const LaunchCtx &L) {
+    dim3 g(DE_GROUPS, L.n_sys);
+    k_trial_one<<<g, 128, 0, L.stream>>>(L.sys);
+}
+
 
 // one block per system, one thread walks the trials in order
 __global__ void k_swap_resolve(const SysDev *__restrict__ sys, int n) {
