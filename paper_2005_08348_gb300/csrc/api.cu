@@ -59,7 +59,9 @@ struct mdas_system {
     std::string err;
     bool unstable = false;
     bool cells_valid = false;   // the cell list matches the current positions and types
-    bool counted = false;       // cell_count holds the integrator's counts of the current positions
+    bool counted = false;       // cell_count holds the step kernel's counts of the current positions
+    bool alpha_ready = false;   // the thermostat factor of the next step is computed
+    int alpha_domain = 0;       // ... for plain MD (0) or the alchemical trajectory (1)
     bool timing = false;
     double pair_ms = 0.0;
     long long pair_launches = 0;
@@ -195,10 +197,22 @@ mdas_status build_cells(mdas_system *s, Batch &b) {
 
 void md_step_launches(const Batch &b, bool lambda, bool counted) {
     LaunchCtx L = b.ctx();
-    launch_thermostat(L);
     launch_cells(L, counted);
-    launch_pair(L, lambda, false, b.precision == 1);
-    launch_integrate(L);
+    launch_step(L, lambda);
+}
+
+// The step kernel leaves the factor of the next step behind; after a state
+// change (or a switch between plain MD and the alchemical trajectory) it is
+// computed from the velocities, per system so batching never changes results.
+mdas_status ensure_alpha(mdas_system *s, Batch &b, int domain) {
+    for (auto *x : b.sys)
+        if (!x->alpha_ready || x->alpha_domain != domain) {
+            launch_thermostat(x->solo->ctx());
+            x->alpha_ready = true;
+            x->alpha_domain = domain;
+        }
+    CK(cudaGetLastError());
+    return MDAS_OK;
 }
 
 __global__ void k_batch_status(const SysDev *__restrict__ sys, int n, int *out) {
@@ -229,7 +243,7 @@ mdas_status check_err(mdas_system *s, Batch &b) {
         for (auto *x : b.sys) x->unstable = true;
         std::string why;
         if (err & ERR_NONFINITE) why += " non-finite velocity;";
-        if (err & ERR_STAGE_OVERFLOW) why += " more than 768 beads in a 27-cell neighbourhood;";
+        if (err & ERR_CELL_OVERFLOW) why += " a cell holds more beads than its capacity;";
         if (err & ERR_TIMEOUT) why += " bounded wait expired;";
         if (err & ERR_ROUNDS) why += " exchange rounds exhausted;";
         return fail(s, MDAS_ERR_UNSTABLE, "unstable:" + why);
@@ -267,24 +281,23 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
     }
     CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
     LaunchCtx L = b.ctx();
-    launch_thermo_draws(L, units * steps_per_unit);
+    // the step kernel of step k sets the factor of step k + 1
+    launch_thermo_draws(L, units * steps_per_unit + 1);
     int ev = 0;
     for (int u = 0; u < units; ++u) {
         for (int k = 0; k < steps_per_unit; ++k) {
-            launch_thermostat(L);
             const bool first = u == 0 && k == 0;
             const bool have_cells = trial && k == 0 && (u > 0 || reuse_first);
             if (!have_cells) launch_cells(L, first ? counted_first : true);
             if (timing) {
                 // external event nodes: recorded (and timed) at every replay
                 cudaEventRecordWithFlags(ge.pair_events[ev].first, b.stream, cudaEventRecordExternal);
-                launch_pair(L, lambda, false, b.precision == 1);
+                launch_step(L, lambda);
                 cudaEventRecordWithFlags(ge.pair_events[ev].second, b.stream, cudaEventRecordExternal);
                 ++ev;
             } else {
-                launch_pair(L, lambda, false, b.precision == 1);
+                launch_step(L, lambda);
             }
-            launch_integrate(L);
         }
         if (trial) {
             launch_cells(L, true);
@@ -326,6 +339,8 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
     bool counted;
     mdas_status st = sync_counted(s, b, &counted);
+    if (st != MDAS_OK) return st;
+    st = ensure_alpha(s, b, lambda ? 1 : 0);
     if (st != MDAS_OK) return st;
     if (n_units > 0) {
         bool reuse = false;
@@ -470,6 +485,14 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     memset(&P, 0, sizeof(P));
     P.n = n; P.n_lip = nl; P.bpl = bpl; P.n_bt = nbt; P.n_lt = nlt; P.n_lipid_beads = nl * bpl;
     P.n_cells = nc[0] * nc[1] * nc[2];
+    {   // cell capacity: four times the mean occupancy, at least 32, a multiple of 32
+        const double mean = (double)n / P.n_cells;
+        P.capc = std::max(32, (int)std::ceil(4.0 * mean / 32.0) * 32);
+        if (P.capc > 1024) {
+            delete s;
+            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: more than 256 beads per cell on average");
+        }
+    }
     for (int k = 0; k < 3; ++k) {
         P.nc[k] = nc[k];
         P.box[k] = d->box[k];
@@ -544,6 +567,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
 
     // ---- device memory: one arena
     const int nbb = (n + BEAD_BLOCK - 1) / BEAD_BLOCK;
+    const size_t nslot = (size_t)P.n_cells * P.capc;
     const size_t vsz = d->precision == MDAS_FP64 ? 32 : 16;
     struct Item { void **ptr; size_t bytes; };
     SysDev &H = s->hs;
@@ -554,11 +578,10 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.pos, 16ull * n}, {(void **)&H.vel, vsz * n},
         {(void **)&H.fx, 8ull * n}, {(void **)&H.fy, 8ull * n}, {(void **)&H.fz, 8ull * n},
         {(void **)&H.ltype, 4ull * std::max(nl, 1)},
-        {(void **)&H.cell_of, 4ull * n}, {(void **)&H.cell_slot, 4ull * n},
-        {(void **)&H.cell_count, 4ull * P.n_cells}, {(void **)&H.cell_start, 4ull * (P.n_cells + 1)},
-        {(void **)&H.tmp_ids, 4ull * n}, {(void **)&H.sorted_id, 4ull * n}, {(void **)&H.sidx, 4ull * n},
-        {(void **)&H.spos, 16ull * n},
-        {(void **)&H.ke_part, 16ull * nbb}, {(void **)&H.bpart, 24ull * nbb}, {(void **)&H.epart, 32ull * P.n_cells},
+        {(void **)&H.cell_count, 4ull * P.n_cells}, {(void **)&H.cell_n, 4ull * P.n_cells},
+        {(void **)&H.tmp_ids, 4ull * nslot}, {(void **)&H.sorted_id, 4ull * nslot}, {(void **)&H.sidx, 4ull * n},
+        {(void **)&H.spos, 16ull * nslot},
+        {(void **)&H.ke_part, 16ull * P.n_cells}, {(void **)&H.bpart, 24ull * nbb}, {(void **)&H.epart, 32ull * P.n_cells},
         {(void **)&H.pos_snap, 16ull * n}, {(void **)&H.vel_snap, vsz * n},
         {(void **)&H.ltype_snap, 4ull * std::max(nl, 1)},
         {(void **)&H.tprop, 16ull * MAX_ROUND_TRIALS}, {(void **)&H.tu, 8ull * MAX_ROUND_TRIALS},
@@ -620,10 +643,9 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     }
     if (st == MDAS_OK) st = make_batch({s}, s->solo);
     if (st == MDAS_OK) {
-        launch_kinetic(s->solo->ctx());
         cudaError_t e = cudaStreamSynchronize(s->stream);
         if (e == cudaSuccess) e = cudaGetLastError();
-        if (e != cudaSuccess) st = cuda_fail(s, e, "create: kinetic energy");
+        if (e != cudaSuccess) st = cuda_fail(s, e, "create: upload");
     }
     if (st != MDAS_OK) {
         g_last_error = s->err;
@@ -771,7 +793,9 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
             launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
             if (md_per_lambda > 0) {
                 GraphEntry *ge;
-                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, s->counted, &ge);
+                mdas_status st = ensure_alpha(s, b, 1);
+                if (st != MDAS_OK) return st;
+                st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, s->counted, &ge);
                 if (st != MDAS_OK) return st;
                 st = replay(s, b, ge);
                 if (st != MDAS_OK) return st;
@@ -784,8 +808,8 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
     }
     launch_mdas_accept(L);
     launch_mdas_restore(L);
-    launch_kinetic(L);
     s->cells_valid = false;
+    s->alpha_ready = false;
     Counters c;
     double r[10];
     CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
@@ -921,7 +945,7 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
     if (s->counted) CK(cudaMemsetAsync(s->hs.cell_count, 0, 4ull * s->hp.n_cells, s->stream));
     s->counted = false;
-    launch_kinetic(s->solo->ctx());
+    s->alpha_ready = false;
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
     s->unstable = false;
@@ -933,12 +957,23 @@ mdas_status mdas_cell_list(mdas_system *s, int32_t *sorted_ids, int32_t *cell_st
     if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "cell_list: NULL system");
     mdas_status st0 = build_cells(s, *s->solo);
     if (st0 != MDAS_OK) return st0;
-    if (sorted_ids) CK(cudaMemcpyAsync(sorted_ids, s->hs.sorted_id, 4ull * s->n, cudaMemcpyDeviceToHost, s->stream));
-    if (cell_start) CK(cudaMemcpyAsync(cell_start, s->hs.cell_start, 4ull * (s->hp.n_cells + 1), cudaMemcpyDeviceToHost, s->stream));
+    const int nc = s->hp.n_cells, capc = s->hp.capc;
+    std::vector<int> cnt(nc), ids((size_t)nc * capc);
+    CK(cudaMemcpyAsync(cnt.data(), s->hs.cell_n, 4ull * nc, cudaMemcpyDeviceToHost, s->stream));
+    if (sorted_ids) CK(cudaMemcpyAsync(ids.data(), s->hs.sorted_id, 4ull * nc * capc, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
+    int o = 0;
+    for (int c = 0; c < nc; ++c) {
+        if (cell_start) cell_start[c] = o;
+        if (sorted_ids)
+            for (int k = 0; k < cnt[c]; ++k) sorted_ids[o + k] = ids[(size_t)c * capc + k];
+        o += cnt[c];
+    }
+    if (cell_start) cell_start[nc] = o;
     if (ncell) for (int k = 0; k < 3; ++k) ncell[k] = s->hp.nc[k];
-    return MDAS_OK;
+    if (o != s->n) return fail(s, MDAS_ERR_UNSTABLE, "cell_list: a cell overflowed its capacity");
+    return check_err(s, *s->solo);
 }
 
 mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32_t md_steps, int32_t swap_trials) {

@@ -8,6 +8,12 @@
 //
 // Every kernel takes an array of systems plus a block map, so one launch can
 // advance one system or a whole batch of them.
+//
+// One MD step is two launches: the cell-list finish (per-cell ordering of the
+// beads the previous step counted into fixed-capacity cells) and the fused
+// step kernel (pair forces, bonded forces, leapfrog update, counting into the
+// next step's cells; the last CTA of each system then computes the next
+// step's thermostat factor).
 #include <cmath>
 #include <cstdio>
 
@@ -22,9 +28,24 @@ struct Vec4<float> { using T = float4; };
 template <>
 struct Vec4<double> { using T = Dbl4; };
 
+__device__ __forceinline__ int cell_of_pos(const Params &P, uint4 q) {
+    const int cx = (int)(((unsigned long long)q.x * (unsigned)P.nc[0]) >> 32);
+    const int cy = (int)(((unsigned long long)q.y * (unsigned)P.nc[1]) >> 32);
+    const int cz = (int)(((unsigned long long)q.z * (unsigned)P.nc[2]) >> 32);
+    return (cz * P.nc[1] + cy) * P.nc[0] + cx;
+}
+
+// count bead `id` into cell c of the next cell list (unordered within the cell)
+__device__ __forceinline__ void count_into_cell(const SysDev &S, const Params &P, int id, int c) {
+    const int slot = atomicAdd(&S.cell_count[c], 1);
+    if (slot < P.capc) S.tmp_ids[c * P.capc + slot] = id;
+    else atomicOr(&S.c->err, ERR_CELL_OVERFLOW);
+}
+
 // ------------------------------------------------------------------ cells
 // Cell of a bead: c_d = floor(u_d * n_d / 2^32) (exact integer arithmetic),
-// cell id = (cz * ny + cy) * nx + cx.
+// cell id = (cz * ny + cy) * nx + cx.  Cells are buckets of capacity capc:
+// bead p of cell c sits at c * capc + p, p < cell_n[c].
 
 __global__ void k_cell_count(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     const int2 bm = bmap[blockIdx.x];
@@ -32,98 +53,39 @@ __global__ void k_cell_count(const SysDev *__restrict__ sys, const int2 *__restr
     const Params &P = *S.p;
     const int i = bm.y + threadIdx.x;
     if (i >= P.n) return;
-    const uint4 q = S.pos[i];
-    const int cx = (int)(((unsigned long long)q.x * (unsigned)P.nc[0]) >> 32);
-    const int cy = (int)(((unsigned long long)q.y * (unsigned)P.nc[1]) >> 32);
-    const int cz = (int)(((unsigned long long)q.z * (unsigned)P.nc[2]) >> 32);
-    const int c = (cz * P.nc[1] + cy) * P.nc[0] + cx;
-    S.cell_of[i] = c;
-    S.cell_slot[i] = atomicAdd(&S.cell_count[c], 1);
-}
-
-// exclusive scan of the cell counts (one block per system); zeroes the
-// counts for the next build and records the largest cell
-__global__ void __launch_bounds__(1024) k_cell_scan(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    const SysDev &S = sys[bmap[blockIdx.x].x];
-    const Params &P = *S.p;
-    const int nc = P.n_cells;
-    const int T = blockDim.x;
-    const int per = (nc + T - 1) / T;
-    const int lo = min(nc, threadIdx.x * per), hi = min(nc, lo + per);
-    int sum = 0, mx = 0;
-    for (int c = lo; c < hi; ++c) { int v = S.cell_count[c]; sum += v; mx = max(mx, v); }
-    __shared__ int warp_sum[32], warp_max[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    int wm = mx;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, o));
-    if (lane == 31) warp_sum[wid] = incl;
-    if (lane == 0) warp_max[wid] = wm;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = T >> 5;
-        int v = lane < nw ? warp_sum[lane] : 0;
-        int m = lane < nw ? warp_max[lane] : 0;
-        int inc = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int x = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += x;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane < nw) warp_sum[lane] = inc - v;   // exclusive warp offsets
-        if (lane == 0) S.c->max_cell = m;
-    }
-    __syncthreads();
-    int run = warp_sum[wid] + incl - sum;
-    for (int c = lo; c < hi; ++c) {
-        S.cell_start[c] = run;
-        run += S.cell_count[c];
-        S.cell_count[c] = 0;
-    }
-    if (threadIdx.x == T - 1) S.cell_start[nc] = run;
-}
-
-__global__ void k_cell_scatter(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
-    const int i = bm.y + threadIdx.x;
-    if (i >= S.p->n) return;
-    S.tmp_ids[S.cell_start[S.cell_of[i]] + S.cell_slot[i]] = i;
+    count_into_cell(S, P, i, cell_of_pos(P, S.pos[i]));
 }
 
 // One warp per cell: order the cell's beads by id (rank = number of smaller
-// ids in the cell) and gather their positions into cell order.
+// ids in the cell), gather their positions into cell order, publish the
+// count and clear the counter for the next step.
 __global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     const int2 bm = bmap[blockIdx.x];
     const SysDev &S = sys[bm.x];
+    const Params &P = *S.p;
     const int c = bm.y + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (c >= S.p->n_cells) return;
-    const int s = S.cell_start[c], e = S.cell_start[c + 1];
-    for (int a = s + lane; a < e; a += 32) {
-        const int id = S.tmp_ids[a];
+    if (c >= P.n_cells) return;
+    const int cnt = min(S.cell_count[c], P.capc);
+    const int base = c * P.capc;
+    for (int a = lane; a < cnt; a += 32) {
+        const int id = S.tmp_ids[base + a];
         int rank = 0;
-        for (int b = s; b < e; ++b) rank += (S.tmp_ids[b] < id);
-        const int p = s + rank;
-        S.sorted_id[p] = id;
-        S.sidx[id] = p;
-        S.spos[p] = S.pos[id];
+        for (int b = 0; b < cnt; ++b) rank += (S.tmp_ids[base + b] < id);
+        S.sorted_id[base + rank] = id;
+        S.sidx[id] = base + rank;
+        S.spos[base + rank] = S.pos[id];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        S.cell_n[c] = cnt;
+        S.cell_count[c] = 0;
     }
 }
 
-// counted: the integrator has already counted the current positions into cells
+// counted: the step kernel has already counted the current positions into cells
 void launch_cells(const LaunchCtx &L, bool counted) {
     if (!counted) k_cell_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-    k_cell_scan<<<L.syss->n, 1024, 0, L.stream>>>(L.sys, L.syss->d);
-    k_cell_scatter<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
     k_cell_finish<<<L.sortcells->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.sortcells->d);
 }
 
@@ -171,6 +133,30 @@ __device__ double bussi_alpha(const Params &P, double K, int nf, double kt, doub
     return sqrt(knew / K);
 }
 
+// The same factor in single precision for FP32 systems (velocities are
+// float; the factor's rounding is far below theirs).
+__device__ float bussi_alpha_f(const Params &P, double K, int nf, double kt, double2 d) {
+    if (P.tau_t <= 0.0 || K <= 0.0 || nf < 3) return 1.0f;
+    const float c = (float)P.therm_c, Kf = (float)K, q = (float)(kt / nf);
+    const float a = sqrtf(c * Kf) + (float)d.x * sqrtf((1.0f - c) * q);
+    const float knew = a * a + (1.0f - c) * q * (float)d.y;
+    return sqrtf(knew / Kf);
+}
+
+// Factor of group g for the step with counter ctr of the current domain,
+// from the precomputed variates when they cover ctr.
+__device__ double alpha_for(const SysDev &S, const Params &P, const Counters &C, int g, double K,
+                            unsigned long long ctr, uint32_t tag) {
+    if (P.tau_t <= 0.0) return 1.0;
+    double2 d;
+    if ((int)tag == C.draw_tag && ctr >= C.draw_base && ctr < C.draw_base + (unsigned long long)C.draw_n)
+        d = S.tdraw[2 * (ctr - C.draw_base) + g];
+    else
+        d = bussi_draws(P, P.nf[g], (uint32_t)g, (uint32_t)ctr, tag);
+    return P.precision == 1 ? bussi_alpha(P, K, P.nf[g], P.ktarget[g], d)
+                            : (double)bussi_alpha_f(P, K, P.nf[g], P.ktarget[g], d);
+}
+
 // grid (ceil(2 n / 64), n_sys): variates for the next n MD steps of the
 // current counter domain (plain MD or alchemical trajectory)
 __global__ void k_thermo_draws(const SysDev *__restrict__ sys, int n) {
@@ -194,15 +180,24 @@ void launch_thermo_draws(const LaunchCtx &L, int n) {
     k_thermo_draws<<<g, 64, 0, L.stream>>>(L.sys, n);
 }
 
+// Thermostat factor of the next step straight from the velocities (after the
+// state was set or the counter domain changed); one block per system, a
+// fixed-order reduction (thread-strided sums, then a tree).
+template <typename Real>
 __global__ void __launch_bounds__(256) k_thermostat(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    using V4 = typename Vec4<Real>::T;
     const SysDev &S = sys[bmap[blockIdx.x].x];
     const Params &P = *S.p;
     Counters &C = *S.c;
     const int t = threadIdx.x;
-    // group kinetic energies: strided partial sums, then a fixed-order tree
     __shared__ double ks[2][256];
     double k0 = 0.0, k1 = 0.0;
-    for (int b = t; b < S.n_bead_blocks; b += 256) { k0 += S.ke_part[2 * b]; k1 += S.ke_part[2 * b + 1]; }
+    const V4 *vel = reinterpret_cast<const V4 *>(S.vel);
+    for (int i = t; i < P.n; i += 256) {
+        const V4 v = vel[i];
+        const double e = 0.5 * P.mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+        if (i < P.n_lipid_beads) k0 += e; else k1 += e;
+    }
     ks[0][t] = k0;
     ks[1][t] = k1;
     __syncthreads();
@@ -213,27 +208,70 @@ __global__ void __launch_bounds__(256) k_thermostat(const SysDev *__restrict__ s
     const int in_at = C.in_at;
     const unsigned long long ctr = in_at ? C.at_step : C.step;
     const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
-    if ((t & 31) == 0 && t < 64) {          // one warp per coupling group
+    if ((t & 31) == 0 && t < 64) {
         const int g = t >> 5;
-        double2 d = make_double2(0.0, 0.0);
-        if (P.tau_t <= 0.0)
-            ;   // no thermostat: alpha = 1
-        else if ((int)tag == C.draw_tag && ctr >= C.draw_base && ctr < C.draw_base + (unsigned long long)C.draw_n)
-            d = S.tdraw[2 * (ctr - C.draw_base) + g];
-        else
-            d = bussi_draws(P, P.nf[g], (uint32_t)g, (uint32_t)ctr, tag);
-        C.alpha[g] = bussi_alpha(P, ks[g][0], P.nf[g], P.ktarget[g], d);
-    }
-    __syncthreads();
-    if (t == 0) {
-        if (in_at) C.at_step = ctr + 1; else C.step = ctr + 1;
-        C.md_steps++;
-        C.force_evals++;
+        C.alpha[g] = alpha_for(S, P, C, g, ks[g][0], ctr, tag);
     }
 }
 
 void launch_thermostat(const LaunchCtx &L) {
-    k_thermostat<<<L.syss->n, 256, 0, L.stream>>>(L.sys, L.syss->d);
+    if (L.precision == 1) k_thermostat<double><<<L.syss->n, 256, 0, L.stream>>>(L.sys, L.syss->d);
+    else k_thermostat<float><<<L.syss->n, 256, 0, L.stream>>>(L.sys, L.syss->d);
+}
+
+// ---------------------------------------------------------- bonded terms
+// Separation r_a - r_b of two beads (exact integer minimum image).
+template <typename Real>
+__device__ __forceinline__ void sep(const Params &P, uint4 a, uint4 b, Real d[3]) {
+    if (sizeof(Real) == 4) {
+        d[0] = (Real)((float)(int)(a.x - b.x) * P.qsf[0]);
+        d[1] = (Real)((float)(int)(a.y - b.y) * P.qsf[1]);
+        d[2] = (Real)((float)(int)(a.z - b.z) * P.qsf[2]);
+    } else {
+        d[0] = (Real)((double)(int)(a.x - b.x) * P.qs[0]);
+        d[1] = (Real)((double)(int)(a.y - b.y) * P.qs[1]);
+        d[2] = (Real)((double)(int)(a.z - b.z) * P.qs[2]);
+    }
+}
+
+// Bonded force on bead i (local index k of lipid l): harmonic bonds to its
+// partners and the cosine-angle terms of every angle containing it.
+// Positions come from the cell-ordered copy (stable during a step).
+template <typename Real>
+__device__ void bonded_force(const SysDev &S, const Params &P, int l, int k, uint4 pi, Real f[3]) {
+    const int base = l * P.bpl;
+    for (int b = 0; b < P.nbond[k]; ++b) {
+        const uint4 pj = S.spos[S.sidx[base + P.bpart[k][b]]];
+        Real d[3];
+        sep<Real>(P, pi, pj, d);
+        const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
+        f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
+    }
+    for (int a = 0; a < P.nang[k]; ++a) {
+        const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
+        const uint4 qi = li == k ? pi : S.spos[S.sidx[base + li]];
+        const uint4 qj = lj == k ? pi : S.spos[S.sidx[base + lj]];
+        const uint4 qk = lk == k ? pi : S.spos[S.sidx[base + lk]];
+        Real A[3], B[3];
+        sep<Real>(P, qi, qj, A);
+        sep<Real>(P, qk, qj, B);
+        const Real la2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+        const Real lb2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const Real iab = (Real)1 / sqrt(la2 * lb2);
+        const Real cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * iab;
+        const Real pre = -(Real)P.kth * (cs - (Real)P.cos0);
+        const Real ia2 = (Real)1 / la2, ib2 = (Real)1 / lb2;
+        for (int d = 0; d < 3; ++d) {
+            const Real dci = B[d] * iab - cs * A[d] * ia2;
+            const Real dck = A[d] * iab - cs * B[d] * ib2;
+            Real g;
+            if (k == li) g = dci;
+            else if (k == lk) g = dck;
+            else g = -(dci + dck);
+            f[d] += pre * g;
+        }
+    }
 }
 
 // ------------------------------------------------------------ pair forces
@@ -242,13 +280,20 @@ void launch_thermostat(const LaunchCtx &L) {
 // integer offset from the centre (wrap-around difference, so every staged copy
 // is the periodic image nearest the cell) and its coordinates in nm.  Threads
 // are (i-bead, j-stream) pairs; each thread first culls its candidates into a
-// private queue of in-cutoff, non-excluded partners (candidates within float
-// rounding of rc are decided exactly from the integer offsets), then evaluates
-// the queue with all lanes busy.  In FP32 the separation of a queued pair comes
-// from the exact integer difference; r^-2 is a correctly rounded reciprocal and
-// r^-6 its error-free cube, so a pair force carries only a few roundings.
-// Partial forces are summed over the streams in a fixed order and stored once
-// per bead; every pair is evaluated from both sides (no atomics on the j bead).
+// private queue (branch-free), then evaluates the queue with all lanes busy,
+// dropping excluded pairs and deciding candidates within float rounding of rc
+// exactly from the integer offsets.  In FP32 the separation of a queued pair
+// comes from the exact integer difference; r^-2 is a correctly rounded
+// reciprocal and r^-6 its error-free cube, so a pair force carries only a few
+// roundings.  Stream partials are summed in 64-bit fixed point.  Every pair is
+// evaluated from both sides (no atomics on the j bead).
+//
+// INTEG: the step kernel.  Each bead's thread then adds its bonded force and
+// applies the leapfrog update with the thermostat factor, writes the new
+// position and velocity, counts the bead into the next step's cells and
+// contributes to its cell's kinetic-energy partial; the last CTA of a system
+// reduces those partials and sets the next step's factor.  Otherwise the total
+// force is stored in fixed point.
 
 // a - b of two frame offsets, wrapped to 32 bits (the minimum image)
 __device__ __forceinline__ int wrap_diff(int a, int b) { return (int)((uint32_t)a - (uint32_t)b); }
@@ -277,8 +322,12 @@ __device__ __forceinline__ StagedPos<Real> frame_coords(const Params &P, int ox,
     return e;
 }
 
-template <typename Real, bool LAM, bool ENERGY>
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 4294967296.0f); }
+__device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * FIX); }
+
+template <typename Real, bool LAM, bool ENERGY, bool INTEG>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    using V4 = typename Vec4<Real>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int2 bm = bmap[blockIdx.x];
     const SysDev &S = sys[bm.x];
@@ -294,10 +343,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     Real *tf6 = tf12 + 256;
     Real *tqq = tf6 + 256;
     uint16_t *q = reinterpret_cast<uint16_t *>(tqq + 256);                     // [QCAP][PAIR_THREADS]
-    Real *red = reinterpret_cast<Real *>(q);                                   // aliases q after the queues drain
+    long long *red = reinterpret_cast<long long *>(q);                         // aliases q after the queues drain
 
     __shared__ int cst[27], ccnt[27], coff[28];
     __shared__ double ered[3][PAIR_THREADS];
+    __shared__ Real kered[2][PAIR_THREADS];
+    __shared__ int last;
 
     for (int k = t; k < 256; k += PAIR_THREADS) {
         if (F32) {
@@ -312,9 +363,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
         const int x = (cx + dx + nx) % nx, y = (cy + dy + ny) % ny, z = (cz + dz + nz) % nz;
         const int cj = (z * ny + y) * nx + x;
-        const int s0 = S.cell_start[cj];
-        cst[t] = s0;
-        ccnt[t] = S.cell_start[cj + 1] - s0;
+        cst[t] = cj * P.capc;
+        ccnt[t] = S.cell_n[cj];
     }
     __syncthreads();
     if (t == 0) {
@@ -339,11 +389,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
     const Real lam = LAM ? (Real)S.c->lambda : (Real)0;
     double elj = 0.0, erf = 0.0, epairs = 0.0;
+    Real ke0 = 0, ke1 = 0;
 
     for (int ib = 0; ib < ni; ib += IW) {
         const int i = ib + il;
         const bool valid = i < ni && js < NS;
-        const uint4 vi = S.spos[ifirst + (valid ? i : 0)];
+        const uint4 vi = S.spos[ifirst + (i < ni ? i : 0)];
         const int oix = (int)(vi.x - rx), oiy = (int)(vi.y - ry), oiz = (int)(vi.z - rz);
         StagedPos<Real> pi = frame_coords<Real>(P, oix, oiy, oiz);
         if (!valid) pi.x = (Real)1e30;            // an idle lane never finds a partner
@@ -461,57 +512,129 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         }
 
         __syncthreads();                          // every queue has drained: red may alias q
-        red[0 * PAIR_THREADS + t] = ax;
-        red[1 * PAIR_THREADS + t] = ay;
-        red[2 * PAIR_THREADS + t] = az;
+        red[0 * PAIR_THREADS + t] = to_fix(ax);
+        red[1 * PAIR_THREADS + t] = to_fix(ay);
+        red[2 * PAIR_THREADS + t] = to_fix(az);
         __syncthreads();
         if (t < IW && ib + t < ni) {
-            Real fx = 0, fy = 0, fz = 0;
-            for (int s = 0; s < NS; ++s) {   // fixed order over the streams
-                fx += red[0 * PAIR_THREADS + s * IW + t];
-                fy += red[1 * PAIR_THREADS + s * IW + t];
-                fz += red[2 * PAIR_THREADS + s * IW + t];
+            long long Fx = 0, Fy = 0, Fz = 0;
+            for (int s = 0; s < NS; ++s) {       // fixed-point sum over the streams
+                Fx += red[0 * PAIR_THREADS + s * IW + t];
+                Fy += red[1 * PAIR_THREADS + s * IW + t];
+                Fz += red[2 * PAIR_THREADS + s * IW + t];
             }
-            const int id = S.sorted_id[ifirst + ib + t];
-            if (F32) {
-                S.fx[id] = __float2ll_rn((float)fx * 4294967296.0f);
-                S.fy[id] = __float2ll_rn((float)fy * 4294967296.0f);
-                S.fz[id] = __float2ll_rn((float)fz * 4294967296.0f);
+            const int p = ifirst + ib + t;
+            const int id = S.sorted_id[p];
+            const uint4 pu = S.spos[p];
+            const int l = meta_lip(pu.w);
+            if (l >= 0) {
+                Real fb[3] = {(Real)0, (Real)0, (Real)0};
+                bonded_force<Real>(S, P, l, meta_k(pu.w), pu, fb);
+                Fx += to_fix(fb[0]); Fy += to_fix(fb[1]); Fz += to_fix(fb[2]);
+            }
+            if (!INTEG) {
+                S.fx[id] = Fx; S.fy[id] = Fy; S.fz[id] = Fz;
             } else {
-                S.fx[id] = __double2ll_rn((double)fx * FIX);
-                S.fy[id] = __double2ll_rn((double)fy * FIX);
-                S.fz[id] = __double2ll_rn((double)fz * FIX);
+                const Real sc = (Real)(1.0 / FIX);
+                const Real f0 = (Real)Fx * sc, f1 = (Real)Fy * sc, f2 = (Real)Fz * sc;
+                const int g = id < P.n_lipid_beads ? 0 : 1;
+                const Real a = (Real)S.c->alpha[g];
+                const Real dtm = (Real)P.dt_over_m;
+                V4 *vel = reinterpret_cast<V4 *>(S.vel);
+                V4 v = vel[id];
+                v.x = a * v.x + f0 * dtm;
+                v.y = a * v.y + f1 * dtm;
+                v.z = a * v.z + f2 * dtm;
+                vel[id] = v;
+                if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&S.c->err, ERR_NONFINITE);
+                uint4 np = pu;
+                if (F32) {
+                    np.x += (uint32_t)__float2int_rn((float)v.x * P.qdtf[0]);
+                    np.y += (uint32_t)__float2int_rn((float)v.y * P.qdtf[1]);
+                    np.z += (uint32_t)__float2int_rn((float)v.z * P.qdtf[2]);
+                } else {
+                    np.x += (uint32_t)(long long)rint((double)v.x * P.qdt[0]);
+                    np.y += (uint32_t)(long long)rint((double)v.y * P.qdt[1]);
+                    np.z += (uint32_t)(long long)rint((double)v.z * P.qdt[2]);
+                }
+                S.pos[id] = np;
+                count_into_cell(S, P, id, cell_of_pos(P, np));
+                const Real e = (Real)0.5 * (Real)P.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+                if (g == 0) ke0 += e; else ke1 += e;
+            }
+        }
+    }
+    if (INTEG) {
+        // this cell's kinetic-energy partials (fixed order), then the ticket
+        kered[0][t] = ke0;
+        kered[1][t] = ke1;
+        __syncthreads();
+        if (t == 0) {
+            Real a0 = 0, a1 = 0;
+            for (int k = 0; k < (ni < PAIR_THREADS ? ni : PAIR_THREADS); ++k) { a0 += kered[0][k]; a1 += kered[1][k]; }
+            S.ke_part[2 * c] = (double)a0;
+            S.ke_part[2 * c + 1] = (double)a1;
+            __threadfence();
+            last = atomicAdd(&S.c->ticket2, 1u) == (unsigned)(P.n_cells - 1);
+        }
+        __syncthreads();
+        if (last) {
+            // the last CTA of this system: group kinetic energies and the next factor
+            __threadfence();
+            double k0 = 0.0, k1 = 0.0;
+            for (int b = t; b < P.n_cells; b += PAIR_THREADS) { k0 += __ldcg(&S.ke_part[2 * b]); k1 += __ldcg(&S.ke_part[2 * b + 1]); }
+            ered[0][t] = k0;
+            ered[1][t] = k1;
+            __syncthreads();
+            for (int w = PAIR_THREADS / 2; w > 0; w >>= 1) {
+                if (t < w) { ered[0][t] += ered[0][t + w]; ered[1][t] += ered[1][t + w]; }
+                __syncthreads();
+            }
+            Counters &C = *S.c;
+            const int in_at = C.in_at;
+            const unsigned long long next = (in_at ? C.at_step : C.step) + 1;
+            const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
+            if ((t & 31) == 0 && t < 64) C.alpha[t >> 5] = alpha_for(S, P, C, t >> 5, ered[t >> 5][0], next, tag);
+            __syncthreads();
+            if (t == 0) {
+                if (in_at) C.at_step = next; else C.step = next;
+                C.md_steps++;
+                C.force_evals++;
+                C.ticket2 = 0;
             }
         }
     }
     if (ENERGY) {
+        __syncthreads();
         ered[0][t] = elj; ered[1][t] = erf; ered[2][t] = epairs;
         __syncthreads();
+        for (int w = PAIR_THREADS / 2; w > 0; w >>= 1) {
+            if (t < w) { ered[0][t] += ered[0][t + w]; ered[1][t] += ered[1][t + w]; ered[2][t] += ered[2][t + w]; }
+            __syncthreads();
+        }
         if (t == 0) {
-            double a = 0, b = 0, p = 0;
-            for (int k = 0; k < PAIR_THREADS; ++k) { a += ered[0][k]; b += ered[1][k]; p += ered[2][k]; }
-            S.epart[4 * c + 0] = a;
-            S.epart[4 * c + 1] = b;
-            S.epart[4 * c + 2] = p;
+            S.epart[4 * c + 0] = ered[0][0];
+            S.epart[4 * c + 1] = ered[1][0];
+            S.epart[4 * c + 2] = ered[2][0];
         }
     }
 }
 
 template <typename Real>
 static size_t pair_smem() {
-    static_assert(3 * PAIR_THREADS * sizeof(double) <= sizeof(uint16_t) * QCAP * PAIR_THREADS, "red fits in q");
+    static_assert(3 * PAIR_THREADS * sizeof(long long) <= sizeof(uint16_t) * QCAP * PAIR_THREADS, "red fits in q");
     return sizeof(StagedPos<Real>) * STAGE_CAP + sizeof(int4) * STAGE_CAP + sizeof(Real) * 3 * 256 +
            sizeof(uint16_t) * QCAP * PAIR_THREADS;
 }
 
-template <typename Real, bool LAM, bool ENERGY>
+template <typename Real, bool LAM, bool ENERGY, bool INTEG>
 static void pair_launch(const LaunchCtx &L) {
-    k_pair<Real, LAM, ENERGY><<<L.cells->n, PAIR_THREADS, pair_smem<Real>(), L.stream>>>(L.sys, L.cells->d);
+    k_pair<Real, LAM, ENERGY, INTEG><<<L.cells->n, PAIR_THREADS, pair_smem<Real>(), L.stream>>>(L.sys, L.cells->d);
 }
 
-template <typename Real, bool LAM, bool ENERGY>
+template <typename Real, bool LAM, bool ENERGY, bool INTEG>
 static cudaError_t pair_attr() {
-    return cudaFuncSetAttribute(k_pair<Real, LAM, ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_pair<Real, LAM, ENERGY, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pair_smem<Real>());
 }
 
@@ -519,210 +642,57 @@ static cudaError_t pair_attr() {
 cudaError_t setup_kernels() {
     static cudaError_t done = cudaErrorNotReady;
     if (done != cudaErrorNotReady) return done;
-    cudaError_t e = pair_attr<float, false, false>();
-    if (e == cudaSuccess) e = pair_attr<float, true, false>();
-    if (e == cudaSuccess) e = pair_attr<double, false, false>();
-    if (e == cudaSuccess) e = pair_attr<double, true, false>();
-    if (e == cudaSuccess) e = pair_attr<double, false, true>();
-    if (e == cudaSuccess) e = pair_attr<double, true, true>();
+    cudaError_t e = pair_attr<float, false, false, false>();
+    if (e == cudaSuccess) e = pair_attr<float, true, false, false>();
+    if (e == cudaSuccess) e = pair_attr<float, false, false, true>();
+    if (e == cudaSuccess) e = pair_attr<float, true, false, true>();
+    if (e == cudaSuccess) e = pair_attr<double, false, false, false>();
+    if (e == cudaSuccess) e = pair_attr<double, true, false, false>();
+    if (e == cudaSuccess) e = pair_attr<double, false, false, true>();
+    if (e == cudaSuccess) e = pair_attr<double, true, false, true>();
+    if (e == cudaSuccess) e = pair_attr<double, false, true, false>();
+    if (e == cudaSuccess) e = pair_attr<double, true, true, false>();
     done = e;
     return e;
 }
 
+// forces only (fixed point, pair + bonded) or energies
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64) {
     if (energy) {
-        if (lambda) pair_launch<double, true, true>(L); else pair_launch<double, false, true>(L);
+        if (lambda) pair_launch<double, true, true, false>(L); else pair_launch<double, false, true, false>(L);
     } else if (fp64) {
-        if (lambda) pair_launch<double, true, false>(L); else pair_launch<double, false, false>(L);
+        if (lambda) pair_launch<double, true, false, false>(L); else pair_launch<double, false, false, false>(L);
     } else {
-        if (lambda) pair_launch<float, true, false>(L); else pair_launch<float, false, false>(L);
+        if (lambda) pair_launch<float, true, false, false>(L); else pair_launch<float, false, false, false>(L);
     }
 }
 
-// ---------------------------------------------------------- bonded terms
-// Separation r_a - r_b of two beads (exact integer minimum image).
-template <typename Real>
-__device__ __forceinline__ void sep(const Params &P, uint4 a, uint4 b, Real d[3]) {
-    if (sizeof(Real) == 4) {
-        d[0] = (Real)((float)(int)(a.x - b.x) * P.qsf[0]);
-        d[1] = (Real)((float)(int)(a.y - b.y) * P.qsf[1]);
-        d[2] = (Real)((float)(int)(a.z - b.z) * P.qsf[2]);
+// one whole MD step (after the cell list of the current positions is built)
+void launch_step(const LaunchCtx &L, bool lambda) {
+    if (L.precision == 1) {
+        if (lambda) pair_launch<double, true, false, true>(L); else pair_launch<double, false, false, true>(L);
     } else {
-        d[0] = (Real)((double)(int)(a.x - b.x) * P.qs[0]);
-        d[1] = (Real)((double)(int)(a.y - b.y) * P.qs[1]);
-        d[2] = (Real)((double)(int)(a.z - b.z) * P.qs[2]);
+        if (lambda) pair_launch<float, true, false, true>(L); else pair_launch<float, false, false, true>(L);
     }
 }
 
-// Bonded force on bead i (local index k of lipid l): harmonic bonds to its
-// partners and the cosine-angle terms of every angle containing it.
-template <typename Real>
-__device__ void bonded_force(const Params &P, const uint4 *__restrict__ pos, int i, int l, int k, uint4 pi, Real f[3]) {
-    const int base = l * P.bpl;
-    for (int b = 0; b < P.nbond[k]; ++b) {
-        const int j = base + P.bpart[k][b];
-        Real d[3];
-        sep<Real>(P, pi, pos[j], d);
-        const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
-        f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
-    }
-    for (int a = 0; a < P.nang[k]; ++a) {
-        const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
-        const uint4 qi = pos[base + li], qj = pos[base + lj], qk = pos[base + lk];
-        Real A[3], B[3];
-        sep<Real>(P, qi, qj, A);
-        sep<Real>(P, qk, qj, B);
-        const Real la2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
-        const Real lb2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-        const Real iab = (Real)1 / sqrt(la2 * lb2);
-        const Real cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * iab;
-        const Real pre = -(Real)P.kth * (cs - (Real)P.cos0);
-        for (int d = 0; d < 3; ++d) {
-            const Real dci = B[d] * iab - cs * A[d] / la2;
-            const Real dck = A[d] * iab - cs * B[d] / lb2;
-            Real g;
-            if (k == li) g = dci;
-            else if (k == lk) g = dck;
-            else g = -(dci + dck);
-            f[d] += pre * g;
-        }
-    }
-}
-
-// ------------------------------------------------------------- integrator
-// v <- alpha_g v + F/m dt ; x <- x + v dt rounded to the fixed-point grid
-// (in the velocity's precision); then the bead is counted into its new cell
-// for the next cell-list build, and the per-block kinetic energy of each
-// group is stored for the next thermostat.
-template <typename Real>
-__global__ void __launch_bounds__(BEAD_BLOCK) k_integrate(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    using V4 = typename Vec4<Real>::T;
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
-    const Params &P = *S.p;
-    const int i = bm.y + threadIdx.x;
-    Real ke[2] = {(Real)0, (Real)0};
-    if (i < P.n) {
-        uint4 pi = S.pos[i];
-        const uint32_t m = pi.w;
-        const int l = meta_lip(m), k = meta_k(m);
-        const Real sc = (Real)(1.0 / FIX);
-        Real f[3] = {(Real)S.fx[i] * sc, (Real)S.fy[i] * sc, (Real)S.fz[i] * sc};
-        if (l >= 0) bonded_force<Real>(P, S.pos, i, l, k, pi, f);
-        const int g = i < P.n_lipid_beads ? 0 : 1;
-        const Real a = (Real)S.c->alpha[g];
-        const Real dtm = (Real)P.dt_over_m;
-        V4 *vel = reinterpret_cast<V4 *>(S.vel);
-        V4 v = vel[i];
-        v.x = a * v.x + f[0] * dtm;
-        v.y = a * v.y + f[1] * dtm;
-        v.z = a * v.z + f[2] * dtm;
-        vel[i] = v;
-        if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&S.c->err, ERR_NONFINITE);
-        if (sizeof(Real) == 4) {
-            pi.x += (uint32_t)__float2int_rn((float)v.x * P.qdtf[0]);
-            pi.y += (uint32_t)__float2int_rn((float)v.y * P.qdtf[1]);
-            pi.z += (uint32_t)__float2int_rn((float)v.z * P.qdtf[2]);
-        } else {
-            pi.x += (uint32_t)(long long)rint((double)v.x * P.qdt[0]);
-            pi.y += (uint32_t)(long long)rint((double)v.y * P.qdt[1]);
-            pi.z += (uint32_t)(long long)rint((double)v.z * P.qdt[2]);
-        }
-        S.pos[i] = pi;
-        const int cx = (int)(((unsigned long long)pi.x * (unsigned)P.nc[0]) >> 32);
-        const int cy = (int)(((unsigned long long)pi.y * (unsigned)P.nc[1]) >> 32);
-        const int cz = (int)(((unsigned long long)pi.z * (unsigned)P.nc[2]) >> 32);
-        const int c = (cz * P.nc[1] + cy) * P.nc[0] + cx;
-        S.cell_of[i] = c;
-        S.cell_slot[i] = atomicAdd(&S.cell_count[c], 1);
-        ke[g] = (Real)0.5 * (Real)P.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
-    }
-    // fixed-order reduction: warp trees in the velocity's precision, warps in FP64
-    __shared__ double part[2][BEAD_BLOCK / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        Real v = ke[g];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[g][wid] = (double)v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double s = 0.0;
-        for (int w = 0; w < BEAD_BLOCK / 32; ++w) s += part[threadIdx.x][w];
-        S.ke_part[2 * (bm.y / BEAD_BLOCK) + threadIdx.x] = s;
-    }
-}
-
-// Kinetic energy partials for the thermostat from the current velocities,
-// reduced exactly as the integrator reduces them.
-template <typename Real>
-__global__ void __launch_bounds__(BEAD_BLOCK) k_kinetic(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    using V4 = typename Vec4<Real>::T;
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
-    const Params &P = *S.p;
-    const int i = bm.y + threadIdx.x;
-    Real ke[2] = {(Real)0, (Real)0};
-    if (i < P.n) {
-        const V4 v = reinterpret_cast<const V4 *>(S.vel)[i];
-        ke[i < P.n_lipid_beads ? 0 : 1] = (Real)0.5 * (Real)P.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
-    }
-    __shared__ double part[2][BEAD_BLOCK / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        Real v = ke[g];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[g][wid] = (double)v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double s = 0.0;
-        for (int w = 0; w < BEAD_BLOCK / 32; ++w) s += part[threadIdx.x][w];
-        S.ke_part[2 * (bm.y / BEAD_BLOCK) + threadIdx.x] = s;
-    }
-}
-
-void launch_integrate(const LaunchCtx &L) {
-    if (L.precision == 1) k_integrate<double><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-    else k_integrate<float><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-}
-
-void launch_kinetic(const LaunchCtx &L) {
-    if (L.precision == 1) k_kinetic<double><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-    else k_kinetic<float><<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-}
-
-// total force of one system (pair + bonded), as double, for the host
-template <typename Real>
+// total force of one system (fixed point) as double, for the host
 __global__ void k_total_force(const SysDev *__restrict__ sys, int si, double *__restrict__ out) {
     const SysDev &S = sys[si];
-    const Params &P = *S.p;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    const uint4 pi = S.pos[i];
-    const Real sc = (Real)(1.0 / FIX);
-    Real f[3] = {(Real)S.fx[i] * sc, (Real)S.fy[i] * sc, (Real)S.fz[i] * sc};
-    const int l = meta_lip(pi.w);
-    if (l >= 0) bonded_force<Real>(P, S.pos, i, l, meta_k(pi.w), pi, f);
-    out[3 * i] = (double)f[0];
-    out[3 * i + 1] = (double)f[1];
-    out[3 * i + 2] = (double)f[2];
+    if (i >= S.p->n) return;
+    out[3 * i] = (double)S.fx[i] * (1.0 / FIX);
+    out[3 * i + 1] = (double)S.fy[i] * (1.0 / FIX);
+    out[3 * i + 2] = (double)S.fz[i] * (1.0 / FIX);
 }
 
 void launch_total_force(const LaunchCtx &L, double *out, int si) {
-    // n of the system is read on the device; the grid covers the largest system
-    const int blocks = L.max_bead_blocks;
-    if (L.precision == 1) k_total_force<double><<<blocks, BEAD_BLOCK, 0, L.stream>>>(L.sys, si, out);
-    else k_total_force<float><<<blocks, BEAD_BLOCK, 0, L.stream>>>(L.sys, si, out);
+    k_total_force<<<L.max_bead_blocks, BEAD_BLOCK, 0, L.stream>>>(L.sys, si, out);
 }
 
 // ------------------------------------------------------- FP64 energies
-// Bond energy counted once by the lower-index bead, angle energy by the vertex.
+// Bond energy counted once by the lower-index bead, angle energy by the
+// vertex, and the exact kinetic energy, per bead; fixed-order block trees.
 __global__ void __launch_bounds__(BEAD_BLOCK) k_bonded_energy(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     const int2 bm = bmap[blockIdx.x];
     const SysDev &S = sys[bm.x];
@@ -766,7 +736,7 @@ __global__ void __launch_bounds__(BEAD_BLOCK) k_bonded_energy(const SysDev *__re
     part[1][threadIdx.x] = ea;
     part[2][threadIdx.x] = ek;
     __syncthreads();
-    for (int w = BEAD_BLOCK / 2; w > 0; w >>= 1) {   // fixed-order tree
+    for (int w = BEAD_BLOCK / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
             for (int q = 0; q < 3; ++q) part[q][threadIdx.x] += part[q][threadIdx.x + w];
         __syncthreads();

@@ -27,7 +27,7 @@ constexpr double BOLTZ = 0.0083144626;
 constexpr double COUL = 138.935458;
 
 enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5 };
-enum : int { ERR_NONFINITE = 1, ERR_STAGE_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8 };
+enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8 };
 
 // Per-bead meta word carried in the 4th lane of every position:
 // bits 0-3 current bead type (A), 4-7 alchemical target type (B),
@@ -43,7 +43,7 @@ __host__ __device__ inline int meta_lip(uint32_t m) { return (int)(m >> 12) - 1;
 // Constant parameters of one system (device memory, read-only in kernels).
 struct Params {
     int n, n_lip, bpl, n_bt, n_lt, n_lipid_beads;
-    int nc[3], n_cells;
+    int nc[3], n_cells, capc;          // cells per edge, cells, bead capacity of a cell
     double box[3], qs[3], qdt[3];      // qs = L/2^32; qdt = dt 2^32 / L
     float qsf[3], qsh[3], qsl[3];      // L/2^32 as float, and as a float pair hi + lo
     double rc, rc2, krf, crf;
@@ -86,6 +86,7 @@ struct Counters {
     unsigned long long draw_base;      // thermostat variates precomputed for counters
     int draw_n, draw_tag;              // [draw_base, draw_base + draw_n) of stream draw_tag
     unsigned int ticket;               // last-block ticket of the fused single trial
+    unsigned int ticket2;              // last-block ticket of the step kernel
 };
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
@@ -98,9 +99,13 @@ struct SysDev {
     void *vel;                         // float4 or double4 per bead
     long long *fx, *fy, *fz;           // pair forces, fixed point
     int *ltype;                        // [n_lip]
-    int *cell_of, *cell_slot, *cell_count, *cell_start, *tmp_ids, *sorted_id, *sidx;
-    uint4 *spos;                       // positions in cell order
-    double *ke_part;                   // [n_bead_blocks * 2]
+    int *cell_count;                   // [n_cells] beads counted into each cell for the next list
+    int *cell_n;                       // [n_cells] beads in each cell of the current list
+    int *tmp_ids;                      // [n_cells * capc] ids as counted (unordered)
+    int *sorted_id;                    // [n_cells * capc] ids in cell order (ascending within a cell)
+    int *sidx;                         // [n] position of a bead in the cell list
+    uint4 *spos;                       // [n_cells * capc] positions in cell order
+    double *ke_part;                   // [n_cells * 2] kinetic energy per cell and group
     double *epart;                     // [n_cells * 4] lj, rf, pairs, (unused)
     double *bpart;                     // [n_bead_blocks * 3] bond, angle, kinetic energies (FP64)
     uint4 *pos_snap;
@@ -172,8 +177,7 @@ void launch_thermostat(const LaunchCtx &L);
 void launch_thermo_draws(const LaunchCtx &L, int n_steps);
 void launch_trial_one(const LaunchCtx &L);
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64);
-void launch_integrate(const LaunchCtx &L);
-void launch_kinetic(const LaunchCtx &L);
+void launch_step(const LaunchCtx &L, bool lambda);
 void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
 void launch_energy_reduce(const LaunchCtx &L);
 

@@ -50,8 +50,8 @@ __device__ double bead_delta(const SysDev &S, const Params &P, int i, uint4 pi, 
     const int li = meta_lip(pi.w), ki = meta_k(pi.w);
     const uint32_t em = P.excl[ki];
     double acc = 0.0;
-    const int e = S.cell_start[cj + 1];
-    for (int p = S.cell_start[cj]; p < e; ++p) {
+    const int e = cj * P.capc + S.cell_n[cj];
+    for (int p = cj * P.capc; p < e; ++p) {
         const uint4 pj = S.spos[p];
         const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
         const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
@@ -242,23 +242,29 @@ __device__ void set_lipid_type(const SysDev &S, const Params &P, int l, int lt) 
 }
 
 // One exchange trial per system, whole: grid (9, n_sys).  Every CTA draws the
-// proposal of trial C.trial, sums the dE over its 3 neighbour cells, and the
-// last CTA to finish (a ticket, no waiting) adds the 9 partial sums in order,
-// takes the Metropolis decision and applies it.  Equal to one sequential
-// trial; used when trials come one at a time (one after every MD step).
+// proposal of trial C.trial and sums the dE over its 3 neighbour cells of
+// every changed bead, one candidate bead per thread (a flat list), so the
+// FP64 work of the in-cutoff pairs is spread over the block; the last CTA to
+// finish (a ticket, no waiting) adds the 9 partial sums in order, takes the
+// Metropolis decision and applies it.  Equal to one sequential trial; used
+// when trials come one at a time (one after every MD step).
 __global__ void __launch_bounds__(128) k_trial_one(const SysDev *__restrict__ sys) {
     const SysDev &S = sys[blockIdx.y];
     const Params &P = *S.p;
     Counters &C = *S.c;
     const int grp = blockIdx.x;
     __shared__ double sh[128];
+    __shared__ int it_beg[6 * MAXT + 1], it_cell[6 * MAXT];
     __shared__ int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT];
+    __shared__ uint4 chg_pos[2 * MAXT];
     __shared__ int nchg, kmask, last;
+    __shared__ double lnu;
     const unsigned long long T = C.trial;
     const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
     const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
     const int ta = S.ltype[a], tb = S.ltype[b];
     const bool null_trial = (a == b) || (ta == tb);
+    if (threadIdx.x == 32) lnu = log(unit53(w.z, w.w));   // off the critical path
     if (threadIdx.x == 0) {
         int m = 0, nc = 0;
         if (!null_trial) {
@@ -278,19 +284,51 @@ __global__ void __launch_bounds__(128) k_trial_one(const SysDev *__restrict__ sy
     }
     __syncthreads();
     const int nc = nchg, m = kmask;
-    auto changed = [&](uint32_t mj, int) {
-        const int l = meta_lip(mj);
-        return (l == a || l == b) && ((m >> meta_k(mj)) & 1);
-    };
-    auto newt = [&](uint32_t mj, int) {
-        const int l = meta_lip(mj);
-        return (int)P.lbt[(l == a ? tb : ta) * 16 + meta_k(mj)];
-    };
+    // items (changed bead, one of this group's 3 cells) and their bead ranges
+    const int nx = P.nc[0], ny = P.nc[1], nz = P.nc[2];
+    if (threadIdx.x < nc * 3) {
+        const int ci = threadIdx.x / 3, slot = grp * 3 + threadIdx.x % 3;
+        const uint4 pi = S.pos[chg_id[ci]];
+        if (threadIdx.x % 3 == 0) chg_pos[ci] = pi;
+        const int cx = (int)(((unsigned long long)pi.x * (unsigned)nx) >> 32);
+        const int cy = (int)(((unsigned long long)pi.y * (unsigned)ny) >> 32);
+        const int cz = (int)(((unsigned long long)pi.z * (unsigned)nz) >> 32);
+        const int dz = slot / 9 - 1, dy = (slot / 3) % 3 - 1, dx = slot % 3 - 1;
+        const int x = (cx + dx + nx) % nx, y = (cy + dy + ny) % ny, z = (cz + dz + nz) % nz;
+        const int cj = (z * ny + y) * nx + x;
+        it_cell[threadIdx.x] = cj;
+        it_beg[threadIdx.x + 1] = S.cell_n[cj];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        it_beg[0] = 0;
+        for (int k = 0; k < nc * 3; ++k) it_beg[k + 1] += it_beg[k];
+    }
+    __syncthreads();
+    const int total = nc > 0 ? it_beg[nc * 3] : 0;
     double acc = 0.0;
-    for (int it = threadIdx.x; it < nc * 3; it += blockDim.x) {
-        const int ci = it / 3, slot = grp * 3 + it % 3;
+    for (int f = threadIdx.x; f < total; f += blockDim.x) {
+        int it = 0;
+        while (f >= it_beg[it + 1]) ++it;
+        const int ci = it / 3;
+        const int p = it_cell[it] * P.capc + (f - it_beg[it]);
         const int i = chg_id[ci];
-        acc += bead_delta(S, P, i, S.pos[i], chg_old[ci], chg_new[ci], slot, newt, changed);
+        const uint4 pi = chg_pos[ci], pj = S.spos[p];
+        const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
+        const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
+        const float r2f = fx * fx + fy * fy + fz * fz;
+        if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
+        const int j = S.sorted_id[p];
+        const int lj = meta_lip(pj.w), kj = meta_k(pj.w);
+        const bool chj = (lj == a || lj == b) && ((m >> kj) & 1);
+        if (j == i || (chj && j < i)) continue;
+        if (lj >= 0 && lj == meta_lip(pi.w) && ((P.excl[meta_k(pi.w)] >> kj) & 1u)) continue;
+        const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 >= P.rc2) continue;
+        const int old_j = meta_ta(pj.w);
+        const int new_j = chj ? (int)P.lbt[(lj == a ? tb : ta) * 16 + kj] : old_j;
+        acc += pair_du(P, chg_old[ci], old_j, chg_new[ci], new_j, r2);
     }
     const double part = block_sum(acc, sh);
     if (threadIdx.x == 0) {
@@ -308,7 +346,7 @@ __global__ void __launch_bounds__(128) k_trial_one(const SysDev *__restrict__ sy
     r.null_trial = null_trial;
     if (!null_trial) {
         r.dE = dE;
-        if (dE + P.kT * log(r.u) <= 0.0) {
+        if (dE + P.kT * lnu <= 0.0) {
             set_lipid_type(S, P, a, tb);
             set_lipid_type(S, P, b, ta);
             r.accepted = 1;
