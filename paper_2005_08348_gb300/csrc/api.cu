@@ -60,8 +60,6 @@ struct mdas_system {
     bool unstable = false;
     bool cells_valid = false;   // the cell list matches the current positions and types
     bool counted = false;       // cell_count holds the step kernel's counts of the current positions
-    bool alpha_ready = false;   // the thermostat factor of the next step is computed
-    int alpha_domain = 0;       // ... for plain MD (0) or the alchemical trajectory (1)
     bool timing = false;
     double pair_ms = 0.0;
     long long pair_launches = 0;
@@ -149,6 +147,7 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
         for (int i = 0; i < x->n; i += BEAD_BLOCK) beads.push_back(make_int2(k, i));
         for (int c = 0; c < x->hp.n_cells; ++c) cells.push_back(make_int2(k, c));
         for (int c = 0; c < x->hp.n_cells; c += CELLS_PER_SORT_BLOCK) sortcells.push_back(make_int2(k, c));
+        sortcells.push_back(make_int2(k, -1));   // the system's thermostat block
         syss.push_back(make_int2(k, 0));
         b->max_bead_blocks = std::max(b->max_bead_blocks, (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK);
     }
@@ -199,20 +198,6 @@ void md_step_launches(const Batch &b, bool lambda, bool counted) {
     LaunchCtx L = b.ctx();
     launch_cells(L, counted);
     launch_step(L, lambda);
-}
-
-// The step kernel leaves the factor of the next step behind; after a state
-// change (or a switch between plain MD and the alchemical trajectory) it is
-// computed from the velocities, per system so batching never changes results.
-mdas_status ensure_alpha(mdas_system *s, Batch &b, int domain) {
-    for (auto *x : b.sys)
-        if (!x->alpha_ready || x->alpha_domain != domain) {
-            launch_thermostat(x->solo->ctx());
-            x->alpha_ready = true;
-            x->alpha_domain = domain;
-        }
-    CK(cudaGetLastError());
-    return MDAS_OK;
 }
 
 __global__ void k_batch_status(const SysDev *__restrict__ sys, int n, int *out) {
@@ -339,8 +324,6 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
     bool counted;
     mdas_status st = sync_counted(s, b, &counted);
-    if (st != MDAS_OK) return st;
-    st = ensure_alpha(s, b, lambda ? 1 : 0);
     if (st != MDAS_OK) return st;
     if (n_units > 0) {
         bool reuse = false;
@@ -793,9 +776,7 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
             launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
             if (md_per_lambda > 0) {
                 GraphEntry *ge;
-                mdas_status st = ensure_alpha(s, b, 1);
-                if (st != MDAS_OK) return st;
-                st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, s->counted, &ge);
+                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, s->counted, &ge);
                 if (st != MDAS_OK) return st;
                 st = replay(s, b, ge);
                 if (st != MDAS_OK) return st;
@@ -809,7 +790,6 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
     launch_mdas_accept(L);
     launch_mdas_restore(L);
     s->cells_valid = false;
-    s->alpha_ready = false;
     Counters c;
     double r[10];
     CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
@@ -941,11 +921,10 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     c.step = in->step; c.trial = in->trial; c.move = in->move; c.at_step = in->at_step;
-    c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0;
+    c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0; c.ke_fresh = 0; c.draw_n = 0;
     CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
     if (s->counted) CK(cudaMemsetAsync(s->hs.cell_count, 0, 4ull * s->hp.n_cells, s->stream));
     s->counted = false;
-    s->alpha_ready = false;
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
     s->unstable = false;

@@ -10,10 +10,10 @@
 // advance one system or a whole batch of them.
 //
 // One MD step is two launches: the cell-list finish (per-cell ordering of the
-// beads the previous step counted into fixed-capacity cells) and the fused
-// step kernel (pair forces, bonded forces, leapfrog update, counting into the
-// next step's cells; the last CTA of each system then computes the next
-// step's thermostat factor).
+// beads the previous step counted into fixed-capacity cells, plus one block
+// per system computing the step's thermostat factor) and the fused step
+// kernel (pair forces, bonded forces, leapfrog update, counting into the next
+// step's cells).
 #include <cmath>
 #include <cstdio>
 
@@ -57,24 +57,24 @@ __global__ void k_cell_count(const SysDev *__restrict__ sys, const int2 *__restr
 }
 
 // One warp per cell: order the cell's beads by id (rank = number of smaller
-// ids in the cell), gather their positions into cell order, publish the
-// count and clear the counter for the next step.
-__global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
-    const Params &P = *S.p;
-    const int c = bm.y + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (c >= P.n_cells) return;
+// ids in the cell, computed with warp shuffles), gather their positions into
+// cell order, publish the count and clear the counter for the next step.
+__device__ void finish_cell(const SysDev &S, const Params &P, int c, int lane) {
     const int cnt = min(S.cell_count[c], P.capc);
     const int base = c * P.capc;
-    for (int a = lane; a < cnt; a += 32) {
-        const int id = S.tmp_ids[base + a];
+    for (int a0 = 0; a0 < cnt; a0 += 32) {
+        const int a = a0 + lane;
+        const int id = a < cnt ? S.tmp_ids[base + a] : 0x7fffffff;
         int rank = 0;
-        for (int b = 0; b < cnt; ++b) rank += (S.tmp_ids[base + b] < id);
-        S.sorted_id[base + rank] = id;
-        S.sidx[id] = base + rank;
-        S.spos[base + rank] = S.pos[id];
+        for (int b0 = 0; b0 < cnt; b0 += 32) {
+            const int other = b0 + lane < cnt ? S.tmp_ids[base + b0 + lane] : 0x7fffffff;
+            for (int k = 0; k < 32; ++k) rank += __shfl_sync(0xffffffffu, other, k) < id;
+        }
+        if (a < cnt) {
+            S.sorted_id[base + rank] = id;
+            S.sidx[id] = base + rank;
+            S.spos[base + rank] = S.pos[id];
+        }
     }
     __syncwarp();
     if (lane == 0) {
@@ -83,10 +83,31 @@ __global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__rest
     }
 }
 
+template <typename Real>
+__device__ void thermostat_block(const SysDev &S, const Params &P);
+
+template <typename Real>
+__global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    const Params &P = *S.p;
+    if (bm.y < 0) {                              // the system's thermostat block
+        thermostat_block<Real>(S, P);
+        return;
+    }
+    const int c = bm.y + (threadIdx.x >> 5);
+    if (c < P.n_cells) finish_cell(S, P, c, threadIdx.x & 31);
+}
+
 // counted: the step kernel has already counted the current positions into cells
+// (the finish grid carries one extra block per system that sets the
+// thermostat factor of the coming step)
 void launch_cells(const LaunchCtx &L, bool counted) {
     if (!counted) k_cell_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-    k_cell_finish<<<L.sortcells->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.sortcells->d);
+    if (L.precision == 1)
+        k_cell_finish<double><<<L.sortcells->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.sortcells->d);
+    else
+        k_cell_finish<float><<<L.sortcells->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.sortcells->d);
 }
 
 // ------------------------------------------------------------ thermostat
@@ -180,28 +201,31 @@ void launch_thermo_draws(const LaunchCtx &L, int n) {
     k_thermo_draws<<<g, 64, 0, L.stream>>>(L.sys, n);
 }
 
-// Thermostat factor of the next step straight from the velocities (after the
-// state was set or the counter domain changed); one block per system, a
-// fixed-order reduction (thread-strided sums, then a tree).
+// Thermostat factor of the coming step (counter C.step, or C.at_step on the
+// alchemical trajectory): group kinetic energies from the per-cell partials
+// the last step kernel left (ke_fresh), else straight from the velocities;
+// fixed-order reductions (thread-strided sums, then a tree).
 template <typename Real>
-__global__ void __launch_bounds__(256) k_thermostat(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+__device__ void thermostat_block(const SysDev &S, const Params &P) {
     using V4 = typename Vec4<Real>::T;
-    const SysDev &S = sys[bmap[blockIdx.x].x];
-    const Params &P = *S.p;
     Counters &C = *S.c;
-    const int t = threadIdx.x;
-    __shared__ double ks[2][256];
+    const int t = threadIdx.x, T = blockDim.x;
+    __shared__ double ks[2][32 * CELLS_PER_SORT_BLOCK];
     double k0 = 0.0, k1 = 0.0;
-    const V4 *vel = reinterpret_cast<const V4 *>(S.vel);
-    for (int i = t; i < P.n; i += 256) {
-        const V4 v = vel[i];
-        const double e = 0.5 * P.mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
-        if (i < P.n_lipid_beads) k0 += e; else k1 += e;
+    if (C.ke_fresh) {
+        for (int b = t; b < P.n_cells; b += T) { k0 += S.ke_part[2 * b]; k1 += S.ke_part[2 * b + 1]; }
+    } else {
+        const V4 *vel = reinterpret_cast<const V4 *>(S.vel);
+        for (int i = t; i < P.n; i += T) {
+            const V4 v = vel[i];
+            const double e = 0.5 * P.mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+            if (i < P.n_lipid_beads) k0 += e; else k1 += e;
+        }
     }
     ks[0][t] = k0;
     ks[1][t] = k1;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
+    for (int w = T / 2; w > 0; w >>= 1) {
         if (t < w) { ks[0][t] += ks[0][t + w]; ks[1][t] += ks[1][t + w]; }
         __syncthreads();
     }
@@ -212,11 +236,6 @@ __global__ void __launch_bounds__(256) k_thermostat(const SysDev *__restrict__ s
         const int g = t >> 5;
         C.alpha[g] = alpha_for(S, P, C, g, ks[g][0], ctr, tag);
     }
-}
-
-void launch_thermostat(const LaunchCtx &L) {
-    if (L.precision == 1) k_thermostat<double><<<L.syss->n, 256, 0, L.stream>>>(L.sys, L.syss->d);
-    else k_thermostat<float><<<L.syss->n, 256, 0, L.stream>>>(L.sys, L.syss->d);
 }
 
 // ---------------------------------------------------------- bonded terms
@@ -234,43 +253,44 @@ __device__ __forceinline__ void sep(const Params &P, uint4 a, uint4 b, Real d[3]
     }
 }
 
-// Bonded force on bead i (local index k of lipid l): harmonic bonds to its
-// partners and the cosine-angle terms of every angle containing it.
-// Positions come from the cell-ordered copy (stable during a step).
+// Bonded force on bead i (local index k of lipid l) from term `term` of its
+// terms: its bonds (harmonic, to each partner) first, then every angle
+// containing it (cosine-harmonic).  Positions come from the cell-ordered
+// copy (stable during a step).
 template <typename Real>
-__device__ void bonded_force(const SysDev &S, const Params &P, int l, int k, uint4 pi, Real f[3]) {
+__device__ void bonded_term(const SysDev &S, const Params &P, int l, int k, uint4 pi, int term, Real f[3]) {
     const int base = l * P.bpl;
-    for (int b = 0; b < P.nbond[k]; ++b) {
-        const uint4 pj = S.spos[S.sidx[base + P.bpart[k][b]]];
+    if (term < P.nbond[k]) {
+        const uint4 pj = S.spos[S.sidx[base + P.bpart[k][term]]];
         Real d[3];
         sep<Real>(P, pi, pj, d);
         const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
         f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
+        return;
     }
-    for (int a = 0; a < P.nang[k]; ++a) {
-        const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
-        const uint4 qi = li == k ? pi : S.spos[S.sidx[base + li]];
-        const uint4 qj = lj == k ? pi : S.spos[S.sidx[base + lj]];
-        const uint4 qk = lk == k ? pi : S.spos[S.sidx[base + lk]];
-        Real A[3], B[3];
-        sep<Real>(P, qi, qj, A);
-        sep<Real>(P, qk, qj, B);
-        const Real la2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
-        const Real lb2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-        const Real iab = (Real)1 / sqrt(la2 * lb2);
-        const Real cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * iab;
-        const Real pre = -(Real)P.kth * (cs - (Real)P.cos0);
-        const Real ia2 = (Real)1 / la2, ib2 = (Real)1 / lb2;
-        for (int d = 0; d < 3; ++d) {
-            const Real dci = B[d] * iab - cs * A[d] * ia2;
-            const Real dck = A[d] * iab - cs * B[d] * ib2;
-            Real g;
-            if (k == li) g = dci;
-            else if (k == lk) g = dck;
-            else g = -(dci + dck);
-            f[d] += pre * g;
-        }
+    const int a = term - P.nbond[k];
+    const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
+    const uint4 qi = li == k ? pi : S.spos[S.sidx[base + li]];
+    const uint4 qj = lj == k ? pi : S.spos[S.sidx[base + lj]];
+    const uint4 qk = lk == k ? pi : S.spos[S.sidx[base + lk]];
+    Real A[3], B[3];
+    sep<Real>(P, qi, qj, A);
+    sep<Real>(P, qk, qj, B);
+    const Real la2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+    const Real lb2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const Real iab = (Real)1 / sqrt(la2 * lb2);
+    const Real cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * iab;
+    const Real pre = -(Real)P.kth * (cs - (Real)P.cos0);
+    const Real ia2 = (Real)1 / la2, ib2 = (Real)1 / lb2;
+    for (int d = 0; d < 3; ++d) {
+        const Real dci = B[d] * iab - cs * A[d] * ia2;
+        const Real dck = A[d] * iab - cs * B[d] * ib2;
+        Real g;
+        if (k == li) g = dci;
+        else if (k == lk) g = dck;
+        else g = -(dci + dck);
+        f[d] += pre * g;
     }
 }
 
@@ -288,12 +308,12 @@ __device__ void bonded_force(const SysDev &S, const Params &P, int l, int k, uin
 // roundings.  Stream partials are summed in 64-bit fixed point.  Every pair is
 // evaluated from both sides (no atomics on the j bead).
 //
-// INTEG: the step kernel.  Each bead's thread then adds its bonded force and
-// applies the leapfrog update with the thermostat factor, writes the new
+// The bonded terms of each i-bead are computed by its stream threads first
+// and join the stream partials.  INTEG: the step kernel; each bead's thread
+// then applies the leapfrog update with the thermostat factor, writes the new
 // position and velocity, counts the bead into the next step's cells and
-// contributes to its cell's kinetic-energy partial; the last CTA of a system
-// reduces those partials and sets the next step's factor.  Otherwise the total
-// force is stored in fixed point.
+// contributes to its cell's kinetic-energy partial.  Otherwise the total force
+// is stored in fixed point.
 
 // a - b of two frame offsets, wrapped to 32 bits (the minimum image)
 __device__ __forceinline__ int wrap_diff(int a, int b) { return (int)((uint32_t)a - (uint32_t)b); }
@@ -348,8 +368,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     __shared__ int cst[27], ccnt[27], coff[28];
     __shared__ double ered[3][PAIR_THREADS];
     __shared__ Real kered[2][PAIR_THREADS];
-    __shared__ int last;
-
     for (int k = t; k < 256; k += PAIR_THREADS) {
         if (F32) {
             tf12[k] = (Real)P.f12f[k]; tf6[k] = (Real)P.f6f[k]; tqq[k] = (Real)P.qqf[k];
@@ -403,6 +421,23 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         const uint32_t lipi = mi >> 12;
         const uint32_t emask = P.excl[ki];
         Real ax = 0, ay = 0, az = 0;
+        // bonded terms of bead i, spread over its streams (they join the
+        // stream partials below)
+        if (valid && lipi != 0) {
+            const int nt = P.nbond[ki] + P.nang[ki];
+            for (int term = js; term < nt; term += NS) {
+                Real fb[3] = {ax, ay, az};
+                bonded_term<Real>(S, P, (int)lipi - 1, ki, vi, term, fb);
+                ax = fb[0]; ay = fb[1]; az = fb[2];
+            }
+        }
+        // the updating thread (stream 0) fetches the bead's velocity early
+        V4 vpre;
+        int idpre = 0;
+        if (INTEG && js == 0 && i < ni) {
+            idpre = S.sorted_id[ifirst + i];
+            vpre = reinterpret_cast<const V4 *>(S.vel)[idpre];
+        }
 
         auto flush = [&](int count) {
             for (int e = 0; e < count; ++e) {
@@ -524,24 +559,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
                 Fz += red[2 * PAIR_THREADS + s * IW + t];
             }
             const int p = ifirst + ib + t;
-            const int id = S.sorted_id[p];
-            const uint4 pu = S.spos[p];
-            const int l = meta_lip(pu.w);
-            if (l >= 0) {
-                Real fb[3] = {(Real)0, (Real)0, (Real)0};
-                bonded_force<Real>(S, P, l, meta_k(pu.w), pu, fb);
-                Fx += to_fix(fb[0]); Fy += to_fix(fb[1]); Fz += to_fix(fb[2]);
-            }
+            const uint4 pu = vi;                 // this thread is (i = ib + t, stream 0)
             if (!INTEG) {
+                const int id = S.sorted_id[p];
                 S.fx[id] = Fx; S.fy[id] = Fy; S.fz[id] = Fz;
             } else {
+                const int id = idpre;
                 const Real sc = (Real)(1.0 / FIX);
                 const Real f0 = (Real)Fx * sc, f1 = (Real)Fy * sc, f2 = (Real)Fz * sc;
                 const int g = id < P.n_lipid_beads ? 0 : 1;
                 const Real a = (Real)S.c->alpha[g];
                 const Real dtm = (Real)P.dt_over_m;
                 V4 *vel = reinterpret_cast<V4 *>(S.vel);
-                V4 v = vel[id];
+                V4 v = vpre;
                 v.x = a * v.x + f0 * dtm;
                 v.y = a * v.y + f1 * dtm;
                 v.z = a * v.z + f2 * dtm;
@@ -565,7 +595,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
         }
     }
     if (INTEG) {
-        // this cell's kinetic-energy partials (fixed order), then the ticket
+        // this cell's kinetic-energy partials (fixed order)
         kered[0][t] = ke0;
         kered[1][t] = ke1;
         __syncthreads();
@@ -574,33 +604,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
             for (int k = 0; k < (ni < PAIR_THREADS ? ni : PAIR_THREADS); ++k) { a0 += kered[0][k]; a1 += kered[1][k]; }
             S.ke_part[2 * c] = (double)a0;
             S.ke_part[2 * c + 1] = (double)a1;
-            __threadfence();
-            last = atomicAdd(&S.c->ticket2, 1u) == (unsigned)(P.n_cells - 1);
-        }
-        __syncthreads();
-        if (last) {
-            // the last CTA of this system: group kinetic energies and the next factor
-            __threadfence();
-            double k0 = 0.0, k1 = 0.0;
-            for (int b = t; b < P.n_cells; b += PAIR_THREADS) { k0 += __ldcg(&S.ke_part[2 * b]); k1 += __ldcg(&S.ke_part[2 * b + 1]); }
-            ered[0][t] = k0;
-            ered[1][t] = k1;
-            __syncthreads();
-            for (int w = PAIR_THREADS / 2; w > 0; w >>= 1) {
-                if (t < w) { ered[0][t] += ered[0][t + w]; ered[1][t] += ered[1][t + w]; }
-                __syncthreads();
-            }
-            Counters &C = *S.c;
-            const int in_at = C.in_at;
-            const unsigned long long next = (in_at ? C.at_step : C.step) + 1;
-            const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
-            if ((t & 31) == 0 && t < 64) C.alpha[t >> 5] = alpha_for(S, P, C, t >> 5, ered[t >> 5][0], next, tag);
-            __syncthreads();
-            if (t == 0) {
-                if (in_at) C.at_step = next; else C.step = next;
+            if (c == 0) {                        // once per system: the step is done
+                Counters &C = *S.c;
+                if (C.in_at) C.at_step++; else C.step++;
                 C.md_steps++;
                 C.force_evals++;
-                C.ticket2 = 0;
+                C.ke_fresh = 1;
             }
         }
     }

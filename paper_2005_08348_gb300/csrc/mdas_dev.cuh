@@ -86,7 +86,7 @@ struct Counters {
     unsigned long long draw_base;      // thermostat variates precomputed for counters
     int draw_n, draw_tag;              // [draw_base, draw_base + draw_n) of stream draw_tag
     unsigned int ticket;               // last-block ticket of the fused single trial
-    unsigned int ticket2;              // last-block ticket of the step kernel
+    int ke_fresh;                      // ke_part holds the kinetic energy of the current velocities
 };
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
@@ -173,7 +173,6 @@ struct LaunchCtx {
 
 cudaError_t setup_kernels();
 void launch_cells(const LaunchCtx &L, bool counted = false);
-void launch_thermostat(const LaunchCtx &L);
 void launch_thermo_draws(const LaunchCtx &L, int n_steps);
 void launch_trial_one(const LaunchCtx &L);
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64);

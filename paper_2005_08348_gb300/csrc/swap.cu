@@ -559,6 +559,7 @@ __global__ void k_restore(const SysDev *__restrict__ sys, const int2 *__restrict
     const SysDev &S = sys[bm.x];
     const int i = bm.y + threadIdx.x;
     if (i >= S.p->n || S.c->mdas_accept) return;
+    if (i == 0) S.c->ke_fresh = 0;            // the velocities go back to the snapshot
     S.pos[i] = S.pos_snap[i];
     reinterpret_cast<V4 *>(S.vel)[i] = reinterpret_cast<const V4 *>(S.vel_snap)[i];
 }
