@@ -210,15 +210,17 @@ __device__ void thermostat_block(const SysDev &S, const Params &P) {
     using V4 = typename Vec4<Real>::T;
     Counters &C = *S.c;
     const int t = threadIdx.x, T = blockDim.x;
-    __shared__ double ks[2][32 * CELLS_PER_SORT_BLOCK];
-    double k0 = 0.0, k1 = 0.0;
+    // sums in the system's precision (FP32 systems: the factor is float anyway)
+    __shared__ Real ks[2][32 * CELLS_PER_SORT_BLOCK];
+    Real k0 = 0, k1 = 0;
     if (C.ke_fresh) {
-        for (int b = t; b < P.n_cells; b += T) { k0 += S.ke_part[2 * b]; k1 += S.ke_part[2 * b + 1]; }
+        for (int b = t; b < P.n_cells; b += T) { k0 += (Real)S.ke_part[2 * b]; k1 += (Real)S.ke_part[2 * b + 1]; }
     } else {
         const V4 *vel = reinterpret_cast<const V4 *>(S.vel);
+        const Real hm = (Real)(0.5 * P.mass);
         for (int i = t; i < P.n; i += T) {
             const V4 v = vel[i];
-            const double e = 0.5 * P.mass * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+            const Real e = hm * (v.x * v.x + v.y * v.y + v.z * v.z);
             if (i < P.n_lipid_beads) k0 += e; else k1 += e;
         }
     }
@@ -234,7 +236,7 @@ __device__ void thermostat_block(const SysDev &S, const Params &P) {
     const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
     if ((t & 31) == 0 && t < 64) {
         const int g = t >> 5;
-        C.alpha[g] = alpha_for(S, P, C, g, ks[g][0], ctr, tag);
+        C.alpha[g] = alpha_for(S, P, C, g, (double)ks[g][0], ctr, tag);
     }
 }
 
@@ -346,7 +348,7 @@ __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 
 __device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * FIX); }
 
 template <typename Real, bool LAM, bool ENERGY, bool INTEG>
-__global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+__global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     using V4 = typename Vec4<Real>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int2 bm = bmap[blockIdx.x];
@@ -405,6 +407,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
     const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
     const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
     const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
+    // parameters used in the inner loops, held in registers
+    const float qh0 = P.qsh[0], qh1 = P.qsh[1], qh2 = P.qsh[2];
+    const float ql0 = P.qsl[0], ql1 = P.qsl[1], ql2 = P.qsl[2];
     const Real lam = LAM ? (Real)S.c->lambda : (Real)0;
     double elj = 0.0, erf = 0.0, epairs = 0.0;
     Real ke0 = 0, ke1 = 0;
@@ -431,13 +436,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
                 ax = fb[0]; ay = fb[1]; az = fb[2];
             }
         }
-        // the updating thread (stream 0) fetches the bead's velocity early
-        V4 vpre;
-        int idpre = 0;
-        if (INTEG && js == 0 && i < ni) {
-            idpre = S.sorted_id[ifirst + i];
-            vpre = reinterpret_cast<const V4 *>(S.vel)[idpre];
-        }
 
         auto flush = [&](int count) {
             for (int e = 0; e < count; ++e) {
@@ -447,9 +445,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
                 if (F32) {
                     const float fx = (float)wrap_diff(oix, ij.x), fy = (float)wrap_diff(oiy, ij.y),
                                 fz = (float)wrap_diff(oiz, ij.z);
-                    dx = (Real)fmaf(fx, P.qsh[0], fx * P.qsl[0]);
-                    dy = (Real)fmaf(fy, P.qsh[1], fy * P.qsl[1]);
-                    dz = (Real)fmaf(fz, P.qsh[2], fz * P.qsl[2]);
+                    dx = (Real)fmaf(fx, qh0, fx * ql0);
+                    dy = (Real)fmaf(fy, qh1, fy * ql1);
+                    dz = (Real)fmaf(fz, qh2, fz * ql2);
                 } else {
                     const StagedPos<Real> pj = sf[j];
                     dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
@@ -546,6 +544,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair(const SysDev *__restrict_
             flush(nq);
         }
 
+        // the updating thread (stream 0) fetches the bead's velocity before the barrier
+        V4 vpre;
+        int idpre = 0;
+        if (INTEG && js == 0 && i < ni) {
+            idpre = S.sorted_id[ifirst + i];
+            vpre = reinterpret_cast<const V4 *>(S.vel)[idpre];
+        }
         __syncthreads();                          // every queue has drained: red may alias q
         red[0 * PAIR_THREADS + t] = to_fix(ax);
         red[1 * PAIR_THREADS + t] = to_fix(ay);

@@ -72,15 +72,15 @@ __device__ double bead_delta(const SysDev &S, const Params &P, int i, uint4 pi, 
     return acc;
 }
 
-// fixed-order tree sum over the block (blockDim.x a power of two <= 128)
+// fixed-order sum over the block: a shuffle tree per warp, then the warp
+// sums in order (blockDim.x a multiple of 32, at most 1024)
 __device__ double block_sum(double v, double *sh) {
-    sh[threadIdx.x] = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    const double s = sh[0];
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
     __syncthreads();
     return s;
 }
