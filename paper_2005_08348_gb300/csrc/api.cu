@@ -921,7 +921,8 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     c.step = in->step; c.trial = in->trial; c.move = in->move; c.at_step = in->at_step;
-    c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0; c.ke_fresh = 0; c.draw_n = 0;
+    c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0; c.ke_fresh = 0; c.ke_pending = 0; c.draw_n = 0;
+    memset(c.ke_slot, 0, sizeof(c.ke_slot));
     CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
     if (s->counted) CK(cudaMemsetAsync(s->hs.cell_count, 0, 4ull * s->hp.n_cells, s->stream));
     s->counted = false;

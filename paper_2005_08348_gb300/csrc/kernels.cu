@@ -210,11 +210,29 @@ __device__ void thermostat_block(const SysDev &S, const Params &P) {
     using V4 = typename Vec4<Real>::T;
     Counters &C = *S.c;
     const int t = threadIdx.x, T = blockDim.x;
-    // sums in the system's precision (FP32 systems: the factor is float anyway)
     __shared__ Real ks[2][32 * CELLS_PER_SORT_BLOCK];
+    __shared__ int fresh;
+    if (t == 0) fresh = C.ke_fresh;
+    if (C.ke_pending) {
+        // the step kernel's integer slots: order-independent sums, read once
+        __shared__ long long kl[2][KE_SLOTS];
+        if (t < KE_SLOTS) {
+            kl[0][t] = C.ke_slot[t][0]; kl[1][t] = C.ke_slot[t][1];
+            C.ke_slot[t][0] = 0; C.ke_slot[t][1] = 0;
+        }
+        __syncthreads();
+        if (t < 2) {
+            long long a = 0;
+            for (int k = 0; k < KE_SLOTS; ++k) a += kl[t][k];
+            C.ke_total[t] = (double)a * (1.0 / FIX);
+        }
+        __syncthreads();
+        if (t == 0) { C.ke_pending = 0; C.ke_fresh = 1; fresh = 1; }
+    }
+    __syncthreads();
     Real k0 = 0, k1 = 0;
-    if (C.ke_fresh) {
-        for (int b = t; b < P.n_cells; b += T) { k0 += (Real)S.ke_part[2 * b]; k1 += (Real)S.ke_part[2 * b + 1]; }
+    if (fresh) {
+        if (t == 0) { k0 = (Real)C.ke_total[0]; k1 = (Real)C.ke_total[1]; }
     } else {
         const V4 *vel = reinterpret_cast<const V4 *>(S.vel);
         const Real hm = (Real)(0.5 * P.mass);
@@ -607,14 +625,16 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
         if (t == 0) {
             Real a0 = 0, a1 = 0;
             for (int k = 0; k < (ni < PAIR_THREADS ? ni : PAIR_THREADS); ++k) { a0 += kered[0][k]; a1 += kered[1][k]; }
-            S.ke_part[2 * c] = (double)a0;
-            S.ke_part[2 * c + 1] = (double)a1;
+            // integer accumulation: the sum does not depend on the order of the CTAs
+            Counters &C = *S.c;
+            atomicAdd((unsigned long long *)&C.ke_slot[c % KE_SLOTS][0], (unsigned long long)to_fix(a0));
+            atomicAdd((unsigned long long *)&C.ke_slot[c % KE_SLOTS][1], (unsigned long long)to_fix(a1));
             if (c == 0) {                        // once per system: the step is done
-                Counters &C = *S.c;
                 if (C.in_at) C.at_step++; else C.step++;
                 C.md_steps++;
                 C.force_evals++;
-                C.ke_fresh = 1;
+                C.ke_pending = 1;
+                C.ke_fresh = 0;
             }
         }
     }

@@ -73,6 +73,8 @@ struct TrialRec {                      // mirrors mdas_trial_record
     unsigned long long index;
 };
 
+constexpr int KE_SLOTS = 64;           // integer accumulators of the step kernel's kinetic energy
+
 // Mutable per-system scalars (device memory).
 struct Counters {
     unsigned long long step, trial, move, at_step;
@@ -86,7 +88,10 @@ struct Counters {
     unsigned long long draw_base;      // thermostat variates precomputed for counters
     int draw_n, draw_tag;              // [draw_base, draw_base + draw_n) of stream draw_tag
     unsigned int ticket;               // last-block ticket of the fused single trial
-    int ke_fresh;                      // ke_part holds the kinetic energy of the current velocities
+    int ke_fresh;                      // ke_total holds the kinetic energy of the current velocities
+    int ke_pending;                    // the step kernel left kinetic energy in ke_slot
+    double ke_total[2];
+    long long ke_slot[KE_SLOTS][2];    // fixed-point kinetic energy per slot and group (2^32 units)
 };
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
