@@ -263,8 +263,13 @@ def run_gpu(args):
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     if os.path.exists(tfile):
+        # DRAM bytes of one step-kernel launch from an ncu capture of this
+        # workload; void once the kernel source has changed since the capture
+        import hashlib
         tj = json.load(open(tfile))
-        if tj.get("beads") == n:
+        src = os.path.join(ROOT, "paper_2005_08348_gb300", "csrc", "kernels.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if tj.get("beads") == n and tj.get("kernels_cu_sha256") == h:
             traffic = tj.get("bytes_per_launch")
     out = {
         "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s", "n_gpus": ws,
