@@ -206,6 +206,36 @@ typedef struct {
 } mdas_counters;
 mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
 
+/* Forces of one state without allocating anything.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory while
+ * they run - code confined to a memory budget another application hands it,
+ * code living between the allocations of a framework that owns the device
+ * heap, or a real-time loop that must not meet cudaMalloc's implicit device
+ * synchronisation.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine; its scratch is one fixed array (about 7 MB) that every GPU which
+ * loads the library holds until the process exits.
+ *
+ * d supplies the force field, box and precision as for mdas_create_system
+ * (d->pos, d->vel, d->lipid_type, allocator hooks and seed are ignored);
+ * pos_fixed [n_beads*3] (fixed-point positions, as mdas_get_state returns
+ * them), lipid_type [n_lipids] and f_out [n_beads*3] are DEVICE pointers the
+ * caller owns; the work runs on d->cuda_stream (NULL: the legacy default
+ * stream) and the call returns after f_out is written.  The result equals
+ * mdas_forces for the same state.
+ *
+ * Limits: n_beads <= 16384, at most 4096 cells (floor(L/rc) per edge), at
+ * most 64 beads in a cell.  Errors: MDAS_ERR_INVALID_ARG for a NULL pointer,
+ * a size beyond these limits or a lipid type outside the table;
+ * MDAS_ERR_UNSTABLE when a cell holds more than 64 beads; MDAS_ERR_CUDA.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream capture.
+ * Every call shares the array and leaves its contents behind (each call clears
+ * what must start at zero); calls that overlap on the GPU race, so serialise
+ * them. */
+mdas_status mdas_forces_noalloc(const mdas_system_desc *d, const uint32_t *pos_fixed, const int32_t *lipid_type,
+                                double *f_out);
+
 const char *mdas_last_error(const mdas_system *s);
 const char *mdas_status_string(mdas_status st);
 

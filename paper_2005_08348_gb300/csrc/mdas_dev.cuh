@@ -27,7 +27,7 @@ constexpr double BOLTZ = 0.0083144626;
 constexpr double COUL = 138.935458;
 
 enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5 };
-enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8 };
+enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8, ERR_BAD_INPUT = 16 };
 
 // Per-bead meta word carried in the 4th lane of every position:
 // bits 0-3 current bead type (A), 4-7 alchemical target type (B),

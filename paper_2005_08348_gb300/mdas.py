@@ -82,7 +82,8 @@ TRIAL_DTYPE = np.dtype([("a", np.int32), ("b", np.int32), ("null", np.int32), ("
 EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_energy", "mdas_md_steps",
            "mdas_swap_trials", "mdas_trial_log", "mdas_alchemical_move", "mdas_delta_energy", "mdas_get_state",
            "mdas_set_state", "mdas_cell_list", "mdas_batch_run", "mdas_philox", "mdas_set_kernel_timing",
-           "mdas_pair_kernel_time", "mdas_get_counters", "mdas_last_error", "mdas_status_string"]
+           "mdas_pair_kernel_time", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
+           "mdas_forces_noalloc"]
 
 
 def library_path() -> str:
@@ -183,8 +184,16 @@ class System:
         if torch_allocator:
             d.dev_alloc, d.dev_free = _torch_allocator()
         self._ptr = C.c_void_p()
+        self._desc_arrays = k
+        self._desc_fields = dict(d=d)
         _check(L.mdas_create_system(C.byref(d), C.byref(self._ptr)))
         self.kT = 0.0083144626 * d.temperature
+
+    def _desc_for_noalloc(self, stream=None):
+        d = self._desc_fields["d"]
+        d.dev_alloc, d.dev_free = _ALLOC(), _FREE()
+        d.cuda_stream = stream
+        return d
 
     # -- lifetime -------------------------------------------------------------
     def close(self):
@@ -290,6 +299,17 @@ class System:
         ms, n = C.c_double(), C.c_int64()
         self._ck(lib().mdas_pair_kernel_time(self._ptr, C.byref(ms), C.byref(n), int(bool(reset))))
         return ms.value, n.value
+
+
+def forces_noalloc(system, pos_fixed_ptr, lipid_type_ptr, f_out_ptr, stream=None):
+    """mdas_forces_noalloc for the force field of `system` (a System) on
+    caller-owned device buffers (integer addresses), e.g. torch tensor
+    data_ptr()s.  Raises MdasError with the returned status."""
+    d = system._desc_for_noalloc(stream)
+    st = lib().mdas_forces_noalloc(C.byref(d), C.c_void_p(pos_fixed_ptr), C.c_void_p(lipid_type_ptr),
+                                   C.c_void_p(f_out_ptr))
+    if st != 0:
+        raise MdasError(st, "forces_noalloc failed")
 
 
 def batch_run(systems, md_steps, swap_trials):
