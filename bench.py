@@ -24,8 +24,6 @@ sys.path.insert(0, ROOT)
 
 MD_PER_STEP = 100
 PAIR_FLOPS = 30          # algorithmic FP32 flops of one pair interaction (FMA = 2)
-LAUNCHES_PER_MD = 7      # thermostat, 4 cell-list kernels, pair, integrate
-LAUNCHES_PER_TRIAL = 8   # 4 cell-list kernels, proposal, conflicts, dE, resolve
 
 
 def parse():
@@ -36,6 +34,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the replica and swap-throughput lines")
     return ap.parse_args()
 
 
@@ -279,7 +278,7 @@ def run_gpu(args):
         "config": config(m, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                              "pairs_per_force_eval": pairs_per_eval}),
         "swap_trials_per_s": trials_per_s, "md_steps_per_s": md * ws / tmax,
-        "gpu_launches": int(md * LAUNCHES_PER_MD + trials * LAUNCHES_PER_TRIAL),
+        "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "e2e": {"value": e2e_value, "unit": "pair-interactions/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "roofline": {"kernel": "k_pair<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
@@ -290,6 +289,9 @@ def run_gpu(args):
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    if not args.no_extra:
+        out["batched_replicas"] = replica_benchmark(stream)
+        out["swap_trials_4608_lipids"] = swap_benchmark(stream)
     if not args.no_cpu_baseline:
         ob = oracle_rate(m)
         out["cpu_baseline"] = {"value": ob["pairs_per_s"], "unit": "pair-interactions/s", "cores": 1,
@@ -300,6 +302,74 @@ def run_gpu(args):
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def _elapsed(stream, fn):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def replica_benchmark(stream, n_rep=64, rounds=3):
+    """64 independent bilayers of 128-2048 lipids, each advanced by 100 MD
+    steps + 100 exchange trials per round: all replicas in one launch per
+    phase (mdas_batch_run) against one replica at a time."""
+    from paper_2005_08348_gb300 import mdas, synth
+    ms = synth.replica_set(n_rep)
+    sys_b = [mdas.System(m, stream=stream.cuda_stream) for m in ms]
+    sys_s = [mdas.System(m, stream=stream.cuda_stream) for m in ms]
+    pairs = sum(s.energy()["pairs"] for s in sys_b)
+    mdas.batch_run(sys_b, MD_PER_STEP, MD_PER_STEP)
+    for s in sys_s:
+        s.md_steps(MD_PER_STEP)
+        s.swap_trials(MD_PER_STEP, log=False)
+
+    def batched():
+        for _ in range(rounds):
+            mdas.batch_run(sys_b, MD_PER_STEP, MD_PER_STEP)
+
+    def solo():
+        for _ in range(rounds):
+            for s in sys_s:
+                s.md_steps(MD_PER_STEP)
+                s.swap_trials(MD_PER_STEP, log=False)
+
+    tb, ts = _elapsed(stream, batched), _elapsed(stream, solo)
+    md = rounds * MD_PER_STEP
+    res = {"workload": f"{n_rep} replicas, {sum(m.n_lipids for m in ms)} lipids, {sum(m.n_beads for m in ms)} beads",
+           "batched_pair_interactions_per_s": pairs * md / tb, "one_at_a_time_pair_interactions_per_s": pairs * md / ts,
+           "batched_swap_trials_per_s": n_rep * md / tb, "one_at_a_time_swap_trials_per_s": n_rep * md / ts,
+           "speedup": ts / tb, "rounds": rounds}
+    for s in sys_b + sys_s:
+        s.close()
+    return res
+
+
+def swap_benchmark(stream, n_batch=1024, n_plain=300):
+    """Exchange trials on the 4608-lipid bilayer (~140k beads): one trial per
+    call (the plain path) against batched calls of 1024 trials."""
+    from paper_2005_08348_gb300 import mdas, synth
+    m = synth.mdas_patch()
+    s = mdas.System(m, stream=stream.cuda_stream)
+    s.swap_trials(16, log=False)
+    t_plain = _elapsed(stream, lambda: [s.swap_trials(1, log=False) for _ in range(n_plain)])
+    stats = {}
+
+    def batched():
+        st, _ = s.swap_trials(n_batch, log=False)
+        stats.update(st)
+
+    s.swap_trials(n_batch, log=False)
+    t_batch = _elapsed(stream, batched)
+    s.close()
+    return {"workload": f"{m.n_lipids} lipids, {m.n_beads} beads", "plain_trials_per_s": n_plain / t_plain,
+            "batched_trials_per_s": n_batch / t_batch, "ratio": (n_batch / t_batch) / (n_plain / t_plain),
+            "batch": n_batch, "rounds_per_batch": stats.get("rounds")}
 
 
 def main():

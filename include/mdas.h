@@ -191,18 +191,20 @@ mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32
  * 0..n-1, key (k0, k1): out [n*4] host. */
 mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out);
 
-/* Kernel timing: when enabled, every pair-kernel launch of mdas_md_steps and
- * mdas_batch_run is bracketed by CUDA events on the launching stream;
+/* Kernel timing: when enabled, every 8th MD-step kernel launch of
+ * mdas_md_steps and mdas_batch_run is bracketed by CUDA events on the
+ * launching stream;
  * mdas_pair_kernel_time returns the sum of their durations (ms) and the launch
  * count since the last reset (reset = 1 clears after reading). */
 mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable);
 mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *launches, int32_t reset);
 
 /* Per-system counters: MD steps, force evaluations (one per MD step and one
- * per exchange trial, as counted in Sec. 3), trials, accepted trials, in-cutoff
- * pairs of the last force evaluation. */
+ * per exchange trial, as counted in Sec. 3), trials, null and accepted trials,
+ * MDAS moves and accepted moves, and the kernel launches of replayed CUDA
+ * graphs that advanced the system. */
 typedef struct {
-    int64_t md_steps, force_evals, trials, null_trials, accepted, moves, moves_accepted;
+    int64_t md_steps, force_evals, trials, null_trials, accepted, moves, moves_accepted, kernel_launches;
 } mdas_counters;
 mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
 

@@ -20,6 +20,7 @@ namespace {
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pair_events;
+    long long kernel_nodes = 0;
 };
 
 struct Batch {
@@ -63,9 +64,12 @@ struct mdas_system {
     bool timing = false;
     double pair_ms = 0.0;
     long long pair_launches = 0;
+    long long kernel_launches = 0;   // kernel launches (graph kernel nodes included) that advanced this system
 };
 
 namespace {
+
+constexpr int TIMING_STRIDE = 8;   // kernel timing brackets every 8th step kernel
 
 std::map<std::vector<mdas_system *>, std::unique_ptr<Batch>> g_batches;
 
@@ -257,7 +261,7 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
     GraphEntry ge;
     cudaGraph_t g;
     if (timing) {
-        for (int k = 0; k < units * steps_per_unit; ++k) {
+        for (int k = 0; k < units * steps_per_unit; k += TIMING_STRIDE) {
             cudaEvent_t e0, e1;
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));
@@ -268,13 +272,13 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
     LaunchCtx L = b.ctx();
     // the step kernel of step k sets the factor of step k + 1
     launch_thermo_draws(L, units * steps_per_unit + 1);
-    int ev = 0;
+    int ev = 0, step_no = 0;
     for (int u = 0; u < units; ++u) {
-        for (int k = 0; k < steps_per_unit; ++k) {
+        for (int k = 0; k < steps_per_unit; ++k, ++step_no) {
             const bool first = u == 0 && k == 0;
             const bool have_cells = trial && k == 0 && (u > 0 || reuse_first);
             if (!have_cells) launch_cells(L, first ? counted_first : true);
-            if (timing) {
+            if (timing && step_no % TIMING_STRIDE == 0) {
                 // external event nodes: recorded (and timed) at every replay
                 cudaEventRecordWithFlags(ge.pair_events[ev].first, b.stream, cudaEventRecordExternal);
                 launch_step(L, lambda);
@@ -291,6 +295,14 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
     }
     cudaError_t e = cudaStreamEndCapture(b.stream, &g);
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes) cudaGraphGetNodes(g, nodes.data(), &n_nodes);
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ge.kernel_nodes++;
+    }
     e = cudaGraphInstantiate(&ge.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
@@ -301,6 +313,7 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
 
 mdas_status replay(mdas_system *s, Batch &b, GraphEntry *ge) {
     CK(cudaGraphLaunch(ge->exec, b.stream));
+    for (auto *x : b.sys) x->kernel_launches += ge->kernel_nodes;
     if (!ge->pair_events.empty()) {
         CK(cudaStreamSynchronize(b.stream));
         for (auto &ev : ge->pair_events) {
@@ -1023,6 +1036,7 @@ mdas_status mdas_get_counters(const mdas_system *cs, mdas_counters *out) {
     out->accepted = (int64_t)c.accepted;
     out->moves = (int64_t)c.moves;
     out->moves_accepted = (int64_t)c.moves_accepted;
+    out->kernel_launches = (int64_t)s->kernel_launches;
     return MDAS_OK;
 }
 
