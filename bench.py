@@ -29,7 +29,7 @@ PAIR_FLOPS = 30          # algorithmic FP32 flops of one pair interaction (FMA =
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-clocks", action="store_true")
@@ -292,6 +292,7 @@ def run_gpu(args):
     if not args.no_extra:
         out["batched_replicas"] = replica_benchmark(stream)
         out["swap_trials_4608_lipids"] = swap_benchmark(stream)
+        out["served"] = serving_benchmark(stream)
     if not args.no_cpu_baseline:
         ob = oracle_rate(m)
         out["cpu_baseline"] = {"value": ob["pairs_per_s"], "unit": "pair-interactions/s", "cores": 1,
@@ -370,6 +371,61 @@ def swap_benchmark(stream, n_batch=1024, n_plain=300):
     return {"workload": f"{m.n_lipids} lipids, {m.n_beads} beads", "plain_trials_per_s": n_plain / t_plain,
             "batched_trials_per_s": n_batch / t_batch, "ratio": (n_batch / t_batch) / (n_plain / t_plain),
             "batch": n_batch, "rounds_per_batch": stats.get("rounds")}
+
+
+def serving_benchmark(stream, n_jobs=48, n_patches=12, seed=1005):
+    """Served sampling: jobs on patches of 128-16384 lipids (log-uniform,
+    2-3 types), mix 60% 256 swap trials / 30% 100 MD steps / 10% one MDAS move
+    (8 pairs = 16 lipids, 10 lambda steps of 5 MD steps), Poisson arrivals at
+    0.25x, 0.5x and 0.9x of the saturation throughput measured first."""
+    import numpy as np
+    from paper_2005_08348_gb300 import mdas, synth
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(128), np.log(16384), n_patches)).astype(int) // 2 * 2
+    pool = [synth.patch(int(n), int(rng.integers(2, 4)), seed=seed * 100 + k, system_id=k)
+            for k, n in enumerate(sizes)]
+
+    def draw_jobs(r):
+        out = []
+        for _ in range(n_jobs):
+            x = r.uniform()
+            kind, n = (mdas.JOB_SWAPS, 256) if x < 0.6 else ((mdas.JOB_MD, 100) if x < 0.9 else (mdas.JOB_MDAS, 0))
+            out.append((pool[int(r.integers(0, n_patches))], kind, n))
+        return out
+
+    def serve(jobs, arrivals):
+        sv = mdas.Server(64 << 30, max_active=16, md_quantum=25, stream=stream.cuda_stream)
+        t0 = sv.clock()
+        k = 0
+        done = []
+        while len(done) < len(jobs):
+            now = sv.clock() - t0
+            while k < len(jobs) and arrivals[k] <= now:
+                p, kind, n = jobs[k]
+                sv.submit(p, kind, n=n, n_pairs=8, n_lambda=10, md_per_lambda=5)
+                k += 1
+            a, q = sv.run(1)
+            done += sv.results()
+            if a == 0 and q == 0 and k < len(jobs):
+                time.sleep(max(0.0, min(0.002, arrivals[k] - (sv.clock() - t0))))
+        span = max(r["t_done"] for r in done) - t0
+        lat = np.array([r["t_done"] - r["t_submit"] for r in done])
+        sv.close()
+        return span, lat
+
+    jobs = draw_jobs(np.random.default_rng(seed + 1))
+    serve(jobs[:8], [0.0] * 8)                          # warm-up
+    span, lat = serve(jobs, [0.0] * n_jobs)
+    sat = n_jobs / span
+    res = {"workload": f"{n_jobs} jobs per rate on {n_patches} patches of {int(sizes.min())}-{int(sizes.max())} lipids",
+           "saturation_jobs_per_s": sat, "rates": []}
+    for frac in (0.25, 0.5, 0.9):
+        r = np.random.default_rng(seed + int(frac * 100))
+        arr = np.cumsum(r.exponential(1.0 / (frac * sat), n_jobs))
+        span, lat = serve(jobs, list(arr))
+        res["rates"].append({"load": frac, "arrival_jobs_per_s": frac * sat, "throughput_jobs_per_s": n_jobs / span,
+                             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+    return res
 
 
 def main():

@@ -238,6 +238,54 @@ mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
 mdas_status mdas_forces_noalloc(const mdas_system_desc *d, const uint32_t *pos_fixed, const int32_t *lipid_type,
                                 double *f_out);
 
+/* ---- serving: continuous batching of jobs on device-resident patches ----
+ * The paper runs one system at a time; this request loop serves many patches
+ * at once.  Jobs are queued with a copy of their patch's description, admitted
+ * in arrival order while the device-memory budget and the slot count allow
+ * (admission by the system's device footprint), and advanced in rounds: all
+ * active MD jobs by one batched quantum of steps, all swap jobs by one batched
+ * evaluation of their trials, each MDAS job by its move.  Jobs that arrive
+ * while others run join at the next round; finished jobs free their memory
+ * and slot.  A job's result does not depend on the other jobs (per-system
+ * Philox keys and counters, deterministic kernels). */
+typedef struct mdas_server mdas_server;
+typedef enum { MDAS_JOB_SWAPS = 0, MDAS_JOB_MD = 1, MDAS_JOB_MDAS = 2 } mdas_job_kind;
+typedef struct {
+    int32_t kind;                      /* mdas_job_kind */
+    int32_t n;                         /* swap trials (SWAPS) or MD steps (MD) */
+    int32_t n_pairs, n_lambda, md_per_lambda;   /* MDAS move parameters */
+} mdas_job;
+typedef struct {
+    int64_t job_id;
+    int32_t kind, status;
+    double t_submit, t_admit, t_done;  /* seconds on the server clock */
+    int64_t md_steps, trials, accepted;
+    double w;                          /* MDAS work */
+    int32_t move_accepted;
+    uint64_t state_hash;               /* FNV-1a of final positions, velocities, types (if kept) */
+} mdas_job_result;
+
+/* hbm_budget_bytes: device memory the active systems may use; max_active:
+ * slots; md_quantum: MD steps per round; keep_state_hash: hash each final
+ * state (for tests); cuda_stream as in mdas_system_desc. */
+mdas_status mdas_server_create(size_t hbm_budget_bytes, int32_t max_active, int32_t md_quantum, int32_t keep_state_hash,
+                               void *cuda_stream, mdas_server **out);
+void mdas_server_destroy(mdas_server *sv);
+/* Queue a job on a patch (d: host description, copied; its stream and
+ * allocator fields are replaced by the server's).  MDAS_ERR_OOM if the patch
+ * alone exceeds the budget. */
+mdas_status mdas_server_submit(mdas_server *sv, const mdas_system_desc *d, const mdas_job *job, int64_t *job_id);
+/* Run up to max_rounds scheduling rounds (admit, advance, retire); reports the
+ * active and queued job counts. */
+mdas_status mdas_server_run(mdas_server *sv, int32_t max_rounds, int32_t *n_active, int32_t *n_queued);
+/* Move up to cap finished-job results to out; *n receives the count. */
+mdas_status mdas_server_results(mdas_server *sv, mdas_job_result *out, int32_t cap, int32_t *n);
+/* Seconds since the server was created (the clock of the result times). */
+double mdas_server_clock(const mdas_server *sv);
+/* Device bytes a system of this description occupies (the server's admission
+ * charge); 0 for an invalid description. */
+size_t mdas_system_footprint(const mdas_system_desc *d);
+
 const char *mdas_last_error(const mdas_system *s);
 const char *mdas_status_string(mdas_status st);
 

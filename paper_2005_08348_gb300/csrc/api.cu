@@ -31,6 +31,8 @@ struct Batch {
     cudaStream_t stream = nullptr;
     int max_bead_blocks = 1;
     int *dscratch = nullptr;      // [2]: pending sum, error or
+    bool use_graphs = true;       // false for batches whose membership changes (the server's)
+    size_t cap_sys = 0, cap_beads = 0, cap_cells = 0, cap_sort = 0;   // device capacity (refillable batches)
     std::map<std::string, GraphEntry> graphs;
     LaunchCtx ctx() const {
         LaunchCtx L;
@@ -163,6 +165,55 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
     CK(upload_map(b->syss, syss));
     CK(cudaMalloc(&b->dscratch, sizeof(int) * 4));
     out = std::move(b);
+    return MDAS_OK;
+}
+
+// Refill a reusable batch with a new set of systems: device arrays only grow.
+mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
+    mdas_system *s = v[0];
+    b.sys = v;
+    b.precision = v[0]->precision;
+    b.stream = v[0]->stream;
+    b.use_graphs = false;
+    b.max_bead_blocks = 1;
+    std::vector<SysDev> hs;
+    std::vector<int2> beads, cells, sortcells, syss;
+    for (int k = 0; k < (int)v.size(); ++k) {
+        const mdas_system *x = v[k];
+        if (x->precision != b.precision || x->stream != b.stream)
+            return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision or stream");
+        hs.push_back(x->hs);
+        for (int i = 0; i < x->n; i += BEAD_BLOCK) beads.push_back(make_int2(k, i));
+        for (int c = 0; c < x->hp.n_cells; ++c) cells.push_back(make_int2(k, c));
+        for (int c = 0; c < x->hp.n_cells; c += CELLS_PER_SORT_BLOCK) sortcells.push_back(make_int2(k, c));
+        sortcells.push_back(make_int2(k, -1));
+        syss.push_back(make_int2(k, 0));
+        b.max_bead_blocks = std::max(b.max_bead_blocks, (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK);
+    }
+    auto grow = [&](void **ptr, size_t &cap, size_t need, size_t elem) -> cudaError_t {
+        if (need <= cap && *ptr) return cudaSuccess;
+        if (*ptr) cudaFree(*ptr);
+        cap = std::max<size_t>(need * 2, 64);
+        return cudaMalloc(ptr, cap * elem);
+    };
+    CK(grow((void **)&b.dsys, b.cap_sys, hs.size(), sizeof(SysDev)));
+    CK(grow((void **)&b.beads.d, b.cap_beads, beads.size(), sizeof(int2)));
+    CK(grow((void **)&b.cells.d, b.cap_cells, cells.size(), sizeof(int2)));
+    CK(grow((void **)&b.sortcells.d, b.cap_sort, sortcells.size(), sizeof(int2)));
+    size_t cap_syss = 0;
+    if (!b.syss.d) CK(grow((void **)&b.syss.d, cap_syss, 4096, sizeof(int2)));
+    if (syss.size() > 4096) return fail(s, MDAS_ERR_INVALID_ARG, "batch: more than 4096 systems");
+    if (!b.dscratch) CK(cudaMalloc(&b.dscratch, sizeof(int) * 4));
+    CK(cudaMemcpyAsync(b.dsys, hs.data(), sizeof(SysDev) * hs.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaMemcpyAsync(b.beads.d, beads.data(), sizeof(int2) * beads.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaMemcpyAsync(b.cells.d, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaMemcpyAsync(b.sortcells.d, sortcells.data(), sizeof(int2) * sortcells.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaMemcpyAsync(b.syss.d, syss.data(), sizeof(int2) * syss.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaStreamSynchronize(b.stream));   // the host vectors go out of scope
+    b.beads.n = (int)beads.size();
+    b.cells.n = (int)cells.size();
+    b.sortcells.n = (int)sortcells.size();
+    b.syss.n = (int)syss.size();
     return MDAS_OK;
 }
 
@@ -338,6 +389,17 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     bool counted;
     mdas_status st = sync_counted(s, b, &counted);
     if (st != MDAS_OK) return st;
+    if (!b.use_graphs) {   // membership changes between calls: plain launches, same arithmetic
+        for (long long k = 0; k < n_steps; ++k) {
+            md_step_launches(b, lambda, counted);
+            counted = true;
+        }
+        set_counted(b, true);
+        for (auto *x : b.sys) x->cells_valid = false;
+        for (auto *x : b.sys) x->kernel_launches += 2 * n_steps;
+        CK(cudaGetLastError());
+        return check_err(s, b);
+    }
     if (n_units > 0) {
         bool reuse = false;
         if (trial) {
@@ -1038,6 +1100,317 @@ mdas_status mdas_get_counters(const mdas_system *cs, mdas_counters *out) {
     out->moves_accepted = (int64_t)c.moves_accepted;
     out->kernel_launches = (int64_t)s->kernel_launches;
     return MDAS_OK;
+}
+
+}  // extern "C"
+
+// ================================================================= serving
+// A request loop over device-resident systems (continuous batching): jobs are
+// queued with a copy of their patch's description, admitted in arrival order
+// while the device-memory budget and the slot count allow, and advanced in
+// rounds in which one batched launch per phase covers every active job of a
+// kind (MD jobs by a quantum of steps, swap jobs by their trials).  New jobs
+// join at the next round; finished jobs leave and free their memory.  Every
+// system keeps its own Philox key and counters, so a job's result does not
+// depend on what else is running.
+
+#include <chrono>
+#include <deque>
+
+namespace {
+
+struct PendingJob {
+    int64_t id = 0;
+    mdas_job job{};
+    double t_submit = 0.0;
+    size_t footprint = 0;
+    mdas_system_desc d{};
+    std::vector<double> pos, vel, eps, sigma, charge;
+    std::vector<int32_t> first, ltype, lbt, bonds, angles;
+};
+
+struct ActiveJob {
+    PendingJob p;
+    mdas_system *sys = nullptr;
+    double t_admit = 0.0;
+    long long remaining = 0;
+    bool done = false;
+    double w = 0.0;
+    int move_accepted = 0;
+};
+
+// arena bytes of a system (the sizes mdas_create_system allocates)
+size_t arena_estimate(const mdas_system_desc *d) {
+    int nc = 1;
+    for (int k = 0; k < 3; ++k) nc *= std::max(3, (int)std::floor(d->box[k] / d->rc));
+    const double mean = (double)d->n_beads / nc;
+    const size_t capc = std::max(32, (int)std::ceil(4.0 * mean / 32.0) * 32);
+    const size_t n = d->n_beads, vsz = d->precision == MDAS_FP64 ? 32 : 16;
+    const size_t nbb = (n + BEAD_BLOCK - 1) / BEAD_BLOCK;
+    size_t t = sizeof(Params) + sizeof(Counters) + 16 * n + vsz * n + 24 * n + 8 * std::max(d->n_lipids, 1) +
+               8 * nc + 24 * nc * capc + 4 * n + 16 * nc + 24 * nbb + 32 * nc + 16 * n + vsz * n +
+               (16 + 8 + 72 + 4 + 128 + 64) * (size_t)MAX_ROUND_TRIALS + sizeof(TrialRec) * (size_t)LOG_CAP + 512 +
+               32 * MAX_DRAW_STEPS + 24 * n;
+    return t + 40 * 256;
+}
+
+}  // namespace
+
+struct mdas_server {
+    size_t budget = 0, in_use = 0;
+    int max_active = 0;
+    int md_quantum = 25;
+    int want_state = 0;
+    cudaStream_t stream = nullptr;
+    std::deque<PendingJob> queue;
+    std::vector<ActiveJob> active;
+    std::vector<mdas_job_result> finished;
+    Batch md_batch, swap_batch;
+    int64_t next_id = 1;
+    std::chrono::steady_clock::time_point t0;
+    std::multimap<size_t, void *> pool;      // freed arenas by size, reused by later jobs
+    std::map<void *, size_t> sizes;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+void *pool_alloc(size_t bytes, void *, void *ctx) {
+    mdas_server *sv = (mdas_server *)ctx;
+    auto it = sv->pool.lower_bound(bytes);
+    if (it != sv->pool.end() && it->first <= 2 * bytes) {
+        void *p = it->second;
+        sv->pool.erase(it);
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    sv->sizes[p] = bytes;
+    return p;
+}
+
+void pool_free(void *p, void *, void *ctx) {
+    mdas_server *sv = (mdas_server *)ctx;
+    sv->pool.emplace(sv->sizes[p], p);
+}
+
+uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
+    const unsigned char *c = (const unsigned char *)data;
+    for (size_t k = 0; k < n; ++k) { h ^= c[k]; h *= 1099511628211ull; }
+    return h;
+}
+
+mdas_status finish_job(mdas_server *sv, ActiveJob &a) {
+    mdas_system *s = a.sys;
+    mdas_job_result r{};
+    r.job_id = a.p.id;
+    r.kind = a.p.job.kind;
+    r.status = MDAS_OK;
+    r.t_submit = a.p.t_submit;
+    r.t_admit = a.t_admit;
+    mdas_counters c{};
+    mdas_status st = mdas_get_counters(s, &c);
+    if (st != MDAS_OK) return st;
+    r.t_done = sv->now();
+    r.md_steps = c.md_steps;
+    r.trials = c.trials;
+    r.accepted = c.accepted;
+    r.w = a.w;
+    r.move_accepted = a.move_accepted;
+    if (sv->want_state) {
+        std::vector<uint32_t> pu(3ull * s->n);
+        std::vector<double> v(3ull * s->n);
+        std::vector<int32_t> lt(std::max(s->n_lip, 1));
+        mdas_state_view sv_{pu.data(), nullptr, v.data(), lt.data(), 0, 0, 0, 0};
+        st = mdas_get_state(s, &sv_);
+        if (st != MDAS_OK) return st;
+        uint64_t h = 1469598103934665603ull;
+        h = fnv1a(h, pu.data(), 4ull * pu.size());
+        h = fnv1a(h, v.data(), 8ull * v.size());
+        h = fnv1a(h, lt.data(), 4ull * s->n_lip);
+        r.state_hash = h;
+    }
+    sv->in_use -= a.p.footprint;
+    mdas_destroy_system(s);
+    a.sys = nullptr;
+    sv->finished.push_back(r);
+    return MDAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mdas_status mdas_server_create(size_t hbm_budget_bytes, int32_t max_active, int32_t md_quantum, int32_t keep_state_hash,
+                               void *cuda_stream, mdas_server **out) {
+    if (!out || hbm_budget_bytes == 0 || max_active <= 0 || md_quantum <= 0)
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_create: bad argument");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    if (!stream) {
+        cudaError_t e = shared_stream(&stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "server_create: stream");
+    }
+    mdas_server *sv = new mdas_server();
+    sv->budget = hbm_budget_bytes;
+    sv->max_active = max_active;
+    sv->md_quantum = md_quantum;
+    sv->want_state = keep_state_hash;
+    sv->stream = stream;
+    sv->t0 = std::chrono::steady_clock::now();
+    *out = sv;
+    return MDAS_OK;
+}
+
+void mdas_server_destroy(mdas_server *sv) {
+    if (!sv) return;
+    for (auto &a : sv->active)
+        if (a.sys) mdas_destroy_system(a.sys);
+    cudaStreamSynchronize(sv->stream);
+    for (auto &kv : sv->sizes) cudaFree(kv.first);
+    destroy_batch(&sv->md_batch);
+    destroy_batch(&sv->swap_batch);
+    delete sv;
+}
+
+mdas_status mdas_server_submit(mdas_server *sv, const mdas_system_desc *d, const mdas_job *job, int64_t *job_id) {
+    if (!sv || !d || !job || d->n_beads <= 0 || !d->pos || !d->lipid_type || !d->lipid_bead_type || !d->eps ||
+        !d->sigma || !d->charge)
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit: bad argument");
+    if (job->kind < MDAS_JOB_SWAPS || job->kind > MDAS_JOB_MDAS || job->n < 0 ||
+        (job->kind == MDAS_JOB_MDAS && (job->n_pairs < 0 || job->n_pairs > MAX_PAIRS || job->n_lambda < 1 || job->md_per_lambda < 0)))
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit: bad job");
+    PendingJob p;
+    p.id = sv->next_id++;
+    p.job = *job;
+    p.t_submit = sv->now();
+    p.footprint = arena_estimate(d);
+    if (p.footprint > sv->budget) return fail(nullptr, MDAS_ERR_OOM, "server_submit: the job alone exceeds the memory budget");
+    const size_t n = d->n_beads, nl = d->n_lipids, nbt = d->n_bead_types;
+    p.pos.assign(d->pos, d->pos + 3 * n);
+    if (d->vel) p.vel.assign(d->vel, d->vel + 3 * n);
+    p.eps.assign(d->eps, d->eps + nbt * nbt);
+    p.sigma.assign(d->sigma, d->sigma + nbt * nbt);
+    p.charge.assign(d->charge, d->charge + nbt);
+    if (d->lipid_first_bead) p.first.assign(d->lipid_first_bead, d->lipid_first_bead + nl);
+    p.ltype.assign(d->lipid_type, d->lipid_type + nl);
+    p.lbt.assign(d->lipid_bead_type, d->lipid_bead_type + (size_t)d->n_lipid_types * d->beads_per_lipid);
+    if (d->n_bonds) p.bonds.assign(d->bonds, d->bonds + 2 * d->n_bonds);
+    if (d->n_angles) p.angles.assign(d->angles, d->angles + 3 * d->n_angles);
+    p.d = *d;
+    if (job_id) *job_id = p.id;
+    sv->queue.push_back(std::move(p));
+    return MDAS_OK;
+}
+
+mdas_status mdas_server_run(mdas_server *sv, int32_t max_rounds, int32_t *n_active, int32_t *n_queued) {
+    if (!sv || max_rounds < 0) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_run: bad argument");
+    for (int r = 0; r < max_rounds; ++r) {
+        // admission in arrival order: a free slot and room in the memory budget
+        while (!sv->queue.empty() && (int)sv->active.size() < sv->max_active &&
+               sv->in_use + sv->queue.front().footprint <= sv->budget) {
+            PendingJob p = std::move(sv->queue.front());
+            sv->queue.pop_front();
+            mdas_system_desc d = p.d;
+            d.pos = p.pos.data();
+            d.vel = p.vel.empty() ? nullptr : p.vel.data();
+            d.eps = p.eps.data(); d.sigma = p.sigma.data(); d.charge = p.charge.data();
+            d.lipid_first_bead = p.first.empty() ? nullptr : p.first.data();
+            d.lipid_type = p.ltype.data();
+            d.lipid_bead_type = p.lbt.data();
+            d.bonds = p.bonds.empty() ? nullptr : p.bonds.data();
+            d.angles = p.angles.empty() ? nullptr : p.angles.data();
+            d.cuda_stream = sv->stream;
+            d.dev_alloc = pool_alloc;
+            d.dev_free = pool_free;
+            d.alloc_ctx = sv;
+            ActiveJob a;
+            mdas_status st = mdas_create_system(&d, &a.sys);
+            if (st != MDAS_OK) return st;
+            a.t_admit = sv->now();
+            a.remaining = p.job.kind == MDAS_JOB_MD ? p.job.n : 1;
+            sv->in_use += p.footprint;
+            a.p = std::move(p);
+            sv->active.push_back(std::move(a));
+        }
+        if (sv->active.empty()) break;
+        // MD jobs: one batched quantum of steps
+        std::vector<mdas_system *> mdv;
+        long long q = sv->md_quantum;
+        for (auto &a : sv->active)
+            if (a.p.job.kind == MDAS_JOB_MD && a.remaining > 0) { mdv.push_back(a.sys); q = std::min(q, a.remaining); }
+        if (!mdv.empty()) {
+            mdas_status st = refill_batch(sv->md_batch, mdv);
+            if (st == MDAS_OK) st = run_md(mdv[0], sv->md_batch, q, 0);
+            if (st != MDAS_OK) return st;
+            for (auto &a : sv->active)
+                if (a.p.job.kind == MDAS_JOB_MD && a.remaining > 0) {
+                    a.remaining -= q;
+                    if (a.remaining == 0) a.done = true;
+                }
+        }
+        // swap jobs: one batched evaluation per trial count
+        std::map<int, std::vector<ActiveJob *>> groups;
+        for (auto &a : sv->active)
+            if (a.p.job.kind == MDAS_JOB_SWAPS && !a.done) groups[a.p.job.n].push_back(&a);
+        for (auto &g : groups) {
+            std::vector<mdas_system *> v;
+            for (auto *a : g.second)
+                if (a->sys->n_lip > 0) v.push_back(a->sys);
+            if (!v.empty() && g.first > 0) {
+                mdas_status st = refill_batch(sv->swap_batch, v);
+                if (st == MDAS_OK) st = run_trials(v[0], sv->swap_batch, g.first, nullptr);
+                if (st != MDAS_OK) return st;
+            }
+            for (auto *a : g.second) a->done = true;
+        }
+        // MDAS jobs: one move each
+        for (auto &a : sv->active)
+            if (a.p.job.kind == MDAS_JOB_MDAS && !a.done) {
+                mdas_move_result mr;
+                mdas_status st = a.sys->n_lip > 0 ? mdas_alchemical_move(a.sys, a.p.job.n_pairs, a.p.job.n_lambda,
+                                                                         a.p.job.md_per_lambda, nullptr, &mr)
+                                                  : MDAS_OK;
+                if (st != MDAS_OK) return st;
+                if (a.sys->n_lip > 0) { a.w = mr.w; a.move_accepted = mr.accepted; }
+                a.done = true;
+            }
+        // completion: results, memory back to the pool, slots free
+        {
+            cudaError_t e = cudaStreamSynchronize(sv->stream);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "server_run");
+        }
+        std::vector<ActiveJob> keep;
+        for (auto &a : sv->active) {
+            if (a.done) {
+                mdas_status st = finish_job(sv, a);
+                if (st != MDAS_OK) return st;
+            } else {
+                keep.push_back(std::move(a));
+            }
+        }
+        sv->active.swap(keep);
+    }
+    if (n_active) *n_active = (int32_t)sv->active.size();
+    if (n_queued) *n_queued = (int32_t)sv->queue.size();
+    return MDAS_OK;
+}
+
+mdas_status mdas_server_results(mdas_server *sv, mdas_job_result *out, int32_t cap, int32_t *n) {
+    if (!sv || !n || cap < 0 || (cap > 0 && !out)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_results: bad argument");
+    const int m = std::min<int>(cap, (int)sv->finished.size());
+    for (int k = 0; k < m; ++k) out[k] = sv->finished[k];
+    sv->finished.erase(sv->finished.begin(), sv->finished.begin() + m);
+    *n = m;
+    return MDAS_OK;
+}
+
+double mdas_server_clock(const mdas_server *sv) { return sv ? sv->now() : 0.0; }
+
+size_t mdas_system_footprint(const mdas_system_desc *d) {
+    if (!d || d->n_beads <= 0 || !(d->rc > 0)) return 0;
+    return arena_estimate(d);
 }
 
 }  // extern "C"

@@ -83,7 +83,8 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_swap_trials", "mdas_trial_log", "mdas_alchemical_move", "mdas_delta_energy", "mdas_get_state",
            "mdas_set_state", "mdas_cell_list", "mdas_batch_run", "mdas_philox", "mdas_set_kernel_timing",
            "mdas_pair_kernel_time", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
-           "mdas_forces_noalloc"]
+           "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
+           "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint"]
 
 
 def library_path() -> str:
@@ -141,6 +142,40 @@ def _current_stream():
     return int(torch.cuda.current_stream().cuda_stream)
 
 
+def make_desc(m, precision=MDAS_FP32, tau_t=None, dt=None, temperature=None, seed=None, system_id=None,
+              eps_rf=None):
+    """mdas_system_desc of a `synth.Membrane`; returns (desc, arrays kept alive)."""
+    k = dict(pos=np.ascontiguousarray(m.pos, np.float64), vel=np.ascontiguousarray(m.vel, np.float64),
+             first=np.ascontiguousarray(m.lipid_first_bead, np.int32),
+             lt=np.ascontiguousarray(m.lipid_type, np.int32),
+             lbt=np.ascontiguousarray(m.lipid_bead_type, np.int32),
+             eps=np.ascontiguousarray(m.eps, np.float64), sig=np.ascontiguousarray(m.sigma, np.float64),
+             q=np.ascontiguousarray(m.charge, np.float64), bonds=np.ascontiguousarray(m.bonds, np.int32),
+             angles=np.ascontiguousarray(m.angles, np.int32))
+    d = Desc()
+    d.n_beads, d.n_lipids = m.n_beads, m.n_lipids
+    d.beads_per_lipid = m.lipid_bead_type.shape[1]
+    d.n_bead_types, d.n_lipid_types = m.eps.shape[0], m.lipid_bead_type.shape[0]
+    d.box = (C.c_double * 3)(*[float(x) for x in m.box])
+    d.pos, d.vel = _p(k["pos"]), _p(k["vel"])
+    d.lipid_first_bead, d.lipid_type, d.lipid_bead_type = _p(k["first"]), _p(k["lt"]), _p(k["lbt"])
+    d.water_bead_type = int(m.water_bead_type)
+    d.eps, d.sigma, d.charge = _p(k["eps"]), _p(k["sig"]), _p(k["q"])
+    d.bonds, d.n_bonds = _p(k["bonds"]), int(m.bonds.shape[0])
+    d.angles, d.n_angles = _p(k["angles"]), int(m.angles.shape[0])
+    d.kb, d.b0, d.ktheta, d.theta0_deg = m.kb, m.b0, m.ktheta, m.theta0_deg
+    d.rc, d.eps_r = m.rc, m.eps_r
+    d.eps_rf = m.eps_rf if eps_rf is None else eps_rf
+    d.temperature = m.temperature if temperature is None else temperature
+    d.dt = m.dt if dt is None else dt
+    d.tau_t = m.tau_t if tau_t is None else tau_t
+    d.mass = m.mass
+    d.seed = int(m.seed if seed is None else seed)
+    d.system_id = int(m.system_id if system_id is None else system_id)
+    d.precision = precision
+    return d, k
+
+
 class System:
     """One device-resident membrane system built from a `synth.Membrane`."""
 
@@ -151,34 +186,7 @@ class System:
         self.n = m.n_beads
         self.n_lipids = m.n_lipids
         self.precision = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
-        k = dict(pos=np.ascontiguousarray(m.pos, np.float64), vel=np.ascontiguousarray(m.vel, np.float64),
-                 first=np.ascontiguousarray(m.lipid_first_bead, np.int32),
-                 lt=np.ascontiguousarray(m.lipid_type, np.int32),
-                 lbt=np.ascontiguousarray(m.lipid_bead_type, np.int32),
-                 eps=np.ascontiguousarray(m.eps, np.float64), sig=np.ascontiguousarray(m.sigma, np.float64),
-                 q=np.ascontiguousarray(m.charge, np.float64), bonds=np.ascontiguousarray(m.bonds, np.int32),
-                 angles=np.ascontiguousarray(m.angles, np.int32))
-        d = Desc()
-        d.n_beads, d.n_lipids = self.n, self.n_lipids
-        d.beads_per_lipid = m.lipid_bead_type.shape[1]
-        d.n_bead_types, d.n_lipid_types = m.eps.shape[0], m.lipid_bead_type.shape[0]
-        d.box = (C.c_double * 3)(*[float(x) for x in m.box])
-        d.pos, d.vel = _p(k["pos"]), _p(k["vel"])
-        d.lipid_first_bead, d.lipid_type, d.lipid_bead_type = _p(k["first"]), _p(k["lt"]), _p(k["lbt"])
-        d.water_bead_type = int(m.water_bead_type)
-        d.eps, d.sigma, d.charge = _p(k["eps"]), _p(k["sig"]), _p(k["q"])
-        d.bonds, d.n_bonds = _p(k["bonds"]), int(m.bonds.shape[0])
-        d.angles, d.n_angles = _p(k["angles"]), int(m.angles.shape[0])
-        d.kb, d.b0, d.ktheta, d.theta0_deg = m.kb, m.b0, m.ktheta, m.theta0_deg
-        d.rc, d.eps_r = m.rc, m.eps_r
-        d.eps_rf = m.eps_rf if eps_rf is None else eps_rf
-        d.temperature = m.temperature if temperature is None else temperature
-        d.dt = m.dt if dt is None else dt
-        d.tau_t = m.tau_t if tau_t is None else tau_t
-        d.mass = m.mass
-        d.seed = int(m.seed if seed is None else seed)
-        d.system_id = int(m.system_id if system_id is None else system_id)
-        d.precision = self.precision
+        d, k = make_desc(m, self.precision, tau_t, dt, temperature, seed, system_id, eps_rf)
         self.stream = _current_stream() if stream is None else int(stream)
         d.cuda_stream = self.stream or None
         if torch_allocator:
@@ -310,6 +318,75 @@ def forces_noalloc(system, pos_fixed_ptr, lipid_type_ptr, f_out_ptr, stream=None
                                    C.c_void_p(f_out_ptr))
     if st != 0:
         raise MdasError(st, "forces_noalloc failed")
+
+
+JOB_SWAPS, JOB_MD, JOB_MDAS = 0, 1, 2
+
+
+class Job(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("n_pairs", C.c_int32), ("n_lambda", C.c_int32),
+                ("md_per_lambda", C.c_int32)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("job_id", C.c_int64), ("kind", C.c_int32), ("status", C.c_int32), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("md_steps", C.c_int64), ("trials", C.c_int64),
+                ("accepted", C.c_int64), ("w", C.c_double), ("move_accepted", C.c_int32),
+                ("state_hash", C.c_uint64)]
+
+
+class Server:
+    """The library's request loop (mdas_server_*): continuous batching of
+    jobs on device-resident patches, admission by device-memory footprint."""
+
+    def __init__(self, budget_bytes, max_active, md_quantum=25, keep_state_hash=False, stream=None):
+        L = lib()
+        L.mdas_server_clock.restype = C.c_double
+        L.mdas_server_destroy.restype = None
+        self._ptr = C.c_void_p()
+        _check(L.mdas_server_create(C.c_size_t(int(budget_bytes)), int(max_active), int(md_quantum),
+                                    int(bool(keep_state_hash)), C.c_void_p(stream) if stream else None,
+                                    C.byref(self._ptr)))
+
+    def submit(self, m, kind, n=0, n_pairs=8, n_lambda=10, md_per_lambda=5, precision=MDAS_FP32):
+        d, keep = make_desc(m, precision)
+        j = Job(int(kind), int(n), int(n_pairs), int(n_lambda), int(md_per_lambda))
+        jid = C.c_int64()
+        _check(lib().mdas_server_submit(self._ptr, C.byref(d), C.byref(j), C.byref(jid)))
+        return jid.value
+
+    def run(self, rounds=1):
+        a, q = C.c_int32(), C.c_int32()
+        _check(lib().mdas_server_run(self._ptr, int(rounds), C.byref(a), C.byref(q)))
+        return a.value, q.value
+
+    def results(self, cap=4096):
+        out = (JobResult * cap)()
+        n = C.c_int32()
+        _check(lib().mdas_server_results(self._ptr, out, int(cap), C.byref(n)))
+        return [{k: getattr(out[i], k) for k, _ in JobResult._fields_} for i in range(n.value)]
+
+    def clock(self):
+        return lib().mdas_server_clock(self._ptr)
+
+    def close(self):
+        if getattr(self, "_ptr", None):
+            lib().mdas_server_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint(m, precision=MDAS_FP32):
+    """Device bytes a system of this membrane occupies."""
+    d, keep = make_desc(m, precision)
+    L = lib()
+    L.mdas_system_footprint.restype = C.c_size_t
+    return int(L.mdas_system_footprint(C.byref(d)))
 
 
 def batch_run(systems, md_steps, swap_trials):

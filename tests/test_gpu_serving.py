@@ -1,0 +1,82 @@
+"""Serving loop (mdas_server_*): continuous batching of MD, swap and MDAS jobs
+on device-resident patches.  Each job's result must be the same alone and in
+the mix, admission must respect the slot count and the memory budget."""
+import numpy as np
+import pytest
+
+from paper_2005_08348_gb300 import mdas, synth
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+def patches():
+    return [synth.patch(n, 2 + k % 2, seed=300 + k, system_id=k) for k, n in enumerate([130, 200, 256, 310, 180, 420])]
+
+
+def jobs(ps):
+    kinds = [(mdas.JOB_MD, 60), (mdas.JOB_SWAPS, 64), (mdas.JOB_MDAS, 0), (mdas.JOB_SWAPS, 64),
+             (mdas.JOB_MD, 35), (mdas.JOB_MDAS, 0)]
+    return [(p, k, n) for p, (k, n) in zip(ps, kinds)]
+
+
+def run(server, js, stagger):
+    """Submit the jobs (two per round when staggered, else all at once) and
+    run rounds until every job is done; results in submission order."""
+    ids = []
+    pending = list(js)
+    res = {}
+    for _ in range(10000):
+        for _ in range(2 if stagger else len(pending)):
+            if pending:
+                p, k, n = pending.pop(0)
+                ids.append(server.submit(p, k, n=n, n_pairs=2, n_lambda=3, md_per_lambda=2))
+        active, queued = server.run(1)
+        for r in server.results():
+            res[r["job_id"]] = r
+        if not pending and active == 0 and queued == 0:
+            break
+    return [res[i] for i in ids]
+
+
+def test_results_same_alone_and_in_the_mix():
+    ps = patches()
+    js = jobs(ps)
+    mix = run(mdas.Server(4 * GB, max_active=3, md_quantum=10, keep_state_hash=True), js, stagger=True)
+    for (p, k, n), r in zip(js, mix):
+        alone = run(mdas.Server(4 * GB, max_active=1, md_quantum=25, keep_state_hash=True), [(p, k, n)], stagger=False)[0]
+        assert r["state_hash"] == alone["state_hash"], (k, n)
+        for key in ("md_steps", "trials", "accepted", "w", "move_accepted"):
+            assert r[key] == alone[key], key
+    kinds = [r["kind"] for r in mix]
+    assert sorted(set(kinds)) == [0, 1, 2]
+    assert all(r["t_done"] >= r["t_admit"] >= r["t_submit"] for r in mix)
+    md = [r for r in mix if r["kind"] == mdas.JOB_MD]
+    assert [r["md_steps"] for r in md] == [60, 35]
+    sw = [r for r in mix if r["kind"] == mdas.JOB_SWAPS]
+    assert all(r["trials"] == 64 for r in sw)
+
+
+def test_admission_by_slots_and_memory():
+    ps = patches()
+    sv = mdas.Server(4 * GB, max_active=2, md_quantum=5)
+    for p in ps:
+        sv.submit(p, mdas.JOB_MD, n=20)
+    seen = []
+    for _ in range(1000):
+        a, q = sv.run(1)
+        seen.append(a)
+        if a == 0 and q == 0:
+            break
+    assert max(seen) <= 2 and len(sv.results()) == len(ps)
+    # a budget that holds one system at a time admits them one by one
+    big = max(mdas.footprint(p) for p in ps[:3])
+    sv = mdas.Server(int(1.5 * big), max_active=8, md_quantum=5)
+    for p in ps[:3]:
+        sv.submit(p, mdas.JOB_MD, n=10)
+    a, q = sv.run(1)
+    assert a == 1 and q == 2
+    with pytest.raises(mdas.MdasError) as e:
+        mdas.Server(mdas.footprint(ps[0]) // 2, max_active=2).submit(ps[0], mdas.JOB_MD, n=5)
+    assert e.value.status == 2
