@@ -383,9 +383,11 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
     Real *tf6 = tf12 + 256;
     Real *tqq = tf6 + 256;
     uint16_t *q = reinterpret_cast<uint16_t *>(tqq + 256);                     // [QCAP][PAIR_THREADS]
+    uint16_t *lst = q + QCAP * PAIR_THREADS;                                   // hits grouped by i-bead
     long long *red = reinterpret_cast<long long *>(q);                         // aliases q after the queues drain
 
     __shared__ int cst[27], ccnt[27], coff[28];
+    __shared__ int cntq[PAIR_THREADS], htot[PAIR_THREADS], hbase[PAIR_THREADS];
     __shared__ double ered[3][PAIR_THREADS];
     __shared__ Real kered[2][PAIR_THREADS];
     for (int k = t; k < 256; k += PAIR_THREADS) {
@@ -455,9 +457,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
             }
         }
 
-        auto flush = [&](int count) {
-            for (int e = 0; e < count; ++e) {
-                const int j = q[e * PAIR_THREADS + t];
+        auto eval1 = [&](int j) {
+            {
                 const int4 ij = si[j];
                 Real dx, dy, dz;
                 if (F32) {
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
                     const double ez = (double)wrap_diff(oiz, ij.z) * P.qs[2];
                     keep = keep && (ex * ex + ey * ey + ez * ez < P.rc2);
                 }
-                if (!keep) continue;
+                if (!keep) return;
                 const int ta = tai * 16 + meta_ta(mj);
                 Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
                 if (LAM) {
@@ -523,6 +524,9 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
                 }
             }
         };
+        auto flush = [&](int count) {
+            for (int e = 0; e < count; ++e) eval1(q[e * PAIR_THREADS + t]);
+        };
 
         for (int base = 0; base < M; base += STAGE_CAP) {
             const int mc = min(STAGE_CAP, M - base);
@@ -559,7 +563,29 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
                 q[nq * PAIR_THREADS + t] = (uint16_t)j;
                 nq += (int)((r2 < rc2) & (r2 > (Real)0));
             }
-            flush(nq);
+            // evaluate the chunk's hits with every bead's hits spread evenly over
+            // its streams (a fixed assignment, so the sums stay deterministic)
+            cntq[t] = js < NS ? nq : 0;
+            __syncthreads();
+            int pre = 0, tot = 0;
+            if (js < NS)
+                for (int s2 = 0; s2 < NS; ++s2) {
+                    const int c2 = cntq[s2 * IW + il];
+                    pre += s2 < js ? c2 : 0;
+                    tot += c2;
+                }
+            if (js == 0) htot[il] = tot;
+            __syncthreads();
+            if (t == 0) {
+                int o = 0;
+                for (int k = 0; k < IW; ++k) { hbase[k] = o; o += htot[k]; }
+            }
+            __syncthreads();
+            if (js < NS)
+                for (int e = 0; e < nq; ++e) lst[hbase[il] + pre + e] = q[e * PAIR_THREADS + t];
+            __syncthreads();
+            if (js < NS)
+                for (int h = js; h < tot; h += NS) eval1(lst[hbase[il] + h]);
         }
 
         // the updating thread (stream 0) fetches the bead's velocity before the barrier
@@ -658,7 +684,7 @@ template <typename Real>
 static size_t pair_smem() {
     static_assert(3 * PAIR_THREADS * sizeof(long long) <= sizeof(uint16_t) * QCAP * PAIR_THREADS, "red fits in q");
     return sizeof(StagedPos<Real>) * STAGE_CAP + sizeof(int4) * STAGE_CAP + sizeof(Real) * 3 * 256 +
-           sizeof(uint16_t) * QCAP * PAIR_THREADS;
+           2 * sizeof(uint16_t) * QCAP * PAIR_THREADS;
 }
 
 template <typename Real, bool LAM, bool ENERGY, bool INTEG>

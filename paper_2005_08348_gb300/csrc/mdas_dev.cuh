@@ -14,7 +14,7 @@ struct __align__(32) Dbl4 {
 constexpr int MAXT = 16;               // bead types, lipid types, beads per lipid
 constexpr int PAIR_THREADS = 128;      // threads per cell in the pair kernel
 constexpr int STAGE_CAP = 384;         // neighbour beads staged per chunk (27 cells)
-constexpr int QCAP = 32;               // per-thread hit queue of the pair kernel
+constexpr int QCAP = 24;               // per-thread hit queue of the pair kernel
 constexpr int BEAD_BLOCK = 128;        // beads per block of per-bead kernels
 constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
