@@ -214,7 +214,7 @@ mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
  * code living between the allocations of a framework that owns the device
  * heap, or a real-time loop that must not meet cudaMalloc's implicit device
  * synchronisation.  It calls no cudaMalloc, cudaFree or allocating library
- * routine; its scratch is one fixed array (about 7 MB) that every GPU which
+ * routine; its scratch is one fixed array (about 8 MB) that every GPU which
  * loads the library holds until the process exits.
  *
  * d supplies the force field, box and precision as for mdas_create_system
@@ -225,7 +225,7 @@ mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
  * stream) and the call returns after f_out is written.  The result equals
  * mdas_forces for the same state.
  *
- * Limits: n_beads <= 16384, at most 4096 cells (floor(L/rc) per edge), at
+ * Limits: n_beads <= 16384, at most 2048 cells (floor(L/rc) per edge), at
  * most 64 beads in a cell.  Errors: MDAS_ERR_INVALID_ARG for a NULL pointer,
  * a size beyond these limits or a lipid type outside the table;
  * MDAS_ERR_UNSTABLE when a cell holds more than 64 beads; MDAS_ERR_CUDA.

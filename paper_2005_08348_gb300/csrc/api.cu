@@ -638,7 +638,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.ltype, 4ull * std::max(nl, 1)},
         {(void **)&H.cell_count, 4ull * P.n_cells}, {(void **)&H.cell_n, 4ull * P.n_cells},
         {(void **)&H.tmp_ids, 4ull * nslot}, {(void **)&H.sorted_id, 4ull * nslot}, {(void **)&H.sidx, 4ull * n},
-        {(void **)&H.spos, 16ull * nslot},
+        {(void **)&H.spos, 16ull * nslot}, {(void **)&H.bforce, vsz * nslot},
         {(void **)&H.ke_part, 16ull * P.n_cells}, {(void **)&H.bpart, 24ull * nbb}, {(void **)&H.epart, 32ull * P.n_cells},
         {(void **)&H.pos_snap, 16ull * n}, {(void **)&H.vel_snap, vsz * n},
         {(void **)&H.ltype_snap, 4ull * std::max(nl, 1)},
@@ -1148,7 +1148,7 @@ size_t arena_estimate(const mdas_system_desc *d) {
     const size_t n = d->n_beads, vsz = d->precision == MDAS_FP64 ? 32 : 16;
     const size_t nbb = (n + BEAD_BLOCK - 1) / BEAD_BLOCK;
     size_t t = sizeof(Params) + sizeof(Counters) + 16 * n + vsz * n + 24 * n + 8 * std::max(d->n_lipids, 1) +
-               8 * nc + 24 * nc * capc + 4 * n + 16 * nc + 24 * nbb + 32 * nc + 16 * n + vsz * n +
+               8 * nc + 24 * nc * capc + vsz * nc * capc + 4 * n + 16 * nc + 24 * nbb + 32 * nc + 16 * n + vsz * n +
                (16 + 8 + 72 + 4 + 128 + 64) * (size_t)MAX_ROUND_TRIALS + sizeof(TrialRec) * (size_t)LOG_CAP + 512 +
                32 * MAX_DRAW_STEPS + 24 * n;
     return t + 40 * 256;

@@ -56,10 +56,16 @@ __global__ void k_cell_count(const SysDev *__restrict__ sys, const int2 *__restr
     count_into_cell(S, P, i, cell_of_pos(P, S.pos[i]));
 }
 
+template <typename Real>
+__device__ void bonded_force_pos(const SysDev &S, const Params &P, int l, int k, uint4 pi, Real f[3]);
+
 // One warp per cell: order the cell's beads by id (rank = number of smaller
 // ids in the cell, computed with warp shuffles), gather their positions into
-// cell order, publish the count and clear the counter for the next step.
+// cell order with each bead's bonded force, publish the count and clear the
+// counter for the next step.
+template <typename Real>
 __device__ void finish_cell(const SysDev &S, const Params &P, int c, int lane) {
+    using V4 = typename Vec4<Real>::T;
     const int cnt = min(S.cell_count[c], P.capc);
     const int base = c * P.capc;
     for (int a0 = 0; a0 < cnt; a0 += 32) {
@@ -71,9 +77,16 @@ __device__ void finish_cell(const SysDev &S, const Params &P, int c, int lane) {
             for (int k = 0; k < 32; ++k) rank += __shfl_sync(0xffffffffu, other, k) < id;
         }
         if (a < cnt) {
+            const uint4 pi = S.pos[id];
             S.sorted_id[base + rank] = id;
             S.sidx[id] = base + rank;
-            S.spos[base + rank] = S.pos[id];
+            S.spos[base + rank] = pi;
+            Real f[3] = {(Real)0, (Real)0, (Real)0};
+            const int l = meta_lip(pi.w);
+            if (l >= 0) bonded_force_pos<Real>(S, P, l, meta_k(pi.w), pi, f);
+            V4 b;
+            b.x = f[0]; b.y = f[1]; b.z = f[2]; b.w = (Real)0;
+            reinterpret_cast<V4 *>(S.bforce)[base + rank] = b;
         }
     }
     __syncwarp();
@@ -96,7 +109,7 @@ __global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__rest
         return;
     }
     const int c = bm.y + (threadIdx.x >> 5);
-    if (c < P.n_cells) finish_cell(S, P, c, threadIdx.x & 31);
+    if (c < P.n_cells) finish_cell<Real>(S, P, c, threadIdx.x & 31);
 }
 
 // counted: the step kernel has already counted the current positions into cells
@@ -273,44 +286,41 @@ __device__ __forceinline__ void sep(const Params &P, uint4 a, uint4 b, Real d[3]
     }
 }
 
-// Bonded force on bead i (local index k of lipid l) from term `term` of its
-// terms: its bonds (harmonic, to each partner) first, then every angle
-// containing it (cosine-harmonic).  Positions come from the cell-ordered
-// copy (stable during a step).
+// All bonded terms of bead (l, k) from the id-ordered positions (stable while
+// the cell list is finished).
 template <typename Real>
-__device__ void bonded_term(const SysDev &S, const Params &P, int l, int k, uint4 pi, int term, Real f[3]) {
+__device__ void bonded_force_pos(const SysDev &S, const Params &P, int l, int k, uint4 pi, Real f[3]) {
     const int base = l * P.bpl;
-    if (term < P.nbond[k]) {
-        const uint4 pj = S.spos[S.sidx[base + P.bpart[k][term]]];
+    for (int b = 0; b < P.nbond[k]; ++b) {
         Real d[3];
-        sep<Real>(P, pi, pj, d);
+        sep<Real>(P, pi, S.pos[base + P.bpart[k][b]], d);
         const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
         f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
-        return;
     }
-    const int a = term - P.nbond[k];
-    const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
-    const uint4 qi = li == k ? pi : S.spos[S.sidx[base + li]];
-    const uint4 qj = lj == k ? pi : S.spos[S.sidx[base + lj]];
-    const uint4 qk = lk == k ? pi : S.spos[S.sidx[base + lk]];
-    Real A[3], B[3];
-    sep<Real>(P, qi, qj, A);
-    sep<Real>(P, qk, qj, B);
-    const Real la2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
-    const Real lb2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-    const Real iab = (Real)1 / sqrt(la2 * lb2);
-    const Real cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * iab;
-    const Real pre = -(Real)P.kth * (cs - (Real)P.cos0);
-    const Real ia2 = (Real)1 / la2, ib2 = (Real)1 / lb2;
-    for (int d = 0; d < 3; ++d) {
-        const Real dci = B[d] * iab - cs * A[d] * ia2;
-        const Real dck = A[d] * iab - cs * B[d] * ib2;
-        Real g;
-        if (k == li) g = dci;
-        else if (k == lk) g = dck;
-        else g = -(dci + dck);
-        f[d] += pre * g;
+    for (int a = 0; a < P.nang[k]; ++a) {
+        const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
+        const uint4 qi = li == k ? pi : S.pos[base + li];
+        const uint4 qj = lj == k ? pi : S.pos[base + lj];
+        const uint4 qk = lk == k ? pi : S.pos[base + lk];
+        Real A[3], B[3];
+        sep<Real>(P, qi, qj, A);
+        sep<Real>(P, qk, qj, B);
+        const Real la2 = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+        const Real lb2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        const Real iab = (Real)1 / sqrt(la2 * lb2);
+        const Real cs = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * iab;
+        const Real pre = -(Real)P.kth * (cs - (Real)P.cos0);
+        const Real ia2 = (Real)1 / la2, ib2 = (Real)1 / lb2;
+        for (int d = 0; d < 3; ++d) {
+            const Real dci = B[d] * iab - cs * A[d] * ia2;
+            const Real dck = A[d] * iab - cs * B[d] * ib2;
+            Real g;
+            if (k == li) g = dci;
+            else if (k == lk) g = dck;
+            else g = -(dci + dck);
+            f[d] += pre * g;
+        }
     }
 }
 
@@ -365,6 +375,13 @@ __device__ __forceinline__ StagedPos<Real> frame_coords(const Params &P, int ox,
 __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 4294967296.0f); }
 __device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * FIX); }
 
+// Asynchronous 16-byte global -> shared copies (no registers held while in flight).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename Real, bool LAM, bool ENERGY, bool INTEG>
 __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     using V4 = typename Vec4<Real>::T;
@@ -376,6 +393,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr bool F32 = sizeof(Real) == 4;
     constexpr int UNROLL = 4;
+    constexpr int NW = PAIR_THREADS / 32;
 
     StagedPos<Real> *sf = reinterpret_cast<StagedPos<Real> *>(smem);          // [STAGE_CAP]
     int4 *si = reinterpret_cast<int4 *>(sf + STAGE_CAP);                       // [STAGE_CAP] offsets + meta
@@ -383,13 +401,26 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
     Real *tf6 = tf12 + 256;
     Real *tqq = tf6 + 256;
     uint16_t *q = reinterpret_cast<uint16_t *>(tqq + 256);                     // [QCAP][PAIR_THREADS]
-    uint16_t *lst = q + QCAP * PAIR_THREADS;                                   // hits grouped by i-bead
     long long *red = reinterpret_cast<long long *>(q);                         // aliases q after the queues drain
 
     __shared__ int cst[27], ccnt[27], coff[28];
-    __shared__ int cntq[PAIR_THREADS], htot[PAIR_THREADS], hbase[PAIR_THREADS];
+    __shared__ int wcnt[NW];
+    __shared__ Real bx[3][PAIR_THREADS];
+    __shared__ Real blo[3], bhi[3];
     __shared__ double ered[3][PAIR_THREADS];
     __shared__ Real kered[2][PAIR_THREADS];
+    __shared__ __align__(16) V4 sbf[PAIR_THREADS];       // bonded force of the chunk's i-beads
+    __shared__ __align__(16) V4 svel[PAIR_THREADS];      // their velocities (step kernel)
+    __shared__ int sid[PAIR_THREADS];                    // their ids
+
+    if (INTEG && c == 0 && t == 0) {            // once per system: count the step
+        Counters &C = *S.c;
+        if (C.in_at) C.at_step++; else C.step++;
+        C.md_steps++;
+        C.force_evals++;
+        C.ke_pending = 1;
+        C.ke_fresh = 0;
+    }
     for (int k = t; k < 256; k += PAIR_THREADS) {
         if (F32) {
             tf12[k] = (Real)P.f12f[k]; tf6[k] = (Real)P.f6f[k]; tqq[k] = (Real)P.qqf[k];
@@ -398,10 +429,13 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
         }
     }
     const int nx = P.nc[0], ny = P.nc[1], nz = P.nc[2];
-    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    const int cz = c / (nx * ny), cxy = c - cz * nx * ny, cy = cxy / nx, cx = cxy - cy * nx;
     if (t < 27) {
         const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        const int x = (cx + dx + nx) % nx, y = (cy + dy + ny) % ny, z = (cz + dz + nz) % nz;
+        int x = cx + dx, y = cy + dy, z = cz + dz;
+        x += x < 0 ? nx : (x >= nx ? -nx : 0);
+        y += y < 0 ? ny : (y >= ny ? -ny : 0);
+        z += z < 0 ? nz : (z >= nz ? -nz : 0);
         const int cj = (z * ny + y) * nx + x;
         cst[t] = cj * P.capc;
         ccnt[t] = S.cell_n[cj];
@@ -427,125 +461,124 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
     const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
     const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
     const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
-    // parameters used in the inner loops, held in registers
+    const Real lam = LAM ? (Real)S.c->lambda : (Real)0;
     const float qh0 = P.qsh[0], qh1 = P.qsh[1], qh2 = P.qsh[2];
     const float ql0 = P.qsl[0], ql1 = P.qsl[1], ql2 = P.qsl[2];
-    const Real lam = LAM ? (Real)S.c->lambda : (Real)0;
     double elj = 0.0, erf = 0.0, epairs = 0.0;
     Real ke0 = 0, ke1 = 0;
 
     for (int ib = 0; ib < ni; ib += IW) {
         const int i = ib + il;
         const bool valid = i < ni && js < NS;
+        // this thread's i-bead, and for stream 0 its bonded force and velocity
         const uint4 vi = S.spos[ifirst + (i < ni ? i : 0)];
+        if (js == 0 && i < ni) {                 // fetched into shared memory during the sweep
+            const int idpre = S.sorted_id[ifirst + i];
+            sid[t] = idpre;
+            const char *gb = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.bforce) + ifirst + i);
+            for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&sbf[t]) + h, gb + h);
+            if (INTEG) {
+                const char *gv = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.vel) + idpre);
+                for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&svel[t]) + h, gv + h);
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
         const int oix = (int)(vi.x - rx), oiy = (int)(vi.y - ry), oiz = (int)(vi.z - rz);
         StagedPos<Real> pi = frame_coords<Real>(P, oix, oiy, oiz);
+        // bounding box of this chunk's i-beads (staged j-beads farther than rc are dropped)
+        if (js == 0) { bx[0][il] = pi.x; bx[1][il] = pi.y; bx[2][il] = pi.z; }
         if (!valid) pi.x = (Real)1e30;            // an idle lane never finds a partner
         const uint32_t mi = vi.w;
         const int tai = meta_ta(mi), tbi = meta_tb(mi), ki = meta_k(mi);
         const uint32_t lipi = mi >> 12;
         const uint32_t emask = P.excl[ki];
         Real ax = 0, ay = 0, az = 0;
-        // bonded terms of bead i, spread over its streams (they join the
-        // stream partials below)
-        if (valid && lipi != 0) {
-            const int nt = P.nbond[ki] + P.nang[ki];
-            for (int term = js; term < nt; term += NS) {
-                Real fb[3] = {ax, ay, az};
-                bonded_term<Real>(S, P, (int)lipi - 1, ki, vi, term, fb);
-                ax = fb[0]; ay = fb[1]; az = fb[2];
-            }
+        __syncthreads();
+        if (t < 3) {
+            const int nib = min(IW, ni - ib);
+            Real lo = bx[t][0], hi = bx[t][0];
+            for (int k = 1; k < nib; ++k) { lo = min(lo, bx[t][k]); hi = max(hi, bx[t][k]); }
+            blo[t] = lo;
+            bhi[t] = hi;
         }
+        __syncthreads();
+        const Real lox = blo[0], loy = blo[1], loz = blo[2], hix = bhi[0], hiy = bhi[1], hiz = bhi[2];
+        const Real rc2m = rc2 * (Real)1.0001;
 
         auto eval1 = [&](int j) {
-            {
-                const int4 ij = si[j];
-                Real dx, dy, dz;
-                if (F32) {
-                    const float fx = (float)wrap_diff(oix, ij.x), fy = (float)wrap_diff(oiy, ij.y),
-                                fz = (float)wrap_diff(oiz, ij.z);
-                    dx = (Real)fmaf(fx, qh0, fx * ql0);
-                    dy = (Real)fmaf(fy, qh1, fy * ql1);
-                    dz = (Real)fmaf(fz, qh2, fz * ql2);
-                } else {
-                    const StagedPos<Real> pj = sf[j];
-                    dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
-                }
-                const Real r2 = dx * dx + dy * dy + dz * dz;
-                const uint32_t mj = (uint32_t)ij.w;
-                bool keep = !(lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u));
-                if (F32 && r2 >= rc2lo) {
-                    // within float rounding of the cutoff: decide from the exact offsets
-                    const double ex = (double)wrap_diff(oix, ij.x) * P.qs[0];
-                    const double ey = (double)wrap_diff(oiy, ij.y) * P.qs[1];
-                    const double ez = (double)wrap_diff(oiz, ij.z) * P.qs[2];
-                    keep = keep && (ex * ex + ey * ey + ez * ez < P.rc2);
-                }
-                if (!keep) return;
-                const int ta = tai * 16 + meta_ta(mj);
-                Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
+            const int4 ij = si[j];
+            Real dx, dy, dz;
+            if (F32) {
+                const float fx = (float)wrap_diff(oix, ij.x), fy = (float)wrap_diff(oiy, ij.y),
+                            fz = (float)wrap_diff(oiz, ij.z);
+                dx = (Real)fmaf(fx, qh0, fx * ql0);
+                dy = (Real)fmaf(fy, qh1, fy * ql1);
+                dz = (Real)fmaf(fz, qh2, fz * ql2);
+            } else {
+                const StagedPos<Real> pj = sf[j];
+                dx = pi.x - pj.x; dy = pi.y - pj.y; dz = pi.z - pj.z;
+            }
+            const Real r2 = dx * dx + dy * dy + dz * dz;
+            const uint32_t mj = (uint32_t)ij.w;
+            bool keep = !(lipi != 0 && (mj >> 12) == lipi && ((emask >> meta_k(mj)) & 1u));
+            if (F32 && r2 >= rc2lo) {
+                // within float rounding of the cutoff: decide from the exact offsets
+                const double ex = (double)wrap_diff(oix, ij.x) * P.qs[0];
+                const double ey = (double)wrap_diff(oiy, ij.y) * P.qs[1];
+                const double ez = (double)wrap_diff(oiz, ij.z) * P.qs[2];
+                keep = keep && (ex * ex + ey * ey + ez * ez < P.rc2);
+            }
+            if (!keep) return;
+            const int ta = tai * 16 + meta_ta(mj);
+            Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
+            if (LAM) {
+                const int tb = tbi * 16 + meta_tb(mj);
+                f12 = ((Real)1 - lam) * f12 + lam * tf12[tb];
+                f6 = ((Real)1 - lam) * f6 + lam * tf6[tb];
+                qq = ((Real)1 - lam) * qq + lam * tqq[tb];
+            }
+            Real rinv, r2inv, r6inv;
+            if (F32) {
+                const float r2i = __frcp_rn((float)r2);
+                const float p = r2i * r2i;
+                const float pe = fmaf(r2i, r2i, -p);                 // exact error of the square
+                r6inv = (Real)fmaf(p, r2i, pe * r2i);               // r2i^3 rounded once
+                r2inv = (Real)r2i;
+                rinv = (Real)rsqrtf((float)r2);
+            } else {
+                rinv = (Real)(1.0 / sqrt((double)r2));
+                r2inv = rinv * rinv;
+                r6inv = r2inv * r2inv * r2inv;
+            }
+            const Real fs = (f12 * r6inv - f6) * r6inv * r2inv + qq * (rinv * r2inv - krf2);
+            ax += fs * dx; ay += fs * dy; az += fs * dz;
+            if (ENERGY) {
+                const int ia = tai * 16 + meta_ta(mj);
+                double c12 = P.c12[ia], c6 = P.c6[ia], qd = P.qq[ia], sh = P.ush[ia];
                 if (LAM) {
-                    const int tb = tbi * 16 + meta_tb(mj);
-                    f12 = ((Real)1 - lam) * f12 + lam * tf12[tb];
-                    f6 = ((Real)1 - lam) * f6 + lam * tf6[tb];
-                    qq = ((Real)1 - lam) * qq + lam * tqq[tb];
+                    const int ibb = tbi * 16 + meta_tb(mj);
+                    const double l = (double)lam;
+                    c12 = (1 - l) * c12 + l * P.c12[ibb];
+                    c6 = (1 - l) * c6 + l * P.c6[ibb];
+                    qd = (1 - l) * qd + l * P.qq[ibb];
+                    sh = (1 - l) * sh + l * P.ush[ibb];
                 }
-                Real rinv, r2inv, r6inv;
-                if (F32) {
-                    const float r2i = __frcp_rn((float)r2);
-                    const float p = r2i * r2i;
-                    const float pe = fmaf(r2i, r2i, -p);                 // exact error of the square
-                    r6inv = (Real)fmaf(p, r2i, pe * r2i);               // r2i^3 rounded once
-                    r2inv = (Real)r2i;
-                    rinv = (Real)rsqrtf((float)r2);
-                } else {
-                    rinv = (Real)(1.0 / sqrt((double)r2));
-                    r2inv = rinv * rinv;
-                    r6inv = r2inv * r2inv * r2inv;
-                }
-                const Real fs = (f12 * r6inv - f6) * r6inv * r2inv + qq * (rinv * r2inv - krf2);
-                ax += fs * dx; ay += fs * dy; az += fs * dz;
-                if (ENERGY) {
-                    const int ia = tai * 16 + meta_ta(mj);
-                    double c12 = P.c12[ia], c6 = P.c6[ia], qd = P.qq[ia], sh = P.ush[ia];
-                    if (LAM) {
-                        const int ibb = tbi * 16 + meta_tb(mj);
-                        const double l = (double)lam;
-                        c12 = (1 - l) * c12 + l * P.c12[ibb];
-                        c6 = (1 - l) * c6 + l * P.c6[ibb];
-                        qd = (1 - l) * qd + l * P.qq[ibb];
-                        sh = (1 - l) * sh + l * P.ush[ibb];
-                    }
-                    const double ri = (double)rinv, r2d = (double)r2;
-                    const double r6 = ri * ri * ri * ri * ri * ri;
-                    elj += 0.5 * (c12 * r6 * r6 - c6 * r6 - sh);
-                    erf += 0.5 * qd * (ri + P.krf * r2d - P.crf);
-                    epairs += 0.5;
-                }
+                const double ri = (double)rinv, r2d = (double)r2;
+                const double r6 = ri * ri * ri * ri * ri * ri;
+                elj += 0.5 * (c12 * r6 * r6 - c6 * r6 - sh);
+                erf += 0.5 * qd * (ri + P.krf * r2d - P.crf);
+                epairs += 0.5;
             }
         };
-        auto flush = [&](int count) {
-            for (int e = 0; e < count; ++e) eval1(q[e * PAIR_THREADS + t]);
-        };
-
-        for (int base = 0; base < M; base += STAGE_CAP) {
-            const int mc = min(STAGE_CAP, M - base);
-            __syncthreads();                      // the previous chunk (or the reduction) is done
-            // stage slots warp by warp, one bead per lane
-            for (int s = warp; s < 27; s += PAIR_THREADS / 32) {
-                const int lo = max(coff[s], base), hi = min(coff[s + 1], base + mc);
-                for (int k = lo + lane; k < hi; k += 32) {
-                    const uint4 v = S.spos[cst[s] + (k - coff[s])];
-                    const int ox = (int)(v.x - rx), oy = (int)(v.y - ry), oz = (int)(v.z - rz);
-                    sf[k - base] = frame_coords<Real>(P, ox, oy, oz);
-                    si[k - base] = make_int4(ox, oy, oz, (int)v.w);
-                }
-            }
-            __syncthreads();
+        // cull the staged list [0, mc) into private queues, then evaluate them
+        auto process = [&](int mc) {
             int nq = 0;
             int j = js;
             for (; j + (UNROLL - 1) * NS < mc; j += UNROLL * NS) {
-                if (nq > QCAP - UNROLL) { flush(nq); nq = 0; }
+                if (nq > QCAP - UNROLL) {
+                    for (int e = 0; e < nq; ++e) eval1(q[e * PAIR_THREADS + t]);
+                    nq = 0;
+                }
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
                     const StagedPos<Real> pj = sf[j + u * NS];
@@ -556,71 +589,88 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
                 }
             }
             for (; j < mc; j += NS) {
-                if (nq == QCAP) { flush(nq); nq = 0; }
+                if (nq == QCAP) {
+                    for (int e = 0; e < nq; ++e) eval1(q[e * PAIR_THREADS + t]);
+                    nq = 0;
+                }
                 const StagedPos<Real> pj = sf[j];
                 const Real dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
                 const Real r2 = dx * dx + dy * dy + dz * dz;
                 q[nq * PAIR_THREADS + t] = (uint16_t)j;
                 nq += (int)((r2 < rc2) & (r2 > (Real)0));
             }
-            // evaluate the chunk's hits with every bead's hits spread evenly over
-            // its streams (a fixed assignment, so the sums stay deterministic)
-            cntq[t] = js < NS ? nq : 0;
-            __syncthreads();
-            int pre = 0, tot = 0;
-            if (js < NS)
-                for (int s2 = 0; s2 < NS; ++s2) {
-                    const int c2 = cntq[s2 * IW + il];
-                    pre += s2 < js ? c2 : 0;
-                    tot += c2;
-                }
-            if (js == 0) htot[il] = tot;
-            __syncthreads();
-            if (t == 0) {
-                int o = 0;
-                for (int k = 0; k < IW; ++k) { hbase[k] = o; o += htot[k]; }
-            }
-            __syncthreads();
-            if (js < NS)
-                for (int e = 0; e < nq; ++e) lst[hbase[il] + pre + e] = q[e * PAIR_THREADS + t];
-            __syncthreads();
-            if (js < NS)
-                for (int h = js; h < tot; h += NS) eval1(lst[hbase[il] + h]);
-        }
+            for (int e = 0; e < nq; ++e) eval1(q[e * PAIR_THREADS + t]);
+        };
 
-        // the updating thread (stream 0) fetches the bead's velocity before the barrier
-        V4 vpre;
-        int idpre = 0;
-        if (INTEG && js == 0 && i < ni) {
-            idpre = S.sorted_id[ifirst + i];
-            vpre = reinterpret_cast<const V4 *>(S.vel)[idpre];
+        // staging: 128 candidates per round (one load per thread), kept when
+        // within rc of the i-beads' box, compacted in candidate order
+        int nst = 0;
+        for (int r0 = 0; r0 < M; r0 += PAIR_THREADS) {
+            const int k = r0 + t;
+            bool keepj = false;
+            StagedPos<Real> e;
+            int4 o;
+            if (k < M) {
+                int lo = 0, hi = 26;                  // the slot holding candidate k
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (coff[mid] <= k) lo = mid; else hi = mid - 1;
+                }
+                const uint4 v = S.spos[cst[lo] + (k - coff[lo])];
+                o = make_int4((int)(v.x - rx), (int)(v.y - ry), (int)(v.z - rz), (int)v.w);
+                e = frame_coords<Real>(P, o.x, o.y, o.z);
+                const Real gx = max(max(lox - e.x, e.x - hix), (Real)0);
+                const Real gy = max(max(loy - e.y, e.y - hiy), (Real)0);
+                const Real gz = max(max(loz - e.z, e.z - hiz), (Real)0);
+                keepj = gx * gx + gy * gy + gz * gz < rc2m;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keepj);
+            if (lane == 0) wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < NW; ++w) { before += w < warp ? wcnt[w] : 0; total += wcnt[w]; }
+            if (nst + total > STAGE_CAP) {        // the staged list is full: use it first
+                process(nst);
+                __syncthreads();
+                nst = 0;
+            }
+            if (keepj) {
+                const int at = nst + before + __popc(bal & ((1u << lane) - 1u));
+                sf[at] = e;
+                si[at] = o;
+            }
+            nst += total;
+            __syncthreads();
         }
+        process(nst);
+
         __syncthreads();                          // every queue has drained: red may alias q
         red[0 * PAIR_THREADS + t] = to_fix(ax);
         red[1 * PAIR_THREADS + t] = to_fix(ay);
         red[2 * PAIR_THREADS + t] = to_fix(az);
         __syncthreads();
         if (t < IW && ib + t < ni) {
-            long long Fx = 0, Fy = 0, Fz = 0;
+            cp_async_wait_all();
+            const V4 bf = sbf[t];
+            long long Fx = to_fix(bf.x), Fy = to_fix(bf.y), Fz = to_fix(bf.z);   // bonded
             for (int s = 0; s < NS; ++s) {       // fixed-point sum over the streams
                 Fx += red[0 * PAIR_THREADS + s * IW + t];
                 Fy += red[1 * PAIR_THREADS + s * IW + t];
                 Fz += red[2 * PAIR_THREADS + s * IW + t];
             }
-            const int p = ifirst + ib + t;
             const uint4 pu = vi;                 // this thread is (i = ib + t, stream 0)
             if (!INTEG) {
-                const int id = S.sorted_id[p];
+                const int id = sid[t];
                 S.fx[id] = Fx; S.fy[id] = Fy; S.fz[id] = Fz;
             } else {
-                const int id = idpre;
+                const int id = sid[t];
                 const Real sc = (Real)(1.0 / FIX);
                 const Real f0 = (Real)Fx * sc, f1 = (Real)Fy * sc, f2 = (Real)Fz * sc;
                 const int g = id < P.n_lipid_beads ? 0 : 1;
                 const Real a = (Real)S.c->alpha[g];
                 const Real dtm = (Real)P.dt_over_m;
                 V4 *vel = reinterpret_cast<V4 *>(S.vel);
-                V4 v = vpre;
+                V4 v = svel[t];
                 v.x = a * v.x + f0 * dtm;
                 v.y = a * v.y + f1 * dtm;
                 v.z = a * v.z + f2 * dtm;
@@ -642,26 +692,19 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
                 if (g == 0) ke0 += e; else ke1 += e;
             }
         }
+        __syncthreads();                          // red (over q) is read before the next chunk
     }
     if (INTEG) {
-        // this cell's kinetic-energy partials (fixed order)
+        // this cell's kinetic-energy partials (fixed order), into the integer slots
         kered[0][t] = ke0;
         kered[1][t] = ke1;
         __syncthreads();
-        if (t == 0) {
+        if (t == 0 && ni > 0) {
             Real a0 = 0, a1 = 0;
             for (int k = 0; k < (ni < PAIR_THREADS ? ni : PAIR_THREADS); ++k) { a0 += kered[0][k]; a1 += kered[1][k]; }
-            // integer accumulation: the sum does not depend on the order of the CTAs
             Counters &C = *S.c;
             atomicAdd((unsigned long long *)&C.ke_slot[c % KE_SLOTS][0], (unsigned long long)to_fix(a0));
             atomicAdd((unsigned long long *)&C.ke_slot[c % KE_SLOTS][1], (unsigned long long)to_fix(a1));
-            if (c == 0) {                        // once per system: the step is done
-                if (C.in_at) C.at_step++; else C.step++;
-                C.md_steps++;
-                C.force_evals++;
-                C.ke_pending = 1;
-                C.ke_fresh = 0;
-            }
         }
     }
     if (ENERGY) {
@@ -684,7 +727,7 @@ template <typename Real>
 static size_t pair_smem() {
     static_assert(3 * PAIR_THREADS * sizeof(long long) <= sizeof(uint16_t) * QCAP * PAIR_THREADS, "red fits in q");
     return sizeof(StagedPos<Real>) * STAGE_CAP + sizeof(int4) * STAGE_CAP + sizeof(Real) * 3 * 256 +
-           2 * sizeof(uint16_t) * QCAP * PAIR_THREADS;
+           sizeof(uint16_t) * QCAP * PAIR_THREADS;
 }
 
 template <typename Real, bool LAM, bool ENERGY, bool INTEG>

@@ -13,7 +13,7 @@ struct __align__(32) Dbl4 {
 
 constexpr int MAXT = 16;               // bead types, lipid types, beads per lipid
 constexpr int PAIR_THREADS = 128;      // threads per cell in the pair kernel
-constexpr int STAGE_CAP = 384;         // neighbour beads staged per chunk (27 cells)
+constexpr int STAGE_CAP = 320;         // neighbour beads staged per chunk (27 cells, pruned)
 constexpr int QCAP = 24;               // per-thread hit queue of the pair kernel
 constexpr int BEAD_BLOCK = 128;        // beads per block of per-bead kernels
 constexpr int CELLS_PER_SORT_BLOCK = 4;
@@ -110,6 +110,7 @@ struct SysDev {
     int *sorted_id;                    // [n_cells * capc] ids in cell order (ascending within a cell)
     int *sidx;                         // [n] position of a bead in the cell list
     uint4 *spos;                       // [n_cells * capc] positions in cell order
+    void *bforce;                      // [n_cells * capc] bonded force in cell order (float4 or double4)
     double *ke_part;                   // [n_cells * 2] kinetic energy per cell and group
     double *epart;                     // [n_cells * 4] lj, rf, pairs, (unused)
     double *bpart;                     // [n_bead_blocks * 3] bond, angle, kinetic energies (FP64)

@@ -27,7 +27,7 @@ using namespace mdas;
 namespace {
 
 constexpr int NA_MAX_BEADS = 16384;
-constexpr int NA_MAX_CELLS = 4096;
+constexpr int NA_MAX_CELLS = 2048;
 constexpr int NA_CAPC = 64;
 constexpr int NA_MAX_DEVICES = 64;
 
@@ -46,13 +46,14 @@ constexpr size_t OFF_CELLN = OFF_COUNT + al(4ull * NA_MAX_CELLS);
 constexpr size_t OFF_TMP = OFF_CELLN + al(4ull * NA_MAX_CELLS);
 constexpr size_t OFF_SORTED = OFF_TMP + al(4ull * NA_MAX_CELLS * NA_CAPC);
 constexpr size_t OFF_SPOS = OFF_SORTED + al(4ull * NA_MAX_CELLS * NA_CAPC);
-constexpr size_t OFF_MAP_BEADS = OFF_SPOS + al(16ull * NA_MAX_CELLS * NA_CAPC);
+constexpr size_t OFF_BFORCE = OFF_SPOS + al(16ull * NA_MAX_CELLS * NA_CAPC);
+constexpr size_t OFF_MAP_BEADS = OFF_BFORCE + al(32ull * NA_MAX_CELLS * NA_CAPC);
 constexpr size_t OFF_MAP_CELLS = OFF_MAP_BEADS + al(8ull * (NA_MAX_BEADS / BEAD_BLOCK + 1));
 constexpr size_t OFF_MAP_SORT = OFF_MAP_CELLS + al(8ull * NA_MAX_CELLS);
 constexpr size_t OFF_MAP_SYS = OFF_MAP_SORT + al(8ull * (NA_MAX_CELLS / CELLS_PER_SORT_BLOCK + 1));
 constexpr size_t NA_BYTES = OFF_MAP_SYS + al(8);
 
-// the scratch: every GPU that loads the library holds it until exit (~7 MB)
+// the scratch: every GPU that loads the library holds it until exit (~8 MB)
 static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
 
 unsigned char *g_na_addr[NA_MAX_DEVICES];
@@ -222,6 +223,7 @@ extern "C" mdas_status mdas_forces_noalloc(const mdas_system_desc *d, const uint
     S.tmp_ids = (int *)(base + OFF_TMP);
     S.sorted_id = (int *)(base + OFF_SORTED);
     S.spos = (uint4 *)(base + OFF_SPOS);
+    S.bforce = (void *)(base + OFF_BFORCE);
     S.n_bead_blocks = (P.n + BEAD_BLOCK - 1) / BEAD_BLOCK;
 
     // the previous call's contents stay in the array: clear what must start at zero
