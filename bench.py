@@ -35,6 +35,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the replica and swap-throughput lines")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="plain kernel launches instead of CUDA-graph replays (same kernels; for profilers)")
     return ap.parse_args()
 
 
@@ -183,6 +185,8 @@ def run_gpu(args):
     m = workload()
     m.system_id = rank
     sysm = mdas.System(m, precision="fp32", stream=stream.cuda_stream)
+    if args.no_graphs:
+        sysm.set_graphs(False)
     n_pairs0 = sysm.energy()["pairs"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -266,9 +270,9 @@ def run_gpu(args):
         # workload; void once the kernel source has changed since the capture
         import hashlib
         tj = json.load(open(tfile))
-        src = os.path.join(ROOT, "paper_2005_08348_gb300", "csrc", "kernels.cu")
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if tj.get("beads") == n and tj.get("kernels_cu_sha256") == h:
+        src = os.path.join(ROOT, "paper_2005_08348_gb300", "csrc", tj.get("source", "plist.cu"))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest() if os.path.exists(src) else None
+        if h is not None and tj.get("beads") == n and tj.get("source_sha256") == h:
             traffic = tj.get("bytes_per_launch")
     out = {
         "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s", "n_gpus": ws,
@@ -276,12 +280,13 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded bilayer, no trained parameters)",
         "config": config(m, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                             "pairs_per_force_eval": pairs_per_eval}),
+                             "pairs_per_force_eval": pairs_per_eval,
+                             "launches": "plain" if args.no_graphs else "cuda graphs"}),
         "swap_trials_per_s": trials_per_s, "md_steps_per_s": md * ws / tmax,
         "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "e2e": {"value": e2e_value, "unit": "pair-interactions/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-        "roofline": {"kernel": "k_pair<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+        "roofline": {"kernel": "k_nl_step<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
                      "traffic": traffic, "avg_launch_us": pair_avg_s * 1e6, "launches": pair_launches,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",

@@ -74,6 +74,9 @@ typedef struct {
     double rc, eps_r, eps_rf;          /* cutoff, relative permittivity, RF dielectric (<= 0: infinity) */
     double temperature, dt, tau_t;     /* K, ps, ps (tau_t <= 0: no thermostat, NVE) */
     double mass;                       /* every bead, amu */
+    double list_skin;                  /* nm: pair-list buffer of the MD step (<= 0: 0.2 nm); an
+                                          implementation parameter that does not change results
+                                          beyond FP32 summation order */
     uint64_t seed;                     /* Philox key = (seed_lo ^ system_id, seed_hi) */
     uint32_t system_id;
     int32_t precision;                 /* mdas_precision: pair arithmetic and velocities */
@@ -197,6 +200,12 @@ mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint
  * mdas_pair_kernel_time returns the sum of their durations (ms) and the launch
  * count since the last reset (reset = 1 clears after reading). */
 mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable);
+
+/* MD segments of mdas_md_steps and mdas_alchemical_move run as CUDA-graph
+ * replays (enable = 1, the default) or as plain launches of the same kernels
+ * in the same order (enable = 0), with identical results.  Plain launches
+ * serve profilers that cannot look into graphs holding conditional nodes. */
+mdas_status mdas_set_graphs(mdas_system *s, int32_t enable);
 mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *launches, int32_t reset);
 
 /* Per-system counters: MD steps, force evaluations (one per MD step and one
@@ -205,6 +214,7 @@ mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *lau
  * graphs that advanced the system. */
 typedef struct {
     int64_t md_steps, force_evals, trials, null_trials, accepted, moves, moves_accepted, kernel_launches;
+    int64_t list_builds;               /* pair-list builds of the MD step */
 } mdas_counters;
 mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
 

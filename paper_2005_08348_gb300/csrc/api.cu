@@ -26,24 +26,69 @@ struct GraphEntry {
 struct Batch {
     std::vector<mdas_system *> sys;
     SysDev *dsys = nullptr;
-    BlockMap beads, cells, sortcells, syss;
+    BlockMap beads, cells, sortcells, syss, nlbeads, lcells, lsort;
     int precision = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;  // captures the bodies of graph conditionals
     int max_bead_blocks = 1;
     int *dscratch = nullptr;      // [2]: pending sum, error or
+    unsigned int *bticket = nullptr;   // last-block ticket of the step kernel over the batch
     bool use_graphs = true;       // false for batches whose membership changes (the server's)
     size_t cap_sys = 0, cap_beads = 0, cap_cells = 0, cap_sort = 0;   // device capacity (refillable batches)
+    size_t cap_nlb = 0, cap_lc = 0, cap_ls = 0;
     std::map<std::string, GraphEntry> graphs;
     LaunchCtx ctx() const {
         LaunchCtx L;
         L.sys = dsys; L.n_sys = (int)sys.size();
         L.beads = &beads; L.cells = &cells; L.sortcells = &sortcells; L.syss = &syss;
+        L.nlbeads = &nlbeads; L.lcells = &lcells; L.lsort = &lsort;
         L.precision = precision; L.stream = stream; L.max_bead_blocks = max_bead_blocks;
+        L.bticket = bticket;
         return L;
     }
 };
 
 std::string g_last_error;
+
+// Pair-list geometry of a description: rl = rc + skin (limited so that every
+// box edge holds 3 list-build cells), the list-build grid, and capacities from
+// the densest list-build cell of the initial positions (a membrane patch may
+// leave part of its box empty): a cell holds up to twice that count (at least
+// four times the mean), a bead's list 1.5 times the number of beads within rl
+// at that density, both multiples of 32.
+struct ListDims {
+    double rl;
+    int ln[3], n_lcells, lcapc, lcap, lrow;
+};
+
+ListDims list_dims(const mdas_system_desc *d) {
+    ListDims L;
+    const double skin = d->list_skin > 0 ? d->list_skin : 0.2;
+    const double lmin = std::min(d->box[0], std::min(d->box[1], d->box[2]));
+    L.rl = std::max(d->rc, std::min(d->rc + skin, lmin / 3.0));
+    for (int k = 0; k < 3; ++k) L.ln[k] = std::max(3, (int)std::floor(d->box[k] / L.rl));
+    L.n_lcells = L.ln[0] * L.ln[1] * L.ln[2];
+    const int n = d->n_beads;
+    std::vector<int> cnt(L.n_lcells, 0);
+    int maxc = 0;
+    for (int i = 0; i < n && d->pos; ++i) {
+        int c[3];
+        for (int k = 0; k < 3; ++k) {
+            double f = d->pos[3 * i + k] / d->box[k];
+            f -= std::floor(f);
+            c[k] = std::min(L.ln[k] - 1, std::max(0, (int)(f * L.ln[k])));
+        }
+        maxc = std::max(maxc, ++cnt[(c[2] * L.ln[1] + c[1]) * L.ln[0] + c[0]]);
+    }
+    const double mean = (double)n / L.n_lcells;
+    L.lcapc = std::max(32, (int)std::ceil(std::max(4.0 * mean, 2.0 * maxc) / 32.0) * 32);
+    const double vol = d->box[0] * d->box[1] * d->box[2];
+    const double dens = std::max((double)n / vol, maxc / (vol / L.n_lcells));
+    const double within = 4.0 / 3.0 * M_PI * L.rl * L.rl * L.rl * dens;
+    L.lcap = std::max(64, (int)std::ceil(1.5 * within / 32.0) * 32);
+    L.lrow = ((n + 31) / 32 * 32) * NL_G;
+    return L;
+}
 
 }  // namespace
 
@@ -62,7 +107,6 @@ struct mdas_system {
     std::string err;
     bool unstable = false;
     bool cells_valid = false;   // the cell list matches the current positions and types
-    bool counted = false;       // cell_count holds the step kernel's counts of the current positions
     bool timing = false;
     double pair_ms = 0.0;
     long long pair_launches = 0;
@@ -133,8 +177,30 @@ void destroy_batch(Batch *b) {
         for (auto &ev : kv.second.pair_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
     }
     free_map(b->beads); free_map(b->cells); free_map(b->sortcells); free_map(b->syss);
+    free_map(b->nlbeads); free_map(b->lcells); free_map(b->lsort);
     if (b->dsys) cudaFree(b->dsys);
     if (b->dscratch) cudaFree(b->dscratch);
+    if (b->bticket) cudaFree(b->bticket);
+    if (b->side) cudaStreamDestroy(b->side);
+}
+
+// block maps of a batch: per system its bead blocks, cells, cell groups of the
+// cell-list finish (plus the thermostat block), step-kernel blocks and
+// list-build cells
+struct Maps {
+    std::vector<int2> beads, cells, sortcells, syss, nlbeads, lcells, lsort;
+    void add(int k, const mdas_system *x);
+};
+
+void Maps::add(int k, const mdas_system *x) {
+    for (int i = 0; i < x->n; i += BEAD_BLOCK) beads.push_back(make_int2(k, i));
+    for (int c = 0; c < x->hp.n_cells; ++c) cells.push_back(make_int2(k, c));
+    for (int c = 0; c < x->hp.n_cells; c += CELLS_PER_SORT_BLOCK) sortcells.push_back(make_int2(k, c));
+    sortcells.push_back(make_int2(k, -1));   // the system's thermostat block
+    syss.push_back(make_int2(k, 0));
+    for (int i = 0; i < x->n; i += NL_BEADS) nlbeads.push_back(make_int2(k, i));
+    for (int c = 0; c < x->hp.n_lcells; ++c) lcells.push_back(make_int2(k, c));
+    for (int c = 0; c < x->hp.n_lcells; c += CELLS_PER_SORT_BLOCK) lsort.push_back(make_int2(k, c));
 }
 
 mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batch> &out) {
@@ -144,26 +210,28 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
     b->precision = v[0]->precision;
     b->stream = v[0]->stream;
     std::vector<SysDev> hs;
-    std::vector<int2> beads, cells, sortcells, syss;
+    Maps mp;
     for (int k = 0; k < (int)v.size(); ++k) {
         const mdas_system *x = v[k];
         if (x->precision != b->precision) return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision");
         if (x->stream != b->stream) return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in CUDA stream");
         hs.push_back(x->hs);
-        for (int i = 0; i < x->n; i += BEAD_BLOCK) beads.push_back(make_int2(k, i));
-        for (int c = 0; c < x->hp.n_cells; ++c) cells.push_back(make_int2(k, c));
-        for (int c = 0; c < x->hp.n_cells; c += CELLS_PER_SORT_BLOCK) sortcells.push_back(make_int2(k, c));
-        sortcells.push_back(make_int2(k, -1));   // the system's thermostat block
-        syss.push_back(make_int2(k, 0));
+        mp.add(k, x);
         b->max_bead_blocks = std::max(b->max_bead_blocks, (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK);
     }
     CK(cudaMalloc(&b->dsys, sizeof(SysDev) * hs.size()));
     CK(cudaMemcpy(b->dsys, hs.data(), sizeof(SysDev) * hs.size(), cudaMemcpyHostToDevice));
-    CK(upload_map(b->beads, beads));
-    CK(upload_map(b->cells, cells));
-    CK(upload_map(b->sortcells, sortcells));
-    CK(upload_map(b->syss, syss));
+    CK(upload_map(b->beads, mp.beads));
+    CK(upload_map(b->cells, mp.cells));
+    CK(upload_map(b->sortcells, mp.sortcells));
+    CK(upload_map(b->syss, mp.syss));
+    CK(upload_map(b->nlbeads, mp.nlbeads));
+    CK(upload_map(b->lcells, mp.lcells));
+    CK(upload_map(b->lsort, mp.lsort));
     CK(cudaMalloc(&b->dscratch, sizeof(int) * 4));
+    CK(cudaMalloc(&b->bticket, sizeof(unsigned int)));
+    CK(cudaMemset(b->bticket, 0, sizeof(unsigned int)));
+    CK(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
     out = std::move(b);
     return MDAS_OK;
 }
@@ -177,19 +245,16 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     b.use_graphs = false;
     b.max_bead_blocks = 1;
     std::vector<SysDev> hs;
-    std::vector<int2> beads, cells, sortcells, syss;
+    Maps mp;
     for (int k = 0; k < (int)v.size(); ++k) {
         const mdas_system *x = v[k];
         if (x->precision != b.precision || x->stream != b.stream)
             return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision or stream");
         hs.push_back(x->hs);
-        for (int i = 0; i < x->n; i += BEAD_BLOCK) beads.push_back(make_int2(k, i));
-        for (int c = 0; c < x->hp.n_cells; ++c) cells.push_back(make_int2(k, c));
-        for (int c = 0; c < x->hp.n_cells; c += CELLS_PER_SORT_BLOCK) sortcells.push_back(make_int2(k, c));
-        sortcells.push_back(make_int2(k, -1));
-        syss.push_back(make_int2(k, 0));
+        mp.add(k, x);
         b.max_bead_blocks = std::max(b.max_bead_blocks, (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK);
     }
+    std::vector<int2> &beads = mp.beads, &cells = mp.cells, &sortcells = mp.sortcells, &syss = mp.syss;
     auto grow = [&](void **ptr, size_t &cap, size_t need, size_t elem) -> cudaError_t {
         if (need <= cap && *ptr) return cudaSuccess;
         if (*ptr) cudaFree(*ptr);
@@ -200,59 +265,41 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     CK(grow((void **)&b.beads.d, b.cap_beads, beads.size(), sizeof(int2)));
     CK(grow((void **)&b.cells.d, b.cap_cells, cells.size(), sizeof(int2)));
     CK(grow((void **)&b.sortcells.d, b.cap_sort, sortcells.size(), sizeof(int2)));
+    CK(grow((void **)&b.nlbeads.d, b.cap_nlb, mp.nlbeads.size(), sizeof(int2)));
+    CK(grow((void **)&b.lcells.d, b.cap_lc, mp.lcells.size(), sizeof(int2)));
+    CK(grow((void **)&b.lsort.d, b.cap_ls, mp.lsort.size(), sizeof(int2)));
     size_t cap_syss = 0;
     if (!b.syss.d) CK(grow((void **)&b.syss.d, cap_syss, 4096, sizeof(int2)));
     if (syss.size() > 4096) return fail(s, MDAS_ERR_INVALID_ARG, "batch: more than 4096 systems");
     if (!b.dscratch) CK(cudaMalloc(&b.dscratch, sizeof(int) * 4));
+    if (!b.bticket) {
+        CK(cudaMalloc(&b.bticket, sizeof(unsigned int)));
+        CK(cudaMemset(b.bticket, 0, sizeof(unsigned int)));
+    }
     CK(cudaMemcpyAsync(b.dsys, hs.data(), sizeof(SysDev) * hs.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.beads.d, beads.data(), sizeof(int2) * beads.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.cells.d, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.sortcells.d, sortcells.data(), sizeof(int2) * sortcells.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.syss.d, syss.data(), sizeof(int2) * syss.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaMemcpyAsync(b.nlbeads.d, mp.nlbeads.data(), sizeof(int2) * mp.nlbeads.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaMemcpyAsync(b.lcells.d, mp.lcells.data(), sizeof(int2) * mp.lcells.size(), cudaMemcpyHostToDevice, b.stream));
+    CK(cudaMemcpyAsync(b.lsort.d, mp.lsort.data(), sizeof(int2) * mp.lsort.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaStreamSynchronize(b.stream));   // the host vectors go out of scope
     b.beads.n = (int)beads.size();
     b.cells.n = (int)cells.size();
     b.sortcells.n = (int)sortcells.size();
     b.syss.n = (int)syss.size();
+    b.nlbeads.n = (int)mp.nlbeads.size();
+    b.lcells.n = (int)mp.lcells.size();
+    b.lsort.n = (int)mp.lsort.size();
     return MDAS_OK;
 }
 
 // ------------------------------------------------------------ step bodies
-// Cell counts: the integrator counts every bead into its new cell, so a build
-// right after it skips the counting pass.  All systems of a batch must agree.
-mdas_status sync_counted(mdas_system *s, Batch &b, bool *counted) {
-    bool all = true, any = false;
-    for (auto *x : b.sys) { all = all && x->counted; any = any || x->counted; }
-    if (any && !all) {
-        for (auto *x : b.sys)
-            if (x->counted) {
-                CK(cudaMemsetAsync(x->hs.cell_count, 0, 4ull * x->hp.n_cells, b.stream));
-                x->counted = false;
-            }
-        all = false;
-    }
-    *counted = all;
-    return MDAS_OK;
-}
-
-void set_counted(Batch &b, bool v) {
-    for (auto *x : b.sys) x->counted = v;
-}
-
 mdas_status build_cells(mdas_system *s, Batch &b) {
-    bool counted;
-    mdas_status st = sync_counted(s, b, &counted);
-    if (st != MDAS_OK) return st;
-    launch_cells(b.ctx(), counted);
-    set_counted(b, false);
+    launch_cells(b.ctx(), false);
     for (auto *x : b.sys) x->cells_valid = true;
     return MDAS_OK;
-}
-
-void md_step_launches(const Batch &b, bool lambda, bool counted) {
-    LaunchCtx L = b.ctx();
-    launch_cells(L, counted);
-    launch_step(L, lambda);
 }
 
 __global__ void k_batch_status(const SysDev *__restrict__ sys, int n, int *out) {
@@ -291,22 +338,52 @@ mdas_status check_err(mdas_system *s, Batch &b) {
     return MDAS_OK;
 }
 
+// Append to the capture on b.stream a conditional node whose body rebuilds
+// the pair lists (kernels return at once for systems whose list is valid);
+// `cond` must have been created on the capturing graph and is set by a kernel
+// captured before this call.
+mdas_status add_build_conditional(mdas_system *s, Batch &b, cudaGraphConditionalHandle cond) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(b.stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(b.side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    LaunchCtx L = b.ctx();
+    L.stream = b.side;
+    launch_nl_build(L, 1);
+    cudaGraph_t body_out;
+    CK(cudaStreamEndCapture(b.side, &body_out));
+    CK(cudaStreamUpdateCaptureDependencies(b.stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return MDAS_OK;
+}
+
+mdas_status new_cond(mdas_system *s, Batch &b, cudaGraphConditionalHandle *out) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    CK(cudaStreamGetCaptureInfo(b.stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    CK(cudaGraphConditionalHandleCreate(out, g, 0, cudaGraphCondAssignDefault));
+    return MDAS_OK;
+}
+
 // Capture (or reuse) a graph of `units` repetitions of [steps_per_unit MD
-// steps + optional exchange trial]; timing adds event pairs around every
-// pair-kernel launch.
-// Capture (or reuse) a graph of `units` repetitions of [steps_per_unit MD
-// steps + optional exchange trial]; its first node draws the thermostat
-// variates of all its steps.  With trials, the cell list a trial builds serves
-// the next MD step as well (positions do not change in between);
-// reuse_first also skips the first step's build because the list is valid
-// when the graph starts; counted_first tells whether the integrator's cell
-// counts are pending at the start.  timing adds event pairs around every
-// pair-kernel launch.
+// steps + optional exchange trial].  It first draws the thermostat variates
+// of all its steps and sets the first step's factor, rebuilds stale pair
+// lists (conditional node), and after every step kernel, which sets the
+// conditional, rebuilds them again if a bead moved too far; so the trial and
+// the next step always find valid lists.  timing adds event pairs around
+// every TIMING_STRIDE-th step kernel.
 mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, bool trial, bool lambda, bool timing,
-                      bool reuse_first, bool counted_first, GraphEntry **out) {
+                      GraphEntry **out) {
     char key[128];
-    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d_r%d_c%d", units, steps_per_unit, (int)trial, (int)lambda,
-             (int)timing, (int)reuse_first, (int)counted_first);
+    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d", units, steps_per_unit, (int)trial, (int)lambda, (int)timing);
     auto it = b.graphs.find(key);
     if (it != b.graphs.end()) { *out = &it->second; return MDAS_OK; }
     GraphEntry ge;
@@ -320,31 +397,40 @@ mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, b
         }
     }
     CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+    mdas_status st = MDAS_OK;
     LaunchCtx L = b.ctx();
     // the step kernel of step k sets the factor of step k + 1
     launch_thermo_draws(L, units * steps_per_unit + 1);
+    launch_thermostat(L);
+    cudaGraphConditionalHandle cond;
+    st = new_cond(s, b, &cond);
+    if (st == MDAS_OK) {
+        launch_nl_decide(L, cond);
+        st = add_build_conditional(s, b, cond);
+    }
     int ev = 0, step_no = 0;
-    for (int u = 0; u < units; ++u) {
-        for (int k = 0; k < steps_per_unit; ++k, ++step_no) {
-            const bool first = u == 0 && k == 0;
-            const bool have_cells = trial && k == 0 && (u > 0 || reuse_first);
-            if (!have_cells) launch_cells(L, first ? counted_first : true);
+    for (int u = 0; u < units && st == MDAS_OK; ++u) {
+        for (int k = 0; k < steps_per_unit && st == MDAS_OK; ++k, ++step_no) {
+            st = new_cond(s, b, &cond);
+            if (st != MDAS_OK) break;
             if (timing && step_no % TIMING_STRIDE == 0) {
                 // external event nodes: recorded (and timed) at every replay
                 cudaEventRecordWithFlags(ge.pair_events[ev].first, b.stream, cudaEventRecordExternal);
-                launch_step(L, lambda);
+                launch_nl_step(L, lambda, cond, 1);
                 cudaEventRecordWithFlags(ge.pair_events[ev].second, b.stream, cudaEventRecordExternal);
                 ++ev;
             } else {
-                launch_step(L, lambda);
+                launch_nl_step(L, lambda, cond, 1);
             }
+            st = add_build_conditional(s, b, cond);
         }
-        if (trial) {
-            launch_cells(L, true);
-            launch_trial_one(L);
-        }
+        if (trial && st == MDAS_OK) launch_trial_nl(L);
     }
     cudaError_t e = cudaStreamEndCapture(b.stream, &g);
+    if (st != MDAS_OK) {
+        if (e == cudaSuccess) cudaGraphDestroy(g);
+        return st;
+    }
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
     size_t n_nodes = 0;
     cudaGraphGetNodes(g, nullptr, &n_nodes);
@@ -377,7 +463,8 @@ mdas_status replay(mdas_system *s, Batch &b, GraphEntry *ge) {
 }
 
 // n_steps MD steps on a batch; after every swap_every-th step one trial.
-mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, bool lambda = false) {
+mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, bool lambda = false,
+                   bool check = true) {
     if (n_steps <= 0) return MDAS_OK;
     const bool trial = swap_every > 0;
     const long long unit = trial ? swap_every : 1;
@@ -385,60 +472,73 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     const long long rem = n_steps % unit;
     bool timing = false;
     for (auto *x : b.sys) timing = timing || x->timing;
-    const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
-    bool counted;
-    mdas_status st = sync_counted(s, b, &counted);
-    if (st != MDAS_OK) return st;
-    if (!b.use_graphs) {   // membership changes between calls: plain launches, same arithmetic
-        for (long long k = 0; k < n_steps; ++k) {
-            md_step_launches(b, lambda, counted);
-            counted = true;
-        }
-        set_counted(b, true);
-        for (auto *x : b.sys) x->cells_valid = false;
-        for (auto *x : b.sys) x->kernel_launches += 2 * n_steps;
-        CK(cudaGetLastError());
-        return check_err(s, b);
-    }
-    if (n_units > 0) {
-        bool reuse = false;
-        if (trial) {
-            bool valid = true;
-            for (auto *x : b.sys) valid = valid && x->cells_valid;
-            if (!valid) {
-                launch_cells(b.ctx(), counted);
-            } else if (counted) {
-                for (auto *x : b.sys) CK(cudaMemsetAsync(x->hs.cell_count, 0, 4ull * x->hp.n_cells, b.stream));
+    for (auto *x : b.sys) x->cells_valid = false;
+    if (!b.use_graphs || n_units == 0 || n_steps < 4) {
+        // plain launches, same arithmetic: the list kernels return at once
+        // for systems whose list is valid
+        LaunchCtx L = b.ctx();
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+        long long launches = 0;
+        for (long long k0 = 0; k0 < n_steps; k0 += MAX_DRAW_STEPS - 1) {
+            const long long k1 = std::min(n_steps, k0 + MAX_DRAW_STEPS - 1);
+            launch_thermo_draws(L, (int)(k1 - k0 + 1));
+            launch_thermostat(L);
+            launches += 2;
+            for (long long k = k0; k < k1; ++k) {
+                launch_nl_build(L, 0);
+                if (timing && k % TIMING_STRIDE == 0) {
+                    cudaEvent_t e0, e1;
+                    CK(cudaEventCreate(&e0));
+                    CK(cudaEventCreate(&e1));
+                    evs.push_back({e0, e1});
+                    CK(cudaEventRecord(e0, b.stream));
+                    launch_nl_step(L, lambda, 0, 0);
+                    CK(cudaEventRecord(e1, b.stream));
+                } else {
+                    launch_nl_step(L, lambda, 0, 0);
+                }
+                launches += 5;
+                if (trial && (k + 1) % unit == 0) { launch_trial_nl(L); ++launches; }
             }
-            reuse = true;
-            counted = false;
         }
-        GraphEntry *ge;
-        for (long long r = 0; r < n_units / E; ++r) {
-            st = get_graph(s, b, (int)E, (int)unit, trial, lambda, timing, reuse, counted, &ge);
-            if (st != MDAS_OK) return st;
-            st = replay(s, b, ge);
-            if (st != MDAS_OK) return st;
-            counted = !trial;
+        for (auto *x : b.sys) x->kernel_launches += launches;
+        CK(cudaGetLastError());
+        if (!evs.empty()) {
+            CK(cudaStreamSynchronize(b.stream));
+            for (auto &ev : evs) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ev.first, ev.second));
+                for (auto *x : b.sys) { x->pair_ms += ms; x->pair_launches += 1; }
+                cudaEventDestroy(ev.first);
+                cudaEventDestroy(ev.second);
+            }
         }
-        const long long left = n_units % E;
-        if (left > 0) {
-            st = get_graph(s, b, (int)left, (int)unit, trial, lambda, timing, reuse, counted, &ge);
-            if (st != MDAS_OK) return st;
-            st = replay(s, b, ge);
-            if (st != MDAS_OK) return st;
-            counted = !trial;
-        }
+        return check ? check_err(s, b) : MDAS_OK;
     }
-    for (long long k = 0; k < rem; ++k) {
-        md_step_launches(b, lambda, counted);
-        counted = true;
+    const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
+    GraphEntry *ge;
+    mdas_status st;
+    for (long long r = 0; r < n_units / E; ++r) {
+        st = get_graph(s, b, (int)E, (int)unit, trial, lambda, timing, &ge);
+        if (st != MDAS_OK) return st;
+        st = replay(s, b, ge);
+        if (st != MDAS_OK) return st;
     }
-    set_counted(b, counted);
-    const bool valid_after = trial && rem == 0 && n_units > 0;
-    for (auto *x : b.sys) x->cells_valid = valid_after;
+    const long long left = n_units % E;
+    if (left > 0) {
+        st = get_graph(s, b, (int)left, (int)unit, trial, lambda, timing, &ge);
+        if (st != MDAS_OK) return st;
+        st = replay(s, b, ge);
+        if (st != MDAS_OK) return st;
+    }
+    if (rem > 0) {
+        st = get_graph(s, b, 1, (int)rem, false, lambda, timing, &ge);
+        if (st != MDAS_OK) return st;
+        st = replay(s, b, ge);
+        if (st != MDAS_OK) return st;
+    }
     CK(cudaGetLastError());
-    return check_err(s, b);
+    return check ? check_err(s, b) : MDAS_OK;
 }
 
 // n exchange trials per system of a batch with sequential semantics.
@@ -571,12 +671,34 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         P.cwu[k] = (unsigned long long)(4294967296.0 / nc[k]);
         P.qdtf[k] = (float)P.qdt[k];
     }
+    {   // pair list
+        const ListDims ld = list_dims(d);
+        P.rl = ld.rl;
+        P.rl2 = P.rl * P.rl;
+        P.rl2f = std::nextafter((float)(P.rl2 * (1.0 + 1e-5)), 1e30f);
+        const double half = 0.5 * (P.rl - d->rc);      // a bead may move this far before a rebuild
+        P.dmax2f = (float)(half * half * (1.0 - 1e-4));
+        for (int k = 0; k < 3; ++k) {
+            P.ln[k] = ld.ln[k];
+            P.lcwu[k] = (unsigned long long)(4294967296.0 / ld.ln[k]);
+        }
+        P.n_lcells = ld.n_lcells;
+        P.lcapc = ld.lcapc;
+        P.lcap = ld.lcap;
+        P.lrow = ld.lrow;
+        if (P.lcapc > 4096 || P.lcap > 4096) {
+            delete s;
+            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: density too high for the pair list");
+        }
+    }
     P.therm_c = d->tau_t > 0 ? std::exp(-d->dt / d->tau_t) : 1.0;
     P.rc2f = std::nextafter((float)(P.rc2 * (1.0 + 1e-5)), 1e30f);
     P.rc2f_lo = (float)(P.rc2 * (1.0 - 1e-5));
     P.krf2f = (float)(2.0 * P.krf);
     P.dt = d->dt; P.tau_t = d->tau_t; P.mass = d->mass; P.kT = BOLTZ * d->temperature;
     P.dt_over_m = d->dt / d->mass;
+    P.dt_over_mf = (float)P.dt_over_m;
+    P.massf = (float)d->mass;
     P.nf[0] = 3 * nl * bpl; P.nf[1] = 3 * (n - nl * bpl);
     for (int g = 0; g < 2; ++g) P.ktarget[g] = 0.5 * P.nf[g] * P.kT;
     P.kb = d->kb; P.b0 = d->b0; P.kth = d->ktheta; P.cos0 = std::cos(d->theta0_deg * M_PI / 180.0);
@@ -623,6 +745,26 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         }
     }
 
+    // bonded partners of each local index (the beads its bonded terms read)
+    memset(P.pidx, -1, sizeof(P.pidx));
+    for (int k = 0; k < bpl; ++k) {
+        auto add = [&](int q) {
+            if (q == k || P.pidx[k][q] >= 0) return true;
+            if (P.npart[k] >= NL_PART) return false;
+            P.pidx[k][q] = (int8_t)P.npart[k];
+            P.part[k][P.npart[k]++] = (int8_t)q;
+            return true;
+        };
+        bool ok = true;
+        for (int b = 0; b < P.nbond[k]; ++b) ok = ok && add(P.bpart[k][b]);
+        for (int a = 0; a < P.nang[k]; ++a)
+            for (int c = 0; c < 3; ++c) ok = ok && add(P.ang[k][a][c]);
+        if (!ok) {
+            delete s;
+            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: a bead has more than 8 bonded partners");
+        }
+    }
+
     // ---- device memory: one arena
     const int nbb = (n + BEAD_BLOCK - 1) / BEAD_BLOCK;
     const size_t nslot = (size_t)P.n_cells * P.capc;
@@ -649,6 +791,10 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.log, sizeof(TrialRec) * (size_t)LOG_CAP}, {(void **)&H.result, 8ull * 64},
         {(void **)&H.tdraw, sizeof(double2) * 2ull * MAX_DRAW_STEPS},
         {(void **)&s->fout, 24ull * n},
+        {(void **)&H.lcell_count, 4ull * P.n_lcells}, {(void **)&H.ltmp, 4ull * P.n_lcells * P.lcapc},
+        {(void **)&H.lcell, 8ull * P.n_lcells}, {(void **)&H.lid, 4ull * n}, {(void **)&H.lk, 4ull * n},
+        {(void **)&H.lpos, 32ull * n}, {(void **)&H.xref, 16ull * n}, {(void **)&H.nl_n, 4ull * NL_G * n},
+        {(void **)&H.nl, 4ull * (size_t)(P.lcap / NL_G) * P.lrow}, {(void **)&H.bslot, 4ull * NL_PART * n},
     };
     size_t total = 0;
     for (auto &it : items) total += (it.bytes + 255) / 256 * 256;
@@ -669,6 +815,8 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     {
         cudaError_t e = cudaMemsetAsync(s->arena, 0, total, s->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dp, &P, sizeof(Params), cudaMemcpyHostToDevice, s->stream);
+        static const int one = 1;   // no pair list yet
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&dc->nl_stale, &one, sizeof(int), cudaMemcpyHostToDevice, s->stream);
         // positions: floor(x / L * 2^32) mod 2^32, with the bead's meta word
         std::vector<uint4> pos(n);
         for (int i = 0; i < n; ++i) {
@@ -850,12 +998,8 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
         for (int k = 1; k <= n_lambda; ++k) {
             launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
             if (md_per_lambda > 0) {
-                GraphEntry *ge;
-                mdas_status st = get_graph(s, b, 1, md_per_lambda, false, true, s->timing, false, s->counted, &ge);
+                mdas_status st = run_md(s, b, md_per_lambda, 0, true, false);
                 if (st != MDAS_OK) return st;
-                st = replay(s, b, ge);
-                if (st != MDAS_OK) return st;
-                s->counted = true;
             }
             mdas_status st = build_cells(s, b);
             if (st != MDAS_OK) return st;
@@ -998,9 +1142,8 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     c.step = in->step; c.trial = in->trial; c.move = in->move; c.at_step = in->at_step;
     c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0; c.ke_fresh = 0; c.ke_pending = 0; c.draw_n = 0;
     memset(c.ke_slot, 0, sizeof(c.ke_slot));
+    c.nl_stale = 1; c.nl_viol = 0; c.sticket = 0; c.nticket = 0;
     CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
-    if (s->counted) CK(cudaMemsetAsync(s->hs.cell_count, 0, 4ull * s->hp.n_cells, s->stream));
-    s->counted = false;
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
     s->unstable = false;
@@ -1077,6 +1220,12 @@ mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable) {
     return MDAS_OK;
 }
 
+mdas_status mdas_set_graphs(mdas_system *s, int32_t enable) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_graphs: NULL system");
+    s->solo->use_graphs = enable != 0;
+    return MDAS_OK;
+}
+
 mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *launches, int32_t reset) {
     if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "pair_kernel_time: NULL system");
     if (total_ms) *total_ms = s->pair_ms;
@@ -1098,7 +1247,10 @@ mdas_status mdas_get_counters(const mdas_system *cs, mdas_counters *out) {
     out->accepted = (int64_t)c.accepted;
     out->moves = (int64_t)c.moves;
     out->moves_accepted = (int64_t)c.moves_accepted;
-    out->kernel_launches = (int64_t)s->kernel_launches;
+    // graph kernel nodes at every replay, plus the 4 list-build kernels of
+    // every graph conditional that ran
+    out->kernel_launches = (int64_t)s->kernel_launches + 4 * (int64_t)c.nl_builds_cond;
+    out->list_builds = (int64_t)c.nl_builds;
     return MDAS_OK;
 }
 
@@ -1151,7 +1303,10 @@ size_t arena_estimate(const mdas_system_desc *d) {
                8 * nc + 24 * nc * capc + vsz * nc * capc + 4 * n + 16 * nc + 24 * nbb + 32 * nc + 16 * n + vsz * n +
                (16 + 8 + 72 + 4 + 128 + 64) * (size_t)MAX_ROUND_TRIALS + sizeof(TrialRec) * (size_t)LOG_CAP + 512 +
                32 * MAX_DRAW_STEPS + 24 * n;
-    return t + 40 * 256;
+    const ListDims ld = list_dims(d);
+    t += 12ull * ld.n_lcells + 4ull * ld.n_lcells * ld.lcapc + 4 * n + 4 * n + 32 * n + 16 * n + 4ull * NL_G * n +
+         4ull * (ld.lcap / NL_G) * ld.lrow + 4ull * NL_PART * n;
+    return t + 50 * 256;
 }
 
 }  // namespace

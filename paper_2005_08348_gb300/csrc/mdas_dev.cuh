@@ -16,6 +16,11 @@ constexpr int PAIR_THREADS = 128;      // threads per cell in the pair kernel
 constexpr int STAGE_CAP = 320;         // neighbour beads staged per chunk (27 cells, pruned)
 constexpr int QCAP = 24;               // per-thread hit queue of the pair kernel
 constexpr int BEAD_BLOCK = 128;        // beads per block of per-bead kernels
+constexpr int NL_G = 4;                // threads per bead in the pair-list step kernel
+constexpr int NL_BLOCK = 128;          // threads per block of the pair-list step kernel
+constexpr int NL_BEADS = NL_BLOCK / NL_G;
+constexpr int NL_PART = 8;             // bonded partners per bead at most
+constexpr int NLB_STAGE = 1024;        // candidates staged per chunk by the list build
 constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
 constexpr int MAX_ROUND_TRIALS = 1024; // trials per batched swap evaluation
@@ -52,12 +57,23 @@ struct Params {
     float qdtf[3];                     // dt 2^32 / L as float (FP32 position update)
     double therm_c;                    // exp(-dt / tau_t)
     double dt, tau_t, mass, kT, dt_over_m;
+    float dt_over_mf, massf;           // the same in single precision (FP32 integrator)
     int nf[2];
     double ktarget[2];
     double kb, b0, kth, cos0;
     uint32_t key0, key1;
     int precision;
     uint32_t rcu[3];                   // rc in fixed-point units per axis (rounded up)
+    // pair list with a skin: every pair closer than rl = rc + skin when the list
+    // was built, found on a grid of cells of edge >= rl
+    int ln[3], n_lcells, lcapc;        // list-build cells per edge, cells, bead capacity of a cell
+    unsigned long long lcwu[3];        // floor(2^32 / ln_d): list-build cell width in fixed-point units
+    int lcap, lrow;                    // entries per bead (NL_G columns of lcap / NL_G rows), row stride
+    double rl, rl2;
+    float rl2f;                        // rl^2 rounded up (build cull)
+    float dmax2f;                      // squared displacement since the build that invalidates the list
+    int8_t npart[16], part[16][NL_PART];   // bonded partners (local indices) of local index k
+    int8_t pidx[16][16];               // local index -> slot in part[k], -1 if not a partner
     // pair tables [ti*16 + tj]; qq includes f / eps_r
     double c12[256], c6[256], qq[256], ush[256];
     float f12f[256], f6f[256], qqf[256];   // 12 C12, 6 C6, f qi qj / eps_r
@@ -80,6 +96,7 @@ struct Counters {
     unsigned long long step, trial, move, at_step;
     unsigned long long md_steps, force_evals, trials, null_trials, accepted, moves, moves_accepted;
     double lambda, w, alpha[2];
+    float alpha_f[2];                  // alpha rounded to float (FP32 integrator)
     int err, in_at, mdas_accept, n_pairs;
     int pairs[2 * MAX_PAIRS];
     int max_cell, pending;
@@ -92,6 +109,13 @@ struct Counters {
     int ke_pending;                    // the step kernel left kinetic energy in ke_slot
     double ke_total[2];
     long long ke_slot[KE_SLOTS][2];    // fixed-point kinetic energy per slot and group (2^32 units)
+    int nl_stale;                      // the pair list must be rebuilt before its next use
+    int nl_viol;                       // a bead moved farther than the skin allows (this step)
+    int nl_par;                        // lpos buffer holding the current positions
+    unsigned int sticket;              // last-block ticket of the step kernel
+    unsigned int nticket;              // last-block ticket of the list-build count kernel
+    unsigned long long nl_builds;      // pair-list builds
+    unsigned long long nl_builds_cond; // of which inside a graph conditional (4 kernels each)
 };
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
@@ -127,6 +151,17 @@ struct SysDev {
     TrialRec *log;                     // [LOG_CAP]
     double *result;                    // scratch for reductions to the host [64]
     double2 *tdraw;                    // [MAX_DRAW_STEPS * 2] (R1, S) per step and group
+    // pair list (list order: beads grouped by list-build cell, ascending id within a cell)
+    int *lcell_count;                  // [n_lcells] beads counted into each list-build cell
+    int *ltmp;                         // [n_lcells * lcapc] ids as counted
+    int2 *lcell;                       // [n_lcells] first list index and count of each cell
+    int *lid;                          // [n] list index -> id
+    int *lk;                           // [n] id -> list index
+    uint4 *lpos;                       // [2 n] positions in list order, two buffers
+    uint4 *xref;                       // [n] positions when the list was built
+    int *nl_n;                         // [n * NL_G] entries in each column of each bead's list
+    int *nl;                           // row r of column g of bead k at [r * lrow + k * NL_G + g]
+    int *bslot;                        // [n * NL_PART] list indices of the bonded partners
     int n_bead_blocks;
 };
 
@@ -172,9 +207,11 @@ struct LaunchCtx {
     const SysDev *sys;        // device array
     int n_sys;
     const BlockMap *beads, *cells, *sortcells, *syss;
+    const BlockMap *nlbeads, *lcells, *lsort;   // pair-list step blocks, list-build cells (one, four per block)
     int precision;
     cudaStream_t stream;
     int max_bead_blocks;
+    unsigned int *bticket;    // device: last-block ticket over the whole batch
 };
 
 cudaError_t setup_kernels();
@@ -184,6 +221,14 @@ void launch_trial_one(const LaunchCtx &L);
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64);
 void launch_step(const LaunchCtx &L, bool lambda);
 void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
+// pair-list MD (kernels.cu): thermostat factor of the coming step; list build
+// (kernels return at once for systems whose list is valid); one step, which
+// sets the graph conditional `cond` (when use_cond) to "some list is stale"
+void launch_thermostat(const LaunchCtx &L);
+void launch_nl_build(const LaunchCtx &L, int in_conditional);
+void launch_nl_decide(const LaunchCtx &L, cudaGraphConditionalHandle cond);
+void launch_nl_step(const LaunchCtx &L, bool lambda, cudaGraphConditionalHandle cond, int use_cond);
+void launch_trial_nl(const LaunchCtx &L);
 void launch_energy_reduce(const LaunchCtx &L);
 
 // swap.cu launchers

@@ -228,15 +228,23 @@ void launch_swap_dE(const LaunchCtx &L, int n) {
     k_swap_dE<<<g, 128, 0, L.stream>>>(L.sys, n);
 }
 
+// New meta word of bead id: the id-ordered positions, and the list-ordered
+// copy while the pair list is valid.
+__device__ __forceinline__ void set_meta(const SysDev &S, const Params &P, int id, uint32_t m) {
+    S.pos[id].w = m;
+    const Counters &C = *S.c;
+    if (!C.nl_stale) S.lpos[(size_t)C.nl_par * P.n + S.lk[id]].w = m;
+}
+
 // Rewrite the A type of every bead of lipid l for lipid type lt (position
-// array and its cell-ordered copy).
+// arrays and the cell-ordered copy).
 __device__ void set_lipid_type(const SysDev &S, const Params &P, int l, int lt) {
     S.ltype[l] = lt;
     for (int k = 0; k < P.bpl; ++k) {
         const int id = l * P.bpl + k;
         const int bt = P.lbt[lt * 16 + k];
         const uint32_t m = meta_make(bt, bt, k, l + 1);
-        S.pos[id].w = m;
+        set_meta(S, P, id, m);
         S.spos[S.sidx[id]].w = m;
     }
 }
@@ -396,6 +404,149 @@ void launch_trial_one(const LaunchCtx &L) {
     k_trial_one<<<g, 128, 0, L.stream>>>(L.sys);
 }
 
+// One exchange trial per system from the pair list (valid whenever an MD
+// step has just run): grid (DE_GROUPS, n_sys).  Items are (changed bead, list
+// column, row); every list holds all partners closer than rc, so the dE is
+// the same sum as over the 27 cells.  The last CTA (a ticket) adds the
+// partial sums in order, decides and applies, as in k_trial_one.
+__global__ void __launch_bounds__(128) k_trial_nl(const SysDev *__restrict__ sys) {
+    const SysDev &S = sys[blockIdx.y];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    const int grp = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
+    __shared__ double sh[4];
+    __shared__ int it_beg[2 * MAXT * NL_G + 1];
+    __shared__ int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT], chg_k[2 * MAXT];
+    __shared__ uint4 chg_pos[2 * MAXT];
+    __shared__ int nchg, last, accept;
+    __shared__ double lnu;
+    const unsigned long long T = C.trial;
+    const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
+    const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
+    const int ta = S.ltype[a], tb = S.ltype[b];
+    const bool null_trial = (a == b) || (ta == tb);
+    int m = 0;                                   // local indices whose bead type changes
+    if (!null_trial)
+        for (int k = 0; k < P.bpl; ++k) m |= (P.lbt[ta * 16 + k] != P.lbt[tb * 16 + k]) << k;
+    const uint4 *cur = S.lpos + (size_t)C.nl_par * P.n;
+    if (t == 32) lnu = log(unit53(w.z, w.w));
+    if (t < 32) {
+        const int side = lane >= P.bpl, k = side ? lane - P.bpl : lane;
+        const bool ch = lane < 2 * P.bpl && ((m >> k) & 1);
+        const unsigned bal = __ballot_sync(0xffffffffu, ch);
+        if (ch) {
+            const int o = __popc(bal & ((1u << lane) - 1u));
+            const int id = (side ? b : a) * P.bpl + k;
+            const int kk = S.lk[id];
+            chg_id[o] = id;
+            chg_k[o] = kk;
+            chg_pos[o] = cur[kk];
+            chg_old[o] = P.lbt[(side ? tb : ta) * 16 + k];
+            chg_new[o] = P.lbt[(side ? ta : tb) * 16 + k];
+        }
+        if (lane == 0) nchg = __popc(bal);
+    }
+    __syncthreads();
+    const int nc = nchg, nit = nc * NL_G;
+    if (t < 32) {
+        // items (changed bead, column): exclusive offsets of their row counts,
+        // NL_G items per lane, one warp scan
+        int v[NL_G], sum = 0;
+#pragma unroll
+        for (int g = 0; g < NL_G; ++g) {
+            const int it = NL_G * lane + g;
+            v[g] = it < nit ? S.nl_n[(size_t)chg_k[it / NL_G] * NL_G + g] : 0;
+            sum += v[g];
+        }
+        int inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += x;
+        }
+        int run = inc - sum;
+#pragma unroll
+        for (int g = 0; g < NL_G; ++g) {
+            const int it = NL_G * lane + g;
+            if (it < nit) it_beg[it] = run;
+            run += v[g];
+        }
+        if (lane == 31) it_beg[nit] = inc;
+    }
+    __syncthreads();
+    const int total = nc > 0 ? it_beg[nit] : 0;
+    double acc = 0.0;
+    for (int f = grp * blockDim.x + t; f < total; f += DE_GROUPS * blockDim.x) {
+        int lo = 0, hi = nit - 1;                 // the item holding entry f
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (it_beg[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int ci = lo / NL_G, g = lo % NL_G, row = f - it_beg[lo];
+        const int kj = S.nl[(size_t)row * P.lrow + (size_t)chg_k[ci] * NL_G + g];
+        const uint4 pi = chg_pos[ci], pj = cur[kj];
+        const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
+        const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
+        const float r2f = fx * fx + fy * fy + fz * fz;
+        if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
+        const int lj = meta_lip(pj.w), kjl = meta_k(pj.w);
+        const bool chj = (lj == a || lj == b) && ((m >> kjl) & 1);
+        if (chj && lj * P.bpl + kjl < chg_id[ci]) continue;     // a changed pair once, by the lower id
+        const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 >= P.rc2) continue;
+        const int old_j = meta_ta(pj.w);
+        const int new_j = chj ? (int)P.lbt[(lj == a ? tb : ta) * 16 + kjl] : old_j;
+        acc += pair_du(P, chg_old[ci], old_j, chg_new[ci], new_j, r2);
+    }
+    const double part = block_sum(acc, sh);
+    if (t == 0) {
+        S.tdE[grp] = part;
+        __threadfence();
+        last = atomicAdd(&C.ticket, 1u) == DE_GROUPS - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (t == 0) {
+        __threadfence();
+        double dE = 0.0;
+        for (int g = 0; g < DE_GROUPS; ++g) dE += __ldcg(&S.tdE[g]);
+        TrialRec r;
+        r.a = a; r.b = b; r.u = unit53(w.z, w.w); r.dE = 0.0; r.accepted = 0; r.index = T;
+        r.null_trial = null_trial;
+        if (!null_trial) {
+            r.dE = dE;
+            r.accepted = dE + P.kT * lnu <= 0.0;
+        }
+        accept = r.accepted;
+        if (r.accepted) { S.ltype[a] = tb; S.ltype[b] = ta; }
+        S.log[T % LOG_CAP] = r;
+        C.trials++;
+        C.force_evals++;
+        C.null_trials += r.null_trial;
+        C.accepted += r.accepted;
+        C.trial = T + 1;
+        C.pending = 0;
+        C.ticket = 0;
+    }
+    __syncthreads();
+    if (accept && t < 2 * P.bpl) {               // the exchange: every bead of both lipids
+        const int side = t >= P.bpl, k = side ? t - P.bpl : t;
+        const int l = side ? b : a, lt = side ? ta : tb;
+        const int id = l * P.bpl + k;
+        const int bt = P.lbt[lt * 16 + k];
+        const uint32_t mm = meta_make(bt, bt, k, l + 1);
+        S.pos[id].w = mm;
+        const_cast<uint4 *>(cur)[S.lk[id]].w = mm;
+    }
+}
+
+void launch_trial_nl(const LaunchCtx &L) {
+    dim3 g(DE_GROUPS, L.n_sys);
+    k_trial_nl<<<g, 128, 0, L.stream>>>(L.sys);
+}
+
 
 // one block per system, one thread walks the trials in order
 __global__ void k_swap_resolve(const SysDev *__restrict__ sys, int n) {
@@ -484,7 +635,7 @@ __global__ void k_mdas_select(const SysDev *__restrict__ sys, int n_pairs, int m
             for (int k = 0; k < P.bpl; ++k) {
                 const int id = l * P.bpl + k;
                 const uint32_t m = S.pos[id].w;
-                S.pos[id].w = meta_make(meta_ta(m), P.lbt[tnew * 16 + k], k, l + 1);
+                set_meta(S, P, id, meta_make(meta_ta(m), P.lbt[tnew * 16 + k], k, l + 1));
             }
         }
     C.w = 0.0;
@@ -569,7 +720,7 @@ __global__ void k_mdas_accept(const SysDev *__restrict__ sys) {
             S.ltype[l] = newt[x];
             for (int k = 0; k < P.bpl; ++k) {
                 const int bt = P.lbt[newt[x] * 16 + k];
-                S.pos[l * P.bpl + k].w = meta_make(bt, bt, k, l + 1);
+                set_meta(S, P, l * P.bpl + k, meta_make(bt, bt, k, l + 1));
             }
         }
     }
@@ -588,7 +739,11 @@ __global__ void k_restore(const SysDev *__restrict__ sys, const int2 *__restrict
     const SysDev &S = sys[bm.x];
     const int i = bm.y + threadIdx.x;
     if (i >= S.p->n || S.c->mdas_accept) return;
-    if (i == 0) { S.c->ke_fresh = 0; S.c->ke_pending = 0; }   // the velocities go back to the snapshot
+    if (i == 0) {   // the velocities go back to the snapshot, the positions leave the pair list
+        S.c->ke_fresh = 0;
+        S.c->ke_pending = 0;
+        S.c->nl_stale = 1;
+    }
     if (i < 2 * KE_SLOTS) S.c->ke_slot[i >> 1][i & 1] = 0;
     S.pos[i] = S.pos_snap[i];
     reinterpret_cast<V4 *>(S.vel)[i] = reinterpret_cast<const V4 *>(S.vel_snap)[i];
@@ -629,7 +784,7 @@ __global__ void k_mark_b(const SysDev *__restrict__ sys, int n, int clear) {
             const uint32_t m = S.pos[id].w;
             const int tb = clear ? meta_ta(m) : (int)P.lbt[C.pairs[MAX_PAIRS + x] * 16 + k];
             const uint32_t nm = meta_make(meta_ta(m), tb, k, l + 1);
-            S.pos[id].w = nm;
+            set_meta(S, P, id, nm);
             S.spos[S.sidx[id]].w = nm;
         }
     }

@@ -47,6 +47,7 @@ class Desc(C.Structure):
         ("kb", C.c_double), ("b0", C.c_double), ("ktheta", C.c_double), ("theta0_deg", C.c_double),
         ("rc", C.c_double), ("eps_r", C.c_double), ("eps_rf", C.c_double),
         ("temperature", C.c_double), ("dt", C.c_double), ("tau_t", C.c_double), ("mass", C.c_double),
+        ("list_skin", C.c_double),
         ("seed", C.c_uint64), ("system_id", C.c_uint32), ("precision", C.c_int32),
         ("cuda_stream", C.c_void_p), ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_ctx", C.c_void_p),
     ]
@@ -73,7 +74,7 @@ class StateView(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("md_steps", "force_evals", "trials", "null_trials", "accepted",
-                                         "moves", "moves_accepted", "kernel_launches")]
+                                         "moves", "moves_accepted", "kernel_launches", "list_builds")]
 
 
 TRIAL_DTYPE = np.dtype([("a", np.int32), ("b", np.int32), ("null", np.int32), ("accepted", np.int32),
@@ -82,7 +83,7 @@ TRIAL_DTYPE = np.dtype([("a", np.int32), ("b", np.int32), ("null", np.int32), ("
 EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_energy", "mdas_md_steps",
            "mdas_swap_trials", "mdas_trial_log", "mdas_alchemical_move", "mdas_delta_energy", "mdas_get_state",
            "mdas_set_state", "mdas_cell_list", "mdas_batch_run", "mdas_philox", "mdas_set_kernel_timing",
-           "mdas_pair_kernel_time", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
+           "mdas_pair_kernel_time", "mdas_set_graphs", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint"]
 
@@ -143,7 +144,7 @@ def _current_stream():
 
 
 def make_desc(m, precision=MDAS_FP32, tau_t=None, dt=None, temperature=None, seed=None, system_id=None,
-              eps_rf=None):
+              eps_rf=None, list_skin=0.0):
     """mdas_system_desc of a `synth.Membrane`; returns (desc, arrays kept alive)."""
     k = dict(pos=np.ascontiguousarray(m.pos, np.float64), vel=np.ascontiguousarray(m.vel, np.float64),
              first=np.ascontiguousarray(m.lipid_first_bead, np.int32),
@@ -170,6 +171,7 @@ def make_desc(m, precision=MDAS_FP32, tau_t=None, dt=None, temperature=None, see
     d.dt = m.dt if dt is None else dt
     d.tau_t = m.tau_t if tau_t is None else tau_t
     d.mass = m.mass
+    d.list_skin = float(list_skin)
     d.seed = int(m.seed if seed is None else seed)
     d.system_id = int(m.system_id if system_id is None else system_id)
     d.precision = precision
@@ -180,13 +182,13 @@ class System:
     """One device-resident membrane system built from a `synth.Membrane`."""
 
     def __init__(self, m, precision="fp32", stream=None, torch_allocator=True, tau_t=None, dt=None,
-                 temperature=None, seed=None, system_id=None, eps_rf=None):
+                 temperature=None, seed=None, system_id=None, eps_rf=None, list_skin=0.0):
         L = lib()
         self.m = m
         self.n = m.n_beads
         self.n_lipids = m.n_lipids
         self.precision = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
-        d, k = make_desc(m, self.precision, tau_t, dt, temperature, seed, system_id, eps_rf)
+        d, k = make_desc(m, self.precision, tau_t, dt, temperature, seed, system_id, eps_rf, list_skin)
         self.stream = _current_stream() if stream is None else int(stream)
         d.cuda_stream = self.stream or None
         if torch_allocator:
@@ -302,6 +304,10 @@ class System:
 
     def set_kernel_timing(self, on=True):
         self._ck(lib().mdas_set_kernel_timing(self._ptr, int(bool(on))))
+
+    def set_graphs(self, on=True):
+        """CUDA-graph replays (default) or plain launches of the same kernels."""
+        self._ck(lib().mdas_set_graphs(self._ptr, int(bool(on))))
 
     def pair_kernel_time(self, reset=False):
         ms, n = C.c_double(), C.c_int64()

@@ -1,0 +1,95 @@
+"""Pair list of the MD step (a Verlet list with a skin, rebuilt when a bead
+has moved half the skin): its rebuilds must not change the physics.
+
+The forces of an MD step are the cutoff sums of Sec. 3 whatever the skin, so
+trajectories with different skins (different rebuild schedules, different
+summation grouping) agree to rounding; graph replays (conditional rebuild
+nodes) and plain launches give the same bits."""
+import numpy as np
+import pytest
+
+from paper_2005_08348_gb300 import mdas, synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rebuilds_happen_and_are_counted():
+    m = synth.mcmd_small()
+    s = mdas.System(m, precision="fp32")
+    s.md_steps(200, swap_every=0)
+    c = s.counters()
+    assert c["md_steps"] == 200
+    assert 2 <= c["list_builds"] < 200, c["list_builds"]
+    # a tiny skin forces a rebuild nearly every step
+    t = mdas.System(m, precision="fp32", list_skin=0.004)
+    t.md_steps(20, swap_every=0)
+    assert t.counters()["list_builds"] >= 10
+
+
+def test_skin_does_not_change_the_trajectory_fp64():
+    m = synth.mcmd_small()
+    out = []
+    for skin in (0.01, 0.3):
+        s = mdas.System(m, precision="fp64", list_skin=skin)
+        s.md_steps(30, swap_every=5)
+        out.append(s.get_state())
+    a, b = out
+    assert np.array_equal(a["ltype"], b["ltype"])
+    d = (a["pos_u"].astype(np.int64) - b["pos_u"].astype(np.int64) + 2**31) % 2**32 - 2**31
+    assert np.abs(d).max() <= 64, np.abs(d).max()
+
+
+def test_graph_and_plain_launches_agree():
+    m = synth.mcmd_small()
+    a = mdas.System(m, precision="fp32")
+    b = mdas.System(m, precision="fp32")
+    a.md_steps(12, swap_every=3)            # graph replays
+    for _ in range(4):
+        b.md_steps(3, swap_every=3)         # short runs take plain launches
+    sa, sb = a.get_state(), b.get_state()
+    assert np.array_equal(sa["pos_u"], sb["pos_u"])
+    assert np.array_equal(sa["vel"], sb["vel"])
+    assert np.array_equal(sa["ltype"], sb["ltype"])
+
+
+def test_one_step_after_rebuild_matches_oracle_fp64():
+    # a state far from the list's build positions (set by set_state) is rebuilt
+    m = synth.mcmd_small()
+    s = mdas.System(m, precision="fp64")
+    s.md_steps(10, swap_every=0)
+    st = s.get_state()
+    rng = np.random.default_rng(5)
+    shift = rng.integers(-2 ** 25, 2 ** 25, size=(m.n_beads, 3))
+    pos_u = ((st["pos_u"].astype(np.int64) + shift) % 2 ** 32).astype(np.uint32)
+    s.set_state(pos_u=pos_u, vel=st["vel"], ltype=st["ltype"], step=st["step"], trial=st["trial"])
+    s.md_steps(1, swap_every=0)
+    got = s.get_state()
+    o = oracle.Oracle(m)
+    so = o.state(pos_u=pos_u, vel=st["vel"], ltype=st["ltype"], step=st["step"])
+    o.md_steps(so, 1)
+    d = (got["pos_u"].astype(np.int64) - so["pos_u"].astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31
+    assert np.abs(d).max() <= 1, np.abs(d).max()
+    assert np.abs(got["vel"] - so["vel"]).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("which", ["small", "large"])
+def test_step_kernel_forces_match_oracle(prec, which):
+    """The MD step's own forces: from rest without a thermostat one step gives
+    v = F dt / m exactly up to one rounding, so F = v m / dt is compared with
+    the oracle's forces at the force tolerance."""
+    m = synth.mcmd_small() if which == "small" else synth.mcmd_large()
+    s = mdas.System(m, precision=prec, tau_t=0.0)
+    s.md_steps(5, swap_every=0)                    # a state the list was built for earlier
+    st = s.get_state()
+    s.set_state(pos_u=st["pos_u"], vel=np.zeros_like(st["vel"]), ltype=st["ltype"], step=st["step"])
+    s.md_steps(8, swap_every=0)                    # moves the beads, keeps the list when it can
+    st = s.get_state()
+    s.set_state(pos_u=st["pos_u"], vel=np.zeros_like(st["vel"]), ltype=st["ltype"], step=st["step"])
+    s.md_steps(1, swap_every=0)
+    F = s.get_state()["vel"] * (m.mass / m.dt)
+    _, Fo = oracle.Oracle(m).energy(st["pos_u"], ltype=st["ltype"])
+    frms = np.sqrt((Fo * Fo).sum(1).mean())
+    err = (np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), frms)).max()
+    assert err < (1e-10 if prec == "fp64" else 1e-5), err

@@ -70,9 +70,11 @@ def test_admission_by_slots_and_memory():
         if a == 0 and q == 0:
             break
     assert max(seen) <= 2 and len(sv.results()) == len(ps)
-    # a budget that holds one system at a time admits them one by one
-    big = max(mdas.footprint(p) for p in ps[:3])
-    sv = mdas.Server(int(1.5 * big), max_active=8, md_quantum=5)
+    # a budget that holds any one of three systems but no two admits them one by one
+    fp = sorted(mdas.footprint(p) for p in ps[:3])
+    budget = fp[0] + fp[1] - 1
+    assert budget >= fp[2]
+    sv = mdas.Server(budget, max_active=8, md_quantum=5)
     for p in ps[:3]:
         sv.submit(p, mdas.JOB_MD, n=10)
     a, q = sv.run(1)
