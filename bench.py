@@ -35,8 +35,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the replica and swap-throughput lines")
-    ap.add_argument("--no-graphs", action="store_true",
-                    help="plain kernel launches instead of CUDA-graph replays (same kernels; for profilers)")
+    ap.add_argument("--separate-launches", action="store_true",
+                    help="one kernel launch per phase instead of the persistent kernel (same arithmetic; for profilers)")
     return ap.parse_args()
 
 
@@ -185,8 +185,8 @@ def run_gpu(args):
     m = workload()
     m.system_id = rank
     sysm = mdas.System(m, precision="fp32", stream=stream.cuda_stream)
-    if args.no_graphs:
-        sysm.set_graphs(False)
+    if args.separate_launches:
+        sysm.set_persistent(False)
     n_pairs0 = sysm.energy()["pairs"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -281,7 +281,7 @@ def run_gpu(args):
         "data": "synthetic (seeded bilayer, no trained parameters)",
         "config": config(m, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                              "pairs_per_force_eval": pairs_per_eval,
-                             "launches": "plain" if args.no_graphs else "cuda graphs"}),
+                             "launches": "separate kernels" if args.separate_launches else "persistent kernel"}),
         "swap_trials_per_s": trials_per_s, "md_steps_per_s": md * ws / tmax,
         "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "e2e": {"value": e2e_value, "unit": "pair-interactions/s", "h2d_bytes_per_step": h2d,

@@ -194,18 +194,22 @@ mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32
  * 0..n-1, key (k0, k1): out [n*4] host. */
 mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out);
 
-/* Kernel timing: when enabled, every 8th MD-step kernel launch of
- * mdas_md_steps and mdas_batch_run is bracketed by CUDA events on the
- * launching stream;
- * mdas_pair_kernel_time returns the sum of their durations (ms) and the launch
- * count since the last reset (reset = 1 clears after reading). */
+/* Kernel timing: when enabled, the MD kernels of mdas_md_steps and
+ * mdas_batch_run are bracketed by CUDA events on the launching stream: each
+ * persistent launch (all phases of its steps), or each separate step kernel.
+ * mdas_pair_kernel_time returns the sum of their durations (ms) and the
+ * number of MD steps they covered since the last reset (reset = 1 clears
+ * after reading). */
 mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable);
 
-/* MD segments of mdas_md_steps and mdas_alchemical_move run as CUDA-graph
- * replays (enable = 1, the default) or as plain launches of the same kernels
- * in the same order (enable = 0), with identical results.  Plain launches
- * serve profilers that cannot look into graphs holding conditional nodes. */
-mdas_status mdas_set_graphs(mdas_system *s, int32_t enable);
+/* MD segments of mdas_md_steps and mdas_alchemical_move run in one
+ * persistent cooperative kernel launch per segment (enable = 1, the default;
+ * one 1024-thread block per SM advances every step, list rebuild,
+ * thermostat update and exchange trial of the segment, with grid-wide
+ * barriers between the phases) or as separate kernel launches per phase
+ * (enable = 0), with identical results.  Separate launches serve profilers
+ * that show one line per kernel. */
+mdas_status mdas_set_persistent(mdas_system *s, int32_t enable);
 mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *launches, int32_t reset);
 
 /* Per-system counters: MD steps, force evaluations (one per MD step and one

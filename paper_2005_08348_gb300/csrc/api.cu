@@ -17,26 +17,19 @@ using namespace mdas;
 
 namespace {
 
-struct GraphEntry {
-    cudaGraphExec_t exec = nullptr;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pair_events;
-    long long kernel_nodes = 0;
-};
-
 struct Batch {
     std::vector<mdas_system *> sys;
     SysDev *dsys = nullptr;
     BlockMap beads, cells, sortcells, syss, nlbeads, lcells, lsort;
     int precision = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t side = nullptr;  // captures the bodies of graph conditionals
     int max_bead_blocks = 1;
     int *dscratch = nullptr;      // [2]: pending sum, error or
     unsigned int *bticket = nullptr;   // last-block ticket of the step kernel over the batch
-    bool use_graphs = true;       // false for batches whose membership changes (the server's)
+    void *rsync = nullptr;        // grid-barrier state of the persistent MD kernel (zeroed)
+    bool persistent = true;       // MD in the persistent kernel (else separate kernel launches)
     size_t cap_sys = 0, cap_beads = 0, cap_cells = 0, cap_sort = 0;   // device capacity (refillable batches)
     size_t cap_nlb = 0, cap_lc = 0, cap_ls = 0;
-    std::map<std::string, GraphEntry> graphs;
     LaunchCtx ctx() const {
         LaunchCtx L;
         L.sys = dsys; L.n_sys = (int)sys.size();
@@ -115,7 +108,6 @@ struct mdas_system {
 
 namespace {
 
-constexpr int TIMING_STRIDE = 8;   // kernel timing brackets every 8th step kernel
 
 std::map<std::vector<mdas_system *>, std::unique_ptr<Batch>> g_batches;
 
@@ -172,16 +164,12 @@ cudaError_t upload_map(BlockMap &m, const std::vector<int2> &v) {
 }
 
 void destroy_batch(Batch *b) {
-    for (auto &kv : b->graphs) {
-        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-        for (auto &ev : kv.second.pair_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
-    }
     free_map(b->beads); free_map(b->cells); free_map(b->sortcells); free_map(b->syss);
     free_map(b->nlbeads); free_map(b->lcells); free_map(b->lsort);
     if (b->dsys) cudaFree(b->dsys);
     if (b->dscratch) cudaFree(b->dscratch);
     if (b->bticket) cudaFree(b->bticket);
-    if (b->side) cudaStreamDestroy(b->side);
+    if (b->rsync) cudaFree(b->rsync);
 }
 
 // block maps of a batch: per system its bead blocks, cells, cell groups of the
@@ -231,7 +219,8 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
     CK(cudaMalloc(&b->dscratch, sizeof(int) * 4));
     CK(cudaMalloc(&b->bticket, sizeof(unsigned int)));
     CK(cudaMemset(b->bticket, 0, sizeof(unsigned int)));
-    CK(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+    CK(cudaMalloc(&b->rsync, md_run_sync_bytes()));
+    CK(cudaMemset(b->rsync, 0, md_run_sync_bytes()));
     out = std::move(b);
     return MDAS_OK;
 }
@@ -242,7 +231,6 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     b.sys = v;
     b.precision = v[0]->precision;
     b.stream = v[0]->stream;
-    b.use_graphs = false;
     b.max_bead_blocks = 1;
     std::vector<SysDev> hs;
     Maps mp;
@@ -275,6 +263,10 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     if (!b.bticket) {
         CK(cudaMalloc(&b.bticket, sizeof(unsigned int)));
         CK(cudaMemset(b.bticket, 0, sizeof(unsigned int)));
+    }
+    if (!b.rsync) {
+        CK(cudaMalloc(&b.rsync, md_run_sync_bytes()));
+        CK(cudaMemset(b.rsync, 0, md_run_sync_bytes()));
     }
     CK(cudaMemcpyAsync(b.dsys, hs.data(), sizeof(SysDev) * hs.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.beads.d, beads.data(), sizeof(int2) * beads.size(), cudaMemcpyHostToDevice, b.stream));
@@ -338,206 +330,94 @@ mdas_status check_err(mdas_system *s, Batch &b) {
     return MDAS_OK;
 }
 
-// Append to the capture on b.stream a conditional node whose body rebuilds
-// the pair lists (kernels return at once for systems whose list is valid);
-// `cond` must have been created on the capturing graph and is set by a kernel
-// captured before this call.
-mdas_status add_build_conditional(mdas_system *s, Batch &b, cudaGraphConditionalHandle cond) {
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t nd = 0;
-    CK(cudaStreamGetCaptureInfo(b.stream, &cs, nullptr, &g, &deps, nullptr, &nd));
-    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
-    np.conditional.handle = cond;
-    np.conditional.type = cudaGraphCondTypeIf;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    CK(cudaStreamBeginCaptureToGraph(b.side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    LaunchCtx L = b.ctx();
-    L.stream = b.side;
-    launch_nl_build(L, 1);
-    cudaGraph_t body_out;
-    CK(cudaStreamEndCapture(b.side, &body_out));
-    CK(cudaStreamUpdateCaptureDependencies(b.stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    return MDAS_OK;
-}
-
-mdas_status new_cond(mdas_system *s, Batch &b, cudaGraphConditionalHandle *out) {
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g;
-    CK(cudaStreamGetCaptureInfo(b.stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
-    CK(cudaGraphConditionalHandleCreate(out, g, 0, cudaGraphCondAssignDefault));
-    return MDAS_OK;
-}
-
-// Capture (or reuse) a graph of `units` repetitions of [steps_per_unit MD
-// steps + optional exchange trial].  It first draws the thermostat variates
-// of all its steps and sets the first step's factor, rebuilds stale pair
-// lists (conditional node), and after every step kernel, which sets the
-// conditional, rebuilds them again if a bead moved too far; so the trial and
-// the next step always find valid lists.  timing adds event pairs around
-// every TIMING_STRIDE-th step kernel.
-mdas_status get_graph(mdas_system *s, Batch &b, int units, int steps_per_unit, bool trial, bool lambda, bool timing,
-                      GraphEntry **out) {
-    char key[128];
-    snprintf(key, sizeof(key), "u%d_s%d_t%d_l%d_m%d", units, steps_per_unit, (int)trial, (int)lambda, (int)timing);
-    auto it = b.graphs.find(key);
-    if (it != b.graphs.end()) { *out = &it->second; return MDAS_OK; }
-    GraphEntry ge;
-    cudaGraph_t g;
-    if (timing) {
-        for (int k = 0; k < units * steps_per_unit; k += TIMING_STRIDE) {
-            cudaEvent_t e0, e1;
-            CK(cudaEventCreate(&e0));
-            CK(cudaEventCreate(&e1));
-            ge.pair_events.push_back({e0, e1});
-        }
+// Timing of the MD kernels: events around each launch, read after the segment.
+struct SegTimer {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+    std::vector<long long> steps;
+    cudaError_t begin(cudaStream_t st, long long n) {
+        if (!on) return cudaSuccess;
+        cudaEvent_t e0, e1;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) return e;
+        evs.push_back({e0, e1});
+        steps.push_back(n);
+        return cudaEventRecord(e0, st);
     }
-    CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
-    mdas_status st = MDAS_OK;
-    LaunchCtx L = b.ctx();
-    // the step kernel of step k sets the factor of step k + 1
-    launch_thermo_draws(L, units * steps_per_unit + 1);
-    launch_thermostat(L);
-    cudaGraphConditionalHandle cond;
-    st = new_cond(s, b, &cond);
-    if (st == MDAS_OK) {
-        launch_nl_decide(L, cond);
-        st = add_build_conditional(s, b, cond);
-    }
-    int ev = 0, step_no = 0;
-    for (int u = 0; u < units && st == MDAS_OK; ++u) {
-        for (int k = 0; k < steps_per_unit && st == MDAS_OK; ++k, ++step_no) {
-            st = new_cond(s, b, &cond);
-            if (st != MDAS_OK) break;
-            if (timing && step_no % TIMING_STRIDE == 0) {
-                // external event nodes: recorded (and timed) at every replay
-                cudaEventRecordWithFlags(ge.pair_events[ev].first, b.stream, cudaEventRecordExternal);
-                launch_nl_step(L, lambda, cond, 1);
-                cudaEventRecordWithFlags(ge.pair_events[ev].second, b.stream, cudaEventRecordExternal);
-                ++ev;
-            } else {
-                launch_nl_step(L, lambda, cond, 1);
-            }
-            st = add_build_conditional(s, b, cond);
-        }
-        if (trial && st == MDAS_OK) launch_trial_nl(L);
-    }
-    cudaError_t e = cudaStreamEndCapture(b.stream, &g);
-    if (st != MDAS_OK) {
-        if (e == cudaSuccess) cudaGraphDestroy(g);
-        return st;
-    }
-    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
-    size_t n_nodes = 0;
-    cudaGraphGetNodes(g, nullptr, &n_nodes);
-    std::vector<cudaGraphNode_t> nodes(n_nodes);
-    if (n_nodes) cudaGraphGetNodes(g, nodes.data(), &n_nodes);
-    for (auto nd : nodes) {
-        cudaGraphNodeType ty;
-        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ge.kernel_nodes++;
-    }
-    e = cudaGraphInstantiate(&ge.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
-    auto r = b.graphs.emplace(key, std::move(ge));
-    *out = &r.first->second;
-    return MDAS_OK;
-}
-
-mdas_status replay(mdas_system *s, Batch &b, GraphEntry *ge) {
-    CK(cudaGraphLaunch(ge->exec, b.stream));
-    for (auto *x : b.sys) x->kernel_launches += ge->kernel_nodes;
-    if (!ge->pair_events.empty()) {
-        CK(cudaStreamSynchronize(b.stream));
-        for (auto &ev : ge->pair_events) {
+    cudaError_t end(cudaStream_t st) { return on ? cudaEventRecord(evs.back().second, st) : cudaSuccess; }
+    cudaError_t collect(Batch &b) {
+        if (evs.empty()) return cudaSuccess;
+        cudaError_t e = cudaStreamSynchronize(b.stream);
+        for (size_t k = 0; k < evs.size() && e == cudaSuccess; ++k) {
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, ev.first, ev.second));
-            for (auto *x : b.sys) { x->pair_ms += ms; x->pair_launches += 1; }
+            e = cudaEventElapsedTime(&ms, evs[k].first, evs[k].second);
+            for (auto *x : b.sys) { x->pair_ms += ms; x->pair_launches += steps[k]; }
         }
+        for (auto &ev : evs) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+        evs.clear();
+        return e;
     }
-    return MDAS_OK;
+};
+
+__global__ void k_run_abort(void *sync, int nbytes, const SysDev *__restrict__ sys, int n_sys) {
+    // a persistent launch that gave up at a barrier: every system of the
+    // batch records it, and the barrier state is cleared for the next launch
+    const int *w = (const int *)sync;
+    const int ab = w[2];
+    if (ab == 0) return;
+    for (int q = threadIdx.x; q < n_sys; q += blockDim.x) atomicOr(&sys[q].c->err, ab);
+    __syncthreads();
+    if (threadIdx.x == 0) memset(sync, 0, nbytes);
 }
 
 // n_steps MD steps on a batch; after every swap_every-th step one trial.
+// Segments of up to MAX_DRAW_STEPS - 1 steps: the thermostat variates of the
+// segment, the first step's factor, then the persistent kernel (or, when it
+// cannot run or plain launches are asked for, the separate kernels step by
+// step, with the same arithmetic).
 mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, bool lambda = false,
                    bool check = true) {
     if (n_steps <= 0) return MDAS_OK;
     const bool trial = swap_every > 0;
-    const long long unit = trial ? swap_every : 1;
-    const long long n_units = n_steps / unit;
-    const long long rem = n_steps % unit;
-    bool timing = false;
-    for (auto *x : b.sys) timing = timing || x->timing;
+    SegTimer tm;
+    for (auto *x : b.sys) tm.on = tm.on || x->timing;
     for (auto *x : b.sys) x->cells_valid = false;
-    if (!b.use_graphs || n_units == 0 || n_steps < 4) {
-        // plain launches, same arithmetic: the list kernels return at once
-        // for systems whose list is valid
-        LaunchCtx L = b.ctx();
-        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
-        long long launches = 0;
-        for (long long k0 = 0; k0 < n_steps; k0 += MAX_DRAW_STEPS - 1) {
-            const long long k1 = std::min(n_steps, k0 + MAX_DRAW_STEPS - 1);
-            launch_thermo_draws(L, (int)(k1 - k0 + 1));
-            launch_thermostat(L);
-            launches += 2;
-            for (long long k = k0; k < k1; ++k) {
-                launch_nl_build(L, 0);
-                if (timing && k % TIMING_STRIDE == 0) {
-                    cudaEvent_t e0, e1;
-                    CK(cudaEventCreate(&e0));
-                    CK(cudaEventCreate(&e1));
-                    evs.push_back({e0, e1});
-                    CK(cudaEventRecord(e0, b.stream));
-                    launch_nl_step(L, lambda, 0, 0);
-                    CK(cudaEventRecord(e1, b.stream));
-                } else {
-                    launch_nl_step(L, lambda, 0, 0);
-                }
-                launches += 5;
-                if (trial && (k + 1) % unit == 0) { launch_trial_nl(L); ++launches; }
-            }
+    LaunchCtx L = b.ctx();
+    const bool persistent = b.persistent && md_run_blocks(b.precision, lambda) > 0;
+    // segments end on a trial boundary so that every trial follows its step
+    long long seg = MAX_DRAW_STEPS - 1;
+    if (trial) seg = std::max<long long>(swap_every, seg / swap_every * swap_every);
+    long long launches = 0;
+    for (long long k0 = 0; k0 < n_steps; k0 += seg) {
+        const long long n = std::min(seg, n_steps - k0);
+        launch_thermo_draws(L, (int)std::min<long long>(n + 1, MAX_DRAW_STEPS));
+        launch_thermostat(L);
+        launches += 2;
+        if (persistent) {
+            CK(tm.begin(b.stream, n));
+            CK(launch_md_run(L, lambda, (int)n, swap_every, b.rsync));
+            CK(tm.end(b.stream));
+            k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
+            launches += 1;
+            continue;
         }
-        for (auto *x : b.sys) x->kernel_launches += launches;
-        CK(cudaGetLastError());
-        if (!evs.empty()) {
-            CK(cudaStreamSynchronize(b.stream));
-            for (auto &ev : evs) {
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, ev.first, ev.second));
-                for (auto *x : b.sys) { x->pair_ms += ms; x->pair_launches += 1; }
-                cudaEventDestroy(ev.first);
-                cudaEventDestroy(ev.second);
-            }
+        // the same order as the persistent kernel: a build for lists made
+        // stale outside, then per step: step, build after a violation, trial
+        launch_nl_build(L);
+        launches += 4;
+        for (long long k = 0; k < n; ++k) {
+            CK(tm.begin(b.stream, 1));
+            launch_nl_step(L, lambda);
+            CK(tm.end(b.stream));
+            launch_nl_build(L);
+            launches += 5;
+            if (trial && (k0 + k + 1) % swap_every == 0) { launch_trial_nl(L); ++launches; }
         }
-        return check ? check_err(s, b) : MDAS_OK;
     }
-    const long long E = std::min<long long>(n_units, trial ? std::max<long long>(1, 64 / unit) : 64);
-    GraphEntry *ge;
-    mdas_status st;
-    for (long long r = 0; r < n_units / E; ++r) {
-        st = get_graph(s, b, (int)E, (int)unit, trial, lambda, timing, &ge);
-        if (st != MDAS_OK) return st;
-        st = replay(s, b, ge);
-        if (st != MDAS_OK) return st;
-    }
-    const long long left = n_units % E;
-    if (left > 0) {
-        st = get_graph(s, b, (int)left, (int)unit, trial, lambda, timing, &ge);
-        if (st != MDAS_OK) return st;
-        st = replay(s, b, ge);
-        if (st != MDAS_OK) return st;
-    }
-    if (rem > 0) {
-        st = get_graph(s, b, 1, (int)rem, false, lambda, timing, &ge);
-        if (st != MDAS_OK) return st;
-        st = replay(s, b, ge);
-        if (st != MDAS_OK) return st;
-    }
+    for (auto *x : b.sys) x->kernel_launches += launches;
     CK(cudaGetLastError());
+    CK(tm.collect(b));
     return check ? check_err(s, b) : MDAS_OK;
 }
 
@@ -1220,9 +1100,9 @@ mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable) {
     return MDAS_OK;
 }
 
-mdas_status mdas_set_graphs(mdas_system *s, int32_t enable) {
-    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_graphs: NULL system");
-    s->solo->use_graphs = enable != 0;
+mdas_status mdas_set_persistent(mdas_system *s, int32_t enable) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_persistent: NULL system");
+    s->solo->persistent = enable != 0;
     return MDAS_OK;
 }
 
@@ -1247,9 +1127,7 @@ mdas_status mdas_get_counters(const mdas_system *cs, mdas_counters *out) {
     out->accepted = (int64_t)c.accepted;
     out->moves = (int64_t)c.moves;
     out->moves_accepted = (int64_t)c.moves_accepted;
-    // graph kernel nodes at every replay, plus the 4 list-build kernels of
-    // every graph conditional that ran
-    out->kernel_launches = (int64_t)s->kernel_launches + 4 * (int64_t)c.nl_builds_cond;
+    out->kernel_launches = (int64_t)s->kernel_launches;
     out->list_builds = (int64_t)c.nl_builds;
     return MDAS_OK;
 }

@@ -25,6 +25,8 @@ constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
 constexpr int MAX_ROUND_TRIALS = 1024; // trials per batched swap evaluation
 constexpr int MAX_PAIRS = 64;
+constexpr int DE_GROUPS = 9;           // blocks that share the energy change of one batched trial
+constexpr int TRIAL_PARTS = 16;        // 128-thread parts of one trial over the pair list
 constexpr int MAX_CHANGED = 2 * MAXT * MAX_PAIRS;
 constexpr double FIX = 4294967296.0;   // force fixed point: 2^32 units per kJ/mol/nm
 constexpr double TWO32 = 4294967296.0;
@@ -111,11 +113,11 @@ struct Counters {
     long long ke_slot[KE_SLOTS][2];    // fixed-point kinetic energy per slot and group (2^32 units)
     int nl_stale;                      // the pair list must be rebuilt before its next use
     int nl_viol;                       // a bead moved farther than the skin allows (this step)
+    int nl_violp[2];                   // the same per step parity (persistent kernel)
     int nl_par;                        // lpos buffer holding the current positions
-    unsigned int sticket;              // last-block ticket of the step kernel
+    unsigned int sticket;              // last-block ticket of the step kernel (separate launches)
     unsigned int nticket;              // last-block ticket of the list-build count kernel
     unsigned long long nl_builds;      // pair-list builds
-    unsigned long long nl_builds_cond; // of which inside a graph conditional (4 kernels each)
 };
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
@@ -166,6 +168,15 @@ struct SysDev {
 };
 
 // ---------------------------------------------------------------- Philox
+// 128 threads of a block that synchronise on their own named barrier `bar`
+// (1..15): the unit of work of the pair-list kernels, run as a whole block or
+// as one of several groups of the persistent kernel's blocks.
+struct Grp {
+    int t, bar;
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory"); }
+};
+constexpr int GRP = 128;
+
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, two 32x32->64
 // multiplications per round, key advanced by the Weyl constants.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -221,13 +232,18 @@ void launch_trial_one(const LaunchCtx &L);
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64);
 void launch_step(const LaunchCtx &L, bool lambda);
 void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
-// pair-list MD (kernels.cu): thermostat factor of the coming step; list build
-// (kernels return at once for systems whose list is valid); one step, which
-// sets the graph conditional `cond` (when use_cond) to "some list is stale"
+// pair-list MD: thermostat factor of the coming step (kernels.cu); list build
+// (its kernels return at once for systems whose list is valid), one step of
+// every system (plist.cu); a whole MD segment in one cooperative launch of
+// the persistent kernel (cudaErrorCooperativeLaunchTooLarge when it cannot
+// run resident on this device), with a zeroed device RunSync of
+// md_run_sync_bytes() bytes per batch
 void launch_thermostat(const LaunchCtx &L);
-void launch_nl_build(const LaunchCtx &L, int in_conditional);
-void launch_nl_decide(const LaunchCtx &L, cudaGraphConditionalHandle cond);
-void launch_nl_step(const LaunchCtx &L, bool lambda, cudaGraphConditionalHandle cond, int use_cond);
+void launch_nl_build(const LaunchCtx &L);
+void launch_nl_step(const LaunchCtx &L, bool lambda);
+int md_run_blocks(int precision, bool lambda);
+cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, void *sync);
+size_t md_run_sync_bytes();
 void launch_trial_nl(const LaunchCtx &L);
 void launch_energy_reduce(const LaunchCtx &L);
 

@@ -1,0 +1,198 @@
+// Exchange-trial arithmetic shared by the kernel translation units: the FP64
+// pair energy change, a fixed-order block sum and one trial over the pair
+// list.  Not part of the public ABI.
+#pragma once
+#include "mdas_dev.cuh"
+
+namespace mdas {
+
+// FP64 change of one pair's energy (LJ with potential shift + reaction field)
+// when its type pair goes from (oi, oj) to (ni, nj), at squared distance r2;
+// 1/r from a float seed refined by two Newton steps (no FP64 divide or sqrt).
+__device__ __forceinline__ double pair_du(const Params &P, int oi, int oj, int ni, int nj, double r2) {
+    const int xo = oi * 16 + oj, xn = ni * 16 + nj;
+    double ri = (double)rsqrtf((float)r2);
+    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+    const double r2i = ri * ri;
+    const double r6 = r2i * r2i * r2i;
+    return (P.c12[xn] - P.c12[xo]) * r6 * r6 - (P.c6[xn] - P.c6[xo]) * r6 - (P.ush[xn] - P.ush[xo]) +
+           (P.qq[xn] - P.qq[xo]) * (ri + P.krf * r2 - P.crf);
+}
+
+// Metropolis test of Eq. 1, accept iff dE + kT ln u <= 0, decided as in FP64:
+// a float logarithm (error far below 1e-3 kJ/mol after the kT factor) settles
+// every case outside a 1e-3 band, the FP64 logarithm the rest.
+__device__ inline bool metropolis(double dE, double kT, double u) {
+    const double est = dE + kT * (double)logf((float)u);
+    if (fabs(est) > 1e-3) return est <= 0.0;
+    return dE + kT * log(u) <= 0.0;
+}
+
+// fixed-order sum over the block: a shuffle tree per warp, then the warp
+// sums in order (blockDim.x a multiple of 32, at most 1024)
+__device__ inline double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    __syncthreads();
+    return s;
+}
+
+struct TrialSmem {
+    double sh[GRP / 32];
+    int it_beg[2 * MAXT * NL_G + 1];
+    int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT], chg_k[2 * MAXT];
+    uint4 chg_pos[2 * MAXT];
+    int nchg, last, accept;
+};
+
+// fixed-order sum over a 128-thread group: a shuffle tree per warp, then the
+// four warp sums in order
+__device__ inline double group_sum(double v, const Grp &g, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((g.t & 31) == 0) sh[g.t >> 5] = v;
+    g.sync();
+    double s = 0.0;
+    for (int w = 0; w < GRP / 32; ++w) s += sh[w];
+    g.sync();
+    return s;
+}
+
+// Part p (of TRIAL_PARTS) of one exchange trial from the pair list (valid
+// whenever an MD step has just run), by one 128-thread group.  The trial's
+// items are (changed bead, list column, row); part p takes every
+// TRIAL_PARTS-th of them, so the FP64 pair terms spread over the parts.
+// Every list holds all partners closer than rc, so the dE is the same sum as
+// over the 27 cells.  The last part to finish (a ticket) adds the part sums
+// in order, takes the Metropolis decision and applies it.
+__device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp &g, TrialSmem &sm) {
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    const int t = g.t, lane = t & 31;
+    const unsigned long long T = C.trial;
+    const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
+    const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
+    const int ta = S.ltype[a], tb = S.ltype[b];
+    const bool null_trial = (a == b) || (ta == tb);
+    int m = 0;                                   // local indices whose bead type changes
+    if (!null_trial)
+        for (int k = 0; k < P.bpl; ++k) m |= (P.lbt[ta * 16 + k] != P.lbt[tb * 16 + k]) << k;
+    const uint4 *cur = S.lpos + (size_t)par * P.n;
+    if (t < 32) {
+        const int side = lane >= P.bpl, k = side ? lane - P.bpl : lane;
+        const bool ch = lane < 2 * P.bpl && ((m >> k) & 1);
+        const unsigned bal = __ballot_sync(0xffffffffu, ch);
+        if (ch) {
+            const int o = __popc(bal & ((1u << lane) - 1u));
+            const int id = (side ? b : a) * P.bpl + k;
+            const int kk = S.lk[id];
+            sm.chg_id[o] = id;
+            sm.chg_k[o] = kk;
+            sm.chg_pos[o] = cur[kk];
+            sm.chg_old[o] = P.lbt[(side ? tb : ta) * 16 + k];
+            sm.chg_new[o] = P.lbt[(side ? ta : tb) * 16 + k];
+        }
+        if (lane == 0) sm.nchg = __popc(bal);
+    }
+    g.sync();
+    const int nc = sm.nchg, nit = nc * NL_G;
+    if (t < 32) {
+        // items (changed bead, column): exclusive offsets of their row counts,
+        // NL_G items per lane, one warp scan
+        int v[NL_G], sum = 0;
+#pragma unroll
+        for (int q = 0; q < NL_G; ++q) {
+            const int it = NL_G * lane + q;
+            v[q] = it < nit ? S.nl_n[(size_t)sm.chg_k[it / NL_G] * NL_G + q] : 0;
+            sum += v[q];
+        }
+        int inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += x;
+        }
+        int run = inc - sum;
+#pragma unroll
+        for (int q = 0; q < NL_G; ++q) {
+            const int it = NL_G * lane + q;
+            if (it < nit) sm.it_beg[it] = run;
+            run += v[q];
+        }
+        if (lane == 31) sm.it_beg[nit] = inc;
+    }
+    g.sync();
+    const int total = nc > 0 ? sm.it_beg[nit] : 0;
+    double acc = 0.0;
+    for (int f = p + TRIAL_PARTS * t; f < total; f += TRIAL_PARTS * GRP) {
+        int lo = 0, hi = nit - 1;                 // the item holding entry f
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sm.it_beg[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int ci = lo / NL_G, q = lo % NL_G, row = f - sm.it_beg[lo];
+        const int kj = S.nl[(size_t)row * P.lrow + (size_t)sm.chg_k[ci] * NL_G + q];
+        const uint4 pi = sm.chg_pos[ci], pj = cur[kj];
+        const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
+        const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
+        const float r2f = fx * fx + fy * fy + fz * fz;
+        if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
+        const int lj = meta_lip(pj.w), kjl = meta_k(pj.w);
+        const bool chj = (lj == a || lj == b) && ((m >> kjl) & 1);
+        if (chj && lj * P.bpl + kjl < sm.chg_id[ci]) continue;     // a changed pair once, by the lower id
+        const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 >= P.rc2) continue;
+        const int old_j = meta_ta(pj.w);
+        const int new_j = chj ? (int)P.lbt[(lj == a ? tb : ta) * 16 + kjl] : old_j;
+        acc += pair_du(P, sm.chg_old[ci], old_j, sm.chg_new[ci], new_j, r2);
+    }
+    const double part = group_sum(acc, g, sm.sh);
+    if (t == 0) {
+        S.tdE[p] = part;
+        __threadfence();
+        sm.last = atomicAdd(&C.ticket, 1u) == TRIAL_PARTS - 1;
+    }
+    g.sync();
+    if (!sm.last) return;
+    if (t == 0) {
+        __threadfence();
+        double dE = 0.0;
+        for (int q = 0; q < TRIAL_PARTS; ++q) dE += __ldcg(&S.tdE[q]);
+        TrialRec r;
+        r.a = a; r.b = b; r.u = unit53(w.z, w.w); r.dE = 0.0; r.accepted = 0; r.index = T;
+        r.null_trial = null_trial;
+        if (!null_trial) {
+            r.dE = dE;
+            r.accepted = metropolis(dE, P.kT, r.u);
+        }
+        sm.accept = r.accepted;
+        if (r.accepted) { S.ltype[a] = tb; S.ltype[b] = ta; }
+        S.log[T % LOG_CAP] = r;
+        C.trials++;
+        C.force_evals++;
+        C.null_trials += r.null_trial;
+        C.accepted += r.accepted;
+        C.trial = T + 1;
+        C.pending = 0;
+        C.ticket = 0;
+    }
+    g.sync();
+    if (sm.accept && t < 2 * P.bpl) {            // the exchange: every bead of both lipids
+        const int side = t >= P.bpl, k = side ? t - P.bpl : t;
+        const int l = side ? b : a, lt = side ? ta : tb;
+        const int id = l * P.bpl + k;
+        const int bt = P.lbt[lt * 16 + k];
+        const uint32_t mm = meta_make(bt, bt, k, l + 1);
+        S.pos[id].w = mm;
+        const_cast<uint4 *>(cur)[S.lk[id]].w = mm;
+    }
+    g.sync();
+}
+
+}  // namespace mdas

@@ -1,4 +1,4 @@
-// Pair-list (Verlet list with a skin) MD step for sm_103a.
+// Pair-list (Verlet list with a skin) MD for sm_103a.
 //
 // The forces are the cutoff sums of arXiv:2005.08348 Sec. 3 (Lennard-Jones
 // with potential shift and reaction field inside rc, harmonic bonds, cosine
@@ -8,42 +8,45 @@
 // Every pair closer than rl = rc + skin when the list is built sits in the
 // lists of both beads.  While no bead has moved farther than skin / 2 since
 // the build, every pair closer than rc is in the lists (triangle inequality),
-// so a step over the lists gives exactly the cutoff sums; the step kernel
-// checks each bead's displacement from its build position and flags the list
-// stale, and the build runs (inside a CUDA-graph conditional node) before the
-// list is used again.
+// so a step over the lists gives exactly the cutoff sums; each step checks
+// every bead's displacement from its build position, and a violation has the
+// list rebuilt before it is used again.
 //
 // List order: beads grouped by cell of a grid of edge >= rl, ascending id
-// within a cell, so that the beads of one block and their partners lie close
-// together in memory.  Positions live in list order in two buffers (read the
-// current one, write the next); the id-ordered position array is written as
-// well, so every other kernel sees the current coordinates.
+// within a cell, so that the beads of one work item and their partners lie
+// close together in memory.  Positions live in list order in two buffers
+// (read the current one, write the next); the id-ordered position array is
+// written as well, so every other kernel sees the current coordinates.
 //
-// Build (4 kernels, each returning at once for a system whose list is valid):
-//   count  - beads into list-build cells; the last block scans the counts
-//   place  - one warp per cell orders its beads by id and places them
-//   build  - one CTA per cell: the lists of its beads from the 27 neighbour
-//            cells (excluded 1-2 pairs left out), and the list indices of
-//            each bead's bonded partners
+// Build: count (beads into list-build cells; the last item of a system scans
+// the counts), place (one warp per cell orders its beads by id and places
+// them), build (the lists of one cell's beads from the 27 neighbour cells,
+// excluded 1-2 pairs left out, and the list indices of each bead's bonded
+// partners).  A bead's list has NL_G columns; partners go to the columns in
+// turn and lane g of the step sums column g.
 //
-// A bead's list has NL_G columns; column g holds the partners found by lane g
-// of the build among every NL_G-th candidate and is summed by lane g of the
-// step kernel.
-//   done   - clears the stale flag and counts the build
+// Step: NL_G threads per bead, each summing its column; the partial forces are
+// summed across the lanes in a fixed tree (the list fixes which entries each
+// lane sums and in which order, so the result is reproducible bit for bit,
+// alone or in a batch), the bonded force joins them and one thread per bead
+// integrates.  Per system, the kinetic energy of the new velocities is summed
+// in integer slots and turned into the next step's thermostat factor.
 //
-// Step kernel: NL_G threads per bead, each summing one column of its list;
-// the partial forces are summed across the NL_G lanes in a fixed tree (the
-// list fixes which entries each lane sums and in which order, so the result
-// is reproducible bit for bit, alone or in a batch), the bonded force joins
-// them, and one thread per bead integrates.  The last block of a system (a ticket, no
-// waiting) sums the kinetic energy, computes the next step's thermostat
-// factor, advances the counters and decides whether the list is stale; the
-// last block of the whole batch sets the graph conditional.
+// Every piece of work is an item for a group of 128 threads that synchronises
+// on its own named barrier, so the same code runs as separate kernels (one
+// group per block) and inside the persistent kernel k_md_run: one block of
+// 1024 threads (8 groups) per SM, which advances whole MD segments (steps,
+// list rebuilds, thermostat, exchange trials) with grid-wide barriers
+// between the phases instead of kernel launches.
 #include <cmath>
 
 #include "mdas_phys.cuh"
+#include "mdas_trial.cuh"
 
 namespace mdas {
+
+constexpr int RUN_GROUPS = 8;                 // groups per block of the persistent kernel
+constexpr int RUN_THREADS = GRP * RUN_GROUPS;
 
 __device__ __forceinline__ int lcell_of(const Params &P, uint4 q) {
     const int cx = (int)(((unsigned long long)q.x * (unsigned)P.ln[0]) >> 32);
@@ -52,69 +55,93 @@ __device__ __forceinline__ int lcell_of(const Params &P, uint4 q) {
     return (cz * P.ln[1] + cy) * P.ln[0] + cx;
 }
 
-// ------------------------------------------------------------------ build
-// grid: the bead blocks of every system (BEAD_BLOCK beads each)
-__global__ void __launch_bounds__(BEAD_BLOCK) k_nl_count(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
+// ------------------------------------------------------- shared memory
+template <typename Real>
+struct StepSmem {
+    using V4 = typename Vec4<Real>::T;
+    V4 tab[256];                              // 12 C12, 6 C6, qq per type pair
+    V4 svel[NL_BEADS];
+    uint4 sxref[NL_BEADS];
+    uint4 spart[NL_BEADS][NL_PART];
+    Real kered[2][NL_BEADS];
+    int sviol;
+};
+
+struct BuildSmem {
+    int2 nb[27];
+    int noff[28];
+    int last;
+    int ws[GRP / 32];
+    float4 sf[NLB_STAGE];                     // frame coordinates, meta word in w
+    int sk[NLB_STAGE];                        // list index
+};
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
+template <typename Real>
+constexpr size_t group_smem() {
+    return (cmax(cmax(sizeof(StepSmem<Real>), sizeof(BuildSmem)), sizeof(TrialSmem)) + 15) & ~(size_t)15;
+}
+
+// ------------------------------------------------------------ build items
+// Count the beads [b0, b0 + GRP) into list-build cells; the last item of the
+// system (a ticket) scans the counts into (first list index, count) per cell.
+__device__ void nl_count_item(const SysDev &S, int b0, const Grp &g, BuildSmem &sm) {
     const Params &P = *S.p;
     Counters &C = *S.c;
-    if (!C.nl_stale) return;
-    const int t = threadIdx.x;
-    const int i = bm.y + t;
+    const int i = b0 + g.t;
     if (i < P.n) {
         const int c = lcell_of(P, S.pos[i]);
         const int slot = atomicAdd(&S.lcell_count[c], 1);
         if (slot < P.lcapc) S.ltmp[c * P.lcapc + slot] = i;
         else atomicOr(&C.err, ERR_CELL_OVERFLOW);
     }
-    __shared__ int last;
-    __shared__ int ws[BEAD_BLOCK / 32];
-    __syncthreads();
-    if (t == 0) {
+    g.sync();
+    if (g.t == 0) {
         __threadfence();
-        last = atomicAdd(&C.nticket, 1u) == (unsigned)(S.n_bead_blocks - 1);
+        sm.last = atomicAdd(&C.nticket, 1u) == (unsigned)(S.n_bead_blocks - 1);
     }
-    __syncthreads();
+    g.sync();
+    const bool last = sm.last;
+    g.sync();
     if (!last) return;
     __threadfence();
-    // exclusive scan of the counts: each thread a run of cells, then the block
+    // exclusive scan: each thread a run of cells, then the group
     const int nc = P.n_lcells;
-    const int per = (nc + BEAD_BLOCK - 1) / BEAD_BLOCK;
-    const int c0 = min(t * per, nc), c1 = min(c0 + per, nc);
+    const int per = (nc + GRP - 1) / GRP;
+    const int c0 = min(g.t * per, nc), c1 = min(c0 + per, nc);
     int sum = 0;
     for (int c = c0; c < c1; ++c) sum += min(__ldcg(&S.lcell_count[c]), P.lcapc);
-    const int lane = t & 31, w = t >> 5;
+    const int lane = g.t & 31, w = g.t >> 5;
     int inc = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int x = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += x;
     }
-    if (lane == 31) ws[w] = inc;
-    __syncthreads();
+    if (lane == 31) sm.ws[w] = inc;
+    g.sync();
     int run = inc - sum;
-    for (int q = 0; q < w; ++q) run += ws[q];
+    for (int q = 0; q < w; ++q) run += sm.ws[q];
     for (int c = c0; c < c1; ++c) {
         const int m = min(__ldcg(&S.lcell_count[c]), P.lcapc);
         S.lcell[c] = make_int2(run, m);
         S.lcell_count[c] = 0;
         run += m;
     }
-    if (t == 0) C.nticket = 0;
+    if (g.t == 0) C.nticket = 0;
+    g.sync();
 }
 
-// grid: CELLS_PER_SORT_BLOCK list-build cells per block, one warp each
-__global__ void __launch_bounds__(32 * CELLS_PER_SORT_BLOCK) k_nl_place(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
+// Place the beads of cells c0 .. c0 + 3 (one warp each) in list order, ranked
+// by id within their cell, into position buffer par.
+__device__ void nl_place_item(const SysDev &S, int c0, int par, const Grp &g) {
     const Params &P = *S.p;
-    if (!S.c->nl_stale) return;
-    const int c = bm.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int c = c0 + (g.t >> 5), lane = g.t & 31;
     if (c >= P.n_lcells) return;
     const int2 lc = S.lcell[c];
     const int cnt = lc.y, base = c * P.lcapc;
-    uint4 *cur = S.lpos + (size_t)S.c->nl_par * P.n;
+    uint4 *cur = S.lpos + (size_t)par * P.n;
     for (int a0 = 0; a0 < cnt; a0 += 32) {
         const int a = a0 + lane;
         const int id = a < cnt ? S.ltmp[base + a] : 0x7fffffff;
@@ -134,27 +161,17 @@ __global__ void __launch_bounds__(32 * CELLS_PER_SORT_BLOCK) k_nl_place(const Sy
     }
 }
 
-// grid: one CTA (128 threads) per list-build cell.  The 27 neighbour cells
-// are staged in shared memory in a frame centred on the cell (exact integer
-// offsets as floats; with 3 or more cells per edge every partner within rl of
-// a bead of the cell has an offset below half a box, so the frame difference
-// is the minimum image).  Thread (bead, g) scans every NL_G-th candidate and
-// appends the partners it finds to column g of the bead's list, the column
-// that lane g of the step kernel reads: no coordination between threads, and
-// the order of every column is fixed by the staging order.
-__global__ void __launch_bounds__(128) k_nl_build(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
+// The lists of the beads of list-build cell c.  The 27 neighbour cells are
+// staged in a frame centred on the cell (exact integer offsets as floats;
+// with 3 or more cells per edge every partner within rl of a bead of the cell
+// has an offset below half a box, so the frame difference is the minimum
+// image).  Thread (bead, g) tests every NL_G-th candidate; the bead's NL_G
+// lanes agree through a ballot on where each partner goes.
+__device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, BuildSmem &sm) {
     const Params &P = *S.p;
     Counters &C = *S.c;
-    if (!C.nl_stale) return;
-    const int c = bm.y;
-    const int t = threadIdx.x;
-    __shared__ int2 nb[27];
-    __shared__ int noff[28];
-    __shared__ float4 sf[NLB_STAGE];       // frame coordinates, meta word in w
-    __shared__ int sk[NLB_STAGE];          // list index
-    const uint4 *cur = S.lpos + (size_t)C.nl_par * P.n;
+    const int t = g.t;
+    const uint4 *cur = S.lpos + (size_t)par * P.n;
     const int nx = P.ln[0], ny = P.ln[1], nz = P.ln[2];
     const int cz = c / (nx * ny), cxy = c - cz * nx * ny, cy = cxy / nx, cx = cxy - cy * nx;
     if (t < 27) {
@@ -163,25 +180,26 @@ __global__ void __launch_bounds__(128) k_nl_build(const SysDev *__restrict__ sys
         x += x < 0 ? nx : (x >= nx ? -nx : 0);
         y += y < 0 ? ny : (y >= ny ? -ny : 0);
         z += z < 0 ? nz : (z >= nz ? -nz : 0);
-        nb[t] = S.lcell[(z * ny + y) * nx + x];
+        sm.nb[t] = S.lcell[(z * ny + y) * nx + x];
     }
-    __syncthreads();
+    g.sync();
     if (t == 0) {
         int o = 0;
-        for (int q = 0; q < 27; ++q) { noff[q] = o; o += nb[q].y; }
-        noff[27] = o;
+        for (int q = 0; q < 27; ++q) { sm.noff[q] = o; o += sm.nb[q].y; }
+        sm.noff[27] = o;
     }
-    __syncthreads();
-    const int M = noff[27];
+    g.sync();
+    const int M = sm.noff[27];
     const uint32_t ox = (uint32_t)(((unsigned long long)(2 * cx + 1) * P.lcwu[0]) >> 1);
     const uint32_t oy = (uint32_t)(((unsigned long long)(2 * cy + 1) * P.lcwu[1]) >> 1);
     const uint32_t oz = (uint32_t)(((unsigned long long)(2 * cz + 1) * P.lcwu[2]) >> 1);
     const float q0 = P.qsf[0], q1 = P.qsf[1], q2 = P.qsf[2];
     const float rl2 = P.rl2f;
     const int capg = P.lcap / NL_G;
-    const int i0 = nb[13].x, ni = nb[13].y;
-    for (int ib = 0; ib < ni; ib += 128 / NL_G) {
-        const int r = ib + t / NL_G, g = t % NL_G;
+    const int i0 = sm.nb[13].x, ni = sm.nb[13].y;
+    const int lane = t & 31, glane = lane & ~(NL_G - 1);
+    for (int ib = 0; ib < ni; ib += GRP / NL_G) {
+        const int r = ib + t / NL_G, gl = t % NL_G;
         const bool act = r < ni;
         const int ki = i0 + (act ? r : 0);
         const uint4 pi = cur[ki];
@@ -189,35 +207,33 @@ __global__ void __launch_bounds__(128) k_nl_build(const SysDev *__restrict__ sys
                     zi = (float)(int)(pi.z - oz) * q2;
         const uint32_t lip = pi.w >> 12;
         const uint32_t em = lip ? P.excl[meta_k(pi.w)] : 0u;
-        // partners go to the columns in turn (entry e: column e % NL_G, row
-        // e / NL_G), so the columns differ by one entry at most; the bead's
-        // NL_G lanes agree on the running count through a ballot
-        const int lane = t & 31, glane = lane & ~(NL_G - 1);
-        const int self = noff[13] + r;            // the bead's own candidate index
+        const int self = sm.noff[13] + r;      // the bead's own candidate index
+        // partner e goes to column e % NL_G, row e / NL_G (the columns differ
+        // by one entry at most)
         int base = 0;
         for (int f0 = 0; f0 < M; f0 += NLB_STAGE) {
             const int mc = min(NLB_STAGE, M - f0);
-            __syncthreads();
-            for (int f = t; f < mc; f += blockDim.x) {
+            g.sync();
+            for (int f = t; f < mc; f += GRP) {
                 const int fg = f0 + f;
                 int lo = 0, hi = 26;              // the neighbour cell holding candidate fg
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (noff[mid] <= fg) lo = mid; else hi = mid - 1;
+                    if (sm.noff[mid] <= fg) lo = mid; else hi = mid - 1;
                 }
-                const int kj = nb[lo].x + (fg - noff[lo]);
+                const int kj = sm.nb[lo].x + (fg - sm.noff[lo]);
                 const uint4 pj = cur[kj];
-                sf[f] = make_float4((float)(int)(pj.x - ox) * q0, (float)(int)(pj.y - oy) * q1,
-                                    (float)(int)(pj.z - oz) * q2, __uint_as_float(pj.w));
-                sk[f] = kj;
+                sm.sf[f] = make_float4((float)(int)(pj.x - ox) * q0, (float)(int)(pj.y - oy) * q1,
+                                       (float)(int)(pj.z - oz) * q2, __uint_as_float(pj.w));
+                sm.sk[f] = kj;
             }
-            __syncthreads();
+            g.sync();
             const int nq = (mc + NL_G - 1) / NL_G;
             for (int q = 0; q < nq; ++q) {
-                const int f = q * NL_G + g;
+                const int f = q * NL_G + gl;
                 bool in = false;
                 if (act && f < mc) {
-                    const float4 e = sf[f];
+                    const float4 e = sm.sf[f];
                     const float dx = xi - e.x, dy = yi - e.y, dz = zi - e.z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
                     const uint32_t mj = __float_as_uint(e.w);
@@ -227,110 +243,76 @@ __global__ void __launch_bounds__(128) k_nl_build(const SysDev *__restrict__ sys
                 const unsigned bal = __ballot_sync(0xffffffffu, in);
                 const unsigned grp = (bal >> glane) & ((1u << NL_G) - 1u);
                 if (in) {
-                    const int e = base + __popc(grp & ((1u << g) - 1u));
+                    const int e = base + __popc(grp & ((1u << gl) - 1u));
                     const int row = e / NL_G, col = e % NL_G;
-                    if (row < capg) S.nl[(size_t)row * P.lrow + (size_t)ki * NL_G + col] = sk[f];
+                    if (row < capg) S.nl[(size_t)row * P.lrow + (size_t)ki * NL_G + col] = sm.sk[f];
                 }
                 base += __popc(grp);
             }
         }
         if (act) {
-            const int cnt = base > g ? (base - g + NL_G - 1) / NL_G : 0;
-            S.nl_n[(size_t)ki * NL_G + g] = min(cnt, capg);
+            const int cnt = base > gl ? (base - gl + NL_G - 1) / NL_G : 0;
+            S.nl_n[(size_t)ki * NL_G + gl] = min(cnt, capg);
             if (base > P.lcap) atomicOr(&C.err, ERR_CELL_OVERFLOW);
             if (lip != 0) {
                 const int kl = meta_k(pi.w);
-                for (int p = g; p < P.npart[kl]; p += NL_G)
+                for (int p = gl; p < P.npart[kl]; p += NL_G)
                     S.bslot[(size_t)ki * NL_PART + p] = S.lk[(int)(lip - 1) * P.bpl + P.part[kl][p]];
             }
         }
     }
+    g.sync();
 }
 
-__global__ void k_nl_done(const SysDev *__restrict__ sys, int n_sys, int in_cond) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n_sys) return;
-    Counters &C = *sys[q].c;
-    if (!C.nl_stale) return;
-    C.nl_stale = 0;
-    C.nl_viol = 0;
-    C.nl_builds++;
-    if (in_cond) C.nl_builds_cond++;
-}
-
-void launch_nl_build(const LaunchCtx &L, int in_conditional) {
-    k_nl_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
-    k_nl_place<<<L.lsort->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.lsort->d);
-    k_nl_build<<<L.lcells->n, 128, 0, L.stream>>>(L.sys, L.lcells->d);
-    k_nl_done<<<(L.n_sys + 127) / 128, 128, 0, L.stream>>>(L.sys, L.n_sys, in_conditional);
-}
-
-// the conditional of a graph's first build: is any list of the batch stale?
-__global__ void k_nl_decide(const SysDev *__restrict__ sys, int n_sys, cudaGraphConditionalHandle cond) {
-    int need = 0;
-    for (int q = threadIdx.x; q < n_sys; q += 32) need |= sys[q].c->nl_stale;
-    need = __any_sync(0xffffffffu, need);
-    if (threadIdx.x == 0) cudaGraphSetConditional(cond, need ? 1u : 0u);
-}
-
-void launch_nl_decide(const LaunchCtx &L, cudaGraphConditionalHandle cond) {
-    k_nl_decide<<<1, 32, 0, L.stream>>>(L.sys, L.n_sys, cond);
-}
-
-// ------------------------------------------------------------------- step
+// ------------------------------------------------------------- step item
+// One MD step of the beads k0 .. k0 + NL_BEADS - 1 (list order): positions
+// read from buffer par, written to buffer par ^ 1 and to the id-ordered
+// array.  The item's kinetic energy goes to integer slot `slot`; a bead that
+// moved farther than the list allows sets *viol.
 template <typename Real, bool LAM>
-__global__ void __launch_bounds__(NL_BLOCK, 8)
-k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap, cudaGraphConditionalHandle cond, int use_cond,
-          unsigned int *__restrict__ bticket, int n_sys) {
+__device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *viol, const Grp &g,
+                             StepSmem<Real> &sm, bool load_tables = true) {
     using V4 = typename Vec4<Real>::T;
     constexpr bool F32 = sizeof(Real) == 4;
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
     const Params &P = *S.p;
     Counters &C = *S.c;
-    const int t = threadIdx.x, il = t / NL_G, g = t % NL_G;
+    const int t = g.t, il = t / NL_G, gl = t % NL_G;
     const int n = P.n;
-    const int k = bm.y + il;
+    const int k = k0 + il;
     const bool valid = k < n;
-
-    __shared__ Real tf12[256], tf6[256], tqq[256];
-    __shared__ __align__(16) V4 svel[NL_BEADS];
-    __shared__ __align__(16) uint4 sxref[NL_BEADS];
-    __shared__ __align__(16) uint4 spart[NL_BEADS][NL_PART];
-    __shared__ Real kered[2][NL_BEADS];
-    __shared__ int sviol, last;
-    __shared__ long long ksum[2][2];
-
-    const int par = C.nl_par;
     const uint4 *__restrict__ cur = S.lpos + (size_t)par * n;
     uint4 *nxt = S.lpos + (size_t)(par ^ 1) * n;
     uint4 pi = make_uint4(0u, 0u, 0u, 0u);
     int cnt = 0, id = 0;
     if (valid) {
         pi = cur[k];
-        cnt = S.nl_n[(size_t)k * NL_G + g];
-        if (g == 0) {
+        cnt = S.nl_n[(size_t)k * NL_G + gl];
+        if (gl == 0) {
             // fetched into shared memory while the pairs are summed
             id = S.lid[k];
             const char *gv = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.vel) + id);
-            for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&svel[il]) + h, gv + h);
-            cp_async16(&sxref[il], S.xref + k);
+            for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&sm.svel[il]) + h, gv + h);
+            cp_async16(&sm.sxref[il], S.xref + k);
             if (meta_lip(pi.w) >= 0) {
                 const int kl = meta_k(pi.w);
-                for (int p = 0; p < P.npart[kl]; ++p) cp_async16(&spart[il][p], cur + S.bslot[(size_t)k * NL_PART + p]);
+                for (int p = 0; p < P.npart[kl]; ++p) cp_async16(&sm.spart[il][p], cur + S.bslot[(size_t)k * NL_PART + p]);
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
         }
     }
-    for (int x = t; x < 256; x += NL_BLOCK) {
-        if (F32) {
-            tf12[x] = (Real)P.f12f[x]; tf6[x] = (Real)P.f6f[x]; tqq[x] = (Real)P.qqf[x];
-        } else {
-            tf12[x] = (Real)(12.0 * P.c12[x]); tf6[x] = (Real)(6.0 * P.c6[x]); tqq[x] = (Real)P.qq[x];
+    if (load_tables)                           // else still there from the group's previous item
+        for (int x = t; x < 256; x += GRP) {
+            V4 e;
+            if (F32) {
+                e.x = (Real)P.f12f[x]; e.y = (Real)P.f6f[x]; e.z = (Real)P.qqf[x];
+            } else {
+                e.x = (Real)(12.0 * P.c12[x]); e.y = (Real)(6.0 * P.c6[x]); e.z = (Real)P.qq[x];
+            }
+            e.w = (Real)0;
+            sm.tab[x] = e;
         }
-    }
-    if (t == 0) sviol = 0;
-    __syncthreads();
+    if (t == 0) sm.sviol = 0;
+    g.sync();
 
     const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
     const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
@@ -344,10 +326,9 @@ k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap, cudaGra
         const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
         Real dx, dy, dz;
         if (F32) {
-            const float fx = (float)ix, fy = (float)iy, fz = (float)iz;
-            dx = (Real)(fx * qs0);
-            dy = (Real)(fy * qs1);
-            dz = (Real)(fz * qs2);
+            dx = (Real)((float)ix * qs0);
+            dy = (Real)((float)iy * qs1);
+            dz = (Real)((float)iz * qs2);
         } else {
             dx = (Real)((double)ix * P.qs[0]);
             dy = (Real)((double)iy * P.qs[1]);
@@ -362,17 +343,20 @@ k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap, cudaGra
         }
         if (!in) return;
         const uint32_t mj = pj.w;
-        const int ta = tai + meta_ta(mj);
-        Real f12 = tf12[ta], f6 = tf6[ta], qq = tqq[ta];
+        const V4 ca = sm.tab[tai + meta_ta(mj)];
+        Real f12 = ca.x, f6 = ca.y, qq = ca.z;
         if (LAM) {
-            const int tb = tbi + meta_tb(mj);
-            f12 = ((Real)1 - lam) * f12 + lam * tf12[tb];
-            f6 = ((Real)1 - lam) * f6 + lam * tf6[tb];
-            qq = ((Real)1 - lam) * qq + lam * tqq[tb];
+            const V4 cb = sm.tab[tbi + meta_tb(mj)];
+            f12 = ((Real)1 - lam) * f12 + lam * cb.x;
+            f6 = ((Real)1 - lam) * f6 + lam * cb.y;
+            qq = ((Real)1 - lam) * qq + lam * cb.z;
         }
         Real rinv, r2inv, r6inv;
         if (F32) {
-            const float r2i = __frcp_rn((float)r2);
+            // 1/r^2: hardware estimate and one Newton-Raphson step
+            float r2i;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2i) : "f"((float)r2));
+            r2i = fmaf(r2i, fmaf(-(float)r2, r2i, 1.0f), r2i);
             const float p = r2i * r2i;
             const float pe = fmaf(r2i, r2i, -p);                  // exact error of the square
             r6inv = (Real)fmaf(p, r2i, pe * r2i);                // r2i^3 rounded once
@@ -387,12 +371,12 @@ k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap, cudaGra
         ax += fs * dx; ay += fs * dy; az += fs * dz;
     };
 
-    // this thread's entries: column g of the bead's list, rows 0 .. cnt - 1
-    const int *__restrict__ lst = S.nl + (size_t)k * NL_G + g;
+    // column gl of the bead's list, rows 0 .. cnt - 1, in groups of 4; the
+    // next group's indices are loaded before the current group is summed
+    // (entries past the end read a valid slot: 0)
+    const int *__restrict__ lst = S.nl + (size_t)k * NL_G + gl;
     const size_t rs = (size_t)P.lrow;
     const int rows = cnt;
-    // groups of 4 entries; the next group's indices are loaded before the
-    // current group is summed (entries past the end read a valid slot: 0)
     auto idx = [&](int r) { return r < rows ? __ldg(lst + (size_t)r * rs) : 0; };
     int j0 = idx(0), j1 = idx(1), j2 = idx(2), j3 = idx(3);
     for (int m = 0; m < rows; m += 4) {
@@ -404,8 +388,7 @@ k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap, cudaGra
         if (m + 3 < rows) pair(q3);
     }
 
-    // partial forces summed over the bead's NL_G lanes in a fixed tree (the
-    // entries of each lane are fixed by the list, so the sum is reproducible)
+    // partial forces summed over the bead's NL_G lanes in a fixed tree
 #pragma unroll
     for (int o = 1; o < NL_G; o <<= 1) {
         ax += __shfl_xor_sync(0xffffffffu, ax, o);
@@ -413,18 +396,18 @@ k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap, cudaGra
         az += __shfl_xor_sync(0xffffffffu, az, o);
     }
     Real e0 = 0, e1 = 0;
-    if (valid && g == 0) {
+    if (valid && gl == 0) {
         cp_async_wait_all();
         Real fb[3] = {(Real)0, (Real)0, (Real)0};
         if (meta_lip(pi.w) >= 0) {
             const int kl = meta_k(pi.w);
-            bonded_force<Real>(P, kl, pi, [&](int li) { return spart[il][P.pidx[kl][li]]; }, fb);
+            bonded_force<Real>(P, kl, pi, [&](int li) { return sm.spart[il][P.pidx[kl][li]]; }, fb);
         }
         const Real f0 = ax + fb[0], f1 = ay + fb[1], f2 = az + fb[2];
         const int grp = id < P.n_lipid_beads ? 0 : 1;
         const Real a = F32 ? (Real)C.alpha_f[grp] : (Real)C.alpha[grp];
         const Real dtm = F32 ? (Real)P.dt_over_mf : (Real)P.dt_over_m;
-        V4 v = svel[il];
+        V4 v = sm.svel[il];
         v.x = a * v.x + f0 * dtm;
         v.y = a * v.y + f1 * dtm;
         v.z = a * v.z + f2 * dtm;
@@ -443,98 +426,378 @@ k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap, cudaGra
         S.pos[id] = np;
         nxt[k] = np;
         // displacement since the list build
-        const uint4 xr = sxref[il];
-        const float ux = (float)(int)(np.x - xr.x) * P.qsf[0];
-        const float uy = (float)(int)(np.y - xr.y) * P.qsf[1];
-        const float uz = (float)(int)(np.z - xr.z) * P.qsf[2];
-        if (ux * ux + uy * uy + uz * uz > P.dmax2f) sviol = 1;
+        const uint4 xr = sm.sxref[il];
+        const float ux = (float)(int)(np.x - xr.x) * qs0;
+        const float uy = (float)(int)(np.y - xr.y) * qs1;
+        const float uz = (float)(int)(np.z - xr.z) * qs2;
+        if (ux * ux + uy * uy + uz * uz > P.dmax2f) sm.sviol = 1;
         const Real ke = (Real)0.5 * (F32 ? (Real)P.massf : (Real)P.mass) * (v.x * v.x + v.y * v.y + v.z * v.z);
         if (grp == 0) e0 = ke; else e1 = ke;
     }
-    if (g == 0) { kered[0][il] = e0; kered[1][il] = e1; }
-    __syncthreads();
+    if (gl == 0) { sm.kered[0][il] = e0; sm.kered[1][il] = e1; }
+    g.sync();
     if (t < 32) {
-        // the block's kinetic energy (fixed-order sums), into an integer slot
-        Real k0 = 0, k1 = 0;
-        for (int q = t; q < NL_BEADS; q += 32) { k0 += kered[0][q]; k1 += kered[1][q]; }
+        // the item's kinetic energy (fixed-order sums), into an integer slot
+        Real k0s = 0, k1s = 0;
+        for (int q = t; q < NL_BEADS; q += 32) { k0s += sm.kered[0][q]; k1s += sm.kered[1][q]; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            k0 += __shfl_xor_sync(0xffffffffu, k0, o);
-            k1 += __shfl_xor_sync(0xffffffffu, k1, o);
+            k0s += __shfl_xor_sync(0xffffffffu, k0s, o);
+            k1s += __shfl_xor_sync(0xffffffffu, k1s, o);
         }
         if (t == 0) {
-            long long *slot = C.ke_slot[blockIdx.x % KE_SLOTS];
-            atomicAdd((unsigned long long *)&slot[0], (unsigned long long)to_fix(k0));
-            atomicAdd((unsigned long long *)&slot[1], (unsigned long long)to_fix(k1));
-            if (sviol) atomicOr(&C.nl_viol, 1);
-            __threadfence();
-            const unsigned nblk = (unsigned)((n + NL_BEADS - 1) / NL_BEADS);
-            last = atomicAdd(&C.sticket, 1u) == nblk - 1;
+            long long *ks = C.ke_slot[slot % KE_SLOTS];
+            atomicAdd((unsigned long long *)&ks[0], (unsigned long long)to_fix(k0s));
+            atomicAdd((unsigned long long *)&ks[1], (unsigned long long)to_fix(k1s));
+            if (sm.sviol) atomicOr(viol, 1);
         }
     }
-    __syncthreads();
-    if (!last) return;
+    g.sync();
+}
 
-    // ---- last block of the system: counters, thermostat factor of the next step
-    __threadfence();
-    if (t < 64) {
-        long long a0 = __ldcg(&C.ke_slot[t][0]), a1 = __ldcg(&C.ke_slot[t][1]);
-        C.ke_slot[t][0] = 0;
-        C.ke_slot[t][1] = 0;
+// After a step of system S (one warp, all items done): kinetic energy from
+// the integer slots (cleared), counters, the thermostat factor of the next
+// step (lanes 0 and 1, one coupling group each).  Real is the system's
+// precision (the factor sees the energy as Real).
+template <typename Real>
+__device__ void nl_step_close(const SysDev &S, int lane) {
+    static_assert(KE_SLOTS == 64, "two slots per lane");
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    long long a0 = __ldcg(&C.ke_slot[lane][0]) + __ldcg(&C.ke_slot[lane + 32][0]);
+    long long a1 = __ldcg(&C.ke_slot[lane][1]) + __ldcg(&C.ke_slot[lane + 32][1]);
+    C.ke_slot[lane][0] = 0; C.ke_slot[lane][1] = 0;
+    C.ke_slot[lane + 32][0] = 0; C.ke_slot[lane + 32][1] = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        }
-        if ((t & 31) == 0) { ksum[t >> 5][0] = a0; ksum[t >> 5][1] = a1; }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
     }
-    __syncthreads();
-    if (t == 0) {
-        C.ke_total[0] = (double)(ksum[0][0] + ksum[1][0]) * (1.0 / FIX);
-        C.ke_total[1] = (double)(ksum[0][1] + ksum[1][1]) * (1.0 / FIX);
+    const int in_at = C.in_at;
+    const unsigned long long ctr = (in_at ? C.at_step : C.step) + 1;
+    const double K0 = (double)a0 * (1.0 / FIX), K1 = (double)a1 * (1.0 / FIX);
+    if (lane < 2) {
+        // the kinetic energy rounded to Real, as the thermostat kernel takes it
+        const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
+        const double al = alpha_for(S, P, C, lane, (double)(Real)(lane ? K1 : K0), ctr, tag);
+        C.alpha[lane] = al;
+        C.alpha_f[lane] = (float)al;
+    }
+    if (lane == 0) {
+        C.ke_total[0] = K0;
+        C.ke_total[1] = K1;
         C.ke_fresh = 1;
         C.ke_pending = 0;
-        if (C.in_at) C.at_step++; else C.step++;
+        if (in_at) C.at_step = ctr; else C.step = ctr;
         C.md_steps++;
         C.force_evals++;
+    }
+    __syncwarp();
+}
+
+// ======================================================== separate kernels
+__global__ void __launch_bounds__(GRP) k_nl_count(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    __shared__ BuildSmem sm;
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    if (!S.c->nl_stale) return;
+    nl_count_item(S, bm.y, Grp{(int)threadIdx.x, 1}, sm);
+}
+
+__global__ void __launch_bounds__(GRP) k_nl_place(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    if (!S.c->nl_stale) return;
+    nl_place_item(S, bm.y, S.c->nl_par, Grp{(int)threadIdx.x, 1});
+}
+
+__global__ void __launch_bounds__(GRP) k_nl_build(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    __shared__ BuildSmem sm;
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    if (!S.c->nl_stale) return;
+    nl_build_item(S, bm.y, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm);
+}
+
+__global__ void k_nl_done(const SysDev *__restrict__ sys, int n_sys) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_sys) return;
+    Counters &C = *sys[q].c;
+    if (!C.nl_stale) return;
+    C.nl_stale = 0;
+    C.nl_viol = 0;
+    C.nl_builds++;
+}
+
+void launch_nl_build(const LaunchCtx &L) {
+    static_assert(CELLS_PER_SORT_BLOCK * 32 == GRP, "place items are one group");
+    k_nl_count<<<L.beads->n, GRP, 0, L.stream>>>(L.sys, L.beads->d);
+    k_nl_place<<<L.lsort->n, GRP, 0, L.stream>>>(L.sys, L.lsort->d);
+    k_nl_build<<<L.lcells->n, GRP, 0, L.stream>>>(L.sys, L.lcells->d);
+    k_nl_done<<<(L.n_sys + 127) / 128, 128, 0, L.stream>>>(L.sys, L.n_sys);
+}
+
+// One step of every system; the last block of a system (a ticket, no
+// waiting) closes the step and flags the list stale after a violation.
+template <typename Real, bool LAM>
+__global__ void __launch_bounds__(GRP, 8) k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    __shared__ StepSmem<Real> sm;
+    __shared__ int last;
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    Counters &C = *S.c;
+    const int par = C.nl_par;
+    nl_step_item<Real, LAM>(S, bm.y, par, blockIdx.x, &C.nl_viol, Grp{(int)threadIdx.x, 1}, sm);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned nblk = (unsigned)((S.p->n + NL_BEADS - 1) / NL_BEADS);
+        last = atomicAdd(&C.sticket, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    nl_step_close<Real>(S, threadIdx.x);
+    if (threadIdx.x == 0) {
         C.nl_stale = __ldcg(&C.nl_viol);
         C.nl_viol = 0;
         C.nl_par = par ^ 1;
         C.sticket = 0;
     }
-    __syncthreads();
-    if (t == 0 || t == 32) {
-        const int grp = t >> 5;
-        const int in_at = C.in_at;
-        const unsigned long long ctr = in_at ? C.at_step : C.step;
-        const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
-        // the kinetic energy rounded to Real, as the thermostat kernel takes it
-        C.alpha[grp] = alpha_for(S, P, C, grp, (double)(Real)C.ke_total[grp], ctr, tag);
-        C.alpha_f[grp] = (float)C.alpha[grp];
-    }
-    if (use_cond && t == 0) {
-        __threadfence();
-        if (atomicAdd(bticket, 1u) == (unsigned)(n_sys - 1)) {
-            __threadfence();
-            int need = 0;
-            for (int q = 0; q < n_sys; ++q) need |= __ldcg(&sys[q].c->nl_stale);
-            *bticket = 0;
-            cudaGraphSetConditional(cond, need ? 1u : 0u);
-        }
-    }
 }
 
 template <typename Real, bool LAM>
-static void nl_step_launch(const LaunchCtx &L, cudaGraphConditionalHandle cond, int use_cond) {
-    k_nl_step<Real, LAM><<<L.nlbeads->n, NL_BLOCK, 0, L.stream>>>(L.sys, L.nlbeads->d, cond, use_cond, L.bticket, L.n_sys);
+static void nl_step_launch(const LaunchCtx &L) {
+    k_nl_step<Real, LAM><<<L.nlbeads->n, GRP, 0, L.stream>>>(L.sys, L.nlbeads->d);
 }
 
-void launch_nl_step(const LaunchCtx &L, bool lambda, cudaGraphConditionalHandle cond, int use_cond) {
+void launch_nl_step(const LaunchCtx &L, bool lambda) {
+    static_assert(NL_BEADS * NL_G == GRP, "a step item is one group");
     if (L.precision == 1) {
-        if (lambda) nl_step_launch<double, true>(L, cond, use_cond); else nl_step_launch<double, false>(L, cond, use_cond);
+        if (lambda) nl_step_launch<double, true>(L); else nl_step_launch<double, false>(L);
     } else {
-        if (lambda) nl_step_launch<float, true>(L, cond, use_cond); else nl_step_launch<float, false>(L, cond, use_cond);
+        if (lambda) nl_step_launch<float, true>(L); else nl_step_launch<float, false>(L);
     }
 }
+
+// ===================================================== persistent kernel
+// Grid barrier over all blocks (one cooperative launch, all blocks resident):
+// arrive on a counter; the last arrival clears it and advances the
+// generation, the others wait for the generation to change.  Every wait is
+// bounded; a block that gives up records ERR_TIMEOUT in abort, and every
+// block returns at its next barrier once abort is set.
+struct RunSync {
+    unsigned int count, gen;
+    int abort;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool grid_barrier(RunSync *rs) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g0 = ld_acquire(&rs->gen);
+        __threadfence();
+        int good = 1;
+        if (atomicAdd(&rs->count, 1u) == gridDim.x - 1) {
+            rs->count = 0;
+            __threadfence();
+            atomicAdd(&rs->gen, 1u);
+        } else {
+            for (long long it = 0; ld_acquire(&rs->gen) == g0; ++it) {
+                if (it > (1ll << 22) || *(volatile int *)&rs->abort) {
+                    atomicOr(&rs->abort, ERR_TIMEOUT);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good && !*(volatile int *)&rs->abort;
+    }
+    __syncthreads();
+    return ok;
+}
+
+struct RunArgs {
+    const SysDev *sys;
+    int n_sys;
+    const int2 *nlmap, *beadmap, *lsortmap, *lcellmap;
+    int n_nl, n_bead, n_lsort, n_lcell;
+    int n_steps, swap_every;
+    RunSync *rs;
+};
+
+// Whether system C needs a list build: lists made stale outside the kernel
+// (which == 0) or a bead that moved too far in step s (which == 1).  The flags
+// do not change between the barrier before such a read and the next one.
+__device__ __forceinline__ int build_flag(const Counters &C, int which, int s) {
+    return which == 0 ? *(volatile const int *)&C.nl_stale : *(volatile const int *)&C.nl_violp[s & 1];
+}
+
+// Whether any system of the batch needs a build (the same answer in every block)
+__device__ bool any_flag(const RunArgs &a, int which, int s) {
+    __shared__ int need;
+    if (threadIdx.x == 0) {
+        int v = 0;
+        for (int q = 0; q < a.n_sys; ++q) v |= build_flag(*a.sys[q].c, which, s);
+        need = v;
+    }
+    __syncthreads();
+    const bool r = need != 0;
+    __syncthreads();
+    return r;
+}
+
+// List build of every system whose flag is set; buffer (nl_par + b) & 1 holds
+// the current positions.  Three barriers.
+__device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &g, int gid, int G, BuildSmem &sm) {
+    for (int it = gid; it < a.n_bead; it += G) {
+        const int2 bm = a.beadmap[it];
+        const SysDev &S = a.sys[bm.x];
+        if (build_flag(*S.c, which, s)) nl_count_item(S, bm.y, g, sm);
+    }
+    if (!grid_barrier(a.rs)) return false;
+    for (int it = gid; it < a.n_lsort; it += G) {
+        const int2 bm = a.lsortmap[it];
+        const SysDev &S = a.sys[bm.x];
+        if (build_flag(*S.c, which, s)) nl_place_item(S, bm.y, (S.c->nl_par + b) & 1, g);
+    }
+    if (!grid_barrier(a.rs)) return false;
+    for (int it = gid; it < a.n_lcell; it += G) {
+        const int2 bm = a.lcellmap[it];
+        const SysDev &S = a.sys[bm.x];
+        if (build_flag(*S.c, which, s)) nl_build_item(S, bm.y, (S.c->nl_par + b) & 1, g, sm);
+    }
+    return grid_barrier(a.rs);
+}
+
+// n_steps MD steps (with a trial after every swap_every-th) of every system,
+// in one cooperative launch of one 1024-thread block per SM.  Per step: the
+// step items, a barrier, the list builds that the step's displacements call
+// for, then per system (block q % gridDim) the step's close and the trial
+// items, and a barrier.  Step s reads position buffer (nl_par + s) & 1.
+template <typename Real, bool LAM>
+__global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int group = threadIdx.x / GRP;
+    const Grp g{(int)threadIdx.x % GRP, 1 + group};
+    // consecutive items go to different SMs
+    const int G = gridDim.x * RUN_GROUPS, gid = group * gridDim.x + blockIdx.x;
+    unsigned char *gsm = dsm + group * group_smem<Real>();
+    StepSmem<Real> &ssm = *reinterpret_cast<StepSmem<Real> *>(gsm);
+    BuildSmem &bsm = *reinterpret_cast<BuildSmem *>(gsm);
+    TrialSmem &tsm = *reinterpret_cast<TrialSmem *>(gsm);
+
+    // lists made stale outside the kernel (a new state, a rejected move)
+    const bool stale0 = any_flag(a, 0, 0);
+    if (stale0) {
+        if (!run_build(a, 0, 0, 0, g, gid, G, bsm)) return;
+        if (threadIdx.x == 0)
+            for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x)
+                if (a.sys[q].c->nl_stale) a.sys[q].c->nl_builds++;
+    }
+    int tab_sys = -1;                          // system whose tables the group holds
+    for (int s = 0; s < a.n_steps; ++s) {
+        for (int it = gid; it < a.n_nl; it += G) {
+            const int2 bm = a.nlmap[it];
+            const SysDev &S = a.sys[bm.x];
+            nl_step_item<Real, LAM>(S, bm.y, (S.c->nl_par + s) & 1, it, &S.c->nl_violp[s & 1], g, ssm,
+                                    bm.x != tab_sys);
+            tab_sys = bm.x;
+        }
+        // flags last read before the previous barrier: clear them for reuse
+        if (threadIdx.x == 0)
+            for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
+                Counters &C = *a.sys[q].c;
+                C.nl_violp[(s + 1) & 1] = 0;
+                if (s == 0) C.nl_stale = 0;
+            }
+        if (!grid_barrier(a.rs)) return;
+        const bool rebuild = any_flag(a, 1, s);
+        if (rebuild) {
+            if (!run_build(a, 1, s, s + 1, g, gid, G, bsm)) return;
+            tab_sys = -1;                      // the build used the same shared memory
+        }
+        if (threadIdx.x < 32)
+            for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
+                const SysDev &S = a.sys[q];
+                nl_step_close<Real>(S, threadIdx.x);
+                if (threadIdx.x == 0 && rebuild && S.c->nl_violp[s & 1]) S.c->nl_builds++;
+            }
+        if (a.swap_every > 0 && (s + 1) % a.swap_every == 0) {
+            for (int it = gid; it < TRIAL_PARTS * a.n_sys; it += G) {
+                const SysDev &S = a.sys[it / TRIAL_PARTS];
+                trial_nl_part(S, it % TRIAL_PARTS, (S.c->nl_par + s + 1) & 1, g, tsm);
+                tab_sys = -1;                  // the trial used the same shared memory
+            }
+        }
+        if (!grid_barrier(a.rs)) return;
+    }
+    if (threadIdx.x == 0)
+        for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
+            Counters &C = *a.sys[q].c;
+            C.nl_par = (C.nl_par + a.n_steps) & 1;
+            C.nl_violp[0] = C.nl_violp[1] = 0;
+            if (a.n_steps == 0) C.nl_stale = 0;
+        }
+}
+
+template <typename Real, bool LAM>
+static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, RunSync *rs, int n_blocks) {
+    RunArgs a;
+    a.sys = L.sys; a.n_sys = L.n_sys;
+    a.nlmap = L.nlbeads->d; a.n_nl = L.nlbeads->n;
+    a.beadmap = L.beads->d; a.n_bead = L.beads->n;
+    a.lsortmap = L.lsort->d; a.n_lsort = L.lsort->n;
+    a.lcellmap = L.lcells->d; a.n_lcell = L.lcells->n;
+    a.n_steps = n_steps; a.swap_every = swap_every; a.rs = rs;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)k_md_run<Real, LAM>, dim3(n_blocks), dim3(RUN_THREADS), args,
+                                       RUN_GROUPS * group_smem<Real>(), L.stream);
+}
+
+template <typename Real, bool LAM>
+static cudaError_t run_setup(int *blocks_per_sm) {
+    const size_t smem = RUN_GROUPS * group_smem<Real>();
+    cudaError_t e = cudaFuncSetAttribute(k_md_run<Real, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_md_run<Real, LAM>, RUN_THREADS, smem);
+}
+
+// Blocks of the persistent kernel on this device: one per SM when a block
+// fits on an SM, else 0 (then the separate kernels are used).
+int md_run_blocks(int precision, bool lambda) {
+    static int cache[2][2] = {{-1, -1}, {-1, -1}};
+    int &c = cache[precision == 1][lambda ? 1 : 0];
+    if (c >= 0) return c;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e;
+    if (precision == 1) e = lambda ? run_setup<double, true>(&per) : run_setup<double, false>(&per);
+    else e = lambda ? run_setup<float, true>(&per) : run_setup<float, false>(&per);
+    c = (e == cudaSuccess && per >= 1) ? sms : 0;
+    cudaGetLastError();
+    return c;
+}
+
+cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, void *sync) {
+    const int nb = md_run_blocks(L.precision, lambda);
+    if (nb <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    RunSync *rs = (RunSync *)sync;
+    if (L.precision == 1)
+        return lambda ? run_launch<double, true>(L, n_steps, swap_every, rs, nb)
+                      : run_launch<double, false>(L, n_steps, swap_every, rs, nb);
+    return lambda ? run_launch<float, true>(L, n_steps, swap_every, rs, nb)
+                  : run_launch<float, false>(L, n_steps, swap_every, rs, nb);
+}
+
+size_t md_run_sync_bytes() { return sizeof(RunSync); }
 
 }  // namespace mdas

@@ -13,23 +13,9 @@
 // other); the rest are re-evaluated in the next round.
 #include <cmath>
 
-#include "mdas_dev.cuh"
+#include "mdas_trial.cuh"
 
 namespace mdas {
-
-// FP64 change of one pair's energy (LJ with potential shift + reaction field)
-// when its type pair goes from (oi, oj) to (ni, nj), at squared distance r2;
-// 1/r from a float seed refined by two Newton steps (no FP64 divide or sqrt).
-__device__ __forceinline__ double pair_du(const Params &P, int oi, int oj, int ni, int nj, double r2) {
-    const int xo = oi * 16 + oj, xn = ni * 16 + nj;
-    double ri = (double)rsqrtf((float)r2);
-    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
-    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
-    const double r2i = ri * ri;
-    const double r6 = r2i * r2i * r2i;
-    return (P.c12[xn] - P.c12[xo]) * r6 * r6 - (P.c6[xn] - P.c6[xo]) * r6 - (P.ush[xn] - P.ush[xo]) +
-           (P.qq[xn] - P.qq[xo]) * (ri + P.krf * r2 - P.crf);
-}
 
 // Sum over the neighbours j in one of the 27 cells around changed bead i of
 // u(new_i, new_j) - u(old_i, old_j); pairs of two changed beads are counted
@@ -70,19 +56,6 @@ __device__ double bead_delta(const SysDev &S, const Params &P, int i, uint4 pi, 
         acc += pair_du(P, old_i, old_j, new_i, new_j, r2);
     }
     return acc;
-}
-
-// fixed-order sum over the block: a shuffle tree per warp, then the warp
-// sums in order (blockDim.x a multiple of 32, at most 1024)
-__device__ double block_sum(double v, double *sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    __syncthreads();
-    return s;
 }
 
 // -------------------------------------------------------------- proposals
@@ -172,7 +145,6 @@ void launch_swap_propose(const LaunchCtx &L, int n) {
 // grid (n * 9, n_sys): CTA (t, g) sums the dE of trial t over the 3
 // neighbour cells (dz, dy) = g of every changed bead (FP64, fixed-order
 // reduction); the 9 partial sums are added in order by the resolve kernel.
-constexpr int DE_GROUPS = 9;
 
 __global__ void __launch_bounds__(128) k_swap_dE(const SysDev *__restrict__ sys, int n) {
     const SysDev &S = sys[blockIdx.y];
@@ -404,146 +376,15 @@ void launch_trial_one(const LaunchCtx &L) {
     k_trial_one<<<g, 128, 0, L.stream>>>(L.sys);
 }
 
-// One exchange trial per system from the pair list (valid whenever an MD
-// step has just run): grid (DE_GROUPS, n_sys).  Items are (changed bead, list
-// column, row); every list holds all partners closer than rc, so the dE is
-// the same sum as over the 27 cells.  The last CTA (a ticket) adds the
-// partial sums in order, decides and applies, as in k_trial_one.
-__global__ void __launch_bounds__(128) k_trial_nl(const SysDev *__restrict__ sys) {
+// One exchange trial per system from the pair list: grid (TRIAL_PARTS, n_sys).
+__global__ void __launch_bounds__(GRP) k_trial_nl(const SysDev *__restrict__ sys) {
+    __shared__ TrialSmem sm;
     const SysDev &S = sys[blockIdx.y];
-    const Params &P = *S.p;
-    Counters &C = *S.c;
-    const int grp = blockIdx.x;
-    const int t = threadIdx.x, lane = t & 31;
-    __shared__ double sh[4];
-    __shared__ int it_beg[2 * MAXT * NL_G + 1];
-    __shared__ int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT], chg_k[2 * MAXT];
-    __shared__ uint4 chg_pos[2 * MAXT];
-    __shared__ int nchg, last, accept;
-    __shared__ double lnu;
-    const unsigned long long T = C.trial;
-    const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
-    const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
-    const int ta = S.ltype[a], tb = S.ltype[b];
-    const bool null_trial = (a == b) || (ta == tb);
-    int m = 0;                                   // local indices whose bead type changes
-    if (!null_trial)
-        for (int k = 0; k < P.bpl; ++k) m |= (P.lbt[ta * 16 + k] != P.lbt[tb * 16 + k]) << k;
-    const uint4 *cur = S.lpos + (size_t)C.nl_par * P.n;
-    if (t == 32) lnu = log(unit53(w.z, w.w));
-    if (t < 32) {
-        const int side = lane >= P.bpl, k = side ? lane - P.bpl : lane;
-        const bool ch = lane < 2 * P.bpl && ((m >> k) & 1);
-        const unsigned bal = __ballot_sync(0xffffffffu, ch);
-        if (ch) {
-            const int o = __popc(bal & ((1u << lane) - 1u));
-            const int id = (side ? b : a) * P.bpl + k;
-            const int kk = S.lk[id];
-            chg_id[o] = id;
-            chg_k[o] = kk;
-            chg_pos[o] = cur[kk];
-            chg_old[o] = P.lbt[(side ? tb : ta) * 16 + k];
-            chg_new[o] = P.lbt[(side ? ta : tb) * 16 + k];
-        }
-        if (lane == 0) nchg = __popc(bal);
-    }
-    __syncthreads();
-    const int nc = nchg, nit = nc * NL_G;
-    if (t < 32) {
-        // items (changed bead, column): exclusive offsets of their row counts,
-        // NL_G items per lane, one warp scan
-        int v[NL_G], sum = 0;
-#pragma unroll
-        for (int g = 0; g < NL_G; ++g) {
-            const int it = NL_G * lane + g;
-            v[g] = it < nit ? S.nl_n[(size_t)chg_k[it / NL_G] * NL_G + g] : 0;
-            sum += v[g];
-        }
-        int inc = sum;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += x;
-        }
-        int run = inc - sum;
-#pragma unroll
-        for (int g = 0; g < NL_G; ++g) {
-            const int it = NL_G * lane + g;
-            if (it < nit) it_beg[it] = run;
-            run += v[g];
-        }
-        if (lane == 31) it_beg[nit] = inc;
-    }
-    __syncthreads();
-    const int total = nc > 0 ? it_beg[nit] : 0;
-    double acc = 0.0;
-    for (int f = grp * blockDim.x + t; f < total; f += DE_GROUPS * blockDim.x) {
-        int lo = 0, hi = nit - 1;                 // the item holding entry f
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (it_beg[mid] <= f) lo = mid; else hi = mid - 1;
-        }
-        const int ci = lo / NL_G, g = lo % NL_G, row = f - it_beg[lo];
-        const int kj = S.nl[(size_t)row * P.lrow + (size_t)chg_k[ci] * NL_G + g];
-        const uint4 pi = chg_pos[ci], pj = cur[kj];
-        const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
-        const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
-        const float r2f = fx * fx + fy * fy + fz * fz;
-        if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
-        const int lj = meta_lip(pj.w), kjl = meta_k(pj.w);
-        const bool chj = (lj == a || lj == b) && ((m >> kjl) & 1);
-        if (chj && lj * P.bpl + kjl < chg_id[ci]) continue;     // a changed pair once, by the lower id
-        const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
-        const double r2 = ex * ex + ey * ey + ez * ez;
-        if (r2 >= P.rc2) continue;
-        const int old_j = meta_ta(pj.w);
-        const int new_j = chj ? (int)P.lbt[(lj == a ? tb : ta) * 16 + kjl] : old_j;
-        acc += pair_du(P, chg_old[ci], old_j, chg_new[ci], new_j, r2);
-    }
-    const double part = block_sum(acc, sh);
-    if (t == 0) {
-        S.tdE[grp] = part;
-        __threadfence();
-        last = atomicAdd(&C.ticket, 1u) == DE_GROUPS - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    if (t == 0) {
-        __threadfence();
-        double dE = 0.0;
-        for (int g = 0; g < DE_GROUPS; ++g) dE += __ldcg(&S.tdE[g]);
-        TrialRec r;
-        r.a = a; r.b = b; r.u = unit53(w.z, w.w); r.dE = 0.0; r.accepted = 0; r.index = T;
-        r.null_trial = null_trial;
-        if (!null_trial) {
-            r.dE = dE;
-            r.accepted = dE + P.kT * lnu <= 0.0;
-        }
-        accept = r.accepted;
-        if (r.accepted) { S.ltype[a] = tb; S.ltype[b] = ta; }
-        S.log[T % LOG_CAP] = r;
-        C.trials++;
-        C.force_evals++;
-        C.null_trials += r.null_trial;
-        C.accepted += r.accepted;
-        C.trial = T + 1;
-        C.pending = 0;
-        C.ticket = 0;
-    }
-    __syncthreads();
-    if (accept && t < 2 * P.bpl) {               // the exchange: every bead of both lipids
-        const int side = t >= P.bpl, k = side ? t - P.bpl : t;
-        const int l = side ? b : a, lt = side ? ta : tb;
-        const int id = l * P.bpl + k;
-        const int bt = P.lbt[lt * 16 + k];
-        const uint32_t mm = meta_make(bt, bt, k, l + 1);
-        S.pos[id].w = mm;
-        const_cast<uint4 *>(cur)[S.lk[id]].w = mm;
-    }
+    trial_nl_part(S, blockIdx.x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm);
 }
 
 void launch_trial_nl(const LaunchCtx &L) {
-    dim3 g(DE_GROUPS, L.n_sys);
+    dim3 g(TRIAL_PARTS, L.n_sys);
     k_trial_nl<<<g, 128, 0, L.stream>>>(L.sys);
 }
 

@@ -83,7 +83,7 @@ TRIAL_DTYPE = np.dtype([("a", np.int32), ("b", np.int32), ("null", np.int32), ("
 EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_energy", "mdas_md_steps",
            "mdas_swap_trials", "mdas_trial_log", "mdas_alchemical_move", "mdas_delta_energy", "mdas_get_state",
            "mdas_set_state", "mdas_cell_list", "mdas_batch_run", "mdas_philox", "mdas_set_kernel_timing",
-           "mdas_pair_kernel_time", "mdas_set_graphs", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
+           "mdas_pair_kernel_time", "mdas_set_persistent", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint"]
 
@@ -305,9 +305,9 @@ class System:
     def set_kernel_timing(self, on=True):
         self._ck(lib().mdas_set_kernel_timing(self._ptr, int(bool(on))))
 
-    def set_graphs(self, on=True):
-        """CUDA-graph replays (default) or plain launches of the same kernels."""
-        self._ck(lib().mdas_set_graphs(self._ptr, int(bool(on))))
+    def set_persistent(self, on=True):
+        """MD in the persistent kernel (default) or as separate kernel launches."""
+        self._ck(lib().mdas_set_persistent(self._ptr, int(bool(on))))
 
     def pair_kernel_time(self, reset=False):
         ms, n = C.c_double(), C.c_int64()

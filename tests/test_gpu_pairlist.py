@@ -40,17 +40,25 @@ def test_skin_does_not_change_the_trajectory_fp64():
     assert np.abs(d).max() <= 64, np.abs(d).max()
 
 
-def test_graph_and_plain_launches_agree():
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_persistent_and_separate_launches_agree(prec):
+    """The persistent kernel and the separate kernels give the same bits, with
+    trials, in one call or split over several."""
     m = synth.mcmd_small()
-    a = mdas.System(m, precision="fp32")
-    b = mdas.System(m, precision="fp32")
-    a.md_steps(12, swap_every=3)            # graph replays
-    for _ in range(4):
-        b.md_steps(3, swap_every=3)         # short runs take plain launches
-    sa, sb = a.get_state(), b.get_state()
-    assert np.array_equal(sa["pos_u"], sb["pos_u"])
-    assert np.array_equal(sa["vel"], sb["vel"])
-    assert np.array_equal(sa["ltype"], sb["ltype"])
+    runs = []
+    for persistent, calls in ((True, [36]), (False, [9, 9, 9, 9]), (True, [12, 24])):
+        s = mdas.System(m, precision=prec)
+        s.set_persistent(persistent)
+        for n in calls:
+            s.md_steps(n, swap_every=3)
+        runs.append((s.get_state(), s.counters()))
+    st0, c0 = runs[0]
+    assert c0["list_builds"] >= 3 and c0["trials"] == 12
+    for st, c in runs[1:]:
+        assert np.array_equal(st["pos_u"], st0["pos_u"])
+        assert np.array_equal(st["vel"], st0["vel"])
+        assert np.array_equal(st["ltype"], st0["ltype"])
+        assert (c["list_builds"], c["accepted"], c["md_steps"]) == (c0["list_builds"], c0["accepted"], c0["md_steps"])
 
 
 def test_one_step_after_rebuild_matches_oracle_fp64():
