@@ -289,7 +289,7 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
 
 // ------------------------------------------------------------ step bodies
 mdas_status build_cells(mdas_system *s, Batch &b) {
-    launch_cells(b.ctx(), false);
+    launch_cells(b.ctx());
     for (auto *x : b.sys) x->cells_valid = true;
     return MDAS_OK;
 }

@@ -1,4 +1,4 @@
-// Force, energy, cell-list and integrator kernels for sm_103a.
+// Cell-list, cell-kernel force / energy and thermostat kernels for sm_103a.
 //
 // Physics (arXiv:2005.08348, Sec. 3 Methods): Lennard-Jones with a
 // potential-shift modifier cut at rc = 1.1 nm, reaction-field electrostatics
@@ -9,11 +9,10 @@
 // Every kernel takes an array of systems plus a block map, so one launch can
 // advance one system or a whole batch of them.
 //
-// One MD step is two launches: the cell-list finish (per-cell ordering of the
-// beads the previous step counted into fixed-capacity cells, plus one block
-// per system computing the step's thermostat factor) and the fused step
-// kernel (pair forces, bonded forces, leapfrog update, counting into the next
-// step's cells).
+// The cell list (fixed-capacity cells of edge >= rc, ordered by id) serves the
+// force and energy entry points, the MDAS work terms and the batched exchange
+// trials; the MD step itself runs over the pair list of plist.cu.  The
+// thermostat factor of a segment's first step comes from thermostat_block.
 #include <cmath>
 #include <cstdio>
 
@@ -110,11 +109,10 @@ __global__ void k_cell_finish(const SysDev *__restrict__ sys, const int2 *__rest
     if (c < P.n_cells) finish_cell<Real>(S, P, c, threadIdx.x & 31);
 }
 
-// counted: the step kernel has already counted the current positions into cells
-// (the finish grid carries one extra block per system that sets the
-// thermostat factor of the coming step)
-void launch_cells(const LaunchCtx &L, bool counted) {
-    if (!counted) k_cell_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
+// count every bead into its cell, then order the cells (the finish grid
+// carries one extra block per system that sets the thermostat factor)
+void launch_cells(const LaunchCtx &L) {
+    k_cell_count<<<L.beads->n, BEAD_BLOCK, 0, L.stream>>>(L.sys, L.beads->d);
     if (L.precision == 1)
         k_cell_finish<double><<<L.sortcells->n, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys, L.sortcells->d);
     else
@@ -146,9 +144,9 @@ void launch_thermo_draws(const LaunchCtx &L, int n) {
 }
 
 // Thermostat factor of the coming step (counter C.step, or C.at_step on the
-// alchemical trajectory): group kinetic energies from the per-cell partials
-// the last step kernel left (ke_fresh), else straight from the velocities;
-// fixed-order reductions (thread-strided sums, then a tree).
+// alchemical trajectory): group kinetic energies as the last MD step left
+// them (ke_fresh), else straight from the velocities; fixed-order reductions
+// (thread-strided sums, then a tree).
 template <typename Real>
 __device__ void thermostat_block(const SysDev &S, const Params &P) {
     using V4 = typename Vec4<Real>::T;
@@ -157,22 +155,6 @@ __device__ void thermostat_block(const SysDev &S, const Params &P) {
     __shared__ Real ks[2][32 * CELLS_PER_SORT_BLOCK];
     __shared__ int fresh;
     if (t == 0) fresh = C.ke_fresh;
-    if (C.ke_pending) {
-        // the step kernel's integer slots: order-independent sums, read once
-        __shared__ long long kl[2][KE_SLOTS];
-        if (t < KE_SLOTS) {
-            kl[0][t] = C.ke_slot[t][0]; kl[1][t] = C.ke_slot[t][1];
-            C.ke_slot[t][0] = 0; C.ke_slot[t][1] = 0;
-        }
-        __syncthreads();
-        if (t < 2) {
-            long long a = 0;
-            for (int k = 0; k < KE_SLOTS; ++k) a += kl[t][k];
-            C.ke_total[t] = (double)a * (1.0 / FIX);
-        }
-        __syncthreads();
-        if (t == 0) { C.ke_pending = 0; C.ke_fresh = 1; fresh = 1; }
-    }
     __syncthreads();
     Real k0 = 0, k1 = 0;
     if (fresh) {
@@ -229,14 +211,10 @@ void launch_thermostat(const LaunchCtx &L) {
 // roundings.  Stream partials are summed in 64-bit fixed point.  Every pair is
 // evaluated from both sides (no atomics on the j bead).
 //
-// The bonded terms of each i-bead are computed by its stream threads first
-// and join the stream partials.  INTEG: the step kernel; each bead's thread
-// then applies the leapfrog update with the thermostat factor, writes the new
-// position and velocity, counts the bead into the next step's cells and
-// contributes to its cell's kinetic-energy partial.  Otherwise the total force
-// is stored in fixed point.
+// The bonded force of each i-bead (computed by the cell-list finish) joins the
+// stream partials, and the total force is stored in fixed point.
 
-template <typename Real, bool LAM, bool ENERGY, bool INTEG>
+template <typename Real, bool LAM, bool ENERGY>
 __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     using V4 = typename Vec4<Real>::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -262,19 +240,9 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
     __shared__ Real bx[3][PAIR_THREADS];
     __shared__ Real blo[3], bhi[3];
     __shared__ double ered[3][PAIR_THREADS];
-    __shared__ Real kered[2][PAIR_THREADS];
     __shared__ __align__(16) V4 sbf[PAIR_THREADS];       // bonded force of the chunk's i-beads
-    __shared__ __align__(16) V4 svel[PAIR_THREADS];      // their velocities (step kernel)
     __shared__ int sid[PAIR_THREADS];                    // their ids
 
-    if (INTEG && c == 0 && t == 0) {            // once per system: count the step
-        Counters &C = *S.c;
-        if (C.in_at) C.at_step++; else C.step++;
-        C.md_steps++;
-        C.force_evals++;
-        C.ke_pending = 1;
-        C.ke_fresh = 0;
-    }
     for (int k = t; k < 256; k += PAIR_THREADS) {
         if (F32) {
             tf12[k] = (Real)P.f12f[k]; tf6[k] = (Real)P.f6f[k]; tqq[k] = (Real)P.qqf[k];
@@ -319,22 +287,17 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
     const float qh0 = P.qsh[0], qh1 = P.qsh[1], qh2 = P.qsh[2];
     const float ql0 = P.qsl[0], ql1 = P.qsl[1], ql2 = P.qsl[2];
     double elj = 0.0, erf = 0.0, epairs = 0.0;
-    Real ke0 = 0, ke1 = 0;
 
     for (int ib = 0; ib < ni; ib += IW) {
         const int i = ib + il;
         const bool valid = i < ni && js < NS;
-        // this thread's i-bead, and for stream 0 its bonded force and velocity
+        // this thread's i-bead, and for stream 0 its bonded force
         const uint4 vi = S.spos[ifirst + (i < ni ? i : 0)];
         if (js == 0 && i < ni) {                 // fetched into shared memory during the sweep
             const int idpre = S.sorted_id[ifirst + i];
             sid[t] = idpre;
             const char *gb = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.bforce) + ifirst + i);
             for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&sbf[t]) + h, gb + h);
-            if (INTEG) {
-                const char *gv = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.vel) + idpre);
-                for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&svel[t]) + h, gv + h);
-            }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
         }
         const int oix = (int)(vi.x - rx), oiy = (int)(vi.y - ry), oiz = (int)(vi.z - rz);
@@ -512,54 +475,10 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_pair(const SysDev *__restri
                 Fy += red[1 * PAIR_THREADS + s * IW + t];
                 Fz += red[2 * PAIR_THREADS + s * IW + t];
             }
-            const uint4 pu = vi;                 // this thread is (i = ib + t, stream 0)
-            if (!INTEG) {
-                const int id = sid[t];
-                S.fx[id] = Fx; S.fy[id] = Fy; S.fz[id] = Fz;
-            } else {
-                const int id = sid[t];
-                const Real sc = (Real)(1.0 / FIX);
-                const Real f0 = (Real)Fx * sc, f1 = (Real)Fy * sc, f2 = (Real)Fz * sc;
-                const int g = id < P.n_lipid_beads ? 0 : 1;
-                const Real a = (Real)S.c->alpha[g];
-                const Real dtm = (Real)P.dt_over_m;
-                V4 *vel = reinterpret_cast<V4 *>(S.vel);
-                V4 v = svel[t];
-                v.x = a * v.x + f0 * dtm;
-                v.y = a * v.y + f1 * dtm;
-                v.z = a * v.z + f2 * dtm;
-                vel[id] = v;
-                if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&S.c->err, ERR_NONFINITE);
-                uint4 np = pu;
-                if (F32) {
-                    np.x += (uint32_t)__float2int_rn((float)v.x * P.qdtf[0]);
-                    np.y += (uint32_t)__float2int_rn((float)v.y * P.qdtf[1]);
-                    np.z += (uint32_t)__float2int_rn((float)v.z * P.qdtf[2]);
-                } else {
-                    np.x += (uint32_t)(long long)rint((double)v.x * P.qdt[0]);
-                    np.y += (uint32_t)(long long)rint((double)v.y * P.qdt[1]);
-                    np.z += (uint32_t)(long long)rint((double)v.z * P.qdt[2]);
-                }
-                S.pos[id] = np;
-                count_into_cell(S, P, id, cell_of_pos(P, np));
-                const Real e = (Real)0.5 * (Real)P.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
-                if (g == 0) ke0 += e; else ke1 += e;
-            }
+            const int id = sid[t];
+            S.fx[id] = Fx; S.fy[id] = Fy; S.fz[id] = Fz;
         }
         __syncthreads();                          // red (over q) is read before the next chunk
-    }
-    if (INTEG) {
-        // this cell's kinetic-energy partials (fixed order), into the integer slots
-        kered[0][t] = ke0;
-        kered[1][t] = ke1;
-        __syncthreads();
-        if (t == 0 && ni > 0) {
-            Real a0 = 0, a1 = 0;
-            for (int k = 0; k < (ni < PAIR_THREADS ? ni : PAIR_THREADS); ++k) { a0 += kered[0][k]; a1 += kered[1][k]; }
-            Counters &C = *S.c;
-            atomicAdd((unsigned long long *)&C.ke_slot[c % KE_SLOTS][0], (unsigned long long)to_fix(a0));
-            atomicAdd((unsigned long long *)&C.ke_slot[c % KE_SLOTS][1], (unsigned long long)to_fix(a1));
-        }
     }
     if (ENERGY) {
         __syncthreads();
@@ -584,14 +503,14 @@ static size_t pair_smem() {
            sizeof(uint16_t) * QCAP * PAIR_THREADS;
 }
 
-template <typename Real, bool LAM, bool ENERGY, bool INTEG>
+template <typename Real, bool LAM, bool ENERGY>
 static void pair_launch(const LaunchCtx &L) {
-    k_pair<Real, LAM, ENERGY, INTEG><<<L.cells->n, PAIR_THREADS, pair_smem<Real>(), L.stream>>>(L.sys, L.cells->d);
+    k_pair<Real, LAM, ENERGY><<<L.cells->n, PAIR_THREADS, pair_smem<Real>(), L.stream>>>(L.sys, L.cells->d);
 }
 
-template <typename Real, bool LAM, bool ENERGY, bool INTEG>
+template <typename Real, bool LAM, bool ENERGY>
 static cudaError_t pair_attr() {
-    return cudaFuncSetAttribute(k_pair<Real, LAM, ENERGY, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_pair<Real, LAM, ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pair_smem<Real>());
 }
 
@@ -599,16 +518,12 @@ static cudaError_t pair_attr() {
 cudaError_t setup_kernels() {
     static cudaError_t done = cudaErrorNotReady;
     if (done != cudaErrorNotReady) return done;
-    cudaError_t e = pair_attr<float, false, false, false>();
-    if (e == cudaSuccess) e = pair_attr<float, true, false, false>();
-    if (e == cudaSuccess) e = pair_attr<float, false, false, true>();
-    if (e == cudaSuccess) e = pair_attr<float, true, false, true>();
-    if (e == cudaSuccess) e = pair_attr<double, false, false, false>();
-    if (e == cudaSuccess) e = pair_attr<double, true, false, false>();
-    if (e == cudaSuccess) e = pair_attr<double, false, false, true>();
-    if (e == cudaSuccess) e = pair_attr<double, true, false, true>();
-    if (e == cudaSuccess) e = pair_attr<double, false, true, false>();
-    if (e == cudaSuccess) e = pair_attr<double, true, true, false>();
+    cudaError_t e = pair_attr<float, false, false>();
+    if (e == cudaSuccess) e = pair_attr<float, true, false>();
+    if (e == cudaSuccess) e = pair_attr<double, false, false>();
+    if (e == cudaSuccess) e = pair_attr<double, true, false>();
+    if (e == cudaSuccess) e = pair_attr<double, false, true>();
+    if (e == cudaSuccess) e = pair_attr<double, true, true>();
     done = e;
     return e;
 }
@@ -616,20 +531,11 @@ cudaError_t setup_kernels() {
 // forces only (fixed point, pair + bonded) or energies
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64) {
     if (energy) {
-        if (lambda) pair_launch<double, true, true, false>(L); else pair_launch<double, false, true, false>(L);
+        if (lambda) pair_launch<double, true, true>(L); else pair_launch<double, false, true>(L);
     } else if (fp64) {
-        if (lambda) pair_launch<double, true, false, false>(L); else pair_launch<double, false, false, false>(L);
+        if (lambda) pair_launch<double, true, false>(L); else pair_launch<double, false, false>(L);
     } else {
-        if (lambda) pair_launch<float, true, false, false>(L); else pair_launch<float, false, false, false>(L);
-    }
-}
-
-// one whole MD step (after the cell list of the current positions is built)
-void launch_step(const LaunchCtx &L, bool lambda) {
-    if (L.precision == 1) {
-        if (lambda) pair_launch<double, true, false, true>(L); else pair_launch<double, false, false, true>(L);
-    } else {
-        if (lambda) pair_launch<float, true, false, true>(L); else pair_launch<float, false, false, true>(L);
+        if (lambda) pair_launch<float, true, false>(L); else pair_launch<float, false, false>(L);
     }
 }
 

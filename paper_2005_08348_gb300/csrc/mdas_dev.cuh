@@ -20,7 +20,7 @@ constexpr int NL_G = 4;                // threads per bead in the pair-list step
 constexpr int NL_BLOCK = 128;          // threads per block of the pair-list step kernel
 constexpr int NL_BEADS = NL_BLOCK / NL_G;
 constexpr int NL_PART = 8;             // bonded partners per bead at most
-constexpr int NLB_STAGE = 1024;        // candidates staged per chunk by the list build
+constexpr int NLB_STAGE = 768;         // candidates staged per chunk by the list build
 constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
 constexpr int MAX_ROUND_TRIALS = 1024; // trials per batched swap evaluation
@@ -226,11 +226,9 @@ struct LaunchCtx {
 };
 
 cudaError_t setup_kernels();
-void launch_cells(const LaunchCtx &L, bool counted = false);
+void launch_cells(const LaunchCtx &L);
 void launch_thermo_draws(const LaunchCtx &L, int n_steps);
-void launch_trial_one(const LaunchCtx &L);
 void launch_pair(const LaunchCtx &L, bool lambda, bool energy, bool fp64);
-void launch_step(const LaunchCtx &L, bool lambda);
 void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
 // pair-list MD: thermostat factor of the coming step (kernels.cu); list build
 // (its kernels return at once for systems whose list is valid), one step of

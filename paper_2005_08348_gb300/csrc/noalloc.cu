@@ -253,7 +253,7 @@ extern "C" mdas_status mdas_forces_noalloc(const mdas_system_desc *d, const uint
     L.precision = d->precision;
     L.stream = stream;
     L.max_bead_blocks = S.n_bead_blocks;
-    launch_cells(L, false);
+    launch_cells(L);
     launch_pair(L, false, false, d->precision == MDAS_FP64);
     launch_total_force(L, f_out, 0);
     NACK(cudaGetLastError());

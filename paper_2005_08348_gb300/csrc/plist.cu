@@ -72,8 +72,10 @@ struct BuildSmem {
     int noff[28];
     int last;
     int ws[GRP / 32];
+    int wn[GRP / 32];                         // candidates near each warp's beads
     float4 sf[NLB_STAGE];                     // frame coordinates, meta word in w
     int sk[NLB_STAGE];                        // list index
+    uint16_t wl[GRP / 32][NLB_STAGE];         // per warp: staged index of those candidates
 };
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
@@ -84,73 +86,64 @@ constexpr size_t group_smem() {
 }
 
 // ------------------------------------------------------------ build items
-// Count the beads [b0, b0 + GRP) into list-build cells; the last item of the
-// system (a ticket) scans the counts into (first list index, count) per cell.
-__device__ void nl_count_item(const SysDev &S, int b0, const Grp &g, BuildSmem &sm) {
+// Count the beads [b0, b0 + GRP) into list-build cells.
+__device__ void nl_count_item(const SysDev &S, int b0, const Grp &g) {
     const Params &P = *S.p;
-    Counters &C = *S.c;
     const int i = b0 + g.t;
     if (i < P.n) {
         const int c = lcell_of(P, S.pos[i]);
         const int slot = atomicAdd(&S.lcell_count[c], 1);
         if (slot < P.lcapc) S.ltmp[c * P.lcapc + slot] = i;
-        else atomicOr(&C.err, ERR_CELL_OVERFLOW);
+        else atomicOr(&S.c->err, ERR_CELL_OVERFLOW);
     }
-    g.sync();
-    if (g.t == 0) {
-        __threadfence();
-        sm.last = atomicAdd(&C.nticket, 1u) == (unsigned)(S.n_bead_blocks - 1);
-    }
-    g.sync();
-    const bool last = sm.last;
-    g.sync();
-    if (!last) return;
-    __threadfence();
-    // exclusive scan: each thread a run of cells, then the group
-    const int nc = P.n_lcells;
-    const int per = (nc + GRP - 1) / GRP;
-    const int c0 = min(g.t * per, nc), c1 = min(c0 + per, nc);
-    int sum = 0;
-    for (int c = c0; c < c1; ++c) sum += min(__ldcg(&S.lcell_count[c]), P.lcapc);
-    const int lane = g.t & 31, w = g.t >> 5;
-    int inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int x = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += x;
-    }
-    if (lane == 31) sm.ws[w] = inc;
-    g.sync();
-    int run = inc - sum;
-    for (int q = 0; q < w; ++q) run += sm.ws[q];
-    for (int c = c0; c < c1; ++c) {
-        const int m = min(__ldcg(&S.lcell_count[c]), P.lcapc);
-        S.lcell[c] = make_int2(run, m);
-        S.lcell_count[c] = 0;
-        run += m;
-    }
-    if (g.t == 0) C.nticket = 0;
-    g.sync();
 }
 
-// Place the beads of cells c0 .. c0 + 3 (one warp each) in list order, ranked
-// by id within their cell, into position buffer par.
-__device__ void nl_place_item(const SysDev &S, int c0, int par, const Grp &g) {
+// Octant (2 x 2 x 2 sub-cells) of a position within its list-build cell.
+__device__ __forceinline__ int loct_of(const Params &P, uint4 q) {
+    const int ox = (int)(((unsigned long long)q.x * (unsigned)(2 * P.ln[0])) >> 32) & 1;
+    const int oy = (int)(((unsigned long long)q.y * (unsigned)(2 * P.ln[1])) >> 32) & 1;
+    const int oz = (int)(((unsigned long long)q.z * (unsigned)(2 * P.ln[2])) >> 32) & 1;
+    return (oz << 2) | (oy << 1) | ox;
+}
+
+// Place the beads of cells c0 .. c0 + 3 (one warp each) in list order into
+// position buffer par, ranked within their cell by (octant, id): beads next to
+// each other in the list are close in space.  The first list index of a cell
+// is the number of beads in the cells before it, summed here by the whole
+// group (every item sums its own prefix: no serial scan).
+__device__ void nl_place_item(const SysDev &S, int c0, int par, const Grp &g, BuildSmem &sm) {
     const Params &P = *S.p;
+    int part = 0;
+    for (int q = g.t; q < c0; q += GRP) part += min(__ldcg(&S.lcell_count[q]), P.lcapc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((g.t & 31) == 0) sm.ws[g.t >> 5] = part;
+    g.sync();
     const int c = c0 + (g.t >> 5), lane = g.t & 31;
+    int first = 0;
+    for (int w = 0; w < GRP / 32; ++w) first += sm.ws[w];
+    for (int q = c0; q < c; ++q) first += min(__ldcg(&S.lcell_count[q]), P.lcapc);
+    g.sync();
     if (c >= P.n_lcells) return;
-    const int2 lc = S.lcell[c];
-    const int cnt = lc.y, base = c * P.lcapc;
+    const int cnt = min(__ldcg(&S.lcell_count[c]), P.lcapc), base = c * P.lcapc;
+    const int2 lc = make_int2(first, cnt);
+    if (lane == 0) S.lcell[c] = lc;
     uint4 *cur = S.lpos + (size_t)par * P.n;
+    auto key = [&](int a) {                    // unique: ids are below 2^28
+        if (a >= cnt) return 0x7fffffff;
+        const int id = S.ltmp[base + a];
+        return (loct_of(P, S.pos[id]) << 28) | id;
+    };
     for (int a0 = 0; a0 < cnt; a0 += 32) {
         const int a = a0 + lane;
-        const int id = a < cnt ? S.ltmp[base + a] : 0x7fffffff;
-        int rank = 0;                          // smaller ids in the cell
+        const int ka = key(a);
+        int rank = 0;                          // smaller keys in the cell
         for (int b0 = 0; b0 < cnt; b0 += 32) {
-            const int other = b0 + lane < cnt ? S.ltmp[base + b0 + lane] : 0x7fffffff;
-            for (int k = 0; k < 32; ++k) rank += __shfl_sync(0xffffffffu, other, k) < id;
+            const int other = key(b0 + lane);
+            for (int k = 0; k < 32; ++k) rank += __shfl_sync(0xffffffffu, other, k) < ka;
         }
         if (a < cnt) {
+            const int id = ka & 0x0fffffff;
             const int k = lc.x + rank;
             const uint4 p = S.pos[id];
             S.lid[k] = id;
@@ -190,6 +183,7 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
     }
     g.sync();
     const int M = sm.noff[27];
+    if (t == 0) S.lcell_count[c] = 0;          // counted afresh at the next build
     const uint32_t ox = (uint32_t)(((unsigned long long)(2 * cx + 1) * P.lcwu[0]) >> 1);
     const uint32_t oy = (uint32_t)(((unsigned long long)(2 * cy + 1) * P.lcwu[1]) >> 1);
     const uint32_t oz = (uint32_t)(((unsigned long long)(2 * cz + 1) * P.lcwu[2]) >> 1);
@@ -197,10 +191,17 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
     const float rl2 = P.rl2f;
     const int capg = P.lcap / NL_G;
     const int i0 = sm.nb[13].x, ni = sm.nb[13].y;
-    const int lane = t & 31, glane = lane & ~(NL_G - 1);
-    for (int ib = 0; ib < ni; ib += GRP / NL_G) {
-        const int r = ib + t / NL_G, gl = t % NL_G;
-        const bool act = r < ni;
+    // lanes per bead: as many (up to 8) as leave every bead of the cell a
+    // group of lanes within one warp, in as few passes as possible
+    int lb = 8;
+    while (lb > 1 && (GRP / 32) * (32 / lb) < ni) --lb;
+    const int bpw = 32 / lb;                   // beads per warp and pass
+    const int lane = t & 31, w = t >> 5;
+    const int bw = lane / lb, gl = lane % lb, glane = bw * lb;
+    const unsigned gmask = (lb == 32 ? 0xffffffffu : (1u << lb) - 1u);
+    for (int ib = 0; ib < ni; ib += (GRP / 32) * bpw) {
+        const int r = ib + w * bpw + bw;
+        const bool act = bw < bpw && r < ni;
         const int ki = i0 + (act ? r : 0);
         const uint4 pi = cur[ki];
         const float xi = (float)(int)(pi.x - ox) * q0, yi = (float)(int)(pi.y - oy) * q1,
@@ -209,7 +210,7 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
         const uint32_t em = lip ? P.excl[meta_k(pi.w)] : 0u;
         const int self = sm.noff[13] + r;      // the bead's own candidate index
         // partner e goes to column e % NL_G, row e / NL_G (the columns differ
-        // by one entry at most)
+        // by one entry at most); the bead's lanes agree on e through a ballot
         int base = 0;
         for (int f0 = 0; f0 < M; f0 += NLB_STAGE) {
             const int mc = min(NLB_STAGE, M - f0);
@@ -228,11 +229,46 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
                 sm.sk[f] = kj;
             }
             g.sync();
-            const int nq = (mc + NL_G - 1) / NL_G;
+            // the candidates within rl of the box around this warp's beads
+            {
+                float lo0 = act ? xi : 3e30f, lo1 = act ? yi : 3e30f, lo2 = act ? zi : 3e30f;
+                float hi0 = act ? xi : -3e30f, hi1 = act ? yi : -3e30f, hi2 = act ? zi : -3e30f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+                    lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+                    lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+                    hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+                    hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+                    hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+                }
+                int nw = 0;
+                for (int f1 = 0; f1 < mc; f1 += 32) {
+                    const int f = f1 + lane;
+                    bool near = false;
+                    if (f < mc) {
+                        const float4 e = sm.sf[f];
+                        const float gx = fmaxf(fmaxf(lo0 - e.x, e.x - hi0), 0.f);
+                        const float gy = fmaxf(fmaxf(lo1 - e.y, e.y - hi1), 0.f);
+                        const float gz = fmaxf(fmaxf(lo2 - e.z, e.z - hi2), 0.f);
+                        near = gx * gx + gy * gy + gz * gz < rl2;
+                    }
+                    const unsigned bn = __ballot_sync(0xffffffffu, near);
+                    if (near) sm.wl[w][nw + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)f;
+                    nw += __popc(bn);
+                }
+                __syncwarp();
+                sm.wn[w] = nw;
+                __syncwarp();
+            }
+            const int mw = sm.wn[w];
+            const uint16_t *wl = sm.wl[w];
+            const int nq = (mw + lb - 1) / lb;
             for (int q = 0; q < nq; ++q) {
-                const int f = q * NL_G + gl;
+                const int u = q * lb + gl;
+                const int f = u < mw ? wl[u] : 0;
                 bool in = false;
-                if (act && f < mc) {
+                if (act && u < mw) {
                     const float4 e = sm.sf[f];
                     const float dx = xi - e.x, dy = yi - e.y, dz = zi - e.z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
@@ -241,7 +277,7 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
                     in = r2 < rl2 && !excl && f0 + f != self;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, in);
-                const unsigned grp = (bal >> glane) & ((1u << NL_G) - 1u);
+                const unsigned grp = (bal >> glane) & gmask;
                 if (in) {
                     const int e = base + __popc(grp & ((1u << gl) - 1u));
                     const int row = e / NL_G, col = e % NL_G;
@@ -251,12 +287,14 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
             }
         }
         if (act) {
-            const int cnt = base > gl ? (base - gl + NL_G - 1) / NL_G : 0;
-            S.nl_n[(size_t)ki * NL_G + gl] = min(cnt, capg);
-            if (base > P.lcap) atomicOr(&C.err, ERR_CELL_OVERFLOW);
+            for (int col = gl; col < NL_G; col += lb) {
+                const int cnt = base > col ? (base - col + NL_G - 1) / NL_G : 0;
+                S.nl_n[(size_t)ki * NL_G + col] = min(cnt, capg);
+            }
+            if (gl == 0 && base > P.lcap) atomicOr(&C.err, ERR_CELL_OVERFLOW);
             if (lip != 0) {
                 const int kl = meta_k(pi.w);
-                for (int p = gl; p < P.npart[kl]; p += NL_G)
+                for (int p = gl; p < P.npart[kl]; p += lb)
                     S.bslot[(size_t)ki * NL_PART + p] = S.lk[(int)(lip - 1) * P.bpl + P.part[kl][p]];
             }
         }
@@ -497,18 +535,18 @@ __device__ void nl_step_close(const SysDev &S, int lane) {
 
 // ======================================================== separate kernels
 __global__ void __launch_bounds__(GRP) k_nl_count(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+    const int2 bm = bmap[blockIdx.x];
+    const SysDev &S = sys[bm.x];
+    if (!S.c->nl_stale) return;
+    nl_count_item(S, bm.y, Grp{(int)threadIdx.x, 1});
+}
+
+__global__ void __launch_bounds__(GRP) k_nl_place(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     __shared__ BuildSmem sm;
     const int2 bm = bmap[blockIdx.x];
     const SysDev &S = sys[bm.x];
     if (!S.c->nl_stale) return;
-    nl_count_item(S, bm.y, Grp{(int)threadIdx.x, 1}, sm);
-}
-
-__global__ void __launch_bounds__(GRP) k_nl_place(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
-    if (!S.c->nl_stale) return;
-    nl_place_item(S, bm.y, S.c->nl_par, Grp{(int)threadIdx.x, 1});
+    nl_place_item(S, bm.y, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm);
 }
 
 __global__ void __launch_bounds__(GRP) k_nl_build(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
@@ -660,13 +698,13 @@ __device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &
     for (int it = gid; it < a.n_bead; it += G) {
         const int2 bm = a.beadmap[it];
         const SysDev &S = a.sys[bm.x];
-        if (build_flag(*S.c, which, s)) nl_count_item(S, bm.y, g, sm);
+        if (build_flag(*S.c, which, s)) nl_count_item(S, bm.y, g);
     }
     if (!grid_barrier(a.rs)) return false;
     for (int it = gid; it < a.n_lsort; it += G) {
         const int2 bm = a.lsortmap[it];
         const SysDev &S = a.sys[bm.x];
-        if (build_flag(*S.c, which, s)) nl_place_item(S, bm.y, (S.c->nl_par + b) & 1, g);
+        if (build_flag(*S.c, which, s)) nl_place_item(S, bm.y, (S.c->nl_par + b) & 1, g, sm);
     }
     if (!grid_barrier(a.rs)) return false;
     for (int it = gid; it < a.n_lcell; it += G) {
@@ -724,8 +762,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
             if (!run_build(a, 1, s, s + 1, g, gid, G, bsm)) return;
             tab_sys = -1;                      // the build used the same shared memory
         }
+        // the close of system q on block gridDim - 1 - q % gridDim (the trial
+        // parts start on the first blocks, so both overlap)
         if (threadIdx.x < 32)
-            for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
+            for (int q = gridDim.x - 1 - blockIdx.x; q < a.n_sys; q += gridDim.x) {
                 const SysDev &S = a.sys[q];
                 nl_step_close<Real>(S, threadIdx.x);
                 if (threadIdx.x == 0 && rebuild && S.c->nl_violp[s & 1]) S.c->nl_builds++;

@@ -221,160 +221,6 @@ __device__ void set_lipid_type(const SysDev &S, const Params &P, int l, int lt) 
     }
 }
 
-// One exchange trial per system, whole: grid (9, n_sys).  Every CTA draws the
-// proposal of trial C.trial and sums the dE over its 3 neighbour cells of
-// every changed bead, one candidate bead per thread (a flat list), so the
-// FP64 work of the in-cutoff pairs is spread over the block; the last CTA to
-// finish (a ticket, no waiting) adds the 9 partial sums in order, takes the
-// Metropolis decision and applies it.  Equal to one sequential trial; used
-// when trials come one at a time (one after every MD step).
-__global__ void __launch_bounds__(128) k_trial_one(const SysDev *__restrict__ sys) {
-    const SysDev &S = sys[blockIdx.y];
-    const Params &P = *S.p;
-    Counters &C = *S.c;
-    const int grp = blockIdx.x;
-    const int t = threadIdx.x, lane = t & 31;
-    __shared__ double sh[4];
-    __shared__ int it_beg[6 * MAXT + 1], it_cell[6 * MAXT];
-    __shared__ int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT];
-    __shared__ uint4 chg_pos[2 * MAXT];
-    __shared__ int nchg, last, accept;
-    __shared__ double lnu;
-    const unsigned long long T = C.trial;
-    const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
-    const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
-    const int ta = S.ltype[a], tb = S.ltype[b];
-    const bool null_trial = (a == b) || (ta == tb);
-    int m = 0;                                   // local indices whose bead type changes
-    if (!null_trial)
-        for (int k = 0; k < P.bpl; ++k) m |= (P.lbt[ta * 16 + k] != P.lbt[tb * 16 + k]) << k;
-    if (t == 32) lnu = log(unit53(w.z, w.w));    // off the critical path
-    if (t < 32) {
-        // changed beads in order (lipid a's, then lipid b's), compacted by ballot
-        const int side = lane >= P.bpl, k = side ? lane - P.bpl : lane;
-        const bool ch = lane < 2 * P.bpl && ((m >> k) & 1);
-        const unsigned bal = __ballot_sync(0xffffffffu, ch);
-        if (ch) {
-            const int o = __popc(bal & ((1u << lane) - 1u));
-            chg_id[o] = (side ? b : a) * P.bpl + k;
-            chg_old[o] = P.lbt[(side ? tb : ta) * 16 + k];
-            chg_new[o] = P.lbt[(side ? ta : tb) * 16 + k];
-        }
-        if (lane == 0) nchg = __popc(bal);
-    }
-    __syncthreads();
-    const int nc = nchg;
-    // items (changed bead, one of this group's 3 cells) with their bead counts
-    const int nx = P.nc[0], ny = P.nc[1], nz = P.nc[2];
-    int cnt = 0;
-    if (t < nc * 3) {
-        const int ci = t / 3, slot = grp * 3 + t % 3;
-        const uint4 pi = S.pos[chg_id[ci]];
-        if (t % 3 == 0) chg_pos[ci] = pi;
-        const int cx = (int)(((unsigned long long)pi.x * (unsigned)nx) >> 32);
-        const int cy = (int)(((unsigned long long)pi.y * (unsigned)ny) >> 32);
-        const int cz = (int)(((unsigned long long)pi.z * (unsigned)nz) >> 32);
-        const int dz = slot / 9 - 1, dy = (slot / 3) % 3 - 1, dx = slot % 3 - 1;
-        const int x = (cx + dx + nx) % nx, y = (cy + dy + ny) % ny, z = (cz + dz + nz) % nz;
-        const int cj = (z * ny + y) * nx + x;
-        it_cell[t] = cj;
-        cnt = S.cell_n[cj];
-        it_beg[t + 1] = cnt;
-    }
-    __syncthreads();
-    if (t < 32) {                                 // exclusive offsets: 3 items per lane, one warp scan
-        int v0 = 3 * lane < nc * 3 ? it_beg[3 * lane + 1] : 0;
-        int v1 = 3 * lane + 1 < nc * 3 ? it_beg[3 * lane + 2] : 0;
-        int v2 = 3 * lane + 2 < nc * 3 ? it_beg[3 * lane + 3] : 0;
-        int sum = v0 + v1 + v2, inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += x;
-        }
-        const int ex = inc - sum;
-        __syncwarp();
-        if (3 * lane < nc * 3) it_beg[3 * lane + 1] = ex + v0;
-        if (3 * lane + 1 < nc * 3) it_beg[3 * lane + 2] = ex + v0 + v1;
-        if (3 * lane + 2 < nc * 3) it_beg[3 * lane + 3] = ex + v0 + v1 + v2;
-        if (lane == 0) it_beg[0] = 0;
-    }
-    __syncthreads();
-    const int nit = nc * 3;
-    const int total = nc > 0 ? it_beg[nit] : 0;
-    double acc = 0.0;
-    for (int f = t; f < total; f += blockDim.x) {
-        int lo = 0, hi = nit - 1;                 // the item holding candidate f
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (it_beg[mid] <= f) lo = mid; else hi = mid - 1;
-        }
-        const int it = lo, ci = it / 3;
-        const int p = it_cell[it] * P.capc + (f - it_beg[it]);
-        const int i = chg_id[ci];
-        const uint4 pi = chg_pos[ci], pj = S.spos[p];
-        const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
-        const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
-        const float r2f = fx * fx + fy * fy + fz * fz;
-        if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
-        const int j = S.sorted_id[p];
-        const int lj = meta_lip(pj.w), kj = meta_k(pj.w);
-        const bool chj = (lj == a || lj == b) && ((m >> kj) & 1);
-        if (j == i || (chj && j < i)) continue;
-        if (lj >= 0 && lj == meta_lip(pi.w) && ((P.excl[meta_k(pi.w)] >> kj) & 1u)) continue;
-        const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
-        const double r2 = ex * ex + ey * ey + ez * ez;
-        if (r2 >= P.rc2) continue;
-        const int old_j = meta_ta(pj.w);
-        const int new_j = chj ? (int)P.lbt[(lj == a ? tb : ta) * 16 + kj] : old_j;
-        acc += pair_du(P, chg_old[ci], old_j, chg_new[ci], new_j, r2);
-    }
-    const double part = block_sum(acc, sh);
-    if (t == 0) {
-        S.tdE[grp] = part;
-        __threadfence();
-        last = atomicAdd(&C.ticket, 1u) == DE_GROUPS - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    if (t == 0) {
-        __threadfence();
-        double dE = 0.0;
-        for (int g = 0; g < DE_GROUPS; ++g) dE += __ldcg(&S.tdE[g]);
-        TrialRec r;
-        r.a = a; r.b = b; r.u = unit53(w.z, w.w); r.dE = 0.0; r.accepted = 0; r.index = T;
-        r.null_trial = null_trial;
-        if (!null_trial) {
-            r.dE = dE;
-            r.accepted = dE + P.kT * lnu <= 0.0;
-        }
-        accept = r.accepted;
-        if (r.accepted) { S.ltype[a] = tb; S.ltype[b] = ta; }
-        S.log[T % LOG_CAP] = r;
-        C.trials++;
-        C.force_evals++;
-        C.null_trials += r.null_trial;
-        C.accepted += r.accepted;
-        C.trial = T + 1;
-        C.pending = 0;
-        C.ticket = 0;
-    }
-    __syncthreads();
-    if (accept && t < 2 * P.bpl) {               // the exchange: every bead of both lipids
-        const int side = t >= P.bpl, k = side ? t - P.bpl : t;
-        const int l = side ? b : a, lt = side ? ta : tb;
-        const int id = l * P.bpl + k;
-        const int bt = P.lbt[lt * 16 + k];
-        const uint32_t mm = meta_make(bt, bt, k, l + 1);
-        S.pos[id].w = mm;
-        S.spos[S.sidx[id]].w = mm;
-    }
-}
-
-void launch_trial_one(const LaunchCtx &L) {
-    dim3 g(DE_GROUPS, L.n_sys);
-    k_trial_one<<<g, 128, 0, L.stream>>>(L.sys);
-}
 
 // One exchange trial per system from the pair list: grid (TRIAL_PARTS, n_sys).
 __global__ void __launch_bounds__(GRP) k_trial_nl(const SysDev *__restrict__ sys) {
