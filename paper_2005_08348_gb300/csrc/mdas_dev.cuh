@@ -110,7 +110,8 @@ struct Counters {
     int ke_fresh;                      // ke_total holds the kinetic energy of the current velocities
     int ke_pending;                    // the step kernel left kinetic energy in ke_slot
     double ke_total[2];
-    long long ke_slot[KE_SLOTS][2];    // fixed-point kinetic energy per slot and group (2^32 units)
+    long long ke_slot[KE_SLOTS][2];    // fixed-point kinetic energy per slot and group (2^16 units per
+                                       // kJ/mol for FP32 systems, 2^32 for FP64)
     int nl_stale;                      // the pair list must be rebuilt before its next use
     int nl_viol;                       // a bead moved farther than the skin allows (this step)
     int nl_violp[2];                   // the same per step parity (persistent kernel)

@@ -96,18 +96,23 @@ __device__ __forceinline__ void sep(const Params &P, uint4 a, uint4 b, Real d[3]
     }
 }
 
-// All bonded terms of bead with local index k at pi; get(li) returns the
-// position of the bead with local index li of the same lipid.
+// Bonded terms of the bead with local index k at pi: term q < nbond is bond
+// q, the rest are its angles; every stride-th term from `first` is added to f
+// (all of them by default).  get(li) returns the position of the bead with
+// local index li of the same lipid.
 template <typename Real, class Get>
-__device__ void bonded_force(const Params &P, int k, uint4 pi, Get get, Real f[3]) {
-    for (int b = 0; b < P.nbond[k]; ++b) {
-        Real d[3];
-        sep<Real>(P, pi, get(P.bpart[k][b]), d);
-        const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
-        f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
-    }
-    for (int a = 0; a < P.nang[k]; ++a) {
+__device__ void bonded_force(const Params &P, int k, uint4 pi, Get get, Real f[3], int first = 0, int stride = 1) {
+    const int nb = P.nbond[k], nt = nb + P.nang[k];
+    for (int q = first; q < nt; q += stride) {
+        if (q < nb) {
+            Real d[3];
+            sep<Real>(P, pi, get(P.bpart[k][q]), d);
+            const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
+            f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
+            continue;
+        }
+        const int a = q - nb;
         const int li = P.ang[k][a][0], lj = P.ang[k][a][1], lk = P.ang[k][a][2];
         const uint4 qi = li == k ? pi : get(li);
         const uint4 qj = lj == k ? pi : get(lj);

@@ -305,11 +305,11 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
 // ------------------------------------------------------------- step item
 // One MD step of the beads k0 .. k0 + NL_BEADS - 1 (list order): positions
 // read from buffer par, written to buffer par ^ 1 and to the id-ordered
-// array.  The item's kinetic energy goes to integer slot `slot`; a bead that
+// array.  The item's kinetic energy goes to an integer slot; a bead that
 // moved farther than the list allows sets *viol.
 template <typename Real, bool LAM>
-__device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *viol, const Grp &g,
-                             StepSmem<Real> &sm, bool load_tables = true) {
+__device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const Grp &g, StepSmem<Real> &sm,
+                             bool load_tables = true) {
     using V4 = typename Vec4<Real>::T;
     constexpr bool F32 = sizeof(Real) == 4;
     const Params &P = *S.p;
@@ -320,23 +320,30 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *vi
     const bool valid = k < n;
     const uint4 *__restrict__ cur = S.lpos + (size_t)par * n;
     uint4 *nxt = S.lpos + (size_t)(par ^ 1) * n;
+    // this lane's list column: its first rows are loaded before anything else
+    // (rows 0 .. 3 always exist; entries past the end hold valid indices)
+    const int *__restrict__ lst = S.nl + (size_t)k * NL_G + gl;
+    const size_t rs = (size_t)P.lrow;
+    int j0 = __ldg(lst), j1 = __ldg(lst + rs), j2 = __ldg(lst + 2 * rs), j3 = __ldg(lst + 3 * rs);
     uint4 pi = make_uint4(0u, 0u, 0u, 0u);
     int cnt = 0, id = 0;
     if (valid) {
         pi = cur[k];
         cnt = S.nl_n[(size_t)k * NL_G + gl];
+        // fetched into shared memory while the pairs are summed: velocity and
+        // build position by lanes 0 and 1, bonded partners spread over the lanes
         if (gl == 0) {
-            // fetched into shared memory while the pairs are summed
             id = S.lid[k];
             const char *gv = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.vel) + id);
             for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&sm.svel[il]) + h, gv + h);
-            cp_async16(&sm.sxref[il], S.xref + k);
-            if (meta_lip(pi.w) >= 0) {
-                const int kl = meta_k(pi.w);
-                for (int p = 0; p < P.npart[kl]; ++p) cp_async16(&sm.spart[il][p], cur + S.bslot[(size_t)k * NL_PART + p]);
-            }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
         }
+        if (gl == 1 % NL_G) cp_async16(&sm.sxref[il], S.xref + k);
+        if (meta_lip(pi.w) >= 0) {
+            const int kl = meta_k(pi.w);
+            for (int p = gl; p < P.npart[kl]; p += NL_G)
+                cp_async16(&sm.spart[il][p], cur + S.bslot[(size_t)k * NL_PART + p]);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     if (load_tables)                           // else still there from the group's previous item
         for (int x = t; x < 256; x += GRP) {
@@ -360,7 +367,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *vi
     const int tai = meta_ta(pi.w) * 16, tbi = meta_tb(pi.w) * 16;
     Real ax = 0, ay = 0, az = 0;
 
-    auto pair = [&](uint4 pj) {
+    auto pair = [&](uint4 pj, bool ok) {
         const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
         Real dx, dy, dz;
         if (F32) {
@@ -373,13 +380,13 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *vi
             dz = (Real)((double)iz * P.qs[2]);
         }
         const Real r2 = dx * dx + dy * dy + dz * dz;
-        bool in = (r2 < rc2) & (r2 > (Real)0);
+        bool in = ok & (r2 < rc2) & (r2 > (Real)0);
         if (F32 && in && r2 >= rc2lo) {
             // within float rounding of the cutoff: decide from the exact offsets
             const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
             in = ex * ex + ey * ey + ez * ez < P.rc2;
         }
-        if (!in) return;
+        const Real r2c = in ? r2 : (Real)1;        // out of range: computed, then dropped
         const uint32_t mj = pj.w;
         const V4 ca = sm.tab[tai + meta_ta(mj)];
         Real f12 = ca.x, f6 = ca.y, qq = ca.z;
@@ -393,37 +400,45 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *vi
         if (F32) {
             // 1/r^2: hardware estimate and one Newton-Raphson step
             float r2i;
-            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2i) : "f"((float)r2));
-            r2i = fmaf(r2i, fmaf(-(float)r2, r2i, 1.0f), r2i);
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r2i) : "f"((float)r2c));
+            r2i = fmaf(r2i, fmaf(-(float)r2c, r2i, 1.0f), r2i);
             const float p = r2i * r2i;
             const float pe = fmaf(r2i, r2i, -p);                  // exact error of the square
             r6inv = (Real)fmaf(p, r2i, pe * r2i);                // r2i^3 rounded once
             r2inv = (Real)r2i;
-            rinv = (Real)rsqrtf((float)r2);
+            rinv = (Real)rsqrtf((float)r2c);
         } else {
-            rinv = (Real)(1.0 / sqrt((double)r2));
+            rinv = (Real)(1.0 / sqrt((double)r2c));
             r2inv = rinv * rinv;
             r6inv = r2inv * r2inv * r2inv;
         }
-        const Real fs = (f12 * r6inv - f6) * r6inv * r2inv + qq * (rinv * r2inv - krf2);
+        Real fs = (f12 * r6inv - f6) * r6inv * r2inv + qq * (rinv * r2inv - krf2);
+        fs = in ? fs : (Real)0;
         ax += fs * dx; ay += fs * dy; az += fs * dz;
     };
 
     // column gl of the bead's list, rows 0 .. cnt - 1, in groups of 4; the
     // next group's indices are loaded before the current group is summed
     // (entries past the end read a valid slot: 0)
-    const int *__restrict__ lst = S.nl + (size_t)k * NL_G + gl;
-    const size_t rs = (size_t)P.lrow;
     const int rows = cnt;
     auto idx = [&](int r) { return r < rows ? __ldg(lst + (size_t)r * rs) : 0; };
-    int j0 = idx(0), j1 = idx(1), j2 = idx(2), j3 = idx(3);
     for (int m = 0; m < rows; m += 4) {
         const uint4 q0 = cur[j0], q1 = cur[j1], q2 = cur[j2], q3 = cur[j3];
         j0 = idx(m + 4); j1 = idx(m + 5); j2 = idx(m + 6); j3 = idx(m + 7);
-        pair(q0);
-        if (m + 1 < rows) pair(q1);
-        if (m + 2 < rows) pair(q2);
-        if (m + 3 < rows) pair(q3);
+        pair(q0, true);
+        pair(q1, m + 1 < rows);
+        pair(q2, m + 2 < rows);
+        pair(q3, m + 3 < rows);
+    }
+    // this lane's share of the bead's bonded terms (partners staged by all
+    // lanes of the bead: wait for the copies, then the warp barrier)
+    cp_async_wait_all();
+    __syncwarp();
+    if (valid && meta_lip(pi.w) >= 0) {
+        Real fb[3] = {(Real)0, (Real)0, (Real)0};
+        const int kl = meta_k(pi.w);
+        bonded_force<Real>(P, kl, pi, [&](int li) { return sm.spart[il][P.pidx[kl][li]]; }, fb, gl, NL_G);
+        ax += fb[0]; ay += fb[1]; az += fb[2];
     }
 
     // partial forces summed over the bead's NL_G lanes in a fixed tree
@@ -435,13 +450,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *vi
     }
     Real e0 = 0, e1 = 0;
     if (valid && gl == 0) {
-        cp_async_wait_all();
-        Real fb[3] = {(Real)0, (Real)0, (Real)0};
-        if (meta_lip(pi.w) >= 0) {
-            const int kl = meta_k(pi.w);
-            bonded_force<Real>(P, kl, pi, [&](int li) { return sm.spart[il][P.pidx[kl][li]]; }, fb);
-        }
-        const Real f0 = ax + fb[0], f1 = ay + fb[1], f2 = az + fb[2];
+        const Real f0 = ax, f1 = ay, f2 = az;
         const int grp = id < P.n_lipid_beads ? 0 : 1;
         const Real a = F32 ? (Real)C.alpha_f[grp] : (Real)C.alpha[grp];
         const Real dtm = F32 ? (Real)P.dt_over_mf : (Real)P.dt_over_m;
@@ -475,7 +484,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *vi
     if (gl == 0) { sm.kered[0][il] = e0; sm.kered[1][il] = e1; }
     g.sync();
     if (t < 32) {
-        // the item's kinetic energy (fixed-order sums), into an integer slot
+        // the item's kinetic energy (fixed-order sums)
         Real k0s = 0, k1s = 0;
         for (int q = t; q < NL_BEADS; q += 32) { k0s += sm.kered[0][q]; k1s += sm.kered[1][q]; }
 #pragma unroll
@@ -484,9 +493,22 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int slot, int *vi
             k1s += __shfl_xor_sync(0xffffffffu, k1s, o);
         }
         if (t == 0) {
-            long long *ks = C.ke_slot[slot % KE_SLOTS];
-            atomicAdd((unsigned long long *)&ks[0], (unsigned long long)to_fix(k0s));
-            atomicAdd((unsigned long long *)&ks[1], (unsigned long long)to_fix(k1s));
+            // integer slot sums (order-free): FP32 items at 2^16 units per
+            // kJ/mol through a 32-bit conversion (an item holds far less than
+            // 2^15 kJ/mol), FP64 items at 2^32 units
+            long long *ks = C.ke_slot[(k0 / NL_BEADS) % KE_SLOTS];
+            long long u0, u1;
+            if (F32) {
+                const float lim = 32768.f;
+                if (!(fabsf((float)k0s) < lim && fabsf((float)k1s) < lim)) atomicOr(&C.err, ERR_NONFINITE);
+                u0 = __float2int_rn(fminf(fmaxf((float)k0s, -lim), lim) * 65536.f);
+                u1 = __float2int_rn(fminf(fmaxf((float)k1s, -lim), lim) * 65536.f);
+            } else {
+                u0 = to_fix(k0s);
+                u1 = to_fix(k1s);
+            }
+            atomicAdd((unsigned long long *)&ks[0], (unsigned long long)u0);
+            atomicAdd((unsigned long long *)&ks[1], (unsigned long long)u1);
             if (sm.sviol) atomicOr(viol, 1);
         }
     }
@@ -502,28 +524,29 @@ __device__ void nl_step_close(const SysDev &S, int lane) {
     static_assert(KE_SLOTS == 64, "two slots per lane");
     const Params &P = *S.p;
     Counters &C = *S.c;
-    long long a0 = __ldcg(&C.ke_slot[lane][0]) + __ldcg(&C.ke_slot[lane + 32][0]);
-    long long a1 = __ldcg(&C.ke_slot[lane][1]) + __ldcg(&C.ke_slot[lane + 32][1]);
+    long long s0 = __ldcg(&C.ke_slot[lane][0]) + __ldcg(&C.ke_slot[lane + 32][0]);
+    long long s1 = __ldcg(&C.ke_slot[lane][1]) + __ldcg(&C.ke_slot[lane + 32][1]);
     C.ke_slot[lane][0] = 0; C.ke_slot[lane][1] = 0;
     C.ke_slot[lane + 32][0] = 0; C.ke_slot[lane + 32][1] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
+    const double unit = sizeof(Real) == 4 ? 1.0 / 65536.0 : 1.0 / FIX;
+    const double a0 = (double)s0 * unit, a1 = (double)s1 * unit;
     const int in_at = C.in_at;
     const unsigned long long ctr = (in_at ? C.at_step : C.step) + 1;
-    const double K0 = (double)a0 * (1.0 / FIX), K1 = (double)a1 * (1.0 / FIX);
     if (lane < 2) {
         // the kinetic energy rounded to Real, as the thermostat kernel takes it
         const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
-        const double al = alpha_for(S, P, C, lane, (double)(Real)(lane ? K1 : K0), ctr, tag);
+        const double al = alpha_for(S, P, C, lane, (double)(Real)(lane ? a1 : a0), ctr, tag);
         C.alpha[lane] = al;
         C.alpha_f[lane] = (float)al;
     }
     if (lane == 0) {
-        C.ke_total[0] = K0;
-        C.ke_total[1] = K1;
+        C.ke_total[0] = a0;
+        C.ke_total[1] = a1;
         C.ke_fresh = 1;
         C.ke_pending = 0;
         if (in_at) C.at_step = ctr; else C.step = ctr;
@@ -585,7 +608,7 @@ __global__ void __launch_bounds__(GRP, 8) k_nl_step(const SysDev *__restrict__ s
     const SysDev &S = sys[bm.x];
     Counters &C = *S.c;
     const int par = C.nl_par;
-    nl_step_item<Real, LAM>(S, bm.y, par, blockIdx.x, &C.nl_viol, Grp{(int)threadIdx.x, 1}, sm);
+    nl_step_item<Real, LAM>(S, bm.y, par, &C.nl_viol, Grp{(int)threadIdx.x, 1}, sm);
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned nblk = (unsigned)((S.p->n + NL_BEADS - 1) / NL_BEADS);
@@ -745,7 +768,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
         for (int it = gid; it < a.n_nl; it += G) {
             const int2 bm = a.nlmap[it];
             const SysDev &S = a.sys[bm.x];
-            nl_step_item<Real, LAM>(S, bm.y, (S.c->nl_par + s) & 1, it, &S.c->nl_violp[s & 1], g, ssm,
+            nl_step_item<Real, LAM>(S, bm.y, (S.c->nl_par + s) & 1, &S.c->nl_violp[s & 1], g, ssm,
                                     bm.x != tab_sys);
             tab_sys = bm.x;
         }
