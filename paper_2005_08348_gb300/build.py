@@ -21,6 +21,10 @@ LIB = os.path.join(BUILD, "libmdas.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "-I", CSRC]
+# The pair-list and trial code is inlined into several kernels (the persistent
+# kernel and the separate ones) that must give identical bits: no implicit
+# multiply-add contraction there (the source writes its FMAs explicitly).
+FILE_FLAGS = {"plist.cu": ["-fmad=false"], "swap.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -50,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc(), *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)

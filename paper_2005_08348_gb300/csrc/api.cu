@@ -56,7 +56,7 @@ struct ListDims {
 
 ListDims list_dims(const mdas_system_desc *d) {
     ListDims L;
-    const double skin = d->list_skin > 0 ? d->list_skin : 0.2;
+    const double skin = d->list_skin > 0 ? d->list_skin : 0.3;
     const double lmin = std::min(d->box[0], std::min(d->box[1], d->box[2]));
     L.rl = std::max(d->rc, std::min(d->rc + skin, lmin / 3.0));
     for (int k = 0; k < 3; ++k) L.ln[k] = std::max(3, (int)std::floor(d->box[k] / L.rl));

@@ -6,6 +6,10 @@
 
 namespace mdas {
 
+// fused multiply-add in the argument's own precision (never promoted)
+__device__ __forceinline__ float fmr(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmr(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename Real>
 struct Vec4 {};
 template <>

@@ -330,8 +330,26 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     if (valid) {
         pi = cur[k];
         cnt = S.nl_n[(size_t)k * NL_G + gl];
-        // fetched into shared memory while the pairs are summed: velocity and
-        // build position by lanes 0 and 1, bonded partners spread over the lanes
+    }
+    if (load_tables) {                         // else still there from the group's previous item
+        for (int x = t; x < 256; x += GRP) {
+            V4 e;
+            if (F32) {
+                e.x = (Real)P.f12f[x]; e.y = (Real)P.f6f[x]; e.z = (Real)P.qqf[x];
+            } else {
+                e.x = (Real)(12.0 * P.c12[x]); e.y = (Real)(6.0 * P.c6[x]); e.z = (Real)P.qq[x];
+            }
+            e.w = (Real)0;
+            sm.tab[x] = e;
+        }
+        if (t == 0) sm.sviol = 0;              // afterwards cleared by every item's end
+        g.sync();
+    }
+    // the first row group's positions, then (while they arrive) the copies
+    // into shared memory the update needs: velocity and build position by
+    // lanes 0 and 1, the bonded partners spread over the bead's lanes
+    uint4 q0 = cur[j0], q1 = cur[j1], q2 = cur[j2], q3 = cur[j3];
+    if (valid) {
         if (gl == 0) {
             id = S.lid[k];
             const char *gv = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.vel) + id);
@@ -345,19 +363,6 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    if (load_tables)                           // else still there from the group's previous item
-        for (int x = t; x < 256; x += GRP) {
-            V4 e;
-            if (F32) {
-                e.x = (Real)P.f12f[x]; e.y = (Real)P.f6f[x]; e.z = (Real)P.qqf[x];
-            } else {
-                e.x = (Real)(12.0 * P.c12[x]); e.y = (Real)(6.0 * P.c6[x]); e.z = (Real)P.qq[x];
-            }
-            e.w = (Real)0;
-            sm.tab[x] = e;
-        }
-    if (t == 0) sm.sviol = 0;
-    g.sync();
 
     const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
     const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
@@ -379,7 +384,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             dy = (Real)((double)iy * P.qs[1]);
             dz = (Real)((double)iz * P.qs[2]);
         }
-        const Real r2 = dx * dx + dy * dy + dz * dz;
+        const Real r2 = fmr(dx, dx, fmr(dy, dy, dz * dz));
         bool in = ok & (r2 < rc2) & (r2 > (Real)0);
         if (F32 && in && r2 >= rc2lo) {
             // within float rounding of the cutoff: decide from the exact offsets
@@ -392,9 +397,9 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         Real f12 = ca.x, f6 = ca.y, qq = ca.z;
         if (LAM) {
             const V4 cb = sm.tab[tbi + meta_tb(mj)];
-            f12 = ((Real)1 - lam) * f12 + lam * cb.x;
-            f6 = ((Real)1 - lam) * f6 + lam * cb.y;
-            qq = ((Real)1 - lam) * qq + lam * cb.z;
+            f12 = fmr((Real)1 - lam, f12, lam * cb.x);
+            f6 = fmr((Real)1 - lam, f6, lam * cb.y);
+            qq = fmr((Real)1 - lam, qq, lam * cb.z);
         }
         Real rinv, r2inv, r6inv;
         if (F32) {
@@ -412,9 +417,9 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             r2inv = rinv * rinv;
             r6inv = r2inv * r2inv * r2inv;
         }
-        Real fs = (f12 * r6inv - f6) * r6inv * r2inv + qq * (rinv * r2inv - krf2);
+        Real fs = fmr(fmr(f12, r6inv, -f6) * r6inv, r2inv, qq * fmr(rinv, r2inv, -krf2));
         fs = in ? fs : (Real)0;
-        ax += fs * dx; ay += fs * dy; az += fs * dz;
+        ax = fmr(fs, dx, ax); ay = fmr(fs, dy, ay); az = fmr(fs, dz, az);
     };
 
     // column gl of the bead's list, rows 0 .. cnt - 1, in groups of 4; the
@@ -423,7 +428,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     const int rows = cnt;
     auto idx = [&](int r) { return r < rows ? __ldg(lst + (size_t)r * rs) : 0; };
     for (int m = 0; m < rows; m += 4) {
-        const uint4 q0 = cur[j0], q1 = cur[j1], q2 = cur[j2], q3 = cur[j3];
+        if (m > 0) { q0 = cur[j0]; q1 = cur[j1]; q2 = cur[j2]; q3 = cur[j3]; }
         j0 = idx(m + 4); j1 = idx(m + 5); j2 = idx(m + 6); j3 = idx(m + 7);
         pair(q0, true);
         pair(q1, m + 1 < rows);
@@ -455,9 +460,9 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         const Real a = F32 ? (Real)C.alpha_f[grp] : (Real)C.alpha[grp];
         const Real dtm = F32 ? (Real)P.dt_over_mf : (Real)P.dt_over_m;
         V4 v = sm.svel[il];
-        v.x = a * v.x + f0 * dtm;
-        v.y = a * v.y + f1 * dtm;
-        v.z = a * v.z + f2 * dtm;
+        v.x = fmr(a, v.x, f0 * dtm);
+        v.y = fmr(a, v.y, f1 * dtm);
+        v.z = fmr(a, v.z, f2 * dtm);
         reinterpret_cast<V4 *>(S.vel)[id] = v;
         if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&C.err, ERR_NONFINITE);
         uint4 np = pi;
@@ -477,8 +482,8 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         const float ux = (float)(int)(np.x - xr.x) * qs0;
         const float uy = (float)(int)(np.y - xr.y) * qs1;
         const float uz = (float)(int)(np.z - xr.z) * qs2;
-        if (ux * ux + uy * uy + uz * uz > P.dmax2f) sm.sviol = 1;
-        const Real ke = (Real)0.5 * (F32 ? (Real)P.massf : (Real)P.mass) * (v.x * v.x + v.y * v.y + v.z * v.z);
+        if (fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > P.dmax2f) sm.sviol = 1;
+        const Real ke = (Real)0.5 * (F32 ? (Real)P.massf : (Real)P.mass) * fmr(v.x, v.x, fmr(v.y, v.y, v.z * v.z));
         if (grp == 0) e0 = ke; else e1 = ke;
     }
     if (gl == 0) { sm.kered[0][il] = e0; sm.kered[1][il] = e1; }
@@ -510,6 +515,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             atomicAdd((unsigned long long *)&ks[0], (unsigned long long)u0);
             atomicAdd((unsigned long long *)&ks[1], (unsigned long long)u1);
             if (sm.sviol) atomicOr(viol, 1);
+            sm.sviol = 0;                      // for the group's next item
         }
     }
     g.sync();
