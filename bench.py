@@ -300,6 +300,7 @@ def run_gpu(args):
     if not args.no_extra:
         out["batched_replicas"] = replica_benchmark(stream)
         out["swap_trials_4608_lipids"] = swap_benchmark(stream)
+        out["mdas_4608_lipids"] = mdas_benchmark(stream)
         out["served"] = serving_benchmark(stream)
     if not args.no_cpu_baseline:
         ob = oracle_rate(m)
@@ -356,6 +357,28 @@ def replica_benchmark(stream, n_rep=64, rounds=3):
            "speedup": ts / tb, "rounds": rounds}
     for s in sys_b + sys_s:
         s.close()
+    return res
+
+
+def mdas_benchmark(stream, n_moves=6):
+    """MDAS moves on the 4608-lipid bilayer (~140k beads): 8 pairs (16
+    lipids) exchanged along 10 lambda steps of 5 MD steps each, FP32 pair
+    arithmetic, FP64 work."""
+    from paper_2005_08348_gb300 import mdas, synth
+    m = synth.mdas_patch()
+    s = mdas.System(m, stream=stream.cuda_stream)
+    s.alchemical_move(8, 10, 5)
+    acc = []
+
+    def moves():
+        for _ in range(n_moves):
+            acc.append(s.alchemical_move(8, 10, 5)["accepted"])
+
+    t = _elapsed(stream, moves)
+    res = {"workload": f"{m.n_lipids} lipids, {m.n_beads} beads; 8 pairs, 10 lambda steps x 5 MD steps",
+           "moves_per_s": n_moves / t, "ms_per_move": 1e3 * t / n_moves,
+           "force_evaluations_per_move": 10 * 5 + 10, "accepted": int(sum(acc)), "moves": n_moves}
+    s.close()
     return res
 
 

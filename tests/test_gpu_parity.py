@@ -297,3 +297,22 @@ def test_nve_drift_bounded(small):
         es.append(s.energy()["total"])
     drift = abs(es[-1] - e0) / abs(e0)
     assert drift < 5e-3, (e0, es)
+
+
+def test_mdas_move_full_size_matches_oracle():
+    """The MDAS workload at full size: 4608-lipid bilayer (~140k beads), a move
+    of 8 pairs (16 lipids) over 10 lambda steps of 5 MD steps each, FP64."""
+    m = synth.mdas_patch()
+    s = mdas.System(m, precision="fp64")
+    o = oracle.Oracle(m)
+    so = o.state()
+    res = s.alchemical_move(8, 10, 5)
+    ro = o.mdas_move(so, 8, 10, 5)
+    assert np.array_equal(res["pairs"], ro["pairs"])
+    assert abs(res["w"] - ro["w"]) < DE_TOL, (res["w"], ro["w"])
+    assert res["u"] == ro["u"] and res["accepted"] == ro["accepted"]
+    st = s.get_state()
+    assert np.array_equal(st["ltype"], so["ltype"])
+    dx = np.abs((st["pos_u"].astype(np.int64) - so["pos_u"].astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31)
+    assert dx.max() <= 4, dx.max()
+    assert st["move"] == so["move"] and st["at_step"] == so["at_step"]
