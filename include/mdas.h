@@ -190,6 +190,25 @@ mdas_status mdas_cell_list(mdas_system *s, int32_t *sorted_ids, int32_t *cell_st
  * must share one precision and one CUDA stream. */
 mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32_t md_steps, int32_t swap_trials);
 
+/* Autotuning of the pair-list skin, the one free parameter of a batch: the
+ * cutoff sums of Sec. 3 do not depend on it, only the list rebuild schedule,
+ * the list lengths and the FP32 summation order do.  For each of the n_skins
+ * candidates (nm, each > 0) the n_systems systems described by descs[] are
+ * created with list_skin = that candidate (each with its descriptor's stream
+ * and allocator; all must share one precision and one stream, as for
+ * mdas_batch_run), advanced by one untimed round, then by `rounds` rounds of
+ * mdas_batch_run(md_steps, swap_trials) timed with CUDA events on their
+ * stream, and destroyed.  us_per_step[c] (host, n_skins entries) receives the
+ * device time per MD step of candidate c, and *best_skin the fastest
+ * candidate: create the systems with desc.list_skin = *best_skin afterwards.
+ * Neither the descriptors nor any existing system change.  Errors:
+ * MDAS_ERR_INVALID_ARG (a NULL pointer, a count <= 0, swap_trials < 0, a
+ * candidate <= 0) before any GPU work; otherwise the first error of a
+ * creation or a round, returned after that candidate's systems are destroyed. */
+mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
+                                int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
+                                double *us_per_step, double *best_skin);
+
 /* Philox4x32-10 evaluated on the GPU for counters (i, c1, c2, c3), i =
  * 0..n-1, key (k0, k1): out [n*4] host. */
 mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out);

@@ -1081,6 +1081,56 @@ mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32
     return st;
 }
 
+mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
+                                int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
+                                double *us_per_step, double *best_skin) {
+    if (!descs || n_systems <= 0 || !skins || n_skins <= 0 || md_steps <= 0 || swap_trials < 0 || rounds <= 0 ||
+        !us_per_step || !best_skin)
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: bad argument");
+    for (int i = 0; i < n_systems; ++i)
+        if (!descs[i]) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: NULL descriptor");
+    for (int c = 0; c < n_skins; ++c)
+        if (!(skins[c] > 0.0)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: a candidate skin is <= 0");
+    int best = -1;
+    for (int c = 0; c < n_skins; ++c) {
+        std::vector<mdas_system_desc> dv(n_systems);
+        std::vector<mdas_system *> sv;
+        for (int i = 0; i < n_systems; ++i) {
+            dv[i] = *descs[i];
+            dv[i].list_skin = skins[c];
+        }
+        mdas_status st = MDAS_OK;
+        for (int i = 0; i < n_systems && st == MDAS_OK; ++i) {
+            mdas_system *x = nullptr;
+            st = mdas_create_system(&dv[i], &x);
+            if (st == MDAS_OK) sv.push_back(x);
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float ms = 0.f;
+        if (st == MDAS_OK) st = mdas_batch_run(sv.data(), n_systems, md_steps, swap_trials);   // untimed round
+        if (st == MDAS_OK) {
+            cudaStream_t q = sv[0]->stream;
+            cudaError_t e = cudaEventCreate(&e0);
+            if (e == cudaSuccess) e = cudaEventCreate(&e1);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, q);
+            for (int r = 0; r < rounds && e == cudaSuccess && st == MDAS_OK; ++r)
+                st = mdas_batch_run(sv.data(), n_systems, md_steps, swap_trials);
+            if (e == cudaSuccess && st == MDAS_OK) e = cudaEventRecord(e1, q);
+            if (e == cudaSuccess && st == MDAS_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && st == MDAS_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess && st == MDAS_OK) st = cuda_fail(nullptr, e, "tune_list_skin");
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        for (auto *x : sv) mdas_destroy_system(x);
+        if (st != MDAS_OK) return st;
+        us_per_step[c] = 1e3 * (double)ms / ((double)rounds * md_steps);
+        if (best < 0 || us_per_step[c] < us_per_step[best]) best = c;
+    }
+    *best_skin = skins[best];
+    return MDAS_OK;
+}
+
 mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out) {
     mdas_system *s = nullptr;
     if (n < 0 || (n > 0 && !out)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "philox: bad argument");

@@ -85,7 +85,8 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_set_state", "mdas_cell_list", "mdas_batch_run", "mdas_philox", "mdas_set_kernel_timing",
            "mdas_pair_kernel_time", "mdas_set_persistent", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
-           "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint"]
+           "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
+           "mdas_tune_list_skin"]
 
 
 def library_path() -> str:
@@ -398,6 +399,28 @@ def footprint(m, precision=MDAS_FP32):
 def batch_run(systems, md_steps, swap_trials):
     arr = (C.c_void_p * len(systems))(*[s._ptr.value for s in systems])
     _check(lib().mdas_batch_run(arr, len(systems), int(md_steps), int(swap_trials)), systems[0]._ptr)
+
+
+def tune_list_skin(models, skins=(0.2, 0.25, 0.3, 0.35, 0.4), md_steps=100, swap_trials=0, rounds=3,
+                   precision="fp32", stream=None):
+    """Time batches of `models` (synth.Membrane list) at each candidate pair-list
+    skin (mdas_tune_list_skin); returns (best skin, {skin: us per MD step})."""
+    prec = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
+    keep, descs = [], []
+    stream = _current_stream() if stream is None else int(stream)
+    for m in models:
+        d, k = make_desc(m, prec)
+        d.cuda_stream = stream or None
+        d.dev_alloc, d.dev_free = _torch_allocator()
+        keep.append((d, k))
+        descs.append(C.pointer(d))
+    arr = (C.POINTER(Desc) * len(descs))(*descs)
+    cand = np.ascontiguousarray(skins, np.float64)
+    us = np.zeros(len(cand), np.float64)
+    best = C.c_double()
+    _check(lib().mdas_tune_list_skin(arr, len(descs), _p(cand), len(cand), int(md_steps), int(swap_trials),
+                                     int(rounds), _p(us), C.byref(best)))
+    return best.value, dict(zip(cand.tolist(), us.tolist()))
 
 
 def philox(k0, k1, c1, c2, c3, n):

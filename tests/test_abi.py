@@ -53,6 +53,20 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     assert lib.mdas_create_system(None, ctypes.byref(out)) == 1
 
 
+def test_tune_list_skin_rejects_bad_arguments_without_touching_the_gpu():
+    from paper_2005_08348_gb300 import mdas
+    lib = mdas.lib()
+    d = mdas.Desc()
+    arr = (ctypes.POINTER(mdas.Desc) * 1)(ctypes.pointer(d))
+    skins = (ctypes.c_double * 2)(0.3, -0.1)
+    us = (ctypes.c_double * 2)()
+    best = ctypes.c_double()
+    assert lib.mdas_tune_list_skin(arr, 1, skins, 2, 10, 0, 1, us, ctypes.byref(best)) == 1
+    assert b"candidate" in lib.mdas_last_error(None)
+    assert lib.mdas_tune_list_skin(arr, 0, skins, 1, 10, 0, 1, us, ctypes.byref(best)) == 1
+    assert lib.mdas_tune_list_skin(arr, 1, skins, 1, 0, 0, 1, us, ctypes.byref(best)) == 1
+
+
 def test_no_cpu_fallback_in_the_product_path():
     pkg = os.path.join(ROOT, "paper_2005_08348_gb300")
     for f in os.listdir(pkg):

@@ -101,3 +101,24 @@ def test_step_kernel_forces_match_oracle(prec, which):
     frms = np.sqrt((Fo * Fo).sum(1).mean())
     err = (np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), frms)).max()
     assert err < (1e-10 if prec == "fp64" else 1e-5), err
+
+
+def test_tune_list_skin_times_every_candidate():
+    """The autotuner creates, times and destroys one batch per candidate skin
+    and leaves the caller's systems alone."""
+    ms = synth.replica_set(3, lo=128, hi=256, seed=11)
+    keep = mdas.System(ms[0], precision="fp32")
+    keep.md_steps(5, swap_every=0)
+    before = keep.get_state()
+    best, us = mdas.tune_list_skin(ms, skins=(0.1, 0.3), md_steps=20, swap_trials=4, rounds=2)
+    assert best in (0.1, 0.3) and set(us) == {0.1, 0.3}
+    assert all(np.isfinite(v) and v > 0 for v in us.values())
+    assert us[best] == min(us.values())
+    after = keep.get_state()
+    assert np.array_equal(before["pos_u"], after["pos_u"])
+    # a system made with the tuned skin runs like any other
+    s = mdas.System(ms[0], precision="fp32", list_skin=best)
+    s.md_steps(10, swap_every=5)
+    assert s.counters()["md_steps"] == 10
+    with pytest.raises(mdas.MdasError):
+        mdas.tune_list_skin(ms[:1], skins=(0.3, 0.0), md_steps=10)
