@@ -422,18 +422,18 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         ax = fmr(fs, dx, ax); ay = fmr(fs, dy, ay); az = fmr(fs, dz, az);
     };
 
-    // column gl of the bead's list, rows 0 .. cnt - 1, in groups of 4; the
-    // next group's indices are loaded before the current group is summed
-    // (entries past the end read a valid slot: 0)
+    // column gl of the bead's list, rows 0 .. cnt - 1, in groups of 4: as
+    // soon as a row is summed, its register takes the position of the row
+    // 4 further on and the index of the row 8 further on, so every load has
+    // a whole group of pairs to arrive (entries past the end read slot 0)
     const int rows = cnt;
     auto idx = [&](int r) { return r < rows ? __ldg(lst + (size_t)r * rs) : 0; };
+    j0 = idx(4); j1 = idx(5); j2 = idx(6); j3 = idx(7);
     for (int m = 0; m < rows; m += 4) {
-        if (m > 0) { q0 = cur[j0]; q1 = cur[j1]; q2 = cur[j2]; q3 = cur[j3]; }
-        j0 = idx(m + 4); j1 = idx(m + 5); j2 = idx(m + 6); j3 = idx(m + 7);
-        pair(q0, true);
-        pair(q1, m + 1 < rows);
-        pair(q2, m + 2 < rows);
-        pair(q3, m + 3 < rows);
+        pair(q0, true);          q0 = cur[j0]; j0 = idx(m + 8);
+        pair(q1, m + 1 < rows);  q1 = cur[j1]; j1 = idx(m + 9);
+        pair(q2, m + 2 < rows);  q2 = cur[j2]; j2 = idx(m + 10);
+        pair(q3, m + 3 < rows);  q3 = cur[j3]; j3 = idx(m + 11);
     }
     // this lane's share of the bead's bonded terms (partners staged by all
     // lanes of the bead: wait for the copies, then the warp barrier)
@@ -648,8 +648,10 @@ void launch_nl_step(const LaunchCtx &L, bool lambda) {
 
 // ===================================================== persistent kernel
 // Grid barrier over all blocks (one cooperative launch, all blocks resident):
-// arrive on a counter; the last arrival clears it and advances the
-// generation, the others wait for the generation to change.  Every wait is
+// arrive on a counter (an acquire-release add after the block barrier, so the
+// block's writes are visible to whoever sees the arrival); the last arrival
+// clears it and advances the generation with a release, the others poll the
+// generation with acquire loads until it changes.  Every wait is
 // bounded; a block that gives up records ERR_TIMEOUT in abort, and every
 // block returns at its next barrier once abort is set.
 struct RunSync {
@@ -668,23 +670,21 @@ __device__ bool grid_barrier(RunSync *rs) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned g0 = ld_acquire(&rs->gen);
-        __threadfence();
         int good = 1;
-        if (atomicAdd(&rs->count, 1u) == gridDim.x - 1) {
-            rs->count = 0;
-            __threadfence();
-            atomicAdd(&rs->gen, 1u);
+        unsigned old;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&rs->count) : "memory");
+        if (old == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(&rs->count), "r"(0u) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&rs->gen) : "memory");
         } else {
             for (long long it = 0; ld_acquire(&rs->gen) == g0; ++it) {
-                if (it > (1ll << 22) || *(volatile int *)&rs->abort) {
+                if (it > (1ll << 23) || *(volatile int *)&rs->abort) {
                     atomicOr(&rs->abort, ERR_TIMEOUT);
                     good = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
         ok = good && !*(volatile int *)&rs->abort;
     }
     __syncthreads();
