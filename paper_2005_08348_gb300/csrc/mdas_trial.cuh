@@ -47,7 +47,7 @@ struct TrialSmem {
     int it_beg[2 * MAXT * NL_G + 1];
     int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT], chg_k[2 * MAXT];
     uint4 chg_pos[2 * MAXT];
-    int nchg, last, accept;
+    int nchg, m, ta, tb, last, accept;
 };
 
 // fixed-order sum over a 128-thread group: a shuffle tree per warp, then the
@@ -70,6 +70,11 @@ __device__ inline double group_sum(double v, const Grp &g, double *sh) {
 // Every list holds all partners closer than rc, so the dE is the same sum as
 // over the 27 cells.  The last part to finish (a ticket) adds the part sums
 // in order, takes the Metropolis decision and applies it.
+//
+// Latency: one warp loads, for the beads of both lipids at once, their list
+// slots with the two lipid types, then their positions and list row counts;
+// it scans the row counts itself, so the entries start after one group
+// barrier.
 __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp &g, TrialSmem &sm) {
     const Params &P = *S.p;
     Counters &C = *S.c;
@@ -77,57 +82,56 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
     const unsigned long long T = C.trial;
     const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
     const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
-    const int ta = S.ltype[a], tb = S.ltype[b];
-    const bool null_trial = (a == b) || (ta == tb);
-    int m = 0;                                   // local indices whose bead type changes
-    if (!null_trial)
-        for (int k = 0; k < P.bpl; ++k) m |= (P.lbt[ta * 16 + k] != P.lbt[tb * 16 + k]) << k;
     const uint4 *cur = S.lpos + (size_t)par * P.n;
     if (t < 32) {
-        const int side = lane >= P.bpl, k = side ? lane - P.bpl : lane;
-        const bool ch = lane < 2 * P.bpl && ((m >> k) & 1);
+        // lane (side, k): local index k of lipid a (side 0) or b (side 1)
+        const int bpl = P.bpl;
+        const int side = lane >= bpl, k = side ? lane - bpl : lane;
+        const bool valid = lane < 2 * bpl;
+        const int id = (side ? b : a) * bpl + k;
+        const int kk = valid ? S.lk[id] : 0;
+        const int ta = S.ltype[a], tb = S.ltype[b];
+        const uint4 pk = cur[kk];
+        const int4 cn = *reinterpret_cast<const int4 *>(S.nl_n + (size_t)kk * NL_G);
+        const bool null_trial = (a == b) || (ta == tb);
+        const int bo = P.lbt[(side ? tb : ta) * 16 + k], bn = P.lbt[(side ? ta : tb) * 16 + k];
+        const bool ch = valid && !null_trial && bo != bn;
         const unsigned bal = __ballot_sync(0xffffffffu, ch);
-        if (ch) {
-            const int o = __popc(bal & ((1u << lane) - 1u));
-            const int id = (side ? b : a) * P.bpl + k;
-            const int kk = S.lk[id];
-            sm.chg_id[o] = id;
-            sm.chg_k[o] = kk;
-            sm.chg_pos[o] = cur[kk];
-            sm.chg_old[o] = P.lbt[(side ? tb : ta) * 16 + k];
-            sm.chg_new[o] = P.lbt[(side ? ta : tb) * 16 + k];
-        }
-        if (lane == 0) sm.nchg = __popc(bal);
-    }
-    g.sync();
-    const int nc = sm.nchg, nit = nc * NL_G;
-    if (t < 32) {
-        // items (changed bead, column): exclusive offsets of their row counts,
-        // NL_G items per lane, one warp scan
-        int v[NL_G], sum = 0;
-#pragma unroll
-        for (int q = 0; q < NL_G; ++q) {
-            const int it = NL_G * lane + q;
-            v[q] = it < nit ? S.nl_n[(size_t)sm.chg_k[it / NL_G] * NL_G + q] : 0;
-            sum += v[q];
-        }
-        int inc = sum;
+        // entries of the changed beads in lane order, columns in order within
+        // a bead: exclusive offsets by one warp scan
+        const int tot = ch ? cn.x + cn.y + cn.z + cn.w : 0;
+        int inc = tot;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int x = __shfl_up_sync(0xffffffffu, inc, d);
             if (lane >= d) inc += x;
         }
-        int run = inc - sum;
-#pragma unroll
-        for (int q = 0; q < NL_G; ++q) {
-            const int it = NL_G * lane + q;
-            if (it < nit) sm.it_beg[it] = run;
-            run += v[q];
+        if (ch) {
+            static_assert(NL_G == 4, "four list columns per bead");
+            const int o = __popc(bal & ((1u << lane) - 1u));
+            sm.chg_id[o] = id;
+            sm.chg_k[o] = kk;
+            sm.chg_pos[o] = pk;
+            sm.chg_old[o] = bo;
+            sm.chg_new[o] = bn;
+            const int run = inc - tot;
+            sm.it_beg[4 * o] = run;
+            sm.it_beg[4 * o + 1] = run + cn.x;
+            sm.it_beg[4 * o + 2] = run + cn.x + cn.y;
+            sm.it_beg[4 * o + 3] = run + cn.x + cn.y + cn.z;
         }
-        if (lane == 31) sm.it_beg[nit] = inc;
+        if (lane == 31) {
+            const int nc = __popc(bal);
+            sm.nchg = nc;
+            sm.it_beg[NL_G * nc] = inc;
+            sm.m = (int)(bal & ((1u << bpl) - 1u));   // local indices whose bead type changes
+            sm.ta = ta;
+            sm.tb = tb;
+        }
     }
     g.sync();
-    const int total = nc > 0 ? sm.it_beg[nit] : 0;
+    const int nc = sm.nchg, nit = nc * NL_G, m = sm.m, ta = sm.ta, tb = sm.tb;
+    const int total = sm.it_beg[nit];
     double acc = 0.0;
     for (int f = p + TRIAL_PARTS * t; f < total; f += TRIAL_PARTS * GRP) {
         int lo = 0, hi = nit - 1;                 // the item holding entry f
@@ -154,16 +158,19 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
     }
     const double part = group_sum(acc, g, sm.sh);
     if (t == 0) {
+        // the part sum, then the ticket: the release of the add publishes the
+        // sum, its acquire (in the last part) makes every other sum visible
         S.tdE[p] = part;
-        __threadfence();
-        sm.last = atomicAdd(&C.ticket, 1u) == TRIAL_PARTS - 1;
+        unsigned old;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&C.ticket) : "memory");
+        sm.last = old == TRIAL_PARTS - 1;
     }
     g.sync();
     if (!sm.last) return;
     if (t == 0) {
-        __threadfence();
         double dE = 0.0;
         for (int q = 0; q < TRIAL_PARTS; ++q) dE += __ldcg(&S.tdE[q]);
+        const bool null_trial = (a == b) || (ta == tb);
         TrialRec r;
         r.a = a; r.b = b; r.u = unit53(w.z, w.w); r.dE = 0.0; r.accepted = 0; r.index = T;
         r.null_trial = null_trial;
@@ -175,7 +182,7 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         if (r.accepted) { S.ltype[a] = tb; S.ltype[b] = ta; }
         S.log[T % LOG_CAP] = r;
         C.trials++;
-        C.force_evals++;
+        atomicAdd(&C.force_evals, 1ull);          // the step's close counts its own evaluation concurrently
         C.null_trials += r.null_trial;
         C.accepted += r.accepted;
         C.trial = T + 1;
@@ -183,14 +190,12 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         C.ticket = 0;
     }
     g.sync();
-    if (sm.accept && t < 2 * P.bpl) {            // the exchange: every bead of both lipids
-        const int side = t >= P.bpl, k = side ? t - P.bpl : t;
-        const int l = side ? b : a, lt = side ? ta : tb;
-        const int id = l * P.bpl + k;
-        const int bt = P.lbt[lt * 16 + k];
+    if (sm.accept && t < nc) {                    // the exchange: beads whose type changes
+        const int id = sm.chg_id[t], l = id / P.bpl, k = id - l * P.bpl;
+        const int bt = sm.chg_new[t];
         const uint32_t mm = meta_make(bt, bt, k, l + 1);
         S.pos[id].w = mm;
-        const_cast<uint4 *>(cur)[S.lk[id]].w = mm;
+        const_cast<uint4 *>(cur)[sm.chg_k[t]].w = mm;
     }
     g.sync();
 }

@@ -557,7 +557,7 @@ __device__ void nl_step_close(const SysDev &S, int lane) {
         C.ke_pending = 0;
         if (in_at) C.at_step = ctr; else C.step = ctr;
         C.md_steps++;
-        C.force_evals++;
+        atomicAdd(&C.force_evals, 1ull);         // a trial's last part counts its own concurrently
     }
     __syncwarp();
 }
