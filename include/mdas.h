@@ -238,6 +238,9 @@ mdas_status mdas_pair_kernel_time(mdas_system *s, double *total_ms, int64_t *lau
 typedef struct {
     int64_t md_steps, force_evals, trials, null_trials, accepted, moves, moves_accepted, kernel_launches;
     int64_t list_builds;               /* pair-list builds of the MD step */
+    int64_t item_redos;                /* step items of the persistent kernel that summed their forces a
+                                          second time: an exchange trial running beside the step was
+                                          accepted and changed bead types the item sees */
 } mdas_counters;
 mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
 

@@ -566,6 +566,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         P.lcapc = ld.lcapc;
         P.lcap = ld.lcap;
         P.lrow = ld.lrow;
+        P.mark_words = (n + NL_BEADS - 1) / NL_BEADS / 32 + 1;
         if (P.lcapc > 4096 || P.lcap > 4096) {
             delete s;
             return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: density too high for the pair list");
@@ -675,6 +676,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.lcell, 8ull * P.n_lcells}, {(void **)&H.lid, 4ull * n}, {(void **)&H.lk, 4ull * n},
         {(void **)&H.lpos, 32ull * n}, {(void **)&H.xref, 16ull * n}, {(void **)&H.nl_n, 4ull * NL_G * n},
         {(void **)&H.nl, 4ull * (size_t)(P.lcap / NL_G) * P.lrow}, {(void **)&H.bslot, 4ull * NL_PART * n},
+        {(void **)&H.tmark, 8ull * P.mark_words},
     };
     size_t total = 0;
     for (auto &it : items) total += (it.bytes + 255) / 256 * 256;
@@ -1179,6 +1181,7 @@ mdas_status mdas_get_counters(const mdas_system *cs, mdas_counters *out) {
     out->moves_accepted = (int64_t)c.moves_accepted;
     out->kernel_launches = (int64_t)s->kernel_launches;
     out->list_builds = (int64_t)c.nl_builds;
+    out->item_redos = (int64_t)c.redos;
     return MDAS_OK;
 }
 
@@ -1233,8 +1236,8 @@ size_t arena_estimate(const mdas_system_desc *d) {
                32 * MAX_DRAW_STEPS + 24 * n;
     const ListDims ld = list_dims(d);
     t += 12ull * ld.n_lcells + 4ull * ld.n_lcells * ld.lcapc + 4 * n + 4 * n + 32 * n + 16 * n + 4ull * NL_G * n +
-         4ull * (ld.lcap / NL_G) * ld.lrow + 4ull * NL_PART * n;
-    return t + 50 * 256;
+         4ull * (ld.lcap / NL_G) * ld.lrow + 4ull * NL_PART * n + 8ull * ((n + NL_BEADS - 1) / NL_BEADS / 32 + 1);
+    return t + 51 * 256;
 }
 
 }  // namespace

@@ -71,6 +71,7 @@ struct Params {
     int ln[3], n_lcells, lcapc;        // list-build cells per edge, cells, bead capacity of a cell
     unsigned long long lcwu[3];        // floor(2^32 / ln_d): list-build cell width in fixed-point units
     int lcap, lrow;                    // entries per bead (NL_G columns of lcap / NL_G rows), row stride
+    int mark_words;                    // 32-bit words of one step-item bitmap (one bit per NL_BEADS list slots)
     double rl, rl2;
     float rl2f;                        // rl^2 rounded up (build cull)
     float dmax2f;                      // squared displacement since the build that invalidates the list
@@ -110,15 +111,20 @@ struct Counters {
     int ke_fresh;                      // ke_total holds the kinetic energy of the current velocities
     int ke_pending;                    // the step kernel left kinetic energy in ke_slot
     double ke_total[2];
-    long long ke_slot[KE_SLOTS][2];    // fixed-point kinetic energy per slot and group (2^16 units per
+    long long ke_slot[2][KE_SLOTS][2]; // [position buffer the step read] fixed-point kinetic energy per slot and group (2^16 units per
                                        // kJ/mol for FP32 systems, 2^32 for FP64)
     int nl_stale;                      // the pair list must be rebuilt before its next use
     int nl_viol;                       // a bead moved farther than the skin allows (this step)
-    int nl_violp[2];                   // the same per step parity (persistent kernel)
+    int nl_violp[3];                   // the same per step s (index s % 3, persistent kernel)
     int nl_par;                        // lpos buffer holding the current positions
     unsigned int sticket;              // last-block ticket of the step kernel (separate launches)
     unsigned int nticket;              // last-block ticket of the list-build count kernel
     unsigned long long nl_builds;      // pair-list builds
+    // overlap of a step with the previous step's close and exchange trial
+    // (persistent kernel): monotonic counts, published with release stores
+    unsigned long long close_seq;      // step closes done (thermostat factor of the next step ready)
+    unsigned int mark_seq;             // trial parts done marking the step items their exchange can change
+    unsigned long long redos;          // step items that summed their forces again after an accepted exchange
 };
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
@@ -165,6 +171,7 @@ struct SysDev {
     int *nl_n;                         // [n * NL_G] entries in each column of each bead's list
     int *nl;                           // row r of column g of bead k at [r * lrow + k * NL_G + g]
     int *bslot;                        // [n * NL_PART] list indices of the bonded partners
+    unsigned *tmark;                   // [2 * mark_words] step items an exchange trial can change, per trial parity
     int n_bead_blocks;
 };
 

@@ -75,7 +75,14 @@ __device__ inline double group_sum(double v, const Grp &g, double *sh) {
 // slots with the two lipid types, then their positions and list row counts;
 // it scans the row counts itself, so the entries start after one group
 // barrier.
-__device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp &g, TrialSmem &sm) {
+//
+// With mark set (the trial runs beside the next MD step), the parts set, in
+// bitmap T & 1, the bit of every step item (NL_BEADS list slots) that holds a
+// changed bead or one of its list partners, then count themselves in
+// mark_seq; the decision is published by the trial counter only after the
+// exchange is applied.  Every trial clears the other bitmap for the next one
+// (its last readers finished before this trial started).
+__device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp &g, TrialSmem &sm, bool mark) {
     const Params &P = *S.p;
     Counters &C = *S.c;
     const int t = g.t, lane = t & 31;
@@ -83,6 +90,9 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
     const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_SWAP, 0u);
     const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
     const uint4 *cur = S.lpos + (size_t)par * P.n;
+    const int words = P.mark_words;
+    unsigned *const mk = S.tmark + (size_t)(T & 1) * words;
+    for (int x = p * GRP + t; x < words; x += TRIAL_PARTS * GRP) S.tmark[(size_t)((T + 1) & 1) * words + x] = 0;
     if (t < 32) {
         // lane (side, k): local index k of lipid a (side 0) or b (side 1)
         const int bpl = P.bpl;
@@ -108,6 +118,7 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         }
         if (ch) {
             static_assert(NL_G == 4, "four list columns per bead");
+            if (mark && p == 0) atomicOr(&mk[kk / NL_BEADS / 32], 1u << (kk / NL_BEADS % 32));
             const int o = __popc(bal & ((1u << lane) - 1u));
             sm.chg_id[o] = id;
             sm.chg_k[o] = kk;
@@ -141,6 +152,7 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         }
         const int ci = lo / NL_G, q = lo % NL_G, row = f - sm.it_beg[lo];
         const int kj = S.nl[(size_t)row * P.lrow + (size_t)sm.chg_k[ci] * NL_G + q];
+        if (mark) atomicOr(&mk[kj / NL_BEADS / 32], 1u << (kj / NL_BEADS % 32));
         const uint4 pi = sm.chg_pos[ci], pj = cur[kj];
         const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
         const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
@@ -156,7 +168,8 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         const int new_j = chj ? (int)P.lbt[(lj == a ? tb : ta) * 16 + kjl] : old_j;
         acc += pair_du(P, sm.chg_old[ci], old_j, sm.chg_new[ci], new_j, r2);
     }
-    const double part = group_sum(acc, g, sm.sh);
+    const double part = group_sum(acc, g, sm.sh);   // (its barriers order the group's marks)
+    if (t == 0 && mark) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&C.mark_seq) : "memory");
     if (t == 0) {
         // the part sum, then the ticket: the release of the add publishes the
         // sum, its acquire (in the last part) makes every other sum visible
@@ -185,7 +198,6 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         atomicAdd(&C.force_evals, 1ull);          // the step's close counts its own evaluation concurrently
         C.null_trials += r.null_trial;
         C.accepted += r.accepted;
-        C.trial = T + 1;
         C.pending = 0;
         C.ticket = 0;
     }
@@ -197,6 +209,9 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         S.pos[id].w = mm;
         const_cast<uint4 *>(cur)[sm.chg_k[t]].w = mm;
     }
+    g.sync();
+    // the decision, published after the exchange (its barrier orders the writes)
+    if (t == 0) asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(&C.trial), "l"(T + 1) : "memory");
     g.sync();
 }
 

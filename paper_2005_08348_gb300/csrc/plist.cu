@@ -65,7 +65,55 @@ struct StepSmem {
     uint4 spart[NL_BEADS][NL_PART];
     Real kered[2][NL_BEADS];
     int sviol;
+    int redo;
 };
+
+// What a step item of the persistent kernel waits for when the previous
+// step's close and exchange trial run at the same time as the step: the
+// thermostat factor (close_seq reaching close_target) and, after a trial,
+// that trial's marks (mark_seq reaching mark_target) and, for a marked item,
+// its decision (trial counter past T).
+struct PipeWait {
+    unsigned long long close_target, T;
+    unsigned mark_target;
+    int has_close, has_trial;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 of a step item: wait (bounded) for what the item needs from the
+// close and the trial running beside it; true when the trial exchanged bead
+// types this item sees, so its forces must be summed again.
+__device__ bool pipe_wait(const SysDev &S, const PipeWait &pw, int item) {
+    Counters &C = *S.c;
+    constexpr long long LIMIT = 1ll << 24;
+    bool ok = true, redo = false;
+    if (pw.has_close)
+        for (long long it = 0; ld_acquire64(&C.close_seq) < pw.close_target; ++it)
+            if (it > LIMIT) { ok = false; break; }
+    if (ok && pw.has_trial) {
+        for (long long it = 0; (int)(ld_acquire32(&C.mark_seq) - pw.mark_target) < 0; ++it)
+            if (it > LIMIT) { ok = false; break; }
+        const unsigned w = __ldcg(&S.tmark[(size_t)(pw.T & 1) * S.p->mark_words + item / 32]);
+        if (ok && ((w >> (item & 31)) & 1u)) {
+            for (long long it = 0; ld_acquire64(&C.trial) <= pw.T; ++it)
+                if (it > LIMIT) { ok = false; break; }
+            redo = ok && __ldcg(&S.log[pw.T % LOG_CAP].accepted) != 0;
+        }
+    }
+    if (!ok) atomicOr(&C.err, ERR_TIMEOUT);
+    return redo;
+}
 
 struct BuildSmem {
     int2 nb[27];
@@ -198,11 +246,17 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
     const int bpw = 32 / lb;                   // beads per warp and pass
     const int lane = t & 31, w = t >> 5;
     const int bw = lane / lb, gl = lane % lb, glane = bw * lb;
-    const unsigned gmask = (lb == 32 ? 0xffffffffu : (1u << lb) - 1u);
+    const unsigned gmask = (lb == 32 ? 0xffffffffu : (1u << lb) - 1u), lmask = (1u << gl) - 1u;
+    // loop invariants in registers (stores through the list pointer could
+    // otherwise alias them and force reloads from global memory)
+    int *const nl = S.nl;
+    const size_t lrow = (size_t)P.lrow;
+    const unsigned lcapg = (unsigned)(capg * NL_G);   // entries a bead's list holds
     for (int ib = 0; ib < ni; ib += (GRP / 32) * bpw) {
         const int r = ib + w * bpw + bw;
         const bool act = bw < bpw && r < ni;
         const int ki = i0 + (act ? r : 0);
+        int *const nlb = nl + (size_t)ki * NL_G;  // row 0 of the bead's list
         const uint4 pi = cur[ki];
         const float xi = (float)(int)(pi.x - ox) * q0, yi = (float)(int)(pi.y - oy) * q1,
                     zi = (float)(int)(pi.z - oz) * q2;
@@ -266,9 +320,10 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
             const int nq = (mw + lb - 1) / lb;
             for (int q = 0; q < nq; ++q) {
                 const int u = q * lb + gl;
-                const int f = u < mw ? wl[u] : 0;
+                const bool have = act && u < mw;
+                const int f = have ? wl[u] : 0;
                 bool in = false;
-                if (act && u < mw) {
+                if (have) {
                     const float4 e = sm.sf[f];
                     const float dx = xi - e.x, dy = yi - e.y, dz = zi - e.z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
@@ -279,9 +334,8 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
                 const unsigned bal = __ballot_sync(0xffffffffu, in);
                 const unsigned grp = (bal >> glane) & gmask;
                 if (in) {
-                    const int e = base + __popc(grp & ((1u << gl) - 1u));
-                    const int row = e / NL_G, col = e % NL_G;
-                    if (row < capg) S.nl[(size_t)row * P.lrow + (size_t)ki * NL_G + col] = sm.sk[f];
+                    const unsigned e = (unsigned)base + __popc(grp & lmask);
+                    if (e < lcapg) nlb[(size_t)(e / NL_G) * lrow + e % NL_G] = sm.sk[f];
                 }
                 base += __popc(grp);
             }
@@ -309,7 +363,7 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
 // moved farther than the list allows sets *viol.
 template <typename Real, bool LAM>
 __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const Grp &g, StepSmem<Real> &sm,
-                             bool load_tables = true) {
+                             bool load_tables = true, const PipeWait *pw = nullptr) {
     using V4 = typename Vec4<Real>::T;
     constexpr bool F32 = sizeof(Real) == 4;
     const Params &P = *S.p;
@@ -369,7 +423,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
     const Real lam = LAM ? (Real)C.lambda : (Real)0;
     const float qs0 = P.qsf[0], qs1 = P.qsf[1], qs2 = P.qsf[2];
-    const int tai = meta_ta(pi.w) * 16, tbi = meta_tb(pi.w) * 16;
+    int tai = meta_ta(pi.w) * 16, tbi = meta_tb(pi.w) * 16;
     Real ax = 0, ay = 0, az = 0;
 
     auto pair = [&](uint4 pj, bool ok) {
@@ -428,36 +482,54 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     // a whole group of pairs to arrive (entries past the end read slot 0)
     const int rows = cnt;
     auto idx = [&](int r) { return r < rows ? __ldg(lst + (size_t)r * rs) : 0; };
-    j0 = idx(4); j1 = idx(5); j2 = idx(6); j3 = idx(7);
-    for (int m = 0; m < rows; m += 4) {
-        pair(q0, true);          q0 = cur[j0]; j0 = idx(m + 8);
-        pair(q1, m + 1 < rows);  q1 = cur[j1]; j1 = idx(m + 9);
-        pair(q2, m + 2 < rows);  q2 = cur[j2]; j2 = idx(m + 10);
-        pair(q3, m + 3 < rows);  q3 = cur[j3]; j3 = idx(m + 11);
-    }
-    // this lane's share of the bead's bonded terms (partners staged by all
-    // lanes of the bead: wait for the copies, then the warp barrier)
-    cp_async_wait_all();
-    __syncwarp();
-    if (valid && meta_lip(pi.w) >= 0) {
-        Real fb[3] = {(Real)0, (Real)0, (Real)0};
-        const int kl = meta_k(pi.w);
-        bonded_force<Real>(P, kl, pi, [&](int li) { return sm.spart[il][P.pidx[kl][li]]; }, fb, gl, NL_G);
-        ax += fb[0]; ay += fb[1]; az += fb[2];
-    }
+    for (int pass = 0;; ++pass) {
+        j0 = idx(4); j1 = idx(5); j2 = idx(6); j3 = idx(7);
+        for (int m = 0; m < rows; m += 4) {
+            pair(q0, true);          q0 = cur[j0]; j0 = idx(m + 8);
+            pair(q1, m + 1 < rows);  q1 = cur[j1]; j1 = idx(m + 9);
+            pair(q2, m + 2 < rows);  q2 = cur[j2]; j2 = idx(m + 10);
+            pair(q3, m + 3 < rows);  q3 = cur[j3]; j3 = idx(m + 11);
+        }
+        // this lane's share of the bead's bonded terms (partners staged by all
+        // lanes of the bead: wait for the copies, then the warp barrier)
+        cp_async_wait_all();
+        __syncwarp();
+        if (valid && meta_lip(pi.w) >= 0) {
+            Real fb[3] = {(Real)0, (Real)0, (Real)0};
+            const int kl = meta_k(pi.w);
+            bonded_force<Real>(P, kl, pi, [&](int li) { return sm.spart[il][P.pidx[kl][li]]; }, fb, gl, NL_G);
+            ax += fb[0]; ay += fb[1]; az += fb[2];
+        }
 
-    // partial forces summed over the bead's NL_G lanes in a fixed tree
+        // partial forces summed over the bead's NL_G lanes in a fixed tree
 #pragma unroll
-    for (int o = 1; o < NL_G; o <<= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, o);
-        ay += __shfl_xor_sync(0xffffffffu, ay, o);
-        az += __shfl_xor_sync(0xffffffffu, az, o);
+        for (int o = 1; o < NL_G; o <<= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            az += __shfl_xor_sync(0xffffffffu, az, o);
+        }
+        // beside the previous step's close and trial: wait for the thermostat
+        // factor and the trial's marks; after an accepted exchange that this
+        // item sees (a changed bead or a changed partner), the same sums again
+        // with the new bead types, read past the L1 cache
+        if (pw == nullptr || pass > 0) break;
+        if (t == 0) sm.redo = pipe_wait(S, *pw, k0 / NL_BEADS);
+        g.sync();
+        if (!sm.redo) break;
+        __threadfence();
+        if (t == 0) atomicAdd(&C.redos, 1ull);
+        if (valid) pi = __ldcg(cur + k);
+        tai = meta_ta(pi.w) * 16;
+        tbi = meta_tb(pi.w) * 16;
+        ax = ay = az = (Real)0;
+        j0 = idx(0); j1 = idx(1); j2 = idx(2); j3 = idx(3);
+        q0 = __ldcg(cur + j0); q1 = __ldcg(cur + j1); q2 = __ldcg(cur + j2); q3 = __ldcg(cur + j3);
     }
     Real e0 = 0, e1 = 0;
     if (valid && gl == 0) {
         const Real f0 = ax, f1 = ay, f2 = az;
         const int grp = id < P.n_lipid_beads ? 0 : 1;
-        const Real a = F32 ? (Real)C.alpha_f[grp] : (Real)C.alpha[grp];
+        const Real a = F32 ? (Real)__ldcg(&C.alpha_f[grp]) : (Real)__ldcg(&C.alpha[grp]);
         const Real dtm = F32 ? (Real)P.dt_over_mf : (Real)P.dt_over_m;
         V4 v = sm.svel[il];
         v.x = fmr(a, v.x, f0 * dtm);
@@ -501,7 +573,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             // integer slot sums (order-free): FP32 items at 2^16 units per
             // kJ/mol through a 32-bit conversion (an item holds far less than
             // 2^15 kJ/mol), FP64 items at 2^32 units
-            long long *ks = C.ke_slot[(k0 / NL_BEADS) % KE_SLOTS];
+            long long *ks = C.ke_slot[par][(k0 / NL_BEADS) % KE_SLOTS];
             long long u0, u1;
             if (F32) {
                 const float lim = 32768.f;
@@ -526,14 +598,15 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
 // step (lanes 0 and 1, one coupling group each).  Real is the system's
 // precision (the factor sees the energy as Real).
 template <typename Real>
-__device__ void nl_step_close(const SysDev &S, int lane) {
+__device__ void nl_step_close(const SysDev &S, int lane, int par) {
     static_assert(KE_SLOTS == 64, "two slots per lane");
     const Params &P = *S.p;
     Counters &C = *S.c;
-    long long s0 = __ldcg(&C.ke_slot[lane][0]) + __ldcg(&C.ke_slot[lane + 32][0]);
-    long long s1 = __ldcg(&C.ke_slot[lane][1]) + __ldcg(&C.ke_slot[lane + 32][1]);
-    C.ke_slot[lane][0] = 0; C.ke_slot[lane][1] = 0;
-    C.ke_slot[lane + 32][0] = 0; C.ke_slot[lane + 32][1] = 0;
+    long long(*ks)[2] = C.ke_slot[par];
+    long long s0 = __ldcg(&ks[lane][0]) + __ldcg(&ks[lane + 32][0]);
+    long long s1 = __ldcg(&ks[lane][1]) + __ldcg(&ks[lane + 32][1]);
+    ks[lane][0] = 0; ks[lane][1] = 0;
+    ks[lane + 32][0] = 0; ks[lane + 32][1] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -560,6 +633,8 @@ __device__ void nl_step_close(const SysDev &S, int lane) {
         atomicAdd(&C.force_evals, 1ull);         // a trial's last part counts its own concurrently
     }
     __syncwarp();
+    // the factor is ready for a step running beside this close
+    if (lane == 0) asm volatile("red.release.gpu.global.add.u64 [%0], 1;" :: "l"(&C.close_seq) : "memory");
 }
 
 // ======================================================== separate kernels
@@ -623,7 +698,7 @@ __global__ void __launch_bounds__(GRP, 8) k_nl_step(const SysDev *__restrict__ s
     __syncthreads();
     if (!last || threadIdx.x >= 32) return;
     __threadfence();
-    nl_step_close<Real>(S, threadIdx.x);
+    nl_step_close<Real>(S, threadIdx.x, par);
     if (threadIdx.x == 0) {
         C.nl_stale = __ldcg(&C.nl_viol);
         C.nl_viol = 0;
@@ -704,7 +779,7 @@ struct RunArgs {
 // (which == 0) or a bead that moved too far in step s (which == 1).  The flags
 // do not change between the barrier before such a read and the next one.
 __device__ __forceinline__ int build_flag(const Counters &C, int which, int s) {
-    return which == 0 ? *(volatile const int *)&C.nl_stale : *(volatile const int *)&C.nl_violp[s & 1];
+    return which == 0 ? *(volatile const int *)&C.nl_stale : *(volatile const int *)&C.nl_violp[s % 3];
 }
 
 // Whether any system of the batch needs a build (the same answer in every block)
@@ -745,10 +820,20 @@ __device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &
 }
 
 // n_steps MD steps (with a trial after every swap_every-th) of every system,
-// in one cooperative launch of one 1024-thread block per SM.  Per step: the
-// step items, a barrier, the list builds that the step's displacements call
-// for, then per system (block q % gridDim) the step's close and the trial
-// items, and a barrier.  Step s reads position buffer (nl_par + s) & 1.
+// in one cooperative launch of one 1024-thread block per SM.  Step s reads
+// position buffer (nl_par + s) & 1.
+//
+// Overlapped mode, when every step item has a group of its own and
+// TRIAL_PARTS + 1 groups per system are left over (the last gids): the close
+// of step s - 1 (thermostat factor) and its exchange trial run beside the
+// items of step s, so a step costs one grid barrier.  An item waits for the
+// factor before it integrates; the trial marks every item that holds a bead
+// whose type the exchange changes or a list partner of one, and a marked item
+// waits for the decision and, if the exchange was accepted, sums its forces
+// again with the new types.  The arithmetic is that of the sequential order
+// (close and trial after the step's barrier, then a second barrier), which
+// runs otherwise.  Per step: items, barrier, list builds called for by the
+// step's displacements.
 template <typename Real, bool LAM>
 __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -761,6 +846,21 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
     BuildSmem &bsm = *reinterpret_cast<BuildSmem *>(gsm);
     TrialSmem &tsm = *reinterpret_cast<TrialSmem *>(gsm);
 
+    const bool pipe = a.n_nl + (TRIAL_PARTS + 1) * a.n_sys <= G;
+    const int dg = G - 1 - gid;                // the last gids: trial parts, then closes
+    const int ptrial = pipe && dg < TRIAL_PARTS * a.n_sys ? dg : -1;
+    const int pclose = pipe && ptrial < 0 && dg < (TRIAL_PARTS + 1) * a.n_sys ? dg - TRIAL_PARTS * a.n_sys : -1;
+    // an item's system before any close, trial or mark of this launch (those
+    // start after the first barrier)
+    unsigned long long close0 = 0, trial0 = 0;
+    unsigned mark0 = 0;
+    if (pipe && gid < a.n_nl) {
+        const Counters &C = *a.sys[a.nlmap[gid].x].c;
+        close0 = *(volatile const unsigned long long *)&C.close_seq;
+        trial0 = *(volatile const unsigned long long *)&C.trial;
+        mark0 = *(volatile const unsigned *)&C.mark_seq;
+    }
+
     // lists made stale outside the kernel (a new state, a rejected move)
     const bool stale0 = any_flag(a, 0, 0);
     if (stale0) {
@@ -771,18 +871,42 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
     }
     int tab_sys = -1;                          // system whose tables the group holds
     for (int s = 0; s < a.n_steps; ++s) {
-        for (int it = gid; it < a.n_nl; it += G) {
-            const int2 bm = a.nlmap[it];
-            const SysDev &S = a.sys[bm.x];
-            nl_step_item<Real, LAM>(S, bm.y, (S.c->nl_par + s) & 1, &S.c->nl_violp[s & 1], g, ssm,
-                                    bm.x != tab_sys);
-            tab_sys = bm.x;
+        const bool tprev = s > 0 && a.swap_every > 0 && s % a.swap_every == 0;   // a trial after step s - 1
+        if (pipe) {
+            if (gid < a.n_nl) {
+                const int2 bm = a.nlmap[gid];
+                const SysDev &S = a.sys[bm.x];
+                const int o = tprev ? s / a.swap_every - 1 : 0;   // that trial's ordinal in this launch
+                PipeWait pw;
+                pw.has_close = s > 0;
+                pw.close_target = close0 + (unsigned long long)s;
+                pw.has_trial = tprev;
+                pw.T = trial0 + (unsigned long long)o;
+                pw.mark_target = mark0 + (unsigned)(TRIAL_PARTS * (o + 1));
+                nl_step_item<Real, LAM>(S, bm.y, (S.c->nl_par + s) & 1, &S.c->nl_violp[s % 3], g, ssm,
+                                        bm.x != tab_sys, &pw);
+                tab_sys = bm.x;
+            } else if (ptrial >= 0 && tprev) {
+                const SysDev &S = a.sys[ptrial / TRIAL_PARTS];
+                trial_nl_part(S, ptrial % TRIAL_PARTS, (S.c->nl_par + s) & 1, g, tsm, true);
+            } else if (pclose >= 0 && s > 0 && g.t < 32) {
+                const SysDev &S = a.sys[pclose];
+                nl_step_close<Real>(S, g.t, (S.c->nl_par + s - 1) & 1);
+            }
+        } else {
+            for (int it = gid; it < a.n_nl; it += G) {
+                const int2 bm = a.nlmap[it];
+                const SysDev &S = a.sys[bm.x];
+                nl_step_item<Real, LAM>(S, bm.y, (S.c->nl_par + s) & 1, &S.c->nl_violp[s % 3], g, ssm,
+                                        bm.x != tab_sys);
+                tab_sys = bm.x;
+            }
         }
-        // flags last read before the previous barrier: clear them for reuse
+        // the flag of step s + 1 (last read at step s - 2, before the previous barrier)
         if (threadIdx.x == 0)
             for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
                 Counters &C = *a.sys[q].c;
-                C.nl_violp[(s + 1) & 1] = 0;
+                C.nl_violp[(s + 1) % 3] = 0;
                 if (s == 0) C.nl_stale = 0;
             }
         if (!grid_barrier(a.rs)) return;
@@ -790,21 +914,38 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
         if (rebuild) {
             if (!run_build(a, 1, s, s + 1, g, gid, G, bsm)) return;
             tab_sys = -1;                      // the build used the same shared memory
+            if (threadIdx.x == 0)
+                for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x)
+                    if (a.sys[q].c->nl_violp[s % 3]) a.sys[q].c->nl_builds++;
         }
-        // the close of system q on block gridDim - 1 - q % gridDim (the trial
-        // parts start on the first blocks, so both overlap)
-        if (threadIdx.x < 32)
-            for (int q = gridDim.x - 1 - blockIdx.x; q < a.n_sys; q += gridDim.x) {
-                const SysDev &S = a.sys[q];
-                nl_step_close<Real>(S, threadIdx.x);
-                if (threadIdx.x == 0 && rebuild && S.c->nl_violp[s & 1]) S.c->nl_builds++;
+        if (!pipe) {
+            // the close of system q on block gridDim - 1 - q % gridDim (the
+            // trial parts start on the first blocks, so both overlap)
+            if (threadIdx.x < 32)
+                for (int q = gridDim.x - 1 - blockIdx.x; q < a.n_sys; q += gridDim.x) {
+                    const SysDev &S = a.sys[q];
+                    nl_step_close<Real>(S, threadIdx.x, (S.c->nl_par + s) & 1);
+                }
+            if (a.swap_every > 0 && (s + 1) % a.swap_every == 0) {
+                for (int it = gid; it < TRIAL_PARTS * a.n_sys; it += G) {
+                    const SysDev &S = a.sys[it / TRIAL_PARTS];
+                    trial_nl_part(S, it % TRIAL_PARTS, (S.c->nl_par + s + 1) & 1, g, tsm, false);
+                    tab_sys = -1;              // the trial used the same shared memory
+                }
             }
-        if (a.swap_every > 0 && (s + 1) % a.swap_every == 0) {
-            for (int it = gid; it < TRIAL_PARTS * a.n_sys; it += G) {
-                const SysDev &S = a.sys[it / TRIAL_PARTS];
-                trial_nl_part(S, it % TRIAL_PARTS, (S.c->nl_par + s + 1) & 1, g, tsm);
-                tab_sys = -1;                  // the trial used the same shared memory
-            }
+            if (!grid_barrier(a.rs)) return;
+        }
+    }
+    if (pipe && a.n_steps > 0) {
+        // the last step's close and trial, then a barrier
+        const int s = a.n_steps;
+        if (pclose >= 0 && g.t < 32) {
+            const SysDev &S = a.sys[pclose];
+            nl_step_close<Real>(S, g.t, (S.c->nl_par + s - 1) & 1);
+        }
+        if (ptrial >= 0 && a.swap_every > 0 && s % a.swap_every == 0) {
+            const SysDev &S = a.sys[ptrial / TRIAL_PARTS];
+            trial_nl_part(S, ptrial % TRIAL_PARTS, (S.c->nl_par + s) & 1, g, tsm, false);
         }
         if (!grid_barrier(a.rs)) return;
     }
@@ -812,7 +953,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
         for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
             Counters &C = *a.sys[q].c;
             C.nl_par = (C.nl_par + a.n_steps) & 1;
-            C.nl_violp[0] = C.nl_violp[1] = 0;
+            C.nl_violp[0] = C.nl_violp[1] = C.nl_violp[2] = 0;
             if (a.n_steps == 0) C.nl_stale = 0;
         }
 }

@@ -226,7 +226,7 @@ __device__ void set_lipid_type(const SysDev &S, const Params &P, int l, int lt) 
 __global__ void __launch_bounds__(GRP) k_trial_nl(const SysDev *__restrict__ sys) {
     __shared__ TrialSmem sm;
     const SysDev &S = sys[blockIdx.y];
-    trial_nl_part(S, blockIdx.x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm);
+    trial_nl_part(S, blockIdx.x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm, false);
 }
 
 void launch_trial_nl(const LaunchCtx &L) {
@@ -431,7 +431,7 @@ __global__ void k_restore(const SysDev *__restrict__ sys, const int2 *__restrict
         S.c->ke_pending = 0;
         S.c->nl_stale = 1;
     }
-    if (i < 2 * KE_SLOTS) S.c->ke_slot[i >> 1][i & 1] = 0;
+    if (i < 4 * KE_SLOTS) (&S.c->ke_slot[0][0][0])[i] = 0;
     S.pos[i] = S.pos_snap[i];
     reinterpret_cast<V4 *>(S.vel)[i] = reinterpret_cast<const V4 *>(S.vel_snap)[i];
 }

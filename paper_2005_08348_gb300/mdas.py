@@ -74,7 +74,8 @@ class StateView(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("md_steps", "force_evals", "trials", "null_trials", "accepted",
-                                         "moves", "moves_accepted", "kernel_launches", "list_builds")]
+                                         "moves", "moves_accepted", "kernel_launches", "list_builds",
+                                         "item_redos")]
 
 
 TRIAL_DTYPE = np.dtype([("a", np.int32), ("b", np.int32), ("null", np.int32), ("accepted", np.int32),

@@ -122,3 +122,27 @@ def test_tune_list_skin_times_every_candidate():
     assert s.counters()["md_steps"] == 10
     with pytest.raises(mdas.MdasError):
         mdas.tune_list_skin(ms[:1], skins=(0.3, 0.0), md_steps=10)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_trials_beside_the_next_step_match_separate_launches(prec):
+    """In the persistent kernel each exchange trial runs beside the next MD
+    step; the items it can change wait for its decision and, after an accepted
+    exchange, sum their forces again.  The result is the bits of trials run
+    strictly after their step (separate launches)."""
+    m = synth.mcmd_small()
+    runs = []
+    for persistent in (True, False):
+        s = mdas.System(m, precision=prec, temperature=450.0)
+        s.set_persistent(persistent)
+        s.md_steps(150, swap_every=1)
+        s.md_steps(7, swap_every=2)
+        runs.append((s.get_state(), s.counters()))
+    (a, ca), (b, cb) = runs
+    assert ca["accepted"] >= 3 and ca["item_redos"] > 0, ca
+    assert cb["item_redos"] == 0
+    assert np.array_equal(a["pos_u"], b["pos_u"])
+    assert np.array_equal(a["vel"], b["vel"])
+    assert np.array_equal(a["ltype"], b["ltype"])
+    for key in ("md_steps", "force_evals", "trials", "null_trials", "accepted", "list_builds"):
+        assert ca[key] == cb[key], key
