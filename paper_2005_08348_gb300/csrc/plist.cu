@@ -79,15 +79,18 @@ struct PipeWait {
     int has_close, has_trial;
 };
 
-__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+// Relaxed polls (an acquire on every poll would invalidate the L1 cache of
+// the SM, which the other items there are using); one acquire fence once
+// the value is seen.
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ unsigned ld_acquire32(const unsigned *p) {
+__device__ __forceinline__ unsigned ld_relaxed32(const unsigned *p) {
     unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -99,15 +102,18 @@ __device__ bool pipe_wait(const SysDev &S, const PipeWait &pw, int item) {
     constexpr long long LIMIT = 1ll << 24;
     bool ok = true, redo = false;
     if (pw.has_close)
-        for (long long it = 0; ld_acquire64(&C.close_seq) < pw.close_target; ++it)
+        for (long long it = 0; ld_relaxed64(&C.close_seq) < pw.close_target; ++it)
             if (it > LIMIT) { ok = false; break; }
+    if (ok && pw.has_trial)
+        for (long long it = 0; (int)(ld_relaxed32(&C.mark_seq) - pw.mark_target) < 0; ++it)
+            if (it > LIMIT) { ok = false; break; }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     if (ok && pw.has_trial) {
-        for (long long it = 0; (int)(ld_acquire32(&C.mark_seq) - pw.mark_target) < 0; ++it)
-            if (it > LIMIT) { ok = false; break; }
         const unsigned w = __ldcg(&S.tmark[(size_t)(pw.T & 1) * S.p->mark_words + item / 32]);
-        if (ok && ((w >> (item & 31)) & 1u)) {
-            for (long long it = 0; ld_acquire64(&C.trial) <= pw.T; ++it)
+        if ((w >> (item & 31)) & 1u) {
+            for (long long it = 0; ld_relaxed64(&C.trial) <= pw.T; ++it)
                 if (it > LIMIT) { ok = false; break; }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             redo = ok && __ldcg(&S.log[pw.T % LOG_CAP].accepted) != 0;
         }
     }
@@ -120,7 +126,8 @@ struct BuildSmem {
     int noff[28];
     int last;
     int ws[GRP / 32];
-    int wn[GRP / 32];                         // candidates near each warp's beads
+    float4 sb[GRP / 32][8];                   // per warp: its beads' frame coordinates, (lipid + 1) << 4 | k in w
+    unsigned sbe[GRP / 32][8];                // and their excluded local indices
     float4 sf[NLB_STAGE];                     // frame coordinates, meta word in w
     int sk[NLB_STAGE];                        // list index
     uint16_t wl[GRP / 32][NLB_STAGE];         // per warp: staged index of those candidates
@@ -206,8 +213,10 @@ __device__ void nl_place_item(const SysDev &S, int c0, int par, const Grp &g, Bu
 // staged in a frame centred on the cell (exact integer offsets as floats;
 // with 3 or more cells per edge every partner within rl of a bead of the cell
 // has an offset below half a box, so the frame difference is the minimum
-// image).  Thread (bead, g) tests every NL_G-th candidate; the bead's NL_G
-// lanes agree through a ballot on where each partner goes.
+// image).  Each warp keeps the candidates near the box around its beads;
+// then lane u tests candidate u of each chunk of 32 against every bead of the
+// warp, and a ballot per bead gives the partners their list entries in
+// candidate order.
 __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, BuildSmem &sm) {
     const Params &P = *S.p;
     Counters &C = *S.c;
@@ -239,33 +248,33 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
     const float rl2 = P.rl2f;
     const int capg = P.lcap / NL_G;
     const int i0 = sm.nb[13].x, ni = sm.nb[13].y;
-    // lanes per bead: as many (up to 8) as leave every bead of the cell a
-    // group of lanes within one warp, in as few passes as possible
-    int lb = 8;
-    while (lb > 1 && (GRP / 32) * (32 / lb) < ni) --lb;
-    const int bpw = 32 / lb;                   // beads per warp and pass
+    // beads per warp and pass (at most 8): warp w takes beads w * bpw .. of
+    // a pass, lane b holds bead b (its frame position and exclusions also in
+    // shared memory, where every lane reads them)
+    const int bpw = max(1, min(8, (ni + GRP / 32 - 1) / (GRP / 32)));
     const int lane = t & 31, w = t >> 5;
-    const int bw = lane / lb, gl = lane % lb, glane = bw * lb;
-    const unsigned gmask = (lb == 32 ? 0xffffffffu : (1u << lb) - 1u), lmask = (1u << gl) - 1u;
+    const unsigned ltmask = (1u << lane) - 1u;
     // loop invariants in registers (stores through the list pointer could
     // otherwise alias them and force reloads from global memory)
     int *const nl = S.nl;
     const size_t lrow = (size_t)P.lrow;
     const unsigned lcapg = (unsigned)(capg * NL_G);   // entries a bead's list holds
+    const int s13 = sm.noff[13];
     for (int ib = 0; ib < ni; ib += (GRP / 32) * bpw) {
-        const int r = ib + w * bpw + bw;
-        const bool act = bw < bpw && r < ni;
-        const int ki = i0 + (act ? r : 0);
-        int *const nlb = nl + (size_t)ki * NL_G;  // row 0 of the bead's list
+        const int rw = ib + w * bpw;               // the warp's first bead of this pass
+        const int nbw = max(0, min(bpw, ni - rw));
+        const bool act = lane < nbw;
+        const int ki = i0 + (act ? rw + lane : 0);
         const uint4 pi = cur[ki];
         const float xi = (float)(int)(pi.x - ox) * q0, yi = (float)(int)(pi.y - oy) * q1,
                     zi = (float)(int)(pi.z - oz) * q2;
         const uint32_t lip = pi.w >> 12;
         const uint32_t em = lip ? P.excl[meta_k(pi.w)] : 0u;
-        const int self = sm.noff[13] + r;      // the bead's own candidate index
-        // partner e goes to column e % NL_G, row e / NL_G (the columns differ
-        // by one entry at most); the bead's lanes agree on e through a ballot
-        int base = 0;
+        if (act) {
+            sm.sb[w][lane] = make_float4(xi, yi, zi, __uint_as_float(pi.w >> 8));   // (lipid + 1) << 4 | k
+            sm.sbe[w][lane] = em;
+        }
+        int base = 0;                              // lane b: entries of bead b so far
         for (int f0 = 0; f0 < M; f0 += NLB_STAGE) {
             const int mc = min(NLB_STAGE, M - f0);
             g.sync();
@@ -284,6 +293,8 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
             }
             g.sync();
             // the candidates within rl of the box around this warp's beads
+            // (their count mw is the same in every lane)
+            int mw = 0;
             {
                 float lo0 = act ? xi : 3e30f, lo1 = act ? yi : 3e30f, lo2 = act ? zi : 3e30f;
                 float hi0 = act ? xi : -3e30f, hi1 = act ? yi : -3e30f, hi2 = act ? zi : -3e30f;
@@ -296,7 +307,6 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
                     hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
                     hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
                 }
-                int nw = 0;
                 for (int f1 = 0; f1 < mc; f1 += 32) {
                     const int f = f1 + lane;
                     bool near = false;
@@ -308,47 +318,53 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
                         near = gx * gx + gy * gy + gz * gz < rl2;
                     }
                     const unsigned bn = __ballot_sync(0xffffffffu, near);
-                    if (near) sm.wl[w][nw + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)f;
-                    nw += __popc(bn);
+                    if (near) sm.wl[w][mw + __popc(bn & ltmask)] = (uint16_t)f;
+                    mw += __popc(bn);
                 }
-                __syncwarp();
-                sm.wn[w] = nw;
                 __syncwarp();
             }
-            const int mw = sm.wn[w];
+            // lane u of a chunk tests compacted candidate c + u against every
+            // bead of the warp; a bead's partners go to its list in candidate
+            // order, entry e at column e % NL_G, row e / NL_G
             const uint16_t *wl = sm.wl[w];
-            const int nq = (mw + lb - 1) / lb;
-            for (int q = 0; q < nq; ++q) {
-                const int u = q * lb + gl;
-                const bool have = act && u < mw;
+            const int fself = s13 + rw - f0;       // staged index of the warp's bead 0
+            for (int c0 = 0; c0 < mw; c0 += 32) {
+                const int u = c0 + lane;
+                const bool have = u < mw;
                 const int f = have ? wl[u] : 0;
-                bool in = false;
-                if (have) {
-                    const float4 e = sm.sf[f];
-                    const float dx = xi - e.x, dy = yi - e.y, dz = zi - e.z;
+                const float4 e = sm.sf[f];
+                const uint32_t jkey = __float_as_uint(e.w) >> 8;   // (lipid + 1) << 4 | k
+                const uint32_t jk = jkey & 15u;
+                const int skf = sm.sk[f];
+                for (int b = 0; b < nbw; ++b) {
+                    const float4 bi = sm.sb[w][b];
+                    const float dx = bi.x - e.x, dy = bi.y - e.y, dz = bi.z - e.z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
-                    const uint32_t mj = __float_as_uint(e.w);
-                    const bool excl = lip != 0 && (mj >> 12) == lip && ((em >> meta_k(mj)) & 1u);
-                    in = r2 < rl2 && !excl && f0 + f != self;
+                    // excluded: the same lipid ((lipid + 1) equal) and a bonded local index
+                    const bool excl = (__float_as_uint(bi.w) ^ jkey) < 16u && ((sm.sbe[w][b] >> jk) & 1u);
+                    const bool in = have && r2 < rl2 && !excl && f != fself + b;
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    if (bal) {
+                        const int bb = __shfl_sync(0xffffffffu, base, b);
+                        if (in) {
+                            const unsigned ei = (unsigned)bb + __popc(bal & ltmask);
+                            if (ei < lcapg)
+                                nl[(size_t)(i0 + rw + b) * NL_G + (size_t)(ei / NL_G) * lrow + ei % NL_G] = skf;
+                        }
+                        if (lane == b) base = bb + __popc(bal);
+                    }
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, in);
-                const unsigned grp = (bal >> glane) & gmask;
-                if (in) {
-                    const unsigned e = (unsigned)base + __popc(grp & lmask);
-                    if (e < lcapg) nlb[(size_t)(e / NL_G) * lrow + e % NL_G] = sm.sk[f];
-                }
-                base += __popc(grp);
             }
         }
         if (act) {
-            for (int col = gl; col < NL_G; col += lb) {
+            for (int col = 0; col < NL_G; ++col) {
                 const int cnt = base > col ? (base - col + NL_G - 1) / NL_G : 0;
                 S.nl_n[(size_t)ki * NL_G + col] = min(cnt, capg);
             }
-            if (gl == 0 && base > P.lcap) atomicOr(&C.err, ERR_CELL_OVERFLOW);
+            if (base > P.lcap) atomicOr(&C.err, ERR_CELL_OVERFLOW);
             if (lip != 0) {
                 const int kl = meta_k(pi.w);
-                for (int p = gl; p < P.npart[kl]; p += lb)
+                for (int p = 0; p < P.npart[kl]; ++p)
                     S.bslot[(size_t)ki * NL_PART + p] = S.lk[(int)(lip - 1) * P.bpl + P.part[kl][p]];
             }
         }
@@ -752,13 +768,14 @@ __device__ bool grid_barrier(RunSync *rs) {
             asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(&rs->count), "r"(0u) : "memory");
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&rs->gen) : "memory");
         } else {
-            for (long long it = 0; ld_acquire(&rs->gen) == g0; ++it) {
+            for (long long it = 0; ld_relaxed32(&rs->gen) == g0; ++it) {
                 if (it > (1ll << 23) || *(volatile int *)&rs->abort) {
                     atomicOr(&rs->abort, ERR_TIMEOUT);
                     good = 0;
                     break;
                 }
             }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
         ok = good && !*(volatile int *)&rs->abort;
     }
