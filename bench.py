@@ -267,14 +267,16 @@ def run_gpu(args):
     achieved = pairs_per_eval * PAIR_FLOPS / pair_avg_s / 1e12 if pair_launches else None
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
-    if os.path.exists(tfile):
+    if os.path.exists(tfile) and not args.separate_launches:
         # DRAM bytes of one step-kernel launch from an ncu capture of this
         # workload; void once the kernel source has changed since the capture
         import hashlib
         tj = json.load(open(tfile))
-        src = os.path.join(ROOT, "paper_2005_08348_gb300", "csrc", tj.get("source", "plist.cu"))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest() if os.path.exists(src) else None
-        if h is not None and tj.get("beads") == n and tj.get("source_sha256") == h:
+        h = hashlib.sha256()
+        for name in tj.get("sources", []):
+            src = os.path.join(ROOT, "paper_2005_08348_gb300", "csrc", name)
+            h.update(open(src, "rb").read() if os.path.exists(src) else b"missing")
+        if tj.get("sources") and tj.get("beads") == n and tj.get("sources_sha256") == h.hexdigest():
             traffic = tj.get("bytes_per_launch")
     out = {
         "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s", "n_gpus": ws,
@@ -288,7 +290,9 @@ def run_gpu(args):
         "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "e2e": {"value": e2e_value, "unit": "pair-interactions/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-        "roofline": {"kernel": "k_md_run<float> (persistent: MD steps, list rebuilds, exchange trials)",
+        "roofline": {"kernel": "k_nl_step<float> + list build + trial kernels (separate launches)"
+                     if args.separate_launches else
+                     "k_md_run<float> (persistent: MD steps, list rebuilds, exchange trials)",
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
                      "traffic": traffic, "us_per_md_step": pair_avg_s * 1e6, "md_steps_timed": pair_launches,
