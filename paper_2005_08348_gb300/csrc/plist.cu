@@ -739,44 +739,37 @@ void launch_nl_step(const LaunchCtx &L, bool lambda) {
 
 // ===================================================== persistent kernel
 // Grid barrier over all blocks (one cooperative launch, all blocks resident):
-// arrive on a counter (an acquire-release add after the block barrier, so the
-// block's writes are visible to whoever sees the arrival); the last arrival
-// clears it and advances the generation with a release, the others poll the
-// generation with acquire loads until it changes.  Every wait is
-// bounded; a block that gives up records ERR_TIMEOUT in abort, and every
-// block returns at its next barrier once abort is set.
+// a monotonic arrival counter.  After the block barrier, thread 0 adds 1 with
+// a release (the block's writes are visible to whoever sees the arrival) and
+// polls, with relaxed loads, until the count reaches base + (barriers passed)
+// x gridDim, then fences once (acquire).  base is the count when the launch
+// began (written by block 0 after the previous launch's last barrier).  Every
+// wait is bounded; a block that gives up records ERR_TIMEOUT in abort, and
+// every block returns at its next barrier once abort is set.
 struct RunSync {
-    unsigned int count, gen;
+    unsigned int count, base;
     int abort;
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
+struct BarState {
+    unsigned base, n;                          // thread 0 of each block: the launch's base, barriers passed
+};
 
-__device__ bool grid_barrier(RunSync *rs) {
+__device__ bool grid_barrier(RunSync *rs, BarState &bs) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned g0 = ld_acquire(&rs->gen);
+        const unsigned target = bs.base + (++bs.n) * gridDim.x;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&rs->count) : "memory");
         int good = 1;
-        unsigned old;
-        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&rs->count) : "memory");
-        if (old == gridDim.x - 1) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(&rs->count), "r"(0u) : "memory");
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&rs->gen) : "memory");
-        } else {
-            for (long long it = 0; ld_relaxed32(&rs->gen) == g0; ++it) {
-                if (it > (1ll << 23) || *(volatile int *)&rs->abort) {
-                    atomicOr(&rs->abort, ERR_TIMEOUT);
-                    good = 0;
-                    break;
-                }
+        for (long long it = 0; (int)(ld_relaxed32(&rs->count) - target) < 0; ++it) {
+            if (it > (1ll << 23) || *(volatile int *)&rs->abort) {
+                atomicOr(&rs->abort, ERR_TIMEOUT);
+                good = 0;
+                break;
             }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         ok = good && !*(volatile int *)&rs->abort;
     }
     __syncthreads();
@@ -815,25 +808,26 @@ __device__ bool any_flag(const RunArgs &a, int which, int s) {
 
 // List build of every system whose flag is set; buffer (nl_par + b) & 1 holds
 // the current positions.  Three barriers.
-__device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &g, int gid, int G, BuildSmem &sm) {
+__device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &g, int gid, int G, BuildSmem &sm,
+                          BarState &bs) {
     for (int it = gid; it < a.n_bead; it += G) {
         const int2 bm = a.beadmap[it];
         const SysDev &S = a.sys[bm.x];
         if (build_flag(*S.c, which, s)) nl_count_item(S, bm.y, g);
     }
-    if (!grid_barrier(a.rs)) return false;
+    if (!grid_barrier(a.rs, bs)) return false;
     for (int it = gid; it < a.n_lsort; it += G) {
         const int2 bm = a.lsortmap[it];
         const SysDev &S = a.sys[bm.x];
         if (build_flag(*S.c, which, s)) nl_place_item(S, bm.y, (S.c->nl_par + b) & 1, g, sm);
     }
-    if (!grid_barrier(a.rs)) return false;
+    if (!grid_barrier(a.rs, bs)) return false;
     for (int it = gid; it < a.n_lcell; it += G) {
         const int2 bm = a.lcellmap[it];
         const SysDev &S = a.sys[bm.x];
         if (build_flag(*S.c, which, s)) nl_build_item(S, bm.y, (S.c->nl_par + b) & 1, g, sm);
     }
-    return grid_barrier(a.rs);
+    return grid_barrier(a.rs, bs);
 }
 
 // n_steps MD steps (with a trial after every swap_every-th) of every system,
@@ -878,10 +872,12 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
         mark0 = *(volatile const unsigned *)&C.mark_seq;
     }
 
+    BarState bs{0u, 0u};
+    if (threadIdx.x == 0) bs.base = *(volatile const unsigned *)&a.rs->base;
     // lists made stale outside the kernel (a new state, a rejected move)
     const bool stale0 = any_flag(a, 0, 0);
     if (stale0) {
-        if (!run_build(a, 0, 0, 0, g, gid, G, bsm)) return;
+        if (!run_build(a, 0, 0, 0, g, gid, G, bsm, bs)) return;
         if (threadIdx.x == 0)
             for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x)
                 if (a.sys[q].c->nl_stale) a.sys[q].c->nl_builds++;
@@ -926,10 +922,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                 C.nl_violp[(s + 1) % 3] = 0;
                 if (s == 0) C.nl_stale = 0;
             }
-        if (!grid_barrier(a.rs)) return;
+        if (!grid_barrier(a.rs, bs)) return;
         const bool rebuild = any_flag(a, 1, s);
         if (rebuild) {
-            if (!run_build(a, 1, s, s + 1, g, gid, G, bsm)) return;
+            if (!run_build(a, 1, s, s + 1, g, gid, G, bsm, bs)) return;
             tab_sys = -1;                      // the build used the same shared memory
             if (threadIdx.x == 0)
                 for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x)
@@ -950,7 +946,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                     tab_sys = -1;              // the trial used the same shared memory
                 }
             }
-            if (!grid_barrier(a.rs)) return;
+            if (!grid_barrier(a.rs, bs)) return;
         }
     }
     if (pipe && a.n_steps > 0) {
@@ -964,8 +960,10 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
             const SysDev &S = a.sys[ptrial / TRIAL_PARTS];
             trial_nl_part(S, ptrial % TRIAL_PARTS, (S.c->nl_par + s) & 1, g, tsm, false);
         }
-        if (!grid_barrier(a.rs)) return;
+        if (!grid_barrier(a.rs, bs)) return;
     }
+    // every block is past the last barrier: the next launch counts from here
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.rs->base = bs.base + bs.n * gridDim.x;
     if (threadIdx.x == 0)
         for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
             Counters &C = *a.sys[q].c;
