@@ -124,6 +124,7 @@ struct Counters {
     // (persistent kernel): monotonic counts, published with release stores
     unsigned long long close_seq;      // step closes done (thermostat factor of the next step ready)
     unsigned int mark_seq;             // trial parts done marking the step items their exchange can change
+    unsigned long long alpha_pack[2];  // (close_seq << 32) | float bits of alpha_f, one word per group (FP32)
     unsigned long long redos;          // step items that summed their forces again after an accepted exchange
 };
 

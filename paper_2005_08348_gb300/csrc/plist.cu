@@ -94,21 +94,38 @@ __device__ __forceinline__ unsigned ld_relaxed32(const unsigned *p) {
     return v;
 }
 
-// Thread 0 of a step item: wait (bounded) for what the item needs from the
-// close and the trial running beside it; true when the trial exchanged bead
-// types this item sees, so its forces must be summed again.
+// The thermostat factor of coupling group grp for a step beside the close.
+// FP32: the factor and its close sequence share one 64-bit word (one relaxed
+// load gives both, no fence); FP64: the sequence, a fence, then the factor.
+template <typename Real>
+__device__ Real alpha_beside_close(Counters &C, int grp, const PipeWait &pw) {
+    constexpr long long LIMIT = 1ll << 24;
+    if (sizeof(Real) == 4) {
+        const unsigned want = (unsigned)pw.close_target;
+        unsigned long long w = ld_relaxed64(&C.alpha_pack[grp]);
+        for (long long it = 0; (unsigned)(w >> 32) != want; ++it) {
+            if (it > LIMIT) { atomicOr(&C.err, ERR_TIMEOUT); break; }
+            w = ld_relaxed64(&C.alpha_pack[grp]);
+        }
+        return (Real)__uint_as_float((unsigned)w);
+    }
+    for (long long it = 0; ld_relaxed64(&C.close_seq) < pw.close_target; ++it)
+        if (it > LIMIT) { atomicOr(&C.err, ERR_TIMEOUT); break; }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return (Real)__ldcg(&C.alpha[grp]);
+}
+
+// Thread 0 of a step item after a trial: wait (bounded) for the trial's
+// marks; true when the trial exchanged bead types this item sees, so its
+// forces must be summed again.
 __device__ bool pipe_wait(const SysDev &S, const PipeWait &pw, int item) {
     Counters &C = *S.c;
     constexpr long long LIMIT = 1ll << 24;
     bool ok = true, redo = false;
-    if (pw.has_close)
-        for (long long it = 0; ld_relaxed64(&C.close_seq) < pw.close_target; ++it)
-            if (it > LIMIT) { ok = false; break; }
-    if (ok && pw.has_trial)
-        for (long long it = 0; (int)(ld_relaxed32(&C.mark_seq) - pw.mark_target) < 0; ++it)
-            if (it > LIMIT) { ok = false; break; }
+    for (long long it = 0; (int)(ld_relaxed32(&C.mark_seq) - pw.mark_target) < 0; ++it)
+        if (it > LIMIT) { ok = false; break; }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    if (ok && pw.has_trial) {
+    if (ok) {
         const unsigned w = __ldcg(&S.tmark[(size_t)(pw.T & 1) * S.p->mark_words + item / 32]);
         if ((w >> (item & 31)) & 1u) {
             for (long long it = 0; ld_relaxed64(&C.trial) <= pw.T; ++it)
@@ -528,7 +545,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         // factor and the trial's marks; after an accepted exchange that this
         // item sees (a changed bead or a changed partner), the same sums again
         // with the new bead types, read past the L1 cache
-        if (pw == nullptr || pass > 0) break;
+        if (pw == nullptr || pass > 0 || !pw->has_trial) break;
         if (t == 0) sm.redo = pipe_wait(S, *pw, k0 / NL_BEADS);
         g.sync();
         if (!sm.redo) break;
@@ -545,7 +562,8 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     if (valid && gl == 0) {
         const Real f0 = ax, f1 = ay, f2 = az;
         const int grp = id < P.n_lipid_beads ? 0 : 1;
-        const Real a = F32 ? (Real)__ldcg(&C.alpha_f[grp]) : (Real)__ldcg(&C.alpha[grp]);
+        const Real a = pw != nullptr && pw->has_close ? alpha_beside_close<Real>(C, grp, *pw)
+                       : (F32 ? (Real)C.alpha_f[grp] : (Real)C.alpha[grp]);
         const Real dtm = F32 ? (Real)P.dt_over_mf : (Real)P.dt_over_m;
         V4 v = sm.svel[il];
         v.x = fmr(a, v.x, f0 * dtm);
@@ -638,6 +656,11 @@ __device__ void nl_step_close(const SysDev &S, int lane, int par) {
         const double al = alpha_for(S, P, C, lane, (double)(Real)(lane ? a1 : a0), ctr, tag);
         C.alpha[lane] = al;
         C.alpha_f[lane] = (float)al;
+        // for a step running beside this close: the factor with its close
+        // sequence (this close is the only writer of close_seq)
+        const unsigned long long seq = ld_relaxed64(&C.close_seq) + 1;
+        const unsigned long long pack = (seq << 32) | __float_as_uint((float)al);
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" :: "l"(&C.alpha_pack[lane]), "l"(pack) : "memory");
     }
     if (lane == 0) {
         C.ke_total[0] = a0;
@@ -837,8 +860,9 @@ __device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &
 // Overlapped mode, when every step item has a group of its own and
 // TRIAL_PARTS + 1 groups per system are left over (the last gids): the close
 // of step s - 1 (thermostat factor) and its exchange trial run beside the
-// items of step s, so a step costs one grid barrier.  An item waits for the
-// factor before it integrates; the trial marks every item that holds a bead
+// items of step s, so a step costs one grid barrier.  An item takes the
+// factor when it integrates (published with the close's sequence number in
+// one word); the trial marks every item that holds a bead
 // whose type the exchange changes or a list partner of one, and a marked item
 // waits for the decision and, if the exchange was accepted, sums its forces
 // again with the new types.  The arithmetic is that of the sequential order
