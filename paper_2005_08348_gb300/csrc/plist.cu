@@ -295,6 +295,8 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
         for (int f0 = 0; f0 < M; f0 += NLB_STAGE) {
             const int mc = min(NLB_STAGE, M - f0);
             g.sync();
+            // every thread copies its candidates' positions (all in flight at
+            // once), then turns them into frame coordinates in place
             for (int f = t; f < mc; f += GRP) {
                 const int fg = f0 + f;
                 int lo = 0, hi = 26;              // the neighbour cell holding candidate fg
@@ -303,10 +305,15 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
                     if (sm.noff[mid] <= fg) lo = mid; else hi = mid - 1;
                 }
                 const int kj = sm.nb[lo].x + (fg - sm.noff[lo]);
-                const uint4 pj = cur[kj];
+                cp_async16(&sm.sf[f], cur + kj);
+                sm.sk[f] = kj;
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            cp_async_wait_all();
+            for (int f = t; f < mc; f += GRP) {
+                const uint4 pj = *reinterpret_cast<const uint4 *>(&sm.sf[f]);
                 sm.sf[f] = make_float4((float)(int)(pj.x - ox) * q0, (float)(int)(pj.y - oy) * q1,
                                        (float)(int)(pj.z - oz) * q2, __uint_as_float(pj.w));
-                sm.sk[f] = kj;
             }
             g.sync();
             // the candidates within rl of the box around this warp's beads
