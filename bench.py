@@ -47,6 +47,18 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The job's time is the slowest rank's: max of x over all ranks (x itself
+    on one rank); device is where the collective's tensor lives ("cuda" for
+    NCCL, "cpu" for gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload():
     from paper_2005_08348_gb300 import synth
     return synth.mcmd_large()
@@ -223,10 +235,7 @@ def run_gpu(args):
     pairs_per_eval = 0.5 * (n_pairs0 + n_pairs1)
     md = c1["md_steps"] - c0["md_steps"]
     trials = c1["trials"] - c0["trials"]
-    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item()) / 1e3
+    tmax = max_over_ranks(total_ms, dist, "cuda") / 1e3
     value = pairs_per_eval * md * ws / tmax
     trials_per_s = trials * ws / tmax
 
