@@ -314,6 +314,7 @@ def run_gpu(args):
         out["batched_replicas"] = replica_benchmark(stream)
         out["swap_trials_4608_lipids"] = swap_benchmark(stream)
         out["mdas_4608_lipids"] = mdas_benchmark(stream)
+        out["head_rdf_4608_lipids"] = rdf_benchmark(stream)
         out["served"] = serving_benchmark(stream)
     if not args.no_cpu_baseline:
         ob = oracle_rate(m)
@@ -397,6 +398,30 @@ def mdas_benchmark(stream, n_moves=6):
            "force_evaluations_per_move": 10 * 5 + 10, "accepted": int(sum(acc)), "moves": n_moves}
     s.close()
     return res
+
+
+def rdf_benchmark(stream, n_calls=50):
+    """The mixing observable (in-plane head-bead pair counts of one lipid
+    type per leaflet) on the 4608-lipid bilayer after some MD: one
+    mdas_head_rdf call (kernels, a 1 KB copy back), against the oracle's
+    O(N^2) count of the same pairs on one host core."""
+    import oracle
+    from paper_2005_08348_gb300 import mdas, synth
+    m = synth.mdas_patch()
+    s = mdas.System(m, stream=stream.cuda_stream)
+    s.md_steps(50, swap_every=0)
+    s.head_rdf(0, 1, 3.0, 60)
+    t = _elapsed(stream, lambda: [s.head_rdf(0, 1, 3.0, 60) for _ in range(n_calls)]) / n_calls
+    st = s.get_state()
+    o = oracle.Oracle(m)
+    t0 = time.perf_counter()
+    co, nho = o.head_rdf(st["pos_u"], st["ltype"], 0, 1, 3.0, 60)
+    t_or = time.perf_counter() - t0
+    c, nh = s.head_rdf(0, 1, 3.0, 60)
+    s.close()
+    return {"workload": f"{m.n_lipids} lipids, type 0 heads, 60 bins to 3 nm", "us_per_call": t * 1e6,
+            "oracle_ms_per_call": t_or * 1e3, "heads": [int(x) for x in nh], "pairs_counted": int(c.sum()),
+            "equal_to_oracle": bool((c == co).all() and (nh == nho).all())}
 
 
 def swap_benchmark(stream, n_batch=1024, n_plain=300):

@@ -190,6 +190,24 @@ mdas_status mdas_cell_list(mdas_system *s, int32_t *sorted_ids, int32_t *cell_st
  * must share one precision and one CUDA stream. */
 mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32_t md_steps, int32_t swap_trials);
 
+/* Mixing observable of Sec. 4: the in-plane radial distribution of the head
+ * beads (local index head_k, e.g. the PO4 bead) of the lipids of type
+ * lipid_type, per leaflet.  A lipid is in leaflet 0 when its head lies above
+ * its last bead along z (the sum of its bonds' z steps from the head to the
+ * last bead, each at its minimum image, is a drop), else in leaflet 1.
+ * counts_out [2 * n_bins] (host, written): at L * n_bins + k, the unordered
+ * pairs of such heads in leaflet L whose in-plane distance (minimum image in
+ * x and y) r lies in [k dr, (k + 1) dr), dr = r_max / n_bins.  n_heads_out
+ * [2] (host): the heads per leaflet.  Bins are decided in FP64 with unfused,
+ * correctly rounded operations (r = sqrt(dx * dx + dy * dy), k = floor(r /
+ * dr)), so the counts are exact integers; g(r) in bin k is counts /
+ * (N_L (N_L - 1) / 2 * pi ((k + 1)^2 - k^2) dr^2 / (Lx Ly)).  Errors:
+ * MDAS_ERR_INVALID_ARG for a NULL argument, lipid_type outside [0,
+ * n_lipid_types), head_k outside [0, beads_per_lipid - 1), n_bins outside
+ * [1, 1024] or r_max outside (0, min(Lx, Ly) / 2], before any GPU work. */
+mdas_status mdas_head_rdf(mdas_system *s, int32_t lipid_type, int32_t head_k, double r_max, int32_t n_bins,
+                          int64_t *counts_out, int32_t *n_heads_out);
+
 /* Autotuning of the pair-list skin, the one free parameter of a batch: the
  * cutoff sums of Sec. 3 do not depend on it, only the list rebuild schedule,
  * the list lengths and the FP32 summation order do.  For each of the n_skins

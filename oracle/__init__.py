@@ -28,7 +28,8 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(src):
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+        # no fused multiply-adds: every expression rounds as written, on any host
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
                                "-o", tmp, src, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -239,6 +240,17 @@ class Oracle:
                     pairs=pout[: 2 * res.n_pairs].reshape(-1, 2).copy())
 
     # -- random numbers -------------------------------------------------------
+    def head_rdf(self, pos_u, ltype, lipid_type, head_k=1, r_max=3.0, n_bins=60):
+        """Pair counts [2, n_bins] of the in-plane head-bead distribution per
+        leaflet and the heads per leaflet [2] (or_head_rdf)."""
+        counts = np.zeros(2 * n_bins, np.int64)
+        nh = np.zeros(2, np.int32)
+        pu = _u32(pos_u).reshape(-1)
+        lt = _i32(ltype)
+        lib().or_head_rdf(C.byref(self.s), _p(pu), _p(lt), int(lipid_type), int(head_k), C.c_double(r_max),
+                          int(n_bins), _p(counts), _p(nh))
+        return counts.reshape(2, n_bins), nh
+
     def bussi_alpha(self, K, nf, kt, i0, i1, tag=TAG_THERMO):
         return lib().or_bussi_alpha(C.byref(self.s), C.c_double(K), int(nf), C.c_double(kt),
                                     C.c_uint32(i0), C.c_uint32(i1), C.c_uint32(tag))

@@ -597,3 +597,53 @@ void or_mdas_move(const or_sys *s, or_state *st, int n_pairs, int n_lambda, int 
     res->w = w; res->u = u; res->accepted = acc; res->n_pairs = np;
     free(ltB); free(btA); free(btB); free(x0); free(v0); free(F);
 }
+
+/* ------------------------------------------------------ head-bead g(r)
+ * Sec. 4: the radial distribution of the head (PO4) beads of one lipid type
+ * monitors mixing; its highest peak is fitted against force evaluations.
+ * Reading (listed in the design notes): the distribution is taken in the
+ * membrane plane, within each leaflet (a lipid belongs to leaflet 0 when its
+ * head bead lies above its last bead along z: the sum of its bonds' z steps,
+ * each at its minimum image, from the head to the last bead), over unordered
+ * pairs of such heads, with the in-plane distance under the minimum image in
+ * x and y.  counts[leaflet * n_bins + k] counts the pairs with
+ * k = floor(r / dr), dr = r_max / n_bins, r = sqrt(dx * dx + dy * dy) < r_max;
+ * n_heads[leaflet] counts the heads.  Fixed-point differences are taken
+ * modulo 2^32 as signed 32-bit values (the minimum image). */
+static double frac_diff(uint32_t a, uint32_t b, double L) { return (double)(int32_t)(a - b) * (L / 4294967296.0); }
+
+void or_head_rdf(const or_sys *s, const uint32_t *pu, const int *ltype, int lt_sel, int head_k,
+                 double r_max, int n_bins, long long *counts, int *n_heads)
+{
+    const int nl = s->n_lipids;
+    int *leaf = (int *)malloc(sizeof(int) * (nl > 0 ? nl : 1));
+    for (int l = 0; l < nl; ++l) {
+        /* head above the last bead: the z steps along the chain from the head
+         * to the last bead, each bond at its minimum image, sum to a drop */
+        long long drop = 0;
+        for (int k = head_k; k < s->bpl - 1; ++k) {
+            const int b = s->lipid_first[l] + k;
+            drop += (int32_t)(pu[3 * b + 2] - pu[3 * (b + 1) + 2]);
+        }
+        leaf[l] = drop > 0 ? 0 : 1;
+    }
+    for (int k = 0; k < 2 * n_bins; ++k) counts[k] = 0;
+    n_heads[0] = n_heads[1] = 0;
+    const double dr = r_max / n_bins, r2max = r_max * r_max;
+    for (int i = 0; i < nl; ++i) {
+        if (ltype[i] != lt_sel) continue;
+        n_heads[leaf[i]]++;
+        const int hi = s->lipid_first[i] + head_k;
+        for (int j = i + 1; j < nl; ++j) {
+            if (ltype[j] != lt_sel || leaf[j] != leaf[i]) continue;
+            const int hj = s->lipid_first[j] + head_k;
+            const double dx = frac_diff(pu[3 * hi], pu[3 * hj], s->box[0]);
+            const double dy = frac_diff(pu[3 * hi + 1], pu[3 * hj + 1], s->box[1]);
+            const double r2 = dx * dx + dy * dy;
+            if (!(r2 < r2max)) continue;
+            const int k = (int)floor(sqrt(r2) / dr);
+            if (k < n_bins) counts[leaf[i] * n_bins + k]++;
+        }
+    }
+    free(leaf);
+}

@@ -96,6 +96,9 @@ struct mdas_system {
     void *arena = nullptr;
     size_t arena_bytes = 0;
     double *fout = nullptr;
+    uint4 *rdf_info = nullptr;           // head-bead distribution: per lipid head and leaflet
+    unsigned long long *rdf_hist = nullptr;
+    int *rdf_nh = nullptr;
     std::unique_ptr<Batch> solo;
     std::string err;
     bool unstable = false;
@@ -385,9 +388,10 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     for (auto *x : b.sys) x->cells_valid = false;
     LaunchCtx L = b.ctx();
     const bool persistent = b.persistent && md_run_blocks(b.precision, lambda) > 0;
-    // segments end on a trial boundary so that every trial follows its step
-    long long seg = MAX_DRAW_STEPS - 1;
-    if (trial) seg = std::max<long long>(swap_every, seg / swap_every * swap_every);
+    // segments of at most MAX_DRAW_STEPS - 1 steps (the precomputed thermostat
+    // variates); a segment starting at step k0 has its trials after local
+    // steps s with (k0 + s + 1) % swap_every == 0
+    const long long seg = MAX_DRAW_STEPS - 1;
     long long launches = 0;
     for (long long k0 = 0; k0 < n_steps; k0 += seg) {
         const long long n = std::min(seg, n_steps - k0);
@@ -396,7 +400,7 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
         launches += 2;
         if (persistent) {
             CK(tm.begin(b.stream, n));
-            CK(launch_md_run(L, lambda, (int)n, swap_every, b.rsync));
+            CK(launch_md_run(L, lambda, (int)n, swap_every, trial ? (int)(k0 % swap_every) : 0, b.rsync));
             CK(tm.end(b.stream));
             k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
             launches += 1;
@@ -672,6 +676,8 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.log, sizeof(TrialRec) * (size_t)LOG_CAP}, {(void **)&H.result, 8ull * 64},
         {(void **)&H.tdraw, sizeof(double2) * 2ull * MAX_DRAW_STEPS},
         {(void **)&s->fout, 24ull * n},
+        {(void **)&s->rdf_info, 16ull * std::max(nl, 1)}, {(void **)&s->rdf_hist, 16ull * RDF_MAX_BINS},
+        {(void **)&s->rdf_nh, 8ull},
         {(void **)&H.lcell_count, 4ull * P.n_lcells}, {(void **)&H.ltmp, 4ull * P.n_lcells * P.lcapc},
         {(void **)&H.lcell, 8ull * P.n_lcells}, {(void **)&H.lid, 4ull * n}, {(void **)&H.lk, 4ull * n},
         {(void **)&H.lpos, 32ull * n}, {(void **)&H.xref, 16ull * n}, {(void **)&H.nl_n, 4ull * NL_G * n},
@@ -1083,6 +1089,31 @@ mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32
     return st;
 }
 
+mdas_status mdas_head_rdf(mdas_system *s, int32_t lipid_type, int32_t head_k, double r_max, int32_t n_bins,
+                          int64_t *counts_out, int32_t *n_heads_out) {
+    if (!s || !counts_out || !n_heads_out) return fail(s, MDAS_ERR_INVALID_ARG, "head_rdf: NULL argument");
+    if (lipid_type < 0 || lipid_type >= s->hp.n_lt || head_k < 0 || head_k >= s->bpl - 1)
+        return fail(s, MDAS_ERR_INVALID_ARG, "head_rdf: lipid type or head bead out of range");
+    if (n_bins < 1 || n_bins > RDF_MAX_BINS || !(r_max > 0.0) ||
+        r_max > 0.5 * std::min(s->hp.box[0], s->hp.box[1]))
+        return fail(s, MDAS_ERR_INVALID_ARG, "head_rdf: n_bins outside [1, 1024] or r_max outside (0, L/2]");
+    if (s->unstable) return fail(s, MDAS_ERR_UNSTABLE, "head_rdf: the system is unstable");
+    Batch &b = *s->solo;
+    LaunchCtx L = b.ctx();
+    launch_head_rdf(L.sys, s->n_lip, lipid_type, head_k, r_max, n_bins, s->rdf_info, s->rdf_nh, s->rdf_hist,
+                    s->stream);
+    std::vector<unsigned long long> h(2 * (size_t)n_bins);
+    int nh[2];
+    CK(cudaMemcpyAsync(h.data(), s->rdf_hist, 8ull * 2 * n_bins, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(nh, s->rdf_nh, 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    for (int k = 0; k < 2 * n_bins; ++k) counts_out[k] = (int64_t)h[k];
+    n_heads_out[0] = nh[0];
+    n_heads_out[1] = nh[1];
+    return MDAS_OK;
+}
+
 mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
                                 int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
                                 double *us_per_step, double *best_skin) {
@@ -1233,7 +1264,7 @@ size_t arena_estimate(const mdas_system_desc *d) {
     size_t t = sizeof(Params) + sizeof(Counters) + 16 * n + vsz * n + 24 * n + 8 * std::max(d->n_lipids, 1) +
                8 * nc + 24 * nc * capc + vsz * nc * capc + 4 * n + 16 * nc + 24 * nbb + 32 * nc + 16 * n + vsz * n +
                (16 + 8 + 72 + 4 + 128 + 64) * (size_t)MAX_ROUND_TRIALS + sizeof(TrialRec) * (size_t)LOG_CAP + 512 +
-               32 * MAX_DRAW_STEPS + 24 * n;
+               32 * MAX_DRAW_STEPS + 24 * n + 16 * std::max(d->n_lipids, 1) + 16 * RDF_MAX_BINS + 8;
     const ListDims ld = list_dims(d);
     t += 12ull * ld.n_lcells + 4ull * ld.n_lcells * ld.lcapc + 4 * n + 4 * n + 32 * n + 16 * n + 4ull * NL_G * n +
          4ull * (ld.lcap / NL_G) * ld.lrow + 4ull * NL_PART * n + 8ull * ((n + NL_BEADS - 1) / NL_BEADS / 32 + 1);

@@ -249,7 +249,7 @@ void launch_thermostat(const LaunchCtx &L);
 void launch_nl_build(const LaunchCtx &L);
 void launch_nl_step(const LaunchCtx &L, bool lambda);
 int md_run_blocks(int precision, bool lambda);
-cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, void *sync);
+cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, void *sync);
 size_t md_run_sync_bytes();
 void launch_trial_nl(const LaunchCtx &L);
 void launch_energy_reduce(const LaunchCtx &L);
@@ -265,6 +265,9 @@ void launch_mdas_accept(const LaunchCtx &L);
 void launch_mdas_restore(const LaunchCtx &L);
 void launch_snapshot(const LaunchCtx &L);
 void launch_delta_energy(const LaunchCtx &L, int n_changed_lipids);
+void launch_head_rdf(const SysDev *dsys, int n_lip, int lt_sel, int head_k, double r_max, int n_bins, uint4 *info,
+                     int *n_heads, unsigned long long *hist, cudaStream_t st);
+constexpr int RDF_MAX_BINS = 1024;     // bins of one head-bead distribution
 void launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int n, uint4 *out,
                    cudaStream_t st);
 

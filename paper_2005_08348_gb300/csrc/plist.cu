@@ -811,7 +811,7 @@ struct RunArgs {
     int n_sys;
     const int2 *nlmap, *beadmap, *lsortmap, *lcellmap;
     int n_nl, n_bead, n_lsort, n_lcell;
-    int n_steps, swap_every;
+    int n_steps, swap_every, trial_off;   // a trial after local step s when (s + 1 + trial_off) % swap_every == 0
     RunSync *rs;
 };
 
@@ -915,12 +915,13 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
     }
     int tab_sys = -1;                          // system whose tables the group holds
     for (int s = 0; s < a.n_steps; ++s) {
-        const bool tprev = s > 0 && a.swap_every > 0 && s % a.swap_every == 0;   // a trial after step s - 1
+        // a trial after step s - 1: the ordinal o of that trial in this launch
+        const bool tprev = s > 0 && a.swap_every > 0 && (s + a.trial_off) % a.swap_every == 0;
         if (pipe) {
             if (gid < a.n_nl) {
                 const int2 bm = a.nlmap[gid];
                 const SysDev &S = a.sys[bm.x];
-                const int o = tprev ? s / a.swap_every - 1 : 0;   // that trial's ordinal in this launch
+                const int o = tprev ? (s + a.trial_off) / a.swap_every - 1 : 0;
                 PipeWait pw;
                 pw.has_close = s > 0;
                 pw.close_target = close0 + (unsigned long long)s;
@@ -970,7 +971,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                     const SysDev &S = a.sys[q];
                     nl_step_close<Real>(S, threadIdx.x, (S.c->nl_par + s) & 1);
                 }
-            if (a.swap_every > 0 && (s + 1) % a.swap_every == 0) {
+            if (a.swap_every > 0 && (s + 1 + a.trial_off) % a.swap_every == 0) {
                 for (int it = gid; it < TRIAL_PARTS * a.n_sys; it += G) {
                     const SysDev &S = a.sys[it / TRIAL_PARTS];
                     trial_nl_part(S, it % TRIAL_PARTS, (S.c->nl_par + s + 1) & 1, g, tsm, false);
@@ -987,7 +988,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
             const SysDev &S = a.sys[pclose];
             nl_step_close<Real>(S, g.t, (S.c->nl_par + s - 1) & 1);
         }
-        if (ptrial >= 0 && a.swap_every > 0 && s % a.swap_every == 0) {
+        if (ptrial >= 0 && a.swap_every > 0 && (s + a.trial_off) % a.swap_every == 0) {
             const SysDev &S = a.sys[ptrial / TRIAL_PARTS];
             trial_nl_part(S, ptrial % TRIAL_PARTS, (S.c->nl_par + s) & 1, g, tsm, false);
         }
@@ -1005,14 +1006,15 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
 }
 
 template <typename Real, bool LAM>
-static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, RunSync *rs, int n_blocks) {
+static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, int trial_off, RunSync *rs,
+                              int n_blocks) {
     RunArgs a;
     a.sys = L.sys; a.n_sys = L.n_sys;
     a.nlmap = L.nlbeads->d; a.n_nl = L.nlbeads->n;
     a.beadmap = L.beads->d; a.n_bead = L.beads->n;
     a.lsortmap = L.lsort->d; a.n_lsort = L.lsort->n;
     a.lcellmap = L.lcells->d; a.n_lcell = L.lcells->n;
-    a.n_steps = n_steps; a.swap_every = swap_every; a.rs = rs;
+    a.n_steps = n_steps; a.swap_every = swap_every; a.trial_off = trial_off; a.rs = rs;
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)k_md_run<Real, LAM>, dim3(n_blocks), dim3(RUN_THREADS), args,
                                        RUN_GROUPS * group_smem<Real>(), L.stream);
@@ -1043,15 +1045,15 @@ int md_run_blocks(int precision, bool lambda) {
     return c;
 }
 
-cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, void *sync) {
+cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, void *sync) {
     const int nb = md_run_blocks(L.precision, lambda);
     if (nb <= 0) return cudaErrorCooperativeLaunchTooLarge;
     RunSync *rs = (RunSync *)sync;
     if (L.precision == 1)
-        return lambda ? run_launch<double, true>(L, n_steps, swap_every, rs, nb)
-                      : run_launch<double, false>(L, n_steps, swap_every, rs, nb);
-    return lambda ? run_launch<float, true>(L, n_steps, swap_every, rs, nb)
-                  : run_launch<float, false>(L, n_steps, swap_every, rs, nb);
+        return lambda ? run_launch<double, true>(L, n_steps, swap_every, trial_off, rs, nb)
+                      : run_launch<double, false>(L, n_steps, swap_every, trial_off, rs, nb);
+    return lambda ? run_launch<float, true>(L, n_steps, swap_every, trial_off, rs, nb)
+                  : run_launch<float, false>(L, n_steps, swap_every, trial_off, rs, nb);
 }
 
 size_t md_run_sync_bytes() { return sizeof(RunSync); }

@@ -87,7 +87,7 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_pair_kernel_time", "mdas_set_persistent", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
-           "mdas_tune_list_skin"]
+           "mdas_tune_list_skin", "mdas_head_rdf"]
 
 
 def library_path() -> str:
@@ -298,6 +298,15 @@ class System:
         start = np.empty(ncell[0] * ncell[1] * ncell[2] + 1, np.int32)
         self._ck(lib().mdas_cell_list(self._ptr, None, _p(start), None))
         return ids, start, ncell
+
+    def head_rdf(self, lipid_type, head_k=1, r_max=3.0, n_bins=60):
+        """In-plane head-bead pair counts per leaflet (mdas_head_rdf):
+        (counts [2, n_bins] int64, heads per leaflet [2])."""
+        counts = np.zeros(2 * int(n_bins), np.int64)
+        nh = np.zeros(2, np.int32)
+        self._ck(lib().mdas_head_rdf(self._ptr, int(lipid_type), int(head_k), C.c_double(r_max), int(n_bins),
+                                     _p(counts), _p(nh)))
+        return counts.reshape(2, int(n_bins)), nh
 
     def counters(self):
         c = Counters()

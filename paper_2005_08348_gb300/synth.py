@@ -127,8 +127,11 @@ def _type_counts(n: int, fracs) -> list[int]:
 def membrane(nx: int, ny: int | None = None, n_lipid_types: int = 2, fracs=None,
              n_water: int | None = None, water_thickness: float | None = None,
              seed: int = 1001, system_id: int = 0, n_lipids: int | None = None,
-             temperature: float = 310.0, jitter: float = 0.02) -> Membrane:
-    """Build a bilayer of nx*ny grid sites per leaflet (n_lipids/2 filled per leaflet)."""
+             temperature: float = 310.0, jitter: float = 0.02, layout: str = "random") -> Membrane:
+    """Build a bilayer of nx*ny grid sites per leaflet (n_lipids/2 filled per leaflet).
+
+    layout "random": lipid types shuffled by seed; "separated": in each leaflet
+    the types fill stripes along x in order (a phase-separated start)."""
     ny = nx if ny is None else ny
     fracs = fracs if fracs is not None else [1.0 / n_lipid_types] * n_lipid_types
     per_leaflet = nx * ny if n_lipids is None else n_lipids // 2
@@ -176,6 +179,17 @@ def membrane(nx: int, ny: int | None = None, n_lipid_types: int = 2, fracs=None,
     counts = _type_counts(n_lip, fracs)
     lt = np.concatenate([np.full(c, t, np.int32) for t, c in enumerate(counts)])
     rng.shuffle(lt)
+    if layout == "separated":
+        # per leaflet, lipids ordered by grid column x then row: types in that order
+        per = _type_counts(per_leaflet, fracs)
+        tl = np.concatenate([np.full(c, t, np.int32) for t, c in enumerate(per)])
+        sites = [(i, j) for j in range(ny) for i in range(nx)][:per_leaflet]
+        order = sorted(range(per_leaflet), key=lambda q: (sites[q][0], sites[q][1]))
+        for leaf in range(2):
+            for rank, q in enumerate(order):
+                lt[leaf * per_leaflet + q] = tl[rank]
+    elif layout != "random":
+        raise ValueError(f"layout {layout!r}")
     kT = BOLTZMANN * temperature
     vel = rng.normal(0.0, math.sqrt(kT / 72.0), size=pos.shape)
     return Membrane(

@@ -146,3 +146,20 @@ def test_trials_beside_the_next_step_match_separate_launches(prec):
     assert np.array_equal(a["ltype"], b["ltype"])
     for key in ("md_steps", "force_evals", "trials", "null_trials", "accepted", "list_builds"):
         assert ca[key] == cb[key], key
+
+
+def test_trials_across_segment_boundaries():
+    """Trial intervals that do not divide the 511-step segments (and one
+    longer than a segment): the same trials and bits as separate launches."""
+    m = synth.mcmd_small()
+    runs = []
+    for persistent in (True, False):
+        s = mdas.System(m, precision="fp32")
+        s.set_persistent(persistent)
+        s.md_steps(1200, swap_every=10)
+        s.md_steps(4100, swap_every=2000)
+        runs.append((s.get_state(), s.counters()))
+    (a, ca), (b, cb) = runs
+    assert ca["trials"] == 120 + 2 == cb["trials"]
+    assert np.array_equal(a["pos_u"], b["pos_u"]) and np.array_equal(a["ltype"], b["ltype"])
+    assert ca["accepted"] == cb["accepted"]

@@ -392,3 +392,89 @@ def test_nve_energy_error_scales_as_dt_squared():
     s2, d2 = fluct(0.005, 400)
     assert 2.8 < s1 / s2 < 5.5, (s1, s2)
     assert d1 < 5 * s1
+
+
+# ---------------------------------------------------------------- head-bead g(r)
+def _lattice_pairs(a, nside, dr, n_bins):
+    """Unordered pairs per bin on a periodic square lattice of N = nside^2
+    heads (spacing a): every lattice vector v within the minimum image gives
+    N / 2 pairs at |v| (counting integer vectors, no positions involved)."""
+    vec = np.zeros(n_bins, np.int64)
+    for p in range(-nside, nside + 1):
+        for q in range(-nside, nside + 1):
+            if (p, q) == (0, 0) or 2 * abs(p) >= nside or 2 * abs(q) >= nside:
+                continue
+            r = math.hypot(p, q) * a
+            if r < n_bins * dr:
+                vec[int(r // dr)] += 1
+    return vec * (nside * nside) // 2
+
+
+def test_head_rdf_square_lattice_closed_form():
+    """Heads on the two leaflets' perfect square lattices (spacing 0.8 nm,
+    offset by half a cell between leaflets): the counts per bin are the
+    lattice's shells, with no pair across the leaflets."""
+    m = synth.membrane(8, n_lipid_types=1, fracs=[1.0], n_water=40, jitter=0.0, seed=3)
+    o = oracle.Oracle(m)
+    r_max, n_bins = 3.1, 40
+    counts, nh = o.head_rdf(m.pos_u, np.zeros(m.n_lipids, np.int32), 0, 1, r_max, n_bins)
+    assert list(nh) == [64, 64]
+    exp = _lattice_pairs(0.8, 8, r_max / n_bins, n_bins)
+    assert np.array_equal(counts[0], exp) and np.array_equal(counts[1], exp)
+
+
+def test_head_rdf_checkerboard_types():
+    """A checkerboard of two types: the type-0 heads form a square lattice of
+    spacing 0.8 * sqrt(2) rotated by 45 degrees (vectors (1,1), (1,-1)), half
+    the sites; type 1 the same by symmetry; a type with no lipid gives zeros."""
+    m = synth.membrane(8, n_lipid_types=2, fracs=[0.5, 0.5], n_water=40, jitter=0.0, seed=3)
+    o = oracle.Oracle(m)
+    lt = np.zeros(m.n_lipids, np.int32)
+    for leaf in range(2):
+        for j in range(8):
+            for i in range(8):
+                lt[leaf * 64 + j * 8 + i] = (i + j) % 2
+    r_max, n_bins = 3.1, 40
+    dr = r_max / n_bins
+    # vectors p (1,1) + q (1,-1) of the sublattice, within the minimum image of the 8x8 box
+    exp = np.zeros(n_bins, np.int64)
+    for vx in range(-3, 4):
+        for vy in range(-3, 4):
+            if (vx, vy) == (0, 0) or (vx + vy) % 2:
+                continue
+            r = math.hypot(vx, vy) * 0.8
+            if r < r_max:
+                exp[int(r // dr)] += 1
+    exp = exp * 32 // 2
+    for t in (0, 1):
+        counts, nh = o.head_rdf(m.pos_u, lt, t, 1, r_max, n_bins)
+        assert list(nh) == [32, 32]
+        assert np.array_equal(counts[0], exp) and np.array_equal(counts[1], exp)
+    counts, nh = o.head_rdf(m.pos_u, lt, 5, 1, r_max, n_bins)
+    assert counts.sum() == 0 and list(nh) == [0, 0]
+
+
+def test_g_of_r_normalisation_uniform_and_separated_layout():
+    """The g(r) normalisation: heads at uniform random positions give g = 1
+    within counting noise (the ideal 2D gas it divides by); the separated
+    layout puts each type in one stripe per leaflet."""
+    from paper_2005_08348_gb300 import mixing
+    rng = np.random.default_rng(4)
+    box = np.array([20.0, 20.0, 10.0])
+    n = 4000
+    r_max, nb = 4.0, 20
+    counts = np.zeros((2, nb), np.int64)
+    for leaf in range(2):
+        p = rng.uniform(0, 20.0, size=(n, 2))
+        for i in range(n):
+            d = p[i + 1:] - p[i]
+            d -= 20.0 * np.round(d / 20.0)
+            r = np.sqrt((d * d).sum(1))
+            counts[leaf] += np.bincount((r[r < r_max] / (r_max / nb)).astype(int), minlength=nb)[:nb]
+    r, g, both = mixing.g_of_r(counts, [n, n], box, r_max)
+    assert np.all(np.abs(both[2:] - 1.0) < 0.05), both
+    m = mixing.bilayer(nx=10, ny=20)
+    lt = m.lipid_type.reshape(2, 200)
+    col = np.arange(200) % 10                      # grid column (x) of each site of a leaflet
+    for leaf in range(2):
+        assert np.array_equal(lt[leaf], (col >= 5).astype(np.int32))
