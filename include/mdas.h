@@ -159,6 +159,22 @@ mdas_status mdas_swap_trials(mdas_system *s, int32_t n_trials, mdas_swap_stats *
  * record is no longer (or not yet) in the log. */
 mdas_status mdas_trial_log(mdas_system *s, uint64_t first, int32_t n, mdas_trial_record *rec);
 
+/* Semi-grand lipid mutations (Sec. 2: a randomly chosen lipid is turned into
+ * a lipid of another type and the change is kept under a Metropolis test):
+ * n_trials trials in order.  Trial T draws Philox (0, T, 6, 0): the lipid a
+ * by multiply-shift of word 0, its new type among the other n_lipid_types - 1
+ * types from word 1 (old + 1 + pick, modulo n_lipid_types), u from words 2-3
+ * (53 bits).  dE = U(after) - U(before) in FP64 over the pairs within rc
+ * that involve a bead whose type changes; accept iff dE - (mu[new] -
+ * mu[old]) + kT ln u <= 0, i.e. the semi-grand weight exp(-(U - sum of the
+ * lipids' mu) / kT).  mu: host, n_lipid_types chemical potentials (kJ/mol),
+ * or NULL for all zero.  Mutations share the trial counter, the statistics
+ * and the log of the exchange trials; in their records b is the new type.
+ * Errors: MDAS_ERR_INVALID_ARG for n_trials < 0 or a non-finite mu, before
+ * any GPU work. */
+mdas_status mdas_mutation_trials(mdas_system *s, int32_t n_trials, const double *mu, mdas_swap_stats *st,
+                                 mdas_trial_record *log);
+
 /* One MDAS move (Sec. 2, Eqs. 2-3): n_pairs disjoint pairs of lipids of
  * different types (pairs [n_pairs*2] host, or NULL to draw them) change into
  * each other over n_lambda steps of lambda on U(l) = (1-l) U_A + l U_B, with

@@ -192,6 +192,17 @@ class Oracle:
         return lt, [dict(a=r.a, b=r.b, null=bool(r.null_trial), accepted=bool(r.accepted), dE=r.dE, u=r.u)
                     for r in recs[:n]]
 
+    def mutation_trials(self, pos_u, ltype, t0, n, mu=None):
+        """Semi-grand mutations in order (or_mutation_trials): returns the
+        records and the final lipid types."""
+        lt = np.array(ltype, np.int32)
+        m = np.zeros(16) if mu is None else np.ascontiguousarray(np.pad(np.asarray(mu, np.float64), (0, 16 - len(mu))))
+        out = (_Trial * n)()
+        lib().or_mutation_trials(C.byref(self.s), _p(_u32(pos_u).reshape(-1)), _p(lt), C.c_uint32(t0), int(n),
+                                 _p(m), out)
+        recs = [dict(a=r.a, b=r.b, null=r.null_trial, accepted=r.accepted, dE=r.dE, u=r.u) for r in out]
+        return recs, lt
+
     # -- dynamics -------------------------------------------------------------
     def state(self, pos_u=None, vel=None, ltype=None, step=0, trial=0, move=0, at_step=0):
         m = self.m

@@ -37,7 +37,7 @@
 #define OR_TWO32 4294967296.0
 
 enum { OR_TAG_THERMO = 1, OR_TAG_SWAP = 2, OR_TAG_MDAS_PAIR = 3, OR_TAG_MDAS_ACC = 4,
-       OR_TAG_AT_THERMO = 5 };
+       OR_TAG_AT_THERMO = 5 , OR_TAG_MUTATE = 6 };
 
 typedef struct {
     int n_beads, n_lipids, bpl, n_bt, n_lt;
@@ -447,6 +447,46 @@ static void swap_trial(const or_sys *s, const uint32_t *pu, int *ltype, uint32_t
 void or_swap_trials(const or_sys *s, const uint32_t *pu, int *ltype, uint32_t t0, int n, or_trial *log_out)
 {
     for (int k = 0; k < n; ++k) swap_trial(s, pu, ltype, t0 + (uint32_t)k, &log_out[k]);
+}
+
+/* Sec. 2: the MC move that turns one randomly chosen lipid into a lipid of
+ * another type, kept under a Metropolis test; here in its semi-grand form with
+ * chemical potentials mu per lipid type.  Trial t draws Philox (0, t, 6, 0):
+ * the lipid from word 0, the new type (old + 1 + pick from word 1 among the
+ * n_lt - 1 others) modulo n_lt, u from words 2-3.  dE = U(after) - U(before)
+ * from two full energies; accept iff dE - (mu[new] - mu[old]) + kT ln u <= 0.
+ * In the record, b holds the new type. */
+void or_mutation_trials(const or_sys *s, const uint32_t *pu, int *ltype, uint32_t t0, int n, const double *mu,
+                        or_trial *log_out)
+{
+    const int nb = s->n_beads;
+    int *bt0 = malloc(sizeof(int) * nb), *bt1 = malloc(sizeof(int) * nb);
+    int *lt1 = malloc(sizeof(int) * s->n_lipids);
+    const double kT = OR_BOLTZ * s->temperature;
+    for (int k = 0; k < n; ++k) {
+        uint32_t w[4];
+        draw(s, 0, t0 + (uint32_t)k, OR_TAG_MUTATE, 0, w);
+        const int a = (int)(((uint64_t)w[0] * (uint64_t)s->n_lipids) >> 32);
+        const int told = ltype[a];
+        const int tnew = s->n_lt > 1 ? (told + 1 + (int)(((uint64_t)w[1] * (uint64_t)(s->n_lt - 1)) >> 32)) % s->n_lt
+                                     : told;
+        or_trial *r = &log_out[k];
+        r->a = a; r->b = tnew; r->u = u53(w[2], w[3]); r->dE = 0.0; r->accepted = 0;
+        r->null_trial = tnew == told;
+        if (r->null_trial) continue;
+        memcpy(lt1, ltype, sizeof(int) * s->n_lipids);
+        lt1[a] = tnew;
+        or_bead_types(s, ltype, bt0);
+        or_bead_types(s, lt1, bt1);
+        const double e0 = or_energy(s, pu, bt0, NULL, 0.0, 1, NULL, NULL);
+        const double e1 = or_energy(s, pu, bt1, NULL, 0.0, 1, NULL, NULL);
+        r->dE = e1 - e0;
+        if (r->dE - (mu[tnew] - mu[told]) + kT * log(r->u) <= 0.0) {
+            ltype[a] = tnew;
+            r->accepted = 1;
+        }
+    }
+    free(bt0); free(bt1); free(lt1);
 }
 
 /* ------------------------------------------------------------ dynamics */

@@ -836,6 +836,42 @@ mdas_status mdas_swap_trials(mdas_system *s, int32_t n_trials, mdas_swap_stats *
     return MDAS_OK;
 }
 
+mdas_status mdas_mutation_trials(mdas_system *s, int32_t n_trials, const double *mu, mdas_swap_stats *stats,
+                                 mdas_trial_record *log) {
+    if (!s || n_trials < 0) return fail(s, MDAS_ERR_INVALID_ARG, "mutation_trials: bad argument");
+    double m[MAXT] = {0.0};
+    if (mu)
+        for (int t = 0; t < s->hp.n_lt; ++t) {
+            if (!std::isfinite(mu[t])) return fail(s, MDAS_ERR_INVALID_ARG, "mutation_trials: mu is not finite");
+            m[t] = mu[t];
+        }
+    if (s->unstable) return fail(s, MDAS_ERR_UNSTABLE, "mutation_trials: system is unstable");
+    if (n_trials == 0 || s->n_lip == 0) return MDAS_OK;
+    Counters c0;
+    CK(cudaMemcpyAsync(&c0, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->hs.c->mu, m, sizeof(m), cudaMemcpyHostToDevice, s->stream));
+    Batch &b = *s->solo;
+    mdas_status st = build_cells(s, b);
+    if (st != MDAS_OK) return st;
+    LaunchCtx L = b.ctx();
+    launch_mutation_trials(L, n_trials);
+    s->kernel_launches += 1;
+    Counters c1;
+    CK(cudaMemcpyAsync(&c1, s->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    if (stats) {
+        stats->trials = (int64_t)(c1.trials - c0.trials);
+        stats->null_trials = (int64_t)(c1.null_trials - c0.null_trials);
+        stats->accepted = (int64_t)(c1.accepted - c0.accepted);
+        stats->rounds = 1;
+    }
+    st = check_err(s, b);
+    if (st != MDAS_OK) return st;
+    if (log) return mdas_trial_log(s, c0.trial, n_trials, log);
+    return MDAS_OK;
+}
+
 mdas_status mdas_trial_log(mdas_system *s, uint64_t first, int32_t n, mdas_trial_record *rec) {
     if (!s || n < 0 || (n > 0 && !rec)) return fail(s, MDAS_ERR_INVALID_ARG, "trial_log: bad argument");
     Counters c;

@@ -33,7 +33,7 @@ constexpr double TWO32 = 4294967296.0;
 constexpr double BOLTZ = 0.0083144626;
 constexpr double COUL = 138.935458;
 
-enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5 };
+enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5, TAG_MUTATE = 6 };
 enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8, ERR_BAD_INPUT = 16 };
 
 // Per-bead meta word carried in the 4th lane of every position:
@@ -105,6 +105,7 @@ struct Counters {
     int max_cell, pending;
     int n_trials_round, rounds;
     double w_part[2 * MAX_PAIRS];
+    double mu[MAXT];                   // chemical potential per lipid type (semi-grand mutations), kJ/mol
     unsigned long long draw_base;      // thermostat variates precomputed for counters
     int draw_n, draw_tag;              // [draw_base, draw_base + draw_n) of stream draw_tag
     unsigned int ticket;               // last-block ticket of the fused single trial
@@ -265,6 +266,7 @@ void launch_mdas_accept(const LaunchCtx &L);
 void launch_mdas_restore(const LaunchCtx &L);
 void launch_snapshot(const LaunchCtx &L);
 void launch_delta_energy(const LaunchCtx &L, int n_changed_lipids);
+void launch_mutation_trials(const LaunchCtx &L, int n);
 void launch_head_rdf(const SysDev *dsys, int n_lip, int lt_sel, int head_k, double r_max, int n_bins, uint4 *info,
                      int *n_heads, unsigned long long *hist, cudaStream_t st);
 constexpr int RDF_MAX_BINS = 1024;     // bins of one head-bead distribution

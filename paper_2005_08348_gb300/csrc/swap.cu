@@ -485,6 +485,69 @@ void launch_delta_energy(const LaunchCtx &L, int n) {
     k_mark_b<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n, 1);
 }
 
+// ------------------------------------------------------------ mutations
+// Semi-grand lipid mutations (Sec. 2: a random lipid turned into a lipid of
+// another type under a Metropolis test), n in order by one block per system.
+// Trial T draws Philox (0, T, TAG_MUTATE, 0): lipid a from word 0, the new
+// type among the other n_lt - 1 types from word 1, u from words 2-3.  dE is
+// the FP64 sum over the changed beads of a and their neighbours in the 27
+// cells (the cell list of the current state); accept iff
+// dE - (mu[new] - mu[old]) + kT ln u <= 0.
+__global__ void __launch_bounds__(128) k_mutation_trials(const SysDev *__restrict__ sys, int n) {
+    const SysDev &S = sys[blockIdx.x];
+    const Params &P = *S.p;
+    Counters &C = *S.c;
+    __shared__ double sh[128];
+    __shared__ int sa, sta, stn;
+    __shared__ double su;
+    for (int x = 0; x < n; ++x) {
+        const unsigned long long T = C.trial + (unsigned long long)x;
+        if (threadIdx.x == 0) {
+            const uint4 w = draw4(P, 0u, (uint32_t)T, TAG_MUTATE, 0u);
+            const int a = pick(w.x, P.n_lip), ta = S.ltype[a];
+            sa = a;
+            sta = ta;
+            stn = P.n_lt > 1 ? (ta + 1 + pick(w.y, P.n_lt - 1)) % P.n_lt : ta;
+            su = unit53(w.z, w.w);
+        }
+        __syncthreads();
+        const int a = sa, ta = sta, tn = stn;
+        auto changed = [&](uint32_t mj, int) {
+            return meta_lip(mj) == a && P.lbt[ta * 16 + meta_k(mj)] != P.lbt[tn * 16 + meta_k(mj)];
+        };
+        auto newt = [&](uint32_t mj, int) { return (int)P.lbt[tn * 16 + meta_k(mj)]; };
+        double acc = 0.0;
+        if (tn != ta)
+            for (int it = threadIdx.x; it < P.bpl * 27; it += blockDim.x) {
+                const int k = it / 27, slot = it % 27;
+                const int oi = P.lbt[ta * 16 + k], ni = P.lbt[tn * 16 + k];
+                if (oi == ni) continue;
+                const int i = a * P.bpl + k;
+                acc += bead_delta(S, P, i, S.pos[i], oi, ni, slot, newt, changed);
+            }
+        const double dE = block_sum(acc, sh);
+        if (threadIdx.x == 0) {
+            TrialRec r;
+            r.a = a; r.b = tn; r.u = su; r.index = T;
+            r.null_trial = tn == ta;
+            r.dE = r.null_trial ? 0.0 : dE;
+            r.accepted = !r.null_trial && metropolis(dE - (C.mu[tn] - C.mu[ta]), P.kT, su);
+            if (r.accepted) set_lipid_type(S, P, a, tn);
+            S.log[T % LOG_CAP] = r;
+            C.trials++;
+            C.force_evals++;
+            C.null_trials += r.null_trial;
+            C.accepted += r.accepted;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) C.trial += (unsigned long long)n;
+}
+
+void launch_mutation_trials(const LaunchCtx &L, int n) {
+    k_mutation_trials<<<L.n_sys, 128, 0, L.stream>>>(L.sys, n);
+}
+
 // ----------------------------------------------------------------- Philox
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int n, uint4 *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -87,7 +87,7 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_pair_kernel_time", "mdas_set_persistent", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
-           "mdas_tune_list_skin", "mdas_head_rdf"]
+           "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials"]
 
 
 def library_path() -> str:
@@ -254,6 +254,15 @@ class System:
         rec = np.zeros(n, TRIAL_DTYPE) if log else None
         self._ck(lib().mdas_swap_trials(self._ptr, int(n), C.byref(st), _p(rec)))
         return dict(trials=st.trials, null=st.null_trials, accepted=st.accepted, rounds=st.rounds), rec
+
+    def mutation_trials(self, n, mu=None, log=True):
+        """Semi-grand mutations (mdas_mutation_trials); mu: per-type chemical
+        potentials (kJ/mol) or None."""
+        st = SwapStats()
+        rec = np.zeros(n, TRIAL_DTYPE) if log else None
+        m = None if mu is None else np.ascontiguousarray(mu, np.float64)
+        self._ck(lib().mdas_mutation_trials(self._ptr, int(n), _p(m), C.byref(st), _p(rec)))
+        return dict(trials=st.trials, null=st.null_trials, accepted=st.accepted), rec
 
     def trial_log(self, first, n):
         rec = np.zeros(n, TRIAL_DTYPE)

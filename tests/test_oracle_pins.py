@@ -478,3 +478,30 @@ def test_g_of_r_normalisation_uniform_and_separated_layout():
     col = np.arange(200) % 10                      # grid column (x) of each site of a leaflet
     for leaf in range(2):
         assert np.array_equal(lt[leaf], (col >= 5).astype(np.int32))
+
+
+def test_mutation_semi_grand_weights_with_equal_types():
+    """Two lipid types with the same beads: every mutation has dE = 0 exactly,
+    so the chain gives each lipid type 1 with probability e^(dmu/kT) / (1 +
+    e^(dmu/kT)), the semi-grand weight (here 3/4); chemical-potential gaps of
+    +-1e6 kJ/mol force acceptance and rejection."""
+    m = synth.tiny(n_side=4)
+    m.lipid_bead_type[1] = m.lipid_bead_type[0]
+    o = oracle.Oracle(m)
+    mu = [0.0, o.kT * math.log(3.0)]
+    n = 6000
+    recs, lt = o.mutation_trials(m.pos_u, m.lipid_type, 0, n, mu)
+    assert all(r["dE"] == 0.0 and not r["null"] for r in recs)
+    cur = np.array(m.lipid_type, np.int32)
+    frac = []
+    for r in recs:
+        if r["accepted"]:
+            cur[r["a"]] = r["b"]
+        frac.append(cur.mean())
+    f = float(np.mean(frac[n // 3:]))
+    assert abs(f - 0.75) < 0.04, f
+    assert np.array_equal(cur, lt)
+    up, _ = o.mutation_trials(m.pos_u, np.zeros(m.n_lipids, np.int32), 0, 50, [0.0, 1e6])
+    assert all(r["accepted"] and r["b"] == 1 for r in up[:1])
+    down, lt2 = o.mutation_trials(m.pos_u, np.zeros(m.n_lipids, np.int32), 0, 50, [0.0, -1e6])
+    assert not any(r["accepted"] for r in down) and lt2.sum() == 0
