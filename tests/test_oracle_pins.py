@@ -505,3 +505,17 @@ def test_mutation_semi_grand_weights_with_equal_types():
     assert all(r["accepted"] and r["b"] == 1 for r in up[:1])
     down, lt2 = o.mutation_trials(m.pos_u, np.zeros(m.n_lipids, np.int32), 0, 50, [0.0, -1e6])
     assert not any(r["accepted"] for r in down) and lt2.sum() == 0
+
+
+def test_leaflets_and_interleaflet_pairs():
+    """The host leaflet rule on the generator's bilayer (upper leaflet first)
+    and on a box too thin for a head-to-tail minimum image; interleaflet pairs
+    are disjoint, across the leaflets and of different types."""
+    from paper_2005_08348_gb300 import mixing
+    for m in (synth.mcmd_small(), synth.membrane(6, n_lipid_types=2, n_water=10, seed=9)):
+        leaf = mixing.leaflets(m.pos_u, m.lipid_first_bead, m.lipid_bead_type.shape[1])
+        half = m.n_lipids // 2
+        assert np.array_equal(leaf, np.repeat([0, 1], half))
+        pairs = mixing.interleaflet_pairs(m.lipid_type, leaf, 5, seed=1)
+        assert len(pairs) == 5 and len(set(pairs.ravel())) == 10
+        assert all(leaf[a] == 0 and leaf[b] == 1 and m.lipid_type[a] != m.lipid_type[b] for a, b in pairs)
