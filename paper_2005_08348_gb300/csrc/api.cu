@@ -922,8 +922,11 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
         for (int k = 1; k <= n_lambda; ++k) {
             launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
             if (md_per_lambda > 0) {
+                // after an MD block the pair list is valid: the work term from it
                 mdas_status st = run_md(s, b, md_per_lambda, 0, true, false);
                 if (st != MDAS_OK) return st;
+                launch_mdas_dE_nl(L, dl);
+                continue;
             }
             mdas_status st = build_cells(s, b);
             if (st != MDAS_OK) return st;

@@ -267,6 +267,7 @@ void launch_mdas_restore(const LaunchCtx &L);
 void launch_snapshot(const LaunchCtx &L);
 void launch_delta_energy(const LaunchCtx &L, int n_changed_lipids);
 void launch_mutation_trials(const LaunchCtx &L, int n);
+void launch_mdas_dE_nl(const LaunchCtx &L, double dlambda);   // the work term from the pair list (valid lists)
 void launch_head_rdf(const SysDev *dsys, int n_lip, int lt_sel, int head_k, double r_max, int n_bins, uint4 *info,
                      int *n_heads, unsigned long long *hist, cudaStream_t st);
 constexpr int RDF_MAX_BINS = 1024;     // bins of one head-bead distribution
