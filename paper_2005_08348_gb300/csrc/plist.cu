@@ -12,18 +12,19 @@
 // every bead's displacement from its build position, and a violation has the
 // list rebuilt before it is used again.
 //
-// List order: beads grouped by cell of a grid of edge >= rl, ascending id
-// within a cell, so that the beads of one work item and their partners lie
-// close together in memory.  Positions live in list order in two buffers
-// (read the current one, write the next); the id-ordered position array is
-// written as well, so every other kernel sees the current coordinates.
+// List order: beads grouped by cell of a grid of edge >= rl, ordered by
+// (octant of the cell, id) within a cell, so that the beads of one work item
+// and their partners lie close together in memory.  Positions live in list
+// order in two buffers (read the current one, write the next); the
+// id-ordered position array is written as well, so every other kernel sees
+// the current coordinates.
 //
-// Build: count (beads into list-build cells; the last item of a system scans
-// the counts), place (one warp per cell orders its beads by id and places
-// them), build (the lists of one cell's beads from the 27 neighbour cells,
-// excluded 1-2 pairs left out, and the list indices of each bead's bonded
-// partners).  A bead's list has NL_G columns; partners go to the columns in
-// turn and lane g of the step sums column g.
+// Build: count (beads into list-build cells), place (each item sums the
+// counts of the cells before its own, then one warp per cell ranks its beads
+// by (octant, id) and places them), build (the lists of one cell's beads from
+// the 27 neighbour cells, excluded 1-2 pairs left out, and the list indices
+// of each bead's bonded partners).  A bead's list has NL_G columns; partners
+// go to the columns in turn and lane g of the step sums column g.
 //
 // Step: NL_G threads per bead, each summing its column; the partial forces are
 // summed across the lanes in a fixed tree (the list fixes which entries each
@@ -37,7 +38,9 @@
 // group per block) and inside the persistent kernel k_md_run: one block of
 // 1024 threads (8 groups) per SM, which advances whole MD segments (steps,
 // list rebuilds, thermostat, exchange trials) with grid-wide barriers
-// between the phases instead of kernel launches.
+// between the phases instead of kernel launches.  When the step items leave
+// groups free, each step runs beside the previous step's close and exchange
+// trial, one grid barrier per step.
 #include <cmath>
 
 #include "mdas_phys.cuh"
