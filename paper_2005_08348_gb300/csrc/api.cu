@@ -380,7 +380,7 @@ __global__ void k_run_abort(void *sync, int nbytes, const SysDev *__restrict__ s
 // cannot run or plain launches are asked for, the separate kernels step by
 // step, with the same arithmetic).
 mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, bool lambda = false,
-                   bool check = true) {
+                   bool check = true, int lam_M = 0, double dlam = 0.0) {
     if (n_steps <= 0) return MDAS_OK;
     const bool trial = swap_every > 0;
     SegTimer tm;
@@ -400,7 +400,8 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
         launches += 2;
         if (persistent) {
             CK(tm.begin(b.stream, n));
-            CK(launch_md_run(L, lambda, (int)n, swap_every, trial ? (int)(k0 % swap_every) : 0, b.rsync));
+            CK(launch_md_run(L, lambda, (int)n, swap_every, trial ? (int)(k0 % swap_every) : 0, lam_M, (int)k0, dlam,
+                             b.rsync));
             CK(tm.end(b.stream));
             k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
             launches += 1;
@@ -417,6 +418,12 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
             launch_nl_build(L);
             launches += 5;
             if (trial && (k0 + k + 1) % swap_every == 0) { launch_trial_nl(L); ++launches; }
+            if (lam_M > 0 && (k0 + k + 1) % lam_M == 0) {
+                // the end of a lambda block: its work term, then the next lambda
+                launch_mdas_dE_nl(L, dlam);
+                launch_mdas_set_lambda(L, (double)((k0 + k + 1) / lam_M) * dlam, 1);
+                launches += 3;
+            }
         }
     }
     for (auto *x : b.sys) x->kernel_launches += launches;
@@ -919,18 +926,20 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
     CK(cudaStreamSynchronize(s->stream));
     if (np > 0) {
         const double dl = 1.0 / n_lambda;
-        for (int k = 1; k <= n_lambda; ++k) {
-            launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
-            if (md_per_lambda > 0) {
-                // after an MD block the pair list is valid: the work term from it
-                mdas_status st = run_md(s, b, md_per_lambda, 0, true, false);
-                if (st != MDAS_OK) return st;
-                launch_mdas_dE_nl(L, dl);
-                continue;
-            }
-            mdas_status st = build_cells(s, b);
+        if (md_per_lambda > 0) {
+            // the whole trajectory in one MD run: lambda advances by dl after
+            // every md_per_lambda steps, each block's work term from the pair
+            // list (valid right after the block's steps)
+            launch_mdas_set_lambda(L, 0.0, 1);
+            mdas_status st = run_md(s, b, (long long)n_lambda * md_per_lambda, 0, true, false, md_per_lambda, dl);
             if (st != MDAS_OK) return st;
-            launch_mdas_dE(L, dl);
+        } else {
+            for (int k = 1; k <= n_lambda; ++k) {
+                launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
+                mdas_status st = build_cells(s, b);
+                if (st != MDAS_OK) return st;
+                launch_mdas_dE(L, dl);
+            }
         }
     }
     launch_mdas_accept(L);

@@ -250,7 +250,8 @@ void launch_thermostat(const LaunchCtx &L);
 void launch_nl_build(const LaunchCtx &L);
 void launch_nl_step(const LaunchCtx &L, bool lambda);
 int md_run_blocks(int precision, bool lambda);
-cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, void *sync);
+cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
+                          int lam_off, double dlam, void *sync);
 size_t md_run_sync_bytes();
 void launch_trial_nl(const LaunchCtx &L);
 void launch_energy_reduce(const LaunchCtx &L);

@@ -215,4 +215,43 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
     g.sync();
 }
 
+// MDAS work term of lipid x of the move (Eq. 2: U_B - U_A at the current
+// coordinates, over the pairs within rc that involve a bead whose A and B
+// types differ, pairs of two such beads once, by the lower id) from the pair
+// list, positions in buffer par; one 128-thread group: thread t walks every
+// other row of list column (t / 2) % NL_G of bead t / 8 (both halves of a
+// column by threads t and t ^ 1); the group sum in fixed order.
+__device__ inline double mdas_work_part(const SysDev &S, int x, int par, const Grp &g, double *sh) {
+    const Params &P = *S.p;
+    const Counters &C = *S.c;
+    static_assert(NL_G == 4 && GRP == 128, "four list columns per bead, 128 threads");
+    const int l = C.pairs[x];
+    const int t = g.t, k = t / 8, col = (t / 2) % NL_G, half = t & 1;
+    const uint4 *cur = S.lpos + (size_t)par * P.n;
+    double acc = 0.0;
+    if (k < P.bpl) {
+        const int i = l * P.bpl + k, ki = S.lk[i];
+        const uint4 pi = cur[ki];
+        const int oi = meta_ta(pi.w), ni = meta_tb(pi.w);
+        if (oi != ni) {
+            const int rows = S.nl_n[(size_t)ki * NL_G + col];
+            for (int r = half; r < rows; r += 2) {
+                const int kj = S.nl[(size_t)r * P.lrow + (size_t)ki * NL_G + col];
+                const uint4 pj = cur[kj];
+                const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
+                const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
+                const float r2f = fx * fx + fy * fy + fz * fz;
+                if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
+                const int oj = meta_ta(pj.w), nj = meta_tb(pj.w);
+                if (oj != nj && meta_lip(pj.w) * P.bpl + meta_k(pj.w) < i) continue;
+                const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
+                const double r2 = ex * ex + ey * ey + ez * ez;
+                if (r2 >= P.rc2) continue;
+                acc += pair_du(P, oi, oj, ni, nj, r2);
+            }
+        }
+    }
+    return group_sum(acc, g, sh);
+}
+
 }  // namespace mdas

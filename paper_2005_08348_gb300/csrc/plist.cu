@@ -815,6 +815,11 @@ struct RunArgs {
     const int2 *nlmap, *beadmap, *lsortmap, *lcellmap;
     int n_nl, n_bead, n_lsort, n_lcell;
     int n_steps, swap_every, trial_off;   // a trial after local step s when (s + 1 + trial_off) % swap_every == 0
+    // alchemical trajectory (LAM): lambda advances by dlam after every lam_M
+    // steps, counted from lam_off; at each block's end the work term of the
+    // block is added to w (lam_M == 0: lambda fixed)
+    int lam_M, lam_off;
+    double dlam;
     RunSync *rs;
 };
 
@@ -966,6 +971,30 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                 for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x)
                     if (a.sys[q].c->nl_violp[s % 3]) a.sys[q].c->nl_builds++;
         }
+        if (LAM && a.lam_M > 0 && (a.lam_off + s + 1) % a.lam_M == 0) {
+            // the end of a lambda block (Eq. 2): each lipid's work term at the
+            // block's last coordinates, then w += dlam * their ordered sum and
+            // the next lambda, read by the next step's items after a barrier
+            for (int it = gid; it < 2 * MAX_PAIRS * a.n_sys; it += G) {
+                const SysDev &S = a.sys[it / (2 * MAX_PAIRS)];
+                const int x = it % (2 * MAX_PAIRS);
+                if (x < 2 * S.c->n_pairs) {
+                    const double wp = mdas_work_part(S, x, (S.c->nl_par + s + 1) & 1, g, tsm.sh);
+                    if (g.t == 0) S.c->w_part[x] = wp;
+                }
+                tab_sys = -1;                  // the work term used the same shared memory
+            }
+            if (!grid_barrier(a.rs, bs)) return;
+            if (threadIdx.x == 0)
+                for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x) {
+                    Counters &C = *a.sys[q].c;
+                    double sum = 0.0;
+                    for (int x = 0; x < 2 * C.n_pairs; ++x) sum += C.w_part[x];
+                    C.w += a.dlam * sum;
+                    C.lambda = (double)((a.lam_off + s + 1) / a.lam_M) * a.dlam;
+                }
+            if (pipe && !grid_barrier(a.rs, bs)) return;
+        }
         if (!pipe) {
             // the close of system q on block gridDim - 1 - q % gridDim (the
             // trial parts start on the first blocks, so both overlap)
@@ -1009,8 +1038,8 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
 }
 
 template <typename Real, bool LAM>
-static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, int trial_off, RunSync *rs,
-                              int n_blocks) {
+static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, int trial_off, int lam_M,
+                              int lam_off, double dlam, RunSync *rs, int n_blocks) {
     RunArgs a;
     a.sys = L.sys; a.n_sys = L.n_sys;
     a.nlmap = L.nlbeads->d; a.n_nl = L.nlbeads->n;
@@ -1018,6 +1047,7 @@ static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, i
     a.lsortmap = L.lsort->d; a.n_lsort = L.lsort->n;
     a.lcellmap = L.lcells->d; a.n_lcell = L.lcells->n;
     a.n_steps = n_steps; a.swap_every = swap_every; a.trial_off = trial_off; a.rs = rs;
+    a.lam_M = lam_M; a.lam_off = lam_off; a.dlam = dlam;
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)k_md_run<Real, LAM>, dim3(n_blocks), dim3(RUN_THREADS), args,
                                        RUN_GROUPS * group_smem<Real>(), L.stream);
@@ -1048,15 +1078,16 @@ int md_run_blocks(int precision, bool lambda) {
     return c;
 }
 
-cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, void *sync) {
+cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
+                          int lam_off, double dlam, void *sync) {
     const int nb = md_run_blocks(L.precision, lambda);
     if (nb <= 0) return cudaErrorCooperativeLaunchTooLarge;
     RunSync *rs = (RunSync *)sync;
     if (L.precision == 1)
-        return lambda ? run_launch<double, true>(L, n_steps, swap_every, trial_off, rs, nb)
-                      : run_launch<double, false>(L, n_steps, swap_every, trial_off, rs, nb);
-    return lambda ? run_launch<float, true>(L, n_steps, swap_every, trial_off, rs, nb)
-                  : run_launch<float, false>(L, n_steps, swap_every, trial_off, rs, nb);
+        return lambda ? run_launch<double, true>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb)
+                      : run_launch<double, false>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
+    return lambda ? run_launch<float, true>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb)
+                  : run_launch<float, false>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
 }
 
 size_t md_run_sync_bytes() { return sizeof(RunSync); }

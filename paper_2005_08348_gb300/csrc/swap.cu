@@ -366,47 +366,15 @@ __global__ void __launch_bounds__(128) k_mdas_dE(const SysDev *__restrict__ sys,
     if (threadIdx.x == 0) C.w_part[x] = s;
 }
 
-// The same sum from the pair list (valid right after an MD block): grid
-// (2 * MAX_PAIRS, n_sys); thread t of lipid x walks every other row of list
-// column (t / 2) % NL_G of changed bead t / 8 (both halves of a column by
-// threads t and t ^ 1).  Every pair within rc is in the lists, so the terms
-// are those of the 27 cells; pairs of two changed beads count once (lower id).
+// The same sum from the pair list (valid right after an MD block), one block
+// per lipid x: grid (2 * MAX_PAIRS, n_sys).
 __global__ void __launch_bounds__(128) k_mdas_dE_nl(const SysDev *__restrict__ sys) {
     const SysDev &S = sys[blockIdx.y];
-    const Params &P = *S.p;
-    Counters &C = *S.c;
-    __shared__ double sh[128];
+    __shared__ double sh[GRP / 32];
     const int x = blockIdx.x;
-    if (x >= 2 * C.n_pairs) return;
-    static_assert(NL_G == 4, "four list columns per bead");
-    const int l = C.pairs[x];
-    const int t = threadIdx.x, k = t / 8, col = (t / 2) % NL_G, half = t & 1;
-    const uint4 *cur = S.lpos + (size_t)C.nl_par * P.n;
-    double acc = 0.0;
-    if (k < P.bpl) {
-        const int i = l * P.bpl + k, ki = S.lk[i];
-        const uint4 pi = cur[ki];
-        const int oi = meta_ta(pi.w), ni = meta_tb(pi.w);
-        if (oi != ni) {
-            const int rows = S.nl_n[(size_t)ki * NL_G + col];
-            for (int r = half; r < rows; r += 2) {
-                const int kj = S.nl[(size_t)r * P.lrow + (size_t)ki * NL_G + col];
-                const uint4 pj = cur[kj];
-                const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
-                const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];
-                const float r2f = fx * fx + fy * fy + fz * fz;
-                if (!(r2f < P.rc2f) || r2f == 0.0f) continue;
-                const int oj = meta_ta(pj.w), nj = meta_tb(pj.w);
-                if (oj != nj && meta_lip(pj.w) * P.bpl + meta_k(pj.w) < i) continue;
-                const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
-                const double r2 = ex * ex + ey * ey + ez * ez;
-                if (r2 >= P.rc2) continue;
-                acc += pair_du(P, oi, oj, ni, nj, r2);
-            }
-        }
-    }
-    const double sum = block_sum(acc, sh);
-    if (threadIdx.x == 0) C.w_part[x] = sum;
+    if (x >= 2 * S.c->n_pairs) return;
+    const double w = mdas_work_part(S, x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sh);
+    if (threadIdx.x == 0) S.c->w_part[x] = w;
 }
 
 __global__ void k_mdas_accumulate(const SysDev *__restrict__ sys, double dlambda, int n_lip) {

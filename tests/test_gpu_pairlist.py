@@ -163,3 +163,22 @@ def test_trials_across_segment_boundaries():
     assert ca["trials"] == 120 + 2 == cb["trials"]
     assert np.array_equal(a["pos_u"], b["pos_u"]) and np.array_equal(a["ltype"], b["ltype"])
     assert ca["accepted"] == cb["accepted"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_alchemical_trajectory_in_one_run_matches_separate_launches(prec):
+    """The MDAS trajectory (lambda advanced and each block's work term added
+    inside the MD run) gives the same work, decision and bits in the
+    persistent kernel as with separate launches."""
+    m = synth.mcmd_small(seed=2024)
+    out = []
+    for persistent in (True, False):
+        s = mdas.System(m, precision=prec)
+        s.set_persistent(persistent)
+        s.md_steps(10, swap_every=0)
+        res = [s.alchemical_move(4, 6, 3) for _ in range(2)]
+        out.append((res, s.get_state()))
+    (ra, sa), (rb, sb) = out
+    for x, y in zip(ra, rb):
+        assert x["w"] == y["w"] and x["accepted"] == y["accepted"]
+    assert np.array_equal(sa["pos_u"], sb["pos_u"]) and np.array_equal(sa["vel"], sb["vel"])
