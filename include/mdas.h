@@ -243,6 +243,20 @@ mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_
                                 int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
                                 double *us_per_step, double *best_skin);
 
+/* The path of the alchemical moves (Sec. 2).  delta = 0 (the default): the
+ * linear path U(lambda) = (1 - lambda) U_A + lambda U_B.  delta > 0 (nm^2):
+ * the soft-core path of Eq. 4 for the Lennard-Jones part of every pair with
+ * a bead whose type changes, each end state taken at r^2 + delta (1 - w)
+ * with its weight w (1 - lambda for A, lambda for B): U_LJ(lambda) =
+ * (1 - lambda) LJ_A(r^2 + delta lambda) + lambda LJ_B(r^2 + delta (1 -
+ * lambda)), each shifted to zero at rc with the same weight; the reaction
+ * field stays linear.  (Eq. 4 is read with sigma^2 / (r^2 + ...) in the
+ * brackets, as its dimensions require.)  The work of a lambda step is then
+ * U_{lambda_k}(x_k) - U_{lambda_{k-1}}(x_k) (Eq. 2); with md_per_lambda = 0
+ * it telescopes to U_B - U_A.  Errors: MDAS_ERR_INVALID_ARG for a NULL
+ * system or a negative or non-finite delta. */
+mdas_status mdas_set_soft_core(mdas_system *s, double delta);
+
 /* Philox4x32-10 evaluated on the GPU for counters (i, c1, c2, c3), i =
  * 0..n-1, key (k0, k1): out [n*4] host. */
 mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out);

@@ -61,7 +61,7 @@ class _Sys(C.Structure):
         ("rc", C.c_double), ("eps_r", C.c_double), ("eps_rf", C.c_double),
         ("temperature", C.c_double), ("dt", C.c_double), ("tau_t", C.c_double), ("mass", C.c_double),
         ("tc_group", C.c_void_p),
-        ("seed", C.c_uint64), ("system_id", C.c_uint32),
+        ("seed", C.c_uint64), ("system_id", C.c_uint32), ("sc_delta", C.c_double),
     ]
 
 
@@ -99,7 +99,7 @@ class Oracle:
     """FP64 reference evaluation of one membrane (a `synth.Membrane` or alike)."""
 
     def __init__(self, m, tau_t=None, dt=None, temperature=None, seed=None, system_id=None,
-                 eps_rf=None, kb=None, ktheta=None):
+                 eps_rf=None, kb=None, ktheta=None, soft_core=0.0):
         self.m = m
         n = m.n_beads
         self.n = n
@@ -132,6 +132,7 @@ class Oracle:
         s.tc_group = _p(grp)
         s.seed = int(m.seed if seed is None else seed)
         s.system_id = int(m.system_id if system_id is None else system_id)
+        s.sc_delta = float(soft_core)
         self.s = s
         self.kT = KB * s.temperature
 

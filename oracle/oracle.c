@@ -54,6 +54,7 @@ typedef struct {
     double temperature, dt, tau_t, mass;
     const int *tc_group;        /* [n_beads], groups 0/1 */
     uint64_t seed; uint32_t system_id;
+    double sc_delta;            /* Eq. 4 soft-core delta (nm^2) of the alchemical path; 0: linear */
 } or_sys;
 
 /* ---------------------------------------------------------------- Philox */
@@ -226,6 +227,20 @@ static void pair_terms(const or_sys *s, int ti, int tj, double r, double *ulj, d
     *fscal = (flj + frf) / r;
 }
 
+/* Reaction field energy and -dU/dr / r of one type pair at distance r (the
+ * reaction-field terms of pair_terms). */
+static void rf_terms(const or_sys *s, int ti, int tj, double r, double *urf, double *fscal)
+{
+    double qq = s->charge[ti] * s->charge[tj];
+    double rc = s->rc;
+    double krf = (s->eps_rf <= 0.0) ? 1.0 / (2.0 * rc * rc * rc)
+                                    : (s->eps_rf - s->eps_r) / ((2.0 * s->eps_rf + s->eps_r) * rc * rc * rc);
+    double crf = 1.0 / rc + krf * rc * rc;
+    double pre = OR_COUL * qq / s->eps_r;
+    *urf = pre * (1.0 / r + krf * r * r - crf);
+    *fscal = pre * (1.0 / (r * r) - 2.0 * krf * r) / r;
+}
+
 /* ------------------------------------------------------------ cell list */
 
 /* Cell of a bead: c_d = floor(u_d * n_d / 2^32) in exact integer arithmetic;
@@ -257,8 +272,26 @@ void or_cell_dims(const or_sys *s, int ncell[3])
 
 /* ------------------------------------------------------------- energies */
 
+/* Eq. 4 soft-core Lennard-Jones of one end state with weight wl (1 - lam for
+ * A, lam for B): wl * [4 eps ((sig^2 / s)^6 - (sig^2 / s)^3)] with s = r^2 +
+ * delta (1 - wl), shifted to zero at rc with the same wl; *fscal = -dU/dr / r.
+ * (Reading: the printed sigma over r^2 is sigma^2 over r^2, so that the
+ * bracket is dimensionless and wl = 1 gives the plain potential.) */
+static void lj_soft(const or_sys *s, int ti, int tj, double r2, double wl, double *u, double *fscal)
+{
+    double eps = s->eps[ti * s->n_bt + tj], sig = s->sigma[ti * s->n_bt + tj];
+    double a = s->sc_delta * (1.0 - wl);
+    double x = sig * sig / (r2 + a), xc = sig * sig / (s->rc * s->rc + a);
+    double x3 = x * x * x, xc3 = xc * xc * xc;
+    *u = wl * (4.0 * eps * (x3 * x3 - x3) - 4.0 * eps * (xc3 * xc3 - xc3));
+    /* d/dr of (sig^2/s)^n = -2 n r (sig^2/s)^n / s */
+    *fscal = wl * 4.0 * eps * (12.0 * x3 * x3 - 6.0 * x3) / (r2 + a);
+}
+
 /* Accumulate one unordered pair (i, j) into terms and forces; bt* give the
- * A and B bead types and lam the mixing weight of U(lam) = (1-lam) U_A + lam U_B. */
+ * A and B bead types and lam the mixing weight of U(lam) = (1-lam) U_A + lam U_B.
+ * With a soft-core delta, a pair with a bead whose type changes takes its
+ * Lennard-Jones part from Eq. 4 for both end states instead. */
 static void add_pair(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
                      int i, int j, double *t, double *F)
 {
@@ -271,11 +304,25 @@ static void add_pair(const or_sys *s, const uint32_t *pu, const int *btA, const 
     double la, ra, fa, lb = 0, rb = 0, fb = 0;
     pair_terms(s, btA[i], btA[j], r, &la, &ra, &fa);
     if (lam != 0.0) pair_terms(s, btB[i], btB[j], r, &lb, &rb, &fb);
-    t[0] += (1.0 - lam) * la + lam * lb;
-    t[1] += (1.0 - lam) * ra + lam * rb;
+    double f;
+    if (s->sc_delta > 0.0 && btB && (btA[i] != btB[i] || btA[j] != btB[j])) {
+        /* the reaction field stays linear; the LJ parts come from Eq. 4 */
+        double ua, fla, ub, flb;
+        lj_soft(s, btA[i], btA[j], r2, 1.0 - lam, &ua, &fla);
+        lj_soft(s, btB[i], btB[j], r2, lam, &ub, &flb);
+        double crf_a, crf_b, frf_a, frf_b;
+        rf_terms(s, btA[i], btA[j], r, &crf_a, &frf_a);
+        rf_terms(s, btB[i], btB[j], r, &crf_b, &frf_b);
+        t[0] += ua + ub;
+        t[1] += (1.0 - lam) * crf_a + lam * crf_b;
+        f = fla + flb + (1.0 - lam) * frf_a + lam * frf_b;
+    } else {
+        t[0] += (1.0 - lam) * la + lam * lb;
+        t[1] += (1.0 - lam) * ra + lam * rb;
+        f = (1.0 - lam) * fa + lam * fb;
+    }
     t[5] += 1.0;
     if (F) {
-        double f = (1.0 - lam) * fa + lam * fb;
         for (int k = 0; k < 3; ++k) { F[3 * i + k] += f * d[k]; F[3 * j + k] -= f * d[k]; }
     }
 }
@@ -622,9 +669,15 @@ void or_mdas_move(const or_sys *s, or_state *st, int n_pairs, int n_lambda, int 
             md_step(s, st, btA, btB, lp, st->at_step, OR_TAG_AT_THERMO, use_cells, F);
             st->at_step++;
         }
-        double uA = or_energy(s, st->pos, btA, NULL, 0.0, use_cells, NULL, NULL);
-        double uB = or_energy(s, st->pos, btB, NULL, 0.0, use_cells, NULL, NULL);
-        w += ((1.0 - lk) * uA + lk * uB) - ((1.0 - lp) * uA + lp * uB);
+        if (s->sc_delta > 0.0) {
+            /* Eq. 2 as defined: U_{lam_k}(x_k) - U_{lam_{k-1}}(x_k) */
+            w += or_energy(s, st->pos, btA, btB, lk, use_cells, NULL, NULL) -
+                 or_energy(s, st->pos, btA, btB, lp, use_cells, NULL, NULL);
+        } else {
+            double uA = or_energy(s, st->pos, btA, NULL, 0.0, use_cells, NULL, NULL);
+            double uB = or_energy(s, st->pos, btB, NULL, 0.0, use_cells, NULL, NULL);
+            w += ((1.0 - lk) * uA + lk * uB) - ((1.0 - lp) * uA + lp * uB);
+        }
     }
     uint32_t wd[4];
     draw(s, 0, st->move, OR_TAG_MDAS_ACC, 0, wd);

@@ -30,15 +30,7 @@ struct Batch {
     bool persistent = true;       // MD in the persistent kernel (else separate kernel launches)
     size_t cap_sys = 0, cap_beads = 0, cap_cells = 0, cap_sort = 0;   // device capacity (refillable batches)
     size_t cap_nlb = 0, cap_lc = 0, cap_ls = 0;
-    LaunchCtx ctx() const {
-        LaunchCtx L;
-        L.sys = dsys; L.n_sys = (int)sys.size();
-        L.beads = &beads; L.cells = &cells; L.sortcells = &sortcells; L.syss = &syss;
-        L.nlbeads = &nlbeads; L.lcells = &lcells; L.lsort = &lsort;
-        L.precision = precision; L.stream = stream; L.max_bead_blocks = max_bead_blocks;
-        L.bticket = bticket;
-        return L;
-    }
+    LaunchCtx ctx() const;
 };
 
 std::string g_last_error;
@@ -108,6 +100,20 @@ struct mdas_system {
     long long pair_launches = 0;
     long long kernel_launches = 0;   // kernel launches (graph kernel nodes included) that advanced this system
 };
+
+namespace {
+LaunchCtx Batch::ctx() const {
+    LaunchCtx L;
+    L.sys = dsys; L.n_sys = (int)sys.size();
+    L.beads = &beads; L.cells = &cells; L.sortcells = &sortcells; L.syss = &syss;
+    L.nlbeads = &nlbeads; L.lcells = &lcells; L.lsort = &lsort;
+    L.precision = precision; L.stream = stream; L.max_bead_blocks = max_bead_blocks;
+    L.bticket = bticket;
+    L.soft = false;
+    for (auto *x : sys) L.soft = L.soft || x->hp.sc_delta > 0.0;
+    return L;
+}
+}  // namespace
 
 namespace {
 
@@ -387,7 +393,7 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     for (auto *x : b.sys) tm.on = tm.on || x->timing;
     for (auto *x : b.sys) x->cells_valid = false;
     LaunchCtx L = b.ctx();
-    const bool persistent = b.persistent && md_run_blocks(b.precision, lambda) > 0;
+    const bool persistent = b.persistent && md_run_blocks(b.precision, !lambda ? 0 : L.soft ? 2 : 1) > 0;
     // segments of at most MAX_DRAW_STEPS - 1 steps (the precomputed thermostat
     // variates); a segment starting at step k0 has its trials after local
     // steps s with (k0 + s + 1) % swap_every == 0
@@ -420,8 +426,9 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
             if (trial && (k0 + k + 1) % swap_every == 0) { launch_trial_nl(L); ++launches; }
             if (lam_M > 0 && (k0 + k + 1) % lam_M == 0) {
                 // the end of a lambda block: its work term, then the next lambda
-                launch_mdas_dE_nl(L, dlam);
-                launch_mdas_set_lambda(L, (double)((k0 + k + 1) / lam_M) * dlam, 1);
+                const long long blk = (k0 + k + 1) / lam_M;       // lambda blocks done
+                launch_mdas_dE_nl(L, (double)(blk - 1) * dlam, (double)blk * dlam, dlam);
+                launch_mdas_set_lambda(L, (double)blk * dlam, 1);
                 launches += 3;
             }
         }
@@ -1228,6 +1235,18 @@ mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint
 mdas_status mdas_set_kernel_timing(mdas_system *s, int32_t enable) {
     if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_kernel_timing: NULL system");
     s->timing = enable != 0;
+    return MDAS_OK;
+}
+
+mdas_status mdas_set_soft_core(mdas_system *s, double delta) {
+    if (!s || !(delta >= 0.0) || !std::isfinite(delta))
+        return fail(s, MDAS_ERR_INVALID_ARG, "set_soft_core: delta must be finite and >= 0");
+    s->hp.sc_delta = delta;
+    s->hp.sc_deltaf = (float)delta;
+    Params *dp = const_cast<Params *>(s->hs.p);
+    CK(cudaMemcpyAsync(&dp->sc_delta, &s->hp.sc_delta, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&dp->sc_deltaf, &s->hp.sc_deltaf, sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     return MDAS_OK;
 }
 

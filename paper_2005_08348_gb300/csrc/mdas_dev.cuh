@@ -72,6 +72,8 @@ struct Params {
     unsigned long long lcwu[3];        // floor(2^32 / ln_d): list-build cell width in fixed-point units
     int lcap, lrow;                    // entries per bead (NL_G columns of lcap / NL_G rows), row stride
     int mark_words;                    // 32-bit words of one step-item bitmap (one bit per NL_BEADS list slots)
+    double sc_delta;                   // Eq. 4 soft-core delta (nm^2) of the alchemical path, 0: linear path
+    float sc_deltaf;
     double rl, rl2;
     float rl2f;                        // rl^2 rounded up (build cull)
     float dmax2f;                      // squared displacement since the build that invalidates the list
@@ -233,6 +235,7 @@ struct LaunchCtx {
     cudaStream_t stream;
     int max_bead_blocks;
     unsigned int *bticket;    // device: last-block ticket over the whole batch
+    bool soft;                // a system of the batch takes the soft-core alchemical path
 };
 
 cudaError_t setup_kernels();
@@ -249,7 +252,7 @@ void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
 void launch_thermostat(const LaunchCtx &L);
 void launch_nl_build(const LaunchCtx &L);
 void launch_nl_step(const LaunchCtx &L, bool lambda);
-int md_run_blocks(int precision, bool lambda);
+int md_run_blocks(int precision, int mode);   // mode: 0 plain MD, 1 linear alchemical path, 2 soft-core path
 cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
                           int lam_off, double dlam, void *sync);
 size_t md_run_sync_bytes();
@@ -268,7 +271,8 @@ void launch_mdas_restore(const LaunchCtx &L);
 void launch_snapshot(const LaunchCtx &L);
 void launch_delta_energy(const LaunchCtx &L, int n_changed_lipids);
 void launch_mutation_trials(const LaunchCtx &L, int n);
-void launch_mdas_dE_nl(const LaunchCtx &L, double dlambda);   // the work term from the pair list (valid lists)
+// the work term of the lambda step l0 -> l1 from the pair list (valid lists)
+void launch_mdas_dE_nl(const LaunchCtx &L, double l0, double l1, double dlambda);
 void launch_head_rdf(const SysDev *dsys, int n_lip, int lt_sel, int head_k, double r_max, int n_bins, uint4 *info,
                      int *n_heads, unsigned long long *hist, cudaStream_t st);
 constexpr int RDF_MAX_BINS = 1024;     // bins of one head-bead distribution

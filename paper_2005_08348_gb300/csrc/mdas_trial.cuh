@@ -215,13 +215,42 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
     g.sync();
 }
 
+// Eq. 4 soft-core Lennard-Jones of one type pair and end state with weight
+// wl (1 - lambda for the A state, lambda for B), shifted to zero at rc with
+// the same wl: wl * [C12 / s^6 - C6 / s^3 - (the same at rc)], s = r^2 +
+// delta (1 - wl).  FP64.
+__device__ __forceinline__ double lj_soft(const Params &P, int x, double r2, double wl) {
+    const double a = P.sc_delta * (1.0 - wl);
+    const double i = 1.0 / (r2 + a), ic = 1.0 / (P.rc2 + a);
+    const double i3 = i * i * i, ic3 = ic * ic * ic;
+    return wl * ((P.c12[x] * i3 - P.c6[x]) * i3 - (P.c12[x] * ic3 - P.c6[x]) * ic3);
+}
+
+// Work of one pair over the lambda step l0 -> l1 on the soft-core path:
+// U_l1 - U_l0 with the Lennard-Jones parts from Eq. 4 for both end states and
+// the reaction field linear in lambda.
+__device__ __forceinline__ double pair_dw_soft(const Params &P, int oi, int oj, int ni, int nj, double r2,
+                                               double l0, double l1) {
+    const int xo = oi * 16 + oj, xn = ni * 16 + nj;
+    double ri = (double)rsqrtf((float)r2);
+    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+    const double lj = (lj_soft(P, xo, r2, 1.0 - l1) + lj_soft(P, xn, r2, l1)) -
+                      (lj_soft(P, xo, r2, 1.0 - l0) + lj_soft(P, xn, r2, l0));
+    return lj + (l1 - l0) * (P.qq[xn] - P.qq[xo]) * (ri + P.krf * r2 - P.crf);
+}
+
 // MDAS work term of lipid x of the move (Eq. 2: U_B - U_A at the current
 // coordinates, over the pairs within rc that involve a bead whose A and B
 // types differ, pairs of two such beads once, by the lower id) from the pair
 // list, positions in buffer par; one 128-thread group: thread t walks every
 // other row of list column (t / 2) % NL_G of bead t / 8 (both halves of a
 // column by threads t and t ^ 1); the group sum in fixed order.
-__device__ inline double mdas_work_part(const SysDev &S, int x, int par, const Grp &g, double *sh) {
+//
+// On the soft-core path (sc_delta > 0) a pair adds its work over the lambda
+// step l0 -> l1 instead (pair_dw_soft), which the caller adds to w as it is.
+__device__ inline double mdas_work_part(const SysDev &S, int x, int par, const Grp &g, double *sh, double l0,
+                                        double l1) {
     const Params &P = *S.p;
     const Counters &C = *S.c;
     static_assert(NL_G == 4 && GRP == 128, "four list columns per bead, 128 threads");
@@ -247,7 +276,7 @@ __device__ inline double mdas_work_part(const SysDev &S, int x, int par, const G
                 const double ex = (double)ix * P.qs[0], ey = (double)iy * P.qs[1], ez = (double)iz * P.qs[2];
                 const double r2 = ex * ex + ey * ey + ez * ez;
                 if (r2 >= P.rc2) continue;
-                acc += pair_du(P, oi, oj, ni, nj, r2);
+                acc += P.sc_delta > 0.0 ? pair_dw_soft(P, oi, oj, ni, nj, r2, l0, l1) : pair_du(P, oi, oj, ni, nj, r2);
             }
         }
     }

@@ -404,7 +404,7 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
 // read from buffer par, written to buffer par ^ 1 and to the id-ordered
 // array.  The item's kinetic energy goes to an integer slot; a bead that
 // moved farther than the list allows sets *viol.
-template <typename Real, bool LAM>
+template <typename Real, int LAM>
 __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const Grp &g, StepSmem<Real> &sm,
                              bool load_tables = true, const PipeWait *pw = nullptr) {
     using V4 = typename Vec4<Real>::T;
@@ -465,6 +465,8 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
     const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
     const Real lam = LAM ? (Real)C.lambda : (Real)0;
+    // LAM: 0 no alchemical path, 1 linear path, 2 soft-core path (Eq. 4)
+    const Real dsc = LAM == 2 ? (F32 ? (Real)P.sc_deltaf : (Real)P.sc_delta) : (Real)0;
     const float qs0 = P.qsf[0], qs1 = P.qsf[1], qs2 = P.qsf[2];
     int tai = meta_ta(pi.w) * 16, tbi = meta_tb(pi.w) * 16;
     Real ax = 0, ay = 0, az = 0;
@@ -492,8 +494,9 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         const uint32_t mj = pj.w;
         const V4 ca = sm.tab[tai + meta_ta(mj)];
         Real f12 = ca.x, f6 = ca.y, qq = ca.z;
+        V4 cb = ca;
         if (LAM) {
-            const V4 cb = sm.tab[tbi + meta_tb(mj)];
+            cb = sm.tab[tbi + meta_tb(mj)];
             f12 = fmr((Real)1 - lam, f12, lam * cb.x);
             f6 = fmr((Real)1 - lam, f6, lam * cb.y);
             qq = fmr((Real)1 - lam, qq, lam * cb.z);
@@ -515,6 +518,15 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             r6inv = r2inv * r2inv * r2inv;
         }
         Real fs = fmr(fmr(f12, r6inv, -f6) * r6inv, r2inv, qq * fmr(rinv, r2inv, -krf2));
+        if (LAM == 2 && (tai != tbi || meta_ta(mj) != meta_tb(mj))) {
+            // Eq. 4 path for a pair with a changing bead: each end state's
+            // Lennard-Jones at s = r^2 + delta (1 - its weight), force/r =
+            // s^-4 (12 C12 s^-3 - 6 C6); the reaction field stays linear
+            const Real ia = (Real)1 / (r2c + dsc * lam), ib = (Real)1 / (r2c + dsc * ((Real)1 - lam));
+            const Real ia3 = ia * ia * ia, ib3 = ib * ib * ib;
+            const Real lja = fmr(ca.x, ia3, -ca.y) * (ia3 * ia), ljb = fmr(cb.x, ib3, -cb.y) * (ib3 * ib);
+            fs = fmr((Real)1 - lam, lja, fmr(lam, ljb, qq * fmr(rinv, r2inv, -krf2)));
+        }
         fs = in ? fs : (Real)0;
         ax = fmr(fs, dx, ax); ay = fmr(fs, dy, ay); az = fmr(fs, dz, az);
     };
@@ -730,7 +742,7 @@ void launch_nl_build(const LaunchCtx &L) {
 
 // One step of every system; the last block of a system (a ticket, no
 // waiting) closes the step and flags the list stale after a violation.
-template <typename Real, bool LAM>
+template <typename Real, int LAM>
 __global__ void __launch_bounds__(GRP, 8) k_nl_step(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
     __shared__ StepSmem<Real> sm;
     __shared__ int last;
@@ -756,7 +768,7 @@ __global__ void __launch_bounds__(GRP, 8) k_nl_step(const SysDev *__restrict__ s
     }
 }
 
-template <typename Real, bool LAM>
+template <typename Real, int LAM>
 static void nl_step_launch(const LaunchCtx &L) {
     k_nl_step<Real, LAM><<<L.nlbeads->n, GRP, 0, L.stream>>>(L.sys, L.nlbeads->d);
 }
@@ -764,9 +776,13 @@ static void nl_step_launch(const LaunchCtx &L) {
 void launch_nl_step(const LaunchCtx &L, bool lambda) {
     static_assert(NL_BEADS * NL_G == GRP, "a step item is one group");
     if (L.precision == 1) {
-        if (lambda) nl_step_launch<double, true>(L); else nl_step_launch<double, false>(L);
+        if (!lambda) nl_step_launch<double, 0>(L);
+        else if (L.soft) nl_step_launch<double, 2>(L);
+        else nl_step_launch<double, 1>(L);
     } else {
-        if (lambda) nl_step_launch<float, true>(L); else nl_step_launch<float, false>(L);
+        if (!lambda) nl_step_launch<float, 0>(L);
+        else if (L.soft) nl_step_launch<float, 2>(L);
+        else nl_step_launch<float, 1>(L);
     }
 }
 
@@ -884,7 +900,7 @@ __device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &
 // (close and trial after the step's barrier, then a second barrier), which
 // runs otherwise.  Per step: items, barrier, list builds called for by the
 // step's displacements.
-template <typename Real, bool LAM>
+template <typename Real, int LAM>
 __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
     extern __shared__ __align__(16) unsigned char dsm[];
     const int group = threadIdx.x / GRP;
@@ -975,11 +991,13 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
             // the end of a lambda block (Eq. 2): each lipid's work term at the
             // block's last coordinates, then w += dlam * their ordered sum and
             // the next lambda, read by the next step's items after a barrier
+            const int blk = (a.lam_off + s + 1) / a.lam_M;   // lambda blocks done
+            const double l0 = (double)(blk - 1) * a.dlam, l1 = (double)blk * a.dlam;
             for (int it = gid; it < 2 * MAX_PAIRS * a.n_sys; it += G) {
                 const SysDev &S = a.sys[it / (2 * MAX_PAIRS)];
                 const int x = it % (2 * MAX_PAIRS);
                 if (x < 2 * S.c->n_pairs) {
-                    const double wp = mdas_work_part(S, x, (S.c->nl_par + s + 1) & 1, g, tsm.sh);
+                    const double wp = mdas_work_part(S, x, (S.c->nl_par + s + 1) & 1, g, tsm.sh, l0, l1);
                     if (g.t == 0) S.c->w_part[x] = wp;
                 }
                 tab_sys = -1;                  // the work term used the same shared memory
@@ -990,8 +1008,8 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                     Counters &C = *a.sys[q].c;
                     double sum = 0.0;
                     for (int x = 0; x < 2 * C.n_pairs; ++x) sum += C.w_part[x];
-                    C.w += a.dlam * sum;
-                    C.lambda = (double)((a.lam_off + s + 1) / a.lam_M) * a.dlam;
+                    C.w += a.sys[q].p->sc_delta > 0.0 ? sum : a.dlam * sum;
+                    C.lambda = (double)blk * a.dlam;
                 }
             if (pipe && !grid_barrier(a.rs, bs)) return;
         }
@@ -1037,7 +1055,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
         }
 }
 
-template <typename Real, bool LAM>
+template <typename Real, int LAM>
 static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, int trial_off, int lam_M,
                               int lam_off, double dlam, RunSync *rs, int n_blocks) {
     RunArgs a;
@@ -1053,7 +1071,7 @@ static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, i
                                        RUN_GROUPS * group_smem<Real>(), L.stream);
 }
 
-template <typename Real, bool LAM>
+template <typename Real, int LAM>
 static cudaError_t run_setup(int *blocks_per_sm) {
     const size_t smem = RUN_GROUPS * group_smem<Real>();
     cudaError_t e = cudaFuncSetAttribute(k_md_run<Real, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1063,16 +1081,18 @@ static cudaError_t run_setup(int *blocks_per_sm) {
 
 // Blocks of the persistent kernel on this device: one per SM when a block
 // fits on an SM, else 0 (then the separate kernels are used).
-int md_run_blocks(int precision, bool lambda) {
-    static int cache[2][2] = {{-1, -1}, {-1, -1}};
-    int &c = cache[precision == 1][lambda ? 1 : 0];
+int md_run_blocks(int precision, int mode) {
+    static int cache[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+    int &c = cache[precision == 1][mode];
     if (c >= 0) return c;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
-    if (precision == 1) e = lambda ? run_setup<double, true>(&per) : run_setup<double, false>(&per);
-    else e = lambda ? run_setup<float, true>(&per) : run_setup<float, false>(&per);
+    if (precision == 1)
+        e = mode == 2 ? run_setup<double, 2>(&per) : mode == 1 ? run_setup<double, 1>(&per) : run_setup<double, 0>(&per);
+    else
+        e = mode == 2 ? run_setup<float, 2>(&per) : mode == 1 ? run_setup<float, 1>(&per) : run_setup<float, 0>(&per);
     c = (e == cudaSuccess && per >= 1) ? sms : 0;
     cudaGetLastError();
     return c;
@@ -1080,14 +1100,18 @@ int md_run_blocks(int precision, bool lambda) {
 
 cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
                           int lam_off, double dlam, void *sync) {
-    const int nb = md_run_blocks(L.precision, lambda);
+    const int mode = !lambda ? 0 : L.soft ? 2 : 1;
+    const int nb = md_run_blocks(L.precision, mode);
     if (nb <= 0) return cudaErrorCooperativeLaunchTooLarge;
     RunSync *rs = (RunSync *)sync;
-    if (L.precision == 1)
-        return lambda ? run_launch<double, true>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb)
-                      : run_launch<double, false>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
-    return lambda ? run_launch<float, true>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb)
-                  : run_launch<float, false>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
+    if (L.precision == 1) {
+        if (mode == 2) return run_launch<double, 2>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
+        if (mode == 1) return run_launch<double, 1>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
+        return run_launch<double, 0>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
+    }
+    if (mode == 2) return run_launch<float, 2>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
+    if (mode == 1) return run_launch<float, 1>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
+    return run_launch<float, 0>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
 }
 
 size_t md_run_sync_bytes() { return sizeof(RunSync); }

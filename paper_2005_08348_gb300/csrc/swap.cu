@@ -368,16 +368,18 @@ __global__ void __launch_bounds__(128) k_mdas_dE(const SysDev *__restrict__ sys,
 
 // The same sum from the pair list (valid right after an MD block), one block
 // per lipid x: grid (2 * MAX_PAIRS, n_sys).
-__global__ void __launch_bounds__(128) k_mdas_dE_nl(const SysDev *__restrict__ sys) {
+__global__ void __launch_bounds__(128) k_mdas_dE_nl(const SysDev *__restrict__ sys, double l0, double l1) {
     const SysDev &S = sys[blockIdx.y];
     __shared__ double sh[GRP / 32];
     const int x = blockIdx.x;
     if (x >= 2 * S.c->n_pairs) return;
-    const double w = mdas_work_part(S, x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sh);
+    const double w = mdas_work_part(S, x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sh, l0, l1);
     if (threadIdx.x == 0) S.c->w_part[x] = w;
 }
 
-__global__ void k_mdas_accumulate(const SysDev *__restrict__ sys, double dlambda, int n_lip) {
+// w += dlambda * (sum of the parts), or the sum itself when the parts hold
+// the step's work already (soft-core path from the pair list, as_is)
+__global__ void k_mdas_accumulate(const SysDev *__restrict__ sys, double dlambda, int n_lip, int as_is) {
     const SysDev &S = sys[blockIdx.x];
     Counters &C = *S.c;
     if (threadIdx.x != 0) return;
@@ -386,19 +388,19 @@ __global__ void k_mdas_accumulate(const SysDev *__restrict__ sys, double dlambda
     double s = 0.0;
     for (int x = 0; x < nl; ++x) s += C.w_part[x];
     if (to_result) S.result[8] = s;
-    else C.w += dlambda * s;
+    else C.w += as_is && S.p->sc_delta > 0.0 ? s : dlambda * s;
 }
 
-void launch_mdas_dE_nl(const LaunchCtx &L, double dlambda) {
+void launch_mdas_dE_nl(const LaunchCtx &L, double l0, double l1, double dlambda) {
     dim3 g(2 * MAX_PAIRS, L.n_sys);
-    k_mdas_dE_nl<<<g, 128, 0, L.stream>>>(L.sys);
-    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, dlambda, -1);
+    k_mdas_dE_nl<<<g, 128, 0, L.stream>>>(L.sys, l0, l1);
+    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, dlambda, -1, 1);
 }
 
 void launch_mdas_dE(const LaunchCtx &L, double dlambda) {
     dim3 g(2 * MAX_PAIRS, L.n_sys);
     k_mdas_dE<<<g, 128, 0, L.stream>>>(L.sys, -1);
-    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, dlambda, -1);
+    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, dlambda, -1, 0);
 }
 
 // Eq. 3: accept with min(1, exp(-w/kT)), i.e. w + kT ln u <= 0, u from
@@ -498,7 +500,7 @@ void launch_delta_energy(const LaunchCtx &L, int n) {
     k_mark_b<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n, 0);
     dim3 g(2 * MAX_PAIRS, L.n_sys);
     k_mdas_dE<<<g, 128, 0, L.stream>>>(L.sys, n);
-    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, 0.0, n);
+    k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, 0.0, n, 0);
     k_mark_b<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n, 1);
 }
 

@@ -87,7 +87,7 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_pair_kernel_time", "mdas_set_persistent", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
-           "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials"]
+           "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core"]
 
 
 def library_path() -> str:
@@ -324,6 +324,10 @@ class System:
 
     def set_kernel_timing(self, on=True):
         self._ck(lib().mdas_set_kernel_timing(self._ptr, int(bool(on))))
+
+    def set_soft_core(self, delta):
+        """Alchemical path: 0 linear, delta > 0 (nm^2) Eq. 4 soft core (mdas_set_soft_core)."""
+        self._ck(lib().mdas_set_soft_core(self._ptr, C.c_double(delta)))
 
     def set_persistent(self, on=True):
         """MD in the persistent kernel (default) or as separate kernel launches."""

@@ -519,3 +519,53 @@ def test_leaflets_and_interleaflet_pairs():
         pairs = mixing.interleaflet_pairs(m.lipid_type, leaf, 5, seed=1)
         assert len(pairs) == 5 and len(set(pairs.ravel())) == 10
         assert all(leaf[a] == 0 and leaf[b] == 1 and m.lipid_type[a] != m.lipid_type[b] for a, b in pairs)
+
+
+# ---------------------------------------------------------------- soft-core alchemical path
+def _sc_system():
+    m = synth.tiny(seed=21)
+    ltB = m.lipid_type.copy()
+    ltB[0], ltB[1] = m.lipid_type[1], m.lipid_type[0]
+    ltB[2], ltB[3] = 1 - ltB[2], 1 - ltB[3]
+    return m, ltB
+
+
+@pytest.mark.parametrize("lam", [0.25, 0.6])
+def test_soft_core_forces_match_energy_gradient(lam):
+    """Eq. 4 path (delta 0.05 nm^2): central finite differences of U(lambda)
+    match F = -grad U (1e-6 rel), pairs with a changed bead included."""
+    m, ltB = _sc_system()
+    o = oracle.Oracle(m, soft_core=0.05)
+    btA, btB = o.bead_types(m.lipid_type), o.bead_types(ltB)
+    _, F = o.energy(m.pos_u, btA=btA, btB=btB, lam=lam)
+    rng = np.random.default_rng(5)
+    k = 1 << 10
+    worst = 0.0
+    frms = np.sqrt((F * F).sum(1).mean())
+    changed = np.flatnonzero(btA != btB)
+    for i in list(changed) + list(rng.choice(m.n_beads, 12, replace=False)):
+        for d in range(3):
+            h = k * m.box[d] / 2 ** 32
+            p, q = m.pos_u.copy(), m.pos_u.copy()
+            p[i, d] += np.uint32(k)
+            q[i, d] -= np.uint32(k)
+            up = o.energy(p, btA=btA, btB=btB, lam=lam, forces=False)[0]["total"]
+            um = o.energy(q, btA=btA, btB=btB, lam=lam, forces=False)[0]["total"]
+            worst = max(worst, abs(-(up - um) / (2 * h) - F[i, d]) / max(abs(F[i, d]), frms))
+    assert worst < 1e-6
+
+
+def test_soft_core_end_states_and_vanishing_delta():
+    """At lambda 0 and 1 the soft-core path is the A and B energy; it differs
+    in between; as delta -> 0 it becomes the linear path (1-l) U_A + l U_B."""
+    m, ltB = _sc_system()
+    lin, sc, tiny = oracle.Oracle(m), oracle.Oracle(m, soft_core=0.05), oracle.Oracle(m, soft_core=1e-12)
+    btA, btB = lin.bead_types(m.lipid_type), lin.bead_types(ltB)
+    e = lambda o, l: o.energy(m.pos_u, btA=btA, btB=btB, lam=l, forces=False)[0]["total"]
+    eA = lin.energy(m.pos_u, btA=btA, forces=False)[0]["total"]
+    eB = lin.energy(m.pos_u, btA=btB, forces=False)[0]["total"]
+    assert abs(e(sc, 0.0) - eA) <= 1e-9 * abs(eA)
+    assert abs(e(sc, 1.0) - eB) <= 1e-9 * abs(eB)
+    for l in (0.3, 0.7):
+        assert abs(e(tiny, l) - ((1 - l) * eA + l * eB)) <= 1e-9 * abs(eA)
+        assert abs(e(sc, l) - e(lin, l)) > 1e-6
