@@ -12,8 +12,9 @@
  *     call returns only after its results are on the host (synchronous).
  *   - Every call returns an mdas_status; on failure mdas_last_error() holds a
  *     one-line message.  A system that reported MDAS_ERR_UNSTABLE (a
- *     non-finite velocity, a cell or neighbourhood overflow) refuses further
- *     dynamics until mdas_set_state() installs a new state.
+ *     non-finite velocity, a cell or neighbourhood overflow) or
+ *     MDAS_ERR_TIMEOUT (a device-side wait of the persistent MD kernel gave
+ *     up) refuses further dynamics until mdas_set_state() installs a state.
  *   - Device-side waits are bounded; no call traps or hangs the GPU.
  *
  * Positions are stored as unsigned 32-bit fractions of the box edge,
@@ -120,6 +121,17 @@ typedef struct {
     double *vel;                       /* [n*3] nm/ps, or NULL */
     int32_t *lipid_type;               /* [n_lipids], or NULL */
     uint64_t step, trial, move, at_step;   /* Philox counters of MD steps, trials, moves, AT steps */
+    /* Exact continuation (optional; zero-initialised members keep the plain
+     * restore).  The pair list is built at earlier positions than the current
+     * ones and the thermostat reads the kinetic energy the last MD step left in
+     * fixed point; with both carried, MD resumed from a saved state repeats
+     * the uninterrupted run bit for bit (exchange trials counted from the
+     * start of each call: resume at a multiple of swap_every). */
+    uint32_t *list_ref;                /* [n*3] fixed-point positions the pair list was built at, bead id order, or NULL */
+    int32_t list_valid;                /* get_state: 1 when list_ref was filled (else the list is rebuilt at the next
+                                        * MD step); set_state: rebuild the list at list_ref instead */
+    int32_t ke_valid;                  /* 1 when ke[] is the kinetic energy the last MD step left */
+    double ke[2];                      /* lipid and solvent kinetic energy, kJ/mol, as that step summed it */
 } mdas_state_view;
 
 /* Create a device-resident system from a description (Sec. 3 force field,
@@ -190,10 +202,15 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
 mdas_status mdas_delta_energy(mdas_system *s, const int32_t *lipids, const int32_t *new_types, int32_t n,
                               double *dE);
 
-/* Copy the state to host arrays (any pointer may be NULL). */
+/* Copy the state to host arrays (any pointer may be NULL); list_valid and
+ * ke_valid report whether list_ref and ke[] hold the continuation state. */
 mdas_status mdas_get_state(const mdas_system *s, mdas_state_view *out);
 
-/* Install a state from host arrays; clears MDAS_ERR_UNSTABLE. */
+/* Install a state from host arrays; clears MDAS_ERR_UNSTABLE.  With
+ * list_valid, the pair list is built at list_ref (which must lie within half
+ * the list skin of pos, per bead and axis, as get_state leaves them: else
+ * MDAS_ERR_INVALID_ARG); with ke_valid, the first thermostat factor takes
+ * ke[] instead of summing the restored velocities. */
 mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in);
 
 /* The cell list of the current positions: sorted_ids [n_beads] (bead ids by
@@ -369,6 +386,15 @@ double mdas_server_clock(const mdas_server *sv);
 /* Device bytes a system of this description occupies (the server's admission
  * charge); 0 for an invalid description. */
 size_t mdas_system_footprint(const mdas_system_desc *d);
+
+/* Health check of the failure path: one block of the persistent MD kernel's
+ * grid barrier waits on this system's barrier state for an arrival that never
+ * comes.  The wait gives up after its poll limit (seconds), the abort reaches
+ * the system as it would from a stalled MD launch, the barrier state is
+ * cleared, and the call returns MDAS_ERR_TIMEOUT; the system then refuses
+ * dynamics until mdas_set_state().  Positions and velocities are untouched
+ * and the CUDA context stays usable.  MDAS_ERR_INVALID_ARG for NULL. */
+mdas_status mdas_wait_timeout_probe(mdas_system *s);
 
 const char *mdas_last_error(const mdas_system *s);
 const char *mdas_status_string(mdas_status st);

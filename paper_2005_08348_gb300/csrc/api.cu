@@ -334,7 +334,9 @@ mdas_status check_err(mdas_system *s, Batch &b) {
         if (err & ERR_CELL_OVERFLOW) why += " a cell holds more beads than its capacity;";
         if (err & ERR_TIMEOUT) why += " bounded wait expired;";
         if (err & ERR_ROUNDS) why += " exchange rounds exhausted;";
-        return fail(s, MDAS_ERR_UNSTABLE, "unstable:" + why);
+        // a wait that gave up left the state partly advanced: refused like an
+        // unstable one, reported as the timeout it was
+        return fail(s, (err & ERR_TIMEOUT) ? MDAS_ERR_TIMEOUT : MDAS_ERR_UNSTABLE, "unstable:" + why);
     }
     return MDAS_OK;
 }
@@ -1029,12 +1031,50 @@ mdas_status mdas_get_state(const mdas_system *cs, mdas_state_view *out) {
         }
     }
     out->step = c.step; out->trial = c.trial; out->move = c.move; out->at_step = c.at_step;
+    // the continuation state: the positions the pair list was built at (kept
+    // in list order on the device) and the kinetic energy of the last step
+    out->list_valid = 0;
+    if (out->list_ref && !c.nl_stale && !c.nl_viol) {
+        std::vector<uint4> xr(n);
+        std::vector<int> lk(n);
+        CK(cudaMemcpyAsync(xr.data(), s->hs.xref, 16ull * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(lk.data(), s->hs.lk, 4ull * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        for (int i = 0; i < n; ++i) {
+            const uint4 r = xr[lk[i]];
+            out->list_ref[3 * i] = r.x; out->list_ref[3 * i + 1] = r.y; out->list_ref[3 * i + 2] = r.z;
+        }
+        out->list_valid = 1;
+    }
+    out->ke_valid = c.ke_fresh;
+    out->ke[0] = c.ke_fresh ? c.ke_total[0] : 0.0;
+    out->ke[1] = c.ke_fresh ? c.ke_total[1] : 0.0;
     return MDAS_OK;
+}
+
+mdas_status mdas_wait_timeout_probe(mdas_system *s) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "wait_timeout_probe: NULL system");
+    Batch &b = *s->solo;
+    CK(launch_barrier_stall(b.rsync, b.stream));
+    k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
+    CK(cudaGetLastError());
+    return check_err(s, b);
+}
+
+// After a list build at the saved build positions: the current positions
+// (id order) into the list-order buffer the next step reads.
+__global__ void k_list_current(const SysDev S, int n, int par) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    S.lpos[(size_t)par * n + k] = S.pos[S.lid[k]];
 }
 
 mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     if (!s || !in) return fail(s, MDAS_ERR_INVALID_ARG, "set_state: NULL argument");
     const int n = s->n, nl = s->n_lip, bpl = s->bpl;
+    const bool keep_list = in->list_valid && in->list_ref;
+    if (keep_list && !in->pos_fixed && !in->pos)
+        return fail(s, MDAS_ERR_INVALID_ARG, "set_state: list_ref without positions");
     std::vector<int> lt(std::max(nl, 1));
     if (in->lipid_type) {
         for (int l = 0; l < nl; ++l)
@@ -1064,7 +1104,25 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
             pos[i].w = meta_make(s->water_bt, s->water_bt, 15, 0);
         }
     }
-    CK(cudaMemcpyAsync(s->hs.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
+    std::vector<uint4> ref;
+    if (keep_list) {
+        // every bead within half the skin of the build position (in FP64; the
+        // step's own test is tighter by 1e-4 of the square)
+        const double half = 0.5 * (s->hp.rl - s->hp.rc);
+        ref.resize(n);
+        for (int i = 0; i < n; ++i) {
+            const uint32_t r[3] = {in->list_ref[3 * i], in->list_ref[3 * i + 1], in->list_ref[3 * i + 2]};
+            const uint32_t u[3] = {pos[i].x, pos[i].y, pos[i].z};
+            double d2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double d = (double)(int32_t)(u[k] - r[k]) * s->hp.qs[k];
+                d2 += d * d;
+            }
+            if (!(d2 <= half * half)) return fail(s, MDAS_ERR_INVALID_ARG, "set_state: list_ref farther than half the skin");
+            ref[i] = make_uint4(r[0], r[1], r[2], pos[i].w);
+        }
+    }
+    CK(cudaMemcpyAsync(s->hs.pos, keep_list ? ref.data() : pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
     if (nl > 0) CK(cudaMemcpyAsync(s->hs.ltype, lt.data(), 4ull * nl, cudaMemcpyHostToDevice, s->stream));
     if (in->vel) {
         if (s->precision == MDAS_FP64) {
@@ -1086,7 +1144,20 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0; c.ke_fresh = 0; c.ke_pending = 0; c.draw_n = 0;
     memset(c.ke_slot, 0, sizeof(c.ke_slot));
     c.nl_stale = 1; c.nl_viol = 0; c.sticket = 0; c.nticket = 0;
+    if (in->ke_valid) {
+        c.ke_fresh = 1;
+        c.ke_total[0] = in->ke[0];
+        c.ke_total[1] = in->ke[1];
+    }
+    if (keep_list) c.nl_par = 0;
     CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
+    if (keep_list) {
+        // the list as it was built (same positions, same order), then the
+        // current positions in its list-order buffer
+        launch_nl_build(s->solo->ctx());
+        CK(cudaMemcpyAsync(s->hs.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
+        k_list_current<<<(n + 255) / 256, 256, 0, s->stream>>>(s->hs, n, 0);
+    }
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
     s->unstable = false;

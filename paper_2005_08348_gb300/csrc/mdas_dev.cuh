@@ -256,6 +256,9 @@ int md_run_blocks(int precision, int mode);   // mode: 0 plain MD, 1 linear alch
 cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
                           int lam_off, double dlam, void *sync);
 size_t md_run_sync_bytes();
+// one block waiting at a grid barrier of `sync` for an arrival that never
+// comes (the bounded wait expires and raises the abort word)
+cudaError_t launch_barrier_stall(void *sync, cudaStream_t stream);
 void launch_trial_nl(const LaunchCtx &L);
 void launch_energy_reduce(const LaunchCtx &L);
 

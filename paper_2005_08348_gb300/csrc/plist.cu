@@ -1116,4 +1116,17 @@ cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap
 
 size_t md_run_sync_bytes() { return sizeof(RunSync); }
 
+// One block at a grid barrier whose last arrival never comes: the wait gives
+// up after its poll limit and raises the abort word exactly as a stalled
+// persistent launch would (the failure path, exercised without a fault).
+__global__ void k_barrier_stall(RunSync *rs) {
+    BarState bs{ld_relaxed32(&rs->count) + 1u, 0u};
+    grid_barrier(rs, bs);
+}
+
+cudaError_t launch_barrier_stall(void *sync, cudaStream_t stream) {
+    k_barrier_stall<<<1, 32, 0, stream>>>(reinterpret_cast<RunSync *>(sync));
+    return cudaGetLastError();
+}
+
 }  // namespace mdas

@@ -69,7 +69,9 @@ class MoveResult(C.Structure):
 
 class StateView(C.Structure):
     _fields_ = [("pos_fixed", C.c_void_p), ("pos", C.c_void_p), ("vel", C.c_void_p), ("lipid_type", C.c_void_p),
-                ("step", C.c_uint64), ("trial", C.c_uint64), ("move", C.c_uint64), ("at_step", C.c_uint64)]
+                ("step", C.c_uint64), ("trial", C.c_uint64), ("move", C.c_uint64), ("at_step", C.c_uint64),
+                ("list_ref", C.c_void_p), ("list_valid", C.c_int32), ("ke_valid", C.c_int32),
+                ("ke", C.c_double * 2)]
 
 
 class Counters(C.Structure):
@@ -87,7 +89,8 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_pair_kernel_time", "mdas_set_persistent", "mdas_get_counters", "mdas_last_error", "mdas_status_string",
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
-           "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core"]
+           "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core",
+           "mdas_wait_timeout_probe"]
 
 
 def library_path() -> str:
@@ -286,18 +289,35 @@ class System:
         pos = np.empty((self.n, 3), np.float64)
         vel = np.empty((self.n, 3), np.float64)
         lt = np.empty(max(self.n_lipids, 1), np.int32)
-        v = StateView(_p(pu), _p(pos), _p(vel), _p(lt), 0, 0, 0, 0)
+        ref = np.empty((self.n, 3), np.uint32)
+        v = StateView(_p(pu), _p(pos), _p(vel), _p(lt), 0, 0, 0, 0, _p(ref))
         self._ck(lib().mdas_get_state(self._ptr, C.byref(v)))
         return dict(pos_u=pu, pos=pos, vel=vel, ltype=lt[: self.n_lipids].copy(), step=v.step, trial=v.trial,
-                    move=v.move, at_step=v.at_step)
+                    move=v.move, at_step=v.at_step, list_ref=ref if v.list_valid else None,
+                    ke=(v.ke[0], v.ke[1]) if v.ke_valid else None)
 
-    def set_state(self, pos_u=None, pos=None, vel=None, ltype=None, step=0, trial=0, move=0, at_step=0):
+    def set_state(self, pos_u=None, pos=None, vel=None, ltype=None, step=0, trial=0, move=0, at_step=0,
+                  list_ref=None, ke=None):
+        """Install a state.  With list_ref and ke as get_state returned them,
+        MD continues exactly as it would have from the saved state."""
         a = None if pos_u is None else np.ascontiguousarray(pos_u, np.uint32)
         b = None if pos is None else np.ascontiguousarray(pos, np.float64)
         c = None if vel is None else np.ascontiguousarray(vel, np.float64)
         d = None if ltype is None else np.ascontiguousarray(ltype, np.int32)
-        v = StateView(_p(a), _p(b), _p(c), _p(d), step, trial, move, at_step)
+        r = None if list_ref is None else np.ascontiguousarray(list_ref, np.uint32)
+        if r is not None and r.size != 3 * self.n:
+            raise ValueError("list_ref must hold n_beads x 3 fixed-point positions")
+        v = StateView(_p(a), _p(b), _p(c), _p(d), step, trial, move, at_step, _p(r), int(r is not None),
+                      int(ke is not None))
+        if ke is not None:
+            v.ke[0], v.ke[1] = float(ke[0]), float(ke[1])
         self._ck(lib().mdas_set_state(self._ptr, C.byref(v)))
+
+    def resume(self, state):
+        """set_state with everything get_state returned (an exact continuation)."""
+        self.set_state(pos_u=state["pos_u"], vel=state["vel"], ltype=state["ltype"], step=state["step"],
+                       trial=state["trial"], move=state["move"], at_step=state["at_step"],
+                       list_ref=state.get("list_ref"), ke=state.get("ke"))
 
     def cell_list(self):
         ids = np.empty(self.n, np.int32)
@@ -328,6 +348,11 @@ class System:
     def set_soft_core(self, delta):
         """Alchemical path: 0 linear, delta > 0 (nm^2) Eq. 4 soft core (mdas_set_soft_core)."""
         self._ck(lib().mdas_set_soft_core(self._ptr, C.c_double(delta)))
+
+    def wait_timeout_probe(self):
+        """Let a grid-barrier wait of the MD kernel expire (raises MdasError,
+        status "timeout"); the system then needs set_state or resume."""
+        self._ck(lib().mdas_wait_timeout_probe(self._ptr))
 
     def set_persistent(self, on=True):
         """MD in the persistent kernel (default) or as separate kernel launches."""

@@ -73,3 +73,39 @@ def test_no_cpu_fallback_in_the_product_path():
         if f.endswith(".py"):
             txt = open(os.path.join(pkg, f)).read()
             assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror of a header struct has the header's size and field
+    offsets (a C program compiled against include/mdas.h prints them)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    from paper_2005_08348_gb300 import mdas
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    trial_names = {"null": "null_trial"}
+    pairs = [(mdas.Desc, "mdas_system_desc"), (mdas.EnergyTerms, "mdas_energy_terms"),
+             (mdas.SwapStats, "mdas_swap_stats"), (mdas.MoveResult, "mdas_move_result"),
+             (mdas.StateView, "mdas_state_view"), (mdas.Counters, "mdas_counters"),
+             (mdas.Job, "mdas_job"), (mdas.JobResult, "mdas_job_result")]
+    lines, want = [], []
+    for py, cname in pairs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(C.sizeof(py))
+        for f in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f[0]}));')
+            want.append(getattr(py, f[0]).offset)
+    lines.append('printf("%zu\\n", sizeof(mdas_trial_record));')
+    want.append(mdas.TRIAL_DTYPE.itemsize)
+    for name in mdas.TRIAL_DTYPE.names:
+        lines.append(f'printf("%zu\\n", offsetof(mdas_trial_record, {trial_names.get(name, name)}));')
+        want.append(mdas.TRIAL_DTYPE.fields[name][1])
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"mdas.h\"\nint main(void) {\n"
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == want
