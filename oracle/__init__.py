@@ -75,6 +75,26 @@ class _Trial(C.Structure):
                 ("dE", C.c_double), ("u", C.c_double)]
 
 
+class _Baro(C.Structure):
+    _fields_ = [("p_ref", C.c_double), ("tau_p", C.c_double), ("beta", C.c_double), ("nst", C.c_int),
+                ("boxv", C.c_double * 3), ("M", C.c_double * 3), ("P", C.c_double * 3)]
+
+
+def barostat(p_ref=1.0, tau_p=12.0, beta=3e-4, nst=10):
+    """Parrinello-Rahman state (or_baro) at rest."""
+    b = _Baro()
+    b.p_ref, b.tau_p, b.beta, b.nst = float(p_ref), float(tau_p), float(beta), int(nst)
+    return b
+
+
+def pr_box_update(dt, box, b, P):
+    """or_pr_box_update on a copy of box; b (from barostat()) is advanced in place."""
+    bx = (C.c_double * 3)(*[float(x) for x in box])
+    pp = (C.c_double * 3)(*[float(x) for x in P])
+    lib().or_pr_box_update(C.c_double(dt), bx, C.byref(b), pp)
+    return np.array(list(bx))
+
+
 class _Move(C.Structure):
     _fields_ = [("w", C.c_double), ("u", C.c_double), ("accepted", C.c_int), ("n_pairs", C.c_int)]
 
@@ -157,6 +177,23 @@ class Oracle:
         terms = dict(lj=t[0], rf=t[1], bond=t[2], angle=t[3], total=t[4], pairs=int(t[5]))
         return terms, F
 
+    @property
+    def box(self):
+        return np.array(list(self.s.box))
+
+    @box.setter
+    def box(self, b):
+        self.s.box = (C.c_double * 3)(*[float(x) for x in b])
+
+    def pressure(self, pos_u, vel, ltype=None, cells=True):
+        """(P [bar], K, Xi [kJ/mol]) diagonals (or_pressure)."""
+        pu = _u32(pos_u).reshape(-1)
+        v = _f64(vel).reshape(-1)
+        bt = self.bead_types(self.m.lipid_type if ltype is None else ltype)
+        P, K, X = np.zeros(3), np.zeros(3), np.zeros(3)
+        lib().or_pressure(C.byref(self.s), _p(pu), _p(v), _p(bt), int(cells), _p(P), _p(K), _p(X))
+        return P, K, X
+
     def cell_dims(self):
         nc = (C.c_int * 3)()
         lib().or_cell_dims(C.byref(self.s), nc)
@@ -227,6 +264,17 @@ class Oracle:
         nt = n_steps // swap_every if swap_every > 0 else 0
         recs = (_Trial * max(nt, 1))()
         lib().or_md_steps(C.byref(self.s), C.byref(cs), int(n_steps), int(swap_every), int(cells), recs)
+        self._back(st, cs)
+        return [dict(a=r.a, b=r.b, null=bool(r.null_trial), accepted=bool(r.accepted), dE=r.dE, u=r.u)
+                for r in recs[:nt]]
+
+    def md_steps_npt(self, st, baro, n_steps, swap_every=0, cells=True):
+        """Constant-pressure MD (or_md_steps_npt): st, baro and self.box advance."""
+        cs = self._cstate(st)
+        nt = n_steps // swap_every if swap_every > 0 else 0
+        recs = (_Trial * max(nt, 1))()
+        lib().or_md_steps_npt(C.byref(self.s), C.byref(cs), C.byref(baro), int(n_steps), int(swap_every),
+                              int(cells), recs)
         self._back(st, cs)
         return [dict(a=r.a, b=r.b, null=bool(r.null_trial), accepted=bool(r.accepted), dE=r.dE, u=r.u)
                 for r in recs[:nt]]

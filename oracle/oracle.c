@@ -19,13 +19,23 @@
  *     coordinates left unchanged and only the potential parameters swapped.
  *   - Sec. 2, linear path U(lambda) = (1-lambda) U_A + lambda U_B, Eq. 2
  *     (work of the alchemical trajectory) and Eq. 3 (its acceptance).
+ *   - Sec. 3: semi-isotropic Parrinello-Rahman pressure coupling (xy and z,
+ *     1 bar, 12 ps) of a rectangular box: the pressure tensor from the
+ *     kinetic energy and the virial, the box equation of motion of
+ *     Parrinello and Rahman (J. Appl. Phys. 1981) with the barostat mass
+ *     4 pi^2 beta / (3 tau_p^2 L_max) inverse, and the particles' -M v term.
  *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
  *     Box-Muller normals, Marsaglia-Tsang gamma variates (ACM TOMS 2000).
  *
  * Readings of points the paper leaves open (listed in the design notes):
  * Delta U = U_after - U_before; eps_rf = infinity by default; only 1-2 bonded
  * pairs are excluded; every bead weighs 72 amu; the thermostat uses the
- * kinetic energy of v(t - dt/2); positions are 32-bit fractions of the box.
+ * kinetic energy of v(t - dt/2); positions are 32-bit fractions of the box
+ * (so the box rescales them without rounding); the pressure takes the
+ * kinetic energy of v(t + dt/2) and the virial of F(x(t)); the box moves every
+ * nst steps (compressibility 3e-4 / bar and nst = 10 by default, the Martini
+ * and GROMACS defaults; the paper gives neither); the alchemical trajectory
+ * of MDAS runs at the box it starts with.
  */
 #include <math.h>
 #include <stdint.h>
@@ -293,7 +303,7 @@ static void lj_soft(const or_sys *s, int ti, int tj, double r2, double wl, doubl
  * With a soft-core delta, a pair with a bead whose type changes takes its
  * Lennard-Jones part from Eq. 4 for both end states instead. */
 static void add_pair(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
-                     int i, int j, double *t, double *F)
+                     int i, int j, double *t, double *F, double *W)
 {
     if (excluded(s, i, j)) return;
     double d[3];
@@ -325,9 +335,12 @@ static void add_pair(const or_sys *s, const uint32_t *pu, const int *btA, const 
     if (F) {
         for (int k = 0; k < 3; ++k) { F[3 * i + k] += f * d[k]; F[3 * j + k] -= f * d[k]; }
     }
+    if (W) {   /* sum of d_a F_a over the pair, F = f d the force on i */
+        for (int k = 0; k < 3; ++k) W[k] += d[k] * (f * d[k]);
+    }
 }
 
-static void bonded(const or_sys *s, const uint32_t *pu, double *t, double *F)
+static void bonded(const or_sys *s, const uint32_t *pu, double *t, double *F, double *W)
 {
     double c0 = cos(s->theta0_deg * M_PI / 180.0);
     for (int l = 0; l < s->n_lipids; ++l) {
@@ -338,10 +351,12 @@ static void bonded(const or_sys *s, const uint32_t *pu, double *t, double *F)
             separation(s, pu, i, j, d);
             double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             t[2] += 0.5 * s->kb * (r - s->b0) * (r - s->b0);
+            double f = -s->kb * (r - s->b0) / r;
             if (F) {
-                double f = -s->kb * (r - s->b0) / r;
                 for (int k = 0; k < 3; ++k) { F[3 * i + k] += f * d[k]; F[3 * j + k] -= f * d[k]; }
             }
+            if (W)
+                for (int k = 0; k < 3; ++k) W[k] += d[k] * (f * d[k]);
         }
         for (int a = 0; a < s->na; ++a) {
             int i = f0 + s->angles[3 * a], j = f0 + s->angles[3 * a + 1], k = f0 + s->angles[3 * a + 2];
@@ -352,15 +367,17 @@ static void bonded(const or_sys *s, const uint32_t *pu, double *t, double *F)
             double lb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
             double c = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) / (la * lb);
             t[3] += 0.5 * s->ktheta * (c - c0) * (c - c0);
-            if (F) {
-                double pre = -s->ktheta * (c - c0);
-                for (int q = 0; q < 3; ++q) {
-                    double dci = B[q] / (la * lb) - c * A[q] / (la * la);
-                    double dck = A[q] / (la * lb) - c * B[q] / (lb * lb);
+            double pre = -s->ktheta * (c - c0);
+            for (int q = 0; q < 3; ++q) {
+                double dci = B[q] / (la * lb) - c * A[q] / (la * la);
+                double dck = A[q] / (la * lb) - c * B[q] / (lb * lb);
+                if (F) {
                     F[3 * i + q] += pre * dci;
                     F[3 * k + q] += pre * dck;
                     F[3 * j + q] -= pre * (dci + dck);
                 }
+                /* the two ends' (r_e - r_vertex)_q F_e,q; the vertex adds nothing */
+                if (W) W[q] += A[q] * (pre * dci) + B[q] * (pre * dck);
             }
         }
     }
@@ -369,17 +386,21 @@ static void bonded(const or_sys *s, const uint32_t *pu, double *t, double *F)
 /* Potential energy U(lam) and, if F != NULL, F = -grad U.
  * terms: [0] LJ, [1] RF, [2] bond, [3] angle, [4] total, [5] number of
  * in-cutoff non-excluded pairs.  use_cells = 0: all N(N-1)/2 pairs;
- * use_cells = 1: the oracle's own cell list (needs >= 3 cells per edge). */
-double or_energy(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
-                 int use_cells, double *terms, double *F)
+ * use_cells = 1: the oracle's own cell list (needs >= 3 cells per edge).
+ * W (if not NULL): W_a = sum over interacting pairs of d_a F_a (d = r_i - r_j
+ * by minimum image, F the force on i), bonds likewise, and per angle the two
+ * ends' (r_end - r_vertex)_a F_end,a; the virial is Xi_a = -W_a / 2. */
+static double energy_core(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
+                          int use_cells, double *terms, double *F, double *W)
 {
     double t[6] = {0, 0, 0, 0, 0, 0};
+    if (W) W[0] = W[1] = W[2] = 0.0;
     int n = s->n_beads;
     if (F) memset(F, 0, sizeof(double) * 3 * (size_t)n);
     if (!btB) btB = btA;
     if (!use_cells) {
         for (int i = 0; i < n; ++i)
-            for (int j = i + 1; j < n; ++j) add_pair(s, pu, btA, btB, lam, i, j, t, F);
+            for (int j = i + 1; j < n; ++j) add_pair(s, pu, btA, btB, lam, i, j, t, F, W);
     } else {
         int nc[3];
         or_cell_dims(s, nc);
@@ -397,16 +418,22 @@ double or_energy(const or_sys *s, const uint32_t *pu, const int *btA, const int 
                         int cj = (z * nc[1] + y) * nc[0] + x;
                         for (int p = start[cj]; p < start[cj + 1]; ++p) {
                             int j = sorted[p];
-                            if (j > i) add_pair(s, pu, btA, btB, lam, i, j, t, F);
+                            if (j > i) add_pair(s, pu, btA, btB, lam, i, j, t, F, W);
                         }
                     }
         }
         free(cell_of); free(sorted); free(start);
     }
-    bonded(s, pu, t, F);
+    bonded(s, pu, t, F, W);
     t[4] = t[0] + t[1] + t[2] + t[3];
     if (terms) memcpy(terms, t, sizeof(t));
     return t[4];
+}
+
+double or_energy(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
+                 int use_cells, double *terms, double *F)
+{
+    return energy_core(s, pu, btA, btB, lam, use_cells, terms, F, NULL);
 }
 
 /* --------------------------------------------------------------- swaps */
@@ -560,10 +587,10 @@ static double group_ke(const or_sys *s, const double *v, int g)
  *   v <- alpha_g v + F/m dt;  x <- x + v dt  (fixed-point, rounded to the grid).
  * counter / tag select the thermostat's Philox stream. */
 static void md_step(const or_sys *s, or_state *st, const int *btA, const int *btB, double lam,
-                    uint32_t counter, uint32_t tag, int use_cells, double *F)
+                    uint32_t counter, uint32_t tag, int use_cells, double *F, const double *M, double *W)
 {
     int n = s->n_beads;
-    or_energy(s, st->pos, btA, btB, lam, use_cells, NULL, F);
+    energy_core(s, st->pos, btA, btB, lam, use_cells, NULL, F, W);
     double alpha[2] = {1.0, 1.0};
     double kT = OR_BOLTZ * s->temperature;
     for (int g = 0; g < 2; ++g) {
@@ -576,6 +603,8 @@ static void md_step(const or_sys *s, or_state *st, const int *btA, const int *bt
         double a = alpha[s->tc_group[i]];
         for (int d = 0; d < 3; ++d) {
             double v = a * st->vel[3 * i + d] + F[3 * i + d] / s->mass * s->dt;
+            /* Parrinello-Rahman coupling of the particles to the box motion */
+            if (M) v -= s->dt * M[d] * st->vel[3 * i + d];
             st->vel[3 * i + d] = v;
             double q = s->dt * OR_TWO32 / s->box[d];
             long long k = llrint(v * q);
@@ -594,7 +623,7 @@ void or_md_steps(const or_sys *s, or_state *st, int n_steps, int swap_every, int
     int nt = 0;
     for (int k = 1; k <= n_steps; ++k) {
         or_bead_types(s, st->ltype, bt);
-        md_step(s, st, bt, NULL, 0.0, st->step, OR_TAG_THERMO, use_cells, F);
+        md_step(s, st, bt, NULL, 0.0, st->step, OR_TAG_THERMO, use_cells, F, NULL, NULL);
         st->step++;
         if (swap_every > 0 && k % swap_every == 0) {
             or_trial rec;
@@ -603,6 +632,102 @@ void or_md_steps(const or_sys *s, or_state *st, int n_steps, int swap_every, int
             if (log_out) log_out[nt] = rec;
             nt++;
         }
+    }
+    free(F); free(bt);
+}
+
+/* ------------------------------------------------------------ pressure */
+
+/* 1 kJ mol^-1 nm^-3 in bar: 10^3 J / (N_A 10^-27 m^3) / 10^5 Pa, with
+ * N_A = 6.02214076e23 mol^-1. */
+#define OR_BAR 16.6053906717
+
+/* Diagonal pressure tensor (Sec. 3 couples the box to it):
+ * P_a = 2 (K_a - Xi_a) / V, K_a = 1/2 sum m v_a^2 of the given velocities,
+ * Xi_a = -W_a / 2 the virial of the forces at positions pu (W as in
+ * energy_core), V = Lx Ly Lz; in bar.  K and Xi are returned in kJ/mol. */
+void or_pressure(const or_sys *s, const uint32_t *pu, const double *vel, const int *bt, int use_cells,
+                 double P[3], double K[3], double Xi[3])
+{
+    double W[3];
+    energy_core(s, pu, bt, NULL, 0.0, use_cells, NULL, NULL, W);
+    double V = s->box[0] * s->box[1] * s->box[2];
+    for (int a = 0; a < 3; ++a) {
+        double k = 0.0;
+        for (int i = 0; i < s->n_beads; ++i) k += 0.5 * s->mass * vel[3 * i + a] * vel[3 * i + a];
+        K[a] = k;
+        Xi[a] = -0.5 * W[a];
+        P[a] = 2.0 * (K[a] - Xi[a]) / V * OR_BAR;
+    }
+}
+
+/* Semi-isotropic Parrinello-Rahman coupling of a rectangular box (Sec. 3:
+ * the xy plane and z coupled separately to p_ref).  The box matrix h =
+ * diag(L) obeys W d2h/dt2 = V (h^T)^-1 (P - p_ref) with the barostat mass
+ * W^-1 = 4 pi^2 beta / (3 tau_p^2 L_max) (beta the compressibility, L_max
+ * the longest edge); the particles feel M = h^-1 dh/dt = diag(dL/dt / L) as
+ * dv/dt = F/m - M v, and keep their fractional coordinates as the box
+ * changes.  Both lateral edges see the mean lateral pressure (Pxx+Pyy)/2. */
+typedef struct {
+    double p_ref;      /* bar */
+    double tau_p;      /* ps */
+    double beta;       /* 1/bar */
+    int nst;           /* MD steps per box update */
+    double boxv[3];    /* dL/dt, nm/ps */
+    double M[3];       /* dL/dt / L, 1/ps */
+    double P[3];       /* pressure of the last update, bar */
+} or_baro;
+
+/* One box update over nst steps of length dt (symplectic Euler: the box
+ * velocity from the pressure P, then the edges from the new velocity), with
+ * V, L_max and 1/L_a from the box before the update. */
+void or_pr_box_update(double dt, double box[3], or_baro *b, const double P[3])
+{
+    double dtp = b->nst * dt;
+    double V = box[0] * box[1] * box[2];
+    double lmax = box[0] > box[1] ? box[0] : box[1];
+    if (box[2] > lmax) lmax = box[2];
+    double winv = 4.0 * M_PI * M_PI * b->beta / (3.0 * b->tau_p * b->tau_p * lmax);
+    double lat = 0.5 * (P[0] + P[1]);
+    double Pd[3] = {lat, lat, P[2]};
+    for (int a = 0; a < 3; ++a) b->boxv[a] += dtp * V * winv * (Pd[a] - b->p_ref) / box[a];
+    for (int a = 0; a < 3; ++a) box[a] += dtp * b->boxv[a];
+    for (int a = 0; a < 3; ++a) b->M[a] = b->boxv[a] / box[a];
+    for (int a = 0; a < 3; ++a) b->P[a] = P[a];
+}
+
+/* n_steps MD steps at constant pressure (the box of s changes).  Per step:
+ * forces and virial at x(n), the thermostat, v <- alpha v + dt (F/m - M v),
+ * x <- x + v dt; the pressure from the virial of those forces and the
+ * kinetic energy of the new velocities; the exchange trial (if due); then,
+ * after every step whose counter reaches a multiple of nst, the box update. */
+void or_md_steps_npt(or_sys *s, or_state *st, or_baro *b, int n_steps, int swap_every, int use_cells,
+                     or_trial *log_out)
+{
+    int n = s->n_beads;
+    double *F = malloc(sizeof(double) * 3 * n);
+    int *bt = malloc(sizeof(int) * n);
+    int nt = 0;
+    for (int k = 1; k <= n_steps; ++k) {
+        or_bead_types(s, st->ltype, bt);
+        double W[3];
+        md_step(s, st, bt, NULL, 0.0, st->step, OR_TAG_THERMO, use_cells, F, b->M, W);
+        st->step++;
+        double P[3];
+        double V = s->box[0] * s->box[1] * s->box[2];
+        for (int a = 0; a < 3; ++a) {
+            double kin = 0.0;
+            for (int i = 0; i < n; ++i) kin += 0.5 * s->mass * st->vel[3 * i + a] * st->vel[3 * i + a];
+            P[a] = 2.0 * (kin + 0.5 * W[a]) / V * OR_BAR;
+        }
+        if (swap_every > 0 && k % swap_every == 0) {
+            or_trial rec;
+            swap_trial(s, st->pos, st->ltype, st->trial, &rec);
+            st->trial++;
+            if (log_out) log_out[nt] = rec;
+            nt++;
+        }
+        if (b->nst > 0 && st->step % (uint32_t)b->nst == 0) or_pr_box_update(s->dt, s->box, b, P);
     }
     free(F); free(bt);
 }
@@ -666,7 +791,7 @@ void or_mdas_move(const or_sys *s, or_state *st, int n_pairs, int n_lambda, int 
     for (int k = 1; k <= n_lambda; ++k) {
         double lp = (double)(k - 1) / n_lambda, lk = (double)k / n_lambda;
         for (int m = 0; m < md_per_lambda; ++m) {
-            md_step(s, st, btA, btB, lp, st->at_step, OR_TAG_AT_THERMO, use_cells, F);
+            md_step(s, st, btA, btB, lp, st->at_step, OR_TAG_AT_THERMO, use_cells, F, NULL, NULL);
             st->at_step++;
         }
         if (s->sc_delta > 0.0) {

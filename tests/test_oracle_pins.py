@@ -569,3 +569,166 @@ def test_soft_core_end_states_and_vanishing_delta():
     for l in (0.3, 0.7):
         assert abs(e(tiny, l) - ((1 - l) * eA + l * eB)) <= 1e-9 * abs(eA)
         assert abs(e(sc, l) - e(lin, l)) > 1e-6
+
+
+# ---- semi-isotropic Parrinello-Rahman pressure coupling (Sec. 3) ----------
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_virial_is_half_the_box_derivative_of_the_energy(seed):
+    """Xi_a = 1/2 dU/d ln L_a at fixed fractional coordinates: central
+    differences of the energy under a stretch of one box edge (pairs, bonds
+    and angles all move with the box)."""
+    m = synth.tiny(n_side=3, n_water=120, seed=seed)
+    O = oracle.Oracle(m)
+    P, K, Xi = O.pressure(m.pos_u, m.vel)
+    L0 = O.box
+    # small enough that no pair crosses the cutoff within +-h (the shifted
+    # Lennard-Jones force does not vanish there)
+    r = pair_distances(m.pos_u.astype(np.float64) * (L0 / 2.0 ** 32), L0)
+    h = min(1e-6, 0.3 * float(np.min(np.abs(r / m.rc - 1.0))))
+    assert h > 1e-9
+    for a in range(3):
+        u = []
+        for sgn in (1, -1):
+            L = L0.copy()
+            L[a] *= 1 + sgn * h
+            O.box = L
+            u.append(O.energy(m.pos_u, forces=False)[0]["total"])
+        O.box = L0
+        dudlnL = (u[0] - u[1]) / (math.log(1 + h) - math.log(1 - h))
+        tol = 1e-6 * (abs(Xi[a]) + 10.0) + 1e-15 * abs(u[0]) / h
+        assert abs(dudlnL - 2 * Xi[a]) <= tol, (a, h, dudlnL, 2 * Xi[a])
+
+
+def test_virial_of_a_stretched_bond_and_a_bent_angle():
+    """One lipid alone (no partners in range): the virial is that of its
+    bonds and angles only, and still matches the box derivative."""
+    m = synth.tiny(n_side=1, n_water=0, seed=33)
+    keep = m.lipid_first_bead[:1]
+    n = 12
+    m.pos_u = m.pos_u[:n].copy()
+    m.pos = m.pos[:n].copy()
+    m.vel = m.vel[:n].copy()
+    m.lipid_first_bead = keep.copy()
+    m.lipid_type = m.lipid_type[:1].copy()
+    # stretch the lipid along x and tilt it so every bond and angle is strained
+    m.pos_u[:, 0] += (np.arange(n, dtype=np.uint32) * np.uint32(1 << 22))
+    m.pos_u[:, 2] += (np.arange(n, dtype=np.uint32) ** 2 * np.uint32(1 << 20))
+    O = oracle.Oracle(m)
+    _, _, Xi = O.pressure(m.pos_u, np.zeros_like(m.vel))
+    L0 = O.box
+    h = 1e-6
+    for a in range(3):
+        u = []
+        for sgn in (1, -1):
+            L = L0.copy()
+            L[a] *= 1 + sgn * h
+            O.box = L
+            u.append(O.energy(m.pos_u, forces=False, cells=False)[0]["total"])
+        O.box = L0
+        d = (u[0] - u[1]) / (math.log(1 + h) - math.log(1 - h))
+        assert abs(d - 2 * Xi[a]) <= 1e-6 * (abs(Xi[a]) + 1.0), (a, d, 2 * Xi[a])
+    assert np.abs(Xi).max() > 1.0
+
+
+def test_ideal_gas_pressure_in_bar():
+    """No interactions: P = n k_B T with SI constants, the velocities chosen so
+    that every axis holds 1/2 N k T exactly."""
+    m = synth.tiny(n_side=3, n_water=120, seed=34)
+    m.eps = np.zeros_like(m.eps)
+    m.charge = np.zeros_like(m.charge)
+    O = oracle.Oracle(m, kb=0.0, ktheta=0.0)
+    T = 310.0
+    R = 1.380649e-23 * 6.02214076e23 * 1e-3          # kJ / mol / K
+    v0 = math.sqrt(R * T / m.mass)                   # nm/ps
+    rng = np.random.default_rng(3)
+    vel = v0 * rng.choice([-1.0, 1.0], size=(m.n_beads, 3))
+    P, K, Xi = O.pressure(m.pos_u, vel)
+    assert np.all(Xi == 0.0)
+    V = float(np.prod(O.box)) * 1e-27                 # m^3
+    expect = m.n_beads / V * 1.380649e-23 * T / 1e5   # bar
+    assert np.allclose(P, expect, rtol=1e-9, atol=0.0), (P, expect)
+
+
+def _box_period(axis_set, tau_p, beta=4.5e-5, L0=10.0, amp=1e-4, p_ref=1.0):
+    """Period of the box coupled to a linear equation of state
+    P = p_ref - (V - V0) / (beta V0) (only the edges in axis_set move)."""
+    nst, dt = 1, tau_p / 4000.0
+    b = oracle.barostat(p_ref=p_ref, tau_p=tau_p, beta=beta, nst=nst)
+    box = np.full(3, L0)
+    for a in axis_set:
+        box[a] = L0 * (1 + amp)
+    V0 = L0 ** 3
+    t, last, ups = 0.0, box[axis_set[0]] - L0, []
+    for k in range(40000):
+        V = float(np.prod(box))
+        p = p_ref - (V - V0) / (beta * V0)
+        P = [p if a in axis_set else p_ref for a in range(3)]
+        box = oracle.pr_box_update(dt, box, b, P)
+        t += nst * dt
+        x = box[axis_set[0]] - L0
+        if last < 0 <= x:
+            ups.append(t - dt * x / (x - last))
+        last = x
+        if len(ups) == 3:
+            break
+    assert len(ups) == 3
+    return (ups[2] - ups[0]) / 2, b
+
+
+def test_pr_box_oscillation_periods():
+    """Linearised: the normal edge alone oscillates with period sqrt(3) tau_p
+    in a cubic box, the two lateral edges together with sqrt(3/2) tau_p (the
+    barostat mass W^-1 = 4 pi^2 beta / (3 tau_p^2 L_max)); an isotropic box
+    would give tau_p itself."""
+    tau = 4.0
+    Tz, _ = _box_period([2], tau)
+    assert abs(Tz / (math.sqrt(3.0) * tau) - 1) < 2e-3, Tz
+    Txy, _ = _box_period([0, 1], tau)
+    assert abs(Txy / (math.sqrt(1.5) * tau) - 1) < 2e-3, Txy
+
+
+def test_pr_box_direction_and_rest():
+    """The box grows under an excess pressure, shrinks under a deficit, stays
+    at rest at p_ref; x and y see their mean pressure."""
+    b = oracle.barostat(p_ref=1.0, tau_p=12.0, beta=3e-4, nst=10)
+    box = oracle.pr_box_update(0.02, [8.0, 8.0, 10.0], b, [1.0, 1.0, 1.0])
+    assert np.all(box == [8.0, 8.0, 10.0]) and np.all(np.array(b.boxv) == 0)
+    box = oracle.pr_box_update(0.02, [8.0, 8.0, 10.0], b, [101.0, -99.0, 51.0])
+    assert box[0] == box[1] == 8.0 and box[2] > 10.0 and b.M[2] > 0
+    b2 = oracle.barostat(p_ref=1.0, tau_p=12.0, beta=3e-4, nst=10)
+    box = oracle.pr_box_update(0.02, [8.0, 8.0, 10.0], b2, [-50.0, -50.0, 1.0])
+    assert box[0] < 8.0 and box[0] == box[1] and box[2] == 10.0
+    assert np.isclose(b2.M[0], b2.boxv[0] / box[0])
+
+
+def test_npt_velocity_coupling_closed_form():
+    """No forces, no thermostat, a box velocity held fixed (no update within
+    the run): v_n = (1 - dt M_a)^n v_0 per axis."""
+    m = synth.tiny(n_side=3, n_water=120, seed=35)
+    m.eps = np.zeros_like(m.eps)
+    m.charge = np.zeros_like(m.charge)
+    O = oracle.Oracle(m, kb=0.0, ktheta=0.0, tau_t=0.0)
+    b = oracle.barostat(nst=1000)
+    M = [0.01, 0.02, -0.03]
+    for a in range(3):
+        b.M[a] = M[a]
+    st = O.state()
+    v0 = st["vel"].copy()
+    O.md_steps_npt(st, b, 7)
+    for a in range(3):
+        assert np.allclose(st["vel"][:, a], v0[:, a] * (1 - m.dt * M[a]) ** 7, rtol=1e-13, atol=0)
+
+
+def test_npt_without_coupling_is_plain_md():
+    """beta = 0 (no box motion): the constant-pressure driver gives the same
+    bits as plain MD, trials included."""
+    m = synth.mcmd_small()
+    O = oracle.Oracle(m)
+    a, b = O.state(), O.state()
+    ra = O.md_steps(a, 6, swap_every=3)
+    bar = oracle.barostat(beta=0.0, nst=2)
+    rb = O.md_steps_npt(b, bar, 6, swap_every=3)
+    assert ra == rb
+    assert np.array_equal(a["pos_u"], b["pos_u"]) and np.array_equal(a["vel"], b["vel"])
+    assert np.all(O.box == m.box)
