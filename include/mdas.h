@@ -57,7 +57,7 @@ typedef enum { MDAS_FP32 = 0, MDAS_FP64 = 1 } mdas_precision;
  * Thermostat coupling groups: lipid beads (group 0) and water beads (group 1). */
 typedef struct {
     int32_t n_beads, n_lipids, beads_per_lipid, n_bead_types, n_lipid_types;
-    double box[3];                     /* rectangular periodic box, fixed (NVT) */
+    double box[3];                     /* rectangular periodic box (fixed unless tau_p > 0) */
     const double *pos;                 /* [n_beads*3], wrapped into the box on entry */
     const double *vel;                 /* [n_beads*3] or NULL (all zero) */
     const int32_t *lipid_first_bead;   /* [n_lipids] */
@@ -86,6 +86,23 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *stream, void *ctx);   /* optional device allocator */
     void (*dev_free)(void *ptr, void *stream, void *ctx);
     void *alloc_ctx;
+    /* Semi-isotropic Parrinello-Rahman pressure coupling (Sec. 3: the xy
+     * plane and z coupled separately to p_ref, coupling constant tau_p).
+     * tau_p <= 0: constant volume.  The box matrix diag(L) follows
+     * W d2L_a/dt2 = V (P_a - p_ref) / L_a (x and y see (Pxx + Pyy) / 2) with
+     * W^-1 = 4 pi^2 compressibility / (3 tau_p^2 L_max), updated every
+     * nstpcouple MD steps from the pressure of the step that ends the
+     * interval (kinetic energy of v(t + dt/2), virial of F(x(t))); the
+     * particles feel dv/dt = F/m - (dL_a/dt / L_a) v_a and keep their
+     * fractional coordinates.  The cell grids are sized for every edge down
+     * to (1 - box_margin) of its initial length; a box below that stops the
+     * dynamics with MDAS_ERR_UNSTABLE.  Alchemical trajectories (MDAS) run at
+     * the box they start with. */
+    double p_ref;                      /* bar */
+    double tau_p;                      /* ps */
+    double compressibility;            /* 1/bar (<= 0: 3e-4) */
+    int32_t nstpcouple;                /* MD steps per box update (<= 0: 10) */
+    double box_margin;                 /* (<= 0: 0.05; at most 0.5) */
 } mdas_system_desc;
 
 typedef struct {
@@ -132,6 +149,11 @@ typedef struct {
                                         * MD step); set_state: rebuild the list at list_ref instead */
     int32_t ke_valid;                  /* 1 when ke[] is the kinetic energy the last MD step left */
     double ke[2];                      /* lipid and solvent kinetic energy, kJ/mol, as that step summed it */
+    /* Pressure coupling: get_state returns the box and its velocity (dL/dt,
+     * nm/ps); set_state installs them when box[0] > 0 (else keeps the
+     * current box).  A box below the cell grids' minimum is refused. */
+    double box[3];
+    double box_velocity[3];
 } mdas_state_view;
 
 /* Create a device-resident system from a description (Sec. 3 force field,
@@ -386,6 +408,11 @@ double mdas_server_clock(const mdas_server *sv);
 /* Device bytes a system of this description occupies (the server's admission
  * charge); 0 for an invalid description. */
 size_t mdas_system_footprint(const mdas_system_desc *d);
+
+/* The current box (nm), its velocity dL/dt (nm/ps) and the pressure tensor
+ * diagonal (bar) of the last box update (zero before the first update and for
+ * systems without pressure coupling).  Any pointer may be NULL. */
+mdas_status mdas_box(const mdas_system *s, double box[3], double box_velocity[3], double pressure[3]);
 
 /* Health check of the failure path: one block of the persistent MD kernel's
  * grid barrier waits on this system's barrier state for an arrival that never

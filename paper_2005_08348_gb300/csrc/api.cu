@@ -46,12 +46,15 @@ struct ListDims {
     int ln[3], n_lcells, lcapc, lcap, lrow;
 };
 
-ListDims list_dims(const mdas_system_desc *d) {
+// Pair-list grid of a system whose box edges may shrink to (1 - shrink) of
+// their length (pressure coupling; 0 for a fixed box).
+ListDims list_dims(const mdas_system_desc *d, double shrink = 0.0) {
     ListDims L;
     const double skin = d->list_skin > 0 ? d->list_skin : 0.3;
-    const double lmin = std::min(d->box[0], std::min(d->box[1], d->box[2]));
+    const double f = 1.0 - shrink;
+    const double lmin = std::min(d->box[0], std::min(d->box[1], d->box[2])) * f;
     L.rl = std::max(d->rc, std::min(d->rc + skin, lmin / 3.0));
-    for (int k = 0; k < 3; ++k) L.ln[k] = std::max(3, (int)std::floor(d->box[k] / L.rl));
+    for (int k = 0; k < 3; ++k) L.ln[k] = std::max(3, (int)std::floor(d->box[k] * f / L.rl));
     L.n_lcells = L.ln[0] * L.ln[1] * L.ln[2];
     const int n = d->n_beads;
     std::vector<int> cnt(L.n_lcells, 0);
@@ -67,7 +70,7 @@ ListDims list_dims(const mdas_system_desc *d) {
     }
     const double mean = (double)n / L.n_lcells;
     L.lcapc = std::max(32, (int)std::ceil(std::max(4.0 * mean, 2.0 * maxc) / 32.0) * 32);
-    const double vol = d->box[0] * d->box[1] * d->box[2];
+    const double vol = d->box[0] * d->box[1] * d->box[2] * f * f * f;
     const double dens = std::max((double)n / vol, maxc / (vol / L.n_lcells));
     const double within = 4.0 / 3.0 * M_PI * L.rl * L.rl * L.rl * dens;
     L.lcap = std::max(64, (int)std::ceil(1.5 * within / 32.0) * 32);
@@ -110,7 +113,11 @@ LaunchCtx Batch::ctx() const {
     L.precision = precision; L.stream = stream; L.max_bead_blocks = max_bead_blocks;
     L.bticket = bticket;
     L.soft = false;
-    for (auto *x : sys) L.soft = L.soft || x->hp.sc_delta > 0.0;
+    L.pc = false;
+    for (auto *x : sys) {
+        L.soft = L.soft || x->hp.sc_delta > 0.0;
+        L.pc = L.pc || x->hp.pc_nst > 0;
+    }
     return L;
 }
 }  // namespace
@@ -334,6 +341,7 @@ mdas_status check_err(mdas_system *s, Batch &b) {
         if (err & ERR_CELL_OVERFLOW) why += " a cell holds more beads than its capacity;";
         if (err & ERR_TIMEOUT) why += " bounded wait expired;";
         if (err & ERR_ROUNDS) why += " exchange rounds exhausted;";
+        if (err & ERR_BOX) why += " the box shrank below what the cell grids allow;";
         // a wait that gave up left the state partly advanced: refused like an
         // unstable one, reported as the timeout it was
         return fail(s, (err & ERR_TIMEOUT) ? MDAS_ERR_TIMEOUT : MDAS_ERR_UNSTABLE, "unstable:" + why);
@@ -395,14 +403,34 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     for (auto *x : b.sys) tm.on = tm.on || x->timing;
     for (auto *x : b.sys) x->cells_valid = false;
     LaunchCtx L = b.ctx();
-    const bool persistent = b.persistent && md_run_blocks(b.precision, !lambda ? 0 : L.soft ? 2 : 1) > 0;
+    const bool persistent = b.persistent && md_run_blocks(b.precision, !lambda ? (L.pc ? 3 : 0) : L.soft ? 2 : 1) > 0;
     // segments of at most MAX_DRAW_STEPS - 1 steps (the precomputed thermostat
     // variates); a segment starting at step k0 has its trials after local
     // steps s with (k0 + s + 1) % swap_every == 0
     const long long seg = MAX_DRAW_STEPS - 1;
     long long launches = 0;
-    for (long long k0 = 0; k0 < n_steps; k0 += seg) {
-        const long long n = std::min(seg, n_steps - k0);
+    // pressure coupling: segments also end where a box update is due (a step
+    // counter that is a multiple of nstpcouple), which follows the segment;
+    // the coupled systems of a batch must share nstpcouple and the phase
+    long long pc_nst = 0, pc_phase = 0;
+    if (L.pc && !lambda) {
+        for (auto *x : b.sys) {
+            if (x->hp.pc_nst <= 0) continue;
+            unsigned long long st = 0;
+            CK(cudaMemcpyAsync(&st, &x->hs.c->step, sizeof(st), cudaMemcpyDeviceToHost, b.stream));
+            CK(cudaStreamSynchronize(b.stream));
+            const long long ph = (long long)(st % (unsigned long long)x->hp.pc_nst);
+            if (pc_nst == 0) {
+                pc_nst = x->hp.pc_nst;
+                pc_phase = ph;
+            } else if (pc_nst != x->hp.pc_nst || ph != pc_phase) {
+                return fail(s, MDAS_ERR_INVALID_ARG, "md: pressure-coupled systems of a batch at different coupling phases");
+            }
+        }
+    }
+    for (long long k0 = 0, n = 0; k0 < n_steps; k0 += n) {
+        n = std::min(seg, n_steps - k0);
+        if (pc_nst > 0) n = std::min(n, pc_nst - (pc_phase + k0) % pc_nst);
         launch_thermo_draws(L, (int)std::min<long long>(n + 1, MAX_DRAW_STEPS));
         launch_thermostat(L);
         launches += 2;
@@ -413,6 +441,7 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
             CK(tm.end(b.stream));
             k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
             launches += 1;
+            if (pc_nst > 0) { launch_pcouple(L); ++launches; }
             continue;
         }
         // the same order as the persistent kernel: a build for lists made
@@ -434,6 +463,13 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
                 launches += 3;
             }
         }
+        if (pc_nst > 0) { launch_pcouple(L); ++launches; }
+    }
+    if (pc_nst > 0) {
+        // the host copy of the box-derived parameters
+        for (auto *x : b.sys)
+            if (x->hp.pc_nst > 0) CK(cudaMemcpyAsync(&x->hp, x->hs.p, sizeof(Params), cudaMemcpyDeviceToHost, b.stream));
+        CK(cudaStreamSynchronize(b.stream));
     }
     for (auto *x : b.sys) x->kernel_launches += launches;
     CK(cudaGetLastError());
@@ -505,11 +541,16 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     if (d->n_bonds < 0 || d->n_angles < 0 || (d->n_bonds && !d->bonds) || (d->n_angles && !d->angles))
         return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: topology");
     if (d->precision != MDAS_FP32 && d->precision != MDAS_FP64) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: precision");
+    // pressure coupling: the cell grids hold for every edge down to (1 - shrink) of its length
+    const bool pcouple = d->tau_p > 0;
+    const double shrink = !pcouple ? 0.0 : d->box_margin > 0 ? std::min(d->box_margin, 0.5) : 0.05;
+    if (pcouple && !(d->compressibility >= 0 && std::isfinite(d->p_ref) && std::isfinite(d->tau_p)))
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: pressure coupling parameters");
     int nc[3];
     for (int k = 0; k < 3; ++k) {
         if (!(d->box[k] > 0)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: box");
-        nc[k] = (int)std::floor(d->box[k] / d->rc);
-        if (nc[k] < 3) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: every box edge must be >= 3 rc");
+        nc[k] = (int)std::floor(d->box[k] * (1.0 - shrink) / d->rc);
+        if (nc[k] < 3) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: every box edge must be >= 3 rc (with the margin)");
     }
     if ((long long)nc[0] * nc[1] * nc[2] > (1 << 26)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: too many cells");
     for (int l = 0; l < nl; ++l) {
@@ -551,28 +592,20 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
             return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: more than 256 beads per cell on average");
         }
     }
+    P.rc = d->rc; P.rc2 = d->rc * d->rc;
+    P.dt = d->dt;
     for (int k = 0; k < 3; ++k) {
         P.nc[k] = nc[k];
-        P.box[k] = d->box[k];
-        P.qs[k] = d->box[k] / TWO32;
-        P.qsf[k] = (float)P.qs[k];
-        P.qsh[k] = (float)P.qs[k];
-        P.qsl[k] = (float)(P.qs[k] - (double)P.qsh[k]);
-        P.qdt[k] = d->dt * TWO32 / d->box[k];
-        P.rcu[k] = (uint32_t)std::ceil(d->rc / P.qs[k]) + 2;
+        box_params(P, k, d->box[k]);
     }
-    P.rc = d->rc; P.rc2 = d->rc * d->rc;
     P.krf = d->eps_rf <= 0 ? 1.0 / (2.0 * d->rc * d->rc * d->rc)
                            : (d->eps_rf - d->eps_r) / ((2.0 * d->eps_rf + d->eps_r) * d->rc * d->rc * d->rc);
     P.crf = 1.0 / d->rc + P.krf * d->rc * d->rc;
     // float cull bounds: every pair with r^2 < rc^2 passes rc2f; pairs in
     // [rc2f_lo, rc2f) are re-decided exactly from integer offsets
-    for (int k = 0; k < 3; ++k) {
-        P.cwu[k] = (unsigned long long)(4294967296.0 / nc[k]);
-        P.qdtf[k] = (float)P.qdt[k];
-    }
+    for (int k = 0; k < 3; ++k) P.cwu[k] = (unsigned long long)(4294967296.0 / nc[k]);
     {   // pair list
-        const ListDims ld = list_dims(d);
+        const ListDims ld = list_dims(d, shrink);
         P.rl = ld.rl;
         P.rl2 = P.rl * P.rl;
         P.rl2f = std::nextafter((float)(P.rl2 * (1.0 + 1e-5)), 1e30f);
@@ -583,6 +616,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
             P.lcwu[k] = (unsigned long long)(4294967296.0 / ld.ln[k]);
         }
         P.n_lcells = ld.n_lcells;
+        for (int k = 0; k < 3; ++k) P.pc_lmin[k] = std::max(nc[k] * d->rc, ld.ln[k] * P.rl);
         P.lcapc = ld.lcapc;
         P.lcap = ld.lcap;
         P.lrow = ld.lrow;
@@ -591,6 +625,12 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
             delete s;
             return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: density too high for the pair list");
         }
+    }
+    if (pcouple) {
+        const double beta = d->compressibility > 0 ? d->compressibility : 3e-4;
+        P.pc_nst = d->nstpcouple > 0 ? d->nstpcouple : 10;
+        P.pc_pref = d->p_ref;
+        P.pc_wc = 4.0 * M_PI * M_PI * beta / (3.0 * d->tau_p * d->tau_p);
     }
     P.therm_c = d->tau_t > 0 ? std::exp(-d->dt / d->tau_t) : 1.0;
     P.rc2f = std::nextafter((float)(P.rc2 * (1.0 + 1e-5)), 1e30f);
@@ -1049,6 +1089,20 @@ mdas_status mdas_get_state(const mdas_system *cs, mdas_state_view *out) {
     out->ke_valid = c.ke_fresh;
     out->ke[0] = c.ke_fresh ? c.ke_total[0] : 0.0;
     out->ke[1] = c.ke_fresh ? c.ke_total[1] : 0.0;
+    for (int k = 0; k < 3; ++k) {
+        out->box[k] = s->hp.box[k];
+        out->box_velocity[k] = s->hp.boxv[k];
+    }
+    return MDAS_OK;
+}
+
+mdas_status mdas_box(const mdas_system *s, double box[3], double box_velocity[3], double pressure[3]) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "box: NULL system");
+    for (int k = 0; k < 3; ++k) {
+        if (box) box[k] = s->hp.box[k];
+        if (box_velocity) box_velocity[k] = s->hp.boxv[k];
+        if (pressure) pressure[k] = s->hp.pres[k];
+    }
     return MDAS_OK;
 }
 
@@ -1075,6 +1129,19 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     const bool keep_list = in->list_valid && in->list_ref;
     if (keep_list && !in->pos_fixed && !in->pos)
         return fail(s, MDAS_ERR_INVALID_ARG, "set_state: list_ref without positions");
+    if (in->box[0] > 0) {
+        // a new box (pressure coupling state): first, so that positions in nm convert with it
+        for (int k = 0; k < 3; ++k)
+            if (!(in->box[k] >= s->hp.pc_lmin[k]) || !std::isfinite(in->box[k]) || !std::isfinite(in->box_velocity[k]))
+                return fail(s, MDAS_ERR_INVALID_ARG, "set_state: box below what the cell grids allow, or not finite");
+        for (int k = 0; k < 3; ++k) {
+            box_params(s->hp, k, in->box[k]);
+            s->hp.boxv[k] = s->hp.pc_nst > 0 ? in->box_velocity[k] : 0.0;
+            s->hp.dtm_pc[k] = s->hp.dt * (s->hp.boxv[k] / in->box[k]);
+            s->hp.dtm_pcf[k] = (float)s->hp.dtm_pc[k];
+        }
+        CK(cudaMemcpyAsync(const_cast<Params *>(s->hs.p), &s->hp, sizeof(Params), cudaMemcpyHostToDevice, s->stream));
+    }
     std::vector<int> lt(std::max(nl, 1));
     if (in->lipid_type) {
         for (int l = 0; l < nl; ++l)

@@ -197,6 +197,57 @@ void launch_thermostat(const LaunchCtx &L) {
     else k_thermostat<float><<<L.n_sys, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys);
 }
 
+// Pressure coupling after an MD segment (Sec. 3: semi-isotropic
+// Parrinello-Rahman, xy and z).  At a step counter that is a multiple of
+// nstpcouple: the pressure tensor of the step that just ended,
+// P_a = 2 (K_a + S_a / 4) / V (S_a counts every virial term twice), one
+// symplectic Euler step of the box equation W d2L_a/dt2 = V (P_a - p_ref) / L_a
+// over the interval (x and y see (Pxx + Pyy) / 2; W^-1 = pc_wc / L_max; V,
+// L_max and L_a of the box before the step), the box-derived parameters, the
+// particles' dt dL_a/dt / L_a for the next interval, and a list rebuild (the
+// list was built at other distances).  A box below the cell grids' minimum
+// stops the system (ERR_BOX) before anything changes.
+__global__ void k_pcouple(const SysDev *__restrict__ sys, int n_sys) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_sys) return;
+    const SysDev &S = sys[q];
+    Params &P = *const_cast<Params *>(S.p);
+    Counters &C = *S.c;
+    if (P.pc_nst <= 0 || C.in_at || C.step % (unsigned long long)P.pc_nst != 0) return;
+    const double V = P.box[0] * P.box[1] * P.box[2];
+    double pr[3];
+    for (int a = 0; a < 3; ++a) pr[a] = 2.0 * (C.pv[a] + 0.25 * C.pv[3 + a]) / V * BAR_PER_KJ_MOL_NM3;
+    const double lmax = fmax(fmax(P.box[0], P.box[1]), P.box[2]);
+    const double winv = P.pc_wc / lmax;
+    const double dtp = (double)P.pc_nst * P.dt;
+    const double lat = 0.5 * (pr[0] + pr[1]);
+    const double pd[3] = {lat, lat, pr[2]};
+    double bv[3], L[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+        bv[a] = P.boxv[a] + dtp * V * winv * (pd[a] - P.pc_pref) / P.box[a];
+        L[a] = P.box[a] + dtp * bv[a];
+        ok = ok && L[a] >= P.pc_lmin[a] && isfinite(L[a]);
+    }
+    if (!ok) {
+        atomicOr(&C.err, ERR_BOX);
+        return;
+    }
+    for (int a = 0; a < 3; ++a) {
+        P.boxv[a] = bv[a];
+        box_params(P, a, L[a]);
+        P.dtm_pc[a] = P.dt * (bv[a] / L[a]);
+        P.dtm_pcf[a] = (float)P.dtm_pc[a];
+        P.pres[a] = pr[a];
+    }
+    C.nl_stale = 1;
+}
+
+void launch_pcouple(const LaunchCtx &L) {
+    if (!L.pc) return;
+    k_pcouple<<<(L.n_sys + 63) / 64, 64, 0, L.stream>>>(L.sys, L.n_sys);
+}
+
 // ------------------------------------------------------------ pair forces
 // One CTA per cell.  The 27 neighbour cells are staged in shared memory (in
 // chunks of STAGE_CAP beads) in a frame centred on the cell: each bead's exact

@@ -34,7 +34,8 @@ constexpr double BOLTZ = 0.0083144626;
 constexpr double COUL = 138.935458;
 
 enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5, TAG_MUTATE = 6 };
-enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8, ERR_BAD_INPUT = 16 };
+enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8, ERR_BAD_INPUT = 16,
+             ERR_BOX = 32 };
 
 // Per-bead meta word carried in the 4th lane of every position:
 // bits 0-3 current bead type (A), 4-7 alchemical target type (B),
@@ -47,7 +48,8 @@ __host__ __device__ inline int meta_tb(uint32_t m) { return (int)((m >> 4) & 15u
 __host__ __device__ inline int meta_k(uint32_t m) { return (int)((m >> 8) & 15u); }
 __host__ __device__ inline int meta_lip(uint32_t m) { return (int)(m >> 12) - 1; }
 
-// Constant parameters of one system (device memory, read-only in kernels).
+// Parameters of one system (device memory).  Kernels read them; only the
+// pressure coupling changes the box fields, between launches (k_pcouple).
 struct Params {
     int n, n_lip, bpl, n_bt, n_lt, n_lipid_beads;
     int nc[3], n_cells, capc;          // cells per edge, cells, bead capacity of a cell
@@ -86,7 +88,31 @@ struct Params {
     uint16_t excl[16];                 // excluded partners of local index k (1-2 bonds)
     int8_t nbond[16], bpart[16][4];
     int8_t nang[16], ang[16][8][3];    // angles containing local index k
+    // semi-isotropic Parrinello-Rahman pressure coupling (Sec. 3), on when pc_nst > 0
+    int pc_nst;                        // MD steps per box update
+    double pc_pref, pc_wc;             // bar; 4 pi^2 beta / (3 tau_p^2) (the inverse barostat mass times L_max)
+    double pc_lmin[3];                 // shortest edges the cell grids allow (nc rc and ln rl)
+    double boxv[3];                    // dL/dt, nm/ps
+    double dtm_pc[3];                  // dt (dL/dt) / L of the current interval (the particles' -M v term)
+    float dtm_pcf[3];
+    double pres[3];                    // pressure tensor diagonal of the last box update, bar
 };
+
+constexpr double BAR_PER_KJ_MOL_NM3 = 16.6053906717;   // 10^3 / N_A / 10^-27 m^3 / 10^5 Pa, N_A = 6.02214076e23
+
+// The parameters that follow from edge k of the box (host at creation and on
+// set_state, device at each box update: one definition for both).
+__host__ __device__ inline void box_params(Params &P, int k, double L) {
+    const double two32 = 4294967296.0;
+    P.box[k] = L;
+    P.qs[k] = L / two32;
+    P.qsf[k] = (float)P.qs[k];
+    P.qsh[k] = (float)P.qs[k];
+    P.qsl[k] = (float)(P.qs[k] - (double)P.qsh[k]);
+    P.qdt[k] = P.dt * two32 / L;
+    P.qdtf[k] = (float)P.qdt[k];
+    P.rcu[k] = (uint32_t)ceil(P.rc / P.qs[k]) + 2;
+}
 
 struct TrialRec {                      // mirrors mdas_trial_record
     int a, b, null_trial, accepted;
@@ -129,6 +155,11 @@ struct Counters {
     unsigned int mark_seq;             // trial parts done marking the step items their exchange can change
     unsigned long long alpha_pack[2];  // (close_seq << 32) | float bits of alpha_f, one word per group (FP32)
     unsigned long long redos;          // step items that summed their forces again after an accepted exchange
+    // pressure coupling: per step [position buffer the step read], fixed-point
+    // (as ke_slot) kinetic energy per axis and S_a = the sum over list entries
+    // of f d_a^2 plus the bonded terms' share (the virial is -S_a / 4)
+    long long pv_slot[2][KE_SLOTS][6];
+    double pv[6];                      // the last closed step's K_a and S_a, kJ/mol
 };
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
@@ -236,6 +267,7 @@ struct LaunchCtx {
     int max_bead_blocks;
     unsigned int *bticket;    // device: last-block ticket over the whole batch
     bool soft;                // a system of the batch takes the soft-core alchemical path
+    bool pc;                  // a system of the batch has pressure coupling (MD steps sum the virial)
 };
 
 cudaError_t setup_kernels();
@@ -252,13 +284,17 @@ void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
 void launch_thermostat(const LaunchCtx &L);
 void launch_nl_build(const LaunchCtx &L);
 void launch_nl_step(const LaunchCtx &L, bool lambda);
-int md_run_blocks(int precision, int mode);   // mode: 0 plain MD, 1 linear alchemical path, 2 soft-core path
+int md_run_blocks(int precision, int mode);   // mode: 0 plain MD, 1 linear alchemical path, 2 soft-core path,
+                                              // 3 plain MD with pressure coupling
 cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
                           int lam_off, double dlam, void *sync);
 size_t md_run_sync_bytes();
 // one block waiting at a grid barrier of `sync` for an arrival that never
 // comes (the bounded wait expires and raises the abort word)
 cudaError_t launch_barrier_stall(void *sync, cudaStream_t stream);
+// after an MD segment: the box update of every pressure-coupled system whose
+// step counter is a multiple of its nstpcouple (kernels.cu)
+void launch_pcouple(const LaunchCtx &L);
 void launch_trial_nl(const LaunchCtx &L);
 void launch_energy_reduce(const LaunchCtx &L);
 

@@ -104,8 +104,13 @@ __device__ __forceinline__ void sep(const Params &P, uint4 a, uint4 b, Real d[3]
 // q, the rest are its angles; every stride-th term from `first` is added to f
 // (all of them by default).  get(li) returns the position of the bead with
 // local index li of the same lipid.
-template <typename Real, class Get>
-__device__ void bonded_force(const Params &P, int k, uint4 pi, Get get, Real f[3], int first = 0, int stride = 1) {
+// VIR: w also gains this bead's share of the virial sums S_a (the bond's
+// f d_a^2, which its other bead adds as well; twice (r_k - r_vertex)_a F_k,a
+// for an angle that k ends), so that S over all beads counts every term
+// twice, like the pair list.
+template <typename Real, bool VIR = false, class Get>
+__device__ void bonded_force(const Params &P, int k, uint4 pi, Get get, Real f[3], int first = 0, int stride = 1,
+                             Real *w = nullptr) {
     const int nb = P.nbond[k], nt = nb + P.nang[k];
     for (int q = first; q < nt; q += stride) {
         if (q < nb) {
@@ -114,6 +119,7 @@ __device__ void bonded_force(const Params &P, int k, uint4 pi, Get get, Real f[3
             const Real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             const Real fs = -(Real)P.kb * (r - (Real)P.b0) / r;
             f[0] += fs * d[0]; f[1] += fs * d[1]; f[2] += fs * d[2];
+            if (VIR) { w[0] += fs * d[0] * d[0]; w[1] += fs * d[1] * d[1]; w[2] += fs * d[2] * d[2]; }
             continue;
         }
         const int a = q - nb;
@@ -138,6 +144,10 @@ __device__ void bonded_force(const Params &P, int k, uint4 pi, Get get, Real f[3
             else if (k == lk) g = dck;
             else g = -(dci + dck);
             f[d] += pre * g;
+            if (VIR) {
+                if (k == li) w[d] += (Real)2 * A[d] * (pre * g);
+                else if (k == lk) w[d] += (Real)2 * B[d] * (pre * g);
+            }
         }
     }
 }

@@ -464,12 +464,16 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     const Real rc2 = F32 ? (Real)P.rc2f : (Real)P.rc2;
     const Real rc2lo = F32 ? (Real)P.rc2f_lo : (Real)P.rc2;
     const Real krf2 = F32 ? (Real)P.krf2f : (Real)(2.0 * P.krf);
-    const Real lam = LAM ? (Real)C.lambda : (Real)0;
-    // LAM: 0 no alchemical path, 1 linear path, 2 soft-core path (Eq. 4)
+    // LAM: 0 no alchemical path, 1 linear path, 2 soft-core path (Eq. 4),
+    // 3 no alchemical path, with the pressure coupling's virial sums and -M v term
+    constexpr bool ALCH = LAM == 1 || LAM == 2;
+    constexpr bool PC = LAM == 3;
+    const Real lam = ALCH ? (Real)C.lambda : (Real)0;
     const Real dsc = LAM == 2 ? (F32 ? (Real)P.sc_deltaf : (Real)P.sc_delta) : (Real)0;
     const float qs0 = P.qsf[0], qs1 = P.qsf[1], qs2 = P.qsf[2];
     int tai = meta_ta(pi.w) * 16, tbi = meta_tb(pi.w) * 16;
     Real ax = 0, ay = 0, az = 0;
+    Real wx = 0, wy = 0, wz = 0;               // PC: sums of f d_a^2 over this lane's entries
 
     auto pair = [&](uint4 pj, bool ok) {
         const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
@@ -495,7 +499,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         const V4 ca = sm.tab[tai + meta_ta(mj)];
         Real f12 = ca.x, f6 = ca.y, qq = ca.z;
         V4 cb = ca;
-        if (LAM) {
+        if (ALCH) {
             cb = sm.tab[tbi + meta_tb(mj)];
             f12 = fmr((Real)1 - lam, f12, lam * cb.x);
             f6 = fmr((Real)1 - lam, f6, lam * cb.y);
@@ -529,6 +533,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         }
         fs = in ? fs : (Real)0;
         ax = fmr(fs, dx, ax); ay = fmr(fs, dy, ay); az = fmr(fs, dz, az);
+        if (PC) { wx = fmr(fs * dx, dx, wx); wy = fmr(fs * dy, dy, wy); wz = fmr(fs * dz, dz, wz); }
     };
 
     // column gl of the bead's list, rows 0 .. cnt - 1, in groups of 4: as
@@ -551,9 +556,12 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         __syncwarp();
         if (valid && meta_lip(pi.w) >= 0) {
             Real fb[3] = {(Real)0, (Real)0, (Real)0};
+            Real wb[3] = {(Real)0, (Real)0, (Real)0};
             const int kl = meta_k(pi.w);
-            bonded_force<Real>(P, kl, pi, [&](int li) { return sm.spart[il][P.pidx[kl][li]]; }, fb, gl, NL_G);
+            bonded_force<Real, PC>(P, kl, pi, [&](int li) { return sm.spart[il][P.pidx[kl][li]]; }, fb, gl, NL_G,
+                                   wb);
             ax += fb[0]; ay += fb[1]; az += fb[2];
+            if (PC) { wx += wb[0]; wy += wb[1]; wz += wb[2]; }
         }
 
         // partial forces summed over the bead's NL_G lanes in a fixed tree
@@ -562,6 +570,11 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             ax += __shfl_xor_sync(0xffffffffu, ax, o);
             ay += __shfl_xor_sync(0xffffffffu, ay, o);
             az += __shfl_xor_sync(0xffffffffu, az, o);
+            if (PC) {
+                wx += __shfl_xor_sync(0xffffffffu, wx, o);
+                wy += __shfl_xor_sync(0xffffffffu, wy, o);
+                wz += __shfl_xor_sync(0xffffffffu, wz, o);
+            }
         }
         // beside the previous step's close and trial: wait for the thermostat
         // factor and the trial's marks; after an accepted exchange that this
@@ -577,10 +590,12 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         tai = meta_ta(pi.w) * 16;
         tbi = meta_tb(pi.w) * 16;
         ax = ay = az = (Real)0;
+        wx = wy = wz = (Real)0;
         j0 = idx(0); j1 = idx(1); j2 = idx(2); j3 = idx(3);
         q0 = __ldcg(cur + j0); q1 = __ldcg(cur + j1); q2 = __ldcg(cur + j2); q3 = __ldcg(cur + j3);
     }
     Real e0 = 0, e1 = 0;
+    Real kx = 0, ky = 0, kz = 0;               // PC: the bead's kinetic energy per axis
     if (valid && gl == 0) {
         const Real f0 = ax, f1 = ay, f2 = az;
         const int grp = id < P.n_lipid_beads ? 0 : 1;
@@ -588,9 +603,16 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
                        : (F32 ? (Real)C.alpha_f[grp] : (Real)C.alpha[grp]);
         const Real dtm = F32 ? (Real)P.dt_over_mf : (Real)P.dt_over_m;
         V4 v = sm.svel[il];
-        v.x = fmr(a, v.x, f0 * dtm);
-        v.y = fmr(a, v.y, f1 * dtm);
-        v.z = fmr(a, v.z, f2 * dtm);
+        if (PC) {
+            // v <- alpha v + dt (F/m - M v), M = diag(dL/dt / L) of the box motion
+            v.x = fmr(a - (F32 ? (Real)P.dtm_pcf[0] : (Real)P.dtm_pc[0]), v.x, f0 * dtm);
+            v.y = fmr(a - (F32 ? (Real)P.dtm_pcf[1] : (Real)P.dtm_pc[1]), v.y, f1 * dtm);
+            v.z = fmr(a - (F32 ? (Real)P.dtm_pcf[2] : (Real)P.dtm_pc[2]), v.z, f2 * dtm);
+        } else {
+            v.x = fmr(a, v.x, f0 * dtm);
+            v.y = fmr(a, v.y, f1 * dtm);
+            v.z = fmr(a, v.z, f2 * dtm);
+        }
         reinterpret_cast<V4 *>(S.vel)[id] = v;
         if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(&C.err, ERR_NONFINITE);
         uint4 np = pi;
@@ -613,6 +635,30 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         if (fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > P.dmax2f) sm.sviol = 1;
         const Real ke = (Real)0.5 * (F32 ? (Real)P.massf : (Real)P.mass) * fmr(v.x, v.x, fmr(v.y, v.y, v.z * v.z));
         if (grp == 0) e0 = ke; else e1 = ke;
+        if (PC) {
+            const Real hm = (Real)0.5 * (F32 ? (Real)P.massf : (Real)P.mass);
+            kx = hm * (v.x * v.x); ky = hm * (v.y * v.y); kz = hm * (v.z * v.z);
+        }
+    }
+    if (PC) {
+        // the warp's 8 beads (their first lanes), fixed-order shuffle sums,
+        // then integer slot sums (order-free)
+        Real q[6] = {kx, ky, kz, wx, wy, wz};
+        const bool own = valid && gl == 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (!own) q[i] = (Real)0;
+#pragma unroll
+            for (int o = NL_G; o < 32; o <<= 1) q[i] += __shfl_xor_sync(0xffffffffu, q[i], o);
+        }
+        if ((t & 31) == 0) {
+            long long *ps = C.pv_slot[par][((k0 / NL_BEADS) * (GRP / 32) + t / 32) % KE_SLOTS];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const long long u = F32 ? __float2ll_rn((float)q[i] * 65536.f) : to_fix((double)q[i]);
+                atomicAdd((unsigned long long *)&ps[i], (unsigned long long)u);
+            }
+        }
     }
     if (gl == 0) { sm.kered[0][il] = e0; sm.kered[1][il] = e1; }
     g.sync();
@@ -653,7 +699,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
 // the integer slots (cleared), counters, the thermostat factor of the next
 // step (lanes 0 and 1, one coupling group each).  Real is the system's
 // precision (the factor sees the energy as Real).
-template <typename Real>
+template <typename Real, bool PC = false>
 __device__ void nl_step_close(const SysDev &S, int lane, int par) {
     static_assert(KE_SLOTS == 64, "two slots per lane");
     const Params &P = *S.p;
@@ -669,6 +715,19 @@ __device__ void nl_step_close(const SysDev &S, int lane, int par) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
     const double unit = sizeof(Real) == 4 ? 1.0 / 65536.0 : 1.0 / FIX;
+    if (PC) {
+        // the step's kinetic energy per axis and virial sums
+        long long(*ps)[6] = C.pv_slot[par];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            long long x = __ldcg(&ps[lane][i]) + __ldcg(&ps[lane + 32][i]);
+            ps[lane][i] = 0;
+            ps[lane + 32][i] = 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) C.pv[i] = (double)x * unit;
+        }
+    }
     const double a0 = (double)s0 * unit, a1 = (double)s1 * unit;
     const int in_at = C.in_at;
     const unsigned long long ctr = (in_at ? C.at_step : C.step) + 1;
@@ -759,7 +818,7 @@ __global__ void __launch_bounds__(GRP, 8) k_nl_step(const SysDev *__restrict__ s
     __syncthreads();
     if (!last || threadIdx.x >= 32) return;
     __threadfence();
-    nl_step_close<Real>(S, threadIdx.x, par);
+    nl_step_close<Real, LAM == 3>(S, threadIdx.x, par);
     if (threadIdx.x == 0) {
         C.nl_stale = __ldcg(&C.nl_viol);
         C.nl_viol = 0;
@@ -776,11 +835,11 @@ static void nl_step_launch(const LaunchCtx &L) {
 void launch_nl_step(const LaunchCtx &L, bool lambda) {
     static_assert(NL_BEADS * NL_G == GRP, "a step item is one group");
     if (L.precision == 1) {
-        if (!lambda) nl_step_launch<double, 0>(L);
+        if (!lambda) L.pc ? nl_step_launch<double, 3>(L) : nl_step_launch<double, 0>(L);
         else if (L.soft) nl_step_launch<double, 2>(L);
         else nl_step_launch<double, 1>(L);
     } else {
-        if (!lambda) nl_step_launch<float, 0>(L);
+        if (!lambda) L.pc ? nl_step_launch<float, 3>(L) : nl_step_launch<float, 0>(L);
         else if (L.soft) nl_step_launch<float, 2>(L);
         else nl_step_launch<float, 1>(L);
     }
@@ -960,7 +1019,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                 trial_nl_part(S, ptrial % TRIAL_PARTS, (S.c->nl_par + s) & 1, g, tsm, true);
             } else if (pclose >= 0 && s > 0 && g.t < 32) {
                 const SysDev &S = a.sys[pclose];
-                nl_step_close<Real>(S, g.t, (S.c->nl_par + s - 1) & 1);
+                nl_step_close<Real, LAM == 3>(S, g.t, (S.c->nl_par + s - 1) & 1);
             }
         } else {
             for (int it = gid; it < a.n_nl; it += G) {
@@ -987,7 +1046,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                 for (int q = blockIdx.x; q < a.n_sys; q += gridDim.x)
                     if (a.sys[q].c->nl_violp[s % 3]) a.sys[q].c->nl_builds++;
         }
-        if (LAM && a.lam_M > 0 && (a.lam_off + s + 1) % a.lam_M == 0) {
+        if ((LAM == 1 || LAM == 2) && a.lam_M > 0 && (a.lam_off + s + 1) % a.lam_M == 0) {
             // the end of a lambda block (Eq. 2): each lipid's work term at the
             // block's last coordinates, then w += dlam * their ordered sum and
             // the next lambda, read by the next step's items after a barrier
@@ -1019,7 +1078,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
             if (threadIdx.x < 32)
                 for (int q = gridDim.x - 1 - blockIdx.x; q < a.n_sys; q += gridDim.x) {
                     const SysDev &S = a.sys[q];
-                    nl_step_close<Real>(S, threadIdx.x, (S.c->nl_par + s) & 1);
+                    nl_step_close<Real, LAM == 3>(S, threadIdx.x, (S.c->nl_par + s) & 1);
                 }
             if (a.swap_every > 0 && (s + 1 + a.trial_off) % a.swap_every == 0) {
                 for (int it = gid; it < TRIAL_PARTS * a.n_sys; it += G) {
@@ -1036,7 +1095,7 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
         const int s = a.n_steps;
         if (pclose >= 0 && g.t < 32) {
             const SysDev &S = a.sys[pclose];
-            nl_step_close<Real>(S, g.t, (S.c->nl_par + s - 1) & 1);
+            nl_step_close<Real, LAM == 3>(S, g.t, (S.c->nl_par + s - 1) & 1);
         }
         if (ptrial >= 0 && a.swap_every > 0 && (s + a.trial_off) % a.swap_every == 0) {
             const SysDev &S = a.sys[ptrial / TRIAL_PARTS];
@@ -1082,7 +1141,7 @@ static cudaError_t run_setup(int *blocks_per_sm) {
 // Blocks of the persistent kernel on this device: one per SM when a block
 // fits on an SM, else 0 (then the separate kernels are used).
 int md_run_blocks(int precision, int mode) {
-    static int cache[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+    static int cache[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
     int &c = cache[precision == 1][mode];
     if (c >= 0) return c;
     int dev = 0, sms = 0, per = 0;
@@ -1090,9 +1149,11 @@ int md_run_blocks(int precision, int mode) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
     if (precision == 1)
-        e = mode == 2 ? run_setup<double, 2>(&per) : mode == 1 ? run_setup<double, 1>(&per) : run_setup<double, 0>(&per);
+        e = mode == 3 ? run_setup<double, 3>(&per) : mode == 2 ? run_setup<double, 2>(&per)
+            : mode == 1 ? run_setup<double, 1>(&per) : run_setup<double, 0>(&per);
     else
-        e = mode == 2 ? run_setup<float, 2>(&per) : mode == 1 ? run_setup<float, 1>(&per) : run_setup<float, 0>(&per);
+        e = mode == 3 ? run_setup<float, 3>(&per) : mode == 2 ? run_setup<float, 2>(&per)
+            : mode == 1 ? run_setup<float, 1>(&per) : run_setup<float, 0>(&per);
     c = (e == cudaSuccess && per >= 1) ? sms : 0;
     cudaGetLastError();
     return c;
@@ -1100,15 +1161,17 @@ int md_run_blocks(int precision, int mode) {
 
 cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
                           int lam_off, double dlam, void *sync) {
-    const int mode = !lambda ? 0 : L.soft ? 2 : 1;
+    const int mode = !lambda ? (L.pc ? 3 : 0) : L.soft ? 2 : 1;
     const int nb = md_run_blocks(L.precision, mode);
     if (nb <= 0) return cudaErrorCooperativeLaunchTooLarge;
     RunSync *rs = (RunSync *)sync;
     if (L.precision == 1) {
+        if (mode == 3) return run_launch<double, 3>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
         if (mode == 2) return run_launch<double, 2>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
         if (mode == 1) return run_launch<double, 1>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
         return run_launch<double, 0>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
     }
+    if (mode == 3) return run_launch<float, 3>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);
     if (mode == 2) return run_launch<float, 2>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
     if (mode == 1) return run_launch<float, 1>(L, n_steps, swap_every, trial_off, lam_M, lam_off, dlam, rs, nb);
     return run_launch<float, 0>(L, n_steps, swap_every, trial_off, 0, 0, 0.0, rs, nb);

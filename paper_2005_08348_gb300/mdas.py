@@ -50,6 +50,8 @@ class Desc(C.Structure):
         ("list_skin", C.c_double),
         ("seed", C.c_uint64), ("system_id", C.c_uint32), ("precision", C.c_int32),
         ("cuda_stream", C.c_void_p), ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_ctx", C.c_void_p),
+        ("p_ref", C.c_double), ("tau_p", C.c_double), ("compressibility", C.c_double), ("nstpcouple", C.c_int32),
+        ("box_margin", C.c_double),
     ]
 
 
@@ -71,7 +73,7 @@ class StateView(C.Structure):
     _fields_ = [("pos_fixed", C.c_void_p), ("pos", C.c_void_p), ("vel", C.c_void_p), ("lipid_type", C.c_void_p),
                 ("step", C.c_uint64), ("trial", C.c_uint64), ("move", C.c_uint64), ("at_step", C.c_uint64),
                 ("list_ref", C.c_void_p), ("list_valid", C.c_int32), ("ke_valid", C.c_int32),
-                ("ke", C.c_double * 2)]
+                ("ke", C.c_double * 2), ("box", C.c_double * 3), ("box_velocity", C.c_double * 3)]
 
 
 class Counters(C.Structure):
@@ -90,7 +92,7 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
            "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core",
-           "mdas_wait_timeout_probe"]
+           "mdas_wait_timeout_probe", "mdas_box"]
 
 
 def library_path() -> str:
@@ -187,13 +189,21 @@ class System:
     """One device-resident membrane system built from a `synth.Membrane`."""
 
     def __init__(self, m, precision="fp32", stream=None, torch_allocator=True, tau_t=None, dt=None,
-                 temperature=None, seed=None, system_id=None, eps_rf=None, list_skin=0.0):
+                 temperature=None, seed=None, system_id=None, eps_rf=None, list_skin=0.0, pcouple=None):
+        """pcouple: None (constant volume) or a dict of p_ref (bar), tau_p (ps),
+        compressibility (1/bar), nstpcouple, box_margin (see mdas_system_desc)."""
         L = lib()
         self.m = m
         self.n = m.n_beads
         self.n_lipids = m.n_lipids
         self.precision = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
         d, k = make_desc(m, self.precision, tau_t, dt, temperature, seed, system_id, eps_rf, list_skin)
+        if pcouple:
+            d.p_ref = float(pcouple.get("p_ref", 1.0))
+            d.tau_p = float(pcouple.get("tau_p", 12.0))
+            d.compressibility = float(pcouple.get("compressibility", 3e-4))
+            d.nstpcouple = int(pcouple.get("nstpcouple", 10))
+            d.box_margin = float(pcouple.get("box_margin", 0.05))
         self.stream = _current_stream() if stream is None else int(stream)
         d.cuda_stream = self.stream or None
         if torch_allocator:
@@ -294,10 +304,17 @@ class System:
         self._ck(lib().mdas_get_state(self._ptr, C.byref(v)))
         return dict(pos_u=pu, pos=pos, vel=vel, ltype=lt[: self.n_lipids].copy(), step=v.step, trial=v.trial,
                     move=v.move, at_step=v.at_step, list_ref=ref if v.list_valid else None,
-                    ke=(v.ke[0], v.ke[1]) if v.ke_valid else None)
+                    ke=(v.ke[0], v.ke[1]) if v.ke_valid else None, box=np.array(list(v.box)),
+                    box_velocity=np.array(list(v.box_velocity)))
+
+    def box(self):
+        """(box [nm], dL/dt [nm/ps], pressure of the last box update [bar])."""
+        b, bv, p = (C.c_double * 3)(), (C.c_double * 3)(), (C.c_double * 3)()
+        self._ck(lib().mdas_box(self._ptr, b, bv, p))
+        return np.array(list(b)), np.array(list(bv)), np.array(list(p))
 
     def set_state(self, pos_u=None, pos=None, vel=None, ltype=None, step=0, trial=0, move=0, at_step=0,
-                  list_ref=None, ke=None):
+                  list_ref=None, ke=None, box=None, box_velocity=None):
         """Install a state.  With list_ref and ke as get_state returned them,
         MD continues exactly as it would have from the saved state."""
         a = None if pos_u is None else np.ascontiguousarray(pos_u, np.uint32)
@@ -311,13 +328,18 @@ class System:
                       int(ke is not None))
         if ke is not None:
             v.ke[0], v.ke[1] = float(ke[0]), float(ke[1])
+        if box is not None:
+            for a in range(3):
+                v.box[a] = float(box[a])
+                v.box_velocity[a] = 0.0 if box_velocity is None else float(box_velocity[a])
         self._ck(lib().mdas_set_state(self._ptr, C.byref(v)))
 
     def resume(self, state):
         """set_state with everything get_state returned (an exact continuation)."""
         self.set_state(pos_u=state["pos_u"], vel=state["vel"], ltype=state["ltype"], step=state["step"],
                        trial=state["trial"], move=state["move"], at_step=state["at_step"],
-                       list_ref=state.get("list_ref"), ke=state.get("ke"))
+                       list_ref=state.get("list_ref"), ke=state.get("ke"), box=state.get("box"),
+                       box_velocity=state.get("box_velocity"))
 
     def cell_list(self):
         ids = np.empty(self.n, np.int32)
