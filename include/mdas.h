@@ -154,6 +154,8 @@ typedef struct {
      * current box).  A box below the cell grids' minimum is refused. */
     double box[3];
     double box_velocity[3];
+    double list_box[3];                /* the box the pair list was built at (get_state; set_state uses it
+                                        * with list_valid when list_box[0] > 0, else the current box) */
 } mdas_state_view;
 
 /* Create a device-resident system from a description (Sec. 3 force field,

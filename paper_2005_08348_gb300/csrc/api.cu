@@ -609,8 +609,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         P.rl = ld.rl;
         P.rl2 = P.rl * P.rl;
         P.rl2f = std::nextafter((float)(P.rl2 * (1.0 + 1e-5)), 1e30f);
-        const double half = 0.5 * (P.rl - d->rc);      // a bead may move this far before a rebuild
-        P.dmax2f = (float)(half * half * (1.0 - 1e-4));
+        P.dmax2f = list_dmax2f(P.rl, d->rc, 1.0);      // a bead may move (rl - rc) / 2 before a rebuild
         for (int k = 0; k < 3; ++k) {
             P.ln[k] = ld.ln[k];
             P.lcwu[k] = (unsigned long long)(4294967296.0 / ld.ln[k]);
@@ -1092,6 +1091,7 @@ mdas_status mdas_get_state(const mdas_system *cs, mdas_state_view *out) {
     for (int k = 0; k < 3; ++k) {
         out->box[k] = s->hp.box[k];
         out->box_velocity[k] = s->hp.boxv[k];
+        out->list_box[k] = out->list_valid ? c.lbox[k] : 0.0;
     }
     return MDAS_OK;
 }
@@ -1224,6 +1224,21 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
         launch_nl_build(s->solo->ctx());
         CK(cudaMemcpyAsync(s->hs.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
         k_list_current<<<(n + 255) / 256, 256, 0, s->stream>>>(s->hs, n, 0);
+        if (in->list_box[0] > 0) {
+            // the box the saved list was built at, and the displacement bound that follows
+            double mu = 1.0;
+            for (int k = 0; k < 3; ++k) {
+                if (!(in->list_box[k] > 0) || !std::isfinite(in->list_box[k]))
+                    return fail(s, MDAS_ERR_INVALID_ARG, "set_state: list_box");
+                mu = std::min(mu, s->hp.box[k] / in->list_box[k]);
+            }
+            double lb[3];
+            for (int k = 0; k < 3; ++k) lb[k] = in->list_box[k];
+            const float d2 = mu * s->hp.rl - s->hp.rc > 0.0 ? list_dmax2f(s->hp.rl, s->hp.rc, mu) : 0.0f;
+            CK(cudaMemcpyAsync(s->hs.c->lbox, lb, sizeof(lb), cudaMemcpyHostToDevice, s->stream));
+            CK(cudaMemcpyAsync(&s->hs.c->dmax2f, &d2, sizeof(d2), cudaMemcpyHostToDevice, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        }
     }
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());

@@ -204,9 +204,10 @@ void launch_thermostat(const LaunchCtx &L) {
 // symplectic Euler step of the box equation W d2L_a/dt2 = V (P_a - p_ref) / L_a
 // over the interval (x and y see (Pxx + Pyy) / 2; W^-1 = pc_wc / L_max; V,
 // L_max and L_a of the box before the step), the box-derived parameters, the
-// particles' dt dL_a/dt / L_a for the next interval, and a list rebuild (the
-// list was built at other distances).  A box below the cell grids' minimum
-// stops the system (ERR_BOX) before anything changes.
+// particles' dt dL_a/dt / L_a for the next interval, and the pair list's
+// displacement bound at the new box (a rebuild when none is left).  A box
+// below the cell grids' minimum stops the system (ERR_BOX) before anything
+// changes.
 __global__ void k_pcouple(const SysDev *__restrict__ sys, int n_sys) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n_sys) return;
@@ -240,7 +241,10 @@ __global__ void k_pcouple(const SysDev *__restrict__ sys, int n_sys) {
         P.dtm_pcf[a] = (float)P.dtm_pc[a];
         P.pres[a] = pr[a];
     }
-    C.nl_stale = 1;
+    double mu = 1.0;
+    for (int a = 0; a < 3; ++a) mu = fmin(mu, L[a] / C.lbox[a]);
+    if (mu * P.rl - P.rc > 0.0) C.dmax2f = list_dmax2f(P.rl, P.rc, mu);
+    else C.nl_stale = 1;
 }
 
 void launch_pcouple(const LaunchCtx &L) {

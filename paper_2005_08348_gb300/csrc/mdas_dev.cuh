@@ -160,7 +160,21 @@ struct Counters {
     // of f d_a^2 plus the bonded terms' share (the virial is -S_a / 4)
     long long pv_slot[2][KE_SLOTS][6];
     double pv[6];                      // the last closed step's K_a and S_a, kJ/mol
+    // the pair list's validity under a changing box: the box it was built at
+    // and the squared displacement since the build that invalidates it,
+    // list_dmax2f(rl, rc, mu) with mu = min(1, min_a box_a / lbox_a)
+    double lbox[3];
+    float dmax2f;
 };
+
+// A list of all pairs closer than rl at a box B stays complete (every pair
+// closer than rc is in it) at a box L >= mu B per axis while no bead has
+// moved farther than (mu rl - rc) / 2: the square of that, with a 1e-4
+// relative margin for the FP32 displacement test (host and device).
+__host__ __device__ inline float list_dmax2f(double rl, double rc, double mu) {
+    const double half = 0.5 * (mu * rl - rc);
+    return (float)(half * half * (1.0 - 1e-4));
+}
 
 constexpr int MAX_DRAW_STEPS = 512;    // precomputed thermostat variates per system
 

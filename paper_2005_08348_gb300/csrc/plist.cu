@@ -165,6 +165,10 @@ constexpr size_t group_smem() {
 __device__ void nl_count_item(const SysDev &S, int b0, const Grp &g) {
     const Params &P = *S.p;
     const int i = b0 + g.t;
+    if (b0 == 0 && g.t == 0) {                 // the box this list is built at (read after the build)
+        for (int k = 0; k < 3; ++k) S.c->lbox[k] = P.box[k];
+        S.c->dmax2f = P.dmax2f;
+    }
     if (i < P.n) {
         const int c = lcell_of(P, S.pos[i]);
         const int slot = atomicAdd(&S.lcell_count[c], 1);
@@ -632,7 +636,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         const float ux = (float)(int)(np.x - xr.x) * qs0;
         const float uy = (float)(int)(np.y - xr.y) * qs1;
         const float uz = (float)(int)(np.z - xr.z) * qs2;
-        if (fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > P.dmax2f) sm.sviol = 1;
+        if (fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > (PC ? __ldcg(&C.dmax2f) : P.dmax2f)) sm.sviol = 1;
         const Real ke = (Real)0.5 * (F32 ? (Real)P.massf : (Real)P.mass) * fmr(v.x, v.x, fmr(v.y, v.y, v.z * v.z));
         if (grp == 0) e0 = ke; else e1 = ke;
         if (PC) {

@@ -73,7 +73,8 @@ class StateView(C.Structure):
     _fields_ = [("pos_fixed", C.c_void_p), ("pos", C.c_void_p), ("vel", C.c_void_p), ("lipid_type", C.c_void_p),
                 ("step", C.c_uint64), ("trial", C.c_uint64), ("move", C.c_uint64), ("at_step", C.c_uint64),
                 ("list_ref", C.c_void_p), ("list_valid", C.c_int32), ("ke_valid", C.c_int32),
-                ("ke", C.c_double * 2), ("box", C.c_double * 3), ("box_velocity", C.c_double * 3)]
+                ("ke", C.c_double * 2), ("box", C.c_double * 3), ("box_velocity", C.c_double * 3),
+                ("list_box", C.c_double * 3)]
 
 
 class Counters(C.Structure):
@@ -305,7 +306,8 @@ class System:
         return dict(pos_u=pu, pos=pos, vel=vel, ltype=lt[: self.n_lipids].copy(), step=v.step, trial=v.trial,
                     move=v.move, at_step=v.at_step, list_ref=ref if v.list_valid else None,
                     ke=(v.ke[0], v.ke[1]) if v.ke_valid else None, box=np.array(list(v.box)),
-                    box_velocity=np.array(list(v.box_velocity)))
+                    box_velocity=np.array(list(v.box_velocity)),
+                    list_box=np.array(list(v.list_box)) if v.list_valid else None)
 
     def box(self):
         """(box [nm], dL/dt [nm/ps], pressure of the last box update [bar])."""
@@ -314,7 +316,7 @@ class System:
         return np.array(list(b)), np.array(list(bv)), np.array(list(p))
 
     def set_state(self, pos_u=None, pos=None, vel=None, ltype=None, step=0, trial=0, move=0, at_step=0,
-                  list_ref=None, ke=None, box=None, box_velocity=None):
+                  list_ref=None, ke=None, box=None, box_velocity=None, list_box=None):
         """Install a state.  With list_ref and ke as get_state returned them,
         MD continues exactly as it would have from the saved state."""
         a = None if pos_u is None else np.ascontiguousarray(pos_u, np.uint32)
@@ -332,6 +334,9 @@ class System:
             for a in range(3):
                 v.box[a] = float(box[a])
                 v.box_velocity[a] = 0.0 if box_velocity is None else float(box_velocity[a])
+        if list_box is not None:
+            for a in range(3):
+                v.list_box[a] = float(list_box[a])
         self._ck(lib().mdas_set_state(self._ptr, C.byref(v)))
 
     def resume(self, state):
@@ -339,7 +344,7 @@ class System:
         self.set_state(pos_u=state["pos_u"], vel=state["vel"], ltype=state["ltype"], step=state["step"],
                        trial=state["trial"], move=state["move"], at_step=state["at_step"],
                        list_ref=state.get("list_ref"), ke=state.get("ke"), box=state.get("box"),
-                       box_velocity=state.get("box_velocity"))
+                       box_velocity=state.get("box_velocity"), list_box=state.get("list_box"))
 
     def cell_list(self):
         ids = np.empty(self.n, np.int32)

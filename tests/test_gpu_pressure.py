@@ -145,3 +145,28 @@ def test_constant_volume_systems_report_no_pressure_and_keep_the_box():
     s.md_steps(20)
     box, bv, P = s.box()
     assert np.array_equal(box, m.box) and not bv.any() and not P.any()
+
+
+def test_fp64_shrinking_box_matches_oracle():
+    """A reference pressure above the system's shrinks the box by several
+    percent in 20 steps: the pair list, built at a larger box, keeps every
+    pair within the cutoff (its displacement bound shrinks with the box), so
+    the trajectory still follows the oracle's, which has no list."""
+    m = synth.mcmd_small()
+    pc = dict(PC, p_ref=4000.0, tau_p=2.0, box_margin=0.2)
+    s = mdas.System(m, precision="fp64", pcouple=pc)
+    o = oracle.Oracle(m)
+    so = o.state()
+    b = _baro(pc)
+    lo = np.array(m.box, float)
+    for _ in range(4):
+        s.md_steps(5, swap_every=5)
+        o.md_steps_npt(so, b, 5, swap_every=5)
+        box, bv, P = s.box()
+        assert np.allclose(P, list(b.P), rtol=1e-7, atol=1e-6), (P, list(b.P))
+        assert np.allclose(box, o.box, rtol=1e-10, atol=0)
+        lo = np.minimum(lo, box)
+    assert np.all(lo < 0.95 * m.box)
+    st = s.get_state()
+    assert np.array_equal(st["ltype"], so["ltype"])
+    assert _dx_nm(st["pos_u"], so["pos_u"], box) < 1e-6
