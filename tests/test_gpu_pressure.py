@@ -170,3 +170,27 @@ def test_fp64_shrinking_box_matches_oracle():
     st = s.get_state()
     assert np.array_equal(st["ltype"], so["ltype"])
     assert _dx_nm(st["pos_u"], so["pos_u"], box) < 1e-6
+
+
+def test_batches_mix_coupled_and_constant_volume_systems():
+    """In one batch a pressure-coupled system and a constant-volume one each
+    get the bits of their solo runs; coupled systems at different coupling
+    phases are refused."""
+    m1, m2 = synth.mcmd_small(), synth.mcmd_small(seed=1009)
+    a = mdas.System(m1, precision="fp32", pcouple=PC)
+    b = mdas.System(m2, precision="fp32")
+    mdas.batch_run([a, b], 17, 0)
+    a2 = mdas.System(m1, precision="fp32", pcouple=PC)
+    a2.md_steps(17)
+    b2 = mdas.System(m2, precision="fp32")
+    b2.md_steps(17)
+    for x, y in ((a, a2), (b, b2)):
+        sx, sy = x.get_state(), y.get_state()
+        for k in ("pos_u", "vel", "box", "box_velocity"):
+            assert np.array_equal(sx[k], sy[k]), k
+    assert not np.array_equal(a.get_state()["box"], m1.box)
+    c = mdas.System(m1, precision="fp32", pcouple=PC)
+    c.md_steps(3)
+    with pytest.raises(mdas.MdasError) as e:
+        mdas.batch_run([a, c], 5, 0)
+    assert e.value.status == 1
