@@ -180,7 +180,10 @@ mdas_status mdas_energy(mdas_system *s, mdas_energy_terms *out);
 
 /* n_steps leapfrog steps with velocity rescaling (Sec. 3); after every
  * swap_every-th step one Metropolis exchange trial (Sec. 2, Eq. 1), swap_every
- * = 0 for none.  Trial records go to the system's trial log. */
+ * = 0 for none.  Trial records go to the system's trial log.  With pressure
+ * coupling (desc.tau_p > 0) the box moves after every step whose counter is a
+ * multiple of nstpcouple; MDAS_ERR_UNSTABLE if it would shrink below what the
+ * cell grids allow (the box is left as it was). */
 mdas_status mdas_md_steps(mdas_system *s, int64_t n_steps, int32_t swap_every);
 
 /* n_trials exchange trials at the current coordinates (Sec. 2: a random pair
@@ -244,7 +247,8 @@ mdas_status mdas_cell_list(mdas_system *s, int32_t *sorted_ids, int32_t *cell_st
 
 /* Advance several systems together, each kernel launch covering all of them:
  * md_steps MD steps, then swap_trials exchange trials per system.  All systems
- * must share one precision and one CUDA stream. */
+ * must share one precision and one CUDA stream; pressure-coupled systems must
+ * share nstpcouple and their step counter modulo it (MDAS_ERR_INVALID_ARG). */
 mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32_t md_steps, int32_t swap_trials);
 
 /* Mixing observable of Sec. 4: the in-plane radial distribution of the head
