@@ -17,6 +17,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -207,7 +208,8 @@ def run_gpu(args):
     sysm.set_kernel_timing(True)
     sysm.pair_kernel_time(reset=True)
     c0 = sysm.counters()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+    # the nvidia-smi clock log of the timed region (BENCH_LOG_DIR, else the temp directory)
+    clocks = Clocks(os.path.join(os.environ.get("BENCH_LOG_DIR") or tempfile.gettempdir(),
                                  f"bench_clocks_r{rank}.csv"), local)
     if not args.no_clocks:
         clocks.start()
