@@ -3,6 +3,10 @@
 Each translation unit compiles in its own nvcc process (in parallel), then one
 link step produces paper_2005_08348_gb300/_build/libmdas.so.  The build is
 skipped when the library is newer than every source.
+
+With MDAS_CHECKED=1 in the environment the checked build is made and loaded
+instead: _build_checked/libmdas_checked.so, compiled with -DMDAS_CHECKED (index
+checks that record an error instead of reading or writing out of range).
 """
 from __future__ import annotations
 
@@ -16,8 +20,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(BUILD, "libmdas.so")
+CHECKED = os.environ.get("MDAS_CHECKED", "") not in ("", "0")
+BUILD = os.path.join(HERE, "_build_checked" if CHECKED else "_build")
+LIB = os.path.join(BUILD, "libmdas_checked.so" if CHECKED else "libmdas.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "-I", CSRC]
@@ -25,6 +30,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompil
 # kernel and the separate ones) that must give identical bits: no implicit
 # multiply-add contraction there (the source writes its FMAs explicitly).
 FILE_FLAGS = {"plist.cu": ["-fmad=false"], "swap.cu": ["-fmad=false"]}
+if CHECKED:
+    FLAGS = FLAGS + ["-DMDAS_CHECKED"]
 
 
 def nvcc() -> str:

@@ -342,6 +342,7 @@ mdas_status check_err(mdas_system *s, Batch &b) {
         if (err & ERR_TIMEOUT) why += " bounded wait expired;";
         if (err & ERR_ROUNDS) why += " exchange rounds exhausted;";
         if (err & ERR_BOX) why += " the box shrank below what the cell grids allow;";
+        if (err & ERR_BOUNDS) why += " an index outside its array (checked build);";
         // a wait that gave up left the state partly advanced: refused like an
         // unstable one, reported as the timeout it was
         return fail(s, (err & ERR_TIMEOUT) ? MDAS_ERR_TIMEOUT : MDAS_ERR_UNSTABLE, "unstable:" + why);

@@ -35,7 +35,22 @@ constexpr double COUL = 138.935458;
 
 enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5, TAG_MUTATE = 6 };
 enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8, ERR_BAD_INPUT = 16,
-             ERR_BOX = 32 };
+             ERR_BOX = 32, ERR_BOUNDS = 64 };
+
+// Checked build (nvcc -DMDAS_CHECKED): an index read from the pair list or a
+// lookup table that falls outside its array is recorded in the system's
+// error word (ERR_BOUNDS) and replaced by 0 before the access.  The release
+// build compiles the check away.
+#ifdef MDAS_CHECKED
+__device__ __forceinline__ int checked_index(int *err, int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;
+    atomicOr(err, ERR_BOUNDS);
+    return 0;
+}
+#define MDAS_IDX(C, i, n) checked_index(&(C).err, (i), (n))
+#else
+#define MDAS_IDX(C, i, n) (i)
+#endif
 
 // Per-bead meta word carried in the 4th lane of every position:
 // bits 0-3 current bead type (A), 4-7 alchemical target type (B),

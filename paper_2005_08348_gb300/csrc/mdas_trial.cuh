@@ -99,7 +99,7 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         const int side = lane >= bpl, k = side ? lane - bpl : lane;
         const bool valid = lane < 2 * bpl;
         const int id = (side ? b : a) * bpl + k;
-        const int kk = valid ? S.lk[id] : 0;
+        const int kk = valid ? MDAS_IDX(*S.c, S.lk[id], P.n) : 0;
         const int ta = S.ltype[a], tb = S.ltype[b];
         const uint4 pk = cur[kk];
         const int4 cn = *reinterpret_cast<const int4 *>(S.nl_n + (size_t)kk * NL_G);
@@ -151,7 +151,7 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
             if (sm.it_beg[mid] <= f) lo = mid; else hi = mid - 1;
         }
         const int ci = lo / NL_G, q = lo % NL_G, row = f - sm.it_beg[lo];
-        const int kj = S.nl[(size_t)row * P.lrow + (size_t)sm.chg_k[ci] * NL_G + q];
+        const int kj = MDAS_IDX(*S.c, S.nl[(size_t)row * P.lrow + (size_t)sm.chg_k[ci] * NL_G + q], P.n);
         if (mark) atomicOr(&mk[kj / NL_BEADS / 32], 1u << (kj / NL_BEADS % 32));
         const uint4 pi = sm.chg_pos[ci], pj = cur[kj];
         const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
@@ -259,13 +259,13 @@ __device__ inline double mdas_work_part(const SysDev &S, int x, int par, const G
     const uint4 *cur = S.lpos + (size_t)par * P.n;
     double acc = 0.0;
     if (k < P.bpl) {
-        const int i = l * P.bpl + k, ki = S.lk[i];
+        const int i = l * P.bpl + k, ki = MDAS_IDX(*S.c, S.lk[i], P.n);
         const uint4 pi = cur[ki];
         const int oi = meta_ta(pi.w), ni = meta_tb(pi.w);
         if (oi != ni) {
             const int rows = S.nl_n[(size_t)ki * NL_G + col];
             for (int r = half; r < rows; r += 2) {
-                const int kj = S.nl[(size_t)r * P.lrow + (size_t)ki * NL_G + col];
+                const int kj = MDAS_IDX(*S.c, S.nl[(size_t)r * P.lrow + (size_t)ki * NL_G + col], P.n);
                 const uint4 pj = cur[kj];
                 const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
                 const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];

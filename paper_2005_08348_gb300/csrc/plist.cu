@@ -223,7 +223,7 @@ __device__ void nl_place_item(const SysDev &S, int c0, int par, const Grp &g, Bu
         }
         if (a < cnt) {
             const int id = ka & 0x0fffffff;
-            const int k = lc.x + rank;
+            const int k = MDAS_IDX(*S.c, lc.x + rank, P.n);
             const uint4 p = S.pos[id];
             S.lid[k] = id;
             S.lk[id] = k;
@@ -396,7 +396,8 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
             if (lip != 0) {
                 const int kl = meta_k(pi.w);
                 for (int p = 0; p < P.npart[kl]; ++p)
-                    S.bslot[(size_t)ki * NL_PART + p] = S.lk[(int)(lip - 1) * P.bpl + P.part[kl][p]];
+                    S.bslot[(size_t)ki * NL_PART + p] =
+                        S.lk[MDAS_IDX(C, (int)(lip - 1) * P.bpl + P.part[kl][p], P.n_lipid_beads)];
             }
         }
     }
@@ -425,7 +426,8 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     // (rows 0 .. 3 always exist; entries past the end hold valid indices)
     const int *__restrict__ lst = S.nl + (size_t)k * NL_G + gl;
     const size_t rs = (size_t)P.lrow;
-    int j0 = __ldg(lst), j1 = __ldg(lst + rs), j2 = __ldg(lst + 2 * rs), j3 = __ldg(lst + 3 * rs);
+    int j0 = MDAS_IDX(C, __ldg(lst), n), j1 = MDAS_IDX(C, __ldg(lst + rs), n);
+    int j2 = MDAS_IDX(C, __ldg(lst + 2 * rs), n), j3 = MDAS_IDX(C, __ldg(lst + 3 * rs), n);
     uint4 pi = make_uint4(0u, 0u, 0u, 0u);
     int cnt = 0, id = 0;
     if (valid) {
@@ -452,7 +454,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     uint4 q0 = cur[j0], q1 = cur[j1], q2 = cur[j2], q3 = cur[j3];
     if (valid) {
         if (gl == 0) {
-            id = S.lid[k];
+            id = MDAS_IDX(C, S.lid[k], n);
             const char *gv = reinterpret_cast<const char *>(reinterpret_cast<const V4 *>(S.vel) + id);
             for (int h = 0; h < (int)sizeof(V4); h += 16) cp_async16(reinterpret_cast<char *>(&sm.svel[il]) + h, gv + h);
         }
@@ -460,7 +462,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         if (meta_lip(pi.w) >= 0) {
             const int kl = meta_k(pi.w);
             for (int p = gl; p < P.npart[kl]; p += NL_G)
-                cp_async16(&sm.spart[il][p], cur + S.bslot[(size_t)k * NL_PART + p]);
+                cp_async16(&sm.spart[il][p], cur + MDAS_IDX(C, S.bslot[(size_t)k * NL_PART + p], n));
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
@@ -545,7 +547,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     // 4 further on and the index of the row 8 further on, so every load has
     // a whole group of pairs to arrive (entries past the end read slot 0)
     const int rows = cnt;
-    auto idx = [&](int r) { return r < rows ? __ldg(lst + (size_t)r * rs) : 0; };
+    auto idx = [&](int r) { return r < rows ? MDAS_IDX(C, __ldg(lst + (size_t)r * rs), n) : 0; };
     for (int pass = 0;; ++pass) {
         j0 = idx(4); j1 = idx(5); j2 = idx(6); j3 = idx(7);
         for (int m = 0; m < rows; m += 4) {
