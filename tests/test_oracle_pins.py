@@ -732,3 +732,21 @@ def test_npt_without_coupling_is_plain_md():
     assert ra == rb
     assert np.array_equal(a["pos_u"], b["pos_u"]) and np.array_equal(a["vel"], b["vel"])
     assert np.all(O.box == m.box)
+
+
+def test_npt_pressure_is_that_of_the_step_forces_and_new_velocities():
+    """The pressure a box update uses is or_pressure (pinned above) taken at
+    the positions the step started from and the box before the update, with
+    the velocities the step produced."""
+    m = synth.tiny(n_side=3, n_water=120, seed=36)
+    O = oracle.Oracle(m)
+    st = O.state()
+    x0, L0 = st["pos_u"].copy(), O.box
+    b = oracle.barostat(nst=1)
+    O.md_steps_npt(st, b, 1)
+    L1 = O.box
+    assert not np.array_equal(L1, L0)
+    O.box = L0
+    P, _, _ = O.pressure(x0, st["vel"])
+    O.box = L1
+    assert np.allclose(list(b.P), P, rtol=1e-12, atol=1e-9), (list(b.P), P)
