@@ -60,7 +60,7 @@ def g_of_r(counts, n_heads, box, r_max):
 
 def max_g(system, lipid_type=1, head_k=1, r_max=3.0, n_bins=20) -> float:
     c, nh = system.head_rdf(lipid_type, head_k, r_max, n_bins)
-    return float(g_of_r(c, nh, system.m.box, r_max)[2].max())
+    return float(g_of_r(c, nh, system.box()[0], r_max)[2].max())   # the current box (pressure coupling)
 
 
 def leaflets(pos_u, lipid_first_bead, bpl: int, head_k: int = 1) -> np.ndarray:
