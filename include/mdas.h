@@ -415,9 +415,12 @@ double mdas_server_clock(const mdas_server *sv);
  * charge); 0 for an invalid description. */
 size_t mdas_system_footprint(const mdas_system_desc *d);
 
-/* The current box (nm), its velocity dL/dt (nm/ps) and the pressure tensor
- * diagonal (bar) of the last box update (zero before the first update and for
- * systems without pressure coupling).  Any pointer may be NULL. */
+/* Pressure coupling state (Sec. 3): the current box (nm), its velocity dL/dt
+ * (nm/ps) and the pressure tensor diagonal (bar) of the last box update,
+ * P_a = 2 (K_a - Xi_a) / V with K the kinetic energy of v(t + dt/2) and Xi
+ * the virial of F(x(t)) (zero before the first update and for systems
+ * without pressure coupling).  Host arrays of 3 doubles; any pointer may be
+ * NULL.  Errors: MDAS_ERR_INVALID_ARG for a NULL system. */
 mdas_status mdas_box(const mdas_system *s, double box[3], double box_velocity[3], double pressure[3]);
 
 /* Health check of the failure path: one block of the persistent MD kernel's
