@@ -46,8 +46,15 @@ struct ListDims {
     int ln[3], n_lcells, lcapc, lcap, lrow;
 };
 
+// The fraction by which each box edge may shrink under pressure coupling
+// (the cell grids are sized for it); 0 for a fixed box.
+double grid_shrink(const mdas_system_desc *d) {
+    if (!(d->tau_p > 0)) return 0.0;
+    return d->box_margin > 0 ? std::min(d->box_margin, 0.5) : 0.05;
+}
+
 // Pair-list grid of a system whose box edges may shrink to (1 - shrink) of
-// their length (pressure coupling; 0 for a fixed box).
+// their length.
 ListDims list_dims(const mdas_system_desc *d, double shrink = 0.0) {
     ListDims L;
     const double skin = d->list_skin > 0 ? d->list_skin : 0.3;
@@ -544,7 +551,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     if (d->precision != MDAS_FP32 && d->precision != MDAS_FP64) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: precision");
     // pressure coupling: the cell grids hold for every edge down to (1 - shrink) of its length
     const bool pcouple = d->tau_p > 0;
-    const double shrink = !pcouple ? 0.0 : d->box_margin > 0 ? std::min(d->box_margin, 0.5) : 0.05;
+    const double shrink = grid_shrink(d);
     if (pcouple && !(d->compressibility >= 0 && std::isfinite(d->p_ref) && std::isfinite(d->tau_p)))
         return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: pressure coupling parameters");
     int nc[3];
@@ -1476,8 +1483,9 @@ struct ActiveJob {
 
 // arena bytes of a system (the sizes mdas_create_system allocates)
 size_t arena_estimate(const mdas_system_desc *d) {
+    const double shrink = grid_shrink(d);
     int nc = 1;
-    for (int k = 0; k < 3; ++k) nc *= std::max(3, (int)std::floor(d->box[k] / d->rc));
+    for (int k = 0; k < 3; ++k) nc *= std::max(3, (int)std::floor(d->box[k] * (1.0 - shrink) / d->rc));
     const double mean = (double)d->n_beads / nc;
     const size_t capc = std::max(32, (int)std::ceil(4.0 * mean / 32.0) * 32);
     const size_t n = d->n_beads, vsz = d->precision == MDAS_FP64 ? 32 : 16;
@@ -1486,7 +1494,7 @@ size_t arena_estimate(const mdas_system_desc *d) {
                8 * nc + 24 * nc * capc + vsz * nc * capc + 4 * n + 16 * nc + 24 * nbb + 32 * nc + 16 * n + vsz * n +
                (16 + 8 + 72 + 4 + 128 + 64) * (size_t)MAX_ROUND_TRIALS + sizeof(TrialRec) * (size_t)LOG_CAP + 512 +
                32 * MAX_DRAW_STEPS + 24 * n + 16 * std::max(d->n_lipids, 1) + 16 * RDF_MAX_BINS + 8;
-    const ListDims ld = list_dims(d);
+    const ListDims ld = list_dims(d, shrink);
     t += 12ull * ld.n_lcells + 4ull * ld.n_lcells * ld.lcapc + 4 * n + 4 * n + 32 * n + 16 * n + 4ull * NL_G * n +
          4ull * (ld.lcap / NL_G) * ld.lrow + 4ull * NL_PART * n + 8ull * ((n + NL_BEADS - 1) / NL_BEADS / 32 + 1);
     return t + 51 * 256;

@@ -186,6 +186,19 @@ def make_desc(m, precision=MDAS_FP32, tau_t=None, dt=None, temperature=None, see
     return d, k
 
 
+def set_pcouple(d, pcouple):
+    """The pressure-coupling fields of a description from a dict of p_ref
+    (bar), tau_p (ps), compressibility (1/bar), nstpcouple and box_margin
+    (None: constant volume)."""
+    if pcouple:
+        d.p_ref = float(pcouple.get("p_ref", 1.0))
+        d.tau_p = float(pcouple.get("tau_p", 12.0))
+        d.compressibility = float(pcouple.get("compressibility", 3e-4))
+        d.nstpcouple = int(pcouple.get("nstpcouple", 10))
+        d.box_margin = float(pcouple.get("box_margin", 0.05))
+    return d
+
+
 class System:
     """One device-resident membrane system built from a `synth.Membrane`."""
 
@@ -199,12 +212,7 @@ class System:
         self.n_lipids = m.n_lipids
         self.precision = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
         d, k = make_desc(m, self.precision, tau_t, dt, temperature, seed, system_id, eps_rf, list_skin)
-        if pcouple:
-            d.p_ref = float(pcouple.get("p_ref", 1.0))
-            d.tau_p = float(pcouple.get("tau_p", 12.0))
-            d.compressibility = float(pcouple.get("compressibility", 3e-4))
-            d.nstpcouple = int(pcouple.get("nstpcouple", 10))
-            d.box_margin = float(pcouple.get("box_margin", 0.05))
+        set_pcouple(d, pcouple)
         self.stream = _current_stream() if stream is None else int(stream)
         d.cuda_stream = self.stream or None
         if torch_allocator:
@@ -463,9 +471,10 @@ class Server:
             pass
 
 
-def footprint(m, precision=MDAS_FP32):
+def footprint(m, precision=MDAS_FP32, pcouple=None):
     """Device bytes a system of this membrane occupies."""
     d, keep = make_desc(m, precision)
+    set_pcouple(d, pcouple)
     L = lib()
     L.mdas_system_footprint.restype = C.c_size_t
     return int(L.mdas_system_footprint(C.byref(d)))

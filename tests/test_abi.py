@@ -109,3 +109,16 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == want
+
+
+def test_footprint_counts_the_pressure_coupling_grids_without_a_gpu():
+    """A pressure-coupled system sizes its cell grids for a box that may
+    shrink, so its lists hold more entries per bead; the admission estimate
+    (host arithmetic only) follows the same sizing."""
+    from paper_2005_08348_gb300 import mdas, synth
+    m = synth.mcmd_small()
+    nvt = mdas.footprint(m)
+    npt = mdas.footprint(m, pcouple=dict(box_margin=0.05))
+    wide = mdas.footprint(m, pcouple=dict(box_margin=0.2))
+    assert nvt < npt < wide
+    assert mdas.footprint(m, pcouple=None) == nvt
