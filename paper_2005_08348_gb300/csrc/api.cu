@@ -499,7 +499,7 @@ mdas_status run_trials(mdas_system *s, Batch &b, int n, int *rounds_out) {
             launch_swap_dE(L, m);
             launch_swap_resolve(L, m);
             ++rounds;
-            int pend, err;
+            int pend = 0, err = 0;
             mdas_status st = batch_status(s, b, &pend, &err);
             if (st != MDAS_OK) return st;
             if (pend == 0) break;
@@ -1569,7 +1569,10 @@ mdas_status finish_job(mdas_server *sv, ActiveJob &a) {
         std::vector<uint32_t> pu(3ull * s->n);
         std::vector<double> v(3ull * s->n);
         std::vector<int32_t> lt(std::max(s->n_lip, 1));
-        mdas_state_view sv_{pu.data(), nullptr, v.data(), lt.data(), 0, 0, 0, 0};
+        mdas_state_view sv_{};
+        sv_.pos_fixed = pu.data();
+        sv_.vel = v.data();
+        sv_.lipid_type = lt.data();
         st = mdas_get_state(s, &sv_);
         if (st != MDAS_OK) return st;
         uint64_t h = 1469598103934665603ull;
