@@ -43,6 +43,7 @@ def lib():
             _lib.or_energy.restype = C.c_double
             _lib.or_swap_dE.restype = C.c_double
             _lib.or_swap_dE_full.restype = C.c_double
+            _lib.or_work_increment.restype = C.c_double
             _lib.or_bussi_alpha.restype = C.c_double
             _lib.or_chi2.restype = C.c_double
             _lib.or_uniform.restype = C.c_double
@@ -216,6 +217,12 @@ class Oracle:
     def swap_dE_full(self, pos_u, ltype, a, b, cells=False):
         return lib().or_swap_dE_full(C.byref(self.s), _p(_u32(pos_u).reshape(-1)), _p(_i32(ltype)),
                                      int(a), int(b), int(cells))
+
+    def work_increment(self, pos_u, btA, btB, l0, l1):
+        """U_{l1}(x) - U_{l0}(x) over the pairs with a bead whose A and B types
+        differ (or_work_increment): the work of one lambda step (Eq. 2)."""
+        return lib().or_work_increment(C.byref(self.s), _p(_u32(pos_u).reshape(-1)), _p(_i32(btA)), _p(_i32(btB)),
+                                       C.c_double(l0), C.c_double(l1))
 
     def swap_proposal(self, t):
         a, b, u = C.c_int(), C.c_int(), C.c_double()

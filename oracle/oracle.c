@@ -487,6 +487,30 @@ double or_swap_dE_full(const or_sys *s, const uint32_t *pu, const int *ltype, in
     return e1 - e0;
 }
 
+/* Work of one lambda step at fixed coordinates (Eq. 2): U_{l1}(x) - U_{l0}(x)
+ * of U(lam) between the bead types btA and btB.  A pair whose two beads keep
+ * their type contributes the same to both energies, so the sum runs over the
+ * pairs with at least one bead whose A and B types differ (a pair of two such
+ * beads once), each pair's energy taken exactly as the full energy takes it
+ * (add_pair, linear or soft-core path). */
+double or_work_increment(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double l0, double l1)
+{
+    int n = s->n_beads;
+    double dw = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (btA[i] == btB[i]) continue;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (btA[j] != btB[j] && j < i) continue; /* both changed: count once */
+            double t0[6] = {0, 0, 0, 0, 0, 0}, t1[6] = {0, 0, 0, 0, 0, 0};
+            add_pair(s, pu, btA, btB, l0, i, j, t0, NULL, NULL);
+            add_pair(s, pu, btA, btB, l1, i, j, t1, NULL, NULL);
+            dw += (t1[0] + t1[1]) - (t0[0] + t0[1]);
+        }
+    }
+    return dw;
+}
+
 /* Proposal of trial number t: two lipid indices by 32-bit multiply-shift
  * and u in (0, 1] from one Philox call. */
 void or_swap_proposal(const or_sys *s, uint32_t t, int *a, int *b, double *u)

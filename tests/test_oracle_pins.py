@@ -272,6 +272,110 @@ def test_mdas_work_without_dynamics_is_the_exchange_energy(K):
     assert res["w"] == pytest.approx(dU, abs=1e-9 * abs(dU) + 1e-9)
 
 
+def _free_flight_system():
+    """Three one-bead lipids, no charges, no bonds.  Only bead types 1 and 2
+    interact (eps 3 kJ/mol).  Lipid a (type 0) flies at 2.5 nm/ps towards the
+    resting probe X (type 2), from 1.3 nm; lipid b (type 1) rests 1.6 nm from
+    X.  In state A nothing is within rc of a partner it interacts with, so
+    every bead moves in a straight line.  Exchanging a and b makes a interact
+    with X."""
+    eps = np.zeros((10, 10))
+    eps[1, 2] = eps[2, 1] = 3.0
+    m = beads([[0.7, 2.0, 2.0], [2.0, 3.6, 2.0], [2.0, 2.0, 2.0]], [0, 1, 2], box=(4.0, 4.0, 4.0), eps=eps,
+              charge=np.zeros(10))
+    m.vel = np.zeros((3, 3))
+    m.vel[0, 0] = 2.5
+    return m
+
+
+def test_mdas_work_is_taken_after_each_block():
+    """Eq. 2 with dynamics (M > 0): the work of a lambda step is
+    U_{lam_k}(x_k) - U_{lam_k-1}(x_k) at the coordinates x_k reached *after*
+    the block's M steps.  In free flight (thermostat off, no force in state
+    A) x_1 = x_0 + M rint(v dt 2^32 / L) exactly.  After 8 steps a is 0.9 nm
+    from X, inside rc, so w is the shifted Lennard-Jones energy there; at
+    x_0 it was 1.3 nm away, so taking the work before the block would give
+    exactly 0."""
+    m = _free_flight_system()
+    o = oracle.Oracle(m, tau_t=0.0)
+    M = 8
+    q = m.dt * 2 ** 32 / m.box[0]
+    x1 = m.pos_u.astype(np.int64)
+    x1[0, 0] = (x1[0, 0] + M * int(np.rint(2.5 * q))) % 2 ** 32
+    x1 = x1.astype(np.uint32)
+    st = o.state()
+    res = o.mdas_move(st, 1, 1, M, pairs=[[0, 1]], cells=False)
+    btA, btB = o.bead_types([0, 1, 2]), o.bead_types([1, 0, 2])
+    uA1 = o.energy(x1, btA=btA, cells=False, forces=False)[0]["total"]
+    uB1 = o.energy(x1, btA=btB, cells=False, forces=False)[0]["total"]
+    uA0 = o.energy(m.pos_u, btA=btA, cells=False, forces=False)[0]["total"]
+    uB0 = o.energy(m.pos_u, btA=btB, cells=False, forces=False)[0]["total"]
+    assert uA1 == 0.0 and uA0 == 0.0 and uB0 == 0.0
+    r = float((int(x1[2, 0]) - int(x1[0, 0])) * (m.box[0] / 2 ** 32))
+    assert 0.85 < r < 0.95
+    lj = lambda x: 4 * 3.0 * ((SIG / x) ** 12 - (SIG / x) ** 6)
+    assert res["w"] == pytest.approx(lj(r) - lj(RC), rel=1e-12)
+    assert res["w"] == pytest.approx(uB1 - uA1, abs=1e-12)
+    assert res["w"] < -0.1                               # the before-the-block reading gives uB0 - uA0 = 0
+    assert res["accepted"]                                # w < 0
+    assert np.array_equal(st["pos_u"], x1)
+    assert st["at_step"] == M
+
+
+@pytest.mark.parametrize("nf", [3, 4, 7])
+def test_bussi_fast_coupling_draws_the_canonical_kinetic_energy(nf):
+    """Bussi et al. (2007) at tau_T -> 0 (c = exp(-dt / tau_T) = 0): the new
+    kinetic energy is drawn from the canonical distribution of Nf degrees of
+    freedom itself, K_new = (K_t / Nf) chi2(Nf), because R1^2 and the
+    chi2(Nf - 1) variate together make Nf squared normals.  A chi2(Nf) in
+    place of chi2(Nf - 1) gives chi2(Nf + 1), which the test rejects."""
+    from scipy.stats import chi2, kstest
+    o = oracle.Oracle(synth.tiny(), tau_t=1e-5, dt=0.02)
+    kt, K = 7.5, 3.0
+    x = np.array([o.bussi_alpha(K, nf, kt, 0, i) ** 2 * K * nf / kt for i in range(20000)])
+    assert kstest(x, chi2(nf).cdf).pvalue > 1e-3
+    assert kstest(x, chi2(nf + 1).cdf).pvalue < 1e-6
+
+
+def test_bussi_kinetic_energy_variance():
+    """Bussi et al. (2007): with s = (1 - c) K_t / Nf the new kinetic energy is
+    c K + 2 sqrt(c K s) R1 + s chi2(Nf), so its mean is c K + (1 - c) K_t and
+    its variance 2 Nf s^2 + 4 c K s.  A wrong R1 coefficient or a dropped
+    cross term moves the variance far outside the bound."""
+    o = oracle.Oracle(synth.tiny(), tau_t=0.1, dt=0.02)
+    c = math.exp(-0.02 / 0.1)
+    nf, kt, K = 60, 30.0, 20.0
+    n = 40000
+    kn = np.array([o.bussi_alpha(K, nf, kt, 0, i) ** 2 * K for i in range(n)])
+    s = (1 - c) * kt / nf
+    mean, var = c * K + (1 - c) * kt, 2 * nf * s * s + 4 * c * K * s
+    assert abs(kn.mean() - mean) < 4 * math.sqrt(var / n)
+    assert abs(kn.var() / var - 1) < 0.05, (kn.var(), var)
+
+
+@pytest.mark.parametrize("soft", [0.0, 0.05])
+def test_work_increment_equals_difference_of_full_energies(soft):
+    """The work of one lambda step summed over the pairs with a changing bead
+    equals the difference of the two full energies U_{l1} - U_{l0}, for two
+    exchanged pairs of a three-type bilayer, linear and soft-core paths."""
+    m = synth.tiny(seed=49, n_lipid_types=3)
+    o = oracle.Oracle(m, soft_core=soft)
+    lt = m.lipid_type
+    pairs = o.mdas_pairs(lt, 0, 2)
+    assert len(pairs) == 2
+    ltB = lt.copy()
+    for a, b in pairs:
+        ltB[a], ltB[b] = lt[b], lt[a]
+    btA, btB = o.bead_types(lt), o.bead_types(ltB)
+    assert (btA != btB).sum() >= 2
+    for l0, l1 in [(0.0, 0.25), (0.4, 0.7), (0.9, 1.0)]:
+        full = (o.energy(m.pos_u, btA=btA, btB=btB, lam=l1, cells=False, forces=False)[0]["total"] -
+                o.energy(m.pos_u, btA=btA, btB=btB, lam=l0, cells=False, forces=False)[0]["total"])
+        got = o.work_increment(m.pos_u, btA, btB, l0, l1)
+        assert got == pytest.approx(full, abs=1e-9 * max(1.0, abs(full)))
+        assert abs(got) > 1e-3
+
+
 def test_lambda_path_is_linear():
     """U(lambda) = (1 - lambda) U_A + lambda U_B (Sec. 2): forces are linear too."""
     m = synth.tiny(seed=46)
