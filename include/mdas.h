@@ -223,6 +223,34 @@ mdas_status mdas_mutation_trials(mdas_system *s, int32_t n_trials, const double 
 mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
                                  const int32_t *pairs, mdas_move_result *r);
 
+/* The same move with every lambda block laid open, for checking the
+ * trajectory against an independent evaluation of Eq. 2 block by block: the
+ * MD of the trajectory runs one lambda block per launch (which gives the bits
+ * of the single run of mdas_alchemical_move), and after block k (0-based) the
+ * work it added, U_{lambda_{k+1}}(x_{k+1}) - U_{lambda_k}(x_{k+1}), goes to
+ * w_blocks[k], the positions to pos_blocks[k][n_beads][3] (fixed point, as
+ * mdas_get_state) and the velocities to vel_blocks[k][n_beads][3] (nm/ps).
+ * Host arrays of n_lambda entries each, any of them NULL.  The state the move
+ * leaves and r are those of mdas_alchemical_move. */
+mdas_status mdas_alchemical_move_trace(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                                       const int32_t *pairs, mdas_move_result *r, double *w_blocks,
+                                       uint32_t *pos_blocks, double *vel_blocks);
+
+/* Exchange of lipids between the two leaflets as an alchemical move (Sec. 4
+ * proposes such moves to equilibrate the composition of the two leaflets):
+ * mdas_alchemical_move with its n_pairs pairs drawn across the leaflets.
+ * Candidate j of move m takes Philox (j, m, 7, 0): a by multiply-shift of
+ * word 0 and b of word 1, each over all lipids; the candidate is kept when a
+ * lies in leaflet 0 and b in leaflet 1, their types differ and neither is
+ * used yet (at most 64 n_pairs + 64 candidates).  A lipid is in leaflet 0
+ * when its bead head_k lies above its last bead (the rule of mdas_head_rdf),
+ * taken at the start of the move.  The proposal is uniform over such pairs
+ * and symmetric: an exchange moves no lipid to the other leaflet.  Errors:
+ * MDAS_ERR_INVALID_ARG for head_k outside [0, beads_per_lipid - 1) and the
+ * errors of mdas_alchemical_move. */
+mdas_status mdas_interleaflet_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                                   int32_t head_k, mdas_move_result *r);
+
 /* FP64 energy change U(after) - U(before) of setting lipids[k] to type
  * new_types[k] (k < n, distinct lipids) at the current coordinates, without
  * applying it (the Delta U of Eq. 1 for any collective type change). */
@@ -232,6 +260,28 @@ mdas_status mdas_delta_energy(mdas_system *s, const int32_t *lipids, const int32
 /* Copy the state to host arrays (any pointer may be NULL); list_valid and
  * ke_valid report whether list_ref and ke[] hold the continuation state. */
 mdas_status mdas_get_state(const mdas_system *s, mdas_state_view *out);
+
+/* Zero-copy device views of a system's state, for frameworks that work on
+ * device memory (a torch tensor over these addresses, for instance).  The
+ * pointers are the library's own arrays: valid until mdas_destroy_system,
+ * holding the state the last call left (every call returns after its stream
+ * is done), and read-only - writing through them would bypass the pair list
+ * and cell bookkeeping; install a state with mdas_set_state instead.
+ * pos: n_beads 16-byte records in bead id order, x, y, z as uint32 fractions
+ * of the box (x = u L / 2^32) and a meta word (bits 0-3 bead type, 4-7
+ * alchemical target type, 8-11 index within the lipid, 12-31 lipid index + 1,
+ * 0 for water).  vel: n_beads records of vel_stride_bytes in bead id order,
+ * x, y, z (nm/ps) and one unused lane, float (FP32 systems, 16 bytes) or
+ * double (FP64 systems, 32 bytes).  lipid_type: n_lipids int32.  box: the
+ * current box (nm).  Errors: MDAS_ERR_INVALID_ARG for a NULL argument. */
+typedef struct {
+    const void *pos;
+    const void *vel;
+    const int32_t *lipid_type;
+    int32_t n_beads, n_lipids, precision, vel_stride_bytes;
+    double box[3];
+} mdas_device_view;
+mdas_status mdas_device_ptrs(mdas_system *s, mdas_device_view *out);
 
 /* Install a state from host arrays; clears MDAS_ERR_UNSTABLE.  With
  * list_valid, the pair list is built at list_ref (which must lie within half
@@ -356,14 +406,15 @@ mdas_status mdas_get_counters(const mdas_system *s, mdas_counters *out);
  *
  * Limits: n_beads <= 16384, at most 2048 cells (floor(L/rc) per edge), at
  * most 64 beads in a cell.  Errors: MDAS_ERR_INVALID_ARG for a NULL pointer,
- * a size beyond these limits or a lipid type outside the table;
- * MDAS_ERR_UNSTABLE when a cell holds more than 64 beads; MDAS_ERR_CUDA.
+ * a size beyond these limits (a cell holding more than 64 beads
+ * included) or a lipid type outside the table; MDAS_ERR_CUDA.
  *
  * The first call on a device looks up the scratch array's device address
  * (with that device current); make that first call before any stream capture.
- * Every call shares the array and leaves its contents behind (each call clears
- * what must start at zero); calls that overlap on the GPU race, so serialise
- * them. */
+ * Every call reads the device error word back and waits for its stream before
+ * it returns.  Every call shares the array and leaves its contents behind
+ * (each call clears what must start at zero); calls that overlap on the GPU
+ * race, so serialise them. */
 mdas_status mdas_forces_noalloc(const mdas_system_desc *d, const uint32_t *pos_fixed, const int32_t *lipid_type,
                                 double *f_out);
 

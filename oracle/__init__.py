@@ -48,6 +48,7 @@ def lib():
             _lib.or_chi2.restype = C.c_double
             _lib.or_uniform.restype = C.c_double
             _lib.or_mdas_pairs.restype = C.c_int
+            _lib.or_interleaflet_pairs.restype = C.c_int
     return _lib
 
 
@@ -290,6 +291,20 @@ class Oracle:
         pairs = np.zeros(2 * n_pairs, np.int32)
         mt = 64 * n_pairs + 64 if max_tries is None else max_tries
         np_ = lib().or_mdas_pairs(C.byref(self.s), _p(_i32(ltype)), C.c_uint32(move), int(n_pairs), int(mt), _p(pairs))
+        return pairs[: 2 * np_].reshape(-1, 2)
+
+    def leaflets(self, pos_u, head_k=1):
+        """Leaflet of every lipid (or_leaflets): 0 when bead head_k lies above the last bead."""
+        leaf = np.empty(max(self.s.n_lipids, 1), np.int32)
+        lib().or_leaflets(C.byref(self.s), _p(_u32(pos_u).reshape(-1)), int(head_k), _p(leaf))
+        return leaf[: self.s.n_lipids]
+
+    def interleaflet_pairs(self, pos_u, ltype, move, n_pairs, head_k=1, max_tries=None):
+        """Pairs of an exchange between the leaflets for move `move` (or_interleaflet_pairs)."""
+        pairs = np.zeros(2 * max(n_pairs, 1), np.int32)
+        mt = 64 * n_pairs + 64 if max_tries is None else max_tries
+        np_ = lib().or_interleaflet_pairs(C.byref(self.s), _p(_u32(pos_u).reshape(-1)), _p(_i32(ltype)),
+                                          C.c_uint32(move), int(n_pairs), int(mt), int(head_k), _p(pairs))
         return pairs[: 2 * np_].reshape(-1, 2)
 
     def mdas_move(self, st, n_pairs, n_lambda, md_per_lambda, pairs=None, cells=True):

@@ -47,7 +47,7 @@
 #define OR_TWO32 4294967296.0
 
 enum { OR_TAG_THERMO = 1, OR_TAG_SWAP = 2, OR_TAG_MDAS_PAIR = 3, OR_TAG_MDAS_ACC = 4,
-       OR_TAG_AT_THERMO = 5 , OR_TAG_MUTATE = 6 };
+       OR_TAG_AT_THERMO = 5 , OR_TAG_MUTATE = 6, OR_TAG_LEAFLET = 7 };
 
 typedef struct {
     int n_beads, n_lipids, bpl, n_bt, n_lt;
@@ -854,21 +854,60 @@ void or_mdas_move(const or_sys *s, or_state *st, int n_pairs, int n_lambda, int 
  * modulo 2^32 as signed 32-bit values (the minimum image). */
 static double frac_diff(uint32_t a, uint32_t b, double L) { return (double)(int32_t)(a - b) * (L / 4294967296.0); }
 
+/* Leaflet of lipid l: 0 when its bead head_k lies above its last bead, i.e.
+ * the z steps along the chain from that bead to the last one, each bond at
+ * its minimum image, sum to a drop; else 1. */
+static int leaflet_of(const or_sys *s, const uint32_t *pu, int l, int head_k)
+{
+    long long drop = 0;
+    for (int k = head_k; k < s->bpl - 1; ++k) {
+        const int b = s->lipid_first[l] + k;
+        drop += (int32_t)(pu[3 * b + 2] - pu[3 * (b + 1) + 2]);
+    }
+    return drop > 0 ? 0 : 1;
+}
+
+void or_leaflets(const or_sys *s, const uint32_t *pu, int head_k, int *leaf)
+{
+    for (int l = 0; l < s->n_lipids; ++l) leaf[l] = leaflet_of(s, pu, l, head_k);
+}
+
+/* Sec. 4 proposes exchanging lipids between the two leaflets.  Pairs for
+ * move m: candidate j draws Philox (j, m, 7, 0), a by multiply-shift of
+ * word 0 and b of word 1 over all lipids; it is kept when a lies in leaflet
+ * 0 and b in leaflet 1 (leaflets at positions pu), their types differ and
+ * neither is already used.  Every such pair is equally likely per
+ * candidate, and an exchange leaves every lipid in its leaflet, so the
+ * proposal is symmetric. */
+int or_interleaflet_pairs(const or_sys *s, const uint32_t *pu, const int *ltype, uint32_t m, int n_pairs,
+                          int max_tries, int head_k, int *pairs)
+{
+    const int nl = s->n_lipids;
+    int *leaf = malloc(sizeof(int) * (nl > 0 ? nl : 1));
+    char *used = calloc((size_t)(nl > 0 ? nl : 1), 1);
+    or_leaflets(s, pu, head_k, leaf);
+    int np = 0;
+    for (int j = 0; j < max_tries && np < n_pairs; ++j) {
+        uint32_t w[4];
+        draw(s, (uint32_t)j, m, OR_TAG_LEAFLET, 0, w);
+        int a = (int)(((uint64_t)w[0] * (uint64_t)nl) >> 32);
+        int b = (int)(((uint64_t)w[1] * (uint64_t)nl) >> 32);
+        if (a == b || ltype[a] == ltype[b] || used[a] || used[b]) continue;
+        if (!(leaf[a] == 0 && leaf[b] == 1)) continue;
+        used[a] = used[b] = 1;
+        pairs[2 * np] = a; pairs[2 * np + 1] = b;
+        np++;
+    }
+    free(leaf); free(used);
+    return np;
+}
+
 void or_head_rdf(const or_sys *s, const uint32_t *pu, const int *ltype, int lt_sel, int head_k,
                  double r_max, int n_bins, long long *counts, int *n_heads)
 {
     const int nl = s->n_lipids;
     int *leaf = (int *)malloc(sizeof(int) * (nl > 0 ? nl : 1));
-    for (int l = 0; l < nl; ++l) {
-        /* head above the last bead: the z steps along the chain from the head
-         * to the last bead, each bond at its minimum image, sum to a drop */
-        long long drop = 0;
-        for (int k = head_k; k < s->bpl - 1; ++k) {
-            const int b = s->lipid_first[l] + k;
-            drop += (int32_t)(pu[3 * b + 2] - pu[3 * (b + 1) + 2]);
-        }
-        leaf[l] = drop > 0 ? 0 : 1;
-    }
+    or_leaflets(s, pu, head_k, leaf);
     for (int k = 0; k < 2 * n_bins; ++k) counts[k] = 0;
     n_heads[0] = n_heads[1] = 0;
     const double dr = r_max / n_bins, r2max = r_max * r_max;

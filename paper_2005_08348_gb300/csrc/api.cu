@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/mdas.h"
+#include "host_params.h"
 #include "mdas_dev.cuh"
 
 using namespace mdas;
@@ -404,7 +405,7 @@ __global__ void k_run_abort(void *sync, int nbytes, const SysDev *__restrict__ s
 // cannot run or plain launches are asked for, the separate kernels step by
 // step, with the same arithmetic).
 mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, bool lambda = false,
-                   bool check = true, int lam_M = 0, double dlam = 0.0) {
+                   bool check = true, int lam_M = 0, double dlam = 0.0, long long lam_base = 0) {
     if (n_steps <= 0) return MDAS_OK;
     const bool trial = swap_every > 0;
     SegTimer tm;
@@ -444,8 +445,8 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
         launches += 2;
         if (persistent) {
             CK(tm.begin(b.stream, n));
-            CK(launch_md_run(L, lambda, (int)n, swap_every, trial ? (int)(k0 % swap_every) : 0, lam_M, (int)k0, dlam,
-                             b.rsync));
+            CK(launch_md_run(L, lambda, (int)n, swap_every, trial ? (int)(k0 % swap_every) : 0, lam_M,
+                             (int)(lam_base + k0), dlam, b.rsync));
             CK(tm.end(b.stream));
             k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
             launches += 1;
@@ -463,9 +464,9 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
             launch_nl_build(L);
             launches += 5;
             if (trial && (k0 + k + 1) % swap_every == 0) { launch_trial_nl(L); ++launches; }
-            if (lam_M > 0 && (k0 + k + 1) % lam_M == 0) {
+            if (lam_M > 0 && (lam_base + k0 + k + 1) % lam_M == 0) {
                 // the end of a lambda block: its work term, then the next lambda
-                const long long blk = (k0 + k + 1) / lam_M;       // lambda blocks done
+                const long long blk = (lam_base + k0 + k + 1) / lam_M;       // lambda blocks done
                 launch_mdas_dE_nl(L, (double)(blk - 1) * dlam, (double)blk * dlam, dlam);
                 launch_mdas_set_lambda(L, (double)blk * dlam, 1);
                 launches += 3;
@@ -514,6 +515,97 @@ mdas_status run_trials(mdas_system *s, Batch &b, int n, int *rounds_out) {
 
 }  // namespace
 
+namespace mdas {
+
+const char *fill_force_field(const mdas_system_desc *d, double shrink, Params &P) {
+    const int n = d->n_beads, nl = d->n_lipids, bpl = d->beads_per_lipid, nbt = d->n_bead_types, nlt = d->n_lipid_types;
+    if (n <= 0 || nl < 0 || bpl <= 0 || bpl > MAXT || nbt <= 0 || nbt > MAXT || nlt <= 0 || nlt > MAXT ||
+        nl * bpl > n || nl >= (1 << 20) || n > (1 << 28))
+        return "sizes out of range";
+    if (!d->lipid_bead_type || !d->eps || !d->sigma || !d->charge) return "missing array";
+    if (d->water_bead_type < 0 || d->water_bead_type >= nbt) return "water type";
+    if (!(d->rc > 0) || !(d->eps_r > 0)) return "rc, eps_r";
+    if (d->n_bonds < 0 || d->n_angles < 0 || (d->n_bonds && !d->bonds) || (d->n_angles && !d->angles)) return "topology";
+    if (d->precision != MDAS_FP32 && d->precision != MDAS_FP64) return "precision";
+    memset(&P, 0, sizeof(P));
+    for (int k = 0; k < 3; ++k) {
+        if (!(d->box[k] > 0)) return "box";
+        P.nc[k] = (int)std::floor(d->box[k] * (1.0 - shrink) / d->rc);
+        if (P.nc[k] < 3) return "every box edge must be >= 3 rc (with the margin)";
+    }
+    for (int k = 0; k < nlt * bpl; ++k)
+        if (d->lipid_bead_type[k] < 0 || d->lipid_bead_type[k] >= nbt) return "lipid bead type";
+    P.n = n; P.n_lip = nl; P.bpl = bpl; P.n_bt = nbt; P.n_lt = nlt; P.n_lipid_beads = nl * bpl;
+    P.n_cells = P.nc[0] * P.nc[1] * P.nc[2];
+    P.rc = d->rc; P.rc2 = d->rc * d->rc;
+    P.dt = d->dt;
+    for (int k = 0; k < 3; ++k) box_params(P, k, d->box[k]);
+    P.krf = d->eps_rf <= 0 ? 1.0 / (2.0 * d->rc * d->rc * d->rc)
+                           : (d->eps_rf - d->eps_r) / ((2.0 * d->eps_rf + d->eps_r) * d->rc * d->rc * d->rc);
+    P.crf = 1.0 / d->rc + P.krf * d->rc * d->rc;
+    for (int k = 0; k < 3; ++k) P.cwu[k] = (unsigned long long)(4294967296.0 / P.nc[k]);
+    // float cull bounds: every pair with r^2 < rc^2 passes rc2f; pairs in
+    // [rc2f_lo, rc2f) are re-decided exactly from integer offsets
+    P.rc2f = std::nextafter((float)(P.rc2 * (1.0 + 1e-5)), 1e30f);
+    P.rc2f_lo = (float)(P.rc2 * (1.0 - 1e-5));
+    P.krf2f = (float)(2.0 * P.krf);
+    P.kb = d->kb; P.b0 = d->b0; P.kth = d->ktheta; P.cos0 = std::cos(d->theta0_deg * M_PI / 180.0);
+    P.precision = d->precision;
+    const double rc6 = std::pow(d->rc, 6);
+    for (int a = 0; a < nbt; ++a)
+        for (int b = 0; b < nbt; ++b) {
+            const double e = d->eps[a * nbt + b], sg = d->sigma[a * nbt + b];
+            const double s6 = std::pow(sg, 6);
+            const int x = a * 16 + b;
+            P.c12[x] = 4.0 * e * s6 * s6;
+            P.c6[x] = 4.0 * e * s6;
+            P.ush[x] = P.c12[x] / (rc6 * rc6) - P.c6[x] / rc6;
+            P.qq[x] = COUL * d->charge[a] * d->charge[b] / d->eps_r;
+            P.f12f[x] = (float)(12.0 * P.c12[x]);
+            P.f6f[x] = (float)(6.0 * P.c6[x]);
+            P.qqf[x] = (float)P.qq[x];
+        }
+    for (int lt = 0; lt < nlt; ++lt)
+        for (int k = 0; k < bpl; ++k) P.lbt[lt * 16 + k] = (uint8_t)d->lipid_bead_type[lt * bpl + k];
+    for (int b = 0; b < d->n_bonds; ++b) {
+        const int p = d->bonds[2 * b], q = d->bonds[2 * b + 1];
+        if (p < 0 || q < 0 || p >= bpl || q >= bpl || p == q || P.nbond[p] >= 4 || P.nbond[q] >= 4)
+            return "bond (at most 4 per bead)";
+        P.excl[p] |= (uint16_t)(1u << q);
+        P.excl[q] |= (uint16_t)(1u << p);
+        P.bpart[p][P.nbond[p]++] = (int8_t)q;
+        P.bpart[q][P.nbond[q]++] = (int8_t)p;
+    }
+    for (int a = 0; a < d->n_angles; ++a) {
+        const int t3[3] = {d->angles[3 * a], d->angles[3 * a + 1], d->angles[3 * a + 2]};
+        for (int r = 0; r < 3; ++r) {
+            const int k = t3[r];
+            if (k < 0 || k >= bpl || P.nang[k] >= 8) return "angle (at most 8 per bead)";
+            for (int c = 0; c < 3; ++c) P.ang[k][P.nang[k]][c] = (int8_t)t3[c];
+            P.nang[k]++;
+        }
+    }
+    // bonded partners of each local index (the beads its bonded terms read)
+    memset(P.pidx, -1, sizeof(P.pidx));
+    for (int k = 0; k < bpl; ++k) {
+        auto add = [&](int q) {
+            if (q == k || P.pidx[k][q] >= 0) return true;
+            if (P.npart[k] >= NL_PART) return false;
+            P.pidx[k][q] = (int8_t)P.npart[k];
+            P.part[k][P.npart[k]++] = (int8_t)q;
+            return true;
+        };
+        bool ok = true;
+        for (int b = 0; b < P.nbond[k]; ++b) ok = ok && add(P.bpart[k][b]);
+        for (int a = 0; a < P.nang[k]; ++a)
+            for (int c = 0; c < 3; ++c) ok = ok && add(P.ang[k][a][c]);
+        if (!ok) return "a bead has more than 8 bonded partners";
+    }
+    return nullptr;
+}
+
+}  // namespace mdas
+
 // =================================================================== ABI
 
 extern "C" {
@@ -537,37 +629,23 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
     mdas_system *s = nullptr;
     if (!d || !out) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: NULL argument");
     *out = nullptr;
-    const int n = d->n_beads, nl = d->n_lipids, bpl = d->beads_per_lipid, nbt = d->n_bead_types, nlt = d->n_lipid_types;
-    if (n <= 0 || nl < 0 || bpl <= 0 || bpl > MAXT || nbt <= 0 || nbt > MAXT || nlt <= 0 || nlt > MAXT ||
-        nl * bpl > n || nl >= (1 << 20) || n > (1 << 28))
-        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: sizes out of range");
-    if (!d->pos || !d->lipid_type || !d->lipid_bead_type || !d->eps || !d->sigma || !d->charge)
-        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: missing array");
-    if (d->water_bead_type < 0 || d->water_bead_type >= nbt) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: water type");
-    if (!(d->rc > 0) || !(d->eps_r > 0) || !(d->mass > 0) || !(d->dt > 0) || !(d->temperature >= 0))
-        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: rc, eps_r, mass, dt, temperature");
-    if (d->n_bonds < 0 || d->n_angles < 0 || (d->n_bonds && !d->bonds) || (d->n_angles && !d->angles))
-        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: topology");
-    if (d->precision != MDAS_FP32 && d->precision != MDAS_FP64) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: precision");
+    const int n = d->n_beads, nl = d->n_lipids, bpl = d->beads_per_lipid, nlt = d->n_lipid_types;
     // pressure coupling: the cell grids hold for every edge down to (1 - shrink) of its length
     const bool pcouple = d->tau_p > 0;
     const double shrink = grid_shrink(d);
+    Params P;
+    if (const char *why = fill_force_field(d, shrink, P)) return fail(nullptr, MDAS_ERR_INVALID_ARG, std::string("create: ") + why);
+    if (!d->pos || !d->lipid_type) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: missing array");
+    if (!(d->mass > 0) || !(d->dt > 0) || !(d->temperature >= 0))
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: rc, eps_r, mass, dt, temperature");
     if (pcouple && !(d->compressibility >= 0 && std::isfinite(d->p_ref) && std::isfinite(d->tau_p)))
         return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: pressure coupling parameters");
-    int nc[3];
-    for (int k = 0; k < 3; ++k) {
-        if (!(d->box[k] > 0)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: box");
-        nc[k] = (int)std::floor(d->box[k] * (1.0 - shrink) / d->rc);
-        if (nc[k] < 3) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: every box edge must be >= 3 rc (with the margin)");
-    }
-    if ((long long)nc[0] * nc[1] * nc[2] > (1 << 26)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: too many cells");
+    if ((long long)P.nc[0] * P.nc[1] * P.nc[2] > (1 << 26)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: too many cells");
     for (int l = 0; l < nl; ++l) {
         if (d->lipid_first_bead && d->lipid_first_bead[l] != l * bpl)
             return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: lipid l must own beads [l*bpl, (l+1)*bpl)");
         if (d->lipid_type[l] < 0 || d->lipid_type[l] >= nlt) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: lipid type");
     }
-    for (int k = 0; k < nlt * bpl; ++k)
-        if (d->lipid_bead_type[k] < 0 || d->lipid_bead_type[k] >= nbt) return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: lipid bead type");
 
     {
         cudaError_t e = setup_kernels();
@@ -587,11 +665,8 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: dev_alloc and dev_free go together");
     }
 
-    // ---- parameters
-    Params &P = s->hp;
-    memset(&P, 0, sizeof(P));
-    P.n = n; P.n_lip = nl; P.bpl = bpl; P.n_bt = nbt; P.n_lt = nlt; P.n_lipid_beads = nl * bpl;
-    P.n_cells = nc[0] * nc[1] * nc[2];
+    // ---- parameters: the force field, then capacities, pair list, thermostat
+    s->hp = P;
     {   // cell capacity: four times the mean occupancy, at least 32, a multiple of 32
         const double mean = (double)n / P.n_cells;
         P.capc = std::max(32, (int)std::ceil(4.0 * mean / 32.0) * 32);
@@ -600,18 +675,6 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
             return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: more than 256 beads per cell on average");
         }
     }
-    P.rc = d->rc; P.rc2 = d->rc * d->rc;
-    P.dt = d->dt;
-    for (int k = 0; k < 3; ++k) {
-        P.nc[k] = nc[k];
-        box_params(P, k, d->box[k]);
-    }
-    P.krf = d->eps_rf <= 0 ? 1.0 / (2.0 * d->rc * d->rc * d->rc)
-                           : (d->eps_rf - d->eps_r) / ((2.0 * d->eps_rf + d->eps_r) * d->rc * d->rc * d->rc);
-    P.crf = 1.0 / d->rc + P.krf * d->rc * d->rc;
-    // float cull bounds: every pair with r^2 < rc^2 passes rc2f; pairs in
-    // [rc2f_lo, rc2f) are re-decided exactly from integer offsets
-    for (int k = 0; k < 3; ++k) P.cwu[k] = (unsigned long long)(4294967296.0 / nc[k]);
     {   // pair list
         const ListDims ld = list_dims(d, shrink);
         P.rl = ld.rl;
@@ -623,7 +686,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
             P.lcwu[k] = (unsigned long long)(4294967296.0 / ld.ln[k]);
         }
         P.n_lcells = ld.n_lcells;
-        for (int k = 0; k < 3; ++k) P.pc_lmin[k] = std::max(nc[k] * d->rc, ld.ln[k] * P.rl);
+        for (int k = 0; k < 3; ++k) P.pc_lmin[k] = std::max(P.nc[k] * d->rc, ld.ln[k] * P.rl);
         P.lcapc = ld.lcapc;
         P.lcap = ld.lcap;
         P.lrow = ld.lrow;
@@ -640,78 +703,15 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         P.pc_wc = 4.0 * M_PI * M_PI * beta / (3.0 * d->tau_p * d->tau_p);
     }
     P.therm_c = d->tau_t > 0 ? std::exp(-d->dt / d->tau_t) : 1.0;
-    P.rc2f = std::nextafter((float)(P.rc2 * (1.0 + 1e-5)), 1e30f);
-    P.rc2f_lo = (float)(P.rc2 * (1.0 - 1e-5));
-    P.krf2f = (float)(2.0 * P.krf);
-    P.dt = d->dt; P.tau_t = d->tau_t; P.mass = d->mass; P.kT = BOLTZ * d->temperature;
+    P.tau_t = d->tau_t; P.mass = d->mass; P.kT = BOLTZ * d->temperature;
     P.dt_over_m = d->dt / d->mass;
     P.dt_over_mf = (float)P.dt_over_m;
     P.massf = (float)d->mass;
     P.nf[0] = 3 * nl * bpl; P.nf[1] = 3 * (n - nl * bpl);
     for (int g = 0; g < 2; ++g) P.ktarget[g] = 0.5 * P.nf[g] * P.kT;
-    P.kb = d->kb; P.b0 = d->b0; P.kth = d->ktheta; P.cos0 = std::cos(d->theta0_deg * M_PI / 180.0);
     P.key0 = (uint32_t)d->seed ^ d->system_id;
     P.key1 = (uint32_t)(d->seed >> 32);
-    P.precision = d->precision;
-    const double rc6 = std::pow(d->rc, 6);
-    for (int a = 0; a < nbt; ++a)
-        for (int b = 0; b < nbt; ++b) {
-            const double e = d->eps[a * nbt + b], sg = d->sigma[a * nbt + b];
-            const double s6 = std::pow(sg, 6);
-            const int x = a * 16 + b;
-            P.c12[x] = 4.0 * e * s6 * s6;
-            P.c6[x] = 4.0 * e * s6;
-            P.ush[x] = P.c12[x] / (rc6 * rc6) - P.c6[x] / rc6;
-            P.qq[x] = COUL * d->charge[a] * d->charge[b] / d->eps_r;
-            P.f12f[x] = (float)(12.0 * P.c12[x]);
-            P.f6f[x] = (float)(6.0 * P.c6[x]);
-            P.qqf[x] = (float)P.qq[x];
-        }
-    for (int lt = 0; lt < nlt; ++lt)
-        for (int k = 0; k < bpl; ++k) P.lbt[lt * 16 + k] = (uint8_t)d->lipid_bead_type[lt * bpl + k];
-    for (int b = 0; b < d->n_bonds; ++b) {
-        const int p = d->bonds[2 * b], q = d->bonds[2 * b + 1];
-        if (p < 0 || q < 0 || p >= bpl || q >= bpl || p == q || P.nbond[p] >= 4 || P.nbond[q] >= 4) {
-            delete s;
-            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: bond (at most 4 per bead)");
-        }
-        P.excl[p] |= (uint16_t)(1u << q);
-        P.excl[q] |= (uint16_t)(1u << p);
-        P.bpart[p][P.nbond[p]++] = (int8_t)q;
-        P.bpart[q][P.nbond[q]++] = (int8_t)p;
-    }
-    for (int a = 0; a < d->n_angles; ++a) {
-        const int t3[3] = {d->angles[3 * a], d->angles[3 * a + 1], d->angles[3 * a + 2]};
-        for (int r = 0; r < 3; ++r) {
-            const int k = t3[r];
-            if (k < 0 || k >= bpl || P.nang[k] >= 8) {
-                delete s;
-                return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: angle (at most 8 per bead)");
-            }
-            for (int c = 0; c < 3; ++c) P.ang[k][P.nang[k]][c] = (int8_t)t3[c];
-            P.nang[k]++;
-        }
-    }
-
-    // bonded partners of each local index (the beads its bonded terms read)
-    memset(P.pidx, -1, sizeof(P.pidx));
-    for (int k = 0; k < bpl; ++k) {
-        auto add = [&](int q) {
-            if (q == k || P.pidx[k][q] >= 0) return true;
-            if (P.npart[k] >= NL_PART) return false;
-            P.pidx[k][q] = (int8_t)P.npart[k];
-            P.part[k][P.npart[k]++] = (int8_t)q;
-            return true;
-        };
-        bool ok = true;
-        for (int b = 0; b < P.nbond[k]; ++b) ok = ok && add(P.bpart[k][b]);
-        for (int a = 0; a < P.nang[k]; ++a)
-            for (int c = 0; c < 3; ++c) ok = ok && add(P.ang[k][a][c]);
-        if (!ok) {
-            delete s;
-            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: a bead has more than 8 bonded partners");
-        }
-    }
+    s->hp = P;
 
     // ---- device memory: one arena
     const int nbb = (n + BEAD_BLOCK - 1) / BEAD_BLOCK;
@@ -953,8 +953,50 @@ mdas_status mdas_trial_log(mdas_system *s, uint64_t first, int32_t n, mdas_trial
     return MDAS_OK;
 }
 
-mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
-                                 const int32_t *pairs, mdas_move_result *res) {
+}  // extern "C"
+
+namespace {
+
+// Per-block output of a traced alchemical move (host arrays, any may be NULL).
+struct MoveTrace {
+    double *w;          // [n_lambda] work added by each block
+    uint32_t *pos;      // [n_lambda][n][3] fixed-point positions after each block
+    double *vel;        // [n_lambda][n][3] velocities after each block
+};
+
+// After lambda block k (0-based) of a traced move: the work the block added
+// (the running work minus *w_prev), the positions and the velocities.
+mdas_status trace_block(mdas_system *s, int k, double *w_prev, const MoveTrace &tr) {
+    const size_t n = (size_t)s->n;
+    double w = 0.0;
+    CK(cudaMemcpyAsync(&w, &s->hs.c->w, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<uint4> p(tr.pos ? n : 0);
+    if (tr.pos) CK(cudaMemcpyAsync(p.data(), s->hs.pos, 16 * n, cudaMemcpyDeviceToHost, s->stream));
+    std::vector<Dbl4> vd(tr.vel && s->precision == 1 ? n : 0);
+    std::vector<float4> vf(tr.vel && s->precision != 1 ? n : 0);
+    if (tr.vel && s->precision == 1) CK(cudaMemcpyAsync(vd.data(), s->hs.vel, 32 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (tr.vel && s->precision != 1) CK(cudaMemcpyAsync(vf.data(), s->hs.vel, 16 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (tr.w) tr.w[k] = w - *w_prev;
+    *w_prev = w;
+    for (size_t i = 0; tr.pos && i < n; ++i) {
+        uint32_t *o = tr.pos + ((size_t)k * n + i) * 3;
+        o[0] = p[i].x; o[1] = p[i].y; o[2] = p[i].z;
+    }
+    for (size_t i = 0; tr.vel && i < n; ++i) {
+        double *o = tr.vel + ((size_t)k * n + i) * 3;
+        if (s->precision == 1) { o[0] = vd[i].x; o[1] = vd[i].y; o[2] = vd[i].z; }
+        else { o[0] = vf[i].x; o[1] = vf[i].y; o[2] = vf[i].z; }
+    }
+    return MDAS_OK;
+}
+
+// One MDAS move (Sec. 2, Eqs. 2-3) with pairs given (pairs), drawn over all
+// lipids (mode 0) or drawn across the leaflets (mode 2, head_k).  With a
+// trace, the trajectory runs one lambda block per MD run (the bits of one
+// run) and each block's work, positions and velocities are copied out.
+mdas_status alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                            const int32_t *pairs, int mode, int head_k, mdas_move_result *res, const MoveTrace *tr) {
     if (!s || n_pairs < 0 || n_pairs > MAX_PAIRS || n_lambda < 1 || md_per_lambda < 0)
         return fail(s, MDAS_ERR_INVALID_ARG, "alchemical_move: bad argument");
     if (s->unstable) return fail(s, MDAS_ERR_UNSTABLE, "alchemical_move: system is unstable");
@@ -974,27 +1016,45 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
         Counters *dc = s->hs.c;
         CK(cudaMemcpyAsync(&dc->pairs, pairs, 8ull * n_pairs, cudaMemcpyHostToDevice, s->stream));
         CK(cudaMemcpyAsync(&dc->n_pairs, &n_pairs, 4, cudaMemcpyHostToDevice, s->stream));
+        mode = 1;
+    }
+    int *leaf = nullptr;
+    if (mode == 2) {
+        // leaflets at the start of the move (scratch: the head-bead info array)
+        leaf = reinterpret_cast<int *>(s->rdf_info);
+        launch_leaflets(L, s->n_lip, head_k, leaf);
     }
     launch_snapshot(L);
-    launch_mdas_select(L, n_pairs, 64 * n_pairs + 64, pairs != nullptr);
+    launch_mdas_select(L, n_pairs, 64 * n_pairs + 64, mode, leaf);
     int np = 0;
     CK(cudaMemcpyAsync(&np, &s->hs.c->n_pairs, 4, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     if (np > 0) {
         const double dl = 1.0 / n_lambda;
+        double w_prev = 0.0;
         if (md_per_lambda > 0) {
             // the whole trajectory in one MD run: lambda advances by dl after
             // every md_per_lambda steps, each block's work term from the pair
             // list (valid right after the block's steps)
             launch_mdas_set_lambda(L, 0.0, 1);
-            mdas_status st = run_md(s, b, (long long)n_lambda * md_per_lambda, 0, true, false, md_per_lambda, dl);
-            if (st != MDAS_OK) return st;
+            if (!tr) {
+                mdas_status st = run_md(s, b, (long long)n_lambda * md_per_lambda, 0, true, false, md_per_lambda, dl);
+                if (st != MDAS_OK) return st;
+            } else {
+                for (int k = 0; k < n_lambda; ++k) {
+                    mdas_status st = run_md(s, b, md_per_lambda, 0, true, false, md_per_lambda, dl,
+                                            (long long)k * md_per_lambda);
+                    if (st == MDAS_OK) st = trace_block(s, k, &w_prev, *tr);
+                    if (st != MDAS_OK) return st;
+                }
+            }
         } else {
             for (int k = 1; k <= n_lambda; ++k) {
                 launch_mdas_set_lambda(L, (double)(k - 1) / n_lambda, 1);
                 mdas_status st = build_cells(s, b);
                 if (st != MDAS_OK) return st;
                 launch_mdas_dE(L, dl);
+                if (tr && (st = trace_block(s, k - 1, &w_prev, *tr)) != MDAS_OK) return st;
             }
         }
     }
@@ -1015,6 +1075,42 @@ mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lamb
         for (int k = 0; k < 2 * c.n_pairs; ++k) res->pairs[k] = c.pairs[k];
     }
     return check_err(s, b);
+}
+
+}  // namespace
+
+extern "C" {
+
+mdas_status mdas_alchemical_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                                 const int32_t *pairs, mdas_move_result *res) {
+    return alchemical_move(s, n_pairs, n_lambda, md_per_lambda, pairs, 0, 1, res, nullptr);
+}
+
+mdas_status mdas_alchemical_move_trace(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                                       const int32_t *pairs, mdas_move_result *res, double *w_blocks,
+                                       uint32_t *pos_blocks, double *vel_blocks) {
+    const MoveTrace tr{w_blocks, pos_blocks, vel_blocks};
+    return alchemical_move(s, n_pairs, n_lambda, md_per_lambda, pairs, 0, 1, res, &tr);
+}
+
+mdas_status mdas_interleaflet_move(mdas_system *s, int32_t n_pairs, int32_t n_lambda, int32_t md_per_lambda,
+                                   int32_t head_k, mdas_move_result *res) {
+    if (s && (head_k < 0 || head_k >= s->bpl - 1))
+        return fail(s, MDAS_ERR_INVALID_ARG, "interleaflet_move: head_k outside [0, beads_per_lipid - 1)");
+    return alchemical_move(s, n_pairs, n_lambda, md_per_lambda, nullptr, 2, head_k, res, nullptr);
+}
+
+mdas_status mdas_device_ptrs(mdas_system *s, mdas_device_view *out) {
+    if (!s || !out) return fail(s, MDAS_ERR_INVALID_ARG, "device_ptrs: NULL argument");
+    out->pos = s->hs.pos;
+    out->vel = s->hs.vel;
+    out->lipid_type = s->hs.ltype;
+    out->n_beads = s->n;
+    out->n_lipids = s->n_lip;
+    out->precision = s->precision;
+    out->vel_stride_bytes = s->precision == 1 ? 32 : 16;
+    for (int k = 0; k < 3; ++k) out->box[k] = s->hp.box[k];
+    return MDAS_OK;
 }
 
 mdas_status mdas_delta_energy(mdas_system *s, const int32_t *lipids, const int32_t *new_types, int32_t n, double *dE) {

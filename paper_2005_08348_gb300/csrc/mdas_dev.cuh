@@ -33,7 +33,8 @@ constexpr double TWO32 = 4294967296.0;
 constexpr double BOLTZ = 0.0083144626;
 constexpr double COUL = 138.935458;
 
-enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5, TAG_MUTATE = 6 };
+enum : uint32_t { TAG_THERMO = 1, TAG_SWAP = 2, TAG_MDAS_PAIR = 3, TAG_MDAS_ACC = 4, TAG_AT_THERMO = 5, TAG_MUTATE = 6,
+                   TAG_LEAFLET = 7 };
 enum : int { ERR_NONFINITE = 1, ERR_CELL_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_ROUNDS = 8, ERR_BAD_INPUT = 16,
              ERR_BOX = 32, ERR_BOUNDS = 64 };
 
@@ -331,7 +332,10 @@ void launch_energy_reduce(const LaunchCtx &L);
 void launch_swap_propose(const LaunchCtx &L, int n_trials);
 void launch_swap_dE(const LaunchCtx &L, int n_trials);
 void launch_swap_resolve(const LaunchCtx &L, int n_trials);
-void launch_mdas_select(const LaunchCtx &L, int n_pairs, int max_tries, int explicit_pairs);
+// pairs of an alchemical move: mode 0 drawn, 1 explicit (in the counters), 2
+// drawn across the leaflets given by leaf[] (system 0 of the batch)
+void launch_mdas_select(const LaunchCtx &L, int n_pairs, int max_tries, int mode, const int *leaf = nullptr);
+void launch_leaflets(const LaunchCtx &L, int n_lip, int head_k, int *leaf);
 void launch_mdas_set_lambda(const LaunchCtx &L, double lambda, int in_at);
 void launch_mdas_dE(const LaunchCtx &L, double dlambda);
 void launch_mdas_accept(const LaunchCtx &L);

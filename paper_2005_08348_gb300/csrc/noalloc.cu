@@ -13,13 +13,15 @@
 // the GPU (different streams, or different host threads) race and must be
 // serialised by the caller.  The first call on a device looks up the array's
 // device address (cudaGetSymbolAddress); make that first call before any
-// stream capture.
+// stream capture.  Every call reads the device error word back and waits for
+// its stream before it returns.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
 #include "../../include/mdas.h"
+#include "host_params.h"
 #include "mdas_dev.cuh"
 
 using namespace mdas;
@@ -92,87 +94,13 @@ __global__ void k_na_maps(int n, int n_cells, int2 *beads, int2 *cells, int2 *so
     if (k == 0) syss[0] = make_int2(0, 0);
 }
 
-// the force-field parameters of a description (the same tables mdas_create_system builds)
+// the force-field parameters of a description: the tables mdas_create_system
+// builds (one shared host function), within this entry point's limits
 mdas_status na_params(const mdas_system_desc *d, Params &P) {
-    const int n = d->n_beads, nl = d->n_lipids, bpl = d->beads_per_lipid, nbt = d->n_bead_types, nlt = d->n_lipid_types;
-    if (n <= 0 || n > NA_MAX_BEADS) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: too many beads");
-    if (nl < 0 || bpl <= 0 || bpl > MAXT || nbt <= 0 || nbt > MAXT || nlt <= 0 || nlt > MAXT || nl * bpl > n)
-        return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: sizes out of range");
-    if (!d->lipid_bead_type || !d->eps || !d->sigma || !d->charge || (d->n_bonds && !d->bonds) || (d->n_angles && !d->angles))
-        return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: missing parameter table");
-    if (!(d->rc > 0) || !(d->eps_r > 0) || d->water_bead_type < 0 || d->water_bead_type >= nbt)
-        return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: rc, eps_r or water type");
-    if (d->precision != MDAS_FP32 && d->precision != MDAS_FP64) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: precision");
-    memset(&P, 0, sizeof(P));
-    int nc[3];
-    for (int k = 0; k < 3; ++k) {
-        if (!(d->box[k] > 0)) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: box");
-        nc[k] = (int)std::floor(d->box[k] / d->rc);
-        if (nc[k] < 3) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: every box edge must be >= 3 rc");
-    }
-    if ((long long)nc[0] * nc[1] * nc[2] > NA_MAX_CELLS)
-        return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: too many cells");
-    P.n = n; P.n_lip = nl; P.bpl = bpl; P.n_bt = nbt; P.n_lt = nlt; P.n_lipid_beads = nl * bpl;
-    P.n_cells = nc[0] * nc[1] * nc[2];
+    if (d->n_beads <= 0 || d->n_beads > NA_MAX_BEADS) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: too many beads");
+    if (const char *why = fill_force_field(d, 0.0, P)) return na_fail(MDAS_ERR_INVALID_ARG, why);
+    if (P.n_cells > NA_MAX_CELLS) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: too many cells");
     P.capc = NA_CAPC;
-    for (int k = 0; k < 3; ++k) {
-        P.nc[k] = nc[k];
-        P.box[k] = d->box[k];
-        P.qs[k] = d->box[k] / TWO32;
-        P.qsf[k] = (float)P.qs[k];
-        P.qsh[k] = (float)P.qs[k];
-        P.qsl[k] = (float)(P.qs[k] - (double)P.qsh[k]);
-        P.qdt[k] = d->dt * TWO32 / d->box[k];
-        P.qdtf[k] = (float)P.qdt[k];
-        P.cwu[k] = (unsigned long long)(4294967296.0 / nc[k]);
-        P.rcu[k] = (uint32_t)std::ceil(d->rc / P.qs[k]) + 2;
-    }
-    P.rc = d->rc; P.rc2 = d->rc * d->rc;
-    P.krf = d->eps_rf <= 0 ? 1.0 / (2.0 * d->rc * d->rc * d->rc)
-                           : (d->eps_rf - d->eps_r) / ((2.0 * d->eps_rf + d->eps_r) * d->rc * d->rc * d->rc);
-    P.crf = 1.0 / d->rc + P.krf * d->rc * d->rc;
-    P.rc2f = std::nextafter((float)(P.rc2 * (1.0 + 1e-5)), 1e30f);
-    P.rc2f_lo = (float)(P.rc2 * (1.0 - 1e-5));
-    P.krf2f = (float)(2.0 * P.krf);
-    P.kb = d->kb; P.b0 = d->b0; P.kth = d->ktheta; P.cos0 = std::cos(d->theta0_deg * M_PI / 180.0);
-    P.precision = d->precision;
-    const double rc6 = std::pow(d->rc, 6);
-    for (int a = 0; a < nbt; ++a)
-        for (int b = 0; b < nbt; ++b) {
-            const double e = d->eps[a * nbt + b], s6 = std::pow(d->sigma[a * nbt + b], 6);
-            const int x = a * 16 + b;
-            P.c12[x] = 4.0 * e * s6 * s6;
-            P.c6[x] = 4.0 * e * s6;
-            P.ush[x] = P.c12[x] / (rc6 * rc6) - P.c6[x] / rc6;
-            P.qq[x] = COUL * d->charge[a] * d->charge[b] / d->eps_r;
-            P.f12f[x] = (float)(12.0 * P.c12[x]);
-            P.f6f[x] = (float)(6.0 * P.c6[x]);
-            P.qqf[x] = (float)P.qq[x];
-        }
-    for (int lt = 0; lt < nlt; ++lt)
-        for (int k = 0; k < bpl; ++k) {
-            const int bt = d->lipid_bead_type[lt * bpl + k];
-            if (bt < 0 || bt >= nbt) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: lipid bead type");
-            P.lbt[lt * 16 + k] = (uint8_t)bt;
-        }
-    for (int b = 0; b < d->n_bonds; ++b) {
-        const int p = d->bonds[2 * b], q = d->bonds[2 * b + 1];
-        if (p < 0 || q < 0 || p >= bpl || q >= bpl || p == q || P.nbond[p] >= 4 || P.nbond[q] >= 4)
-            return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: bond");
-        P.excl[p] |= (uint16_t)(1u << q);
-        P.excl[q] |= (uint16_t)(1u << p);
-        P.bpart[p][P.nbond[p]++] = (int8_t)q;
-        P.bpart[q][P.nbond[q]++] = (int8_t)p;
-    }
-    for (int a = 0; a < d->n_angles; ++a) {
-        const int t3[3] = {d->angles[3 * a], d->angles[3 * a + 1], d->angles[3 * a + 2]};
-        for (int r = 0; r < 3; ++r) {
-            const int k = t3[r];
-            if (k < 0 || k >= bpl || P.nang[k] >= 8) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: angle");
-            for (int c = 0; c < 3; ++c) P.ang[k][P.nang[k]][c] = (int8_t)t3[c];
-            P.nang[k]++;
-        }
-    }
     return MDAS_OK;
 }
 
@@ -261,8 +189,10 @@ extern "C" mdas_status mdas_forces_noalloc(const mdas_system_desc *d, const uint
     NACK(cudaMemcpyAsync(&err, &S.c->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     NACK(cudaStreamSynchronize(stream));
     if (err & ERR_BAD_INPUT) return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: lipid type out of range");
+    // a cell over this entry point's fixed capacity is a size limit of the
+    // call, not an instability of the state
     if (err & ERR_CELL_OVERFLOW)
-        return na_fail(MDAS_ERR_UNSTABLE, "forces_noalloc: cell overflow");
+        return na_fail(MDAS_ERR_INVALID_ARG, "forces_noalloc: more than 64 beads in a cell");
     if (err) return na_fail(MDAS_ERR_UNSTABLE, "forces_noalloc: device error flag");
     return MDAS_OK;
 }

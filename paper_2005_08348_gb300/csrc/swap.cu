@@ -293,19 +293,27 @@ void launch_swap_resolve(const LaunchCtx &L, int n) {
 // Pick up to n_pairs disjoint lipid pairs of different types: candidate j
 // from Philox call (j, move, TAG_MDAS_PAIR, 0), skipped when the lipids
 // coincide, share a type, or one is already used.  Then mark the B types.
-__global__ void k_mdas_select(const SysDev *__restrict__ sys, int n_pairs, int max_tries, int explicit_pairs) {
+// The pairs of an alchemical move: explicit (mode 1), drawn over all lipids
+// (mode 0, Philox (j, move, TAG_MDAS_PAIR, 0) for candidate j), or drawn
+// across the leaflets (mode 2, Philox (j, move, TAG_LEAFLET, 0); a candidate
+// is kept when a lies in leaflet 0 and b in leaflet 1 by leaf[]).  Then the
+// B types of the pairs' beads.
+__global__ void k_mdas_select(const SysDev *__restrict__ sys, int n_pairs, int max_tries, int mode,
+                              const int *__restrict__ leaf) {
     const SysDev &S = sys[blockIdx.x];
     const Params &P = *S.p;
     Counters &C = *S.c;
     if (threadIdx.x != 0) return;
     int np = 0;
-    if (explicit_pairs) {
+    if (mode == 1) {
         np = C.n_pairs;
     } else {
+        const uint32_t tag = mode == 2 ? TAG_LEAFLET : TAG_MDAS_PAIR;
         for (int j = 0; j < max_tries && np < n_pairs; ++j) {
-            const uint4 w = draw4(P, (uint32_t)j, (uint32_t)C.move, TAG_MDAS_PAIR, 0u);
+            const uint4 w = draw4(P, (uint32_t)j, (uint32_t)C.move, tag, 0u);
             const int a = pick(w.x, P.n_lip), b = pick(w.y, P.n_lip);
             if (a == b || S.ltype[a] == S.ltype[b]) continue;
+            if (mode == 2 && !(leaf[a] == 0 && leaf[b] == 1)) continue;
             bool used = false;
             for (int k = 0; k < 2 * np && !used; ++k) used = C.pairs[k] == a || C.pairs[k] == b;
             if (used) continue;
@@ -328,8 +336,28 @@ __global__ void k_mdas_select(const SysDev *__restrict__ sys, int n_pairs, int m
     C.w = 0.0;
 }
 
-void launch_mdas_select(const LaunchCtx &L, int n_pairs, int max_tries, int explicit_pairs) {
-    k_mdas_select<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n_pairs, max_tries, explicit_pairs);
+void launch_mdas_select(const LaunchCtx &L, int n_pairs, int max_tries, int mode, const int *leaf) {
+    k_mdas_select<<<L.n_sys, 32, 0, L.stream>>>(L.sys, n_pairs, max_tries, mode, leaf);
+}
+
+// Leaflet of every lipid of system 0: 0 when its head (local index head_k)
+// lies above its last bead, i.e. the z steps of its bonds from the head to
+// the last bead, each at its minimum image, sum to a drop (exact integers).
+__global__ void k_leaflets(const SysDev *__restrict__ sys, int head_k, int *__restrict__ leaf) {
+    const SysDev &S = *sys;
+    const Params &P = *S.p;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= P.n_lip) return;
+    long long drop = 0;
+    for (int k = head_k; k < P.bpl - 1; ++k) {
+        const int b = l * P.bpl + k;
+        drop += (int)(S.pos[b].z - S.pos[b + 1].z);
+    }
+    leaf[l] = drop > 0 ? 0 : 1;
+}
+
+void launch_leaflets(const LaunchCtx &L, int n_lip, int head_k, int *leaf) {
+    k_leaflets<<<(n_lip + 127) / 128, 128, 0, L.stream>>>(L.sys, head_k, leaf);
 }
 
 __global__ void k_mdas_set_lambda(const SysDev *__restrict__ sys, double lambda, int in_at) {

@@ -77,6 +77,22 @@ class StateView(C.Structure):
                 ("list_box", C.c_double * 3)]
 
 
+class DeviceView(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("vel", C.c_void_p), ("lipid_type", C.c_void_p),
+                ("n_beads", C.c_int32), ("n_lipids", C.c_int32), ("precision", C.c_int32),
+                ("vel_stride_bytes", C.c_int32), ("box", C.c_double * 3)]
+
+
+class _DeviceArray:
+    """A device array for torch.as_tensor (the CUDA array interface), holding
+    the system it belongs to so that the memory outlives the tensor's use."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.__cuda_array_interface__ = dict(shape=tuple(shape), typestr=typestr, data=(int(ptr), False),
+                                             version=2, strides=None)
+        self._owner = owner
+
+
 class Counters(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("md_steps", "force_evals", "trials", "null_trials", "accepted",
                                          "moves", "moves_accepted", "kernel_launches", "list_builds",
@@ -93,7 +109,8 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_forces_noalloc", "mdas_server_create", "mdas_server_destroy", "mdas_server_submit",
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
            "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core",
-           "mdas_wait_timeout_probe", "mdas_box"]
+           "mdas_wait_timeout_probe", "mdas_box", "mdas_alchemical_move_trace", "mdas_interleaflet_move",
+           "mdas_device_ptrs"]
 
 
 def library_path() -> str:
@@ -224,7 +241,13 @@ class System:
         self.kT = 0.0083144626 * d.temperature
 
     def _desc_for_noalloc(self, stream=None):
-        d = self._desc_fields["d"]
+        """A copy of the creation descriptor for mdas_forces_noalloc, with the
+        system's current box (positions are fractions of it, and pressure
+        coupling or set_state may have changed it since creation)."""
+        d = Desc()
+        C.pointer(d)[0] = self._desc_fields["d"]
+        box, _, _ = self.box()
+        d.box = (C.c_double * 3)(*[float(x) for x in box])
         d.dev_alloc, d.dev_free = _ALLOC(), _FREE()
         d.cuda_stream = stream
         return d
@@ -302,7 +325,47 @@ class System:
         pr = np.array(r.pairs[: 2 * r.n_pairs], np.int32).reshape(-1, 2)
         return dict(w=r.w, u=r.u, accepted=bool(r.accepted), n_pairs=r.n_pairs, pairs=pr)
 
+    def alchemical_move_trace(self, n_pairs, n_lambda, md_per_lambda, pairs=None, positions=True, velocities=True):
+        """mdas_alchemical_move_trace: the move plus, per lambda block, the work
+        it added, the positions (fixed point) and the velocities after it."""
+        r = MoveResult()
+        pin = None
+        if pairs is not None:
+            pin = np.ascontiguousarray(np.asarray(pairs).reshape(-1), np.int32)
+            n_pairs = pin.size // 2
+        w = np.zeros(int(n_lambda), np.float64)
+        pos = np.zeros((int(n_lambda), self.n, 3), np.uint32) if positions else None
+        vel = np.zeros((int(n_lambda), self.n, 3), np.float64) if velocities else None
+        self._ck(lib().mdas_alchemical_move_trace(self._ptr, int(n_pairs), int(n_lambda), int(md_per_lambda),
+                                                  _p(pin), C.byref(r), _p(w), _p(pos), _p(vel)))
+        pr = np.array(r.pairs[: 2 * r.n_pairs], np.int32).reshape(-1, 2)
+        return dict(w=r.w, u=r.u, accepted=bool(r.accepted), n_pairs=r.n_pairs, pairs=pr, w_blocks=w,
+                    pos_blocks=pos, vel_blocks=vel)
+
+    def interleaflet_move(self, n_pairs, n_lambda, md_per_lambda, head_k=1):
+        """mdas_interleaflet_move: an alchemical move whose pairs are drawn
+        across the two leaflets."""
+        r = MoveResult()
+        self._ck(lib().mdas_interleaflet_move(self._ptr, int(n_pairs), int(n_lambda), int(md_per_lambda),
+                                              int(head_k), C.byref(r)))
+        pr = np.array(r.pairs[: 2 * r.n_pairs], np.int32).reshape(-1, 2)
+        return dict(w=r.w, u=r.u, accepted=bool(r.accepted), n_pairs=r.n_pairs, pairs=pr)
+
     # -- state ------------------------------------------------------------------
+    def device_views(self):
+        """Zero-copy torch tensors over the system's device state
+        (mdas_device_ptrs), read-only by contract: pos [n, 4] int32 (x, y, z
+        fixed point and the meta word, as raw bits), vel [n, 4] float32 or
+        float64, ltype [n_lipids] int32, and the box."""
+        import torch
+        v = DeviceView()
+        self._ck(lib().mdas_device_ptrs(self._ptr, C.byref(v)))
+        vt = "<f8" if v.vel_stride_bytes == 32 else "<f4"
+        pos = torch.as_tensor(_DeviceArray(v.pos, (v.n_beads, 4), "<i4", self), device="cuda")
+        vel = torch.as_tensor(_DeviceArray(v.vel, (v.n_beads, 4), vt, self), device="cuda")
+        lt = torch.as_tensor(_DeviceArray(v.lipid_type, (max(v.n_lipids, 0),), "<i4", self), device="cuda")
+        return dict(pos=pos, vel=vel, ltype=lt, box=np.array(list(v.box)))
+
     def get_state(self):
         pu = np.empty((self.n, 3), np.uint32)
         pos = np.empty((self.n, 3), np.float64)

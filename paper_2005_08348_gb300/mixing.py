@@ -63,38 +63,6 @@ def max_g(system, lipid_type=1, head_k=1, r_max=3.0, n_bins=20) -> float:
     return float(g_of_r(c, nh, system.box()[0], r_max)[2].max())   # the current box (pressure coupling)
 
 
-def leaflets(pos_u, lipid_first_bead, bpl: int, head_k: int = 1) -> np.ndarray:
-    """Leaflet of every lipid, 0 when its head lies above its last bead: the
-    z steps of its bonds from the head to the last bead, each at its minimum
-    image, sum to a drop (the rule mdas_head_rdf uses)."""
-    z = np.asarray(pos_u)[:, 2].astype(np.int64)
-    first = np.asarray(lipid_first_bead, np.int64)
-    drop = np.zeros(len(first), np.int64)
-    for k in range(head_k, bpl - 1):
-        drop += (z[first + k] - z[first + k + 1] + 2 ** 31) % 2 ** 32 - 2 ** 31
-    return np.where(drop > 0, 0, 1).astype(np.int32)
-
-
-def interleaflet_pairs(ltype, leaf, n_pairs: int, seed: int = 0) -> np.ndarray:
-    """n_pairs disjoint lipid pairs (a in leaflet 0, b in leaflet 1, of
-    different types) drawn uniformly: the exchange between the two leaflets
-    that Sec. 4 proposes as an alchemical move (mdas_alchemical_move with
-    these pairs)."""
-    rng = np.random.default_rng(seed)
-    ltype = np.asarray(ltype)
-    up, lo = np.flatnonzero(leaf == 0), np.flatnonzero(leaf == 1)
-    used, pairs = set(), []
-    for _ in range(100 * max(n_pairs, 1) + 1000):
-        if len(pairs) == n_pairs or len(up) == 0 or len(lo) == 0:
-            break
-        a, b = int(rng.choice(up)), int(rng.choice(lo))
-        if a in used or b in used or ltype[a] == ltype[b]:
-            continue
-        used.update((a, b))
-        pairs.append((a, b))
-    return np.array(pairs, np.int32).reshape(-1, 2)
-
-
 def exp_fit(x, y):
     """Least-squares y = a + b exp(-x / tau); None when the fit fails."""
     from scipy.optimize import curve_fit

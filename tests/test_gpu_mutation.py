@@ -41,21 +41,22 @@ def test_mutations_match_oracle(which, n, mu):
 
 
 def test_interleaflet_alchemical_exchange_matches_oracle():
-    """Sec. 4's exchange between the leaflets as an alchemical move: pairs of
-    lipids from opposite leaflets, the same work and decision as the oracle."""
-    from paper_2005_08348_gb300 import mixing
+    """Sec. 4's exchange between the leaflets as an alchemical move: the pairs
+    are drawn on the GPU from Philox counters (mdas_interleaflet_move) and
+    equal the oracle's; the same work and decision as the oracle's move."""
     m = synth.mcmd_small(seed=2025)
     s = mdas.System(m, precision="fp64")
     o = oracle.Oracle(m)
     so = o.state()
     for rep in range(3):
         st = s.get_state()
-        leaf = mixing.leaflets(st["pos_u"], m.lipid_first_bead, m.lipid_bead_type.shape[1])
+        leaf = o.leaflets(st["pos_u"])
         assert (leaf == 0).sum() == (leaf == 1).sum() == m.n_lipids // 2
-        pairs = mixing.interleaflet_pairs(st["ltype"], leaf, 4, seed=rep)
-        assert len(pairs) == 4 and all(leaf[a] != leaf[b] for a, b in pairs)
-        res = s.alchemical_move(4, 5, 3, pairs=pairs)
-        ro = o.mdas_move(so, 4, 5, 3, pairs=pairs)
+        pairs_o = o.interleaflet_pairs(st["pos_u"], st["ltype"], st["move"], 4)
+        res = s.interleaflet_move(4, 5, 3)
+        assert np.array_equal(res["pairs"], pairs_o)
+        assert len(pairs_o) == 4 and all(leaf[a] == 0 and leaf[b] == 1 for a, b in pairs_o)
+        ro = o.mdas_move(so, 4, 5, 3, pairs=pairs_o)
         assert abs(res["w"] - ro["w"]) < 1e-4, (res["w"], ro["w"])
         assert res["u"] == ro["u"] and res["accepted"] == ro["accepted"]
         assert np.array_equal(s.get_state()["ltype"], so["ltype"])

@@ -612,17 +612,39 @@ def test_mutation_semi_grand_weights_with_equal_types():
 
 
 def test_leaflets_and_interleaflet_pairs():
-    """The host leaflet rule on the generator's bilayer (upper leaflet first)
-    and on a box too thin for a head-to-tail minimum image; interleaflet pairs
-    are disjoint, across the leaflets and of different types."""
-    from paper_2005_08348_gb300 import mixing
+    """The leaflet rule on the generator's bilayer (upper leaflet first) and
+    on a box too thin for a head-to-tail minimum image; pairs of an exchange
+    between the leaflets (Sec. 4) are disjoint, across the leaflets and of
+    different types."""
     for m in (synth.mcmd_small(), synth.membrane(6, n_lipid_types=2, n_water=10, seed=9)):
-        leaf = mixing.leaflets(m.pos_u, m.lipid_first_bead, m.lipid_bead_type.shape[1])
+        o = oracle.Oracle(m)
+        leaf = o.leaflets(m.pos_u)
         half = m.n_lipids // 2
         assert np.array_equal(leaf, np.repeat([0, 1], half))
-        pairs = mixing.interleaflet_pairs(m.lipid_type, leaf, 5, seed=1)
-        assert len(pairs) == 5 and len(set(pairs.ravel())) == 10
-        assert all(leaf[a] == 0 and leaf[b] == 1 and m.lipid_type[a] != m.lipid_type[b] for a, b in pairs)
+        for move in range(3):
+            pairs = o.interleaflet_pairs(m.pos_u, m.lipid_type, move, 5)
+            assert len(pairs) == 5 and len(set(pairs.ravel())) == 10
+            assert all(leaf[a] == 0 and leaf[b] == 1 and m.lipid_type[a] != m.lipid_type[b] for a, b in pairs)
+
+
+def test_interleaflet_proposal_is_uniform():
+    """One pair per move: every (leaflet-0 lipid, leaflet-1 lipid) pair of
+    different types is proposed equally often (chi-squared), and no other
+    pair ever is."""
+    from scipy.stats import chisquare
+    m = synth.membrane(3, n_lipid_types=2, n_water=10, seed=12)       # 9 lipids per leaflet
+    o = oracle.Oracle(m)
+    leaf, lt = o.leaflets(m.pos_u), m.lipid_type
+    valid = [(a, b) for a in range(m.n_lipids) for b in range(m.n_lipids)
+             if leaf[a] == 0 and leaf[b] == 1 and lt[a] != lt[b]]
+    assert len(valid) >= 10
+    counts = dict.fromkeys(valid, 0)
+    n = 40 * len(valid)
+    for move in range(n):
+        (a, b), = o.interleaflet_pairs(m.pos_u, lt, move, 1)
+        counts[(int(a), int(b))] += 1
+    assert sum(counts.values()) == n
+    assert chisquare(list(counts.values())).pvalue > 1e-3
 
 
 # ---------------------------------------------------------------- soft-core alchemical path

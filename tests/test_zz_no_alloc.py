@@ -50,3 +50,24 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(mdas.MdasError) as e:
         mdas.forces_noalloc(s, buf.data_ptr(), buf.data_ptr(), buf.data_ptr())
     assert e.value.status == 1
+
+
+def test_noalloc_forces_after_pressure_coupling_use_the_current_box():
+    """Positions are fractions of the box: after box updates (Sec. 3 pressure
+    coupling) the allocation-free call must read them in the current box, as
+    mdas_forces does, not in the box the system was created with."""
+    import torch
+    m = synth.mcmd_small()
+    s = mdas.System(m, precision="fp64", pcouple=dict(nstpcouple=5, tau_p=1.0))
+    s.md_steps(20)
+    box, _, _ = s.box()
+    assert np.abs(box - m.box).max() > 1e-4 * m.box.max()
+    st = s.get_state()
+    F_ref = s.forces()
+    pos = torch.from_numpy(st["pos_u"].reshape(-1).view(np.int32).copy()).cuda()
+    lt = torch.from_numpy(st["ltype"].astype(np.int32)).cuda()
+    f_out = torch.full((m.n_beads * 3,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    mdas.forces_noalloc(s, pos.data_ptr(), lt.data_ptr(), f_out.data_ptr())
+    F = f_out.cpu().numpy().reshape(-1, 3)
+    assert force_err(F, F_ref) < F_TOL, force_err(F, F_ref)
