@@ -76,11 +76,20 @@ def config(m, extra=None):
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_rate(m, budget_s=12.0, min_evals=2):
-    """FP64 oracle: force evaluations + exchange trials on the same system,
-    one host thread, until the time budget is spent."""
+def host_cores():
+    """Host cores this process may use (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:  # noqa: BLE001 - not every host has affinity masks
+        return os.cpu_count() or 1
+
+
+def oracle_rate(m, budget_s=12.0, min_evals=2, threads=False):
+    """FP64 oracle: force evaluations + exchange trials on the same system
+    until the time budget is spent, on one host thread or (threads=True, the
+    OpenMP build) on all host cores."""
     import oracle
-    o = oracle.Oracle(m)
+    o = oracle.Oracle(m, threads=threads)
     st = o.state()
     t0 = time.perf_counter()
     pairs = 0
@@ -104,7 +113,10 @@ def run_reference(args):
         return
     m = workload()
     import oracle
-    o = oracle.Oracle(m)
+    cores = host_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    threads = oracle.lib_omp() is not None
+    o = oracle.Oracle(m, threads=threads)
     st = o.state()
     pairs = o.energy(st["pos_u"], forces=False)[0]["pairs"]
     for _ in range(args.warmup):
@@ -114,14 +126,16 @@ def run_reference(args):
         o.md_steps(st, 1, swap_every=1)
     dt = time.perf_counter() - t0
     value = pairs * args.steps / dt
-    sample = f"{args.steps} oracle MD steps with one exchange trial each on the 1152-lipid system"
+    used = cores if threads else 1
+    sample = (f"{args.steps} oracle MD steps with one exchange trial each on the 1152-lipid system, "
+              + (f"energies on {used} host cores (OpenMP build)" if threads else "one host thread"))
     print(json.dumps({
         "impl": "reference", "metric": "pair-interactions/s", "value": value, "unit": "pair-interactions/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config(m, {"reference_step": "1 MD step + 1 exchange trial (bounded sample)"}),
-        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": used, "kind": "oracle",
+                         "sample": sample, "host_cores": cores},
         "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "swap_trials_per_s": args.steps / dt,
     }))
@@ -321,12 +335,21 @@ def run_gpu(args):
         out["npt_1152_lipids"] = _extra(npt_benchmark, stream)
         out["served"] = _extra(serving_benchmark, stream)
     if not args.no_cpu_baseline:
-        ob = oracle_rate(m)
-        out["cpu_baseline"] = {"value": ob["pairs_per_s"], "unit": "pair-interactions/s", "cores": 1,
+        import oracle
+        cores = host_cores()
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        one = oracle_rate(m, budget_s=8.0)
+        omp = oracle_rate(m, budget_s=8.0, threads=True) if oracle.lib_omp() is not None else None
+        ob, used = (omp, cores) if omp else (one, 1)
+        out["cpu_baseline"] = {"value": ob["pairs_per_s"], "unit": "pair-interactions/s", "cores": used,
                                "kind": "oracle", "sample": f"{ob['evals']} FP64 force evaluations "
                                f"(half of them inside oracle MD steps with one exchange trial) on the same "
-                               f"1152-lipid system, {ob['seconds']:.1f} s, one host thread",
-                               "swap_trials_per_s": ob["trials_per_s"]}
+                               f"1152-lipid system, {ob['seconds']:.1f} s, "
+                               + (f"{used} host cores (OpenMP build of the oracle)" if omp else "one host thread"),
+                               "swap_trials_per_s": ob["trials_per_s"], "host_cores": cores,
+                               "single_thread": {"value": one["pairs_per_s"], "cores": 1,
+                                                 "swap_trials_per_s": one["trials_per_s"],
+                                                 "sample": f"{one['evals']} force evaluations, {one['seconds']:.1f} s"}}
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()

@@ -35,6 +35,39 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str | None:
+    """The same source built with OpenMP (the energy's cell loop split over
+    the host cores, per-thread sums added in thread order): for timing the
+    CPU baseline on all cores only; None when the compiler has no OpenMP."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(src):
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB_OMP + f".{os.getpid()}.tmp"
+        r = subprocess.run(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                            "-shared", "-o", tmp, src, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def lib_omp():
+    """The OpenMP build (build_omp), loaded; None when it cannot be built."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            path = build_omp()
+            if path is None:
+                return None
+            _lib_omp = C.CDLL(path)
+            _lib_omp.or_energy.restype = C.c_double
+    return _lib_omp
+
+
 def lib():
     global _lib
     with _lock:
@@ -121,8 +154,13 @@ class Oracle:
     """FP64 reference evaluation of one membrane (a `synth.Membrane` or alike)."""
 
     def __init__(self, m, tau_t=None, dt=None, temperature=None, seed=None, system_id=None,
-                 eps_rf=None, kb=None, ktheta=None, soft_core=0.0):
+                 eps_rf=None, kb=None, ktheta=None, soft_core=0.0, threads=False):
+        """threads=True: energies and MD steps through the OpenMP build on all
+        host cores (timing only; the tests use the single-thread build)."""
         self.m = m
+        self._L = lib_omp() if threads else lib()
+        if self._L is None:
+            raise RuntimeError("the OpenMP build of the oracle is not available on this host")
         n = m.n_beads
         self.n = n
         self._keep = dict(
@@ -174,8 +212,8 @@ class Oracle:
         btB = btA if btB is None else _i32(btB)
         t = np.zeros(6)
         F = np.zeros((self.n, 3)) if forces else None
-        lib().or_energy(C.byref(self.s), _p(pu), _p(btA), _p(btB), C.c_double(lam), int(cells), _p(t),
-                        _p(F) if forces else None)
+        self._L.or_energy(C.byref(self.s), _p(pu), _p(btA), _p(btB), C.c_double(lam), int(cells), _p(t),
+                          _p(F) if forces else None)
         terms = dict(lj=t[0], rf=t[1], bond=t[2], angle=t[3], total=t[4], pairs=int(t[5]))
         return terms, F
 
@@ -271,7 +309,7 @@ class Oracle:
         cs = self._cstate(st)
         nt = n_steps // swap_every if swap_every > 0 else 0
         recs = (_Trial * max(nt, 1))()
-        lib().or_md_steps(C.byref(self.s), C.byref(cs), int(n_steps), int(swap_every), int(cells), recs)
+        self._L.or_md_steps(C.byref(self.s), C.byref(cs), int(n_steps), int(swap_every), int(cells), recs)
         self._back(st, cs)
         return [dict(a=r.a, b=r.b, null=bool(r.null_trial), accepted=bool(r.accepted), dE=r.dE, u=r.u)
                 for r in recs[:nt]]

@@ -41,6 +41,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_BOLTZ 0.0083144626
 #define OR_COUL 138.935458
@@ -383,6 +386,26 @@ static void bonded(const or_sys *s, const uint32_t *pu, double *t, double *F, do
     }
 }
 
+/* The pairs (i, j > i) of bead i with the beads of its cell and the 26
+ * neighbouring cells of the oracle's cell list. */
+static void pairs_of_bead(const or_sys *s, const uint32_t *pu, const int *btA, const int *btB, double lam,
+                          const int nc[3], const int *cell_of, const int *sorted, const int *start, int i,
+                          double *t, double *F, double *W)
+{
+    int c = cell_of[i];
+    int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = (cx + dx + nc[0]) % nc[0], y = (cy + dy + nc[1]) % nc[1], z = (cz + dz + nc[2]) % nc[2];
+                int cj = (z * nc[1] + y) * nc[0] + x;
+                for (int p = start[cj]; p < start[cj + 1]; ++p) {
+                    int j = sorted[p];
+                    if (j > i) add_pair(s, pu, btA, btB, lam, i, j, t, F, W);
+                }
+            }
+}
+
 /* Potential energy U(lam) and, if F != NULL, F = -grad U.
  * terms: [0] LJ, [1] RF, [2] bond, [3] angle, [4] total, [5] number of
  * in-cutoff non-excluded pairs.  use_cells = 0: all N(N-1)/2 pairs;
@@ -408,20 +431,32 @@ static double energy_core(const or_sys *s, const uint32_t *pu, const int *btA, c
         int *cell_of = malloc(sizeof(int) * n), *sorted = malloc(sizeof(int) * n);
         int *start = malloc(sizeof(int) * (ncell + 1));
         or_cell_list(n, pu, nc, cell_of, sorted, start);
-        for (int i = 0; i < n; ++i) {
-            int c = cell_of[i];
-            int cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int x = (cx + dx + nc[0]) % nc[0], y = (cy + dy + nc[1]) % nc[1], z = (cz + dz + nc[2]) % nc[2];
-                        int cj = (z * nc[1] + y) * nc[0] + x;
-                        for (int p = start[cj]; p < start[cj + 1]; ++p) {
-                            int j = sorted[p];
-                            if (j > i) add_pair(s, pu, btA, btB, lam, i, j, t, F, W);
-                        }
-                    }
+#ifndef _OPENMP
+        for (int i = 0; i < n; ++i) pairs_of_bead(s, pu, btA, btB, lam, nc, cell_of, sorted, start, i, t, F, W);
+#else
+        /* Timing build only (compiled with -fopenmp for the CPU baseline on
+         * all host cores): the beads are split over the threads, each with
+         * its own sums, which are added in thread order afterwards.  The
+         * parity build has no OpenMP and runs the loop above. */
+        int nth = omp_get_max_threads();
+        double *tt = calloc((size_t)6 * nth, sizeof(double));
+        double *FF = F ? calloc((size_t)3 * n * nth, sizeof(double)) : NULL;
+        double *WW = W ? calloc((size_t)3 * nth, sizeof(double)) : NULL;
+#pragma omp parallel
+        {
+            int th = omp_get_thread_num();
+#pragma omp for schedule(dynamic, 64)
+            for (int i = 0; i < n; ++i)
+                pairs_of_bead(s, pu, btA, btB, lam, nc, cell_of, sorted, start, i, tt + 6 * th,
+                              FF ? FF + (size_t)3 * n * th : NULL, WW ? WW + 3 * th : NULL);
         }
+        for (int th = 0; th < nth; ++th) {
+            for (int k = 0; k < 6; ++k) t[k] += tt[6 * th + k];
+            if (F) for (size_t k = 0; k < (size_t)3 * n; ++k) F[k] += FF[(size_t)3 * n * th + k];
+            if (W) for (int k = 0; k < 3; ++k) W[k] += WW[3 * th + k];
+        }
+        free(tt); free(FF); free(WW);
+#endif
         free(cell_of); free(sorted); free(start);
     }
     bonded(s, pu, t, F, W);
