@@ -1604,10 +1604,11 @@ struct mdas_server {
     int md_quantum = 25;
     int want_state = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t upload = nullptr;           // uploads of admitted patches, beside the round's device work
     std::deque<PendingJob> queue;
     std::vector<ActiveJob> active;
     std::vector<mdas_job_result> finished;
-    Batch md_batch, swap_batch;
+    Batch md_batch, swap_batch, mdas_batch, mdas_run_batch;
     int64_t next_id = 1;
     std::chrono::steady_clock::time_point t0;
     std::multimap<size_t, void *> pool;      // freed arenas by size, reused by later jobs
@@ -1684,6 +1685,99 @@ mdas_status finish_job(mdas_server *sv, ActiveJob &a) {
     return MDAS_OK;
 }
 
+// Admit queued jobs in arrival order while a slot and room in the memory
+// budget are free.  A patch is created with its uploads on the upload stream,
+// so they run beside whatever the round has already launched on the server's
+// stream; the system then works on the server's stream.
+mdas_status admit(mdas_server *sv) {
+    while (!sv->queue.empty() && (int)sv->active.size() < sv->max_active &&
+           sv->in_use + sv->queue.front().footprint <= sv->budget) {
+        PendingJob p = std::move(sv->queue.front());
+        sv->queue.pop_front();
+        mdas_system_desc d = p.d;
+        d.pos = p.pos.data();
+        d.vel = p.vel.empty() ? nullptr : p.vel.data();
+        d.eps = p.eps.data(); d.sigma = p.sigma.data(); d.charge = p.charge.data();
+        d.lipid_first_bead = p.first.empty() ? nullptr : p.first.data();
+        d.lipid_type = p.ltype.data();
+        d.lipid_bead_type = p.lbt.data();
+        d.bonds = p.bonds.empty() ? nullptr : p.bonds.data();
+        d.angles = p.angles.empty() ? nullptr : p.angles.data();
+        d.cuda_stream = sv->upload;
+        d.dev_alloc = pool_alloc;
+        d.dev_free = pool_free;
+        d.alloc_ctx = sv;
+        ActiveJob a;
+        mdas_status st = mdas_create_system(&d, &a.sys);
+        if (st != MDAS_OK) return st;
+        // creation waited for its uploads: from here on the server's stream
+        a.sys->stream = sv->stream;
+        a.sys->solo->stream = sv->stream;
+        a.t_admit = sv->now();
+        a.remaining = p.job.kind == MDAS_JOB_MD ? p.job.n : 1;
+        sv->in_use += p.footprint;
+        a.p = std::move(p);
+        sv->active.push_back(std::move(a));
+    }
+    return MDAS_OK;
+}
+
+// The MDAS jobs of one parameter set (pairs, lambda steps, MD steps per
+// lambda) as one batched move: every launch of mdas_alchemical_move covers
+// all of them (pair selection, the alchemical trajectory of those that found
+// pairs in one MD run, the Metropolis test, the restore).  Per system the
+// arithmetic is that of its own move.
+mdas_status batched_moves(mdas_server *sv, const std::vector<ActiveJob *> &jobs) {
+    const mdas_job &j = jobs[0]->p.job;
+    std::vector<mdas_system *> v;
+    for (auto *a : jobs) v.push_back(a->sys);
+    mdas_system *s = v[0];                    // where errors are reported
+    mdas_status st = refill_batch(sv->mdas_batch, v);
+    if (st != MDAS_OK) return st;
+    LaunchCtx L = sv->mdas_batch.ctx();
+    launch_snapshot(L);
+    launch_mdas_select(L, j.n_pairs, 64 * j.n_pairs + 64, 0);
+    std::vector<int> np(v.size(), 0);
+    for (size_t k = 0; k < v.size(); ++k)
+        CK(cudaMemcpyAsync(&np[k], &v[k]->hs.c->n_pairs, 4, cudaMemcpyDeviceToHost, sv->stream));
+    CK(cudaStreamSynchronize(sv->stream));
+    std::vector<mdas_system *> run;
+    for (size_t k = 0; k < v.size(); ++k)
+        if (np[k] > 0) run.push_back(v[k]);
+    if (!run.empty()) {
+        st = refill_batch(sv->mdas_run_batch, run);
+        if (st != MDAS_OK) return st;
+        LaunchCtx R = sv->mdas_run_batch.ctx();
+        const double dl = 1.0 / j.n_lambda;
+        if (j.md_per_lambda > 0) {
+            launch_mdas_set_lambda(R, 0.0, 1);
+            st = run_md(run[0], sv->mdas_run_batch, (long long)j.n_lambda * j.md_per_lambda, 0, true, false,
+                        j.md_per_lambda, dl);
+            if (st != MDAS_OK) return st;
+        } else {
+            for (int k = 1; k <= j.n_lambda; ++k) {
+                launch_mdas_set_lambda(R, (double)(k - 1) / j.n_lambda, 1);
+                st = build_cells(run[0], sv->mdas_run_batch);
+                if (st != MDAS_OK) return st;
+                launch_mdas_dE(R, dl);
+            }
+        }
+    }
+    launch_mdas_accept(L);
+    launch_mdas_restore(L);
+    std::vector<Counters> c(v.size());
+    for (size_t k = 0; k < v.size(); ++k)
+        CK(cudaMemcpyAsync(&c[k], v[k]->hs.c, sizeof(Counters), cudaMemcpyDeviceToHost, sv->stream));
+    CK(cudaStreamSynchronize(sv->stream));
+    CK(cudaGetLastError());
+    for (size_t k = 0; k < v.size(); ++k) {
+        v[k]->cells_valid = false;
+        jobs[k]->w = c[k].w;
+        jobs[k]->move_accepted = c[k].mdas_accept;
+    }
+    return check_err(v[0], sv->mdas_batch);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1703,6 +1797,13 @@ mdas_status mdas_server_create(size_t hbm_budget_bytes, int32_t max_active, int3
     sv->md_quantum = md_quantum;
     sv->want_state = keep_state_hash;
     sv->stream = stream;
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&sv->upload, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete sv;
+            return cuda_fail(nullptr, e, "server_create: upload stream");
+        }
+    }
     sv->t0 = std::chrono::steady_clock::now();
     *out = sv;
     return MDAS_OK;
@@ -1716,6 +1817,9 @@ void mdas_server_destroy(mdas_server *sv) {
     for (auto &kv : sv->sizes) cudaFree(kv.first);
     destroy_batch(&sv->md_batch);
     destroy_batch(&sv->swap_batch);
+    destroy_batch(&sv->mdas_batch);
+    destroy_batch(&sv->mdas_run_batch);
+    if (sv->upload) cudaStreamDestroy(sv->upload);
     delete sv;
 }
 
@@ -1752,48 +1856,32 @@ mdas_status mdas_server_submit(mdas_server *sv, const mdas_system_desc *d, const
 mdas_status mdas_server_run(mdas_server *sv, int32_t max_rounds, int32_t *n_active, int32_t *n_queued) {
     if (!sv || max_rounds < 0) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_run: bad argument");
     for (int r = 0; r < max_rounds; ++r) {
-        // admission in arrival order: a free slot and room in the memory budget
-        while (!sv->queue.empty() && (int)sv->active.size() < sv->max_active &&
-               sv->in_use + sv->queue.front().footprint <= sv->budget) {
-            PendingJob p = std::move(sv->queue.front());
-            sv->queue.pop_front();
-            mdas_system_desc d = p.d;
-            d.pos = p.pos.data();
-            d.vel = p.vel.empty() ? nullptr : p.vel.data();
-            d.eps = p.eps.data(); d.sigma = p.sigma.data(); d.charge = p.charge.data();
-            d.lipid_first_bead = p.first.empty() ? nullptr : p.first.data();
-            d.lipid_type = p.ltype.data();
-            d.lipid_bead_type = p.lbt.data();
-            d.bonds = p.bonds.empty() ? nullptr : p.bonds.data();
-            d.angles = p.angles.empty() ? nullptr : p.angles.data();
-            d.cuda_stream = sv->stream;
-            d.dev_alloc = pool_alloc;
-            d.dev_free = pool_free;
-            d.alloc_ctx = sv;
-            ActiveJob a;
-            mdas_status st = mdas_create_system(&d, &a.sys);
+        // an idle server admits at once (there is no work to overlap with)
+        if (sv->active.empty()) {
+            mdas_status st = admit(sv);
             if (st != MDAS_OK) return st;
-            a.t_admit = sv->now();
-            a.remaining = p.job.kind == MDAS_JOB_MD ? p.job.n : 1;
-            sv->in_use += p.footprint;
-            a.p = std::move(p);
-            sv->active.push_back(std::move(a));
         }
         if (sv->active.empty()) break;
-        // MD jobs: one batched quantum of steps
+        // MD jobs: one batched quantum of steps, launched without waiting
         std::vector<mdas_system *> mdv;
         long long q = sv->md_quantum;
         for (auto &a : sv->active)
             if (a.p.job.kind == MDAS_JOB_MD && a.remaining > 0) { mdv.push_back(a.sys); q = std::min(q, a.remaining); }
         if (!mdv.empty()) {
             mdas_status st = refill_batch(sv->md_batch, mdv);
-            if (st == MDAS_OK) st = run_md(mdv[0], sv->md_batch, q, 0);
+            if (st == MDAS_OK) st = run_md(mdv[0], sv->md_batch, q, 0, false, false);
             if (st != MDAS_OK) return st;
             for (auto &a : sv->active)
                 if (a.p.job.kind == MDAS_JOB_MD && a.remaining > 0) {
                     a.remaining -= q;
                     if (a.remaining == 0) a.done = true;
                 }
+        }
+        // jobs that arrived meanwhile, created while the quantum runs; new MD
+        // jobs start with the next round, new swap and MDAS jobs below
+        {
+            mdas_status st = admit(sv);
+            if (st != MDAS_OK) return st;
         }
         // swap jobs: one batched evaluation per trial count
         std::map<int, std::vector<ActiveJob *>> groups;
@@ -1810,18 +1898,23 @@ mdas_status mdas_server_run(mdas_server *sv, int32_t max_rounds, int32_t *n_acti
             }
             for (auto *a : g.second) a->done = true;
         }
-        // MDAS jobs: one move each
+        // MDAS jobs: one batched move per parameter set
+        std::map<std::vector<int>, std::vector<ActiveJob *>> moves;
         for (auto &a : sv->active)
             if (a.p.job.kind == MDAS_JOB_MDAS && !a.done) {
-                mdas_move_result mr;
-                mdas_status st = a.sys->n_lip > 0 ? mdas_alchemical_move(a.sys, a.p.job.n_pairs, a.p.job.n_lambda,
-                                                                         a.p.job.md_per_lambda, nullptr, &mr)
-                                                  : MDAS_OK;
-                if (st != MDAS_OK) return st;
-                if (a.sys->n_lip > 0) { a.w = mr.w; a.move_accepted = mr.accepted; }
                 a.done = true;
+                if (a.sys->n_lip > 0)
+                    moves[{a.p.job.n_pairs, a.p.job.n_lambda, a.p.job.md_per_lambda}].push_back(&a);
             }
-        // completion: results, memory back to the pool, slots free
+        for (auto &g : moves) {
+            mdas_status st = batched_moves(sv, g.second);
+            if (st != MDAS_OK) return st;
+        }
+        // completion: errors of the MD quantum, results, memory back to the pool, slots free
+        if (!mdv.empty()) {
+            mdas_status st = check_err(mdv[0], sv->md_batch);
+            if (st != MDAS_OK) return st;
+        }
         {
             cudaError_t e = cudaStreamSynchronize(sv->stream);
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "server_run");

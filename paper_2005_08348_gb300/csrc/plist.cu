@@ -367,22 +367,30 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
                 const uint32_t jkey = __float_as_uint(e.w) >> 8;   // (lipid + 1) << 4 | k
                 const uint32_t jk = jkey & 15u;
                 const int skf = sm.sk[f];
-                for (int b = 0; b < nbw; ++b) {
+                // the tests of all the warp's beads first (independent: shared
+                // loads, arithmetic and votes in flight together), then the
+                // entries, bead by bead in the same order as one loop would
+                unsigned bal[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
                     const float4 bi = sm.sb[w][b];
                     const float dx = bi.x - e.x, dy = bi.y - e.y, dz = bi.z - e.z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
                     // excluded: the same lipid ((lipid + 1) equal) and a bonded local index
                     const bool excl = (__float_as_uint(bi.w) ^ jkey) < 16u && ((sm.sbe[w][b] >> jk) & 1u);
-                    const bool in = have && r2 < rl2 && !excl && f != fself + b;
-                    const unsigned bal = __ballot_sync(0xffffffffu, in);
-                    if (bal) {
+                    const bool in = b < nbw && have && r2 < rl2 && !excl && f != fself + b;
+                    bal[b] = __ballot_sync(0xffffffffu, in);
+                }
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    if (bal[b]) {
                         const int bb = __shfl_sync(0xffffffffu, base, b);
-                        if (in) {
-                            const unsigned ei = (unsigned)bb + __popc(bal & ltmask);
+                        if ((bal[b] >> lane) & 1u) {
+                            const unsigned ei = (unsigned)bb + __popc(bal[b] & ltmask);
                             if (ei < lcapg)
                                 nl[(size_t)(i0 + rw + b) * NL_G + (size_t)(ei / NL_G) * lrow + ei % NL_G] = skf;
                         }
-                        if (lane == b) base = bb + __popc(bal);
+                        if (lane == b) base = bb + __popc(bal[b]);
                     }
                 }
             }

@@ -82,3 +82,20 @@ def test_admission_by_slots_and_memory():
     with pytest.raises(mdas.MdasError) as e:
         mdas.Server(mdas.footprint(ps[0]) // 2, max_active=2).submit(ps[0], mdas.JOB_MD, n=5)
     assert e.value.status == 2
+
+
+def test_mdas_jobs_run_as_one_batched_move():
+    """MDAS jobs that are active together run as one batched move (one launch
+    per phase for all of them); each result equals the job run alone."""
+    ps = patches()[:4]
+    js = [(p, mdas.JOB_MDAS, 0) for p in ps]
+    sv = mdas.Server(4 * GB, max_active=4, md_quantum=10, keep_state_hash=True)
+    ids = [sv.submit(p, k, n=n, n_pairs=2, n_lambda=3, md_per_lambda=2) for p, k, n in js]
+    assert sv.run(1) == (0, 0)                           # all four done in one round
+    res = {r["job_id"]: r for r in sv.results()}
+    mix = [res[i] for i in ids]
+    for (p, k, n), r in zip(js, mix):
+        alone = run(mdas.Server(4 * GB, max_active=1, md_quantum=25, keep_state_hash=True), [(p, k, n)],
+                    stagger=False)[0]
+        assert r["state_hash"] == alone["state_hash"]
+        assert (r["w"], r["move_accepted"], r["md_steps"]) == (alone["w"], alone["move_accepted"], alone["md_steps"])
