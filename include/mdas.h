@@ -455,6 +455,23 @@ void mdas_server_destroy(mdas_server *sv);
  * allocator fields are replaced by the server's).  MDAS_ERR_OOM if the patch
  * alone exceeds the budget. */
 mdas_status mdas_server_submit(mdas_server *sv, const mdas_system_desc *d, const mdas_job *job, int64_t *job_id);
+/* Resident patches: a patch added to the server stays on the device, and its
+ * state (positions, velocities, lipid types, Philox counters) carries from
+ * one job to the next.  mdas_server_add_patch creates it from a copy of d
+ * (stream and allocator fields replaced by the server's) and charges its
+ * footprint to the memory budget at once: MDAS_ERR_OOM when it does not fit
+ * what is left.  mdas_server_submit_to queues a job on it; the jobs of one
+ * patch run one after another in submission order, jobs on different patches
+ * together (batched like the jobs above), each admitted when a slot is free
+ * and its patch idle.  A job's result reports the counters it advanced.
+ * mdas_server_patch_state copies an idle patch's state to host arrays (as
+ * mdas_get_state; MDAS_ERR_BUSY while a job runs on it), and
+ * mdas_server_remove_patch frees an idle patch without queued jobs
+ * (MDAS_ERR_BUSY otherwise).  Unknown patch ids: MDAS_ERR_INVALID_ARG. */
+mdas_status mdas_server_add_patch(mdas_server *sv, const mdas_system_desc *d, int64_t *patch_id);
+mdas_status mdas_server_submit_to(mdas_server *sv, int64_t patch_id, const mdas_job *job, int64_t *job_id);
+mdas_status mdas_server_patch_state(mdas_server *sv, int64_t patch_id, mdas_state_view *out);
+mdas_status mdas_server_remove_patch(mdas_server *sv, int64_t patch_id);
 /* Run up to max_rounds scheduling rounds (admit, advance, retire); reports the
  * active and queued job counts. */
 mdas_status mdas_server_run(mdas_server *sv, int32_t max_rounds, int32_t *n_active, int32_t *n_queued);

@@ -28,6 +28,9 @@ struct Batch {
     int *dscratch = nullptr;      // [2]: pending sum, error or
     unsigned int *bticket = nullptr;   // last-block ticket of the step kernel over the batch
     void *rsync = nullptr;        // grid-barrier state of the persistent MD kernel (zeroed)
+    void *part = nullptr;         // partition of the persistent kernel's groups among the systems
+    size_t part_cap = 0;
+    int part_groups = 0;          // groups the partition was made for (0: none made yet)
     bool persistent = true;       // MD in the persistent kernel (else separate kernel launches)
     size_t cap_sys = 0, cap_beads = 0, cap_cells = 0, cap_sort = 0;   // device capacity (refillable batches)
     size_t cap_nlb = 0, cap_lc = 0, cap_ls = 0;
@@ -194,6 +197,7 @@ void destroy_batch(Batch *b) {
     if (b->dscratch) cudaFree(b->dscratch);
     if (b->bticket) cudaFree(b->bticket);
     if (b->rsync) cudaFree(b->rsync);
+    if (b->part) cudaFree(b->part);
 }
 
 // block maps of a batch: per system its bead blocks, cells, cell groups of the
@@ -308,6 +312,7 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     b.nlbeads.n = (int)mp.nlbeads.size();
     b.lcells.n = (int)mp.lcells.size();
     b.lsort.n = (int)mp.lsort.size();
+    b.part_groups = 0;                     // the partition is made again for the new systems
     return MDAS_OK;
 }
 
@@ -388,15 +393,83 @@ struct SegTimer {
     }
 };
 
-__global__ void k_run_abort(void *sync, int nbytes, const SysDev *__restrict__ sys, int n_sys) {
+__global__ void k_run_abort(void *sync, int nbytes, const SysDev *__restrict__ sys, int n_sys, SysBar *bars) {
     // a persistent launch that gave up at a barrier: every system of the
     // batch records it, and the barrier state is cleared for the next launch
     const int *w = (const int *)sync;
     const int ab = w[2];
     if (ab == 0) return;
-    for (int q = threadIdx.x; q < n_sys; q += blockDim.x) atomicOr(&sys[q].c->err, ab);
+    for (int q = threadIdx.x; q < n_sys; q += blockDim.x) {
+        atomicOr(&sys[q].c->err, ab);
+        if (bars) bars[q].count = bars[q].base = 0u;
+    }
     __syncthreads();
     if (threadIdx.x == 0) memset(sync, 0, nbytes);
+}
+
+// The partition of a persistent launch's groups among the systems of a
+// batch (partitioned mode): groups in proportion to each system's step
+// items, at least one each; false when the batch does not need it (one
+// system, or every step item has a group of its own) or cannot have it
+// (more systems than groups).
+mdas_status make_partition(mdas_system *s, Batch &b, int groups, bool *use) {
+    const int n = (int)b.sys.size();
+    *use = false;
+    std::vector<int> items(n);
+    long long total = 0;
+    for (int q = 0; q < n; ++q) {
+        items[q] = (b.sys[q]->n + NL_BEADS - 1) / NL_BEADS;
+        total += items[q];
+    }
+    if (n < 2 || n > groups / 2 || total + (long long)(TRIAL_PARTS + 1) * n <= groups) return MDAS_OK;
+    *use = true;
+    if (b.part_groups == groups) return MDAS_OK;
+    std::vector<int> ng(n);
+    int used = 0;
+    for (int q = 0; q < n; ++q) {
+        ng[q] = std::max(1, (int)((long long)groups * items[q] / total));
+        used += ng[q];
+    }
+    while (used > groups) {                // take back from the system with the fewest items per group
+        int best = -1;
+        for (int q = 0; q < n; ++q)
+            if (ng[q] > 1 && (best < 0 || (double)items[q] / ng[q] < (double)items[best] / ng[best])) best = q;
+        if (best < 0) { *use = false; return MDAS_OK; }
+        --ng[best]; --used;
+    }
+    while (used < groups) {                // give to the system with the most items per group
+        int best = 0;
+        for (int q = 1; q < n; ++q)
+            if ((double)items[q] / ng[q] > (double)items[best] / ng[best]) best = q;
+        ++ng[best]; ++used;
+    }
+    const PartLayout pl = part_layout(n, groups);
+    std::vector<char> host(pl.bytes, 0);
+    SysRange *r = (SysRange *)(host.data() + pl.ranges);
+    int *gs = (int *)(host.data() + pl.gsys);
+    int g0 = 0, nl0 = 0, bd0 = 0, ls0 = 0, lc0 = 0;
+    for (int q = 0; q < n; ++q) {
+        const mdas_system *x = b.sys[q];
+        r[q].g0 = g0; r[q].ng = ng[q];
+        r[q].nl0 = nl0; r[q].nln = (x->n + NL_BEADS - 1) / NL_BEADS;
+        r[q].bd0 = bd0; r[q].bdn = (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK;
+        r[q].ls0 = ls0; r[q].lsn = (x->hp.n_lcells + CELLS_PER_SORT_BLOCK - 1) / CELLS_PER_SORT_BLOCK;
+        r[q].lc0 = lc0; r[q].lcn = x->hp.n_lcells;
+        for (int k = 0; k < ng[q]; ++k) gs[g0 + k] = q;
+        g0 += ng[q]; nl0 += r[q].nln; bd0 += r[q].bdn; ls0 += r[q].lsn; lc0 += r[q].lcn;
+    }
+    if (nl0 != b.nlbeads.n || bd0 != b.beads.n || ls0 != b.lsort.n || lc0 != b.lcells.n)
+        return fail(s, MDAS_ERR_INVALID_ARG, "batch: block maps do not match the partition");
+    if (pl.bytes > b.part_cap) {
+        if (b.part) cudaFree(b.part);
+        b.part = nullptr;
+        CK(cudaMalloc(&b.part, pl.bytes));
+        b.part_cap = pl.bytes;
+    }
+    CK(cudaMemcpyAsync(b.part, host.data(), pl.bytes, cudaMemcpyHostToDevice, b.stream));
+    CK(cudaStreamSynchronize(b.stream));
+    b.part_groups = groups;
+    return MDAS_OK;
 }
 
 // n_steps MD steps on a batch; after every swap_every-th step one trial.
@@ -412,7 +485,17 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     for (auto *x : b.sys) tm.on = tm.on || x->timing;
     for (auto *x : b.sys) x->cells_valid = false;
     LaunchCtx L = b.ctx();
-    const bool persistent = b.persistent && md_run_blocks(b.precision, !lambda ? (L.pc ? 3 : 0) : L.soft ? 2 : 1) > 0;
+    const int run_mode = !lambda ? (L.pc ? 3 : 0) : L.soft ? 2 : 1;
+    const bool persistent = b.persistent && md_run_blocks(b.precision, run_mode) > 0;
+    if (persistent) {
+        bool use = false;
+        mdas_status st = make_partition(s, b, md_run_groups(b.precision, run_mode), &use);
+        if (st != MDAS_OK) return st;
+        if (use) {
+            L.part = b.part;
+            L.part_groups = b.part_groups;
+        }
+    }
     // segments of at most MAX_DRAW_STEPS - 1 steps (the precomputed thermostat
     // variates); a segment starting at step k0 has its trials after local
     // steps s with (k0 + s + 1) % swap_every == 0
@@ -448,7 +531,9 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
             CK(launch_md_run(L, lambda, (int)n, swap_every, trial ? (int)(k0 % swap_every) : 0, lam_M,
                              (int)(lam_base + k0), dlam, b.rsync));
             CK(tm.end(b.stream));
-            k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
+            k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size(),
+                                                 L.part ? (SysBar *)((char *)L.part + part_layout((int)b.sys.size(),
+                                                          L.part_groups).bars) : nullptr);
             launches += 1;
             if (pc_nst > 0) { launch_pcouple(L); ++launches; }
             continue;
@@ -1214,7 +1299,7 @@ mdas_status mdas_wait_timeout_probe(mdas_system *s) {
     if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "wait_timeout_probe: NULL system");
     Batch &b = *s->solo;
     CK(launch_barrier_stall(b.rsync, b.stream));
-    k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size());
+    k_run_abort<<<1, 32, 0, b.stream>>>(b.rsync, (int)md_run_sync_bytes(), b.dsys, (int)b.sys.size(), nullptr);
     CK(cudaGetLastError());
     return check_err(s, b);
 }
@@ -1559,6 +1644,7 @@ namespace {
 
 struct PendingJob {
     int64_t id = 0;
+    int64_t patch = -1;                      // a resident patch, or -1: the job brings its own patch (d)
     mdas_job job{};
     double t_submit = 0.0;
     size_t footprint = 0;
@@ -1570,6 +1656,7 @@ struct PendingJob {
 struct ActiveJob {
     PendingJob p;
     mdas_system *sys = nullptr;
+    mdas_counters c0{};                      // the patch's counters when the job started (resident patches)
     double t_admit = 0.0;
     long long remaining = 0;
     bool done = false;
@@ -1598,7 +1685,18 @@ size_t arena_estimate(const mdas_system_desc *d) {
 
 }  // namespace
 
+// A patch kept on the device between jobs: its state carries from one job
+// to the next; one job at a time runs on it.
+struct ResidentPatch {
+    mdas_system *sys = nullptr;
+    size_t footprint = 0;
+    bool busy = false;                       // a job on it is active
+    int queued = 0;                          // jobs on it waiting in the queue
+};
+
 struct mdas_server {
+    std::map<int64_t, ResidentPatch> patches;
+    int64_t next_patch = 1;
     size_t budget = 0, in_use = 0;
     int max_active = 0;
     int md_quantum = 25;
@@ -1647,6 +1745,7 @@ uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
 
 mdas_status finish_job(mdas_server *sv, ActiveJob &a) {
     mdas_system *s = a.sys;
+    const bool resident = a.p.patch >= 0;
     mdas_job_result r{};
     r.job_id = a.p.id;
     r.kind = a.p.job.kind;
@@ -1657,9 +1756,9 @@ mdas_status finish_job(mdas_server *sv, ActiveJob &a) {
     mdas_status st = mdas_get_counters(s, &c);
     if (st != MDAS_OK) return st;
     r.t_done = sv->now();
-    r.md_steps = c.md_steps;
-    r.trials = c.trials;
-    r.accepted = c.accepted;
+    r.md_steps = c.md_steps - a.c0.md_steps;
+    r.trials = c.trials - a.c0.trials;
+    r.accepted = c.accepted - a.c0.accepted;
     r.w = a.w;
     r.move_accepted = a.move_accepted;
     if (sv->want_state) {
@@ -1678,10 +1777,57 @@ mdas_status finish_job(mdas_server *sv, ActiveJob &a) {
         h = fnv1a(h, lt.data(), 4ull * s->n_lip);
         r.state_hash = h;
     }
-    sv->in_use -= a.p.footprint;
-    mdas_destroy_system(s);
+    if (resident) {
+        sv->patches[a.p.patch].busy = false;
+    } else {
+        sv->in_use -= a.p.footprint;
+        mdas_destroy_system(s);
+    }
     a.sys = nullptr;
     sv->finished.push_back(r);
+    return MDAS_OK;
+}
+
+// A system created from a copy of a description for the server: uploads on
+// the upload stream, then working on the server's stream.
+mdas_status server_create(mdas_server *sv, const PendingJob &p, mdas_system **out) {
+    mdas_system_desc d = p.d;
+    d.pos = p.pos.data();
+    d.vel = p.vel.empty() ? nullptr : p.vel.data();
+    d.eps = p.eps.data(); d.sigma = p.sigma.data(); d.charge = p.charge.data();
+    d.lipid_first_bead = p.first.empty() ? nullptr : p.first.data();
+    d.lipid_type = p.ltype.data();
+    d.lipid_bead_type = p.lbt.data();
+    d.bonds = p.bonds.empty() ? nullptr : p.bonds.data();
+    d.angles = p.angles.empty() ? nullptr : p.angles.data();
+    d.cuda_stream = sv->upload;
+    d.dev_alloc = pool_alloc;
+    d.dev_free = pool_free;
+    d.alloc_ctx = sv;
+    mdas_status st = mdas_create_system(&d, out);
+    if (st != MDAS_OK) return st;
+    // creation waited for its uploads: from here on the server's stream
+    (*out)->stream = sv->stream;
+    (*out)->solo->stream = sv->stream;
+    return MDAS_OK;
+}
+
+// A host copy of a description's arrays (the job or patch keeps them).
+mdas_status copy_desc(const mdas_system_desc *d, PendingJob &p) {
+    if (!d || d->n_beads <= 0 || !d->pos || !d->lipid_type || !d->lipid_bead_type || !d->eps || !d->sigma || !d->charge)
+        return MDAS_ERR_INVALID_ARG;
+    const size_t n = d->n_beads, nl = d->n_lipids, nbt = d->n_bead_types;
+    p.pos.assign(d->pos, d->pos + 3 * n);
+    if (d->vel) p.vel.assign(d->vel, d->vel + 3 * n);
+    p.eps.assign(d->eps, d->eps + nbt * nbt);
+    p.sigma.assign(d->sigma, d->sigma + nbt * nbt);
+    p.charge.assign(d->charge, d->charge + nbt);
+    if (d->lipid_first_bead) p.first.assign(d->lipid_first_bead, d->lipid_first_bead + nl);
+    p.ltype.assign(d->lipid_type, d->lipid_type + nl);
+    p.lbt.assign(d->lipid_bead_type, d->lipid_bead_type + (size_t)d->n_lipid_types * d->beads_per_lipid);
+    if (d->n_bonds) p.bonds.assign(d->bonds, d->bonds + 2 * d->n_bonds);
+    if (d->n_angles) p.angles.assign(d->angles, d->angles + 3 * d->n_angles);
+    p.d = *d;
     return MDAS_OK;
 }
 
@@ -1689,34 +1835,34 @@ mdas_status finish_job(mdas_server *sv, ActiveJob &a) {
 // budget are free.  A patch is created with its uploads on the upload stream,
 // so they run beside whatever the round has already launched on the server's
 // stream; the system then works on the server's stream.
-mdas_status admit(mdas_server *sv) {
-    while (!sv->queue.empty() && (int)sv->active.size() < sv->max_active &&
-           sv->in_use + sv->queue.front().footprint <= sv->budget) {
-        PendingJob p = std::move(sv->queue.front());
-        sv->queue.pop_front();
-        mdas_system_desc d = p.d;
-        d.pos = p.pos.data();
-        d.vel = p.vel.empty() ? nullptr : p.vel.data();
-        d.eps = p.eps.data(); d.sigma = p.sigma.data(); d.charge = p.charge.data();
-        d.lipid_first_bead = p.first.empty() ? nullptr : p.first.data();
-        d.lipid_type = p.ltype.data();
-        d.lipid_bead_type = p.lbt.data();
-        d.bonds = p.bonds.empty() ? nullptr : p.bonds.data();
-        d.angles = p.angles.empty() ? nullptr : p.angles.data();
-        d.cuda_stream = sv->upload;
-        d.dev_alloc = pool_alloc;
-        d.dev_free = pool_free;
-        d.alloc_ctx = sv;
+mdas_status admit(mdas_server *sv, bool resident_only) {
+    for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)sv->active.size() < sv->max_active;) {
+        PendingJob &q = *it;
         ActiveJob a;
-        mdas_status st = mdas_create_system(&d, &a.sys);
-        if (st != MDAS_OK) return st;
-        // creation waited for its uploads: from here on the server's stream
-        a.sys->stream = sv->stream;
-        a.sys->solo->stream = sv->stream;
+        if (q.patch < 0 && resident_only) { ++it; continue; }
+        if (q.patch >= 0) {
+            // a job on a resident patch: its patch must be idle (jobs on one
+            // patch run one after another, in submission order)
+            ResidentPatch &rp = sv->patches[q.patch];
+            if (rp.busy) { ++it; continue; }
+            rp.busy = true;
+            rp.queued--;
+            a.sys = rp.sys;
+            mdas_status st = mdas_get_counters(a.sys, &a.c0);
+            if (st != MDAS_OK) return st;
+        } else {
+            // a job with its own patch: created now if the memory budget allows
+            // (arrival order: a job that does not fit waits, and so do the jobs
+            // with their own patches behind it)
+            if (sv->in_use + q.footprint > sv->budget) break;
+            mdas_status st = server_create(sv, q, &a.sys);
+            if (st != MDAS_OK) return st;
+            sv->in_use += q.footprint;
+        }
         a.t_admit = sv->now();
-        a.remaining = p.job.kind == MDAS_JOB_MD ? p.job.n : 1;
-        sv->in_use += p.footprint;
-        a.p = std::move(p);
+        a.remaining = q.job.kind == MDAS_JOB_MD ? q.job.n : 1;
+        a.p = std::move(q);
+        it = sv->queue.erase(it);
         sv->active.push_back(std::move(a));
     }
     return MDAS_OK;
@@ -1812,7 +1958,8 @@ mdas_status mdas_server_create(size_t hbm_budget_bytes, int32_t max_active, int3
 void mdas_server_destroy(mdas_server *sv) {
     if (!sv) return;
     for (auto &a : sv->active)
-        if (a.sys) mdas_destroy_system(a.sys);
+        if (a.sys && a.p.patch < 0) mdas_destroy_system(a.sys);
+    for (auto &kv : sv->patches) mdas_destroy_system(kv.second.sys);
     cudaStreamSynchronize(sv->stream);
     for (auto &kv : sv->sizes) cudaFree(kv.first);
     destroy_batch(&sv->md_batch);
@@ -1823,42 +1970,91 @@ void mdas_server_destroy(mdas_server *sv) {
     delete sv;
 }
 
+namespace {
+
+bool job_ok(const mdas_job *job) {
+    return job && job->kind >= MDAS_JOB_SWAPS && job->kind <= MDAS_JOB_MDAS && job->n >= 0 &&
+           !(job->kind == MDAS_JOB_MDAS &&
+             (job->n_pairs < 0 || job->n_pairs > MAX_PAIRS || job->n_lambda < 1 || job->md_per_lambda < 0));
+}
+
+}  // namespace
+
 mdas_status mdas_server_submit(mdas_server *sv, const mdas_system_desc *d, const mdas_job *job, int64_t *job_id) {
-    if (!sv || !d || !job || d->n_beads <= 0 || !d->pos || !d->lipid_type || !d->lipid_bead_type || !d->eps ||
-        !d->sigma || !d->charge)
-        return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit: bad argument");
-    if (job->kind < MDAS_JOB_SWAPS || job->kind > MDAS_JOB_MDAS || job->n < 0 ||
-        (job->kind == MDAS_JOB_MDAS && (job->n_pairs < 0 || job->n_pairs > MAX_PAIRS || job->n_lambda < 1 || job->md_per_lambda < 0)))
-        return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit: bad job");
+    if (!sv || !d || !job) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit: bad argument");
+    if (!job_ok(job)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit: bad job");
     PendingJob p;
+    if (copy_desc(d, p) != MDAS_OK) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit: bad argument");
+    p.footprint = arena_estimate(d);
+    if (p.footprint > sv->budget) return fail(nullptr, MDAS_ERR_OOM, "server_submit: the job alone exceeds the memory budget");
     p.id = sv->next_id++;
     p.job = *job;
     p.t_submit = sv->now();
-    p.footprint = arena_estimate(d);
-    if (p.footprint > sv->budget) return fail(nullptr, MDAS_ERR_OOM, "server_submit: the job alone exceeds the memory budget");
-    const size_t n = d->n_beads, nl = d->n_lipids, nbt = d->n_bead_types;
-    p.pos.assign(d->pos, d->pos + 3 * n);
-    if (d->vel) p.vel.assign(d->vel, d->vel + 3 * n);
-    p.eps.assign(d->eps, d->eps + nbt * nbt);
-    p.sigma.assign(d->sigma, d->sigma + nbt * nbt);
-    p.charge.assign(d->charge, d->charge + nbt);
-    if (d->lipid_first_bead) p.first.assign(d->lipid_first_bead, d->lipid_first_bead + nl);
-    p.ltype.assign(d->lipid_type, d->lipid_type + nl);
-    p.lbt.assign(d->lipid_bead_type, d->lipid_bead_type + (size_t)d->n_lipid_types * d->beads_per_lipid);
-    if (d->n_bonds) p.bonds.assign(d->bonds, d->bonds + 2 * d->n_bonds);
-    if (d->n_angles) p.angles.assign(d->angles, d->angles + 3 * d->n_angles);
-    p.d = *d;
     if (job_id) *job_id = p.id;
     sv->queue.push_back(std::move(p));
     return MDAS_OK;
 }
 
+mdas_status mdas_server_add_patch(mdas_server *sv, const mdas_system_desc *d, int64_t *patch_id) {
+    if (!sv || !d || !patch_id) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_add_patch: bad argument");
+    PendingJob p;
+    if (copy_desc(d, p) != MDAS_OK) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_add_patch: bad argument");
+    const size_t fp = arena_estimate(d);
+    if (sv->in_use + fp > sv->budget)
+        return fail(nullptr, MDAS_ERR_OOM, "server_add_patch: the patch does not fit the free memory budget");
+    ResidentPatch rp;
+    mdas_status st = server_create(sv, p, &rp.sys);
+    if (st != MDAS_OK) return st;
+    rp.footprint = fp;
+    sv->in_use += fp;
+    *patch_id = sv->next_patch++;
+    sv->patches[*patch_id] = rp;
+    return MDAS_OK;
+}
+
+mdas_status mdas_server_submit_to(mdas_server *sv, int64_t patch_id, const mdas_job *job, int64_t *job_id) {
+    if (!sv || !job) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit_to: bad argument");
+    if (!job_ok(job)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit_to: bad job");
+    auto it = sv->patches.find(patch_id);
+    if (it == sv->patches.end()) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_submit_to: no such patch");
+    PendingJob p;
+    p.id = sv->next_id++;
+    p.patch = patch_id;
+    p.job = *job;
+    p.t_submit = sv->now();
+    it->second.queued++;
+    if (job_id) *job_id = p.id;
+    sv->queue.push_back(std::move(p));
+    return MDAS_OK;
+}
+
+mdas_status mdas_server_remove_patch(mdas_server *sv, int64_t patch_id) {
+    if (!sv) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_remove_patch: bad argument");
+    auto it = sv->patches.find(patch_id);
+    if (it == sv->patches.end()) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_remove_patch: no such patch");
+    if (it->second.busy || it->second.queued > 0)
+        return fail(nullptr, MDAS_ERR_BUSY, "server_remove_patch: the patch has active or queued jobs");
+    sv->in_use -= it->second.footprint;
+    mdas_destroy_system(it->second.sys);
+    sv->patches.erase(it);
+    return MDAS_OK;
+}
+
+mdas_status mdas_server_patch_state(mdas_server *sv, int64_t patch_id, mdas_state_view *out) {
+    if (!sv || !out) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_patch_state: bad argument");
+    auto it = sv->patches.find(patch_id);
+    if (it == sv->patches.end()) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_patch_state: no such patch");
+    if (it->second.busy) return fail(nullptr, MDAS_ERR_BUSY, "server_patch_state: a job is running on the patch");
+    return mdas_get_state(it->second.sys, out);
+}
+
 mdas_status mdas_server_run(mdas_server *sv, int32_t max_rounds, int32_t *n_active, int32_t *n_queued) {
     if (!sv || max_rounds < 0) return fail(nullptr, MDAS_ERR_INVALID_ARG, "server_run: bad argument");
     for (int r = 0; r < max_rounds; ++r) {
-        // an idle server admits at once (there is no work to overlap with)
-        if (sv->active.empty()) {
-            mdas_status st = admit(sv);
+        // jobs on resident patches join at once (nothing to create); an idle
+        // server admits every kind at once (there is no work to overlap with)
+        {
+            mdas_status st = admit(sv, !sv->active.empty());
             if (st != MDAS_OK) return st;
         }
         if (sv->active.empty()) break;
@@ -1880,7 +2076,7 @@ mdas_status mdas_server_run(mdas_server *sv, int32_t max_rounds, int32_t *n_acti
         // jobs that arrived meanwhile, created while the quantum runs; new MD
         // jobs start with the next round, new swap and MDAS jobs below
         {
-            mdas_status st = admit(sv);
+            mdas_status st = admit(sv, false);
             if (st != MDAS_OK) return st;
         }
         // swap jobs: one batched evaluation per trial count

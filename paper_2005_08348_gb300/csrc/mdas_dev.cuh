@@ -298,7 +298,37 @@ struct LaunchCtx {
     unsigned int *bticket;    // device: last-block ticket over the whole batch
     bool soft;                // a system of the batch takes the soft-core alchemical path
     bool pc;                  // a system of the batch has pressure coupling (MD steps sum the virial)
+    // partitioned batches (the persistent kernel): device buffer of
+    // part_layout(n_sys, part_groups) bytes (per system its groups, map ranges and
+    // barrier state; the system of every group), or nullptr
+    void *part = nullptr;
+    int part_groups = 0;
 };
+
+// One system's share of a partitioned persistent launch: its groups
+// [g0, g0 + ng) and its ranges in the step-item, bead-block, place and
+// list-build-cell maps.
+struct SysRange {
+    int g0, ng, nl0, nln, bd0, bdn, ls0, lsn, lc0, lcn;
+};
+// Barrier state of one system's groups (monotonic arrival count, the launch's base).
+struct SysBar {
+    unsigned count, base;
+};
+// Byte offsets in the partition buffer: ranges, barrier states, group -> system.
+struct PartLayout {
+    size_t ranges, bars, gsys, bytes;
+};
+inline PartLayout part_layout(int n_sys, int groups) {
+    PartLayout l;
+    l.ranges = 0;
+    l.bars = (sizeof(SysRange) * (size_t)n_sys + 15) / 16 * 16;
+    l.gsys = l.bars + (sizeof(SysBar) * (size_t)n_sys + 15) / 16 * 16;
+    l.bytes = l.gsys + 4 * (size_t)groups;
+    return l;
+}
+// groups of 128 threads in one launch of the persistent MD kernel on this device (0 if it cannot run)
+int md_run_groups(int precision, int mode);
 
 cudaError_t setup_kernels();
 void launch_cells(const LaunchCtx &L);

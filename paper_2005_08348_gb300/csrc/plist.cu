@@ -41,6 +41,7 @@
 // between the phases instead of kernel launches.  When the step items leave
 // groups free, each step runs beside the previous step's close and exchange
 // trial, one grid barrier per step.
+#include <algorithm>
 #include <cmath>
 
 #include "mdas_phys.cuh"
@@ -901,6 +902,11 @@ __device__ bool grid_barrier(RunSync *rs, BarState &bs) {
 struct RunArgs {
     const SysDev *sys;
     int n_sys;
+    // partitioned mode: per system its groups and map ranges, its barrier
+    // state, the system of every group (nullptr: not partitioned)
+    const SysRange *ranges;
+    SysBar *sbar;
+    const int *gsys;
     const int2 *nlmap, *beadmap, *lsortmap, *lcellmap;
     int n_nl, n_bead, n_lsort, n_lcell;
     int n_steps, swap_every, trial_off;   // a trial after local step s when (s + 1 + trial_off) % swap_every == 0
@@ -955,6 +961,136 @@ __device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &
         if (build_flag(*S.c, which, s)) nl_build_item(S, bm.y, (S.c->nl_par + b) & 1, g, sm);
     }
     return grid_barrier(a.rs, bs);
+}
+
+// Barrier over the groups of one system (partitioned mode): thread 0 of
+// each group adds 1 with a release and polls, with relaxed loads, until the
+// system's count reaches base + (barriers passed) x groups, then fences once.
+// Bounded like the grid barrier: a group that gives up raises the launch's
+// abort word, and every group leaves at its next barrier once it is set.
+__device__ bool sys_barrier(SysBar *sb, unsigned base, unsigned &passes, int ng, RunSync *rs, const Grp &g, int *ok) {
+    g.sync();
+    if (g.t == 0) {
+        const unsigned target = base + (++passes) * (unsigned)ng;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&sb->count) : "memory");
+        int good = 1;
+        for (long long it = 0; (int)(ld_relaxed32(&sb->count) - target) < 0; ++it) {
+            if (it > (1ll << 23) || *(volatile int *)&rs->abort) {
+                atomicOr(&rs->abort, ERR_TIMEOUT);
+                good = 0;
+                break;
+            }
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        *ok = good && !*(volatile int *)&rs->abort;
+    }
+    g.sync();
+    return *ok != 0;
+}
+
+// Partitioned mode (a batch of several systems whose step items do not all
+// fit the groups at once): every group belongs to one system and the
+// systems' groups advance independently, each system with barriers over its
+// own groups only.  Per system the order is the sequential one (items,
+// barrier, list build after a violation, the lambda block's work term, the
+// close and the trial, barrier), so its arithmetic is that of the system
+// alone; while one system's groups wait at a barrier, other systems' groups
+// on the same SM keep working.
+template <typename Real, int LAM>
+__device__ void run_partitioned(const RunArgs &a, int gid, const Grp &g, StepSmem<Real> &ssm, BuildSmem &bsm,
+                                TrialSmem &tsm, int *ok) {
+    const int q = a.gsys[gid];
+    if (q < 0) return;
+    const SysRange R = a.ranges[q];
+    const int lg = gid - R.g0, ng = R.ng;
+    const SysDev &S = a.sys[q];
+    Counters &C = *S.c;
+    SysBar *sb = a.sbar + q;
+    unsigned base = 0, passes = 0;
+    if (g.t == 0) base = *(volatile const unsigned *)&sb->base;
+    auto bar = [&]() { return sys_barrier(sb, base, passes, ng, a.rs, g, ok); };
+    // the list build of this system (three barriers); position buffer par
+    auto build = [&](int par) {
+        for (int it = lg; it < R.bdn; it += ng) nl_count_item(S, a.beadmap[R.bd0 + it].y, g);
+        if (!bar()) return false;
+        for (int it = lg; it < R.lsn; it += ng) nl_place_item(S, a.lsortmap[R.ls0 + it].y, par, g, bsm);
+        if (!bar()) return false;
+        for (int it = lg; it < R.lcn; it += ng) nl_build_item(S, a.lcellmap[R.lc0 + it].y, par, g, bsm);
+        return bar();
+    };
+    bool tab = true;                           // the pair tables must be (re)loaded into shared memory
+    if (*(volatile const int *)&C.nl_stale) {  // lists made stale outside the kernel
+        if (!build(C.nl_par & 1)) return;
+        tab = true;
+        if (lg == 0 && g.t == 0) C.nl_builds++;
+    }
+    constexpr bool PC = LAM == 3;
+    for (int s = 0; s < a.n_steps; ++s) {
+        for (int it = lg; it < R.nln; it += ng) {
+            nl_step_item<Real, LAM>(S, a.nlmap[R.nl0 + it].y, (C.nl_par + s) & 1, &C.nl_violp[s % 3], g, ssm, tab);
+            tab = false;
+        }
+        // the flag of step s + 1 (last read at step s - 2, before the previous barrier)
+        if (lg == 0 && g.t == 0) {
+            C.nl_violp[(s + 1) % 3] = 0;
+            if (s == 0) C.nl_stale = 0;
+        }
+        if (!bar()) return;
+        if (*(volatile const int *)&C.nl_violp[s % 3]) {
+            if (!build((C.nl_par + s + 1) & 1)) return;
+            tab = true;
+            if (lg == 0 && g.t == 0) C.nl_builds++;
+        }
+        if ((LAM == 1 || LAM == 2) && a.lam_M > 0 && (a.lam_off + s + 1) % a.lam_M == 0) {
+            // the end of a lambda block (Eq. 2): each lipid's work term at the
+            // block's last coordinates, then w += dlam * their ordered sum
+            const int blk = (a.lam_off + s + 1) / a.lam_M;
+            const double l0 = (double)(blk - 1) * a.dlam, l1 = (double)blk * a.dlam;
+            for (int x = lg; x < 2 * C.n_pairs; x += ng) {
+                const double wp = mdas_work_part(S, x, (C.nl_par + s + 1) & 1, g, tsm.sh, l0, l1);
+                if (g.t == 0) C.w_part[x] = wp;
+                tab = true;
+            }
+            if (!bar()) return;
+            if (lg == 0 && g.t == 0) {
+                double sum = 0.0;
+                for (int x = 0; x < 2 * C.n_pairs; ++x) sum += C.w_part[x];
+                C.w += S.p->sc_delta > 0.0 ? sum : a.dlam * sum;
+                C.lambda = (double)blk * a.dlam;
+            }
+        }
+        // the close on the system's last group, the trial parts from its first
+        if (lg == ng - 1 && g.t < 32) nl_step_close<Real, PC>(S, g.t, (C.nl_par + s) & 1);
+        if (a.swap_every > 0 && (s + 1 + a.trial_off) % a.swap_every == 0) {
+            for (int p = lg; p < TRIAL_PARTS; p += ng) {
+                trial_nl_part(S, p, (C.nl_par + s + 1) & 1, g, tsm, false);
+                tab = true;
+            }
+        }
+        if (!bar()) return;
+    }
+    // every group of the system is past its last barrier: the next launch
+    // counts from here
+    if (lg == 0 && g.t == 0) {
+        sb->base = base + passes * (unsigned)ng;
+        C.nl_par = (C.nl_par + a.n_steps) & 1;
+        C.nl_violp[0] = C.nl_violp[1] = C.nl_violp[2] = 0;
+        if (a.n_steps == 0) C.nl_stale = 0;
+    }
+}
+
+// The partitioned mode as a kernel of its own (same launch shape as
+// k_md_run, so either runs resident on the same device).
+template <typename Real, int LAM>
+__global__ void __launch_bounds__(RUN_THREADS, 1) k_md_part(RunArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ int gok[RUN_GROUPS];
+    const int group = threadIdx.x / GRP;
+    const Grp g{(int)threadIdx.x % GRP, 1 + group};
+    const int gid = group * gridDim.x + blockIdx.x;
+    unsigned char *gsm = dsm + group * group_smem<Real>();
+    run_partitioned<Real, LAM>(a, gid, g, *reinterpret_cast<StepSmem<Real> *>(gsm), *reinterpret_cast<BuildSmem *>(gsm),
+                               *reinterpret_cast<TrialSmem *>(gsm), &gok[group]);
 }
 
 // n_steps MD steps (with a trial after every swap_every-th) of every system,
@@ -1133,6 +1269,14 @@ static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, i
                               int lam_off, double dlam, RunSync *rs, int n_blocks) {
     RunArgs a;
     a.sys = L.sys; a.n_sys = L.n_sys;
+    a.ranges = nullptr; a.sbar = nullptr; a.gsys = nullptr;
+    if (L.part) {
+        const PartLayout pl = part_layout(L.n_sys, L.part_groups);
+        char *base = (char *)L.part;
+        a.ranges = (const SysRange *)(base + pl.ranges);
+        a.sbar = (SysBar *)(base + pl.bars);
+        a.gsys = (const int *)(base + pl.gsys);
+    }
     a.nlmap = L.nlbeads->d; a.n_nl = L.nlbeads->n;
     a.beadmap = L.beads->d; a.n_bead = L.beads->n;
     a.lsortmap = L.lsort->d; a.n_lsort = L.lsort->n;
@@ -1140,16 +1284,23 @@ static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, i
     a.n_steps = n_steps; a.swap_every = swap_every; a.trial_off = trial_off; a.rs = rs;
     a.lam_M = lam_M; a.lam_off = lam_off; a.dlam = dlam;
     void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((const void *)k_md_run<Real, LAM>, dim3(n_blocks), dim3(RUN_THREADS), args,
-                                       RUN_GROUPS * group_smem<Real>(), L.stream);
+    const void *fn = a.gsys ? (const void *)k_md_part<Real, LAM> : (const void *)k_md_run<Real, LAM>;
+    return cudaLaunchCooperativeKernel(fn, dim3(n_blocks), dim3(RUN_THREADS), args, RUN_GROUPS * group_smem<Real>(),
+                                       L.stream);
 }
 
 template <typename Real, int LAM>
 static cudaError_t run_setup(int *blocks_per_sm) {
     const size_t smem = RUN_GROUPS * group_smem<Real>();
     cudaError_t e = cudaFuncSetAttribute(k_md_run<Real, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_md_part<Real, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_md_run<Real, LAM>, RUN_THREADS, smem);
+    int per_part = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_md_run<Real, LAM>, RUN_THREADS, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_part, k_md_part<Real, LAM>, RUN_THREADS, smem);
+    if (e == cudaSuccess) *blocks_per_sm = std::min(*blocks_per_sm, per_part);
+    return e;
 }
 
 // Blocks of the persistent kernel on this device: one per SM when a block
@@ -1172,6 +1323,8 @@ int md_run_blocks(int precision, int mode) {
     cudaGetLastError();
     return c;
 }
+
+int md_run_groups(int precision, int mode) { return md_run_blocks(precision, mode) * RUN_GROUPS; }
 
 cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
                           int lam_off, double dlam, void *sync) {

@@ -110,7 +110,8 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_server_run", "mdas_server_results", "mdas_server_clock", "mdas_system_footprint",
            "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core",
            "mdas_wait_timeout_probe", "mdas_box", "mdas_alchemical_move_trace", "mdas_interleaflet_move",
-           "mdas_device_ptrs"]
+           "mdas_device_ptrs", "mdas_server_add_patch", "mdas_server_submit_to", "mdas_server_patch_state",
+           "mdas_server_remove_patch"]
 
 
 def library_path() -> str:
@@ -507,6 +508,32 @@ class Server:
         jid = C.c_int64()
         _check(lib().mdas_server_submit(self._ptr, C.byref(d), C.byref(j), C.byref(jid)))
         return jid.value
+
+    def add_patch(self, m, precision=MDAS_FP32):
+        """A device-resident patch (mdas_server_add_patch); returns its id."""
+        d, keep = make_desc(m, precision)
+        pid = C.c_int64()
+        _check(lib().mdas_server_add_patch(self._ptr, C.byref(d), C.byref(pid)))
+        return pid.value
+
+    def submit_to(self, patch_id, kind, n=0, n_pairs=8, n_lambda=10, md_per_lambda=5):
+        """Queue a job on a resident patch (mdas_server_submit_to)."""
+        j = Job(int(kind), int(n), int(n_pairs), int(n_lambda), int(md_per_lambda))
+        jid = C.c_int64()
+        _check(lib().mdas_server_submit_to(self._ptr, C.c_int64(patch_id), C.byref(j), C.byref(jid)))
+        return jid.value
+
+    def patch_state(self, patch_id, n_beads, n_lipids):
+        """Positions (fixed point), velocities and lipid types of an idle resident patch."""
+        pu = np.empty((n_beads, 3), np.uint32)
+        vel = np.empty((n_beads, 3), np.float64)
+        lt = np.empty(max(n_lipids, 1), np.int32)
+        v = StateView(_p(pu), None, _p(vel), _p(lt))
+        _check(lib().mdas_server_patch_state(self._ptr, C.c_int64(patch_id), C.byref(v)))
+        return dict(pos_u=pu, vel=vel, ltype=lt[:n_lipids].copy(), step=v.step, trial=v.trial, move=v.move)
+
+    def remove_patch(self, patch_id):
+        _check(lib().mdas_server_remove_patch(self._ptr, C.c_int64(patch_id)))
 
     def run(self, rounds=1):
         a, q = C.c_int32(), C.c_int32()
