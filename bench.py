@@ -538,13 +538,16 @@ def swap_benchmark(stream, n_batch=1024, n_plain=300):
 
 
 def serving_benchmark(stream, n_jobs=500, n_patches=48, seed=1005):
-    """Served sampling: each job's patch is drawn uniformly from a pool of 48
-    seeded patches whose sizes are log-uniform over 128-16384 lipids (2-3
-    types); job mix 60% 256 swap trials / 30% 100 MD steps / 10% one MDAS move
-    (8 pairs = 16 lipids, 10 lambda steps of 5 MD steps); Poisson arrivals at
-    0.25x, 0.5x and 0.9x of the saturation throughput measured first (all
-    jobs submitted at once).  Beside it, the plain path: the same jobs one at
-    a time through the one-system calls (create, run, destroy), no batching."""
+    """Served sampling on device-resident patches: 48 seeded patches whose
+    sizes are log-uniform over 128-16384 lipids (2-3 types) are added to the
+    server once; each job draws its patch uniformly (so patch sizes are
+    log-uniform per job) and its kind from the mix 60% 256 swap trials / 30%
+    100 MD steps / 10% one MDAS move (8 pairs = 16 lipids, 10 lambda steps of
+    5 MD steps); a patch's jobs run in order on its state.  Poisson arrivals
+    at 0.25x, 0.5x and 0.9x of the saturation throughput measured first (all
+    jobs submitted at once).  Beside it, the plain path: the same jobs on the
+    same device-resident systems, one job at a time through the one-system
+    calls (no batching)."""
     import numpy as np
     from paper_2005_08348_gb300 import mdas, synth
     rng = np.random.default_rng(seed)
@@ -557,50 +560,53 @@ def serving_benchmark(stream, n_jobs=500, n_patches=48, seed=1005):
         for _ in range(n_jobs):
             x = r.uniform()
             kind, n = (mdas.JOB_SWAPS, 256) if x < 0.6 else ((mdas.JOB_MD, 100) if x < 0.9 else (mdas.JOB_MDAS, 0))
-            out.append((pool[int(r.integers(0, n_patches))], kind, n))
+            out.append((int(r.integers(0, n_patches)), kind, n))
         return out
 
+    sv = mdas.Server(64 << 30, max_active=64, md_quantum=25, stream=stream.cuda_stream)
+    pids = [sv.add_patch(p) for p in pool]
+
     def serve(jobs, arrivals):
-        sv = mdas.Server(64 << 30, max_active=16, md_quantum=25, stream=stream.cuda_stream)
         t0 = sv.clock()
         k = 0
         done = []
         while len(done) < len(jobs):
             now = sv.clock() - t0
             while k < len(jobs) and arrivals[k] <= now:
-                p, kind, n = jobs[k]
-                sv.submit(p, kind, n=n, n_pairs=8, n_lambda=10, md_per_lambda=5)
+                q, kind, n = jobs[k]
+                sv.submit_to(pids[q], kind, n=n, n_pairs=8, n_lambda=10, md_per_lambda=5)
                 k += 1
-            a, q = sv.run(1)
+            a, qd = sv.run(1)
             done += sv.results()
-            if a == 0 and q == 0 and k < len(jobs):
+            if a == 0 and qd == 0 and k < len(jobs):
                 time.sleep(max(0.0, min(0.002, arrivals[k] - (sv.clock() - t0))))
         span = max(r["t_done"] for r in done) - t0
         lat = np.array([r["t_done"] - r["t_submit"] for r in done])
-        sv.close()
         return span, lat
+
+    plain_sys = [mdas.System(p, stream=stream.cuda_stream) for p in pool]
 
     def plain(jobs):
         t0 = time.perf_counter()
-        for p, kind, n in jobs:
-            s = mdas.System(p, stream=stream.cuda_stream)
+        for q, kind, n in jobs:
+            s = plain_sys[q]
             if kind == mdas.JOB_MD:
                 s.md_steps(n)
             elif kind == mdas.JOB_SWAPS:
                 s.swap_trials(n, log=False)
             else:
                 s.alchemical_move(8, 10, 5)
-            s.close()
         return time.perf_counter() - t0
 
     jobs = draw_jobs(np.random.default_rng(seed + 1))
-    serve(jobs[:16], [0.0] * 16)                        # warm-up
+    serve(jobs[:32], [0.0] * 32)                        # warm-up
+    plain(jobs[:32])
     t_plain = plain(jobs)
     span, lat = serve(jobs, [0.0] * n_jobs)
     sat = n_jobs / span
-    lipids = np.array([p.n_lipids for p, _, _ in jobs])
-    res = {"workload": f"{n_jobs} jobs per rate; patches drawn per job from {n_patches} seeded patches of "
-                       f"{int(sizes.min())}-{int(sizes.max())} lipids (log-uniform sizes)",
+    lipids = np.array([pool[q].n_lipids for q, _, _ in jobs])
+    res = {"workload": f"{n_jobs} jobs per rate on {n_patches} device-resident patches of "
+                       f"{int(sizes.min())}-{int(sizes.max())} lipids (log-uniform sizes), patch drawn per job",
            "job_lipids_median": int(np.median(lipids)), "job_lipids_max": int(lipids.max()),
            "saturation_jobs_per_s": sat, "plain_one_at_a_time_jobs_per_s": n_jobs / t_plain,
            "served_over_plain": sat * t_plain / n_jobs, "rates": []}
@@ -611,6 +617,9 @@ def serving_benchmark(stream, n_jobs=500, n_patches=48, seed=1005):
         res["rates"].append({"load": frac, "arrival_jobs_per_s": frac * sat, "throughput_jobs_per_s": n_jobs / span,
                              "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                              "max_ms": float(lat.max() * 1e3)})
+    for s in plain_sys:
+        s.close()
+    sv.close()
     return res
 
 

@@ -72,6 +72,7 @@ __global__ void k_swap_propose(const SysDev *__restrict__ sys, int n) {
     S.tprop[t] = make_int4(a, b, -1, -1);
     S.tu[t] = unit53(w.z, w.w);
     S.tstate[t] = 0;
+    if (t == 0) S.c->pending = n;              // this system has trials to resolve
 }
 
 // bounding box of lipid l in fixed-point units: centre and half widths
@@ -280,9 +281,14 @@ __global__ void k_swap_resolve(const SysDev *__restrict__ sys, int n) {
         C.accepted += r.accepted;
         S.tstate[t] = 1;
     }
+    // the trial counter advances once, in the round that resolves this
+    // system's last trial (in a batch, later rounds for other systems'
+    // trials find nothing pending here)
+    if (C.pending != 0) {
+        C.rounds++;
+        if (pending == 0) C.trial += (unsigned long long)n;
+    }
     C.pending = pending;
-    C.rounds++;
-    if (pending == 0) C.trial += (unsigned long long)n;
 }
 
 void launch_swap_resolve(const LaunchCtx &L, int n) {

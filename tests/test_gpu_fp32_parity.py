@@ -204,6 +204,8 @@ def test_batch_of_replicas_128_to_2048_lipids():
         s = mdas.System(m)
         s.md_steps(12)
         s.swap_trials(24, log=False)
+        s.md_steps(7)
+        s.swap_trials(16, log=False)
         solo.append(s.get_state())
         s.close()
     sy = [mdas.System(m) for m in ms]
@@ -211,11 +213,14 @@ def test_batch_of_replicas_128_to_2048_lipids():
     x = 2                                         # the 512-lipid replica
     post_md = sy[x].get_state()
     mdas.batch_run(sy, 0, 24)
+    mid = sy[x].get_state()
+    mdas.batch_run(sy, 7, 16)                     # a second round: the trial counters must have kept step
     for s, st in zip(sy, solo):
         g = s.get_state()
         assert np.array_equal(g["pos_u"], st["pos_u"])
         assert np.array_equal(g["vel"], st["vel"])
         assert np.array_equal(g["ltype"], st["ltype"])
+        assert (g["step"], g["trial"]) == (st["step"], st["trial"])
     o = oracle.Oracle(ms[x])
     lt_o, rec_o = o.swap_trials(post_md["pos_u"], post_md["ltype"], post_md["trial"], 24)
     rec = sy[x].trial_log(post_md["trial"], 24)
@@ -230,4 +235,4 @@ def test_batch_of_replicas_128_to_2048_lipids():
         else:
             assert bool(g["accepted"]) == r["accepted"]
     assert ties == 0
-    assert np.array_equal(sy[x].get_state()["ltype"], lt_o)
+    assert np.array_equal(mid["ltype"], lt_o)

@@ -99,3 +99,61 @@ def test_mdas_jobs_run_as_one_batched_move():
                     stagger=False)[0]
         assert r["state_hash"] == alone["state_hash"]
         assert (r["w"], r["move_accepted"], r["md_steps"]) == (alone["w"], alone["move_accepted"], alone["md_steps"])
+
+
+def test_resident_patches_carry_state_between_jobs():
+    """Resident patches (mdas_server_add_patch / submit_to): each patch's jobs
+    run one after another in submission order on its device-resident state,
+    patches run together; every patch ends in the state of the same job
+    sequence run alone through the one-system calls."""
+    ps = patches()[:3]
+    seq = [(mdas.JOB_MD, 30), (mdas.JOB_SWAPS, 40), (mdas.JOB_MD, 15), (mdas.JOB_MDAS, 0)]
+    sv = mdas.Server(4 * GB, max_active=8, md_quantum=10)
+    pids = [sv.add_patch(p) for p in ps]
+    for kind, n in seq:                                    # interleaved over the patches
+        for pid in pids:
+            sv.submit_to(pid, kind, n=n, n_pairs=2, n_lambda=3, md_per_lambda=2)
+    done = []
+    for _ in range(1000):
+        a, q = sv.run(1)
+        done += sv.results()
+        if a == 0 and q == 0:
+            break
+    assert len(done) == len(seq) * len(ps)
+    assert sorted(r["md_steps"] for r in done if r["kind"] == mdas.JOB_MD) == sorted([30, 15] * 3)
+    for p, pid in zip(ps, pids):
+        s = mdas.System(p)
+        for kind, n in seq:
+            if kind == mdas.JOB_MD:
+                s.md_steps(n)
+            elif kind == mdas.JOB_SWAPS:
+                s.swap_trials(n, log=False)
+            else:
+                s.alchemical_move(2, 3, 2)
+        ref = s.get_state()
+        got = sv.patch_state(pid, p.n_beads, p.n_lipids)
+        assert np.array_equal(got["pos_u"], ref["pos_u"])
+        assert np.array_equal(got["vel"], ref["vel"])
+        assert np.array_equal(got["ltype"], ref["ltype"])
+        assert (got["trial"], got["move"]) == (ref["trial"], ref["move"])
+
+
+def test_resident_patch_admission_and_removal():
+    ps = patches()[:2]
+    fp = mdas.footprint(ps[0])
+    sv = mdas.Server(fp + fp // 2, max_active=4)
+    pid = sv.add_patch(ps[0])
+    with pytest.raises(mdas.MdasError) as e:             # no room left for a second patch
+        sv.add_patch(ps[1])
+    assert e.value.status == 2
+    sv.submit_to(pid, mdas.JOB_MD, n=5)
+    with pytest.raises(mdas.MdasError) as e:             # a queued job holds the patch
+        sv.remove_patch(pid)
+    assert e.value.status == 6
+    while sv.run(1) != (0, 0):
+        pass
+    sv.remove_patch(pid)
+    pid2 = sv.add_patch(ps[1])                            # its memory is back
+    with pytest.raises(mdas.MdasError):
+        sv.submit_to(pid, mdas.JOB_MD, n=5)               # removed
+    sv.remove_patch(pid2)
