@@ -338,6 +338,30 @@ mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_
                                 int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
                                 double *us_per_step, double *best_skin);
 
+/* Layout of batches in the persistent MD kernel.  enable = 1 (the default):
+ * when a batch's step items do not all fit the kernel's groups at once, each
+ * system gets a share of the groups in proportion to its step items and
+ * barriers over its own groups only, so the systems advance independently
+ * (one system's barriers, list builds and exchange trials do not hold up the
+ * others); enable = 0: all systems advance in lockstep with kernel-wide
+ * barriers.  A batch is partitioned only when all its systems allow it.  The
+ * results are the same bits either way.  Errors: MDAS_ERR_INVALID_ARG for a
+ * NULL system. */
+mdas_status mdas_set_partitioned(mdas_system *s, int32_t enable);
+
+/* Autotuning of a batch's work shape: for each of the n_skins candidate
+ * list skins (nm, each > 0) and each of the two layouts of
+ * mdas_set_partitioned (0: lockstep, 1: partitioned), the systems described
+ * by descs[] are created, advanced by one untimed round and timed over
+ * `rounds` rounds of mdas_batch_run(md_steps, swap_trials) with CUDA events
+ * on their stream, then destroyed.  us_per_step (host, 2 n_skins entries,
+ * candidate 2 c + layout) receives the device time per MD step; *best_skin
+ * and *best_partitioned the fastest candidate.  Neither the descriptors nor
+ * any existing system change.  Errors as mdas_tune_list_skin. */
+mdas_status mdas_tune_batch(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
+                            int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
+                            double *us_per_step, double *best_skin, int32_t *best_partitioned);
+
 /* The path of the alchemical moves (Sec. 2).  delta = 0 (the default): the
  * linear path U(lambda) = (1 - lambda) U_A + lambda U_B.  delta > 0 (nm^2):
  * the soft-core path of Eq. 4 for the Lennard-Jones part of every pair with

@@ -110,6 +110,7 @@ struct mdas_system {
     bool unstable = false;
     bool cells_valid = false;   // the cell list matches the current positions and types
     bool timing = false;
+    bool partition = true;      // batches may give this system its own share of the persistent kernel's groups
     double pair_ms = 0.0;
     long long pair_launches = 0;
     long long kernel_launches = 0;   // kernel launches (graph kernel nodes included) that advanced this system
@@ -422,6 +423,8 @@ mdas_status make_partition(mdas_system *s, Batch &b, int groups, bool *use) {
         total += items[q];
     }
     if (n < 2 || n > groups / 2 || total + (long long)(TRIAL_PARTS + 1) * n <= groups) return MDAS_OK;
+    for (auto *x : b.sys)
+        if (!x->partition) return MDAS_OK;
     *use = true;
     if (b.part_groups == groups) return MDAS_OK;
     std::vector<int> ng(n);
@@ -1511,53 +1514,104 @@ mdas_status mdas_head_rdf(mdas_system *s, int32_t lipid_type, int32_t head_k, do
     return MDAS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device time per MD step of a batch made from descs with the given list skin
+// and layout (partitioned or in lockstep): one untimed round, then `rounds`
+// rounds of mdas_batch_run timed with CUDA events on the batch's stream; the
+// systems are destroyed afterwards.
+mdas_status time_batch(const mdas_system_desc *const *descs, int n_systems, double skin, int partitioned, int md_steps,
+                       int swap_trials, int rounds, double *us) {
+    std::vector<mdas_system_desc> dv(n_systems);
+    std::vector<mdas_system *> sv;
+    for (int i = 0; i < n_systems; ++i) {
+        dv[i] = *descs[i];
+        dv[i].list_skin = skin;
+    }
+    mdas_status st = MDAS_OK;
+    for (int i = 0; i < n_systems && st == MDAS_OK; ++i) {
+        mdas_system *x = nullptr;
+        st = mdas_create_system(&dv[i], &x);
+        if (st == MDAS_OK) {
+            x->partition = partitioned != 0;
+            sv.push_back(x);
+        }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    if (st == MDAS_OK) st = mdas_batch_run(sv.data(), n_systems, md_steps, swap_trials);   // untimed round
+    if (st == MDAS_OK) {
+        cudaStream_t q = sv[0]->stream;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, q);
+        for (int r = 0; r < rounds && e == cudaSuccess && st == MDAS_OK; ++r)
+            st = mdas_batch_run(sv.data(), n_systems, md_steps, swap_trials);
+        if (e == cudaSuccess && st == MDAS_OK) e = cudaEventRecord(e1, q);
+        if (e == cudaSuccess && st == MDAS_OK) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess && st == MDAS_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess && st == MDAS_OK) st = cuda_fail(nullptr, e, "tune: timing");
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (auto *x : sv) mdas_destroy_system(x);
+    if (st == MDAS_OK) *us = 1e3 * (double)ms / ((double)rounds * md_steps);
+    return st;
+}
+
+mdas_status tune_args(const char *who, const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
+                      int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds) {
+    if (!descs || n_systems <= 0 || !skins || n_skins <= 0 || md_steps <= 0 || swap_trials < 0 || rounds <= 0)
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, std::string(who) + ": bad argument");
+    for (int i = 0; i < n_systems; ++i)
+        if (!descs[i]) return fail(nullptr, MDAS_ERR_INVALID_ARG, std::string(who) + ": NULL descriptor");
+    for (int c = 0; c < n_skins; ++c)
+        if (!(skins[c] > 0.0)) return fail(nullptr, MDAS_ERR_INVALID_ARG, std::string(who) + ": a candidate skin is <= 0");
+    return MDAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
                                 int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
                                 double *us_per_step, double *best_skin) {
-    if (!descs || n_systems <= 0 || !skins || n_skins <= 0 || md_steps <= 0 || swap_trials < 0 || rounds <= 0 ||
-        !us_per_step || !best_skin)
-        return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: bad argument");
-    for (int i = 0; i < n_systems; ++i)
-        if (!descs[i]) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: NULL descriptor");
-    for (int c = 0; c < n_skins; ++c)
-        if (!(skins[c] > 0.0)) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: a candidate skin is <= 0");
+    mdas_status st = tune_args("tune_list_skin", descs, n_systems, skins, n_skins, md_steps, swap_trials, rounds);
+    if (st != MDAS_OK) return st;
+    if (!us_per_step || !best_skin) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: bad argument");
     int best = -1;
     for (int c = 0; c < n_skins; ++c) {
-        std::vector<mdas_system_desc> dv(n_systems);
-        std::vector<mdas_system *> sv;
-        for (int i = 0; i < n_systems; ++i) {
-            dv[i] = *descs[i];
-            dv[i].list_skin = skins[c];
-        }
-        mdas_status st = MDAS_OK;
-        for (int i = 0; i < n_systems && st == MDAS_OK; ++i) {
-            mdas_system *x = nullptr;
-            st = mdas_create_system(&dv[i], &x);
-            if (st == MDAS_OK) sv.push_back(x);
-        }
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        float ms = 0.f;
-        if (st == MDAS_OK) st = mdas_batch_run(sv.data(), n_systems, md_steps, swap_trials);   // untimed round
-        if (st == MDAS_OK) {
-            cudaStream_t q = sv[0]->stream;
-            cudaError_t e = cudaEventCreate(&e0);
-            if (e == cudaSuccess) e = cudaEventCreate(&e1);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, q);
-            for (int r = 0; r < rounds && e == cudaSuccess && st == MDAS_OK; ++r)
-                st = mdas_batch_run(sv.data(), n_systems, md_steps, swap_trials);
-            if (e == cudaSuccess && st == MDAS_OK) e = cudaEventRecord(e1, q);
-            if (e == cudaSuccess && st == MDAS_OK) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess && st == MDAS_OK) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess && st == MDAS_OK) st = cuda_fail(nullptr, e, "tune_list_skin");
-        }
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
-        for (auto *x : sv) mdas_destroy_system(x);
+        st = time_batch(descs, n_systems, skins[c], 1, md_steps, swap_trials, rounds, &us_per_step[c]);
         if (st != MDAS_OK) return st;
-        us_per_step[c] = 1e3 * (double)ms / ((double)rounds * md_steps);
         if (best < 0 || us_per_step[c] < us_per_step[best]) best = c;
     }
     *best_skin = skins[best];
+    return MDAS_OK;
+}
+
+mdas_status mdas_tune_batch(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
+                            int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
+                            double *us_per_step, double *best_skin, int32_t *best_partitioned) {
+    mdas_status st = tune_args("tune_batch", descs, n_systems, skins, n_skins, md_steps, swap_trials, rounds);
+    if (st != MDAS_OK) return st;
+    if (!us_per_step || !best_skin || !best_partitioned) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_batch: bad argument");
+    int best = -1;
+    for (int c = 0; c < 2 * n_skins; ++c) {
+        st = time_batch(descs, n_systems, skins[c / 2], c % 2, md_steps, swap_trials, rounds, &us_per_step[c]);
+        if (st != MDAS_OK) return st;
+        if (best < 0 || us_per_step[c] < us_per_step[best]) best = c;
+    }
+    *best_skin = skins[best / 2];
+    *best_partitioned = best % 2;
+    return MDAS_OK;
+}
+
+mdas_status mdas_set_partitioned(mdas_system *s, int32_t enable) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_partitioned: NULL system");
+    s->partition = enable != 0;
     return MDAS_OK;
 }
 
