@@ -349,18 +349,32 @@ mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_
  * NULL system. */
 mdas_status mdas_set_partitioned(mdas_system *s, int32_t enable);
 
+/* Waves of a batch's MD: with max_beads > 0, mdas_batch_run advances the
+ * MD of a batch whose first system has this setting in waves of
+ * consecutive systems holding at most max_beads beads together (a single
+ * larger system forms a wave of its own), each wave one persistent launch
+ * per segment, so that a wave's working set stays closer to what the L2
+ * cache holds; the exchange trials still run over the whole batch.  0 (the
+ * default): the whole batch at once.  The results are the same bits.
+ * Errors: MDAS_ERR_INVALID_ARG for a NULL system or max_beads < 0. */
+mdas_status mdas_set_batch_wave(mdas_system *s, int64_t max_beads);
+
 /* Autotuning of a batch's work shape: for each of the n_skins candidate
- * list skins (nm, each > 0) and each of the two layouts of
- * mdas_set_partitioned (0: lockstep, 1: partitioned), the systems described
- * by descs[] are created, advanced by one untimed round and timed over
- * `rounds` rounds of mdas_batch_run(md_steps, swap_trials) with CUDA events
- * on their stream, then destroyed.  us_per_step (host, 2 n_skins entries,
- * candidate 2 c + layout) receives the device time per MD step; *best_skin
- * and *best_partitioned the fastest candidate.  Neither the descriptors nor
- * any existing system change.  Errors as mdas_tune_list_skin. */
+ * list skins (nm, each > 0), each of the two layouts of mdas_set_partitioned
+ * (0: lockstep, 1: partitioned) and each of the n_waves wave sizes of
+ * mdas_set_batch_wave (beads, >= 0), the systems described by descs[] are
+ * created, advanced by one untimed round and timed over `rounds` rounds of
+ * mdas_batch_run(md_steps, swap_trials) with CUDA events on their stream,
+ * then destroyed.  us_per_step (host, n_skins * 2 * n_waves entries,
+ * candidate (skin * 2 + layout) * n_waves + wave) receives the device time
+ * per MD step; *best_skin, *best_partitioned and *best_wave the fastest
+ * candidate.  Neither the descriptors nor any existing system change.
+ * Errors as mdas_tune_list_skin, and for a NULL waves array, n_waves <= 0
+ * or a wave size < 0. */
 mdas_status mdas_tune_batch(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
-                            int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
-                            double *us_per_step, double *best_skin, int32_t *best_partitioned);
+                            int32_t n_skins, const int64_t *waves, int32_t n_waves, int32_t md_steps,
+                            int32_t swap_trials, int32_t rounds, double *us_per_step, double *best_skin,
+                            int32_t *best_partitioned, int64_t *best_wave);
 
 /* The path of the alchemical moves (Sec. 2).  delta = 0 (the default): the
  * linear path U(lambda) = (1 - lambda) U_A + lambda U_B.  delta > 0 (nm^2):

@@ -111,6 +111,7 @@ struct mdas_system {
     bool cells_valid = false;   // the cell list matches the current positions and types
     bool timing = false;
     bool partition = true;      // batches may give this system its own share of the persistent kernel's groups
+    long long wave_beads = 0;   // a batch's MD runs in waves of systems of at most this many beads (0: all at once)
     double pair_ms = 0.0;
     long long pair_launches = 0;
     long long kernel_launches = 0;   // kernel launches (graph kernel nodes included) that advanced this system
@@ -1471,16 +1472,41 @@ mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32
         if (x->unstable) return fail(x, MDAS_ERR_UNSTABLE, "batch_run: a system is unstable");
     }
     mdas_system *s = v[0];
-    auto it = g_batches.find(v);
-    if (it == g_batches.end()) {
-        std::unique_ptr<Batch> b;
-        mdas_status st = make_batch(v, b);
-        if (st != MDAS_OK) return st;
-        it = g_batches.emplace(v, std::move(b)).first;
-    }
-    Batch &b = *it->second;
-    mdas_status st = run_md(s, b, md_steps, 0);
+    auto batch_of = [&](const std::vector<mdas_system *> &w, Batch **out) {
+        auto it = g_batches.find(w);
+        if (it == g_batches.end()) {
+            std::unique_ptr<Batch> b;
+            mdas_status st = make_batch(w, b);
+            if (st != MDAS_OK) return st;
+            it = g_batches.emplace(w, std::move(b)).first;
+        }
+        *out = it->second.get();
+        return MDAS_OK;
+    };
+    Batch *bp = nullptr;
+    mdas_status st = batch_of(v, &bp);
     if (st != MDAS_OK) return st;
+    Batch &b = *bp;
+    long long total = 0;
+    for (auto *x : v) total += x->n;
+    const long long wave = s->wave_beads;
+    if (wave > 0 && total > wave && md_steps > 0) {
+        // MD in waves of consecutive systems (each wave's working set closer
+        // to what the L2 cache holds); every system's arithmetic is its own,
+        // so the bits are those of one batch
+        for (size_t k = 0; k < v.size();) {
+            std::vector<mdas_system *> w;
+            long long beads = 0;
+            while (k < v.size() && (w.empty() || beads + v[k]->n <= wave)) { beads += v[k]->n; w.push_back(v[k++]); }
+            Batch *wb = nullptr;
+            st = batch_of(w, &wb);
+            if (st == MDAS_OK) st = run_md(w[0], *wb, md_steps, 0);
+            if (st != MDAS_OK) return st;
+        }
+    } else {
+        st = run_md(s, b, md_steps, 0);
+        if (st != MDAS_OK) return st;
+    }
     if (swap_trials > 0) {
         for (auto *x : v)
             if (x->n_lip == 0) return fail(x, MDAS_ERR_INVALID_ARG, "batch_run: a system has no lipids");
@@ -1522,8 +1548,8 @@ namespace {
 // and layout (partitioned or in lockstep): one untimed round, then `rounds`
 // rounds of mdas_batch_run timed with CUDA events on the batch's stream; the
 // systems are destroyed afterwards.
-mdas_status time_batch(const mdas_system_desc *const *descs, int n_systems, double skin, int partitioned, int md_steps,
-                       int swap_trials, int rounds, double *us) {
+mdas_status time_batch(const mdas_system_desc *const *descs, int n_systems, double skin, int partitioned,
+                       long long wave, int md_steps, int swap_trials, int rounds, double *us) {
     std::vector<mdas_system_desc> dv(n_systems);
     std::vector<mdas_system *> sv;
     for (int i = 0; i < n_systems; ++i) {
@@ -1536,6 +1562,7 @@ mdas_status time_batch(const mdas_system_desc *const *descs, int n_systems, doub
         st = mdas_create_system(&dv[i], &x);
         if (st == MDAS_OK) {
             x->partition = partitioned != 0;
+            x->wave_beads = wave;
             sv.push_back(x);
         }
     }
@@ -1584,7 +1611,7 @@ mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_
     if (!us_per_step || !best_skin) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: bad argument");
     int best = -1;
     for (int c = 0; c < n_skins; ++c) {
-        st = time_batch(descs, n_systems, skins[c], 1, md_steps, swap_trials, rounds, &us_per_step[c]);
+        st = time_batch(descs, n_systems, skins[c], 1, 0, md_steps, swap_trials, rounds, &us_per_step[c]);
         if (st != MDAS_OK) return st;
         if (best < 0 || us_per_step[c] < us_per_step[best]) best = c;
     }
@@ -1593,19 +1620,33 @@ mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_
 }
 
 mdas_status mdas_tune_batch(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
-                            int32_t n_skins, int32_t md_steps, int32_t swap_trials, int32_t rounds,
-                            double *us_per_step, double *best_skin, int32_t *best_partitioned) {
+                            int32_t n_skins, const int64_t *waves, int32_t n_waves, int32_t md_steps,
+                            int32_t swap_trials, int32_t rounds, double *us_per_step, double *best_skin,
+                            int32_t *best_partitioned, int64_t *best_wave) {
     mdas_status st = tune_args("tune_batch", descs, n_systems, skins, n_skins, md_steps, swap_trials, rounds);
     if (st != MDAS_OK) return st;
-    if (!us_per_step || !best_skin || !best_partitioned) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_batch: bad argument");
+    if (!waves || n_waves <= 0 || !us_per_step || !best_skin || !best_partitioned || !best_wave)
+        return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_batch: bad argument");
+    for (int v = 0; v < n_waves; ++v)
+        if (waves[v] < 0) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_batch: a wave size is < 0");
     int best = -1;
-    for (int c = 0; c < 2 * n_skins; ++c) {
-        st = time_batch(descs, n_systems, skins[c / 2], c % 2, md_steps, swap_trials, rounds, &us_per_step[c]);
+    const int nc = n_skins * 2 * n_waves;
+    for (int c = 0; c < nc; ++c) {
+        const int ks = c / (2 * n_waves), kl = (c / n_waves) % 2, kw = c % n_waves;
+        st = time_batch(descs, n_systems, skins[ks], kl, (long long)waves[kw], md_steps, swap_trials, rounds,
+                        &us_per_step[c]);
         if (st != MDAS_OK) return st;
         if (best < 0 || us_per_step[c] < us_per_step[best]) best = c;
     }
-    *best_skin = skins[best / 2];
-    *best_partitioned = best % 2;
+    *best_skin = skins[best / (2 * n_waves)];
+    *best_partitioned = (best / n_waves) % 2;
+    *best_wave = waves[best % n_waves];
+    return MDAS_OK;
+}
+
+mdas_status mdas_set_batch_wave(mdas_system *s, int64_t max_beads) {
+    if (!s || max_beads < 0) return fail(s, MDAS_ERR_INVALID_ARG, "set_batch_wave: bad argument");
+    s->wave_beads = (long long)max_beads;
     return MDAS_OK;
 }
 

@@ -111,7 +111,7 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core",
            "mdas_wait_timeout_probe", "mdas_box", "mdas_alchemical_move_trace", "mdas_interleaflet_move",
            "mdas_device_ptrs", "mdas_server_add_patch", "mdas_server_submit_to", "mdas_server_patch_state",
-           "mdas_server_remove_patch", "mdas_tune_batch", "mdas_set_partitioned"]
+           "mdas_server_remove_patch", "mdas_tune_batch", "mdas_set_partitioned", "mdas_set_batch_wave"]
 
 
 def library_path() -> str:
@@ -458,6 +458,11 @@ class System:
         groups (mdas_set_partitioned; the default) or run it in lockstep."""
         self._ck(lib().mdas_set_partitioned(self._ptr, int(bool(on))))
 
+    def set_batch_wave(self, max_beads):
+        """Batches led by this system run their MD in waves of at most
+        max_beads beads (mdas_set_batch_wave; 0: all at once)."""
+        self._ck(lib().mdas_set_batch_wave(self._ptr, C.c_int64(int(max_beads))))
+
     def set_persistent(self, on=True):
         """MD in the persistent kernel (default) or as separate kernel launches."""
         self._ck(lib().mdas_set_persistent(self._ptr, int(bool(on))))
@@ -602,10 +607,12 @@ def tune_list_skin(models, skins=(0.2, 0.25, 0.3, 0.35, 0.4), md_steps=100, swap
     return best.value, dict(zip(cand.tolist(), us.tolist()))
 
 
-def tune_batch(models, skins=(0.2, 0.3, 0.4), md_steps=100, swap_trials=0, rounds=3, precision="fp32", stream=None):
-    """Time batches of `models` at every (list skin, layout) candidate
-    (mdas_tune_batch); returns (best skin, best layout partitioned?, {(skin,
-    partitioned): us per MD step})."""
+def tune_batch(models, skins=(0.2, 0.3, 0.4), waves=(0,), md_steps=100, swap_trials=0, rounds=3, precision="fp32",
+               stream=None):
+    """Time batches of `models` at every (list skin, layout, wave size)
+    candidate (mdas_tune_batch); returns (best skin, best layout
+    partitioned?, best wave size, {(skin, partitioned, wave): us per MD
+    step})."""
     prec = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
     keep, descs = [], []
     stream = _current_stream() if stream is None else int(stream)
@@ -617,12 +624,14 @@ def tune_batch(models, skins=(0.2, 0.3, 0.4), md_steps=100, swap_trials=0, round
         descs.append(C.pointer(d))
     arr = (C.POINTER(Desc) * len(descs))(*descs)
     cand = np.ascontiguousarray(skins, np.float64)
-    us = np.zeros(2 * len(cand), np.float64)
-    best, part = C.c_double(), C.c_int32()
-    _check(lib().mdas_tune_batch(arr, len(descs), _p(cand), len(cand), int(md_steps), int(swap_trials), int(rounds),
-                                 _p(us), C.byref(best), C.byref(part)))
-    table = {(float(cand[c // 2]), bool(c % 2)): float(us[c]) for c in range(2 * len(cand))}
-    return best.value, bool(part.value), table
+    wv = np.ascontiguousarray(waves, np.int64)
+    nw = len(wv)
+    us = np.zeros(2 * len(cand) * nw, np.float64)
+    best, part, wave = C.c_double(), C.c_int32(), C.c_int64()
+    _check(lib().mdas_tune_batch(arr, len(descs), _p(cand), len(cand), _p(wv), nw, int(md_steps), int(swap_trials),
+                                 int(rounds), _p(us), C.byref(best), C.byref(part), C.byref(wave)))
+    table = {(float(cand[c // (2 * nw)]), bool((c // nw) % 2), int(wv[c % nw])): float(us[c]) for c in range(len(us))}
+    return best.value, bool(part.value), wave.value, table
 
 
 def philox(k0, k1, c1, c2, c3, n):

@@ -185,20 +185,24 @@ def test_alchemical_trajectory_in_one_run_matches_separate_launches(prec):
 
 
 def test_tune_batch_times_skins_and_layouts_with_the_same_bits():
-    """The batch tuner times every (skin, layout) candidate; the two layouts
-    of a batch (partitioned, lockstep) give the same bits."""
+    """The batch tuner times every (skin, layout, wave) candidate; the layouts
+    of a batch (partitioned, lockstep) and its waves give the same bits."""
     ms = synth.replica_set(6, lo=600, hi=2048, seed=12)
-    best, part, us = mdas.tune_batch(ms, skins=(0.25, 0.3), md_steps=20, swap_trials=8, rounds=1)
-    assert set(us) == {(0.25, False), (0.25, True), (0.3, False), (0.3, True)}
-    assert us[(best, part)] == min(us.values())
+    best, part, wave, us = mdas.tune_batch(ms, skins=(0.25, 0.3), waves=(0, 60_000), md_steps=20, swap_trials=8,
+                                           rounds=1)
+    assert set(us) == {(sk, p, w) for sk in (0.25, 0.3) for p in (False, True) for w in (0, 60_000)}
+    assert us[(best, part, wave)] == min(us.values())
     out = []
-    for layout in (True, False):
+    for layout, wv in ((True, 0), (False, 0), (True, 60_000)):
         sy = [mdas.System(m) for m in ms]
         for s in sy:
             s.set_partitioned(layout)
+            s.set_batch_wave(wv)
         mdas.batch_run(sy, 15, 10)
         mdas.batch_run(sy, 15, 10)
         out.append([s.get_state() for s in sy])
-    for a, b in zip(*out):
-        assert np.array_equal(a["pos_u"], b["pos_u"]) and np.array_equal(a["vel"], b["vel"])
-        assert np.array_equal(a["ltype"], b["ltype"]) and a["trial"] == b["trial"]
+    for runs in zip(*out):
+        a = runs[0]
+        for b in runs[1:]:
+            assert np.array_equal(a["pos_u"], b["pos_u"]) and np.array_equal(a["vel"], b["vel"])
+            assert np.array_equal(a["ltype"], b["ltype"]) and a["trial"] == b["trial"]
