@@ -140,8 +140,8 @@ def test_resident_patches_carry_state_between_jobs():
 
 def test_resident_patch_admission_and_removal():
     ps = patches()[:2]
-    fp = mdas.footprint(ps[0])
-    sv = mdas.Server(fp + fp // 2, max_active=4)
+    f0, f1 = mdas.footprint(ps[0]), mdas.footprint(ps[1])
+    sv = mdas.Server(max(f0, f1) + min(f0, f1) // 2, max_active=4)   # either patch alone, not both
     pid = sv.add_patch(ps[0])
     with pytest.raises(mdas.MdasError) as e:             # no room left for a second patch
         sv.add_patch(ps[1])
