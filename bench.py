@@ -255,26 +255,27 @@ def run_gpu(args):
     value = pairs_per_eval * md * ws / tmax
     trials_per_s = trials * ws / tmax
 
-    # end to end through the C ABI with host buffers: upload the state, run a
-    # round, read the state back, every step
-    st = sysm.get_state()
-    host = {k: st[k] for k in ("pos_u", "vel", "ltype")}
+    # end to end through the C ABI with pinned host buffers: upload the state
+    # (mdas_set_state_packed: positions, velocities, lipid types), run a
+    # round, read the state back (mdas_get_state_packed), every step
+    n = m.n_beads
+    hbuf = (torch.empty((n, 4), dtype=torch.int32).pin_memory(), torch.empty((n, 4), dtype=torch.float32).pin_memory(),
+            torch.empty(m.n_lipids, dtype=torch.int32).pin_memory())
+    sysm.get_state_packed(*hbuf)
     for _ in range(2):
-        sysm.set_state(pos_u=host["pos_u"], vel=host["vel"], ltype=host["ltype"], step=st["step"], trial=st["trial"])
+        sysm.set_state_packed(*hbuf)
         sysm.md_steps(MD_PER_STEP, swap_every=1)
-        st = sysm.get_state()
+        sysm.get_state_packed(*hbuf)
     torch.cuda.synchronize()
     e2e_steps = max(3, args.steps // 2)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        sysm.set_state(pos_u=host["pos_u"], vel=host["vel"], ltype=host["ltype"], step=st["step"], trial=st["trial"])
+        sysm.set_state_packed(*hbuf)
         sysm.md_steps(MD_PER_STEP, swap_every=1)
-        st = sysm.get_state()
+        sysm.get_state_packed(*hbuf)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    n = m.n_beads
-    h2d = 16 * n + 16 * n + 4 * m.n_lipids          # fixed-point positions + meta, float4 velocities, types
-    d2h = 16 * n + 16 * n + 4 * m.n_lipids
+    h2d = d2h = sum(t.numel() * t.element_size() for t in hbuf)   # every array, each way, every step
     e2e_value = pairs_per_eval * MD_PER_STEP * ws / e2e_s
 
     if rank != 0:

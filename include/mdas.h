@@ -290,6 +290,22 @@ mdas_status mdas_device_ptrs(mdas_system *s, mdas_device_view *out);
  * ke[] instead of summing the restored velocities. */
 mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in);
 
+/* The state in the library's own layout, one copy per array on the system's
+ * stream and no conversion, for callers that move whole states often (a new
+ * state per job, a checkpoint per round); host pointers (pinned memory copies
+ * fastest), any of them may be NULL.  pos4: n_beads records of four uint32,
+ * x, y, z as fractions of the box (x = u L / 2^32) and the meta word of
+ * mdas_device_view (ignored by set: rebuilt from the lipid types).  vel4:
+ * n_beads records of four float (FP32 systems, 16 bytes) or double (FP64
+ * systems, 32 bytes), x, y, z in nm/ps and one unused lane.  lipid_type:
+ * n_lipids int32.  get returns after its copies are done.  set checks the
+ * lipid types (MDAS_ERR_INVALID_ARG if one is out of range, before any copy),
+ * keeps the step, trial and move counters, makes the pair list and cell list
+ * stale (rebuilt by the next call that needs them), clears MDAS_ERR_UNSTABLE,
+ * and returns after its copies are done (the host arrays may be reused). */
+mdas_status mdas_get_state_packed(const mdas_system *s, uint32_t *pos4, void *vel4, int32_t *lipid_type);
+mdas_status mdas_set_state_packed(mdas_system *s, const uint32_t *pos4, const void *vel4, const int32_t *lipid_type);
+
 /* The cell list of the current positions: sorted_ids [n_beads] (bead ids by
  * cell, ascending id within a cell), cell_start [n_cells+1]; cell dims in
  * ncell[3] (floor(L/rc) per edge).  Any pointer may be NULL. */

@@ -1316,6 +1316,66 @@ __global__ void k_list_current(const SysDev S, int n, int par) {
     S.lpos[(size_t)par * n + k] = S.pos[S.lid[k]];
 }
 
+// The counters of a newly installed state (both ways of installing one):
+// no error, no pending exchange, alchemical or kinetic-energy work, the pair
+// list to be rebuilt.  The step, trial and move counters are the caller's.
+__host__ __device__ inline void new_state_counters(Counters &c) {
+    c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0; c.ke_fresh = 0; c.ke_pending = 0; c.draw_n = 0;
+    for (int g = 0; g < 2; ++g)
+        for (int q = 0; q < KE_SLOTS; ++q) c.ke_slot[g][q][0] = c.ke_slot[g][q][1] = 0;
+    c.nl_stale = 1; c.nl_viol = 0; c.sticket = 0; c.nticket = 0;
+}
+
+// A packed state upload, after the copies: each bead's meta word from the
+// lipid types (the host checked them), the counters of a new state.
+__global__ void k_state_packed(const SysDev S, int n, int nl, int bpl, int water_bt) {
+    const Params &P = *S.p;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        uint4 q = S.pos[i];
+        if (i < nl * bpl) {
+            const int bt = P.lbt[S.ltype[i / bpl] * 16 + i % bpl];
+            q.w = meta_make(bt, bt, i % bpl, i / bpl + 1);
+        } else {
+            q.w = meta_make(water_bt, water_bt, 15, 0);
+        }
+        S.pos[i] = q;
+    }
+    if (i == 0) new_state_counters(*S.c);
+}
+
+mdas_status mdas_get_state_packed(const mdas_system *cs, uint32_t *pos4, void *vel4, int32_t *lipid_type) {
+    mdas_system *s = const_cast<mdas_system *>(cs);
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "get_state_packed: NULL system");
+    const size_t n = s->n, vsz = s->precision == MDAS_FP64 ? 32 : 16;
+    if (pos4) CK(cudaMemcpyAsync(pos4, s->hs.pos, 16 * n, cudaMemcpyDeviceToHost, s->stream));
+    if (vel4) CK(cudaMemcpyAsync(vel4, s->hs.vel, vsz * n, cudaMemcpyDeviceToHost, s->stream));
+    if (lipid_type && s->n_lip > 0)
+        CK(cudaMemcpyAsync(lipid_type, s->hs.ltype, 4ull * s->n_lip, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MDAS_OK;
+}
+
+mdas_status mdas_set_state_packed(mdas_system *s, const uint32_t *pos4, const void *vel4, const int32_t *lipid_type) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_state_packed: NULL system");
+    const size_t n = s->n, vsz = s->precision == MDAS_FP64 ? 32 : 16;
+    if (lipid_type)
+        for (int l = 0; l < s->n_lip; ++l)
+            if (lipid_type[l] < 0 || lipid_type[l] >= s->hp.n_lt)
+                return fail(s, MDAS_ERR_INVALID_ARG, "set_state_packed: lipid type");
+    if (pos4) CK(cudaMemcpyAsync(s->hs.pos, pos4, 16 * n, cudaMemcpyHostToDevice, s->stream));
+    if (vel4) CK(cudaMemcpyAsync(s->hs.vel, vel4, vsz * n, cudaMemcpyHostToDevice, s->stream));
+    if (lipid_type && s->n_lip > 0)
+        CK(cudaMemcpyAsync(s->hs.ltype, lipid_type, 4ull * s->n_lip, cudaMemcpyHostToDevice, s->stream));
+    k_state_packed<<<(int)((n + 255) / 256), 256, 0, s->stream>>>(s->hs, (int)n, s->n_lip, s->bpl, s->water_bt);
+    CK(cudaGetLastError());
+    // the host arrays may be reused once the call returns
+    CK(cudaStreamSynchronize(s->stream));
+    s->unstable = false;
+    s->cells_valid = false;
+    return MDAS_OK;
+}
+
 mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     if (!s || !in) return fail(s, MDAS_ERR_INVALID_ARG, "set_state: NULL argument");
     const int n = s->n, nl = s->n_lip, bpl = s->bpl;
@@ -1401,9 +1461,7 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     CK(cudaMemcpyAsync(&c, s->hs.c, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     c.step = in->step; c.trial = in->trial; c.move = in->move; c.at_step = in->at_step;
-    c.err = 0; c.in_at = 0; c.lambda = 0.0; c.pending = 0; c.ke_fresh = 0; c.ke_pending = 0; c.draw_n = 0;
-    memset(c.ke_slot, 0, sizeof(c.ke_slot));
-    c.nl_stale = 1; c.nl_viol = 0; c.sticket = 0; c.nticket = 0;
+    new_state_counters(c);
     if (in->ke_valid) {
         c.ke_fresh = 1;
         c.ke_total[0] = in->ke[0];

@@ -20,7 +20,7 @@ constexpr int NL_G = 4;                // threads per bead in the pair-list step
 constexpr int NL_BLOCK = 128;          // threads per block of the pair-list step kernel
 constexpr int NL_BEADS = NL_BLOCK / NL_G;
 constexpr int NL_PART = 8;             // bonded partners per bead at most
-constexpr int NLB_STAGE = 768;         // candidates staged per chunk by the list build
+constexpr int NLB_STAGE = 384;         // candidates staged per chunk by the list build (two chunks for a typical cell)
 constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
 constexpr int MAX_ROUND_TRIALS = 1024; // trials per batched swap evaluation

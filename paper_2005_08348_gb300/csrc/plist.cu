@@ -1295,6 +1295,18 @@ static cudaError_t run_setup(int *blocks_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(k_md_run<Real, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_md_part<Real, LAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        // no more shared memory than the block needs: the rest of the SM's
+        // 256 KB stays L1 cache for the step's position gathers
+        int dev = 0, maxsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int carve = maxsm > 0 ? std::min(100, (int)(100.0 * (double)(smem + 4096) / maxsm) + 1) : 100;
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_md_run<Real, LAM>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_md_part<Real, LAM>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    }
     if (e != cudaSuccess) return e;
     int per_part = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_md_run<Real, LAM>, RUN_THREADS, smem);

@@ -111,7 +111,8 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_tune_list_skin", "mdas_head_rdf", "mdas_mutation_trials", "mdas_set_soft_core",
            "mdas_wait_timeout_probe", "mdas_box", "mdas_alchemical_move_trace", "mdas_interleaflet_move",
            "mdas_device_ptrs", "mdas_server_add_patch", "mdas_server_submit_to", "mdas_server_patch_state",
-           "mdas_server_remove_patch", "mdas_tune_batch", "mdas_set_partitioned", "mdas_set_batch_wave"]
+           "mdas_server_remove_patch", "mdas_tune_batch", "mdas_set_partitioned", "mdas_set_batch_wave",
+           "mdas_get_state_packed", "mdas_set_state_packed"]
 
 
 def library_path() -> str:
@@ -410,6 +411,44 @@ class System:
             for a in range(3):
                 v.list_box[a] = float(list_box[a])
         self._ck(lib().mdas_set_state(self._ptr, C.byref(v)))
+
+    def _packed_args(self, pos4, vel4, lipid_type):
+        """Host addresses of packed-state arrays (numpy arrays or CPU torch
+        tensors, C-contiguous, the sizes mdas_get_state_packed documents)."""
+        vbytes = 32 if self.precision == MDAS_FP64 else 16
+        out = []
+        for a, nbytes in ((pos4, 16 * self.n), (vel4, vbytes * self.n), (lipid_type, 4 * self.n_lipids)):
+            if a is None:
+                out.append(None)
+                continue
+            if hasattr(a, "data_ptr"):                  # a torch tensor
+                if a.device.type != "cpu" or not a.is_contiguous() or a.numel() * a.element_size() != nbytes:
+                    raise ValueError("packed state: a contiguous CPU tensor of %d bytes is needed" % nbytes)
+                out.append(C.c_void_p(a.data_ptr()))
+            else:
+                if not a.flags["C_CONTIGUOUS"] or a.nbytes != nbytes:
+                    raise ValueError("packed state: a C-contiguous array of %d bytes is needed" % nbytes)
+                out.append(C.c_void_p(a.ctypes.data))
+        return out
+
+    def get_state_packed(self, pos4=None, vel4=None, lipid_type=None):
+        """The state in the library's layout into host arrays (mdas_get_state_packed):
+        pos4 [n, 4] uint32 (x, y, z fixed point, meta word), vel4 [n, 4] float32
+        (FP32 systems) or float64, lipid_type [n_lipids] int32.  Pass numpy arrays
+        or (pinned) CPU torch tensors to fill; by default numpy arrays are made."""
+        if pos4 is None and vel4 is None and lipid_type is None:
+            pos4 = np.empty((self.n, 4), np.uint32)
+            vel4 = np.empty((self.n, 4), np.float64 if self.precision == MDAS_FP64 else np.float32)
+            lipid_type = np.empty(self.n_lipids, np.int32)
+        a, b, c = self._packed_args(pos4, vel4, lipid_type)
+        self._ck(lib().mdas_get_state_packed(self._ptr, a, b, c))
+        return pos4, vel4, lipid_type
+
+    def set_state_packed(self, pos4=None, vel4=None, lipid_type=None):
+        """Install a state in the library's layout (mdas_set_state_packed); the
+        step, trial and move counters are kept, the pair list is rebuilt."""
+        a, b, c = self._packed_args(pos4, vel4, lipid_type)
+        self._ck(lib().mdas_set_state_packed(self._ptr, a, b, c))
 
     def resume(self, state):
         """set_state with everything get_state returned (an exact continuation)."""

@@ -111,3 +111,51 @@ def test_expired_wait_is_reported_and_the_run_resumes():
     b.md_steps(12, swap_every=3)
     b.md_steps(24, swap_every=3)
     same(a.get_state(), b.get_state())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_packed_state_round_trip(prec):
+    """mdas_get_state_packed / mdas_set_state_packed: the library's own layout
+    holds the same state as get_state; installing it continues exactly as
+    set_state with the same arrays (both rebuild the pair list); meta words
+    follow the lipid types; a bad lipid type is refused before any copy."""
+    torch = pytest.importorskip("torch")
+    m = synth.mcmd_small()
+    a = mdas.System(m, precision=prec)
+    a.md_steps(30, swap_every=2)
+    pos4, vel4, lt = a.get_state_packed()
+    st = a.get_state()
+    assert np.array_equal(pos4[:, :3], st["pos_u"])
+    assert np.array_equal(vel4[:, :3].astype(np.float64), st["vel"])
+    assert np.array_equal(lt, st["ltype"])
+    bpl = synth.BEADS_PER_LIPID
+    lip_beads = m.n_lipids * bpl
+    bt = pos4[:lip_beads, 3] & 15
+    assert np.array_equal(bt, m.lipid_bead_type[np.repeat(lt, bpl), np.tile(np.arange(bpl), m.n_lipids)])
+    assert np.all(pos4[lip_beads:, 3] & 15 == m.water_bead_type)
+    # a new lipid-type assignment travels with the packed state
+    lt2 = lt.copy()
+    lt2[:4] = (lt2[:4] + 1) % 2
+    b, c = mdas.System(m, precision=prec), mdas.System(m, precision=prec)
+    p4 = pos4.copy()
+    p4[:, 3] = 0                                          # meta words are rebuilt from the types
+    b.set_state_packed(p4, vel4, lt2)
+    c.set_state(pos_u=st["pos_u"], vel=st["vel"], ltype=lt2)
+    for s in (b, c):
+        s.md_steps(40, swap_every=1)
+    same(b.get_state(), c.get_state())
+    assert b.energy()["total"] == c.energy()["total"]
+    # pinned torch tensors as the host arrays
+    tp = torch.empty((m.n_beads, 4), dtype=torch.int32).pin_memory()
+    tv = torch.empty((m.n_beads, 4), dtype=torch.float64 if prec == "fp64" else torch.float32).pin_memory()
+    tl = torch.empty(m.n_lipids, dtype=torch.int32).pin_memory()
+    b.get_state_packed(tp, tv, tl)
+    sb = b.get_state()
+    assert np.array_equal(tp.numpy()[:, :3].view(np.uint32), sb["pos_u"])
+    assert np.array_equal(tl.numpy(), sb["ltype"])
+    bad = lt.copy()
+    bad[0] = 99
+    with pytest.raises(mdas.MdasError) as e:
+        b.set_state_packed(p4, vel4, bad)
+    assert e.value.status == 1
+    same(b.get_state(), sb)                               # nothing was installed
