@@ -146,13 +146,14 @@ void launch_thermo_draws(const LaunchCtx &L, int n) {
 // Thermostat factor of the coming step (counter C.step, or C.at_step on the
 // alchemical trajectory): group kinetic energies as the last MD step left
 // them (ke_fresh), else straight from the velocities; fixed-order reductions
-// (thread-strided sums, then a tree).
+// (thread-strided sums, a shuffle tree per warp, the warps in order by a
+// shuffle tree in warp 0).  Any block size that is a multiple of 32.
 template <typename Real>
 __device__ void thermostat_block(const SysDev &S, const Params &P) {
     using V4 = typename Vec4<Real>::T;
     Counters &C = *S.c;
-    const int t = threadIdx.x, T = blockDim.x;
-    __shared__ Real ks[2][32 * CELLS_PER_SORT_BLOCK];
+    const int t = threadIdx.x, T = blockDim.x, lane = t & 31;
+    __shared__ Real ws[2][32];
     __shared__ int fresh;
     if (t == 0) fresh = C.ke_fresh;
     __syncthreads();
@@ -162,39 +163,49 @@ __device__ void thermostat_block(const SysDev &S, const Params &P) {
     } else {
         const V4 *vel = reinterpret_cast<const V4 *>(S.vel);
         const Real hm = (Real)(0.5 * P.mass);
+#pragma unroll 4
         for (int i = t; i < P.n; i += T) {
             const V4 v = vel[i];
             const Real e = hm * (v.x * v.x + v.y * v.y + v.z * v.z);
             if (i < P.n_lipid_beads) k0 += e; else k1 += e;
         }
     }
-    ks[0][t] = k0;
-    ks[1][t] = k1;
-    __syncthreads();
-    for (int w = T / 2; w > 0; w >>= 1) {
-        if (t < w) { ks[0][t] += ks[0][t + w]; ks[1][t] += ks[1][t + w]; }
-        __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        k0 += __shfl_xor_sync(0xffffffffu, k0, o);
+        k1 += __shfl_xor_sync(0xffffffffu, k1, o);
     }
-    const int in_at = C.in_at;
-    const unsigned long long ctr = in_at ? C.at_step : C.step;
-    const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
-    if ((t & 31) == 0 && t < 64) {
-        const int g = t >> 5;
-        C.alpha[g] = alpha_for(S, P, C, g, (double)ks[g][0], ctr, tag);
-        C.alpha_f[g] = (float)C.alpha[g];
+    if (lane == 0) { ws[0][t >> 5] = k0; ws[1][t >> 5] = k1; }
+    __syncthreads();
+    if (t < 32) {
+        k0 = lane < T / 32 ? ws[0][lane] : (Real)0;
+        k1 = lane < T / 32 ? ws[1][lane] : (Real)0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            k0 += __shfl_xor_sync(0xffffffffu, k0, o);
+            k1 += __shfl_xor_sync(0xffffffffu, k1, o);
+        }
+        const int in_at = C.in_at;
+        const unsigned long long ctr = in_at ? C.at_step : C.step;
+        const uint32_t tag = in_at ? TAG_AT_THERMO : TAG_THERMO;
+        if (lane < 2) {                         // lane g: coupling group g
+            C.alpha[lane] = alpha_for(S, P, C, lane, (double)(lane == 0 ? k0 : k1), ctr, tag);
+            C.alpha_f[lane] = (float)C.alpha[lane];
+        }
     }
 }
 
 // grid (n_sys): the thermostat factor of the coming step of every system
+constexpr int THERMO_THREADS = 1024;
 template <typename Real>
-__global__ void __launch_bounds__(32 * CELLS_PER_SORT_BLOCK) k_thermostat(const SysDev *__restrict__ sys) {
+__global__ void __launch_bounds__(THERMO_THREADS) k_thermostat(const SysDev *__restrict__ sys) {
     const SysDev &S = sys[blockIdx.x];
     thermostat_block<Real>(S, *S.p);
 }
 
 void launch_thermostat(const LaunchCtx &L) {
-    if (L.precision == 1) k_thermostat<double><<<L.n_sys, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys);
-    else k_thermostat<float><<<L.n_sys, 32 * CELLS_PER_SORT_BLOCK, 0, L.stream>>>(L.sys);
+    if (L.precision == 1) k_thermostat<double><<<L.n_sys, THERMO_THREADS, 0, L.stream>>>(L.sys);
+    else k_thermostat<float><<<L.n_sys, THERMO_THREADS, 0, L.stream>>>(L.sys);
 }
 
 // Pressure coupling after an MD segment (Sec. 3: semi-isotropic
