@@ -102,14 +102,19 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
         const int kk = valid ? MDAS_IDX(*S.c, S.lk[id], P.n) : 0;
         const int ta = S.ltype[a], tb = S.ltype[b];
         const uint4 pk = cur[kk];
-        const int4 cn = *reinterpret_cast<const int4 *>(S.nl_n + (size_t)kk * NL_G);
+        int cn[NL_G];
+#pragma unroll
+        for (int c = 0; c < NL_G; ++c) cn[c] = S.nl_n[(size_t)kk * NL_G + c];
         const bool null_trial = (a == b) || (ta == tb);
         const int bo = P.lbt[(side ? tb : ta) * 16 + k], bn = P.lbt[(side ? ta : tb) * 16 + k];
         const bool ch = valid && !null_trial && bo != bn;
         const unsigned bal = __ballot_sync(0xffffffffu, ch);
         // entries of the changed beads in lane order, columns in order within
         // a bead: exclusive offsets by one warp scan
-        const int tot = ch ? cn.x + cn.y + cn.z + cn.w : 0;
+        int tot = 0;
+#pragma unroll
+        for (int c = 0; c < NL_G; ++c) tot += cn[c];
+        if (!ch) tot = 0;
         int inc = tot;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -117,7 +122,6 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
             if (lane >= d) inc += x;
         }
         if (ch) {
-            static_assert(NL_G == 4, "four list columns per bead");
             if (mark && p == 0) atomicOr(&mk[kk / NL_BEADS / 32], 1u << (kk / NL_BEADS % 32));
             const int o = __popc(bal & ((1u << lane) - 1u));
             sm.chg_id[o] = id;
@@ -125,11 +129,12 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
             sm.chg_pos[o] = pk;
             sm.chg_old[o] = bo;
             sm.chg_new[o] = bn;
-            const int run = inc - tot;
-            sm.it_beg[4 * o] = run;
-            sm.it_beg[4 * o + 1] = run + cn.x;
-            sm.it_beg[4 * o + 2] = run + cn.x + cn.y;
-            sm.it_beg[4 * o + 3] = run + cn.x + cn.y + cn.z;
+            int run = inc - tot;
+#pragma unroll
+            for (int c = 0; c < NL_G; ++c) {
+                sm.it_beg[NL_G * o + c] = run;
+                run += cn[c];
+            }
         }
         if (lane == 31) {
             const int nc = __popc(bal);
@@ -243,9 +248,9 @@ __device__ __forceinline__ double pair_dw_soft(const Params &P, int oi, int oj, 
 // MDAS work term of lipid x of the move (Eq. 2: U_B - U_A at the current
 // coordinates, over the pairs within rc that involve a bead whose A and B
 // types differ, pairs of two such beads once, by the lower id) from the pair
-// list, positions in buffer par; one 128-thread group: thread t walks every
-// other row of list column (t / 2) % NL_G of bead t / 8 (both halves of a
-// column by threads t and t ^ 1); the group sum in fixed order.
+// list, positions in buffer par; one 128-thread group: the 8 threads of
+// bead t / 8 share its NL_G list columns, 8 / NL_G threads per column, each
+// walking every (8 / NL_G)-th row; the group sum in fixed order.
 //
 // On the soft-core path (sc_delta > 0) a pair adds its work over the lambda
 // step l0 -> l1 instead (pair_dw_soft), which the caller adds to w as it is.
@@ -253,9 +258,10 @@ __device__ inline double mdas_work_part(const SysDev &S, int x, int par, const G
                                         double l1) {
     const Params &P = *S.p;
     const Counters &C = *S.c;
-    static_assert(NL_G == 4 && GRP == 128, "four list columns per bead, 128 threads");
+    static_assert(NL_G <= 8 && 8 % NL_G == 0 && GRP == 128, "at most eight list columns per bead, 128 threads");
+    constexpr int TPC = 8 / NL_G;              // threads per list column
     const int l = C.pairs[x];
-    const int t = g.t, k = t / 8, col = (t / 2) % NL_G, half = t & 1;
+    const int t = g.t, k = t / 8, col = (t % 8) / TPC, sub = t % TPC;
     const uint4 *cur = S.lpos + (size_t)par * P.n;
     double acc = 0.0;
     if (k < P.bpl) {
@@ -264,7 +270,7 @@ __device__ inline double mdas_work_part(const SysDev &S, int x, int par, const G
         const int oi = meta_ta(pi.w), ni = meta_tb(pi.w);
         if (oi != ni) {
             const int rows = S.nl_n[(size_t)ki * NL_G + col];
-            for (int r = half; r < rows; r += 2) {
+            for (int r = sub; r < rows; r += TPC) {
                 const int kj = MDAS_IDX(*S.c, S.nl[(size_t)r * P.lrow + (size_t)ki * NL_G + col], P.n);
                 const uint4 pj = cur[kj];
                 const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
