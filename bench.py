@@ -371,17 +371,20 @@ def replica_benchmark(stream, n_rep=64, rounds=3):
     """64 independent bilayers of 128-2048 lipids, each advanced by 100 MD
     steps + 100 exchange trials per round: all replicas in one launch per
     phase (mdas_batch_run) against one replica at a time, both with the
-    pair-list skin the autotuner picks for the batch."""
+    pair-list skin the autotuner picks for the batch; the batch also takes the
+    tuner's layout and step shape, the replicas run alone the default shape
+    (4 lanes per bead, the faster one for a lone system)."""
     from paper_2005_08348_gb300 import mdas, synth
     ms = synth.replica_set(n_rep)
-    skin, part, wave, tune = mdas.tune_batch(ms, skins=(0.25, 0.3), waves=(0, 400_000),
-                                             md_steps=MD_PER_STEP, swap_trials=MD_PER_STEP, rounds=1,
-                                             stream=stream.cuda_stream)
+    skin, part, wave, lanes, tune = mdas.tune_batch(ms, skins=(0.25, 0.3), waves=(0,), lanes=(2, 4),
+                                                    md_steps=MD_PER_STEP, swap_trials=MD_PER_STEP, rounds=1,
+                                                    stream=stream.cuda_stream)
     sys_b = [mdas.System(m, stream=stream.cuda_stream, list_skin=skin) for m in ms]
-    sys_s = [mdas.System(m, stream=stream.cuda_stream, list_skin=skin) for m in ms]
+    sys_s = [mdas.System(m, stream=stream.cuda_stream, list_skin=skin) for m in ms]   # 4 lanes: a lone system's best
     for s in sys_b:
         s.set_partitioned(part)
         s.set_batch_wave(wave)
+        s.set_list_lanes(lanes)
     pairs = sum(s.energy()["pairs"] for s in sys_b)
     mdas.batch_run(sys_b, MD_PER_STEP, MD_PER_STEP)
     for s in sys_s:
@@ -405,9 +408,9 @@ def replica_benchmark(stream, n_rep=64, rounds=3):
            "batched_swap_trials_per_s": n_rep * md / tb, "one_at_a_time_swap_trials_per_s": n_rep * md / ts,
            "speedup": ts / tb, "rounds": rounds, "list_skin_nm": skin,
            "layout": "partitioned (systems advance independently)" if part else "lockstep (kernel-wide barriers)",
-           "wave_beads": wave or "all",
-           "autotune_us_per_md_step": {f"skin {k[0]:g} {'partitioned' if k[1] else 'lockstep'} wave {k[2] or 'all'}":
-                                       round(v, 2) for k, v in tune.items()}}
+           "wave_beads": wave or "all", "list_lanes_per_bead": lanes, "one_at_a_time_list_lanes_per_bead": 4,
+           "autotune_us_per_md_step": {f"skin {k[0]:g} {'partitioned' if k[1] else 'lockstep'} wave {k[2] or 'all'} "
+                                       f"lanes {k[3]}": round(v, 2) for k, v in tune.items()}}
     for s in sys_b + sys_s:
         s.close()
     return res

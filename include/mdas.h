@@ -375,22 +375,35 @@ mdas_status mdas_set_partitioned(mdas_system *s, int32_t enable);
  * Errors: MDAS_ERR_INVALID_ARG for a NULL system or max_beads < 0. */
 mdas_status mdas_set_batch_wave(mdas_system *s, int64_t max_beads);
 
+/* The step shape of a system's pair-list MD: `lanes` list columns (threads)
+ * per bead, 128 / lanes beads per step item; 4 (the default) suits a system
+ * advanced alone (shorter chains per thread), 2 a large batch (fewer per-bead
+ * reductions per pair).  All systems of a batch must agree
+ * (MDAS_ERR_INVALID_ARG otherwise); a change takes effect at the next MD call,
+ * which builds the pair list again.  The forces are the same sums in another
+ * order (FP32 bits may differ between shapes, not within one).  Errors:
+ * MDAS_ERR_INVALID_ARG for a NULL system or lanes other than 2 or 4. */
+mdas_status mdas_set_list_lanes(mdas_system *s, int32_t lanes);
+
 /* Autotuning of a batch's work shape: for each of the n_skins candidate
  * list skins (nm, each > 0), each of the two layouts of mdas_set_partitioned
- * (0: lockstep, 1: partitioned) and each of the n_waves wave sizes of
- * mdas_set_batch_wave (beads, >= 0), the systems described by descs[] are
- * created, advanced by one untimed round and timed over `rounds` rounds of
+ * (0: lockstep, 1: partitioned), each of the n_waves wave sizes of
+ * mdas_set_batch_wave (beads, >= 0) and each of the n_lanes step shapes of
+ * mdas_set_list_lanes (2 or 4), the systems described by descs[] are created,
+ * advanced by one untimed round and timed over `rounds` rounds of
  * mdas_batch_run(md_steps, swap_trials) with CUDA events on their stream,
- * then destroyed.  us_per_step (host, n_skins * 2 * n_waves entries,
- * candidate (skin * 2 + layout) * n_waves + wave) receives the device time
- * per MD step; *best_skin, *best_partitioned and *best_wave the fastest
- * candidate.  Neither the descriptors nor any existing system change.
- * Errors as mdas_tune_list_skin, and for a NULL waves array, n_waves <= 0
- * or a wave size < 0. */
+ * then destroyed.  us_per_step (host, n_skins * 2 * n_waves * n_lanes
+ * entries, candidate ((skin * 2 + layout) * n_waves + wave) * n_lanes + lanes)
+ * receives the device time per MD step; *best_skin, *best_partitioned,
+ * *best_wave and *best_lanes the fastest candidate.  Neither the descriptors
+ * nor any existing system change.  Errors as mdas_tune_list_skin, and for a
+ * NULL waves or lanes array, n_waves or n_lanes <= 0, a wave size < 0 or a
+ * lane count other than 2 or 4. */
 mdas_status mdas_tune_batch(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
-                            int32_t n_skins, const int64_t *waves, int32_t n_waves, int32_t md_steps,
-                            int32_t swap_trials, int32_t rounds, double *us_per_step, double *best_skin,
-                            int32_t *best_partitioned, int64_t *best_wave);
+                            int32_t n_skins, const int64_t *waves, int32_t n_waves, const int32_t *lanes,
+                            int32_t n_lanes, int32_t md_steps, int32_t swap_trials, int32_t rounds,
+                            double *us_per_step, double *best_skin, int32_t *best_partitioned, int64_t *best_wave,
+                            int32_t *best_lanes);
 
 /* The path of the alchemical moves (Sec. 2).  delta = 0 (the default): the
  * linear path U(lambda) = (1 - lambda) U_A + lambda U_B.  delta > 0 (nm^2):

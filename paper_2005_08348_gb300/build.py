@@ -29,7 +29,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompil
 # The pair-list and trial code is inlined into several kernels (the persistent
 # kernel and the separate ones) that must give identical bits: no implicit
 # multiply-add contraction there (the source writes its FMAs explicitly).
-FILE_FLAGS = {"plist.cu": ["-fmad=false"], "swap.cu": ["-fmad=false"]}
+FILE_FLAGS = {"plist.cu": ["-fmad=false"], "plist_g2.cu": ["-fmad=false"], "swap.cu": ["-fmad=false"]}
 if CHECKED:
     FLAGS = FLAGS + ["-DMDAS_CHECKED"]
 

@@ -32,6 +32,7 @@ struct Batch {
     size_t part_cap = 0;
     int part_groups = 0;          // groups the partition was made for (0: none made yet)
     bool persistent = true;       // MD in the persistent kernel (else separate kernel launches)
+    int lanes = NL_LANES;         // list columns per bead of the batch's pair lists (all its systems agree)
     size_t cap_sys = 0, cap_beads = 0, cap_cells = 0, cap_sort = 0;   // device capacity (refillable batches)
     size_t cap_nlb = 0, cap_lc = 0, cap_ls = 0;
     LaunchCtx ctx() const;
@@ -47,7 +48,7 @@ std::string g_last_error;
 // at that density, both multiples of 32.
 struct ListDims {
     double rl;
-    int ln[3], n_lcells, lcapc, lcap, lrow;
+    int ln[3], n_lcells, lcapc, lcap, npad;
 };
 
 // The fraction by which each box edge may shrink under pressure coupling
@@ -85,7 +86,7 @@ ListDims list_dims(const mdas_system_desc *d, double shrink = 0.0) {
     const double dens = std::max((double)n / vol, maxc / (vol / L.n_lcells));
     const double within = 4.0 / 3.0 * M_PI * L.rl * L.rl * L.rl * dens;
     L.lcap = std::max(64, (int)std::ceil(1.5 * within / 32.0) * 32);
-    L.lrow = ((n + 31) / 32 * 32) * NL_G;
+    L.npad = (n + 31) / 32 * 32;
     return L;
 }
 
@@ -112,6 +113,8 @@ struct mdas_system {
     bool timing = false;
     bool partition = true;      // batches may give this system its own share of the persistent kernel's groups
     long long wave_beads = 0;   // a batch's MD runs in waves of systems of at most this many beads (0: all at once)
+    int lanes = NL_LANES;       // list columns per bead this system's MD uses (mdas_set_list_lanes)
+    int list_lanes = 0;         // the list columns its current pair list was built with (0: none yet)
     double pair_ms = 0.0;
     long long pair_launches = 0;
     long long kernel_launches = 0;   // kernel launches (graph kernel nodes included) that advanced this system
@@ -124,6 +127,7 @@ LaunchCtx Batch::ctx() const {
     L.beads = &beads; L.cells = &cells; L.sortcells = &sortcells; L.syss = &syss;
     L.nlbeads = &nlbeads; L.lcells = &lcells; L.lsort = &lsort;
     L.precision = precision; L.stream = stream; L.max_bead_blocks = max_bead_blocks;
+    L.lanes = lanes;
     L.bticket = bticket;
     L.soft = false;
     L.pc = false;
@@ -207,6 +211,7 @@ void destroy_batch(Batch *b) {
 // list-build cells
 struct Maps {
     std::vector<int2> beads, cells, sortcells, syss, nlbeads, lcells, lsort;
+    int lanes = NL_LANES;      // the batch's list columns per bead (step items of NL_BLOCK / lanes beads)
     void add(int k, const mdas_system *x);
 };
 
@@ -216,7 +221,7 @@ void Maps::add(int k, const mdas_system *x) {
     for (int c = 0; c < x->hp.n_cells; c += CELLS_PER_SORT_BLOCK) sortcells.push_back(make_int2(k, c));
     sortcells.push_back(make_int2(k, -1));   // the system's thermostat block
     syss.push_back(make_int2(k, 0));
-    for (int i = 0; i < x->n; i += NL_BEADS) nlbeads.push_back(make_int2(k, i));
+    for (int i = 0; i < x->n; i += NL_BLOCK / lanes) nlbeads.push_back(make_int2(k, i));
     for (int c = 0; c < x->hp.n_lcells; ++c) lcells.push_back(make_int2(k, c));
     for (int c = 0; c < x->hp.n_lcells; c += CELLS_PER_SORT_BLOCK) lsort.push_back(make_int2(k, c));
 }
@@ -227,12 +232,15 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
     b->sys = v;
     b->precision = v[0]->precision;
     b->stream = v[0]->stream;
+    b->lanes = v[0]->lanes;
     std::vector<SysDev> hs;
     Maps mp;
+    mp.lanes = b->lanes;
     for (int k = 0; k < (int)v.size(); ++k) {
         const mdas_system *x = v[k];
         if (x->precision != b->precision) return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision");
         if (x->stream != b->stream) return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in CUDA stream");
+        if (x->lanes != b->lanes) return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in list lanes");
         hs.push_back(x->hs);
         mp.add(k, x);
         b->max_bead_blocks = std::max(b->max_bead_blocks, (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK);
@@ -261,13 +269,15 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     b.sys = v;
     b.precision = v[0]->precision;
     b.stream = v[0]->stream;
+    b.lanes = v[0]->lanes;
     b.max_bead_blocks = 1;
     std::vector<SysDev> hs;
     Maps mp;
+    mp.lanes = b.lanes;
     for (int k = 0; k < (int)v.size(); ++k) {
         const mdas_system *x = v[k];
-        if (x->precision != b.precision || x->stream != b.stream)
-            return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision or stream");
+        if (x->precision != b.precision || x->stream != b.stream || x->lanes != b.lanes)
+            return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision, stream or list lanes");
         hs.push_back(x->hs);
         mp.add(k, x);
         b.max_bead_blocks = std::max(b.max_bead_blocks, (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK);
@@ -420,7 +430,7 @@ mdas_status make_partition(mdas_system *s, Batch &b, int groups, bool *use) {
     std::vector<int> items(n);
     long long total = 0;
     for (int q = 0; q < n; ++q) {
-        items[q] = (b.sys[q]->n + NL_BEADS - 1) / NL_BEADS;
+        items[q] = (b.sys[q]->n + NL_BLOCK / b.lanes - 1) / (NL_BLOCK / b.lanes);
         total += items[q];
     }
     if (n < 2 || n > groups / 2 || total + (long long)(TRIAL_PARTS + 1) * n <= groups) return MDAS_OK;
@@ -455,7 +465,7 @@ mdas_status make_partition(mdas_system *s, Batch &b, int groups, bool *use) {
     for (int q = 0; q < n; ++q) {
         const mdas_system *x = b.sys[q];
         r[q].g0 = g0; r[q].ng = ng[q];
-        r[q].nl0 = nl0; r[q].nln = (x->n + NL_BEADS - 1) / NL_BEADS;
+        r[q].nl0 = nl0; r[q].nln = (x->n + NL_BLOCK / b.lanes - 1) / (NL_BLOCK / b.lanes);
         r[q].bd0 = bd0; r[q].bdn = (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK;
         r[q].ls0 = ls0; r[q].lsn = (x->hp.n_lcells + CELLS_PER_SORT_BLOCK - 1) / CELLS_PER_SORT_BLOCK;
         r[q].lc0 = lc0; r[q].lcn = x->hp.n_lcells;
@@ -488,12 +498,19 @@ mdas_status run_md(mdas_system *s, Batch &b, long long n_steps, int swap_every, 
     SegTimer tm;
     for (auto *x : b.sys) tm.on = tm.on || x->timing;
     for (auto *x : b.sys) x->cells_valid = false;
+    // a list laid out for another step shape is built again for this batch's
+    static const int one = 1;
+    for (auto *x : b.sys)
+        if (x->list_lanes != b.lanes) {
+            CK(cudaMemcpyAsync(&x->hs.c->nl_stale, &one, sizeof(int), cudaMemcpyHostToDevice, b.stream));
+            x->list_lanes = b.lanes;
+        }
     LaunchCtx L = b.ctx();
     const int run_mode = !lambda ? (L.pc ? 3 : 0) : L.soft ? 2 : 1;
-    const bool persistent = b.persistent && md_run_blocks(b.precision, run_mode) > 0;
+    const bool persistent = b.persistent && md_run_blocks(b.precision, run_mode, b.lanes) > 0;
     if (persistent) {
         bool use = false;
-        mdas_status st = make_partition(s, b, md_run_groups(b.precision, run_mode), &use);
+        mdas_status st = make_partition(s, b, md_run_groups(b.precision, run_mode, b.lanes), &use);
         if (st != MDAS_OK) return st;
         if (use) {
             L.part = b.part;
@@ -778,8 +795,8 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         for (int k = 0; k < 3; ++k) P.pc_lmin[k] = std::max(P.nc[k] * d->rc, ld.ln[k] * P.rl);
         P.lcapc = ld.lcapc;
         P.lcap = ld.lcap;
-        P.lrow = ld.lrow;
-        P.mark_words = (n + NL_BEADS - 1) / NL_BEADS / 32 + 1;
+        P.npad = ld.npad;
+        P.mark_words = (n + NL_BEADS_MIN - 1) / NL_BEADS_MIN / 32 + 1;
         if (P.lcapc > 4096 || P.lcap > 4096) {
             delete s;
             return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: density too high for the pair list");
@@ -832,8 +849,8 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&s->rdf_nh, 8ull},
         {(void **)&H.lcell_count, 4ull * P.n_lcells}, {(void **)&H.ltmp, 4ull * P.n_lcells * P.lcapc},
         {(void **)&H.lcell, 8ull * P.n_lcells}, {(void **)&H.lid, 4ull * n}, {(void **)&H.lk, 4ull * n},
-        {(void **)&H.lpos, 32ull * n}, {(void **)&H.xref, 16ull * n}, {(void **)&H.nl_n, 4ull * NL_G * n},
-        {(void **)&H.nl, 4ull * (size_t)(P.lcap / NL_G) * P.lrow}, {(void **)&H.bslot, 4ull * NL_PART * n},
+        {(void **)&H.lpos, 32ull * n}, {(void **)&H.xref, 16ull * n}, {(void **)&H.nl_n, 4ull * NL_LANES_MAX * n},
+        {(void **)&H.nl, 4ull * (size_t)P.lcap * P.npad}, {(void **)&H.bslot, 4ull * NL_PART * n},
         {(void **)&H.tmark, 8ull * P.mark_words},
     };
     size_t total = 0;
@@ -1473,6 +1490,7 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
         // the list as it was built (same positions, same order), then the
         // current positions in its list-order buffer
         launch_nl_build(s->solo->ctx());
+        s->list_lanes = s->solo->lanes;
         CK(cudaMemcpyAsync(s->hs.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
         k_list_current<<<(n + 255) / 256, 256, 0, s->stream>>>(s->hs, n, 0);
         if (in->list_box[0] > 0) {
@@ -1602,12 +1620,12 @@ mdas_status mdas_head_rdf(mdas_system *s, int32_t lipid_type, int32_t head_k, do
 
 namespace {
 
-// Device time per MD step of a batch made from descs with the given list skin
-// and layout (partitioned or in lockstep): one untimed round, then `rounds`
-// rounds of mdas_batch_run timed with CUDA events on the batch's stream; the
-// systems are destroyed afterwards.
+// Device time per MD step of a batch made from descs with the given list
+// skin, layout (partitioned or in lockstep), wave size and list columns per
+// bead: one untimed round, then `rounds` rounds of mdas_batch_run timed with
+// CUDA events on the batch's stream; the systems are destroyed afterwards.
 mdas_status time_batch(const mdas_system_desc *const *descs, int n_systems, double skin, int partitioned,
-                       long long wave, int md_steps, int swap_trials, int rounds, double *us) {
+                       long long wave, int lanes, int md_steps, int swap_trials, int rounds, double *us) {
     std::vector<mdas_system_desc> dv(n_systems);
     std::vector<mdas_system *> sv;
     for (int i = 0; i < n_systems; ++i) {
@@ -1622,6 +1640,7 @@ mdas_status time_batch(const mdas_system_desc *const *descs, int n_systems, doub
             x->partition = partitioned != 0;
             x->wave_beads = wave;
             sv.push_back(x);
+            st = mdas_set_list_lanes(x, lanes);
         }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1669,7 +1688,7 @@ mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_
     if (!us_per_step || !best_skin) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_list_skin: bad argument");
     int best = -1;
     for (int c = 0; c < n_skins; ++c) {
-        st = time_batch(descs, n_systems, skins[c], 1, 0, md_steps, swap_trials, rounds, &us_per_step[c]);
+        st = time_batch(descs, n_systems, skins[c], 1, 0, NL_LANES, md_steps, swap_trials, rounds, &us_per_step[c]);
         if (st != MDAS_OK) return st;
         if (best < 0 || us_per_step[c] < us_per_step[best]) best = c;
     }
@@ -1678,27 +1697,34 @@ mdas_status mdas_tune_list_skin(const mdas_system_desc *const *descs, int32_t n_
 }
 
 mdas_status mdas_tune_batch(const mdas_system_desc *const *descs, int32_t n_systems, const double *skins,
-                            int32_t n_skins, const int64_t *waves, int32_t n_waves, int32_t md_steps,
-                            int32_t swap_trials, int32_t rounds, double *us_per_step, double *best_skin,
-                            int32_t *best_partitioned, int64_t *best_wave) {
+                            int32_t n_skins, const int64_t *waves, int32_t n_waves, const int32_t *lanes,
+                            int32_t n_lanes, int32_t md_steps, int32_t swap_trials, int32_t rounds,
+                            double *us_per_step, double *best_skin, int32_t *best_partitioned, int64_t *best_wave,
+                            int32_t *best_lanes) {
     mdas_status st = tune_args("tune_batch", descs, n_systems, skins, n_skins, md_steps, swap_trials, rounds);
     if (st != MDAS_OK) return st;
-    if (!waves || n_waves <= 0 || !us_per_step || !best_skin || !best_partitioned || !best_wave)
+    if (!waves || n_waves <= 0 || !lanes || n_lanes <= 0 || !us_per_step || !best_skin || !best_partitioned ||
+        !best_wave || !best_lanes)
         return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_batch: bad argument");
     for (int v = 0; v < n_waves; ++v)
         if (waves[v] < 0) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_batch: a wave size is < 0");
+    for (int v = 0; v < n_lanes; ++v)
+        if (!nl_lanes_ok(lanes[v])) return fail(nullptr, MDAS_ERR_INVALID_ARG, "tune_batch: lanes must be 2 or 4");
     int best = -1;
-    const int nc = n_skins * 2 * n_waves;
+    const int per_skin = 2 * n_waves * n_lanes;
+    const int nc = n_skins * per_skin;
     for (int c = 0; c < nc; ++c) {
-        const int ks = c / (2 * n_waves), kl = (c / n_waves) % 2, kw = c % n_waves;
-        st = time_batch(descs, n_systems, skins[ks], kl, (long long)waves[kw], md_steps, swap_trials, rounds,
-                        &us_per_step[c]);
+        const int ks = c / per_skin, kl = (c / (n_waves * n_lanes)) % 2, kw = (c / n_lanes) % n_waves,
+                  kn = c % n_lanes;
+        st = time_batch(descs, n_systems, skins[ks], kl, (long long)waves[kw], lanes[kn], md_steps, swap_trials,
+                        rounds, &us_per_step[c]);
         if (st != MDAS_OK) return st;
         if (best < 0 || us_per_step[c] < us_per_step[best]) best = c;
     }
-    *best_skin = skins[best / (2 * n_waves)];
-    *best_partitioned = (best / n_waves) % 2;
-    *best_wave = waves[best % n_waves];
+    *best_skin = skins[best / per_skin];
+    *best_partitioned = (best / (n_waves * n_lanes)) % 2;
+    *best_wave = waves[(best / n_lanes) % n_waves];
+    *best_lanes = lanes[best % n_lanes];
     return MDAS_OK;
 }
 
@@ -1712,6 +1738,16 @@ mdas_status mdas_set_partitioned(mdas_system *s, int32_t enable) {
     if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_partitioned: NULL system");
     s->partition = enable != 0;
     return MDAS_OK;
+}
+
+mdas_status mdas_set_list_lanes(mdas_system *s, int32_t lanes) {
+    if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_list_lanes: NULL system");
+    if (!nl_lanes_ok(lanes)) return fail(s, MDAS_ERR_INVALID_ARG, "set_list_lanes: 2 or 4 list columns per bead");
+    if (lanes == s->lanes) return MDAS_OK;
+    s->lanes = lanes;
+    // the system's own batch takes the new step shape (its step items change);
+    // the pair list is built again at the next MD call
+    return refill_batch(*s->solo, {s});
 }
 
 mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out) {
@@ -1831,8 +1867,8 @@ size_t arena_estimate(const mdas_system_desc *d) {
                (16 + 8 + 72 + 4 + 128 + 64) * (size_t)MAX_ROUND_TRIALS + sizeof(TrialRec) * (size_t)LOG_CAP + 512 +
                32 * MAX_DRAW_STEPS + 24 * n + 16 * std::max(d->n_lipids, 1) + 16 * RDF_MAX_BINS + 8;
     const ListDims ld = list_dims(d, shrink);
-    t += 12ull * ld.n_lcells + 4ull * ld.n_lcells * ld.lcapc + 4 * n + 4 * n + 32 * n + 16 * n + 4ull * NL_G * n +
-         4ull * (ld.lcap / NL_G) * ld.lrow + 4ull * NL_PART * n + 8ull * ((n + NL_BEADS - 1) / NL_BEADS / 32 + 1);
+    t += 12ull * ld.n_lcells + 4ull * ld.n_lcells * ld.lcapc + 4 * n + 4 * n + 32 * n + 16 * n + 4ull * NL_LANES_MAX * n +
+         4ull * ld.lcap * ld.npad + 4ull * NL_PART * n + 8ull * ((n + NL_BEADS_MIN - 1) / NL_BEADS_MIN / 32 + 1);
     return t + 51 * 256;
 }
 

@@ -16,9 +16,15 @@ constexpr int PAIR_THREADS = 128;      // threads per cell in the pair kernel
 constexpr int STAGE_CAP = 320;         // neighbour beads staged per chunk (27 cells, pruned)
 constexpr int QCAP = 24;               // per-thread hit queue of the pair kernel
 constexpr int BEAD_BLOCK = 128;        // beads per block of per-bead kernels
-constexpr int NL_G = 4;                // threads per bead in the pair-list step kernel
-constexpr int NL_BLOCK = 128;          // threads per block of the pair-list step kernel
-constexpr int NL_BEADS = NL_BLOCK / NL_G;
+// Pair-list step shape: an item of NL_BLOCK threads takes NL_BLOCK / G beads,
+// G threads (list columns) per bead; G is 4 by default (a single system's
+// latency-bound step) or 2 (batches, bound by throughput), a template
+// parameter of every list kernel.
+constexpr int NL_BLOCK = 128;          // threads per step item
+constexpr int NL_LANES = 4;            // list columns per bead unless a system asks for another count
+constexpr int NL_LANES_MAX = 4;        // the most list columns per bead of any shape (array sizes)
+constexpr int NL_BEADS_MIN = NL_BLOCK / NL_LANES_MAX;   // beads of the smallest step item
+__host__ __device__ constexpr bool nl_lanes_ok(int g) { return g == 2 || g == 4; }
 constexpr int NL_PART = 8;             // bonded partners per bead at most
 constexpr int NLB_STAGE = 384;         // candidates staged per chunk by the list build (two chunks for a typical cell)
 constexpr int CELLS_PER_SORT_BLOCK = 4;
@@ -88,8 +94,10 @@ struct Params {
     // was built, found on a grid of cells of edge >= rl
     int ln[3], n_lcells, lcapc;        // list-build cells per edge, cells, bead capacity of a cell
     unsigned long long lcwu[3];        // floor(2^32 / ln_d): list-build cell width in fixed-point units
-    int lcap, lrow;                    // entries per bead (NL_G columns of lcap / NL_G rows), row stride
-    int mark_words;                    // 32-bit words of one step-item bitmap (one bit per NL_BEADS list slots)
+    int lcap, npad;                    // entries per bead (G columns of lcap / G rows); beads padded to 32
+                                       // (a list row of G columns per bead spans npad * G entries)
+    int mark_words;                    // 32-bit words of one step-item bitmap (one bit per step item; sized
+                                       // for items of NL_BEADS_MIN beads)
     double sc_delta;                   // Eq. 4 soft-core delta (nm^2) of the alchemical path, 0: linear path
     float sc_deltaf;
     double rl, rl2;
@@ -233,8 +241,8 @@ struct SysDev {
     int *lk;                           // [n] id -> list index
     uint4 *lpos;                       // [2 n] positions in list order, two buffers
     uint4 *xref;                       // [n] positions when the list was built
-    int *nl_n;                         // [n * NL_G] entries in each column of each bead's list
-    int *nl;                           // row r of column g of bead k at [r * lrow + k * NL_G + g]
+    int *nl_n;                         // [n * G] entries in each column of each bead's list
+    int *nl;                           // row r of column g of bead k at [r * npad * G + k * G + g]
     int *bslot;                        // [n * NL_PART] list indices of the bonded partners
     unsigned *tmark;                   // [2 * mark_words] step items an exchange trial can change, per trial parity
     int n_bead_blocks;
@@ -298,6 +306,7 @@ struct LaunchCtx {
     unsigned int *bticket;    // device: last-block ticket over the whole batch
     bool soft;                // a system of the batch takes the soft-core alchemical path
     bool pc;                  // a system of the batch has pressure coupling (MD steps sum the virial)
+    int lanes = NL_LANES;     // list columns per bead of the batch's pair lists (nl_lanes_ok)
     // partitioned batches (the persistent kernel): device buffer of
     // part_layout(n_sys, part_groups) bytes (per system its groups, map ranges and
     // barrier state; the system of every group), or nullptr
@@ -328,7 +337,7 @@ inline PartLayout part_layout(int n_sys, int groups) {
     return l;
 }
 // groups of 128 threads in one launch of the persistent MD kernel on this device (0 if it cannot run)
-int md_run_groups(int precision, int mode);
+int md_run_groups(int precision, int mode, int lanes);
 
 cudaError_t setup_kernels();
 void launch_cells(const LaunchCtx &L);
@@ -344,8 +353,8 @@ void launch_total_force(const LaunchCtx &L, double *out, int sys_index);
 void launch_thermostat(const LaunchCtx &L);
 void launch_nl_build(const LaunchCtx &L);
 void launch_nl_step(const LaunchCtx &L, bool lambda);
-int md_run_blocks(int precision, int mode);   // mode: 0 plain MD, 1 linear alchemical path, 2 soft-core path,
-                                              // 3 plain MD with pressure coupling
+int md_run_blocks(int precision, int mode, int lanes);   // mode: 0 plain MD, 1 linear alchemical path,
+                                                         // 2 soft-core path, 3 plain MD with pressure coupling
 cudaError_t launch_md_run(const LaunchCtx &L, bool lambda, int n_steps, int swap_every, int trial_off, int lam_M,
                           int lam_off, double dlam, void *sync);
 size_t md_run_sync_bytes();

@@ -44,7 +44,7 @@ __device__ inline double block_sum(double v, double *sh) {
 
 struct TrialSmem {
     double sh[GRP / 32];
-    int it_beg[2 * MAXT * NL_G + 1];
+    int it_beg[2 * MAXT * NL_LANES_MAX + 1];
     int chg_id[2 * MAXT], chg_new[2 * MAXT], chg_old[2 * MAXT], chg_k[2 * MAXT];
     uint4 chg_pos[2 * MAXT];
     int nchg, m, ta, tb, last, accept;
@@ -82,7 +82,9 @@ __device__ inline double group_sum(double v, const Grp &g, double *sh) {
 // mark_seq; the decision is published by the trial counter only after the
 // exchange is applied.  Every trial clears the other bitmap for the next one
 // (its last readers finished before this trial started).
+template <int G>
 __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp &g, TrialSmem &sm, bool mark) {
+    constexpr int NL_G = G, NL_BEADS = NL_BLOCK / G;
     const Params &P = *S.p;
     Counters &C = *S.c;
     const int t = g.t, lane = t & 31;
@@ -156,7 +158,7 @@ __device__ inline void trial_nl_part(const SysDev &S, int p, int par, const Grp 
             if (sm.it_beg[mid] <= f) lo = mid; else hi = mid - 1;
         }
         const int ci = lo / NL_G, q = lo % NL_G, row = f - sm.it_beg[lo];
-        const int kj = MDAS_IDX(*S.c, S.nl[(size_t)row * P.lrow + (size_t)sm.chg_k[ci] * NL_G + q], P.n);
+        const int kj = MDAS_IDX(*S.c, S.nl[(size_t)row * P.npad * NL_G + (size_t)sm.chg_k[ci] * NL_G + q], P.n);
         if (mark) atomicOr(&mk[kj / NL_BEADS / 32], 1u << (kj / NL_BEADS % 32));
         const uint4 pi = sm.chg_pos[ci], pj = cur[kj];
         const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
@@ -254,8 +256,10 @@ __device__ __forceinline__ double pair_dw_soft(const Params &P, int oi, int oj, 
 //
 // On the soft-core path (sc_delta > 0) a pair adds its work over the lambda
 // step l0 -> l1 instead (pair_dw_soft), which the caller adds to w as it is.
+template <int G>
 __device__ inline double mdas_work_part(const SysDev &S, int x, int par, const Grp &g, double *sh, double l0,
                                         double l1) {
+    constexpr int NL_G = G;
     const Params &P = *S.p;
     const Counters &C = *S.c;
     static_assert(NL_G <= 8 && 8 % NL_G == 0 && GRP == 128, "at most eight list columns per bead, 128 threads");
@@ -271,7 +275,7 @@ __device__ inline double mdas_work_part(const SysDev &S, int x, int par, const G
         if (oi != ni) {
             const int rows = S.nl_n[(size_t)ki * NL_G + col];
             for (int r = sub; r < rows; r += TPC) {
-                const int kj = MDAS_IDX(*S.c, S.nl[(size_t)r * P.lrow + (size_t)ki * NL_G + col], P.n);
+                const int kj = MDAS_IDX(*S.c, S.nl[(size_t)r * P.npad * NL_G + (size_t)ki * NL_G + col], P.n);
                 const uint4 pj = cur[kj];
                 const int ix = (int)(pi.x - pj.x), iy = (int)(pi.y - pj.y), iz = (int)(pi.z - pj.z);
                 const float fx = (float)ix * P.qsf[0], fy = (float)iy * P.qsf[1], fz = (float)iz * P.qsf[2];

@@ -224,15 +224,17 @@ __device__ void set_lipid_type(const SysDev &S, const Params &P, int l, int lt) 
 
 
 // One exchange trial per system from the pair list: grid (TRIAL_PARTS, n_sys).
+template <int G>
 __global__ void __launch_bounds__(GRP) k_trial_nl(const SysDev *__restrict__ sys) {
     __shared__ TrialSmem sm;
     const SysDev &S = sys[blockIdx.y];
-    trial_nl_part(S, blockIdx.x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm, false);
+    trial_nl_part<G>(S, blockIdx.x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm, false);
 }
 
 void launch_trial_nl(const LaunchCtx &L) {
     dim3 g(TRIAL_PARTS, L.n_sys);
-    k_trial_nl<<<g, 128, 0, L.stream>>>(L.sys);
+    if (L.lanes == 2) k_trial_nl<2><<<g, 128, 0, L.stream>>>(L.sys);
+    else k_trial_nl<4><<<g, 128, 0, L.stream>>>(L.sys);
 }
 
 
@@ -402,12 +404,13 @@ __global__ void __launch_bounds__(128) k_mdas_dE(const SysDev *__restrict__ sys,
 
 // The same sum from the pair list (valid right after an MD block), one block
 // per lipid x: grid (2 * MAX_PAIRS, n_sys).
+template <int G>
 __global__ void __launch_bounds__(128) k_mdas_dE_nl(const SysDev *__restrict__ sys, double l0, double l1) {
     const SysDev &S = sys[blockIdx.y];
     __shared__ double sh[GRP / 32];
     const int x = blockIdx.x;
     if (x >= 2 * S.c->n_pairs) return;
-    const double w = mdas_work_part(S, x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sh, l0, l1);
+    const double w = mdas_work_part<G>(S, x, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sh, l0, l1);
     if (threadIdx.x == 0) S.c->w_part[x] = w;
 }
 
@@ -427,7 +430,8 @@ __global__ void k_mdas_accumulate(const SysDev *__restrict__ sys, double dlambda
 
 void launch_mdas_dE_nl(const LaunchCtx &L, double l0, double l1, double dlambda) {
     dim3 g(2 * MAX_PAIRS, L.n_sys);
-    k_mdas_dE_nl<<<g, 128, 0, L.stream>>>(L.sys, l0, l1);
+    if (L.lanes == 2) k_mdas_dE_nl<2><<<g, 128, 0, L.stream>>>(L.sys, l0, l1);
+    else k_mdas_dE_nl<4><<<g, 128, 0, L.stream>>>(L.sys, l0, l1);
     k_mdas_accumulate<<<L.n_sys, 32, 0, L.stream>>>(L.sys, dlambda, -1, 1);
 }
 

@@ -112,7 +112,7 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_wait_timeout_probe", "mdas_box", "mdas_alchemical_move_trace", "mdas_interleaflet_move",
            "mdas_device_ptrs", "mdas_server_add_patch", "mdas_server_submit_to", "mdas_server_patch_state",
            "mdas_server_remove_patch", "mdas_tune_batch", "mdas_set_partitioned", "mdas_set_batch_wave",
-           "mdas_get_state_packed", "mdas_set_state_packed"]
+           "mdas_get_state_packed", "mdas_set_state_packed", "mdas_set_list_lanes"]
 
 
 def library_path() -> str:
@@ -492,6 +492,11 @@ class System:
         status "timeout"); the system then needs set_state or resume."""
         self._ck(lib().mdas_wait_timeout_probe(self._ptr))
 
+    def set_list_lanes(self, lanes):
+        """List columns (threads) per bead of this system's pair-list step, 2
+        or 4 (mdas_set_list_lanes); all systems of a batch must agree."""
+        self._ck(lib().mdas_set_list_lanes(self._ptr, int(lanes)))
+
     def set_partitioned(self, on=True):
         """Batches give this system its own share of the persistent kernel's
         groups (mdas_set_partitioned; the default) or run it in lockstep."""
@@ -646,12 +651,12 @@ def tune_list_skin(models, skins=(0.2, 0.25, 0.3, 0.35, 0.4), md_steps=100, swap
     return best.value, dict(zip(cand.tolist(), us.tolist()))
 
 
-def tune_batch(models, skins=(0.2, 0.3, 0.4), waves=(0,), md_steps=100, swap_trials=0, rounds=3, precision="fp32",
-               stream=None):
-    """Time batches of `models` at every (list skin, layout, wave size)
-    candidate (mdas_tune_batch); returns (best skin, best layout
-    partitioned?, best wave size, {(skin, partitioned, wave): us per MD
-    step})."""
+def tune_batch(models, skins=(0.2, 0.3, 0.4), waves=(0,), lanes=(2, 4), md_steps=100, swap_trials=0, rounds=3,
+               precision="fp32", stream=None):
+    """Time batches of `models` at every (list skin, layout, wave size, list
+    lanes) candidate (mdas_tune_batch); returns (best skin, best layout
+    partitioned?, best wave size, best lanes, {(skin, partitioned, wave,
+    lanes): us per MD step})."""
     prec = MDAS_FP64 if precision in ("fp64", MDAS_FP64, "f64") else MDAS_FP32
     keep, descs = [], []
     stream = _current_stream() if stream is None else int(stream)
@@ -664,13 +669,16 @@ def tune_batch(models, skins=(0.2, 0.3, 0.4), waves=(0,), md_steps=100, swap_tri
     arr = (C.POINTER(Desc) * len(descs))(*descs)
     cand = np.ascontiguousarray(skins, np.float64)
     wv = np.ascontiguousarray(waves, np.int64)
-    nw = len(wv)
-    us = np.zeros(2 * len(cand) * nw, np.float64)
-    best, part, wave = C.c_double(), C.c_int32(), C.c_int64()
-    _check(lib().mdas_tune_batch(arr, len(descs), _p(cand), len(cand), _p(wv), nw, int(md_steps), int(swap_trials),
-                                 int(rounds), _p(us), C.byref(best), C.byref(part), C.byref(wave)))
-    table = {(float(cand[c // (2 * nw)]), bool((c // nw) % 2), int(wv[c % nw])): float(us[c]) for c in range(len(us))}
-    return best.value, bool(part.value), wave.value, table
+    ln = np.ascontiguousarray(lanes, np.int32)
+    nw, nn = len(wv), len(ln)
+    us = np.zeros(2 * len(cand) * nw * nn, np.float64)
+    best, part, wave, lane = C.c_double(), C.c_int32(), C.c_int64(), C.c_int32()
+    _check(lib().mdas_tune_batch(arr, len(descs), _p(cand), len(cand), _p(wv), nw, _p(ln), nn, int(md_steps),
+                                 int(swap_trials), int(rounds), _p(us), C.byref(best), C.byref(part), C.byref(wave),
+                                 C.byref(lane)))
+    table = {(float(cand[c // (2 * nw * nn)]), bool((c // (nw * nn)) % 2), int(wv[(c // nn) % nw]), int(ln[c % nn])):
+             float(us[c]) for c in range(len(us))}
+    return best.value, bool(part.value), wave.value, lane.value, table
 
 
 def philox(k0, k1, c1, c2, c3, n):

@@ -40,14 +40,16 @@ def test_skin_does_not_change_the_trajectory_fp64():
     assert np.abs(d).max() <= 64, np.abs(d).max()
 
 
+@pytest.mark.parametrize("lanes", [4, 2])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_persistent_and_separate_launches_agree(prec):
+def test_persistent_and_separate_launches_agree(prec, lanes):
     """The persistent kernel and the separate kernels give the same bits, with
-    trials, in one call or split over several."""
+    trials, in one call or split over several (both step shapes)."""
     m = synth.mcmd_small()
     runs = []
     for persistent, calls in ((True, [36]), (False, [9, 9, 9, 9]), (True, [12, 24])):
         s = mdas.System(m, precision=prec)
+        s.set_list_lanes(lanes)
         s.set_persistent(persistent)
         for n in calls:
             s.md_steps(n, swap_every=3)
@@ -81,14 +83,16 @@ def test_one_step_after_rebuild_matches_oracle_fp64():
     assert np.abs(got["vel"] - so["vel"]).max() < 1e-10
 
 
+@pytest.mark.parametrize("lanes", [4, 2])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("which", ["small", "large"])
-def test_step_kernel_forces_match_oracle(prec, which):
+def test_step_kernel_forces_match_oracle(prec, which, lanes):
     """The MD step's own forces: from rest without a thermostat one step gives
     v = F dt / m exactly up to one rounding, so F = v m / dt is compared with
     the oracle's forces at the force tolerance."""
     m = synth.mcmd_small() if which == "small" else synth.mcmd_large()
     s = mdas.System(m, precision=prec, tau_t=0.0)
+    s.set_list_lanes(lanes)
     s.md_steps(5, swap_every=0)                    # a state the list was built for earlier
     st = s.get_state()
     s.set_state(pos_u=st["pos_u"], vel=np.zeros_like(st["vel"]), ltype=st["ltype"], step=st["step"])
@@ -124,8 +128,9 @@ def test_tune_list_skin_times_every_candidate():
         mdas.tune_list_skin(ms[:1], skins=(0.3, 0.0), md_steps=10)
 
 
+@pytest.mark.parametrize("lanes", [4, 2])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_trials_beside_the_next_step_match_separate_launches(prec):
+def test_trials_beside_the_next_step_match_separate_launches(prec, lanes):
     """In the persistent kernel each exchange trial runs beside the next MD
     step; the items it can change wait for its decision and, after an accepted
     exchange, sum their forces again.  The result is the bits of trials run
@@ -134,6 +139,7 @@ def test_trials_beside_the_next_step_match_separate_launches(prec):
     runs = []
     for persistent in (True, False):
         s = mdas.System(m, precision=prec, temperature=450.0)
+        s.set_list_lanes(lanes)
         s.set_persistent(persistent)
         s.md_steps(150, swap_every=1)
         s.md_steps(7, swap_every=2)
@@ -165,8 +171,9 @@ def test_trials_across_segment_boundaries():
     assert ca["accepted"] == cb["accepted"]
 
 
+@pytest.mark.parametrize("lanes", [4, 2])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_alchemical_trajectory_in_one_run_matches_separate_launches(prec):
+def test_alchemical_trajectory_in_one_run_matches_separate_launches(prec, lanes):
     """The MDAS trajectory (lambda advanced and each block's work term added
     inside the MD run) gives the same work, decision and bits in the
     persistent kernel as with separate launches."""
@@ -174,6 +181,7 @@ def test_alchemical_trajectory_in_one_run_matches_separate_launches(prec):
     out = []
     for persistent in (True, False):
         s = mdas.System(m, precision=prec)
+        s.set_list_lanes(lanes)
         s.set_persistent(persistent)
         s.md_steps(10, swap_every=0)
         res = [s.alchemical_move(4, 6, 3) for _ in range(2)]
@@ -184,18 +192,23 @@ def test_alchemical_trajectory_in_one_run_matches_separate_launches(prec):
     assert np.array_equal(sa["pos_u"], sb["pos_u"]) and np.array_equal(sa["vel"], sb["vel"])
 
 
-def test_tune_batch_times_skins_and_layouts_with_the_same_bits():
-    """The batch tuner times every (skin, layout, wave) candidate; the layouts
-    of a batch (partitioned, lockstep) and its waves give the same bits."""
+@pytest.mark.parametrize("lanes", [4, 2])
+def test_tune_batch_times_skins_and_layouts_with_the_same_bits(lanes):
+    """The batch tuner times every (skin, layout, wave, lanes) candidate; the
+    layouts of a batch (partitioned, lockstep) and its waves give the same
+    bits, for either step shape."""
     ms = synth.replica_set(6, lo=600, hi=2048, seed=12)
-    best, part, wave, us = mdas.tune_batch(ms, skins=(0.25, 0.3), waves=(0, 60_000), md_steps=20, swap_trials=8,
-                                           rounds=1)
-    assert set(us) == {(sk, p, w) for sk in (0.25, 0.3) for p in (False, True) for w in (0, 60_000)}
-    assert us[(best, part, wave)] == min(us.values())
+    if lanes == 4:
+        best, part, wave, lane, us = mdas.tune_batch(ms, skins=(0.25, 0.3), waves=(0, 60_000), lanes=(2, 4),
+                                                     md_steps=20, swap_trials=8, rounds=1)
+        assert set(us) == {(sk, p, w, n) for sk in (0.25, 0.3) for p in (False, True) for w in (0, 60_000)
+                           for n in (2, 4)}
+        assert us[(best, part, wave, lane)] == min(us.values())
     out = []
     for layout, wv in ((True, 0), (False, 0), (True, 60_000)):
         sy = [mdas.System(m) for m in ms]
         for s in sy:
+            s.set_list_lanes(lanes)
             s.set_partitioned(layout)
             s.set_batch_wave(wv)
         mdas.batch_run(sy, 15, 10)
@@ -206,3 +219,30 @@ def test_tune_batch_times_skins_and_layouts_with_the_same_bits():
         for b in runs[1:]:
             assert np.array_equal(a["pos_u"], b["pos_u"]) and np.array_equal(a["vel"], b["vel"])
             assert np.array_equal(a["ltype"], b["ltype"]) and a["trial"] == b["trial"]
+
+
+def test_list_lanes_switch_and_refusals():
+    """A system may change its step shape between MD calls (its pair list is
+    built again for the new shape); the systems of a batch must agree, and
+    only 2 or 4 list columns per bead exist."""
+    m = synth.mcmd_small()
+    a = mdas.System(m)
+    a.md_steps(10, swap_every=2)
+    b0 = a.counters()["list_builds"]
+    a.set_list_lanes(2)
+    a.md_steps(10, swap_every=2)
+    c = a.counters()
+    assert c["md_steps"] == 20 and c["trials"] == 10 and c["list_builds"] > b0
+    st = a.get_state()
+    to, _ = oracle.Oracle(m).energy(st["pos_u"], ltype=st["ltype"], forces=False)
+    assert abs(a.energy()["potential"] - to["total"]) <= 1e-9 * abs(to["total"])
+    with pytest.raises(mdas.MdasError) as err:
+        a.set_list_lanes(3)
+    assert err.value.status == 1
+    b = mdas.System(m)
+    with pytest.raises(mdas.MdasError) as err:
+        mdas.batch_run([a, b], 5, 0)
+    assert err.value.status == 1
+    b.set_list_lanes(2)
+    mdas.batch_run([a, b], 5, 0)
+    assert a.counters()["md_steps"] == 25 and b.counters()["md_steps"] == 5

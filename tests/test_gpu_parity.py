@@ -154,10 +154,13 @@ def test_one_step_map(prec, small):
         assert dpos.max() <= 256 and dv < 2e-5, (dpos.max(), dv)
 
 
-def test_fp64_trajectory_with_trials(small):
+@pytest.mark.parametrize("lanes", [4, 2])
+def test_fp64_trajectory_with_trials(small, lanes):
     """200 steps at 20 fs with a trial every 10 steps, FP64 (the 128-lipid MC-MD
-    workload): trial decisions identical, states close at the end."""
+    workload), both step shapes: trial decisions identical, states close at
+    the end."""
     s = mdas.System(small, precision="fp64")
+    s.set_list_lanes(lanes)
     s.md_steps(200, swap_every=10)
     st = s.get_state()
     rec = s.trial_log(0, 20)
@@ -242,17 +245,21 @@ def test_deterministic_rerun(large):
     assert out[0] == out[1]
 
 
-def test_batch_equals_solo():
+@pytest.mark.parametrize("lanes", [4, 2])
+def test_batch_equals_solo(lanes):
     ms = [synth.patch(n, 2 + (n % 2), seed=50 + n, system_id=k) for k, n in enumerate([130, 258, 400])]
     solo = []
     for m in ms:
         s = mdas.System(m)
+        s.set_list_lanes(lanes)
         s.md_steps(12)
         s.swap_trials(20, log=False)
         st = s.get_state()
         solo.append(st)
         s.close()
     sy = [mdas.System(m) for m in ms]
+    for s in sy:
+        s.set_list_lanes(lanes)
     mdas.batch_run(sy, 12, 20)
     for s, st in zip(sy, solo):
         b = s.get_state()
