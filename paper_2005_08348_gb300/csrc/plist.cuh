@@ -421,6 +421,14 @@ __device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, Bui
     g.sync();
 }
 
+// A list entry: read once per step, so it skips L1 (which keeps the
+// positions and tables the step reuses)
+__device__ __forceinline__ int ld_list(const int *p) {
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // ------------------------------------------------------------- step item
 // One MD step of the beads k0 .. k0 + NL_BEADS - 1 (list order): positions
 // read from buffer par, written to buffer par ^ 1 and to the id-ordered
@@ -444,8 +452,8 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     // (rows 0 .. 3 always exist; entries past the end hold valid indices)
     const int *__restrict__ lst = S.nl + (size_t)k * NL_G + gl;
     const size_t rs = (size_t)P.npad * G;
-    int j0 = MDAS_IDX(C, __ldg(lst), n), j1 = MDAS_IDX(C, __ldg(lst + rs), n);
-    int j2 = MDAS_IDX(C, __ldg(lst + 2 * rs), n), j3 = MDAS_IDX(C, __ldg(lst + 3 * rs), n);
+    int j0 = MDAS_IDX(C, ld_list(lst), n), j1 = MDAS_IDX(C, ld_list(lst + rs), n);
+    int j2 = MDAS_IDX(C, ld_list(lst + 2 * rs), n), j3 = MDAS_IDX(C, ld_list(lst + 3 * rs), n);
     uint4 pi = make_uint4(0u, 0u, 0u, 0u);
     int cnt = 0, id = 0;
     if (valid) {
@@ -565,7 +573,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
     // 4 further on and the index of the row 8 further on, so every load has
     // a whole group of pairs to arrive (entries past the end read slot 0)
     const int rows = cnt;
-    auto idx = [&](int r) { return r < rows ? MDAS_IDX(C, __ldg(lst + (size_t)r * rs), n) : 0; };
+    auto idx = [&](int r) { return r < rows ? MDAS_IDX(C, ld_list(lst + (size_t)r * rs), n) : 0; };
     for (int pass = 0;; ++pass) {
         j0 = idx(4); j1 = idx(5); j2 = idx(6); j3 = idx(7);
         for (int m = 0; m < rows; m += 4) {
