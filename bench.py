@@ -334,6 +334,7 @@ def run_gpu(args):
         out["mutations_4608_lipids"] = _extra(mutation_benchmark, stream)
         out["head_rdf_4608_lipids"] = _extra(rdf_benchmark, stream)
         out["npt_1152_lipids"] = _extra(npt_benchmark, stream)
+        out["fp64_mcmd_128_lipids"] = _extra(fp64_benchmark, stream)
         out["served"] = _extra(serving_benchmark, stream)
     if not args.no_cpu_baseline:
         import oracle
@@ -523,6 +524,25 @@ def npt_benchmark(stream, n_steps=1000):
             out["pressure_bar_last_update"] = [round(float(x), 2) for x in p]
         s.close()
     out["npt_over_nvt_time"] = out["nvt_md_steps_per_s"] / out["npt_md_steps_per_s"]
+    return out
+
+
+def fp64_benchmark(stream, rounds=10):
+    """Plain MC-MD in FP64 on the 128-lipid bilayer: rounds of 200 MD steps
+    with one exchange trial every 10 steps (the FP64 workload the oracle runs
+    in lockstep in the parity tests), and the same rounds in FP32."""
+    from paper_2005_08348_gb300 import mdas, synth
+    m = synth.mcmd_small()
+    out = {"workload": f"{m.n_lipids} lipids, {m.n_beads} beads; 200 MD steps + 20 trials per round"}
+    for prec in ("fp64", "fp32"):
+        s = mdas.System(m, precision=prec, stream=stream.cuda_stream)
+        s.md_steps(200, swap_every=10)
+        pairs = s.energy()["pairs"]
+        t = _elapsed(stream, lambda: [s.md_steps(200, swap_every=10) for _ in range(rounds)])
+        out[f"{prec}_md_steps_per_s"] = 200 * rounds / t
+        out[f"{prec}_pair_interactions_per_s"] = pairs * 200 * rounds / t
+        out[f"{prec}_swap_trials_per_s"] = 20 * rounds / t
+        s.close()
     return out
 
 

@@ -266,6 +266,9 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
 // Refill a reusable batch with a new set of systems: device arrays only grow.
 mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     mdas_system *s = v[0];
+    for (const mdas_system *x : v)             // checked before the batch changes
+        if (x->precision != s->precision || x->stream != s->stream || x->lanes != s->lanes)
+            return fail(s, MDAS_ERR_INVALID_ARG, "batch: systems differ in precision, stream or list lanes");
     b.sys = v;
     b.precision = v[0]->precision;
     b.stream = v[0]->stream;
@@ -1555,6 +1558,15 @@ mdas_status mdas_batch_run(mdas_system *const *systems, int32_t n_systems, int32
             mdas_status st = make_batch(w, b);
             if (st != MDAS_OK) return st;
             it = g_batches.emplace(w, std::move(b)).first;
+        } else {
+            // a system changed its step shape since the batch was made: the
+            // batch's step items follow (and the systems must still agree)
+            bool same = true;
+            for (auto *x : w) same = same && x->lanes == it->second->lanes;
+            if (!same) {
+                mdas_status st = refill_batch(*it->second, w);
+                if (st != MDAS_OK) return st;
+            }
         }
         *out = it->second.get();
         return MDAS_OK;
@@ -1744,10 +1756,13 @@ mdas_status mdas_set_list_lanes(mdas_system *s, int32_t lanes) {
     if (!s) return fail(nullptr, MDAS_ERR_INVALID_ARG, "set_list_lanes: NULL system");
     if (!nl_lanes_ok(lanes)) return fail(s, MDAS_ERR_INVALID_ARG, "set_list_lanes: 2 or 4 list columns per bead");
     if (lanes == s->lanes) return MDAS_OK;
+    const int before = s->lanes;
     s->lanes = lanes;
     // the system's own batch takes the new step shape (its step items change);
     // the pair list is built again at the next MD call
-    return refill_batch(*s->solo, {s});
+    mdas_status st = refill_batch(*s->solo, {s});
+    if (st != MDAS_OK) s->lanes = before;
+    return st;
 }
 
 mdas_status mdas_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n, uint32_t *out) {

@@ -246,3 +246,11 @@ def test_list_lanes_switch_and_refusals():
     b.set_list_lanes(2)
     mdas.batch_run([a, b], 5, 0)
     assert a.counters()["md_steps"] == 25 and b.counters()["md_steps"] == 5
+    # the batch of these two systems follows a later change of shape (and its agreement check too)
+    a.set_list_lanes(4)
+    with pytest.raises(mdas.MdasError) as err:
+        mdas.batch_run([a, b], 5, 0)
+    assert err.value.status == 1
+    b.set_list_lanes(4)
+    mdas.batch_run([a, b], 5, 0)
+    assert a.counters()["md_steps"] == 30 and b.counters()["md_steps"] == 10

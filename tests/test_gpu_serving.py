@@ -157,3 +157,19 @@ def test_resident_patch_admission_and_removal():
     with pytest.raises(mdas.MdasError):
         sv.submit_to(pid, mdas.JOB_MD, n=5)               # removed
     sv.remove_patch(pid2)
+
+
+def test_largest_patch_same_alone_and_in_the_mix():
+    """Jobs on a patch at the served workload's largest size (16384 lipids,
+    ~413k beads) beside small ones: MD and MDAS results on it, and the small
+    jobs' results, are the same alone and in the mix."""
+    big = synth.patch(16384, 3, seed=777, system_id=40)
+    small = patches()[:2]
+    js = [(big, mdas.JOB_MD, 30), (small[0], mdas.JOB_SWAPS, 64), (small[1], mdas.JOB_MD, 25), (big, mdas.JOB_MDAS, 0)]
+    mix = run(mdas.Server(16 * GB, max_active=4, md_quantum=10, keep_state_hash=True), js, stagger=True)
+    for (p, k, n), r in zip(js, mix):
+        alone = run(mdas.Server(16 * GB, max_active=1, md_quantum=25, keep_state_hash=True), [(p, k, n)],
+                    stagger=False)[0]
+        assert r["state_hash"] == alone["state_hash"], (k, n)
+        for key in ("md_steps", "trials", "accepted", "w", "move_accepted"):
+            assert r[key] == alone[key], key
