@@ -121,7 +121,7 @@ typedef struct {
 
 typedef struct {
     int64_t trials, null_trials, accepted;
-    int32_t rounds;                    /* speculation rounds used by the batched evaluation */
+    int32_t rounds;                    /* speculation rounds used (one per trial on the sequential path) */
 } mdas_swap_stats;
 
 #define MDAS_MAX_PAIRS 64
@@ -188,9 +188,10 @@ mdas_status mdas_md_steps(mdas_system *s, int64_t n_steps, int32_t swap_every);
 
 /* n_trials exchange trials at the current coordinates (Sec. 2: a random pair
  * of lipids of different types exchange types, coordinates unchanged,
- * accepted with min(1, exp(-dE/kT)), Eq. 1), evaluated in batched rounds whose
- * result equals processing the trials one after another.  st and log
- * ([n_trials]) may be NULL. */
+ * accepted with min(1, exp(-dE/kT)), Eq. 1), with the result of processing
+ * the trials one after another: on the path mdas_set_trial_path selects
+ * (from the pair lists one after another, or in speculative rounds).  st and
+ * log ([n_trials]) may be NULL. */
 mdas_status mdas_swap_trials(mdas_system *s, int32_t n_trials, mdas_swap_stats *st, mdas_trial_record *log);
 
 /* Copy trial records first .. first+n-1 of the system's trial log (kept for
@@ -384,6 +385,24 @@ mdas_status mdas_set_batch_wave(mdas_system *s, int64_t max_beads);
  * order (FP32 bits may differ between shapes, not within one).  Errors:
  * MDAS_ERR_INVALID_ARG for a NULL system or lanes other than 2 or 4. */
 mdas_status mdas_set_list_lanes(mdas_system *s, int32_t lanes);
+
+/* How exchange trials run when several are asked for at once
+ * (mdas_swap_trials, mdas_batch_run, served swap jobs): MDAS_TRIALS_SPECULATIVE
+ * evaluates every pending trial against the current types in rounds, and
+ * resolves in order each one that no earlier accepted or pending trial can
+ * influence (the rest are evaluated again in the next round: few rounds when
+ * trials rarely meet, as in a large bilayer); MDAS_TRIALS_SEQUENTIAL runs
+ * them one after another from the pair lists, every system of a batch at
+ * once (one launch per trial, no rounds: better where trials keep meeting, as
+ * in small bilayers); MDAS_TRIALS_AUTO (the default) runs them sequentially
+ * unless a system of the batch has pressure coupling (its lists may predate
+ * the last box update), then speculatively.  Both give the sequential
+ * order's decisions (dE sums in another order, the same within rounding);
+ * mdas_swap_stats.rounds counts one round per trial on the sequential path.
+ * A batch takes its first system's choice.  Errors: MDAS_ERR_INVALID_ARG for
+ * a NULL system or an unknown path. */
+enum { MDAS_TRIALS_AUTO = 0, MDAS_TRIALS_SPECULATIVE = 1, MDAS_TRIALS_SEQUENTIAL = 2 };
+mdas_status mdas_set_trial_path(mdas_system *s, int32_t path);
 
 /* Autotuning of a batch's work shape: for each of the n_skins candidate
  * list skins (nm, each > 0), each of the two layouts of mdas_set_partitioned

@@ -112,7 +112,7 @@ EXPORTS = ["mdas_create_system", "mdas_destroy_system", "mdas_forces", "mdas_ene
            "mdas_wait_timeout_probe", "mdas_box", "mdas_alchemical_move_trace", "mdas_interleaflet_move",
            "mdas_device_ptrs", "mdas_server_add_patch", "mdas_server_submit_to", "mdas_server_patch_state",
            "mdas_server_remove_patch", "mdas_tune_batch", "mdas_set_partitioned", "mdas_set_batch_wave",
-           "mdas_get_state_packed", "mdas_set_state_packed", "mdas_set_list_lanes"]
+           "mdas_get_state_packed", "mdas_set_state_packed", "mdas_set_list_lanes", "mdas_set_trial_path"]
 
 
 def library_path() -> str:
@@ -496,6 +496,12 @@ class System:
         """List columns (threads) per bead of this system's pair-list step, 2
         or 4 (mdas_set_list_lanes); all systems of a batch must agree."""
         self._ck(lib().mdas_set_list_lanes(self._ptr, int(lanes)))
+
+    def set_trial_path(self, path):
+        """How several exchange trials at once run (mdas_set_trial_path): "auto",
+        "speculative" (rounds) or "sequential" (from the pair lists)."""
+        code = {"auto": 0, "speculative": 1, "sequential": 2}[path] if isinstance(path, str) else int(path)
+        self._ck(lib().mdas_set_trial_path(self._ptr, code))
 
     def set_partitioned(self, on=True):
         """Batches give this system its own share of the persistent kernel's

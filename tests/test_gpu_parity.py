@@ -106,12 +106,15 @@ def test_delta_energy_matches_oracle(large):
         n += 1
 
 
+@pytest.mark.parametrize("path", ["speculative", "sequential"])
 @pytest.mark.parametrize("which", ["small", "large"])
-def test_batched_trials_equal_sequential_oracle(which, small, large):
-    """mdas_swap_trials evaluates trials in speculative rounds; the outcome
-    must equal the oracle's one-after-another processing (Sec. 2, Eq. 1)."""
+def test_batched_trials_equal_sequential_oracle(which, path, small, large):
+    """mdas_swap_trials evaluates trials in speculative rounds or one after
+    another from the pair lists; either outcome must equal the oracle's
+    one-after-another processing (Sec. 2, Eq. 1)."""
     m = small if which == "small" else large
     s = mdas.System(m, temperature=600.0)
+    s.set_trial_path(path)
     st0 = s.get_state()
     stats, rec = s.swap_trials(256)
     o = oracle.Oracle(m, temperature=600.0)
@@ -245,13 +248,14 @@ def test_deterministic_rerun(large):
     assert out[0] == out[1]
 
 
-@pytest.mark.parametrize("lanes", [4, 2])
-def test_batch_equals_solo(lanes):
+@pytest.mark.parametrize("lanes,path", [(4, "speculative"), (2, "speculative"), (4, "sequential")])
+def test_batch_equals_solo(lanes, path):
     ms = [synth.patch(n, 2 + (n % 2), seed=50 + n, system_id=k) for k, n in enumerate([130, 258, 400])]
     solo = []
     for m in ms:
         s = mdas.System(m)
         s.set_list_lanes(lanes)
+        s.set_trial_path(path)
         s.md_steps(12)
         s.swap_trials(20, log=False)
         st = s.get_state()
@@ -260,6 +264,7 @@ def test_batch_equals_solo(lanes):
     sy = [mdas.System(m) for m in ms]
     for s in sy:
         s.set_list_lanes(lanes)
+        s.set_trial_path(path)
     mdas.batch_run(sy, 12, 20)
     for s, st in zip(sy, solo):
         b = s.get_state()
