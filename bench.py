@@ -373,19 +373,27 @@ def replica_benchmark(stream, n_rep=64, rounds=3):
     steps + 100 exchange trials per round: all replicas in one launch per
     phase (mdas_batch_run) against one replica at a time, both with the
     pair-list skin the autotuner picks for the batch; the batch also takes the
-    tuner's layout and step shape, the replicas run alone the default shape
-    (4 lanes per bead, the faster one for a lone system)."""
+    tuner's layout and step shape, each replica run alone its own faster
+    shape (four lanes while its step items fit one wave of the GPU's groups,
+    else two) and the faster exchange-trial path."""
     from paper_2005_08348_gb300 import mdas, synth
     ms = synth.replica_set(n_rep)
     skin, part, wave, lanes, tune = mdas.tune_batch(ms, skins=(0.25, 0.3), waves=(0,), lanes=(2, 4),
                                                     md_steps=MD_PER_STEP, swap_trials=MD_PER_STEP, rounds=1,
                                                     stream=stream.cuda_stream)
     sys_b = [mdas.System(m, stream=stream.cuda_stream, list_skin=skin) for m in ms]
-    sys_s = [mdas.System(m, stream=stream.cuda_stream, list_skin=skin) for m in ms]   # 4 lanes: a lone system's best
+    sys_s = [mdas.System(m, stream=stream.cuda_stream, list_skin=skin) for m in ms]
     for s in sys_b:
         s.set_partitioned(part)
         s.set_batch_wave(wave)
         s.set_list_lanes(lanes)
+    # a lone replica's faster step shape: four lanes while its four-lane step
+    # items and its trial and close groups fit one wave of the persistent
+    # kernel's groups (152 SMs x 8), else two (measured crossover)
+    groups = 152 * 8
+    solo_lanes = [4 if (m.n_beads + 31) // 32 + 17 <= groups else 2 for m in ms]
+    for s, ln in zip(sys_s, solo_lanes):
+        s.set_list_lanes(ln)
     pairs = sum(s.energy()["pairs"] for s in sys_b)
     mdas.batch_run(sys_b, MD_PER_STEP, MD_PER_STEP)
     for s in sys_s:
@@ -418,7 +426,8 @@ def replica_benchmark(stream, n_rep=64, rounds=3):
            "batched_swap_trials_per_s": n_rep * md / tb, "one_at_a_time_swap_trials_per_s": n_rep * md / ts,
            "speedup": ts / tb, "rounds": rounds, "list_skin_nm": skin,
            "layout": "partitioned (systems advance independently)" if part else "lockstep (kernel-wide barriers)",
-           "wave_beads": wave or "all", "list_lanes_per_bead": lanes, "one_at_a_time_list_lanes_per_bead": 4,
+           "wave_beads": wave or "all", "list_lanes_per_bead": lanes,
+           "one_at_a_time_list_lanes_per_bead": {"4": solo_lanes.count(4), "2": solo_lanes.count(2)},
            "trial_path": "sequential", "one_at_a_time_trial_path": solo_path,
            "one_at_a_time_ms_per_round_by_trial_path": {k: round(1e3 * v / rounds, 2) for k, v in ts_path.items()},
            "autotune_us_per_md_step": {f"skin {k[0]:g} {'partitioned' if k[1] else 'lockstep'} wave {k[2] or 'all'} "
