@@ -122,3 +122,26 @@ def test_footprint_counts_the_pressure_coupling_grids_without_a_gpu():
     wide = mdas.footprint(m, pcouple=dict(box_margin=0.2))
     assert nvt < npt < wide
     assert mdas.footprint(m, pcouple=None) == nvt
+
+
+def test_shape_path_and_state_calls_reject_bad_arguments_without_touching_the_gpu():
+    """The step-shape, trial-path, packed-state and batch-tuner calls check
+    their arguments on the host first (MDAS_ERR_INVALID_ARG, no CUDA call)."""
+    from paper_2005_08348_gb300 import mdas
+    lib = mdas.lib()
+    assert lib.mdas_set_list_lanes(None, 2) == 1
+    assert lib.mdas_set_trial_path(None, 0) == 1
+    assert lib.mdas_get_state_packed(None, None, None, None) == 1
+    assert lib.mdas_set_state_packed(None, None, None, None) == 1
+    d = mdas.Desc()
+    arr = (ctypes.POINTER(mdas.Desc) * 1)(ctypes.pointer(d))
+    skins = (ctypes.c_double * 1)(0.3)
+    waves = (ctypes.c_int64 * 1)(0)
+    lanes = (ctypes.c_int32 * 2)(4, 3)                    # 3 lanes per bead does not exist
+    us = (ctypes.c_double * 4)()
+    best, part, wave, lane = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    assert lib.mdas_tune_batch(arr, 1, skins, 1, waves, 1, lanes, 2, 10, 0, 1, us, ctypes.byref(best),
+                               ctypes.byref(part), ctypes.byref(wave), ctypes.byref(lane)) == 1
+    assert b"lanes" in lib.mdas_last_error(None)
+    assert lib.mdas_tune_batch(arr, 1, skins, 1, waves, 1, lanes, 0, 10, 0, 1, us, ctypes.byref(best),
+                               ctypes.byref(part), ctypes.byref(wave), ctypes.byref(lane)) == 1
