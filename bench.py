@@ -274,7 +274,7 @@ def run_gpu(args):
         sysm.md_steps(MD_PER_STEP, swap_every=1)
         sysm.get_state_packed(*hbuf)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")   # the slowest rank's
     h2d = d2h = sum(t.numel() * t.element_size() for t in hbuf)   # every array, each way, every step
     e2e_value = pairs_per_eval * MD_PER_STEP * ws / e2e_s
 
@@ -327,7 +327,9 @@ def run_gpu(args):
         "clocks": clk,
         "wall_s_timed": wall,
     }
-    if not args.no_extra:
+    # the informational lines and the CPU baseline belong to the one-GPU run
+    # (a multi-GPU run would hold every GPU while rank 0 alone works on them)
+    if not args.no_extra and ws == 1:
         out["batched_replicas"] = _extra(replica_benchmark, stream)
         out["swap_trials_4608_lipids"] = _extra(swap_benchmark, stream)
         out["mdas_4608_lipids"] = _extra(mdas_benchmark, stream)
@@ -336,7 +338,7 @@ def run_gpu(args):
         out["npt_1152_lipids"] = _extra(npt_benchmark, stream)
         out["fp64_mcmd_128_lipids"] = _extra(fp64_benchmark, stream)
         out["served"] = _extra(serving_benchmark, stream)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:
         import oracle
         cores = host_cores()
         os.environ.setdefault("OMP_NUM_THREADS", str(cores))
