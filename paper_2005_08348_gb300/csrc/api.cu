@@ -21,7 +21,7 @@ namespace {
 struct Batch {
     std::vector<mdas_system *> sys;
     SysDev *dsys = nullptr;
-    BlockMap beads, cells, sortcells, syss, nlbeads, lcells, lsort;
+    BlockMap beads, cells, sortcells, syss, nlbeads, lsort;
     int precision = 0;
     cudaStream_t stream = nullptr;
     int max_bead_blocks = 1;
@@ -35,7 +35,7 @@ struct Batch {
     int lanes = NL_LANES;         // list columns per bead of the batch's pair lists (all its systems agree)
     int trial_path = MDAS_TRIALS_AUTO;   // how batched exchange trials run (the first system's choice)
     size_t cap_sys = 0, cap_beads = 0, cap_cells = 0, cap_sort = 0;   // device capacity (refillable batches)
-    size_t cap_nlb = 0, cap_lc = 0, cap_ls = 0;
+    size_t cap_nlb = 0, cap_ls = 0;
     LaunchCtx ctx() const;
 };
 
@@ -127,7 +127,7 @@ LaunchCtx Batch::ctx() const {
     LaunchCtx L;
     L.sys = dsys; L.n_sys = (int)sys.size();
     L.beads = &beads; L.cells = &cells; L.sortcells = &sortcells; L.syss = &syss;
-    L.nlbeads = &nlbeads; L.lcells = &lcells; L.lsort = &lsort;
+    L.nlbeads = &nlbeads; L.lsort = &lsort;
     L.precision = precision; L.stream = stream; L.max_bead_blocks = max_bead_blocks;
     L.lanes = lanes;
     L.bticket = bticket;
@@ -200,7 +200,7 @@ cudaError_t upload_map(BlockMap &m, const std::vector<int2> &v) {
 
 void destroy_batch(Batch *b) {
     free_map(b->beads); free_map(b->cells); free_map(b->sortcells); free_map(b->syss);
-    free_map(b->nlbeads); free_map(b->lcells); free_map(b->lsort);
+    free_map(b->nlbeads); free_map(b->lsort);
     if (b->dsys) cudaFree(b->dsys);
     if (b->dscratch) cudaFree(b->dscratch);
     if (b->bticket) cudaFree(b->bticket);
@@ -210,9 +210,9 @@ void destroy_batch(Batch *b) {
 
 // block maps of a batch: per system its bead blocks, cells, cell groups of the
 // cell-list finish (plus the thermostat block), step-kernel blocks and
-// list-build cells
+// list-build place items (four cells each)
 struct Maps {
-    std::vector<int2> beads, cells, sortcells, syss, nlbeads, lcells, lsort;
+    std::vector<int2> beads, cells, sortcells, syss, nlbeads, lsort;
     int lanes = NL_LANES;      // the batch's list columns per bead (step items of NL_BLOCK / lanes beads)
     void add(int k, const mdas_system *x);
 };
@@ -224,7 +224,6 @@ void Maps::add(int k, const mdas_system *x) {
     sortcells.push_back(make_int2(k, -1));   // the system's thermostat block
     syss.push_back(make_int2(k, 0));
     for (int i = 0; i < x->n; i += NL_BLOCK / lanes) nlbeads.push_back(make_int2(k, i));
-    for (int c = 0; c < x->hp.n_lcells; ++c) lcells.push_back(make_int2(k, c));
     for (int c = 0; c < x->hp.n_lcells; c += CELLS_PER_SORT_BLOCK) lsort.push_back(make_int2(k, c));
 }
 
@@ -255,7 +254,6 @@ mdas_status make_batch(const std::vector<mdas_system *> &v, std::unique_ptr<Batc
     CK(upload_map(b->sortcells, mp.sortcells));
     CK(upload_map(b->syss, mp.syss));
     CK(upload_map(b->nlbeads, mp.nlbeads));
-    CK(upload_map(b->lcells, mp.lcells));
     CK(upload_map(b->lsort, mp.lsort));
     CK(cudaMalloc(&b->dscratch, sizeof(int) * 4));
     CK(cudaMalloc(&b->bticket, sizeof(unsigned int)));
@@ -301,7 +299,6 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     CK(grow((void **)&b.cells.d, b.cap_cells, cells.size(), sizeof(int2)));
     CK(grow((void **)&b.sortcells.d, b.cap_sort, sortcells.size(), sizeof(int2)));
     CK(grow((void **)&b.nlbeads.d, b.cap_nlb, mp.nlbeads.size(), sizeof(int2)));
-    CK(grow((void **)&b.lcells.d, b.cap_lc, mp.lcells.size(), sizeof(int2)));
     CK(grow((void **)&b.lsort.d, b.cap_ls, mp.lsort.size(), sizeof(int2)));
     size_t cap_syss = 0;
     if (!b.syss.d) CK(grow((void **)&b.syss.d, cap_syss, 4096, sizeof(int2)));
@@ -321,7 +318,6 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     CK(cudaMemcpyAsync(b.sortcells.d, sortcells.data(), sizeof(int2) * sortcells.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.syss.d, syss.data(), sizeof(int2) * syss.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.nlbeads.d, mp.nlbeads.data(), sizeof(int2) * mp.nlbeads.size(), cudaMemcpyHostToDevice, b.stream));
-    CK(cudaMemcpyAsync(b.lcells.d, mp.lcells.data(), sizeof(int2) * mp.lcells.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaMemcpyAsync(b.lsort.d, mp.lsort.data(), sizeof(int2) * mp.lsort.size(), cudaMemcpyHostToDevice, b.stream));
     CK(cudaStreamSynchronize(b.stream));   // the host vectors go out of scope
     b.beads.n = (int)beads.size();
@@ -329,7 +325,6 @@ mdas_status refill_batch(Batch &b, const std::vector<mdas_system *> &v) {
     b.sortcells.n = (int)sortcells.size();
     b.syss.n = (int)syss.size();
     b.nlbeads.n = (int)mp.nlbeads.size();
-    b.lcells.n = (int)mp.lcells.size();
     b.lsort.n = (int)mp.lsort.size();
     b.part_groups = 0;                     // the partition is made again for the new systems
     return MDAS_OK;
@@ -468,18 +463,17 @@ mdas_status make_partition(mdas_system *s, Batch &b, int groups, bool *use) {
     std::vector<char> host(pl.bytes, 0);
     SysRange *r = (SysRange *)(host.data() + pl.ranges);
     int *gs = (int *)(host.data() + pl.gsys);
-    int g0 = 0, nl0 = 0, bd0 = 0, ls0 = 0, lc0 = 0;
+    int g0 = 0, nl0 = 0, bd0 = 0, ls0 = 0;
     for (int q = 0; q < n; ++q) {
         const mdas_system *x = b.sys[q];
         r[q].g0 = g0; r[q].ng = ng[q];
         r[q].nl0 = nl0; r[q].nln = (x->n + NL_BLOCK / b.lanes - 1) / (NL_BLOCK / b.lanes);
         r[q].bd0 = bd0; r[q].bdn = (x->n + BEAD_BLOCK - 1) / BEAD_BLOCK;
         r[q].ls0 = ls0; r[q].lsn = (x->hp.n_lcells + CELLS_PER_SORT_BLOCK - 1) / CELLS_PER_SORT_BLOCK;
-        r[q].lc0 = lc0; r[q].lcn = x->hp.n_lcells;
         for (int k = 0; k < ng[q]; ++k) gs[g0 + k] = q;
-        g0 += ng[q]; nl0 += r[q].nln; bd0 += r[q].bdn; ls0 += r[q].lsn; lc0 += r[q].lcn;
+        g0 += ng[q]; nl0 += r[q].nln; bd0 += r[q].bdn; ls0 += r[q].lsn;
     }
-    if (nl0 != b.nlbeads.n || bd0 != b.beads.n || ls0 != b.lsort.n || lc0 != b.lcells.n)
+    if (nl0 != b.nlbeads.n || bd0 != b.beads.n || ls0 != b.lsort.n)
         return fail(s, MDAS_ERR_INVALID_ARG, "batch: block maps do not match the partition");
     if (pl.bytes > b.part_cap) {
         if (b.part) cudaFree(b.part);
@@ -900,6 +894,7 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         {(void **)&H.lcell, 8ull * P.n_lcells}, {(void **)&H.lid, 4ull * n}, {(void **)&H.lk, 4ull * n},
         {(void **)&H.lpos, 32ull * n}, {(void **)&H.xref, 16ull * n}, {(void **)&H.nl_n, 4ull * NL_LANES_MAX * n},
         {(void **)&H.nl, 4ull * (size_t)P.lcap * P.npad}, {(void **)&H.bslot, 4ull * NL_PART * n},
+        {(void **)&H.btask, 8ull * (n / NLB_BEADS + P.n_lcells + 1)},
         {(void **)&H.tmark, 8ull * P.mark_words},
     };
     size_t total = 0;
@@ -1940,8 +1935,9 @@ size_t arena_estimate(const mdas_system_desc *d) {
                32 * MAX_DRAW_STEPS + 24 * n + 16 * std::max(d->n_lipids, 1) + 16 * RDF_MAX_BINS + 8;
     const ListDims ld = list_dims(d, shrink);
     t += 12ull * ld.n_lcells + 4ull * ld.n_lcells * ld.lcapc + 4 * n + 4 * n + 32 * n + 16 * n + 4ull * NL_LANES_MAX * n +
-         4ull * ld.lcap * ld.npad + 4ull * NL_PART * n + 8ull * ((n + NL_BEADS_MIN - 1) / NL_BEADS_MIN / 32 + 1);
-    return t + 51 * 256;
+         4ull * ld.lcap * ld.npad + 4ull * NL_PART * n + 8ull * ((n + NL_BEADS_MIN - 1) / NL_BEADS_MIN / 32 + 1) +
+         8ull * (n / NLB_BEADS + ld.n_lcells + 1);
+    return t + 52 * 256;
 }
 
 }  // namespace

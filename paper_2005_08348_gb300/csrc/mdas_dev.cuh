@@ -26,7 +26,10 @@ constexpr int NL_LANES_MAX = 4;        // the most list columns per bead of any 
 constexpr int NL_BEADS_MIN = NL_BLOCK / NL_LANES_MAX;   // beads of the smallest step item
 __host__ __device__ constexpr bool nl_lanes_ok(int g) { return g == 2 || g == 4; }
 constexpr int NL_PART = 8;             // bonded partners per bead at most
-constexpr int NLB_STAGE = 384;         // candidates staged per chunk by the list build (two chunks for a typical cell)
+constexpr int NLB_BEADS = 8;           // beads of one list-build task (one warp)
+constexpr int NL_BUILD_BLOCKS = 152 * 8;   // blocks of the list-build kernel (separate launches)
+// list-build tasks of a cell with the given number of beads
+__host__ __device__ constexpr int nl_build_tasks(int beads) { return (beads + NLB_BEADS - 1) / NLB_BEADS; }
 constexpr int CELLS_PER_SORT_BLOCK = 4;
 constexpr int LOG_CAP = 65536;         // trial records kept per system
 constexpr int MAX_ROUND_TRIALS = 1024; // trials per batched swap evaluation
@@ -170,6 +173,7 @@ struct Counters {
     int nl_viol;                       // a bead moved farther than the skin allows (this step)
     int nl_violp[3];                   // the same per step s (index s % 3, persistent kernel)
     int nl_par;                        // lpos buffer holding the current positions
+    int nbtask;                        // list-build tasks of the build in progress (written by its place items)
     unsigned int sticket;              // last-block ticket of the step kernel (separate launches)
     unsigned int nticket;              // last-block ticket of the list-build count kernel
     unsigned long long nl_builds;      // pair-list builds
@@ -244,6 +248,7 @@ struct SysDev {
     int *nl_n;                         // [n * G] entries in each column of each bead's list
     int *nl;                           // row r of column g of bead k at [r * npad * G + k * G + g]
     int *bslot;                        // [n * NL_PART] list indices of the bonded partners
+    int2 *btask;                       // [n / NLB_BEADS + n_lcells + 1] list-build tasks: cell, tasks << 16 | task
     unsigned *tmark;                   // [2 * mark_words] step items an exchange trial can change, per trial parity
     int n_bead_blocks;
 };
@@ -299,7 +304,7 @@ struct LaunchCtx {
     const SysDev *sys;        // device array
     int n_sys;
     const BlockMap *beads, *cells, *sortcells, *syss;
-    const BlockMap *nlbeads, *lcells, *lsort;   // pair-list step blocks, list-build cells (one, four per block)
+    const BlockMap *nlbeads, *lsort;   // pair-list step blocks, list-build place items (four cells per block)
     int precision;
     cudaStream_t stream;
     int max_bead_blocks;
@@ -315,10 +320,9 @@ struct LaunchCtx {
 };
 
 // One system's share of a partitioned persistent launch: its groups
-// [g0, g0 + ng) and its ranges in the step-item, bead-block, place and
-// list-build-cell maps.
+// [g0, g0 + ng) and its ranges in the step-item, bead-block and place maps.
 struct SysRange {
-    int g0, ng, nl0, nln, bd0, bdn, ls0, lsn, lc0, lcn;
+    int g0, ng, nl0, nln, bd0, bdn, ls0, lsn;
 };
 // Barrier state of one system's groups (monotonic arrival count, the launch's base).
 struct SysBar {

@@ -21,10 +21,13 @@
 //
 // Build: count (beads into list-build cells), place (each item sums the
 // counts of the cells before its own, then one warp per cell ranks its beads
-// by (octant, id) and places them), build (the lists of one cell's beads from
-// the 27 neighbour cells, excluded 1-2 pairs left out, and the list indices
-// of each bead's bonded partners).  A bead's list has NL_G columns; partners
-// go to the columns in turn and lane g of the step sums column g.
+// by (octant, id), places them and writes the cell's build tasks: runs of at
+// most NLB_BEADS of its beads), build (one warp per task: the lists of its
+// beads from the 27 neighbour cells, excluded 1-2 pairs left out, and the
+// list indices of each bead's bonded partners; tasks are independent warps,
+// so a build of a lone system is one round of tasks over the GPU's warps).
+// A bead's list has NL_G columns; partners go to the columns in turn and lane
+// g of the step sums column g.
 //
 // Step: NL_G threads per bead, each summing its column; the partial forces are
 // summed across the lanes in a fixed tree (the list fixes which entries each
@@ -148,16 +151,18 @@ static __device__ bool pipe_wait(const SysDev &S, const PipeWait &pw, int item) 
     return redo;
 }
 
+// Scratch of one warp's list-build task (list-build tasks are independent
+// warps: no group barriers)
+struct BuildWarp {
+    float4 nf[64];                            // candidates near the task's beads (a ring): frame coordinates, meta word in w
+    int nk[64];                               // and their list indices
+    float4 sb[NLB_BEADS];                     // the task's beads: frame coordinates, (lipid + 1) << 4 | k in w
+    unsigned sbe[NLB_BEADS];                  // and their excluded local indices
+};
+
 struct BuildSmem {
-    int2 nb[27];
-    int noff[28];
-    int last;
-    int ws[GRP / 32];
-    float4 sb[GRP / 32][8];                   // per warp: its beads' frame coordinates, (lipid + 1) << 4 | k in w
-    unsigned sbe[GRP / 32][8];                // and their excluded local indices
-    float4 sf[NLB_STAGE];                     // frame coordinates, meta word in w
-    int sk[NLB_STAGE];                        // list index
-    uint16_t wl[GRP / 32][NLB_STAGE];         // per warp: staged index of those candidates
+    int ws[GRP / 32], wt[GRP / 32];           // place: per-warp sums of earlier cells' beads and tasks
+    BuildWarp w[GRP / 32];
 };
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
@@ -199,21 +204,37 @@ __device__ __forceinline__ int loct_of(const Params &P, uint4 q) {
 // group (every item sums its own prefix: no serial scan).
 static __device__ void nl_place_item(const SysDev &S, int c0, int par, const Grp &g, BuildSmem &sm) {
     const Params &P = *S.p;
-    int part = 0;
-    for (int q = g.t; q < c0; q += GRP) part += min(__ldcg(&S.lcell_count[q]), P.lcapc);
+    int part = 0, tpart = 0;
+    for (int q = g.t; q < c0; q += GRP) {
+        const int m = min(__ldcg(&S.lcell_count[q]), P.lcapc);
+        part += m;
+        tpart += nl_build_tasks(m);
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((g.t & 31) == 0) sm.ws[g.t >> 5] = part;
+    for (int o = 16; o > 0; o >>= 1) {
+        part += __shfl_xor_sync(0xffffffffu, part, o);
+        tpart += __shfl_xor_sync(0xffffffffu, tpart, o);
+    }
+    if ((g.t & 31) == 0) { sm.ws[g.t >> 5] = part; sm.wt[g.t >> 5] = tpart; }
     g.sync();
     const int c = c0 + (g.t >> 5), lane = g.t & 31;
-    int first = 0;
-    for (int w = 0; w < GRP / 32; ++w) first += sm.ws[w];
-    for (int q = c0; q < c; ++q) first += min(__ldcg(&S.lcell_count[q]), P.lcapc);
+    int first = 0, tfirst = 0;
+    for (int w = 0; w < GRP / 32; ++w) { first += sm.ws[w]; tfirst += sm.wt[w]; }
+    for (int q = c0; q < c; ++q) {
+        const int m = min(__ldcg(&S.lcell_count[q]), P.lcapc);
+        first += m;
+        tfirst += nl_build_tasks(m);
+    }
     g.sync();
     if (c >= P.n_lcells) return;
     const int cnt = min(__ldcg(&S.lcell_count[c]), P.lcapc), base = c * P.lcapc;
     const int2 lc = make_int2(first, cnt);
     if (lane == 0) S.lcell[c] = lc;
+    // the cell's list-build tasks (cell, tasks << 16 | task) and, after the
+    // last cell, the number of tasks
+    const int ntk = nl_build_tasks(cnt);
+    for (int x = lane; x < ntk; x += 32) S.btask[tfirst + x] = make_int2(c, (ntk << 16) | x);
+    if (lane == 0 && c == P.n_lcells - 1) S.c->nbtask = tfirst + ntk;
     uint4 *cur = S.lpos + (size_t)par * P.n;
     auto key = [&](int a) {                    // unique: ids are below 2^28
         if (a >= cnt) return 0x7fffffff;
@@ -240,185 +261,232 @@ static __device__ void nl_place_item(const SysDev &S, int c0, int par, const Grp
     }
 }
 
-// The lists of the beads of list-build cell c.  The 27 neighbour cells are
-// staged in a frame centred on the cell (exact integer offsets as floats;
-// with 3 or more cells per edge every partner within rl of a bead of the cell
-// has an offset below half a box, so the frame difference is the minimum
-// image).  Each warp keeps the candidates near the box around its beads;
-// then lane u tests candidate u of each chunk of 32 against every bead of the
-// warp, and a ballot per bead gives the partners their list entries in
-// candidate order.
-template <int G>
-__device__ void nl_build_item(const SysDev &S, int c, int par, const Grp &g, BuildSmem &sm) {
+// One list-build task: the lists of beads b0 .. b0 + nb - 1 (at most
+// NLB_BEADS, a run of one list-build cell's beads) for one warp.  The 27
+// neighbour cells are read in a frame centred on the cell (exact integer
+// offsets as floats; with 3 or more cells per edge every partner within rl of
+// a bead of the cell has an offset below half a box, so the frame difference
+// is the minimum image), cell by cell, 32 candidates at a time; those near
+// the box around the task's beads go to a ring in shared memory, and every 32
+// of them lane u tests candidate u against every bead of the task: a ballot
+// per bead gives the partners their list entries in candidate order (cells
+// in order, beads in list order within a cell), dealt to the columns in turn.
+//
+// PF: the positions of the next two chunks of candidates are loaded while
+// the current one is filtered (shorter latency per task, more registers:
+// taken where a build is one round of tasks on an otherwise idle GPU, the
+// persistent kernel of lone systems and the separate launches; a batch's
+// partitioned kernel, bound by its instruction issue, walks without).
+template <int G, bool PF>
+__device__ void nl_build_task(const SysDev &S, int task, int par, int lane, BuildWarp &sw) {
     constexpr int NL_G = G;
+    constexpr unsigned FULL = 0xffffffffu;
     const Params &P = *S.p;
     Counters &C = *S.c;
-    const int t = g.t;
+    const int2 tk = S.btask[task];
+    const int c = tk.x, sub = tk.y & 0xffff, ntk = tk.y >> 16;
     const uint4 *cur = S.lpos + (size_t)par * P.n;
     const int nx = P.ln[0], ny = P.ln[1], nz = P.ln[2];
     const int cz = c / (nx * ny), cxy = c - cz * nx * ny, cy = cxy / nx, cx = cxy - cy * nx;
-    if (t < 27) {
-        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    // lane q < 27: first list index and bead count of neighbour cell q (13: the cell itself)
+    int2 nbq = make_int2(0, 0);
+    if (lane < 27) {
+        const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
         int x = cx + dx, y = cy + dy, z = cz + dz;
         x += x < 0 ? nx : (x >= nx ? -nx : 0);
         y += y < 0 ? ny : (y >= ny ? -ny : 0);
         z += z < 0 ? nz : (z >= nz ? -nz : 0);
-        sm.nb[t] = S.lcell[(z * ny + y) * nx + x];
+        nbq = S.lcell[(z * ny + y) * nx + x];
     }
-    g.sync();
-    if (t == 0) {
-        int o = 0;
-        for (int q = 0; q < 27; ++q) { sm.noff[q] = o; o += sm.nb[q].y; }
-        sm.noff[27] = o;
-    }
-    g.sync();
-    const int M = sm.noff[27];
-    if (t == 0) S.lcell_count[c] = 0;          // counted afresh at the next build
+    const int i0 = __shfl_sync(FULL, nbq.x, 13), ni = __shfl_sync(FULL, nbq.y, 13);
+    if (sub == 0 && lane == 0) S.lcell_count[c] = 0;   // counted afresh at the next build
+    // this task's run of the cell's beads (the runs differ by one bead at most)
+    const int b0 = sub * ni / ntk, nbw = (sub + 1) * ni / ntk - b0, kb = i0 + b0;
     const uint32_t ox = (uint32_t)(((unsigned long long)(2 * cx + 1) * P.lcwu[0]) >> 1);
     const uint32_t oy = (uint32_t)(((unsigned long long)(2 * cy + 1) * P.lcwu[1]) >> 1);
     const uint32_t oz = (uint32_t)(((unsigned long long)(2 * cz + 1) * P.lcwu[2]) >> 1);
     const float q0 = P.qsf[0], q1 = P.qsf[1], q2 = P.qsf[2];
     const float rl2 = P.rl2f;
     const int capg = P.lcap / NL_G;
-    const int i0 = sm.nb[13].x, ni = sm.nb[13].y;
-    // beads per warp and pass (at most 8): warp w takes beads w * bpw .. of
-    // a pass, lane b holds bead b (its frame position and exclusions also in
-    // shared memory, where every lane reads them)
-    const int bpw = max(1, min(8, (ni + GRP / 32 - 1) / (GRP / 32)));
-    const int lane = t & 31, w = t >> 5;
     const unsigned ltmask = (1u << lane) - 1u;
+    // lane b holds bead b of the run (its frame position and exclusions also
+    // in shared memory, where every lane reads them)
+    const bool act = lane < nbw;
+    const int ki = kb + (act ? lane : 0);
+    const uint4 pi = cur[ki];
+    const float xi = (float)(int)(pi.x - ox) * q0, yi = (float)(int)(pi.y - oy) * q1,
+                zi = (float)(int)(pi.z - oz) * q2;
+    const uint32_t lip = pi.w >> 12;
+    const uint32_t em = lip ? P.excl[meta_k(pi.w)] : 0u;
+    if (act) {
+        sw.sb[lane] = make_float4(xi, yi, zi, __uint_as_float(pi.w >> 8));   // (lipid + 1) << 4 | k
+        sw.sbe[lane] = em;
+    }
+    // the box around the run's beads
+    float lo0 = act ? xi : 3e30f, lo1 = act ? yi : 3e30f, lo2 = act ? zi : 3e30f;
+    float hi0 = act ? xi : -3e30f, hi1 = act ? yi : -3e30f, hi2 = act ? zi : -3e30f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo0 = fminf(lo0, __shfl_xor_sync(FULL, lo0, o));
+        lo1 = fminf(lo1, __shfl_xor_sync(FULL, lo1, o));
+        lo2 = fminf(lo2, __shfl_xor_sync(FULL, lo2, o));
+        hi0 = fmaxf(hi0, __shfl_xor_sync(FULL, hi0, o));
+        hi1 = fmaxf(hi1, __shfl_xor_sync(FULL, hi1, o));
+        hi2 = fmaxf(hi2, __shfl_xor_sync(FULL, hi2, o));
+    }
+    __syncwarp();
     // loop invariants in registers (stores through the list pointer could
     // otherwise alias them and force reloads from global memory)
     int *const nl = S.nl;
     const size_t lrow = (size_t)P.npad * G;
     const unsigned lcapg = (unsigned)(capg * NL_G);   // entries a bead's list holds
-    const int s13 = sm.noff[13];
-    for (int ib = 0; ib < ni; ib += (GRP / 32) * bpw) {
-        const int rw = ib + w * bpw;               // the warp's first bead of this pass
-        const int nbw = max(0, min(bpw, ni - rw));
-        const bool act = lane < nbw;
-        const int ki = i0 + (act ? rw + lane : 0);
-        const uint4 pi = cur[ki];
-        const float xi = (float)(int)(pi.x - ox) * q0, yi = (float)(int)(pi.y - oy) * q1,
-                    zi = (float)(int)(pi.z - oz) * q2;
-        const uint32_t lip = pi.w >> 12;
-        const uint32_t em = lip ? P.excl[meta_k(pi.w)] : 0u;
-        if (act) {
-            sm.sb[w][lane] = make_float4(xi, yi, zi, __uint_as_float(pi.w >> 8));   // (lipid + 1) << 4 | k
-            sm.sbe[w][lane] = em;
+    int base = 0;                                     // lane b: entries of bead b so far
+    unsigned head = 0, tail = 0;                      // ring entries head .. tail - 1 wait for their tests
+    // lane u tests ring entry head + u (u < nt) against every bead of the run
+    // (all tests first: shared loads, arithmetic and votes in flight
+    // together), then the entries, bead by bead
+    auto test = [&](int nt) {
+        const bool have = lane < nt;
+        const int sl = (int)((head + (unsigned)lane) & 63u);
+        const float4 e = sw.nf[sl];
+        const int kj = sw.nk[sl];
+        const uint32_t jkey = __float_as_uint(e.w) >> 8;   // (lipid + 1) << 4 | k
+        const uint32_t jk = jkey & 15u;
+        unsigned bal[NLB_BEADS];
+#pragma unroll
+        for (int b = 0; b < NLB_BEADS; ++b) {
+            const float4 bi = sw.sb[b];
+            const float dx = bi.x - e.x, dy = bi.y - e.y, dz = bi.z - e.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            // excluded: the same lipid ((lipid + 1) equal) and a bonded local index
+            const bool excl = (__float_as_uint(bi.w) ^ jkey) < 16u && ((sw.sbe[b] >> jk) & 1u);
+            const bool in = b < nbw && have && r2 < rl2 && !excl && kj != kb + b;
+            bal[b] = __ballot_sync(FULL, in);
         }
-        int base = 0;                              // lane b: entries of bead b so far
-        for (int f0 = 0; f0 < M; f0 += NLB_STAGE) {
-            const int mc = min(NLB_STAGE, M - f0);
-            g.sync();
-            // every thread copies its candidates' positions (all in flight at
-            // once), then turns them into frame coordinates in place
-            for (int f = t; f < mc; f += GRP) {
-                const int fg = f0 + f;
-                int lo = 0, hi = 26;              // the neighbour cell holding candidate fg
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (sm.noff[mid] <= fg) lo = mid; else hi = mid - 1;
-                }
-                const int kj = sm.nb[lo].x + (fg - sm.noff[lo]);
-                cp_async16(&sm.sf[f], cur + kj);
-                sm.sk[f] = kj;
-            }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            cp_async_wait_all();
-            for (int f = t; f < mc; f += GRP) {
-                const uint4 pj = *reinterpret_cast<const uint4 *>(&sm.sf[f]);
-                sm.sf[f] = make_float4((float)(int)(pj.x - ox) * q0, (float)(int)(pj.y - oy) * q1,
-                                       (float)(int)(pj.z - oz) * q2, __uint_as_float(pj.w));
-            }
-            g.sync();
-            // the candidates within rl of the box around this warp's beads
-            // (their count mw is the same in every lane)
-            int mw = 0;
-            {
-                float lo0 = act ? xi : 3e30f, lo1 = act ? yi : 3e30f, lo2 = act ? zi : 3e30f;
-                float hi0 = act ? xi : -3e30f, hi1 = act ? yi : -3e30f, hi2 = act ? zi : -3e30f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
-                    lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
-                    lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
-                    hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
-                    hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
-                    hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+        for (int b = 0; b < NLB_BEADS; ++b) {
+            if (bal[b]) {
+                const int bb = __shfl_sync(FULL, base, b);
+                if ((bal[b] >> lane) & 1u) {
+                    const unsigned ei = (unsigned)bb + __popc(bal[b] & ltmask);
+                    if (ei < lcapg) nl[(size_t)(kb + b) * NL_G + (size_t)(ei / NL_G) * lrow + ei % NL_G] = kj;
                 }
-                for (int f1 = 0; f1 < mc; f1 += 32) {
-                    const int f = f1 + lane;
-                    bool near = false;
-                    if (f < mc) {
-                        const float4 e = sm.sf[f];
-                        const float gx = fmaxf(fmaxf(lo0 - e.x, e.x - hi0), 0.f);
-                        const float gy = fmaxf(fmaxf(lo1 - e.y, e.y - hi1), 0.f);
-                        const float gz = fmaxf(fmaxf(lo2 - e.z, e.z - hi2), 0.f);
-                        near = gx * gx + gy * gy + gz * gz < rl2;
-                    }
-                    const unsigned bn = __ballot_sync(0xffffffffu, near);
-                    if (near) sm.wl[w][mw + __popc(bn & ltmask)] = (uint16_t)f;
-                    mw += __popc(bn);
-                }
-                __syncwarp();
-            }
-            // lane u of a chunk tests compacted candidate c + u against every
-            // bead of the warp; a bead's partners go to its list in candidate
-            // order, entry e at column e % NL_G, row e / NL_G
-            const uint16_t *wl = sm.wl[w];
-            const int fself = s13 + rw - f0;       // staged index of the warp's bead 0
-            for (int c0 = 0; c0 < mw; c0 += 32) {
-                const int u = c0 + lane;
-                const bool have = u < mw;
-                const int f = have ? wl[u] : 0;
-                const float4 e = sm.sf[f];
-                const uint32_t jkey = __float_as_uint(e.w) >> 8;   // (lipid + 1) << 4 | k
-                const uint32_t jk = jkey & 15u;
-                const int skf = sm.sk[f];
-                // the tests of all the warp's beads first (independent: shared
-                // loads, arithmetic and votes in flight together), then the
-                // entries, bead by bead in the same order as one loop would
-                unsigned bal[8];
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const float4 bi = sm.sb[w][b];
-                    const float dx = bi.x - e.x, dy = bi.y - e.y, dz = bi.z - e.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    // excluded: the same lipid ((lipid + 1) equal) and a bonded local index
-                    const bool excl = (__float_as_uint(bi.w) ^ jkey) < 16u && ((sm.sbe[w][b] >> jk) & 1u);
-                    const bool in = b < nbw && have && r2 < rl2 && !excl && f != fself + b;
-                    bal[b] = __ballot_sync(0xffffffffu, in);
-                }
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    if (bal[b]) {
-                        const int bb = __shfl_sync(0xffffffffu, base, b);
-                        if ((bal[b] >> lane) & 1u) {
-                            const unsigned ei = (unsigned)bb + __popc(bal[b] & ltmask);
-                            if (ei < lcapg)
-                                nl[(size_t)(i0 + rw + b) * NL_G + (size_t)(ei / NL_G) * lrow + ei % NL_G] = skf;
-                        }
-                        if (lane == b) base = bb + __popc(bal[b]);
-                    }
-                }
+                if (lane == b) base = bb + __popc(bal[b]);
             }
         }
-        if (act) {
-            for (int col = 0; col < NL_G; ++col) {
-                const int cnt = base > col ? (base - col + NL_G - 1) / NL_G : 0;
-                S.nl_n[(size_t)ki * NL_G + col] = min(cnt, capg);
-            }
-            if (base > P.lcap) atomicOr(&C.err, ERR_CELL_OVERFLOW);
-            if (lip != 0) {
-                const int kl = meta_k(pi.w);
-                for (int p = 0; p < P.npart[kl]; ++p)
-                    S.bslot[(size_t)ki * NL_PART + p] =
-                        S.lk[MDAS_IDX(C, (int)(lip - 1) * P.bpl + P.part[kl][p], P.n_lipid_beads)];
-            }
+        head += (unsigned)nt;
+        __syncwarp();                                 // the tested slots may be written next
+    };
+    // the candidates cell by cell, 32 at a time (a chunk: j0 .. j0 + 31 of
+    // cell q)
+    int q = 0, j0 = -32, qf = __shfl_sync(FULL, nbq.x, 0), qn = __shfl_sync(FULL, nbq.y, 0);
+    auto next_chunk = [&]() {
+        j0 += 32;
+        while (j0 >= qn && q < 27) {
+            ++q;
+            j0 = 0;
+            qf = __shfl_sync(FULL, nbq.x, q);      // lanes 27 .. 31 hold no cell: q = 27 ends the walk
+            qn = __shfl_sync(FULL, nbq.y, q);
+        }
+    };
+    auto load = [&](uint4 &p, int &k, bool &v) {
+        const int j = j0 + lane;
+        v = q < 27 && j < qn;
+        k = qf + j;
+        p = v ? cur[k] : make_uint4(0u, 0u, 0u, 0u);
+    };
+    uint4 p1 = make_uint4(0u, 0u, 0u, 0u), p2 = p1;
+    int k1 = 0, k2 = 0;
+    bool v1 = false, v2 = false, m2 = false;
+    next_chunk();
+    bool m1 = q < 27;                                 // a chunk is left
+    if (PF) {
+        load(p1, k1, v1);
+        next_chunk();
+        m2 = q < 27;
+        load(p2, k2, v2);
+    }
+    while (m1) {
+        uint4 pj;
+        int kj;
+        bool v;
+        if (PF) {
+            pj = p1; kj = k1; v = v1;
+            p1 = p2; k1 = k2; v1 = v2; m1 = m2;
+            next_chunk();
+            m2 = q < 27;
+            load(p2, k2, v2);
+        } else {
+            load(pj, kj, v);
+            next_chunk();
+            m1 = q < 27;
+        }
+        bool near = false;
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v) {
+            e = make_float4((float)(int)(pj.x - ox) * q0, (float)(int)(pj.y - oy) * q1,
+                            (float)(int)(pj.z - oz) * q2, __uint_as_float(pj.w));
+            // the candidate is within rl of the box around the run's beads
+            const float gx = fmaxf(fmaxf(lo0 - e.x, e.x - hi0), 0.f);
+            const float gy = fmaxf(fmaxf(lo1 - e.y, e.y - hi1), 0.f);
+            const float gz = fmaxf(fmaxf(lo2 - e.z, e.z - hi2), 0.f);
+            near = gx * gx + gy * gy + gz * gz < rl2;
+        }
+        const unsigned bn = __ballot_sync(FULL, near);
+        if (near) {
+            const int sl = (int)((tail + (unsigned)__popc(bn & ltmask)) & 63u);
+            sw.nf[sl] = e;
+            sw.nk[sl] = kj;
+        }
+        tail += (unsigned)__popc(bn);
+        __syncwarp();
+        if (tail - head >= 32u) test(32);             // at most 63 wait: the ring holds 64
+    }
+    if (tail != head) test((int)(tail - head));
+    if (act) {
+        for (int col = 0; col < NL_G; ++col) {
+            const int cnt = base > col ? (base - col + NL_G - 1) / NL_G : 0;
+            S.nl_n[(size_t)ki * NL_G + col] = min(cnt, capg);
+        }
+        if (base > P.lcap) atomicOr(&C.err, ERR_CELL_OVERFLOW);
+        if (lip != 0) {
+            const int kl = meta_k(pi.w);
+            for (int p = 0; p < P.npart[kl]; ++p)
+                S.bslot[(size_t)ki * NL_PART + p] =
+                    S.lk[MDAS_IDX(C, (int)(lip - 1) * P.bpl + P.part[kl][p], P.n_lipid_beads)];
         }
     }
-    g.sync();
+}
+
+// The list-build tasks of the systems whose flag is set, dealt to warps
+// gw = 0 .. nw - 1 in turn: task x of the batch (the systems' tasks one after
+// another) goes to warp x mod nw.  Every lane of a warp calls it alike.
+template <int G, typename Flag, typename Par>
+__device__ void nl_build_dealt(const SysDev *sys, int n_sys, int gw, int nw, int lane, BuildWarp &sw, Flag flag,
+                               Par par) {
+    constexpr unsigned FULL = 0xffffffffu;
+    int off = 0;                               // tasks of the earlier windows of 32 systems, modulo nw
+    for (int q0 = 0; q0 < n_sys; q0 += 32) {
+        const int q = q0 + lane;
+        int T = 0;
+        if (q < n_sys && flag(sys[q])) T = __ldcg(&sys[q].c->nbtask);
+        int incl = T;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += x;
+        }
+        const int nq = min(32, n_sys - q0);
+        for (int j = 0; j < nq; ++j) {
+            const int Tj = __shfl_sync(FULL, T, j), ej = __shfl_sync(FULL, incl - T, j);
+            if (Tj == 0) continue;
+            int t = gw - (int)(((long long)off + ej) % nw);
+            if (t < 0) t += nw;
+            const SysDev &S = sys[q0 + j];
+            for (; t < Tj; t += nw) nl_build_task<G, true>(S, t, par(S), lane, sw);
+        }
+        off = (int)(((long long)off + __shfl_sync(FULL, incl, 31)) % nw);
+    }
 }
 
 // A list entry: read once per step, so it skips L1 (which keeps the
@@ -806,12 +874,12 @@ static __global__ void __launch_bounds__(GRP) k_nl_place(const SysDev *__restric
 }
 
 template <int G>
-__global__ void __launch_bounds__(GRP) k_nl_build(const SysDev *__restrict__ sys, const int2 *__restrict__ bmap) {
+__global__ void __launch_bounds__(GRP) k_nl_build(const SysDev *__restrict__ sys, int n_sys) {
     __shared__ BuildSmem sm;
-    const int2 bm = bmap[blockIdx.x];
-    const SysDev &S = sys[bm.x];
-    if (!S.c->nl_stale) return;
-    nl_build_item<G>(S, bm.y, S.c->nl_par, Grp{(int)threadIdx.x, 1}, sm);
+    const int w = threadIdx.x >> 5;
+    nl_build_dealt<G>(sys, n_sys, w * gridDim.x + blockIdx.x, (GRP / 32) * gridDim.x, threadIdx.x & 31, sm.w[w],
+                      [](const SysDev &S) { return S.c->nl_stale != 0; },
+                      [](const SysDev &S) { return S.c->nl_par; });
 }
 
 static __global__ void k_nl_done(const SysDev *__restrict__ sys, int n_sys) {
@@ -829,7 +897,7 @@ void launch_nl_build_t(const LaunchCtx &L) {
     static_assert(CELLS_PER_SORT_BLOCK * 32 == GRP, "place items are one group");
     k_nl_count<<<L.beads->n, GRP, 0, L.stream>>>(L.sys, L.beads->d);
     k_nl_place<<<L.lsort->n, GRP, 0, L.stream>>>(L.sys, L.lsort->d);
-    k_nl_build<G><<<L.lcells->n, GRP, 0, L.stream>>>(L.sys, L.lcells->d);
+    k_nl_build<G><<<NL_BUILD_BLOCKS, GRP, 0, L.stream>>>(L.sys, L.n_sys);
     k_nl_done<<<(L.n_sys + 127) / 128, 128, 0, L.stream>>>(L.sys, L.n_sys);
 }
 
@@ -927,8 +995,8 @@ struct RunArgs {
     const SysRange *ranges;
     SysBar *sbar;
     const int *gsys;
-    const int2 *nlmap, *beadmap, *lsortmap, *lcellmap;
-    int n_nl, n_bead, n_lsort, n_lcell;
+    const int2 *nlmap, *beadmap, *lsortmap;
+    int n_nl, n_bead, n_lsort;
     int n_steps, swap_every, trial_off;   // a trial after local step s when (s + 1 + trial_off) % swap_every == 0
     // alchemical trajectory (LAM): lambda advances by dlam after every lam_M
     // steps, counted from lam_off; at each block's end the work term of the
@@ -976,11 +1044,11 @@ __device__ bool run_build(const RunArgs &a, int which, int s, int b, const Grp &
         if (build_flag(*S.c, which, s)) nl_place_item(S, bm.y, (S.c->nl_par + b) & 1, g, sm);
     }
     if (!grid_barrier(a.rs, bs)) return false;
-    for (int it = gid; it < a.n_lcell; it += G) {
-        const int2 bm = a.lcellmap[it];
-        const SysDev &S = a.sys[bm.x];
-        if (build_flag(*S.c, which, s)) nl_build_item<NG>(S, bm.y, (S.c->nl_par + b) & 1, g, sm);
-    }
+    // one warp per task, consecutive tasks on different SMs
+    const int w = g.t >> 5;
+    nl_build_dealt<NG>(a.sys, a.n_sys, w * G + gid, (GRP / 32) * G, g.t & 31, sm.w[w],
+                       [&](const SysDev &S) { return build_flag(*S.c, which, s) != 0; },
+                       [&](const SysDev &S) { return (S.c->nl_par + b) & 1; });
     return grid_barrier(a.rs, bs);
 }
 
@@ -1036,7 +1104,12 @@ __device__ void run_partitioned(const RunArgs &a, int gid, const Grp &g, StepSme
         if (!bar()) return false;
         for (int it = lg; it < R.lsn; it += ng) nl_place_item(S, a.lsortmap[R.ls0 + it].y, par, g, bsm);
         if (!bar()) return false;
-        for (int it = lg; it < R.lcn; it += ng) nl_build_item<G>(S, a.lcellmap[R.lc0 + it].y, par, g, bsm);
+        {
+            // the system's list-build tasks over its groups' warps in turn
+            const int T = __ldcg(&C.nbtask), w = g.t >> 5;
+            for (int t = w * ng + lg; t < T; t += (GRP / 32) * ng)
+                nl_build_task<G, false>(S, t, par, g.t & 31, bsm.w[w]);
+        }
         return bar();
     };
     bool tab = true;                           // the pair tables must be (re)loaded into shared memory
@@ -1301,7 +1374,6 @@ static cudaError_t run_launch(const LaunchCtx &L, int n_steps, int swap_every, i
     a.nlmap = L.nlbeads->d; a.n_nl = L.nlbeads->n;
     a.beadmap = L.beads->d; a.n_bead = L.beads->n;
     a.lsortmap = L.lsort->d; a.n_lsort = L.lsort->n;
-    a.lcellmap = L.lcells->d; a.n_lcell = L.lcells->n;
     a.n_steps = n_steps; a.swap_every = swap_every; a.trial_off = trial_off; a.rs = rs;
     a.lam_M = lam_M; a.lam_off = lam_off; a.dlam = dlam;
     void *args[] = {&a};
