@@ -380,7 +380,7 @@ def replica_benchmark(stream, n_rep=64, rounds=3):
     else two) and the faster exchange-trial path."""
     from paper_2005_08348_gb300 import mdas, synth
     ms = synth.replica_set(n_rep)
-    skin, part, wave, lanes, tune = mdas.tune_batch(ms, skins=(0.25, 0.3), waves=(0,), lanes=(2, 4),
+    skin, part, wave, lanes, tune = mdas.tune_batch(ms, skins=(0.3, 0.35), waves=(0,), lanes=(2, 4),
                                                     md_steps=MD_PER_STEP, swap_trials=MD_PER_STEP, rounds=1,
                                                     stream=stream.cuda_stream)
     sys_b = [mdas.System(m, stream=stream.cuda_stream, list_skin=skin) for m in ms]

@@ -75,7 +75,7 @@ typedef struct {
     double rc, eps_r, eps_rf;          /* cutoff, relative permittivity, RF dielectric (<= 0: infinity) */
     double temperature, dt, tau_t;     /* K, ps, ps (tau_t <= 0: no thermostat, NVE) */
     double mass;                       /* every bead, amu */
-    double list_skin;                  /* nm: pair-list buffer of the MD step (<= 0: 0.3 nm); an
+    double list_skin;                  /* nm: pair-list buffer of the MD step (<= 0: 0.35 nm); an
                                           implementation parameter that does not change results
                                           beyond FP32 summation order */
     uint64_t seed;                     /* Philox key = (seed_lo ^ system_id, seed_hi) */

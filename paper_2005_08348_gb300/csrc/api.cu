@@ -63,7 +63,7 @@ double grid_shrink(const mdas_system_desc *d) {
 // their length.
 ListDims list_dims(const mdas_system_desc *d, double shrink = 0.0) {
     ListDims L;
-    const double skin = d->list_skin > 0 ? d->list_skin : 0.3;
+    const double skin = d->list_skin > 0 ? d->list_skin : 0.35;
     const double f = 1.0 - shrink;
     const double lmin = std::min(d->box[0], std::min(d->box[1], d->box[2])) * f;
     L.rl = std::max(d->rc, std::min(d->rc + skin, lmin / 3.0));
