@@ -76,6 +76,8 @@ struct StepSmem {
     V4 svel[NB];
     uint4 sxref[NB];
     uint4 spart[NB][NL_PART];
+    Real kered[2][NB];
+    int sviol;
     int redo;
 };
 
@@ -527,7 +529,6 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         cnt = S.nl_n[(size_t)k * NL_G + gl];
     }
     if (load_tables) {                         // else still there from the group's previous item
-        g.sync();                              // the group's warps may still read the previous tables
         for (int x = t; x < 256; x += GRP) {
             V4 e;
             if (F32) {
@@ -538,6 +539,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             e.w = (Real)0;
             sm.tab[x] = e;
         }
+        if (t == 0) sm.sviol = 0;              // afterwards cleared by every item's end
         g.sync();
     }
     // the first row group's positions, then (while they arrive) the copies
@@ -693,7 +695,6 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         q0 = __ldcg(cur + j0); q1 = __ldcg(cur + j1); q2 = __ldcg(cur + j2); q3 = __ldcg(cur + j3);
     }
     Real e0 = 0, e1 = 0;
-    bool moved = false;                        // the bead moved farther than the list allows
     Real kx = 0, ky = 0, kz = 0;               // PC: the bead's kinetic energy per axis
     if (valid && gl == 0) {
         const Real f0 = ax, f1 = ay, f2 = az;
@@ -731,7 +732,7 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
         const float ux = (float)(int)(np.x - xr.x) * qs0;
         const float uy = (float)(int)(np.y - xr.y) * qs1;
         const float uz = (float)(int)(np.z - xr.z) * qs2;
-        moved = fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > (PC ? __ldcg(&C.dmax2f) : P.dmax2f);
+        if (fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > (PC ? __ldcg(&C.dmax2f) : P.dmax2f)) sm.sviol = 1;
         const Real ke = (Real)0.5 * (F32 ? (Real)P.massf : (Real)P.mass) * fmr(v.x, v.x, fmr(v.y, v.y, v.z * v.z));
         if (grp == 0) e0 = ke; else e1 = ke;
         if (PC) {
@@ -759,36 +760,39 @@ __device__ void nl_step_item(const SysDev &S, int k0, int par, int *viol, const 
             }
         }
     }
-    // the warp's kinetic energy: its beads' values (their first lanes) in a
-    // fixed shuffle tree, then integer slot sums (order-free); and whether
-    // one of its beads moved too far.  Warps end on their own: an item has
-    // no barrier after its last use of the group's tables (the next item
-    // that loads tables waits for the group first)
-    Real k0s = e0, k1s = e1;
+    if (gl == 0) { sm.kered[0][il] = e0; sm.kered[1][il] = e1; }
+    g.sync();
+    if (t < 32) {
+        // the item's kinetic energy (fixed-order sums)
+        Real k0s = 0, k1s = 0;
+        for (int q = t; q < NL_BEADS; q += 32) { k0s += sm.kered[0][q]; k1s += sm.kered[1][q]; }
 #pragma unroll
-    for (int o = NL_G; o < 32; o <<= 1) {
-        k0s += __shfl_xor_sync(0xffffffffu, k0s, o);
-        k1s += __shfl_xor_sync(0xffffffffu, k1s, o);
-    }
-    const bool wmoved = __any_sync(0xffffffffu, moved);
-    if ((t & 31) == 0) {
-        // FP32 warps at 2^16 units per kJ/mol through a 32-bit conversion (a
-        // warp holds far less than 2^15 kJ/mol), FP64 warps at 2^32 units
-        long long *ks = C.ke_slot[par][((k0 / NL_BEADS) * (GRP / 32) + t / 32) % KE_SLOTS];
-        long long u0, u1;
-        if (F32) {
-            const float lim = 32768.f;
-            if (!(fabsf((float)k0s) < lim && fabsf((float)k1s) < lim)) atomicOr(&C.err, ERR_NONFINITE);
-            u0 = __float2int_rn(fminf(fmaxf((float)k0s, -lim), lim) * 65536.f);
-            u1 = __float2int_rn(fminf(fmaxf((float)k1s, -lim), lim) * 65536.f);
-        } else {
-            u0 = to_fix(k0s);
-            u1 = to_fix(k1s);
+        for (int o = 16; o > 0; o >>= 1) {
+            k0s += __shfl_xor_sync(0xffffffffu, k0s, o);
+            k1s += __shfl_xor_sync(0xffffffffu, k1s, o);
         }
-        atomicAdd((unsigned long long *)&ks[0], (unsigned long long)u0);
-        atomicAdd((unsigned long long *)&ks[1], (unsigned long long)u1);
-        if (wmoved) atomicOr(viol, 1);
+        if (t == 0) {
+            // integer slot sums (order-free): FP32 items at 2^16 units per
+            // kJ/mol through a 32-bit conversion (an item holds far less than
+            // 2^15 kJ/mol), FP64 items at 2^32 units
+            long long *ks = C.ke_slot[par][(k0 / NL_BEADS) % KE_SLOTS];
+            long long u0, u1;
+            if (F32) {
+                const float lim = 32768.f;
+                if (!(fabsf((float)k0s) < lim && fabsf((float)k1s) < lim)) atomicOr(&C.err, ERR_NONFINITE);
+                u0 = __float2int_rn(fminf(fmaxf((float)k0s, -lim), lim) * 65536.f);
+                u1 = __float2int_rn(fminf(fmaxf((float)k1s, -lim), lim) * 65536.f);
+            } else {
+                u0 = to_fix(k0s);
+                u1 = to_fix(k1s);
+            }
+            atomicAdd((unsigned long long *)&ks[0], (unsigned long long)u0);
+            atomicAdd((unsigned long long *)&ks[1], (unsigned long long)u1);
+            if (sm.sviol) atomicOr(viol, 1);
+            sm.sviol = 0;                      // for the group's next item
+        }
     }
+    g.sync();
 }
 
 // After a step of system S (one warp, all items done): kinetic energy from
@@ -908,9 +912,8 @@ __global__ void __launch_bounds__(GRP, 8) k_nl_step(const SysDev *__restrict__ s
     Counters &C = *S.c;
     const int par = C.nl_par;
     nl_step_item<Real, LAM, G>(S, bm.y, par, &C.nl_viol, Grp{(int)threadIdx.x, 1}, sm);
-    __threadfence();                           // every warp's slot sums, before the block's ticket
-    __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const unsigned nblk = (unsigned)((S.p->n + NL_BLOCK / G - 1) / (NL_BLOCK / G));
         last = atomicAdd(&C.sticket, 1u) == nblk - 1;
     }
