@@ -1531,9 +1531,24 @@ mdas_status mdas_set_state(mdas_system *s, const mdas_state_view *in) {
     if (keep_list) c.nl_par = 0;
     CK(cudaMemcpyAsync(s->hs.c, &c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
     if (keep_list) {
-        // the list as it was built (same positions, same order), then the
-        // current positions in its list-order buffer
+        // the list as it was built (same positions, same order, and under
+        // pressure coupling the same box: the build's distances in nm follow
+        // the box), then the current positions in its list-order buffer
+        bool other_box = false;
+        for (int k = 0; k < 3; ++k) other_box |= in->list_box[0] > 0 && in->list_box[k] != s->hp.box[k];
+        Params lp = s->hp;
+        if (other_box) {
+            for (int k = 0; k < 3; ++k) {
+                if (!(in->list_box[k] >= s->hp.pc_lmin[k]) || !std::isfinite(in->list_box[k]))
+                    return fail(s, MDAS_ERR_INVALID_ARG, "set_state: list_box");
+                box_params(lp, k, in->list_box[k]);
+            }
+            CK(cudaMemcpyAsync(const_cast<Params *>(s->hs.p), &lp, sizeof(Params), cudaMemcpyHostToDevice, s->stream));
+        }
         launch_nl_build(s->solo->ctx());
+        if (other_box)
+            CK(cudaMemcpyAsync(const_cast<Params *>(s->hs.p), &s->hp, sizeof(Params), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
         s->list_lanes = s->solo->lanes;
         CK(cudaMemcpyAsync(s->hs.pos, pos.data(), 16ull * n, cudaMemcpyHostToDevice, s->stream));
         k_list_current<<<(n + 255) / 256, 256, 0, s->stream>>>(s->hs, n, 0);
