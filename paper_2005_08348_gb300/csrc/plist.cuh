@@ -1027,6 +1027,34 @@ static __device__ bool any_flag(const RunArgs &a, int which, int s) {
     return r;
 }
 
+// A grid barrier after which thread 0 reads the systems' list flags `which`
+// of step s together with the abort word (one round trip after the barrier's
+// fence instead of two); *flag is the same in every block.
+static __device__ bool grid_barrier_flag(RunSync *rs, BarState &bs, const RunArgs &a, int which, int s, bool *flag) {
+    __shared__ int ok, need;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned target = bs.base + (++bs.n) * gridDim.x;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&rs->count) : "memory");
+        int good = 1;
+        for (long long it = 0; (int)(ld_relaxed32(&rs->count) - target) < 0; ++it) {
+            if (it > (1ll << 23) || *(volatile int *)&rs->abort) {
+                atomicOr(&rs->abort, ERR_TIMEOUT);
+                good = 0;
+                break;
+            }
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        int v = 0;
+        for (int q = 0; q < a.n_sys; ++q) v |= build_flag(*a.sys[q].c, which, s);
+        need = v;
+        ok = good && !*(volatile int *)&rs->abort;
+    }
+    __syncthreads();
+    *flag = need != 0;
+    return ok;
+}
+
 // List build of every system whose flag is set; buffer (nl_par + b) & 1 holds
 // the current positions.  Three barriers.
 template <int NG>
@@ -1281,8 +1309,8 @@ __global__ void __launch_bounds__(RUN_THREADS, 1) k_md_run(RunArgs a) {
                 C.nl_violp[(s + 1) % 3] = 0;
                 if (s == 0) C.nl_stale = 0;
             }
-        if (!grid_barrier(a.rs, bs)) return;
-        const bool rebuild = any_flag(a, 1, s);
+        bool rebuild;
+        if (!grid_barrier_flag(a.rs, bs, a, 1, s, &rebuild)) return;
         if (rebuild) {
             if (!run_build<G>(a, 1, s, s + 1, g, gid, ngr, bsm, bs)) return;
             tab_sys = -1;                      // the build used the same shared memory
