@@ -837,6 +837,10 @@ mdas_status mdas_create_system(const mdas_system_desc *d, mdas_system **out) {
         P.n_lcells = ld.n_lcells;
         for (int k = 0; k < 3; ++k) P.pc_lmin[k] = std::max(P.nc[k] * d->rc, ld.ln[k] * P.rl);
         P.lcapc = ld.lcapc;
+        if (P.lcapc > NLB_BEADS * 32767) {     // a cell's build tasks are counted in 15 bits
+            delete s;
+            return fail(nullptr, MDAS_ERR_INVALID_ARG, "create: too many beads in a list-build cell");
+        }
         P.lcap = ld.lcap;
         P.npad = ld.npad;
         P.mark_words = (n + NL_BEADS_MIN - 1) / NL_BEADS_MIN / 32 + 1;
